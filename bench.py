@@ -1,0 +1,347 @@
+"""Throughput of the fused RD3Q41 collide-and-stream update on GB300.
+
+One step = one fused pull update (stream + moments + energy-conserving
+equilibrium + BGK) of every node of the grid: one kernel launch.
+
+Default workload: 512^3 periodic bcc grid (2 * 512^3 nodes), thermoacoustic
+case (Gaussian density pulse of amplitude 1e-2, sigma = 8 cells, at the
+centre, plus a seeded 16^3-Fourier-box temperature perturbation of max 1e-3),
+nu = 0.01, FP32 arithmetic with populations stored as FP16 deviations
+h = f/w - 1.  The other storage precisions are timed on the same workload and
+reported under "by_precision".
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--n 512] [--precision f16]
+For N > 1 (torchrun), every rank runs an independent replica (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+DTYPE_NAME = {"f64": "f64", "f32": "f32", "f16": "f32 (f16 storage)", "bf16": "f32 (bf16 storage)"}
+NU = 0.01
+STEP_KERNEL_SOURCES = ["lb_common.cuh", "lb_kernels.cuh", "lb_step_f32.cu", "lb_step_f64.cu"]
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=512)
+    p.add_argument("--precision", default="f16", choices=list(BYTES))
+    p.add_argument("--no-secondary", action="store_true", help="skip the other storage precisions")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in STEP_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1909_08406_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic(precision, n):
+    """dram read+write bytes per launch of the step kernel from the committed ncu
+    summary, if it was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    e = d.get(precision)
+    if not e or e.get("kernel_hash") != kernel_hash():
+        return None
+    # scale a smaller capture to this grid by the node count (traffic ~ nodes)
+    return e["dram_bytes_per_launch"] * (2 * n ** 3) / e["nodes"]
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.file.flush()
+        with open(self.file.name) as fh:
+            rows = [r.strip().split(", ") for r in fh if r.strip()]
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def time_steps(lb, ctx, torch, steps, warmup):
+    """Per-launch device times (ms) of `steps` single-step launches after `warmup`."""
+    for _ in range(warmup):
+        lb.lb_step(ctx, 1)
+    lb.lb_sync(ctx)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(stream)
+    for k in range(steps):
+        lb.lb_step(ctx, 1)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    lb.lb_sync(ctx)
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    return ev[0].elapsed_time(ev[-1]), per
+
+
+def cpu_oracle_sample(n_box, target_s=10.0, max_steps=20):
+    """The FP64 oracle, as it stands, on a periodic n_box^3 box of the same workload
+    recipe, for as many steps as fit in about target_s seconds (at least 1)."""
+    import oracle
+    from paper_1909_08406_gb300 import workloads as wl
+    th0 = oracle.theta0()
+    sigma = 8.0 * n_box / 512.0 if n_box < 512 else 8.0
+    fl = wl.thermoacoustic_pulse(n_box, th0, sigma=max(sigma, 2.0), kmax=min(8, n_box // 4))
+    f = oracle.init_fields(fl["rho"].numpy(), fl["u"].numpy(), fl["theta"].numpy())
+    tau = NU / th0
+    t0 = time.perf_counter()
+    f = oracle.step(f, tau, 1)
+    one = time.perf_counter() - t0
+    steps = max(1, min(max_steps, int(target_s / max(one, 1e-9)) - 1))
+    t0 = time.perf_counter()
+    f = oracle.step(f, tau, steps)
+    el = time.perf_counter() - t0
+    nodes = 2 * n_box ** 3
+    return {"mlups": nodes * steps / el / 1e6, "cores": oracle.max_threads(), "steps": steps, "seconds": el,
+            "nodes": nodes}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    box = 64
+    import oracle
+    from paper_1909_08406_gb300 import workloads as wl
+    th0 = oracle.theta0()
+    fl = wl.thermoacoustic_pulse(box, th0, sigma=2.0, kmax=8)
+    f = oracle.init_fields(fl["rho"].numpy(), fl["u"].numpy(), fl["theta"].numpy())
+    tau = NU / th0
+    f = oracle.step(f, tau, max(args.warmup, 0))
+    steps = max(1, args.steps)
+    t0 = time.perf_counter()
+    f = oracle.step(f, tau, steps)
+    el = time.perf_counter() - t0
+    nodes = 2 * box ** 3
+    v = nodes * steps / el / 1e6
+    sample = (f"{box}^3 periodic box of the thermoacoustic recipe (sigma 2 cells), FP64 oracle, "
+              f"{steps} steps after {args.warmup} warm-up steps")
+    line = {"impl": "reference", "metric": "MLUPS", "value": v, "unit": "MLUPS", "n_gpus": world, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"thermoacoustic {args.n}^3 (reference arm: bounded {box}^3 sample)"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1909_08406_gb300 import lb
+    from paper_1909_08406_gb300 import workloads as wl
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    n = args.n
+    nodes = 2 * n ** 3
+    th0 = lb.lb_theta0()
+    tau = NU / th0
+
+    # CPU baseline first (rank 0, N = 1 only): plain C oracle, no GPU involved.
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        box = 96 if n >= 96 else n
+        cpu = cpu_oracle_sample(box)
+
+    fields = wl.thermoacoustic_pulse(n, th0, device="cuda")
+    precs = [args.precision] + ([] if args.no_secondary else [p for p in ("f32", "bf16", "f16", "f64")
+                                                              if p != args.precision])
+    results = {}
+    clocks = None
+    for prec in precs:
+        head = prec == args.precision
+        steps = args.steps if head else (max(3, args.steps // 10) if prec == "f64" else max(5, args.steps // 2))
+        warm = args.warmup if head else 3
+        ctx = lb.lb_init((n, n, n), tau, prec)
+        try:
+            lb.lb_set_fields(ctx, fields["rho"], fields["u"], fields["theta"])
+            lb.lb_sync(ctx)
+            barrier()
+            torch.cuda.synchronize()
+            sampler = ClockSampler(local) if head else None
+            if sampler:
+                sampler.__enter__()
+            total_ms, per = time_steps(lb, ctx, torch, steps, warm)
+            if sampler:
+                sampler.__exit__(None, None, None)
+                clocks = sampler.summary()
+            barrier()
+            total_ms = max_over_ranks(total_ms)
+            alg = nodes * 41 * 2 * BYTES[prec]
+            avg_ms = sum(per) / len(per)
+            results[prec] = {"mlups": world * nodes * steps / (total_ms * 1e-3) / 1e6,
+                             "ms_per_step": total_ms / steps, "kernel_ms": avg_ms,
+                             "achieved_gbs": alg / (avg_ms * 1e-3) / 1e9, "alg_bytes_per_launch": alg,
+                             "steps": steps, "warmup": warm}
+        finally:
+            lb.lb_destroy(ctx)
+        torch.cuda.empty_cache()
+
+    # end to end through the C ABI with host buffers: upload fields, K steps, read back all fields
+    e2e = None
+    if not args.no_e2e:
+        prec = args.precision
+        host = {k: torch.empty(v.shape, dtype=torch.float64, pin_memory=True) for k, v in fields.items()}
+        for k in host:
+            host[k].copy_(fields[k])
+        del fields
+        torch.cuda.empty_cache()
+        ctx = lb.lb_init((n, n, n), tau, prec)
+        try:
+            lb.lb_set_fields(ctx, host["rho"], host["u"], host["theta"])
+            lb.lb_step(ctx, 2)
+            lb.lb_sync(ctx)
+            barrier()
+            t0 = time.perf_counter()
+            lb.lb_set_fields(ctx, host["rho"], host["u"], host["theta"])
+            lb.lb_step(ctx, args.steps)
+            lb.lb_get_moments(ctx, host["rho"], host["u"], host["theta"])
+            lb.lb_sync(ctx)
+            el = max_over_ranks(time.perf_counter() - t0)
+        finally:
+            lb.lb_destroy(ctx)
+        io = 5 * nodes * 8
+        e2e = {"value": world * nodes * args.steps / el / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": io / args.steps, "d2h_bytes_per_step": io / args.steps,
+               "seconds": el, "note": "lb_set_fields from pinned host (rho,u,theta f64), "
+                                      "K x lb_step, lb_get_moments to pinned host"}
+
+    if rank != 0:
+        return
+    r = results[args.precision]
+    peak, peak_kind = measured_peaks()
+    traffic = ncu_traffic(args.precision, n)
+    line = {
+        "metric": "MLUPS", "value": r["mlups"], "unit": "MLUPS", "n_gpus": world, "steps": r["steps"],
+        "warmup": r["warmup"], "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPE_NAME[args.precision], "data": "synthetic",
+        "config": {"workload": f"thermoacoustic pulse, {n}^3 periodic bcc grid ({nodes} nodes), nu = {NU}, "
+                               f"{args.precision} storage", "grid": n, "nodes": nodes, "precision": args.precision,
+                   "l2": "inputs larger than L2 (population buffers of "
+                         f"{nodes * 41 * BYTES[args.precision] / 1e9:.1f} GB each)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": r["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                     "frac": r["achieved_gbs"] / peak, "traffic": traffic, "peak_kind": peak_kind,
+                     "kernel": f"k_step<{args.precision}>", "alg_bytes_per_launch": r["alg_bytes_per_launch"]},
+        "by_precision": {p: {"mlups": v["mlups"], "achieved_gbs": v["achieved_gbs"],
+                             "frac_of_hbm": v["achieved_gbs"] / peak, "ms_per_step": v["ms_per_step"],
+                             "steps": v["steps"]} for p, v in results.items()},
+        "gpu_launches": r["steps"],
+        "clocks": clocks,
+        "e2e": e2e,
+        "cpu_baseline": None if cpu is None else {
+            "value": cpu["mlups"], "unit": "MLUPS", "cores": cpu["cores"], "kind": "oracle",
+            "sample": f"FP64 oracle on a {round((cpu['nodes'] / 2) ** (1 / 3))}^3 periodic box of the same "
+                      f"thermoacoustic recipe, {cpu['steps']} steps ({cpu['seconds']:.1f} s)"},
+        "kernel_hash": kernel_hash(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

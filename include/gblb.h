@@ -1,0 +1,155 @@
+/*
+ * gblb — RD3Q41 energy-conserving crystallographic lattice Boltzmann solver
+ * for NVIDIA GB300 (sm_103a).  C ABI.
+ *
+ * Model (Kolluru, Atif, Namburi, Ansumali, arXiv:1909.08406):
+ *   - 41 discrete velocities in five energy shells plus rest (Sec. IV,
+ *     Table I): sc-1 (+-1,0,0), sc-2 (+-2,0,0), fcc-1 (+-1,+-1,0),
+ *     bcc-1 (+-1,+-1,+-1), bcc-1/2 (+-1/2,+-1/2,+-1/2); w_0 = 1 - sum of the
+ *     others and theta_0 = sum_i w_i c_ix^2 (Sec. III, Eq. allWeights).
+ *   - bcc grid: two simple-cubic sub-lattices A (integer positions) and B
+ *     (offset by (1/2,1/2,1/2)) (Sec. IV).  A grid of nx*ny*nz cells has
+ *     2*nx*ny*nz nodes and is periodic in every direction.
+ *   - discrete BGK update f_i(x + c_i, t + 1) = f_i + 2 beta (f_i^eq - f_i),
+ *     beta = 1 / (2 tau + 1) (Sec. II), with the energy-conserving
+ *     equilibrium of Sec. V, Eq. (feqGenU3): the rest-state equilibrium to
+ *     O(eta^3), eta = theta/theta_0 - 1, times the velocity series with
+ *     M_2, M_2', A_1, A_2.  M_2 and M_2' are evaluated exactly from the
+ *     weights.  Unless LB_FLAG_PAPER_LITERAL is given, the equilibrium also
+ *     carries the momentum projection f~_i c_i . dj / (rho theta) that
+ *     makes momentum an exact collision invariant (the printed series
+ *     misses it at O(u^3 eta^2)).
+ *   - kinematic viscosity nu = tau theta_0; thermal diffusivity = nu
+ *     (Prandtl number 1); isentropic sound speed sqrt(5 theta_0 / 3).
+ *
+ * Array layouts (all C order, x fastest):
+ *   scalar field   a[s][nz][ny][nx]            s = 0 (A), 1 (B)
+ *   velocity       u[3][s][nz][ny][nx]         component-major
+ *   populations    f[s][41][nz][ny][nx]        velocity order of lb_velocity_set
+ * Scalar fields and populations crossing this interface are float64.
+ *
+ * Ownership: the context owns every device buffer it allocates (population
+ * buffers, reduction partials, staging) and frees them in lb_destroy.  Caller
+ * buffers stay the caller's: they are read or written during the call (or, for
+ * device pointers, by work the call enqueues on the context's stream) and
+ * never retained.  "on_device" != 0 means the pointer is device memory of the
+ * context's GPU; 0 means host memory (pageable or pinned).
+ *
+ * Streams and errors: work is enqueued on the stream given to lb_init (NULL =
+ * the legacy default stream).  Calls that return data to the host synchronise
+ * that stream.  Every call returns an lb_status; lb_last_error gives a
+ * message.  A device-side error word is set when a node's density or
+ * temperature becomes non-positive or non-finite; it is sticky and is reported
+ * as LB_ERR_UNSTABLE by lb_sync and every synchronising call.
+ */
+#ifndef GBLB_H
+#define GBLB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_ctx lb_ctx;
+
+typedef enum {
+    LB_OK = 0,
+    LB_ERR_ARG = -1,      /* invalid argument (null pointer, size, enum)            */
+    LB_ERR_OOM = -2,      /* device or host allocation failed                        */
+    LB_ERR_CUDA = -3,     /* a CUDA runtime call failed (message in lb_last_error)   */
+    LB_ERR_THETA0 = -4,   /* theta0 argument disagrees with the weights             */
+    LB_ERR_UNSTABLE = -5, /* a node reached rho <= 0, theta <= 0 or a non-finite value */
+    LB_ERR_TIMEOUT = -6,  /* a bounded device wait gave up                           */
+    LB_ERR_STATE = -7     /* call not valid in the current state                    */
+} lb_status;
+
+typedef enum {
+    LB_F64 = 0,      /* FP64 arithmetic, populations stored as FP64 f_i                 */
+    LB_F32 = 1,      /* FP32 arithmetic, stored as FP32 h_i = f_i / w_i - 1              */
+    LB_F32_S16F = 2, /* FP32 arithmetic, stored as FP16 h_i (round to nearest even)     */
+    LB_F32_S16B = 3  /* FP32 arithmetic, stored as BF16 h_i (round to nearest even)     */
+} lb_precision;
+
+#define LB_RD3Q41 41
+
+/* lb_init flags */
+#define LB_FLAG_PAPER_LITERAL 1u /* equilibrium exactly as printed (no momentum projection) */
+
+typedef struct {
+    int64_t nx, ny, nz; /* simple-cubic cells per axis, each >= 1; nodes = 2 nx ny nz */
+} lb_grid;
+
+/* Velocity set of the library, in its population order (pairs +c, -c at
+ * indices 2k+1, 2k+2; index 0 is rest).  c2 receives 41*3 doubled components
+ * 2 c_i (integers), w receives the 41 weights (Table I; w_0 derived).  Either
+ * pointer may be NULL. */
+lb_status lb_velocity_set(int *c2, double *w);
+
+/* Reference temperature theta_0 = sum_i w_i c_ix^2 from the Table I weights. */
+double lb_theta0(void);
+
+/* Create a solver context.
+ *   grid          cells per axis (each 1 .. 2^30, total nodes < 2^40)
+ *   velocity_set  must be LB_RD3Q41
+ *   theta0        <= 0: use the derived theta_0; otherwise it must equal the
+ *                 derived value to 1e-12 relative, else LB_ERR_THETA0
+ *   tau           mean free time, > 0 (beta = 1/(2 tau + 1)); +inf gives
+ *                 beta = 0 (free streaming, collision is the identity)
+ *   precision     lb_precision
+ *   flags         LB_FLAG_* bits
+ *   cuda_stream   cudaStream_t to enqueue on (NULL = legacy default stream)
+ * Allocates two population buffers of 2*41*nodes/2 elements of the storage
+ * type.  The populations are zero until lb_set_fields / lb_set_populations. */
+lb_status lb_init(lb_ctx **out, lb_grid grid, int velocity_set, double theta0, double tau, lb_precision precision,
+                  unsigned flags, void *cuda_stream);
+
+/* Replace the stream the context enqueues on. */
+lb_status lb_set_stream(lb_ctx *ctx, void *cuda_stream);
+
+/* Set the populations to the equilibrium (Eq. feqGenU3) of the given fields:
+ * rho[s][z][y][x], u[3][s][z][y][x], theta[s][z][y][x] (float64).  The stored
+ * state is then the post-collision state at t = 0. */
+lb_status lb_set_fields(lb_ctx *ctx, const double *rho, const double *u, const double *theta, int on_device);
+
+/* Advance n >= 0 time steps: each step streams (pull) and collides every node
+ * in one fused kernel.  Asynchronous on the context's stream. */
+lb_status lb_step(lb_ctx *ctx, int64_t n);
+
+/* Node moments of the current state: rho, u = j/rho, theta = (<f,c^2>/rho - u^2)/3
+ * (Sec. II), into caller arrays in the field layouts above.  Any output
+ * pointer may be NULL. */
+lb_status lb_get_moments(lb_ctx *ctx, double *rho, double *u, double *theta, int on_device);
+
+/* Global sums in FP64, deterministic order: out[0] = mass sum <f,1>,
+ * out[1..3] = momentum sum <f,c>, out[4] = energy sum <f,c^2/2>.  out is host memory. */
+lb_status lb_conserved(lb_ctx *ctx, double out[5]);
+
+/* Current (post-collision) populations as float64 f_i in the population
+ * layout.  lb_set_populations stores them (rounded to the storage type). */
+lb_status lb_get_populations(lb_ctx *ctx, double *f, int on_device);
+lb_status lb_set_populations(lb_ctx *ctx, const double *f, int on_device);
+
+/* Raw storage (checkpoint / restart): lb_state_bytes bytes, layout
+ * [s][41][nz][ny][nx] of the storage type (f64 f_i, or h_i = f_i/w_i - 1 as
+ * f32 / f16 / bf16).  Restoring a saved state reproduces the run bit for bit. */
+int64_t lb_state_bytes(const lb_ctx *ctx);
+lb_status lb_get_state(lb_ctx *ctx, void *raw, int on_device);
+lb_status lb_set_state(lb_ctx *ctx, const void *raw, int on_device);
+
+/* Number of time steps taken since the last lb_set_fields / lb_set_populations / lb_set_state. */
+int64_t lb_time(const lb_ctx *ctx);
+
+/* Wait for the context's stream; report the sticky device error word. */
+lb_status lb_sync(lb_ctx *ctx);
+
+lb_status lb_destroy(lb_ctx *ctx);
+
+/* Message for the last failing call on ctx (or for a failing lb_init when ctx is NULL). */
+const char *lb_last_error(const lb_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBLB_H */

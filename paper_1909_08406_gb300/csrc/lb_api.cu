@@ -1,0 +1,452 @@
+// C ABI of the RD3Q41 solver (declared in include/gblb.h): context
+// management, host/device transfers and the time-step loop.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "gblb.h"
+#include "lb_launch.h"
+
+using namespace gblb;
+
+// Table I of the paper (Sec. IV): weight of one velocity of each moving shell.
+static const double kTableI[5] = {
+    0.04743040745116578,  // sc-1
+    0.00165687664501576,  // sc-2
+    0.00651175327832464,  // fcc-1
+    0.00454087801154440,  // bcc-1
+    0.04917980624482672,  // bcc-1/2
+};
+
+struct Lattice {
+    LaunchConsts lc;
+    double theta0;
+};
+
+// Lattice constants from Table I.  w_0 = 1 - sum of the other weights and
+// theta_0 = sum_i w_i c_ix^2 (Sec. III, Eq. allWeights).  The rest-state
+// equilibrium polynomial (Sec. V) per shell: with s = c^2/theta_0,
+//   f~/(w rho) = 1 + eta (s-3)/2 + eta^2 (s^2-10s+15)/8 + eta^3 (s^3-21s^2+105s-105)/48.
+// M_2 = <f~, c^2 c_x^2>/(5 rho theta^2) - 1 and M_2' = <f~, c_x^2 c_y^2>/(rho theta^2) - 1
+// are cubic polynomials in eta divided by (1+eta)^2; their coefficients are
+// summed here exactly over the lattice, once, in FP64.
+static Lattice make_lattice() {
+    Lattice L;
+    double w41[kQ];
+    double sum = 0.0;
+    for (int i = 1; i < kQ; ++i) {
+        w41[i] = kTableI[vel(i).shell - 1];
+        sum += w41[i];
+    }
+    w41[0] = 1.0 - sum;
+    double th0 = 0.0;
+    for (int i = 0; i < kQ; ++i) th0 += w41[i] * (0.5 * vel(i).x) * (0.5 * vel(i).x);
+    L.theta0 = th0;
+    Consts<double> k;
+    memset(&k, 0, sizeof k);
+    double pk[kShells][4];
+    for (int s = 0; s < kShells; ++s) {
+        int first = -1;
+        for (int i = 0; i < kQ; ++i)
+            if (vel(i).shell == s && first < 0) first = i;
+        const Vel c = vel(first);
+        const double csq = 0.25 * (c.x * c.x + c.y * c.y + c.z * c.z);
+        const double st = csq / th0;
+        k.w[s] = w41[first];
+        k.c2[s] = csq;
+        k.p1[s] = 0.5 * (st - 3.0);
+        k.p2[s] = (st * st - 10.0 * st + 15.0) / 8.0;
+        k.p3[s] = (st * st * st - 21.0 * st * st + 105.0 * st - 105.0) / 48.0;
+        pk[s][0] = 1.0;
+        pk[s][1] = k.p1[s];
+        pk[s][2] = k.p2[s];
+        pk[s][3] = k.p3[s];
+        for (int i = 0; i < kQ; ++i) {
+            if (vel(i).shell != s) continue;
+            const double cx = 0.5 * vel(i).x, cy = 0.5 * vel(i).y;
+            k.n2[s] += cx * cx;
+            k.n4[s] += cx * cx * cx * cx;
+            k.n22[s] += cx * cx * cy * cy;
+        }
+    }
+    double A[4] = {0, 0, 0, 0}, B[4] = {0, 0, 0, 0};
+    for (int i = 0; i < kQ; ++i) {
+        const Vel c = vel(i);
+        const double cx = 0.5 * c.x, cy = 0.5 * c.y, cz = 0.5 * c.z;
+        const double csq = cx * cx + cy * cy + cz * cz;
+        for (int p = 0; p < 4; ++p) {
+            A[p] += w41[i] * csq * cx * cx * pk[c.shell][p];
+            B[p] += w41[i] * cx * cx * cy * cy * pk[c.shell][p];
+        }
+    }
+    const double t2 = th0 * th0;
+    const double one_two_one[4] = {1.0, 2.0, 1.0, 0.0};  // (1 + eta)^2
+    for (int p = 0; p < 4; ++p) {
+        k.m2[p] = A[p] / (5.0 * t2) - one_two_one[p];
+        k.m2p[p] = B[p] / t2 - one_two_one[p];
+    }
+    k.theta0 = th0;
+    k.inv_3theta0 = 1.0 / (3.0 * th0);
+    L.lc.kd = k;
+    Consts<float>& f = L.lc.kf;
+    for (int s = 0; s < kShells; ++s) {
+        f.w[s] = (float)k.w[s];
+        f.c2[s] = (float)k.c2[s];
+        f.p1[s] = (float)k.p1[s];
+        f.p2[s] = (float)k.p2[s];
+        f.p3[s] = (float)k.p3[s];
+        f.n2[s] = (float)k.n2[s];
+        f.n4[s] = (float)k.n4[s];
+        f.n22[s] = (float)k.n22[s];
+    }
+    for (int p = 0; p < 4; ++p) {
+        f.m2[p] = (float)k.m2[p];
+        f.m2p[p] = (float)k.m2p[p];
+    }
+    f.theta0 = (float)th0;
+    f.inv_3theta0 = (float)(1.0 / (3.0 * th0));
+    for (int i = 0; i < kQ; ++i) L.lc.w41.w[i] = w41[i];
+    L.lc.theta0 = th0;
+    return L;
+}
+
+static const Lattice& lattice() {
+    static const Lattice L = make_lattice();
+    return L;
+}
+
+struct lb_ctx {
+    lb_grid g;
+    Dims d;
+    int prec;
+    bool project;
+    double tau, twobeta;
+    cudaStream_t stream;
+    int device;
+    void* buf[2];
+    int cur;
+    size_t esize;
+    int* d_err;
+    double* d_partials;
+    int nblocks;
+    double* d_out5;
+    double* d_stage;
+    int64_t stage_doubles;
+    int64_t time;
+    std::string msg;
+};
+
+static std::string g_init_msg;
+
+static lb_status fail(lb_ctx* c, lb_status s, const std::string& m) {
+    if (c)
+        c->msg = m;
+    else
+        g_init_msg = m;
+    return s;
+}
+
+#define CK(ctx, call)                                                                                 \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA,              \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                          \
+    } while (0)
+
+static int64_t nodes_of(const lb_ctx* c) { return 2 * c->d.plane; }
+
+// Staging buffer for host transfers (float64), allocated on first use.
+static lb_status ensure_stage(lb_ctx* c) {
+    if (c->d_stage) return LB_OK;
+    const int64_t total = 2 * kQ * c->d.plane;
+    int64_t want = (int64_t)1 << 26;  // 64 Mi doubles = 512 MiB
+    if (want > total) want = total;
+    if (want < 5) want = 5;
+    CK(c, cudaMalloc(&c->d_stage, (size_t)want * sizeof(double)));
+    c->stage_doubles = want;
+    return LB_OK;
+}
+
+extern "C" {
+
+lb_status lb_velocity_set(int* c2, double* w) {
+    const Lattice& L = lattice();
+    for (int i = 0; i < kQ; ++i) {
+        if (c2) {
+            c2[3 * i + 0] = vel(i).x;
+            c2[3 * i + 1] = vel(i).y;
+            c2[3 * i + 2] = vel(i).z;
+        }
+        if (w) w[i] = L.lc.w41.w[i];
+    }
+    return LB_OK;
+}
+
+double lb_theta0(void) { return lattice().theta0; }
+
+lb_status lb_init(lb_ctx** out, lb_grid grid, int velocity_set, double theta0, double tau, lb_precision precision,
+                  unsigned flags, void* cuda_stream) {
+    if (!out) return fail(nullptr, LB_ERR_ARG, "lb_init: out is NULL");
+    *out = nullptr;
+    if (velocity_set != LB_RD3Q41) return fail(nullptr, LB_ERR_ARG, "lb_init: only the RD3Q41 velocity set exists");
+    if (grid.nx < 1 || grid.ny < 1 || grid.nz < 1 || grid.nx > (1 << 30) || grid.ny > (1 << 30) ||
+        grid.nz > (1 << 30))
+        return fail(nullptr, LB_ERR_ARG, "lb_init: grid extents must be in [1, 2^30]");
+    if (2 * grid.ny * grid.nz > 0x7fffffffLL || (grid.nx + 127) / 128 > 65535)
+        return fail(nullptr, LB_ERR_ARG, "lb_init: grid too large for the launch geometry");
+    if (grid.nx * grid.ny > ((int64_t)1 << 40) / grid.nz)
+        return fail(nullptr, LB_ERR_ARG, "lb_init: more than 2^40 cells");
+    if ((int)precision < LB_F64 || (int)precision > LB_F32_S16B)
+        return fail(nullptr, LB_ERR_ARG, "lb_init: unknown precision");
+    if (!(tau > 0.0)) return fail(nullptr, LB_ERR_ARG, "lb_init: tau must be > 0 (or +inf)");
+    if (flags & ~LB_FLAG_PAPER_LITERAL) return fail(nullptr, LB_ERR_ARG, "lb_init: unknown flag bits");
+    const Lattice& L = lattice();
+    if (theta0 > 0.0 && fabs(theta0 / L.theta0 - 1.0) > 1e-12)
+        return fail(nullptr, LB_ERR_THETA0, "lb_init: theta0 differs from sum_i w_i c_ix^2 of the Table I weights");
+
+    lb_ctx* c = new lb_ctx();
+    c->g = grid;
+    c->d.nx = (int)grid.nx;
+    c->d.ny = (int)grid.ny;
+    c->d.nz = (int)grid.nz;
+    c->d.plane = grid.nx * grid.ny * grid.nz;
+    c->d.rows = 2 * grid.ny * grid.nz;
+    c->prec = (int)precision;
+    c->project = !(flags & LB_FLAG_PAPER_LITERAL);
+    c->tau = tau;
+    c->twobeta = isinf(tau) ? 0.0 : 2.0 / (2.0 * tau + 1.0);
+    c->stream = (cudaStream_t)cuda_stream;
+    c->esize = storage_bytes(c->prec);
+    c->cur = 0;
+    c->time = 0;
+    cudaError_t e = cudaGetDevice(&c->device);
+    int sms = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(nullptr, LB_ERR_CUDA, std::string("lb_init: ") + cudaGetErrorString(e));
+    }
+    c->nblocks = sms > 0 ? 4 * sms : 256;
+    const size_t bytes = (size_t)(2 * kQ) * (size_t)c->d.plane * c->esize;
+    void* p[2] = {nullptr, nullptr};
+    int* err = nullptr;
+    double* part = nullptr;
+    e = cudaMalloc(&p[0], bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&p[1], bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&part, (size_t)(c->nblocks * 5 + 5) * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemsetAsync(p[0], 0, bytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p[1], 0, bytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cudaFree(p[0]);
+        cudaFree(p[1]);
+        cudaFree(err);
+        cudaFree(part);
+        delete c;
+        cudaGetLastError();
+        return fail(nullptr, e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA,
+                    std::string("lb_init: ") + cudaGetErrorString(e));
+    }
+    c->buf[0] = p[0];
+    c->buf[1] = p[1];
+    c->d_err = err;
+    c->d_partials = part;
+    c->d_out5 = part + c->nblocks * 5;
+    *out = c;
+    return LB_OK;
+}
+
+lb_status lb_set_stream(lb_ctx* c, void* cuda_stream) {
+    if (!c) return LB_ERR_ARG;
+    c->stream = (cudaStream_t)cuda_stream;
+    return LB_OK;
+}
+
+lb_status lb_sync(lb_ctx* c) {
+    if (!c) return LB_ERR_ARG;
+    CK(c, cudaSetDevice(c->device));
+    CK(c, cudaStreamSynchronize(c->stream));
+    int h = 0;
+    CK(c, cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) return fail(c, LB_ERR_UNSTABLE, "a node reached rho <= 0, theta <= 0 or a non-finite moment");
+    return LB_OK;
+}
+
+lb_status lb_set_fields(lb_ctx* c, const double* rho, const double* u, const double* theta, int on_device) {
+    if (!c || !rho || !u || !theta) return fail(c, LB_ERR_ARG, "lb_set_fields: null argument");
+    CK(c, cudaSetDevice(c->device));
+    const int64_t n = nodes_of(c);
+    const LaunchConsts& lc = lattice().lc;
+    void* dst = c->buf[c->cur];
+    if (on_device) {
+        CK(c, launch_init(c->prec, c->project, dst, c->d, lc, 0, n, rho, u, n, theta, c->d_err, c->stream));
+    } else {
+        lb_status s = ensure_stage(c);
+        if (s != LB_OK) return s;
+        const int64_t chunk = c->stage_doubles / 5;
+        for (int64_t q0 = 0; q0 < n; q0 += chunk) {
+            const int64_t cnt = n - q0 < chunk ? n - q0 : chunk;
+            double* sr = c->d_stage;
+            double* su = sr + cnt;
+            double* st = su + 3 * cnt;
+            const size_t b = (size_t)cnt * sizeof(double);
+            CK(c, cudaMemcpyAsync(sr, rho + q0, b, cudaMemcpyHostToDevice, c->stream));
+            for (int k = 0; k < 3; ++k)
+                CK(c, cudaMemcpyAsync(su + k * cnt, u + k * n + q0, b, cudaMemcpyHostToDevice, c->stream));
+            CK(c, cudaMemcpyAsync(st, theta + q0, b, cudaMemcpyHostToDevice, c->stream));
+            CK(c, launch_init(c->prec, c->project, dst, c->d, lc, q0, cnt, sr, su, cnt, st, c->d_err, c->stream));
+        }
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    c->time = 0;
+    return LB_OK;
+}
+
+lb_status lb_step(lb_ctx* c, int64_t n) {
+    if (!c || n < 0) return fail(c, LB_ERR_ARG, "lb_step: bad argument");
+    CK(c, cudaSetDevice(c->device));
+    const LaunchConsts& lc = lattice().lc;
+    for (int64_t t = 0; t < n; ++t) {
+        CK(c, launch_step(c->prec, c->project, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc, c->twobeta, c->d_err,
+                          c->stream));
+        c->cur ^= 1;
+        c->time += 1;
+    }
+    return LB_OK;
+}
+
+lb_status lb_get_moments(lb_ctx* c, double* rho, double* u, double* theta, int on_device) {
+    if (!c) return LB_ERR_ARG;
+    CK(c, cudaSetDevice(c->device));
+    const int64_t n = nodes_of(c);
+    const LaunchConsts& lc = lattice().lc;
+    const void* src = c->buf[c->cur];
+    if (on_device) {
+        CK(c, launch_moments(c->prec, src, c->d, lc, 0, n, rho, u, n, theta, c->stream));
+        return LB_OK;
+    }
+    lb_status s = ensure_stage(c);
+    if (s != LB_OK) return s;
+    const int64_t chunk = c->stage_doubles / 5;
+    for (int64_t q0 = 0; q0 < n; q0 += chunk) {
+        const int64_t cnt = n - q0 < chunk ? n - q0 : chunk;
+        double* sr = c->d_stage;
+        double* su = sr + cnt;
+        double* st = su + 3 * cnt;
+        const size_t b = (size_t)cnt * sizeof(double);
+        CK(c, launch_moments(c->prec, src, c->d, lc, q0, cnt, rho ? sr : nullptr, u ? su : nullptr, cnt,
+                             theta ? st : nullptr, c->stream));
+        if (rho) CK(c, cudaMemcpyAsync(rho + q0, sr, b, cudaMemcpyDeviceToHost, c->stream));
+        if (u)
+            for (int k = 0; k < 3; ++k)
+                CK(c, cudaMemcpyAsync(u + k * n + q0, su + k * cnt, b, cudaMemcpyDeviceToHost, c->stream));
+        if (theta) CK(c, cudaMemcpyAsync(theta + q0, st, b, cudaMemcpyDeviceToHost, c->stream));
+    }
+    return lb_sync(c);
+}
+
+lb_status lb_conserved(lb_ctx* c, double out[5]) {
+    if (!c || !out) return fail(c, LB_ERR_ARG, "lb_conserved: null argument");
+    CK(c, cudaSetDevice(c->device));
+    const LaunchConsts& lc = lattice().lc;
+    CK(c, launch_conserved(c->prec, c->buf[c->cur], c->d, lc, c->d_partials, c->nblocks, c->d_out5, c->stream));
+    double s[5];
+    CK(c, cudaMemcpyAsync(s, c->d_out5, sizeof s, cudaMemcpyDeviceToHost, c->stream));
+    lb_status st = lb_sync(c);
+    if (st != LB_OK) return st;
+    const double n = (double)nodes_of(c);
+    out[0] = n + s[0];
+    out[1] = s[1];
+    out[2] = s[2];
+    out[3] = s[3];
+    out[4] = 0.5 * (3.0 * lattice().theta0 * n + s[4]);
+    return LB_OK;
+}
+
+lb_status lb_get_populations(lb_ctx* c, double* f, int on_device) {
+    if (!c || !f) return fail(c, LB_ERR_ARG, "lb_get_populations: null argument");
+    CK(c, cudaSetDevice(c->device));
+    const int64_t total = 2 * kQ * c->d.plane;
+    const LaunchConsts& lc = lattice().lc;
+    const void* src = c->buf[c->cur];
+    if (on_device) {
+        CK(c, launch_to_f64(c->prec, src, c->d, lc, 0, total, f, c->stream));
+        return LB_OK;
+    }
+    lb_status s = ensure_stage(c);
+    if (s != LB_OK) return s;
+    for (int64_t e0 = 0; e0 < total; e0 += c->stage_doubles) {
+        const int64_t cnt = total - e0 < c->stage_doubles ? total - e0 : c->stage_doubles;
+        CK(c, launch_to_f64(c->prec, src, c->d, lc, e0, cnt, c->d_stage, c->stream));
+        CK(c, cudaMemcpyAsync(f + e0, c->d_stage, (size_t)cnt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    }
+    return lb_sync(c);
+}
+
+lb_status lb_set_populations(lb_ctx* c, const double* f, int on_device) {
+    if (!c || !f) return fail(c, LB_ERR_ARG, "lb_set_populations: null argument");
+    CK(c, cudaSetDevice(c->device));
+    const int64_t total = 2 * kQ * c->d.plane;
+    const LaunchConsts& lc = lattice().lc;
+    void* dst = c->buf[c->cur];
+    if (on_device) {
+        CK(c, launch_from_f64(c->prec, f, dst, c->d, lc, 0, total, c->stream));
+    } else {
+        lb_status s = ensure_stage(c);
+        if (s != LB_OK) return s;
+        for (int64_t e0 = 0; e0 < total; e0 += c->stage_doubles) {
+            const int64_t cnt = total - e0 < c->stage_doubles ? total - e0 : c->stage_doubles;
+            CK(c, cudaMemcpyAsync(c->d_stage, f + e0, (size_t)cnt * sizeof(double), cudaMemcpyHostToDevice,
+                                  c->stream));
+            CK(c, launch_from_f64(c->prec, c->d_stage, dst, c->d, lc, e0, cnt, c->stream));
+        }
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    c->time = 0;
+    return LB_OK;
+}
+
+int64_t lb_state_bytes(const lb_ctx* c) { return c ? (int64_t)(2 * kQ) * c->d.plane * (int64_t)c->esize : -1; }
+
+lb_status lb_get_state(lb_ctx* c, void* raw, int on_device) {
+    if (!c || !raw) return fail(c, LB_ERR_ARG, "lb_get_state: null argument");
+    CK(c, cudaSetDevice(c->device));
+    CK(c, cudaMemcpyAsync(raw, c->buf[c->cur], (size_t)lb_state_bytes(c),
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (on_device) return LB_OK;
+    return lb_sync(c);
+}
+
+lb_status lb_set_state(lb_ctx* c, const void* raw, int on_device) {
+    if (!c || !raw) return fail(c, LB_ERR_ARG, "lb_set_state: null argument");
+    CK(c, cudaSetDevice(c->device));
+    CK(c, cudaMemcpyAsync(c->buf[c->cur], raw, (size_t)lb_state_bytes(c),
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    if (!on_device) CK(c, cudaStreamSynchronize(c->stream));
+    c->time = 0;
+    return LB_OK;
+}
+
+int64_t lb_time(const lb_ctx* c) { return c ? c->time : -1; }
+
+lb_status lb_destroy(lb_ctx* c) {
+    if (!c) return LB_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->buf[0]);
+    cudaFree(c->buf[1]);
+    cudaFree(c->d_err);
+    cudaFree(c->d_partials);
+    cudaFree(c->d_stage);
+    delete c;
+    return LB_OK;
+}
+
+const char* lb_last_error(const lb_ctx* c) { return c ? c->msg.c_str() : g_init_msg.c_str(); }
+
+}  // extern "C"

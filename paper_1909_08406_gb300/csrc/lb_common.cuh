@@ -1,0 +1,298 @@
+// Shared device code of the RD3Q41 solver: the velocity table, the storage
+// codecs and the fused per-node collision (moments, energy-conserving
+// equilibrium, BGK relaxation).
+//
+// Model: arXiv:1909.08406.  Velocity shells and weights: Sec. IV, Table I.
+// Moments: Sec. II.  Rest-state equilibrium to O(eta^3) and the velocity
+// series Eq. (feqGenU3): Sec. V.  BGK update: Sec. II.
+//
+// The per-node arithmetic is organised around the +-c pairs of the velocity
+// set: for a pair the equilibrium splits into an even part (shared) and an odd
+// part (sign-flipped), so each pair costs one dot product, a handful of FMAs
+// and two relaxations.  All shell-dependent quantities are folded into six
+// per-node shell constants.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+#include <utility>
+
+namespace gblb {
+
+constexpr int kQ = 41;
+constexpr int kShells = 6;  // rest, sc-1, sc-2, fcc-1, bcc-1, bcc-1/2
+
+// Doubled velocity components 2 c_i, ordered rest then +-c pairs (2k+1, 2k+2).
+struct Vel {
+    int x, y, z, shell;
+};
+
+__host__ __device__ constexpr Vel vel(int i) {
+    constexpr Vel t[kQ] = {
+        {0, 0, 0, 0},
+        // sc-1
+        {2, 0, 0, 1}, {-2, 0, 0, 1}, {0, 2, 0, 1}, {0, -2, 0, 1}, {0, 0, 2, 1}, {0, 0, -2, 1},
+        // sc-2
+        {4, 0, 0, 2}, {-4, 0, 0, 2}, {0, 4, 0, 2}, {0, -4, 0, 2}, {0, 0, 4, 2}, {0, 0, -4, 2},
+        // fcc-1
+        {2, 2, 0, 3}, {-2, -2, 0, 3}, {2, -2, 0, 3}, {-2, 2, 0, 3},
+        {2, 0, 2, 3}, {-2, 0, -2, 3}, {2, 0, -2, 3}, {-2, 0, 2, 3},
+        {0, 2, 2, 3}, {0, -2, -2, 3}, {0, 2, -2, 3}, {0, -2, 2, 3},
+        // bcc-1
+        {2, 2, 2, 4}, {-2, -2, -2, 4}, {2, 2, -2, 4}, {-2, -2, 2, 4},
+        {2, -2, 2, 4}, {-2, 2, -2, 4}, {-2, 2, 2, 4}, {2, -2, -2, 4},
+        // bcc-1/2
+        {1, 1, 1, 5}, {-1, -1, -1, 5}, {1, 1, -1, 5}, {-1, -1, 1, 5},
+        {1, -1, 1, 5}, {-1, 1, -1, 5}, {-1, 1, 1, 5}, {1, -1, -1, 5},
+    };
+    return t[i];
+}
+
+// Per-shell lattice constants in the compute type.
+template <class R>
+struct Consts {
+    R w[kShells];    // weight of one velocity of the shell
+    R c2[kShells];   // c^2 of the shell
+    R p1[kShells];   // rest equilibrium f~/(w rho) = 1 + eta p1 + eta^2 p2 + eta^3 p3
+    R p2[kShells];
+    R p3[kShells];
+    R n2[kShells];   // sum over the shell of c_x^2
+    R n4[kShells];   // sum over the shell of c_x^4
+    R n22[kShells];  // sum over the shell of c_x^2 c_y^2
+    R m2[4];         // M_2  (1+eta)^2 = m2[0] + m2[1] eta + m2[2] eta^2 + m2[3] eta^3
+    R m2p[4];        // M_2' (1+eta)^2 likewise
+    R theta0;
+    R inv_3theta0;
+};
+
+template <int... Is, class F>
+__device__ __forceinline__ void static_for_impl(std::integer_sequence<int, Is...>, F&& f) {
+    (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+    static_for_impl(std::make_integer_sequence<int, N>{}, f);
+}
+
+// ---------------------------------------------------------------------------
+// Storage codecs.  value(): stored element -> working value v (f or h);
+// dev(): deviation f - w from v; relax(): new stored element from v and
+// x = 2 beta h^eq; to_raw(): rounding to the storage type.
+// ---------------------------------------------------------------------------
+struct CodecF64 {  // stores f_i
+    using raw_t = double;
+    using R = double;
+    static constexpr bool stores_f = true;
+    static __device__ __forceinline__ R value(raw_t r) { return r; }
+    static __device__ __forceinline__ R dev(R v, R w) { return v - w; }
+    static __device__ __forceinline__ R relax(R v, R omb, R x, R w, R tb) { return fma(omb, v, w * (tb + x)); }
+    static __device__ __forceinline__ raw_t to_raw(R v) { return v; }
+};
+
+struct CodecF32 {  // stores h_i = f_i / w_i - 1
+    using raw_t = float;
+    using R = float;
+    static constexpr bool stores_f = false;
+    static __device__ __forceinline__ R value(raw_t r) { return r; }
+    static __device__ __forceinline__ R dev(R v, R w) { return w * v; }
+    static __device__ __forceinline__ R relax(R v, R omb, R x, R, R) { return fmaf(omb, v, x); }
+    static __device__ __forceinline__ raw_t to_raw(R v) { return v; }
+};
+
+struct CodecF16 {
+    using raw_t = __half;
+    using R = float;
+    static constexpr bool stores_f = false;
+    static __device__ __forceinline__ R value(raw_t r) { return __half2float(r); }
+    static __device__ __forceinline__ R dev(R v, R w) { return w * v; }
+    static __device__ __forceinline__ R relax(R v, R omb, R x, R, R) { return fmaf(omb, v, x); }
+    static __device__ __forceinline__ raw_t to_raw(R v) { return __float2half_rn(v); }
+};
+
+struct CodecBF16 {
+    using raw_t = __nv_bfloat16;
+    using R = float;
+    static constexpr bool stores_f = false;
+    static __device__ __forceinline__ R value(raw_t r) { return __bfloat162float(r); }
+    static __device__ __forceinline__ R dev(R v, R w) { return w * v; }
+    static __device__ __forceinline__ R relax(R v, R omb, R x, R, R) { return fmaf(omb, v, x); }
+    static __device__ __forceinline__ raw_t to_raw(R v) { return __float2bfloat16_rn(v); }
+};
+
+// Moments of one node from the deviations d_i = f_i - w_i (Sec. II):
+// drho = rho - 1, j = rho u, dk = <f, c^2> - 3 theta_0.
+template <class R>
+struct NodeMoments {
+    R drho, jx, jy, jz, dk;
+};
+
+template <class R>
+__device__ __forceinline__ NodeMoments<R> moments_from_dev(const R (&d)[kQ]) {
+    NodeMoments<R> m;
+    m.drho = d[0];
+    m.jx = R(0);
+    m.jy = R(0);
+    m.jz = R(0);
+    m.dk = R(0);
+    static_for<20>([&](auto K) {
+        constexpr int ip = 2 * K + 1, im = 2 * K + 2;
+        constexpr Vel c = vel(ip);
+        const R s = d[ip] + d[im];
+        const R df = d[ip] - d[im];
+        m.drho += s;
+        // c2 components are doubled: c = c2 / 2
+        if constexpr (c.x != 0) m.jx = fma(R(0.5 * c.x), df, m.jx);
+        if constexpr (c.y != 0) m.jy = fma(R(0.5 * c.y), df, m.jy);
+        if constexpr (c.z != 0) m.jz = fma(R(0.5 * c.z), df, m.jz);
+        constexpr double csq = 0.25 * (c.x * c.x + c.y * c.y + c.z * c.z);
+        m.dk = fma(R(csq), s, m.dk);
+    });
+    return m;
+}
+
+// Primitive variables of a node: rho, u, eta = theta / theta_0 - 1.
+template <class R>
+struct NodeState {
+    R drho, rho, ux, uy, uz, eta;
+};
+
+template <class R>
+__device__ __forceinline__ NodeState<R> state_from_moments(const NodeMoments<R>& m, const Consts<R>& K) {
+    NodeState<R> st;
+    st.drho = m.drho;
+    st.rho = R(1) + m.drho;
+    const R inv_rho = R(1) / st.rho;
+    st.ux = m.jx * inv_rho;
+    st.uy = m.jy * inv_rho;
+    st.uz = m.jz * inv_rho;
+    const R usq = st.ux * st.ux + st.uy * st.uy + st.uz * st.uz;
+    // theta = (<f,c^2>/rho - u^2)/3  =>  eta = (dk - 3 theta0 drho - rho u^2) / (3 theta0 rho)
+    st.eta = (m.dk - R(3) * K.theta0 * m.drho - st.rho * usq) * inv_rho * K.inv_3theta0;
+    return st;
+}
+
+template <class R>
+__device__ __forceinline__ bool state_ok(const NodeState<R>& st) {
+    // rho > 0, theta > 0 and both finite (NaN fails every comparison)
+    return st.rho > R(0) && st.rho < R(1e30) && st.eta > R(-1) && st.eta < R(1e30) && st.ux == st.ux &&
+           st.uy == st.uy && st.uz == st.uz && fabs(st.ux) < R(1e30) && fabs(st.uy) < R(1e30) &&
+           fabs(st.uz) < R(1e30);
+}
+
+// Equilibrium (Eq. feqGenU3, with the optional momentum projection) and BGK
+// relaxation of one node.  v[i] are the working values of the node's incoming
+// populations (f or h, see the codec), tb = 2 beta, omb = 1 - 2 beta.
+// sink(I, value) receives the new working value of population I.
+template <class Codec, bool PROJECT, class Sink>
+__device__ __forceinline__ void equilibrium_relax(const NodeState<typename Codec::R>& st,
+                                                  const Consts<typename Codec::R>& K, typename Codec::R tb,
+                                                  typename Codec::R omb, const typename Codec::R (&v)[kQ], Sink&& sink) {
+    using R = typename Codec::R;
+    const R rho = st.rho, eta = st.eta;
+    const R inv_1pe = R(1) / (R(1) + eta);           // theta_0 / theta
+    const R inv_theta = inv_1pe / K.theta0;          // 1 / theta
+    const R usq = st.ux * st.ux + st.uy * st.uy + st.uz * st.uz;
+    const R g = usq * inv_theta;                     // u^2 / theta
+    // M_2, M_2' from their exact polynomials; A_1, A_2 (Sec. V)
+    const R r2 = inv_1pe * inv_1pe;
+    const R M2 = (K.m2[0] + eta * (K.m2[1] + eta * (K.m2[2] + eta * K.m2[3]))) * r2;
+    const R M2p = (K.m2p[0] + eta * (K.m2p[1] + eta * (K.m2p[2] + eta * K.m2p[3]))) * r2;
+    const R A1 = R(2.5) * M2 / (R(1) + R(2.5) * M2);
+    const R A2 = R(5) * A1 * (R(1) - M2) - (R(3) + M2p - R(5) * M2);
+    // rest-state factors per shell: f~_s = w_s rho R_s, R_s - 1 = eta (p1 + eta (p2 + eta p3))
+    R rR[kShells], rRm1[kShells];
+#pragma unroll
+    for (int s = 0; s < kShells; ++s) {
+        const R Rm1 = eta * (K.p1[s] + eta * (K.p2[s] + eta * K.p3[s]));
+        rR[s] = rho + rho * Rm1;       // rho R_s
+        rRm1[s] = st.drho + rho * Rm1; // rho R_s - 1
+    }
+    // per-shell even constant C_s and odd factor D_s of the series
+    //   X_i = C_s + a^2/2 + a D_s + a^3/6,  a = u.c/theta
+    //   C_s = -g (1 - A1)/2 - g c_s^2 A1 / (6 theta),  D_s = 1 + g A2 / 6 - g c_s^2 A1 / (6 theta)
+    R Cs[kShells], Dm1[kShells];
+    const R gA1_6t = g * A1 * inv_theta * R(1.0 / 6.0);
+#pragma unroll
+    for (int s = 0; s < kShells; ++s) {
+        Cs[s] = R(-0.5) * g * (R(1) - A1) - gA1_6t * K.c2[s];
+        Dm1[s] = g * A2 * R(1.0 / 6.0) - gA1_6t * K.c2[s];
+    }
+    const R upx = st.ux * inv_theta, upy = st.uy * inv_theta, upz = st.uz * inv_theta;
+    // momentum projection v = dj / (rho theta), dj = rho u - sum_i f^eq_i c_i in closed form:
+    //   dj_a = -(u_a/theta) sum_s f~_s n2_s (D_s - 1) - [S4 u_a^3 + 3 S22 u_a (u^2 - u_a^2)] / (6 theta^3)
+    R vx = R(0), vy = R(0), vz = R(0);
+    if constexpr (PROJECT) {
+        R S = R(0), S4 = R(0), S22 = R(0);
+#pragma unroll
+        for (int s = 1; s < kShells; ++s) {
+            const R ft = K.w[s] * rR[s];
+            S = fma(ft * K.n2[s], Dm1[s], S);
+            S4 = fma(ft, K.n4[s], S4);
+            S22 = fma(ft, K.n22[s], S22);
+        }
+        const R it3 = inv_theta * inv_theta * inv_theta * R(1.0 / 6.0);
+        const R ux2 = st.ux * st.ux, uy2 = st.uy * st.uy, uz2 = st.uz * st.uz;
+        const R djx = -upx * S - it3 * st.ux * (S4 * ux2 + R(3) * S22 * (usq - ux2));
+        const R djy = -upy * S - it3 * st.uy * (S4 * uy2 + R(3) * S22 * (usq - uy2));
+        const R djz = -upz * S - it3 * st.uz * (S4 * uz2 + R(3) * S22 * (usq - uz2));
+        const R k = inv_theta / rho;
+        vx = djx * k;
+        vy = djy * k;
+        vz = djz * k;
+    }
+    // rest population: a = 0
+    {
+        const R P0 = tb * rR[0];
+        const R x0 = fma(P0, Cs[0], tb * rRm1[0]);
+        sink(std::integral_constant<int, 0>{}, Codec::relax(v[0], omb, x0, K.w[0], tb));
+    }
+    static_for<20>([&](auto KK) {
+        constexpr int ip = 2 * KK + 1, im = 2 * KK + 2;
+        constexpr Vel c = vel(ip);
+        constexpr int s = c.shell;
+        const R P = tb * rR[s];
+        const R B = fma(P, Cs[s], tb * rRm1[s]);
+        const R Ds = R(1) + Dm1[s];
+        // p_s = D_s u / theta + v
+        R a = R(0), q = R(0);
+        if constexpr (c.x != 0) {
+            a = fma(R(0.5 * c.x), upx, a);
+            q = fma(R(0.5 * c.x), fma(Ds, upx, vx), q);
+        }
+        if constexpr (c.y != 0) {
+            a = fma(R(0.5 * c.y), upy, a);
+            q = fma(R(0.5 * c.y), fma(Ds, upy, vy), q);
+        }
+        if constexpr (c.z != 0) {
+            a = fma(R(0.5 * c.z), upz, a);
+            q = fma(R(0.5 * c.z), fma(Ds, upz, vz), q);
+        }
+        const R a2 = a * a;
+        const R t = fma(R(0.5) * P, a2, B);
+        const R o = fma(P * R(1.0 / 6.0), a2 * a, P * q);
+        sink(std::integral_constant<int, ip>{}, Codec::relax(v[ip], omb, t + o, K.w[s], tb));
+        sink(std::integral_constant<int, im>{}, Codec::relax(v[im], omb, t - o, K.w[s], tb));
+    });
+}
+
+// Geometry of one population buffer.
+struct Dims {
+    int nx, ny, nz;
+    int64_t plane;  // nx * ny * nz
+    int64_t rows;   // 2 * ny * nz
+};
+
+// coordinate of (a) wrapped into [0, n) for a in [-2, n + 1]
+__device__ __forceinline__ int wrap(int a, int n) {
+    a = a < 0 ? a + n : a;
+    a = a < 0 ? a + n : a;
+    a = a >= n ? a - n : a;
+    a = a >= n ? a - n : a;
+    return a;
+}
+
+}  // namespace gblb

@@ -1,0 +1,209 @@
+// Kernel templates of the RD3Q41 solver.  Each translation unit that includes
+// this header instantiates the kernels for the codecs it needs (FP32-family
+// kernels are compiled with double-precision-use warnings enabled).
+#pragma once
+
+#include "lb_common.cuh"
+#include "lb_launch.h"
+
+namespace gblb {
+
+constexpr int kStepThreads = 128;
+
+template <class T>
+__device__ __forceinline__ T ld_stream(const T* p) {
+    return __ldg(p);
+}
+
+// Fused pull update (Sec. II): node (s, z, y, x) gathers f*_i(x - c_i, t) for
+// all 41 velocities, computes its moments, the equilibrium and the BGK
+// relaxation, and writes its 41 post-collision values.  Integer links stay on
+// the sub-lattice (shifts 0, +-1, +-2 cells); the bcc-1/2 links come from the
+// other sub-lattice: for A (s = 0) a component +1/2 reads cell r - 1 and -1/2
+// reads cell r; for B (s = 1) +1/2 reads cell r and -1/2 reads cell r + 1.
+// Grid: blockIdx.x = row (s, z, y), blockIdx.y * blockDim.x + threadIdx.x = x.
+template <class Codec, bool PROJECT>
+__global__ void __launch_bounds__(kStepThreads) k_step(const typename Codec::raw_t* __restrict__ src,
+                                                       typename Codec::raw_t* __restrict__ dst, Dims d,
+                                                       Consts<typename Codec::R> K, typename Codec::R tb,
+                                                       int* __restrict__ err) {
+    using R = typename Codec::R;
+    using T = typename Codec::raw_t;
+    const int x = blockIdx.y * blockDim.x + threadIdx.x;
+    if (x >= d.nx) return;
+    const int64_t row = blockIdx.x;
+    const int y = (int)(row % d.ny);
+    const int64_t zr = row / d.ny;
+    const int z = (int)(zr % d.nz);
+    const int s = (int)(zr / d.nz);
+    const int64_t nxy = (int64_t)d.nx * d.ny;
+
+    // coordinate / offset of the upwind cell for a shift delta = k - 2 (source = x - delta)
+    int xs[5];
+    int64_t yo[5], zo[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        xs[k] = wrap(x - (k - 2), d.nx);
+        yo[k] = (int64_t)wrap(y - (k - 2), d.ny) * d.nx;
+        zo[k] = (int64_t)wrap(z - (k - 2), d.nz) * nxy;
+    }
+    // half links: component +1/2 has delta = 1 - s, component -1/2 has delta = -s
+    const int hxp = s ? xs[2] : xs[3], hxm = s ? xs[1] : xs[2];
+    const int64_t hyp = s ? yo[2] : yo[3], hym = s ? yo[1] : yo[2];
+    const int64_t hzp = s ? zo[2] : zo[3], hzm = s ? zo[1] : zo[2];
+
+    const T* same = src + (int64_t)s * kQ * d.plane;
+    const T* other = src + (int64_t)(1 - s) * kQ * d.plane;
+
+    R v[kQ];
+    static_for<kQ>([&](auto I) {
+        constexpr Vel c = vel(I);
+        if constexpr (c.shell == 5) {
+            const int64_t off = (c.z > 0 ? hzp : hzm) + (c.y > 0 ? hyp : hym) + (c.x > 0 ? hxp : hxm);
+            v[I] = Codec::value(ld_stream(other + (int64_t)I * d.plane + off));
+        } else {
+            const int64_t off = zo[c.z / 2 + 2] + yo[c.y / 2 + 2] + xs[c.x / 2 + 2];
+            v[I] = Codec::value(ld_stream(same + (int64_t)I * d.plane + off));
+        }
+    });
+
+    R dv[kQ];
+    static_for<kQ>([&](auto I) { dv[I] = Codec::dev(v[I], K.w[vel(I).shell]); });
+    const NodeMoments<R> m = moments_from_dev(dv);
+    const NodeState<R> st = state_from_moments(m, K);
+    if (!state_ok(st)) atomicOr(err, 1);
+
+    T* out = dst + (int64_t)s * kQ * d.plane + (int64_t)z * nxy + (int64_t)y * d.nx + x;
+    equilibrium_relax<Codec, PROJECT>(st, K, tb, R(1) - tb, v,
+                                      [&](auto I, R val) { out[(int64_t)I * d.plane] = Codec::to_raw(val); });
+}
+
+// Populations = equilibrium of the given float64 fields, for nodes
+// q in [q0, q0 + count), q = s * plane + (z * ny + y) * nx + x.  Field
+// pointers are indexed by q - q0 (u component c at c * ustride + q - q0).
+template <class Codec, bool PROJECT>
+__global__ void __launch_bounds__(256) k_init(typename Codec::raw_t* __restrict__ dst, Dims d, Consts<typename Codec::R> K,
+                                              double theta0, int64_t q0, int64_t count, const double* __restrict__ rho,
+                                              const double* __restrict__ u, int64_t ustride,
+                                              const double* __restrict__ theta, int* __restrict__ err) {
+    using R = typename Codec::R;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const int64_t q = q0 + k;
+    const int s = q >= d.plane;
+    const int64_t node = q - s * d.plane;
+    NodeState<R> st;
+    st.drho = (R)(rho[k] - 1.0);
+    st.rho = (R)rho[k];
+    st.ux = (R)u[k];
+    st.uy = (R)u[ustride + k];
+    st.uz = (R)u[2 * ustride + k];
+    st.eta = (R)(theta[k] / theta0 - 1.0);
+    if (!state_ok(st)) atomicOr(err, 1);
+    R zero[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) zero[i] = R(0);
+    typename Codec::raw_t* out = dst + (int64_t)s * kQ * d.plane + node;
+    equilibrium_relax<Codec, PROJECT>(st, K, R(1), R(0), zero,
+                                      [&](auto I, R val) { out[(int64_t)I * d.plane] = Codec::to_raw(val); });
+}
+
+template <class Codec>
+__device__ __forceinline__ NodeMoments<typename Codec::R> node_moments_at(const typename Codec::raw_t* __restrict__ src,
+                                                                          const Dims& d, int64_t q,
+                                                                          const Consts<typename Codec::R>& K) {
+    using R = typename Codec::R;
+    const int s = q >= d.plane;
+    const int64_t node = q - s * d.plane;
+    const typename Codec::raw_t* base = src + (int64_t)s * kQ * d.plane + node;
+    R dv[kQ];
+    static_for<kQ>([&](auto I) { dv[I] = Codec::dev(Codec::value(base[(int64_t)I * d.plane]), K.w[vel(I).shell]); });
+    return moments_from_dev(dv);
+}
+
+// Moments of nodes q in [q0, q0 + count) into float64 fields indexed by q - q0.
+template <class Codec>
+__global__ void __launch_bounds__(256) k_moments(const typename Codec::raw_t* __restrict__ src, Dims d,
+                                                 Consts<typename Codec::R> K, double theta0, int64_t q0, int64_t count,
+                                                 double* __restrict__ rho, double* __restrict__ u, int64_t ustride,
+                                                 double* __restrict__ theta) {
+    using R = typename Codec::R;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const NodeMoments<R> m = node_moments_at<Codec>(src, d, q0 + k, K);
+    const NodeState<R> st = state_from_moments(m, K);
+    if (rho) rho[k] = 1.0 + (double)m.drho;
+    if (u) {
+        u[k] = (double)st.ux;
+        u[ustride + k] = (double)st.uy;
+        u[2 * ustride + k] = (double)st.uz;
+    }
+    if (theta) theta[k] = theta0 * (1.0 + (double)st.eta);
+}
+
+constexpr int kRedThreads = 256;
+
+// Per-block FP64 partial sums of (drho, jx, jy, jz, dk) over all nodes, in a
+// fixed order (grid-stride loop, then a shared-memory tree): deterministic
+// for a given grid size.
+template <class Codec>
+__global__ void __launch_bounds__(kRedThreads) k_conserved(const typename Codec::raw_t* __restrict__ src, Dims d,
+                                                           Consts<typename Codec::R> K, double* __restrict__ partials) {
+    using R = typename Codec::R;
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    const int64_t n = 2 * d.plane;
+    for (int64_t q = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; q < n; q += (int64_t)gridDim.x * kRedThreads) {
+        const NodeMoments<R> m = node_moments_at<Codec>(src, d, q, K);
+        acc[0] += (double)m.drho;
+        acc[1] += (double)m.jx;
+        acc[2] += (double)m.jy;
+        acc[3] += (double)m.jz;
+        acc[4] += (double)m.dk;
+    }
+    __shared__ double sh[5][kRedThreads];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+#pragma unroll
+            for (int k = 0; k < 5; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) partials[(int64_t)blockIdx.x * 5 + k] = sh[k][0];
+}
+
+// Raw storage <-> float64 populations for elements e in [e0, e0 + count) of the
+// [s][41][nz][ny][nx] array; the float64 side is indexed by e - e0.
+template <class Codec>
+__global__ void __launch_bounds__(256) k_to_f64(const typename Codec::raw_t* __restrict__ src, int64_t plane, W41 w,
+                                                int64_t e0, int64_t count, double* __restrict__ f) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const int64_t e = e0 + k;
+    const int i = (int)((e / plane) % kQ);
+    const double v = (double)Codec::value(src[e]);
+    if constexpr (Codec::stores_f)
+        f[k] = v;
+    else
+        f[k] = w.w[i] * (1.0 + v);
+}
+
+template <class Codec>
+__global__ void __launch_bounds__(256) k_from_f64(const double* __restrict__ f, int64_t plane, W41 w, int64_t e0,
+                                                  int64_t count, typename Codec::raw_t* __restrict__ dst) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const int64_t e = e0 + k;
+    const int i = (int)((e / plane) % kQ);
+    double h;
+    if constexpr (Codec::stores_f)
+        h = f[k];
+    else
+        h = (f[k] - w.w[i]) / w.w[i];
+    dst[e] = Codec::to_raw((typename Codec::R)h);
+}
+
+}  // namespace gblb

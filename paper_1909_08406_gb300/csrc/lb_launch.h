@@ -1,0 +1,63 @@
+// Host-side launchers of the RD3Q41 kernels (one set per storage precision).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lb_common.cuh"
+
+namespace gblb {
+
+struct W41 {
+    double w[kQ];  // per-population weights, library order
+};
+
+struct LaunchConsts {
+    Consts<float> kf;
+    Consts<double> kd;
+    W41 w41;
+    double theta0;
+};
+
+// Storage precision codes (match lb_precision in gblb.h).
+enum Prec { kF64 = 0, kF32 = 1, kF16 = 2, kBF16 = 3 };
+
+size_t storage_bytes(int prec);
+
+// One fused pull step src -> dst over the whole grid.
+cudaError_t launch_step(int prec, bool project, const void* src, void* dst, const Dims& d, const LaunchConsts& c,
+                        double twobeta, int* err, cudaStream_t st);
+
+// Equilibrium of float64 fields for nodes [q0, q0 + count).
+cudaError_t launch_init(int prec, bool project, void* dst, const Dims& d, const LaunchConsts& c, int64_t q0,
+                        int64_t count, const double* rho, const double* u, int64_t ustride, const double* theta,
+                        int* err, cudaStream_t st);
+
+// Node moments for nodes [q0, q0 + count) into float64 fields (any may be null).
+cudaError_t launch_moments(int prec, const void* src, const Dims& d, const LaunchConsts& c, int64_t q0, int64_t count,
+                           double* rho, double* u, int64_t ustride, double* theta, cudaStream_t st);
+
+// Global FP64 sums (drho, jx, jy, jz, dk) -> out5 (device), via nblocks partials.
+cudaError_t launch_conserved(int prec, const void* src, const Dims& d, const LaunchConsts& c, double* partials,
+                             int nblocks, double* out5, cudaStream_t st);
+
+// Raw storage <-> float64 populations for elements [e0, e0 + count).
+cudaError_t launch_to_f64(int prec, const void* src, const Dims& d, const LaunchConsts& c, int64_t e0, int64_t count,
+                          double* f, cudaStream_t st);
+cudaError_t launch_from_f64(int prec, const double* f, void* dst, const Dims& d, const LaunchConsts& c, int64_t e0,
+                            int64_t count, cudaStream_t st);
+
+// Per-precision step launchers (defined in the per-precision translation units).
+cudaError_t launch_step_f64(bool project, const void* src, void* dst, const Dims& d, const LaunchConsts& c,
+                            double twobeta, int* err, cudaStream_t st);
+cudaError_t launch_step_f32(int prec, bool project, const void* src, void* dst, const Dims& d, const LaunchConsts& c,
+                            double twobeta, int* err, cudaStream_t st);
+
+inline dim3 step_grid(const Dims& d, int threads) {
+    return dim3((unsigned)d.rows, (unsigned)((d.nx + threads - 1) / threads), 1);
+}
+inline int step_threads(const Dims& d) {
+    return d.nx >= 128 ? 128 : ((d.nx + 31) / 32) * 32;
+}
+
+}  // namespace gblb

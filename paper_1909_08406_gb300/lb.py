@@ -1,0 +1,211 @@
+"""Thin Python binding of the C ABI in ``include/gblb.h`` (argument marshalling only).
+
+Every function has the name of its C counterpart.  Array arguments may be
+torch tensors (CPU or CUDA) or numpy arrays; they must be float64 and
+C-contiguous in the layouts of ``gblb.h``.  CUDA tensors are passed as device
+pointers, everything else as host pointers.  The stream defaults to torch's
+current stream.  All compute happens in ``libgblb.so``; if the library is
+missing, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgblb.so")
+
+LB_OK = 0
+STATUS = {0: "LB_OK", -1: "LB_ERR_ARG", -2: "LB_ERR_OOM", -3: "LB_ERR_CUDA", -4: "LB_ERR_THETA0",
+          -5: "LB_ERR_UNSTABLE", -6: "LB_ERR_TIMEOUT", -7: "LB_ERR_STATE"}
+PRECISION = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
+LB_RD3Q41 = 41
+LB_FLAG_PAPER_LITERAL = 1
+
+
+class LbError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libgblb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(or python -m paper_1909_08406_gb300.build)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double
+        L.lb_velocity_set.argtypes = [vp, vp]
+        L.lb_theta0.restype = dp
+        L.lb_init.argtypes = [ctypes.POINTER(vp), _Grid, ctypes.c_int, dp, dp, ctypes.c_int, ctypes.c_uint, vp]
+        L.lb_set_stream.argtypes = [vp, vp]
+        L.lb_set_fields.argtypes = [vp, vp, vp, vp, ctypes.c_int]
+        L.lb_step.argtypes = [vp, i64]
+        L.lb_get_moments.argtypes = [vp, vp, vp, vp, ctypes.c_int]
+        L.lb_conserved.argtypes = [vp, vp]
+        L.lb_get_populations.argtypes = [vp, vp, ctypes.c_int]
+        L.lb_set_populations.argtypes = [vp, vp, ctypes.c_int]
+        L.lb_state_bytes.argtypes = [vp]
+        L.lb_state_bytes.restype = i64
+        L.lb_get_state.argtypes = [vp, vp, ctypes.c_int]
+        L.lb_set_state.argtypes = [vp, vp, ctypes.c_int]
+        L.lb_time.argtypes = [vp]
+        L.lb_time.restype = i64
+        L.lb_sync.argtypes = [vp]
+        L.lb_destroy.argtypes = [vp]
+        L.lb_last_error.argtypes = [vp]
+        L.lb_last_error.restype = ctypes.c_char_p
+        for name in ("lb_velocity_set", "lb_init", "lb_set_stream", "lb_set_fields", "lb_step", "lb_get_moments",
+                     "lb_conserved", "lb_get_populations", "lb_set_populations", "lb_get_state", "lb_set_state",
+                     "lb_sync", "lb_destroy"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status, ctx):
+    if status != LB_OK:
+        msg = lib().lb_last_error(ctx)
+        raise LbError(status, msg.decode() if msg else "")
+
+
+def _ptr(a, writable=False):
+    """(pointer, on_device) of a float64 C-contiguous torch tensor / numpy array (or None)."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        if writable and not a.flags["WRITEABLE"]:
+            raise ValueError("array is read-only")
+        return a.ctypes.data, 0
+    import torch
+    if isinstance(a, torch.Tensor):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), int(a.is_cuda)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _f64(a, writable=False):
+    if a is None:
+        return None, 0
+    dt = a.dtype
+    if str(dt) not in ("float64", "torch.float64"):
+        raise TypeError("arrays crossing the interface are float64")
+    return _ptr(a, writable)
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    import torch
+    if torch.cuda.is_available():
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+def lb_velocity_set():
+    """(c2 [41,3] int32 doubled components, w [41] float64) in the library's population order."""
+    c2 = np.zeros((41, 3), dtype=np.int32)
+    w = np.zeros(41)
+    _check(lib().lb_velocity_set(c2.ctypes.data, w.ctypes.data), None)
+    return c2, w
+
+
+def lb_theta0():
+    return lib().lb_theta0()
+
+
+def lb_init(grid, tau, precision="f32", theta0=0.0, velocity_set=LB_RD3Q41, flags=0, stream=None):
+    """Create a context; grid = (nx, ny, nz).  Returns an opaque handle (int)."""
+    nx, ny, nz = (int(v) for v in grid)
+    h = ctypes.c_void_p()
+    st = lib().lb_init(ctypes.byref(h), _Grid(nx, ny, nz), int(velocity_set), float(theta0), float(tau),
+                       PRECISION[precision] if isinstance(precision, str) else int(precision), int(flags),
+                       _stream(stream))
+    _check(st, None)
+    return h.value
+
+
+def lb_set_stream(ctx, stream=None):
+    _check(lib().lb_set_stream(ctx, _stream(stream)), ctx)
+
+
+def lb_set_fields(ctx, rho, u, theta):
+    (pr, d0), (pu, d1), (pt, d2) = _f64(rho), _f64(u), _f64(theta)
+    if not (d0 == d1 == d2):
+        raise ValueError("rho, u, theta must all be on the host or all on the device")
+    _check(lib().lb_set_fields(ctx, pr, pu, pt, d0), ctx)
+
+
+def lb_step(ctx, n=1):
+    _check(lib().lb_step(ctx, int(n)), ctx)
+
+
+def lb_get_moments(ctx, rho=None, u=None, theta=None):
+    ps = [_f64(a, writable=True) for a in (rho, u, theta)]
+    devs = {d for (p, d) in ps if p is not None}
+    if len(devs) > 1:
+        raise ValueError("outputs must all be on the host or all on the device")
+    _check(lib().lb_get_moments(ctx, ps[0][0], ps[1][0], ps[2][0], devs.pop() if devs else 0), ctx)
+
+
+def lb_conserved(ctx):
+    out = np.zeros(5)
+    _check(lib().lb_conserved(ctx, out.ctypes.data), ctx)
+    return out
+
+
+def lb_get_populations(ctx, f):
+    p, d = _f64(f, writable=True)
+    _check(lib().lb_get_populations(ctx, p, d), ctx)
+
+
+def lb_set_populations(ctx, f):
+    p, d = _f64(f)
+    _check(lib().lb_set_populations(ctx, p, d), ctx)
+
+
+def lb_state_bytes(ctx):
+    return int(lib().lb_state_bytes(ctx))
+
+
+def lb_get_state(ctx, raw):
+    p, d = _ptr(raw, writable=True)
+    _check(lib().lb_get_state(ctx, p, d), ctx)
+
+
+def lb_set_state(ctx, raw):
+    p, d = _ptr(raw)
+    _check(lib().lb_set_state(ctx, p, d), ctx)
+
+
+def lb_time(ctx):
+    return int(lib().lb_time(ctx))
+
+
+def lb_sync(ctx):
+    _check(lib().lb_sync(ctx), ctx)
+
+
+def lb_destroy(ctx):
+    _check(lib().lb_destroy(ctx), ctx)
+
+
+def lb_last_error(ctx=None):
+    m = lib().lb_last_error(ctx)
+    return m.decode() if m else ""

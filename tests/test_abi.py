@@ -1,0 +1,81 @@
+"""C ABI checks that need no GPU: the library loads, exports every entry point
+declared in include/gblb.h, reports the paper's velocity set, and rejects bad
+arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = set()
+    for hdr in os.listdir(os.path.join(ROOT, "include")):
+        if not hdr.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", hdr)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"\b(lb_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1909_08406_gb300 import build, lb
+    build.build()
+    return lb.lib()
+
+
+def test_library_exports_every_declared_symbol(L):
+    names = _declared_symbols()
+    assert "lb_init" in names and "lb_step" in names
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_velocity_set_matches_oracle(L):
+    from paper_1909_08406_gb300 import lb
+    c2, w = lb.lb_velocity_set()
+    c2o, wo, _ = oracle.velocities()
+    by_vel = {tuple((2 * c).astype(int)): wt for c, wt in zip(c2o, wo)}
+    assert {tuple(v) for v in c2} == set(by_vel)
+    for v, wt in zip(c2, w):
+        assert wt == pytest.approx(by_vel[tuple(v)], rel=0, abs=1e-17)
+    # +-c pairs at 2k+1, 2k+2
+    for k in range(20):
+        assert np.array_equal(c2[2 * k + 1], -c2[2 * k + 2])
+    assert lb.lb_theta0() == pytest.approx(oracle.theta0(), rel=1e-15)
+
+
+def test_init_rejects_bad_arguments(L):
+    from paper_1909_08406_gb300 import lb
+    th = lb.lb_theta0()
+    with pytest.raises(lb.LbError) as e:
+        lb.lb_init((8, 8, 8), tau=0.5, theta0=th * (1 + 1e-9))
+    assert e.value.status == -4
+    with pytest.raises(lb.LbError) as e:
+        lb.lb_init((8, 8, 8), tau=0.5, velocity_set=27)
+    assert e.value.status == -1
+    with pytest.raises(lb.LbError) as e:
+        lb.lb_init((0, 8, 8), tau=0.5)
+    assert e.value.status == -1
+    with pytest.raises(lb.LbError) as e:
+        lb.lb_init((8, 8, 8), tau=-1.0)
+    assert e.value.status == -1
+    with pytest.raises(lb.LbError) as e:
+        lb.lb_init((8, 8, 8), tau=0.5, precision=7)
+    assert e.value.status == -1
+    assert "theta" in lb.lb_last_error() or "precision" in lb.lb_last_error()
+
+
+def test_null_context_is_rejected(L):
+    assert L.lb_step(None, ctypes.c_int64(1)) == -1
+    assert L.lb_sync(None) == -1
+    assert L.lb_destroy(None) == 0

@@ -1,0 +1,230 @@
+"""GPU parity: the CUDA path against the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (max |f_gpu - f_oracle| / f_oracle over every population):
+  * streaming (tau = inf, collision is the identity): bit-exact in every
+    storage type;
+  * FP64: 1e-12 after 200 steps of the 32^3 standing wave, 1e-12 after 20
+    steps of random fields (only summation order differs);
+  * FP32 arithmetic: each step rounds h = f/w - 1 to the storage type and
+    evaluates the equilibrium in FP32 in deviation form, so the error per step
+    is ~ eps_store |h| + ~1e-7 |h|; the bounds below allow sqrt(steps) growth
+    with a factor 4 margin for |h| <~ 0.05 (f32 2e-7, f16 1e-4, bf16 8e-4 after
+    20 steps).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import STORE_EPS, TORCH_DTYPE, decode, lib_to_oracle_perm, to_lib_order, to_oracle_order
+from paper_1909_08406_gb300 import lb
+from paper_1909_08406_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+PRECS = ["f64", "f32", "f16", "bf16"]
+RANDOM_FIELD_TOL = {"f64": 1e-12, "f32": 2e-7, "f16": 1e-4, "bf16": 8e-4}
+
+
+@pytest.fixture(scope="module")
+def perm():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return lib_to_oracle_perm()
+
+
+@pytest.fixture(scope="module")
+def w_lib():
+    return lb.lb_velocity_set()[1]
+
+
+def _fields_np(fl):
+    return fl["rho"].numpy(), fl["u"].numpy(), fl["theta"].numpy()
+
+
+def _run_gpu(shape, tau, prec, fields, steps, flags=0):
+    ctx = lb.lb_init(shape, tau, prec, flags=flags)
+    try:
+        lb.lb_set_fields(ctx, fields["rho"].cuda(), fields["u"].cuda(), fields["theta"].cuda())
+        lb.lb_step(ctx, steps)
+        nx, ny, nz = shape
+        f = np.empty((2, 41, nz, ny, nx))
+        lb.lb_get_populations(ctx, f)
+        lb.lb_sync(ctx)
+    finally:
+        lb.lb_destroy(ctx)
+    return f
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("shape", [(4, 4, 4), (3, 5, 7), (1, 2, 5), (133, 3, 2)])
+def test_streaming_is_bit_exact(prec, shape, perm, w_lib):
+    nx, ny, nz = shape
+    rng = np.random.default_rng(100 + nx)
+    h = 0.1 * rng.uniform(-1, 1, size=(2, 41, nz, ny, nx))
+    if prec == "f64":
+        stored = np.asarray(w_lib)[None, :, None, None, None] * (1 + h)
+    else:
+        stored = h
+    raw = torch.from_numpy(stored).to(TORCH_DTYPE[prec]).cuda().contiguous()
+    ctx = lb.lb_init(shape, math.inf, prec)
+    try:
+        lb.lb_set_state(ctx, raw)
+        lb.lb_step(ctx, 1)
+        out = torch.empty_like(raw)
+        lb.lb_get_state(ctx, out)
+        lb.lb_sync(ctx)
+    finally:
+        lb.lb_destroy(ctx)
+    exact_in = raw.cpu().to(torch.float64).numpy()  # stored values are exact in float64
+    ref = oracle.stream(to_oracle_order(exact_in, perm))
+    got = to_oracle_order(out.cpu().to(torch.float64).numpy(), perm)
+    assert np.array_equal(got, ref)
+
+
+def test_config1_f64_standing_wave_200_steps(perm):
+    """32^3, FP64, nu = 0.01, rho = 1 + 1e-3 sin(2 pi x / 32): every population after 200 steps."""
+    N = 32
+    th0 = lb.lb_theta0()
+    tau = 0.01 / th0
+    fl = wl.standing_wave(N, N, N, th0, amplitude=1e-3)
+    got = to_oracle_order(_run_gpu((N, N, N), tau, "f64", fl, 200), perm)
+    ref = oracle.step(oracle.init_fields(*_fields_np(fl)), tau, 200)
+    rel = np.abs(got - ref) / np.abs(ref)
+    assert rel.max() <= 1e-12, rel.max()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("project", [True, False])
+def test_random_fields_parity(prec, project, perm):
+    shape = (133, 5, 3)  # two x-blocks with a ragged tail, odd y/z
+    th0 = lb.lb_theta0()
+    amp = 0.05 if prec in ("f64", "f32") else 0.02
+    fl = wl.random_fields(*shape, th0, seed=7, du=amp, drho=amp, dtheta=amp)
+    tau = 0.3
+    steps = 20
+    got = to_oracle_order(_run_gpu(shape, tau, prec, fl, steps, flags=0 if project else lb.LB_FLAG_PAPER_LITERAL),
+                          perm)
+    ref = oracle.step(oracle.init_fields(*_fields_np(fl), project=project), tau, steps, project=project)
+    rel = np.abs(got - ref) / np.abs(ref)
+    assert rel.max() <= RANDOM_FIELD_TOL[prec], rel.max()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_init_from_fields(prec, perm):
+    shape = (37, 4, 3)
+    th0 = lb.lb_theta0()
+    fl = wl.random_fields(*shape, th0, seed=8, du=0.05, drho=0.05, dtheta=0.05)
+    got = to_oracle_order(_run_gpu(shape, 0.5, prec, fl, 0), perm)
+    ref = oracle.init_fields(*_fields_np(fl))
+    h_ref_max = np.max(np.abs(ref / oracle.velocities()[1][None, :, None, None, None] - 1))
+    tol = {"f64": 1e-14}.get(prec, STORE_EPS[prec] * h_ref_max + 2e-7 * h_ref_max)
+    rel = np.abs(got - ref) / np.abs(ref)
+    assert rel.max() <= tol, (rel.max(), tol)
+
+
+@pytest.mark.parametrize("on_device", [False, True])
+def test_moments_and_conserved_f64(on_device, perm):
+    shape = (9, 7, 5)
+    th0 = lb.lb_theta0()
+    fl = wl.random_fields(*shape, th0, seed=9, du=0.05, drho=0.05, dtheta=0.05)
+    f_or = oracle.step(oracle.init_fields(*_fields_np(fl)), 0.4, 3)
+    nx, ny, nz = shape
+    ctx = lb.lb_init(shape, 0.4, "f64")
+    try:
+        f_lib = to_lib_order(f_or, perm)
+        if on_device:
+            lb.lb_set_populations(ctx, torch.from_numpy(f_lib).cuda())
+            rho = torch.empty((2, nz, ny, nx), dtype=torch.float64, device="cuda")
+            u = torch.empty((3, 2, nz, ny, nx), dtype=torch.float64, device="cuda")
+            th = torch.empty_like(rho)
+            lb.lb_get_moments(ctx, rho, u, th)
+            lb.lb_sync(ctx)
+            rho, u, th = rho.cpu().numpy(), u.cpu().numpy(), th.cpu().numpy()
+        else:
+            lb.lb_set_populations(ctx, f_lib)
+            rho = np.empty((2, nz, ny, nx))
+            u = np.empty((3, 2, nz, ny, nx))
+            th = np.empty_like(rho)
+            lb.lb_get_moments(ctx, rho, u, th)
+        cons = lb.lb_conserved(ctx)
+    finally:
+        lb.lb_destroy(ctx)
+    r_or, u_or, t_or = oracle.get_moments(f_or)
+    assert np.max(np.abs(rho - r_or)) < 1e-14
+    assert np.max(np.abs(u - u_or)) < 1e-14
+    assert np.max(np.abs(th - t_or) / t_or) < 1e-13
+    c_or = oracle.conserved(f_or)
+    assert cons[0] == pytest.approx(c_or[0], rel=1e-13)
+    assert np.max(np.abs(cons[1:4] - c_or[1:4])) < 1e-12
+    assert cons[4] == pytest.approx(c_or[4], rel=1e-13)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_checkpoint_restart_is_bitwise(prec):
+    shape = (20, 6, 5)
+    th0 = lb.lb_theta0()
+    fl = wl.random_fields(*shape, th0, seed=10, du=0.02, drho=0.02, dtheta=0.02)
+    ctx = lb.lb_init(shape, 0.3, prec)
+    try:
+        lb.lb_set_fields(ctx, fl["rho"], fl["u"], fl["theta"])
+        lb.lb_step(ctx, 7)
+        saved = np.empty(lb.lb_state_bytes(ctx), dtype=np.uint8)
+        lb.lb_get_state(ctx, saved)
+        lb.lb_step(ctx, 9)
+        a = np.empty_like(saved)
+        lb.lb_get_state(ctx, a)
+        lb.lb_set_state(ctx, saved)
+        lb.lb_step(ctx, 9)
+        b = np.empty_like(saved)
+        lb.lb_get_state(ctx, b)
+    finally:
+        lb.lb_destroy(ctx)
+    assert np.array_equal(a, b)
+    assert not np.array_equal(a, saved)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_conservation_over_steps(prec):
+    shape = (16, 12, 8)
+    th0 = lb.lb_theta0()
+    fl = wl.random_fields(*shape, th0, seed=11, du=0.03, drho=0.03, dtheta=0.03)
+    ctx = lb.lb_init(shape, 0.25, prec)
+    try:
+        lb.lb_set_fields(ctx, fl["rho"], fl["u"], fl["theta"])
+        c0 = lb.lb_conserved(ctx)
+        lb.lb_step(ctx, 100)
+        c1 = lb.lb_conserved(ctx)
+    finally:
+        lb.lb_destroy(ctx)
+    n = 2 * 16 * 12 * 8
+    tol = 1e-13 if prec == "f64" else 1e-6
+    assert abs(c1[0] - c0[0]) < tol * n
+    assert np.max(np.abs(c1[1:4] - c0[1:4])) < tol * n
+    assert abs(c1[4] - c0[4]) < tol * c0[4]
+
+
+def test_unstable_state_is_reported():
+    shape = (8, 4, 4)
+    th0 = lb.lb_theta0()
+    fl = wl.random_fields(*shape, th0, seed=12, du=0.01, drho=0.01, dtheta=0.01)
+    fl["rho"][0, 1, 2, 3] = -1.0
+    ctx = lb.lb_init(shape, 0.5, "f32")
+    try:
+        lb.lb_set_fields(ctx, fl["rho"], fl["u"], fl["theta"])
+        with pytest.raises(lb.LbError) as e:
+            lb.lb_sync(ctx)
+        assert e.value.status == -5
+    finally:
+        lb.lb_destroy(ctx)
+
+
+def test_free_streaming_time_counter():
+    ctx = lb.lb_init((4, 4, 4), 0.5, "f32")
+    try:
+        assert lb.lb_time(ctx) == 0
+        lb.lb_step(ctx, 3)
+        assert lb.lb_time(ctx) == 3
+    finally:
+        lb.lb_destroy(ctx)
