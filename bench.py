@@ -33,7 +33,7 @@ sys.path.insert(0, ROOT)
 BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 DTYPE_NAME = {"f64": "f64", "f32": "f32", "f16": "f32 (f16 storage)", "bf16": "f32 (bf16 storage)"}
 NU = 0.01
-STEP_KERNEL_SOURCES = ["lb_common.cuh", "lb_kernels.cuh", "lb_step_f32.cu", "lb_step_f64.cu"]
+STEP_KERNEL_SOURCES = ["lb_common.cuh", "lb_kernels.cuh", "lb_step_tma.cuh", "lb_step_f32.cu", "lb_step_f64.cu"]
 
 
 def parse():
@@ -253,11 +253,16 @@ def main():
                                                               if p != args.precision])
     results = {}
     clocks = None
-    for prec in precs:
-        head = prec == args.precision
+    runs = [(p, 0) for p in precs]
+    if not args.no_secondary:
+        runs.insert(1, (args.precision, lb.LB_FLAG_NO_STAGING))  # the direct-load kernel, for comparison
+    for prec, flags in runs:
+        head = prec == args.precision and flags == 0
+        key = prec if flags == 0 else prec + "_direct"
         steps = args.steps if head else (max(3, args.steps // 10) if prec == "f64" else max(5, args.steps // 2))
         warm = args.warmup if head else 3
-        ctx = lb.lb_init((n, n, n), tau, prec)
+        ctx = lb.lb_init((n, n, n), tau, prec, flags=flags)
+        variant = lb.lb_step_variant(ctx)
         try:
             lb.lb_set_fields(ctx, fields["rho"], fields["u"], fields["theta"])
             lb.lb_sync(ctx)
@@ -274,10 +279,11 @@ def main():
             total_ms = max_over_ranks(total_ms)
             alg = nodes * 41 * 2 * BYTES[prec]
             avg_ms = sum(per) / len(per)
-            results[prec] = {"mlups": world * nodes * steps / (total_ms * 1e-3) / 1e6,
-                             "ms_per_step": total_ms / steps, "kernel_ms": avg_ms,
-                             "achieved_gbs": alg / (avg_ms * 1e-3) / 1e9, "alg_bytes_per_launch": alg,
-                             "steps": steps, "warmup": warm}
+            results[key] = {"mlups": world * nodes * steps / (total_ms * 1e-3) / 1e6,
+                            "ms_per_step": total_ms / steps, "kernel_ms": avg_ms,
+                            "achieved_gbs": alg / (avg_ms * 1e-3) / 1e9, "alg_bytes_per_launch": alg,
+                            "steps": steps, "warmup": warm,
+                            "kernel": f"k_step_tma (TMA-staged, tile {variant})" if variant else "k_step (direct)"}
         finally:
             lb.lb_destroy(ctx)
         torch.cuda.empty_cache()
@@ -327,10 +333,10 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": r["achieved_gbs"], "peak": peak, "unit": "GB/s",
                      "frac": r["achieved_gbs"] / peak, "traffic": traffic, "peak_kind": peak_kind,
-                     "kernel": f"k_step<{args.precision}>", "alg_bytes_per_launch": r["alg_bytes_per_launch"]},
+                     "kernel": r["kernel"], "alg_bytes_per_launch": r["alg_bytes_per_launch"]},
         "by_precision": {p: {"mlups": v["mlups"], "achieved_gbs": v["achieved_gbs"],
                              "frac_of_hbm": v["achieved_gbs"] / peak, "ms_per_step": v["ms_per_step"],
-                             "steps": v["steps"]} for p, v in results.items()},
+                             "steps": v["steps"], "kernel": v["kernel"]} for p, v in results.items()},
         "gpu_launches": r["steps"],
         "clocks": clocks,
         "e2e": e2e,

@@ -67,7 +67,7 @@ typedef enum {
 typedef enum {
     LB_F64 = 0,      /* FP64 arithmetic, populations stored as FP64 f_i                 */
     LB_F32 = 1,      /* FP32 arithmetic, stored as FP32 h_i = f_i / w_i - 1              */
-    LB_F32_S16F = 2, /* FP32 arithmetic, stored as FP16 h_i (round to nearest even)     */
+    LB_F32_S16F = 2, /* FP32 arithmetic, stored as FP16 2^8 h_i (round to nearest even) */
     LB_F32_S16B = 3  /* FP32 arithmetic, stored as BF16 h_i (round to nearest even)     */
 } lb_precision;
 
@@ -75,6 +75,7 @@ typedef enum {
 
 /* lb_init flags */
 #define LB_FLAG_PAPER_LITERAL 1u /* equilibrium exactly as printed (no momentum projection) */
+#define LB_FLAG_NO_STAGING 2u    /* always use the direct-load step kernel (see lb_step_variant) */
 
 typedef struct {
     int64_t nx, ny, nz; /* simple-cubic cells per axis, each >= 1; nodes = 2 nx ny nz */
@@ -131,11 +132,19 @@ lb_status lb_get_populations(lb_ctx *ctx, double *f, int on_device);
 lb_status lb_set_populations(lb_ctx *ctx, const double *f, int on_device);
 
 /* Raw storage (checkpoint / restart): lb_state_bytes bytes, layout
- * [s][41][nz][ny][nx] of the storage type (f64 f_i, or h_i = f_i/w_i - 1 as
- * f32 / f16 / bf16).  Restoring a saved state reproduces the run bit for bit. */
+ * [s][41][nz][ny][nx] of the storage type: f64 f_i; f32 h_i; f16 2^8 h_i;
+ * bf16 h_i, with h_i = f_i/w_i - 1.  Restoring a saved state reproduces the
+ * run bit for bit. */
 int64_t lb_state_bytes(const lb_ctx *ctx);
 lb_status lb_get_state(lb_ctx *ctx, void *raw, int on_device);
 lb_status lb_set_state(lb_ctx *ctx, const void *raw, int on_device);
+
+/* Step kernel used by this context: the tile width (128 or 256) of the
+ * shared-memory-staged kernel, whose rows are fetched by TMA bulk copies
+ * (FP32/FP16/BF16 storage, nx a multiple of 128 and of 16 bytes), or 0 for the
+ * direct-load kernel (FP64, other grids, or LB_FLAG_NO_STAGING).  Both compute
+ * the same update. */
+int lb_step_variant(const lb_ctx *ctx);
 
 /* Number of time steps taken since the last lb_set_fields / lb_set_populations / lb_set_state. */
 int64_t lb_time(const lb_ctx *ctx);

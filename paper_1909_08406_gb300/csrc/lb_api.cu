@@ -122,6 +122,7 @@ struct lb_ctx {
     Dims d;
     int prec;
     bool project;
+    int variant;
     double tau, twobeta;
     cudaStream_t stream;
     int device;
@@ -202,7 +203,7 @@ lb_status lb_init(lb_ctx** out, lb_grid grid, int velocity_set, double theta0, d
     if ((int)precision < LB_F64 || (int)precision > LB_F32_S16B)
         return fail(nullptr, LB_ERR_ARG, "lb_init: unknown precision");
     if (!(tau > 0.0)) return fail(nullptr, LB_ERR_ARG, "lb_init: tau must be > 0 (or +inf)");
-    if (flags & ~LB_FLAG_PAPER_LITERAL) return fail(nullptr, LB_ERR_ARG, "lb_init: unknown flag bits");
+    if (flags & ~(LB_FLAG_PAPER_LITERAL | LB_FLAG_NO_STAGING)) return fail(nullptr, LB_ERR_ARG, "lb_init: unknown flag bits");
     const Lattice& L = lattice();
     if (theta0 > 0.0 && fabs(theta0 / L.theta0 - 1.0) > 1e-12)
         return fail(nullptr, LB_ERR_THETA0, "lb_init: theta0 differs from sum_i w_i c_ix^2 of the Table I weights");
@@ -216,6 +217,7 @@ lb_status lb_init(lb_ctx** out, lb_grid grid, int velocity_set, double theta0, d
     c->d.rows = 2 * grid.ny * grid.nz;
     c->prec = (int)precision;
     c->project = !(flags & LB_FLAG_PAPER_LITERAL);
+    c->variant = (flags & LB_FLAG_NO_STAGING) ? kVariantDirect : kVariantStaged;
     c->tau = tau;
     c->twobeta = isinf(tau) ? 0.0 : 2.0 / (2.0 * tau + 1.0);
     c->stream = (cudaStream_t)cuda_stream;
@@ -273,8 +275,14 @@ lb_status lb_sync(lb_ctx* c) {
     CK(c, cudaStreamSynchronize(c->stream));
     int h = 0;
     CK(c, cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h & 2) return fail(c, LB_ERR_TIMEOUT, "a bounded wait in the staged step kernel gave up");
     if (h) return fail(c, LB_ERR_UNSTABLE, "a node reached rho <= 0, theta <= 0 or a non-finite moment");
     return LB_OK;
+}
+
+int lb_step_variant(const lb_ctx* c) {
+    if (!c) return -1;
+    return c->variant == kVariantStaged ? tma_tile_width(c->prec, c->d) : 0;
 }
 
 lb_status lb_set_fields(lb_ctx* c, const double* rho, const double* u, const double* theta, int on_device) {
@@ -312,8 +320,8 @@ lb_status lb_step(lb_ctx* c, int64_t n) {
     CK(c, cudaSetDevice(c->device));
     const LaunchConsts& lc = lattice().lc;
     for (int64_t t = 0; t < n; ++t) {
-        CK(c, launch_step(c->prec, c->project, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc, c->twobeta, c->d_err,
-                          c->stream));
+        CK(c, launch_step(c->prec, c->project, c->variant, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc, c->twobeta,
+                          c->d_err, c->stream));
         c->cur ^= 1;
         c->time += 1;
     }

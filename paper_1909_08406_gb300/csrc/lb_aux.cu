@@ -36,10 +36,10 @@ static cudaError_t dispatch(int prec, F&& f) {
 
 static unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-cudaError_t launch_step(int prec, bool project, const void* src, void* dst, const Dims& d, const LaunchConsts& c,
-                        double twobeta, int* err, cudaStream_t st) {
+cudaError_t launch_step(int prec, bool project, int variant, const void* src, void* dst, const Dims& d,
+                        const LaunchConsts& c, double twobeta, int* err, cudaStream_t st) {
     if (prec == kF64) return launch_step_f64(project, src, dst, d, c, twobeta, err, st);
-    return launch_step_f32(prec, project, src, dst, d, c, twobeta, err, st);
+    return launch_step_f32(prec, project, variant, src, dst, d, c, twobeta, err, st);
 }
 
 cudaError_t launch_init(int prec, bool project, void* dst, const Dims& d, const LaunchConsts& c, int64_t q0,

@@ -52,6 +52,17 @@ __host__ __device__ constexpr Vel vel(int i) {
     return t[i];
 }
 
+// The velocity table as data, for lookups with a run-time index.
+struct VelTable {
+    Vel v[kQ];
+};
+__host__ __device__ constexpr VelTable make_vel_table() {
+    VelTable t{};
+    for (int i = 0; i < kQ; ++i) t.v[i] = vel(i);
+    return t;
+}
+static __constant__ VelTable c_vel = make_vel_table();
+
 // Per-shell lattice constants in the compute type.
 template <class R>
 struct Consts {
@@ -79,14 +90,15 @@ __device__ __forceinline__ void static_for(F&& f) {
 }
 
 // ---------------------------------------------------------------------------
-// Storage codecs.  value(): stored element -> working value v (f or h);
-// dev(): deviation f - w from v; relax(): new stored element from v and
-// x = 2 beta h^eq; to_raw(): rounding to the storage type.
+// Storage codecs.  value(): stored element -> working value v (f, or
+// kScale * h); dev(v, w / kScale): deviation f - w; relax(): new working value
+// from v and x = 2 beta kScale h^eq; to_raw(): rounding to the storage type.
 // ---------------------------------------------------------------------------
 struct CodecF64 {  // stores f_i
     using raw_t = double;
     using R = double;
     static constexpr bool stores_f = true;
+    static constexpr double kScale = 1.0;
     static __device__ __forceinline__ R value(raw_t r) { return r; }
     static __device__ __forceinline__ R dev(R v, R w) { return v - w; }
     static __device__ __forceinline__ R relax(R v, R omb, R x, R w, R tb) { return fma(omb, v, w * (tb + x)); }
@@ -97,16 +109,22 @@ struct CodecF32 {  // stores h_i = f_i / w_i - 1
     using raw_t = float;
     using R = float;
     static constexpr bool stores_f = false;
+    static constexpr double kScale = 1.0;
     static __device__ __forceinline__ R value(raw_t r) { return r; }
     static __device__ __forceinline__ R dev(R v, R w) { return w * v; }
     static __device__ __forceinline__ R relax(R v, R omb, R x, R, R) { return fmaf(omb, v, x); }
     static __device__ __forceinline__ raw_t to_raw(R v) { return v; }
 };
 
+// FP16 stores 2^8 h_i: the power-of-two scale is exact and moves FP16's
+// subnormal range (|x| < 6.1e-5) down to |h| < 2.4e-7, while |h| up to 255
+// stays finite.  The scale is folded into the per-shell constants, so the
+// working value v is the stored (scaled) number.
 struct CodecF16 {
     using raw_t = __half;
     using R = float;
     static constexpr bool stores_f = false;
+    static constexpr double kScale = 256.0;
     static __device__ __forceinline__ R value(raw_t r) { return __half2float(r); }
     static __device__ __forceinline__ R dev(R v, R w) { return w * v; }
     static __device__ __forceinline__ R relax(R v, R omb, R x, R, R) { return fmaf(omb, v, x); }
@@ -117,6 +135,7 @@ struct CodecBF16 {
     using raw_t = __nv_bfloat16;
     using R = float;
     static constexpr bool stores_f = false;
+    static constexpr double kScale = 1.0;
     static __device__ __forceinline__ R value(raw_t r) { return __bfloat162float(r); }
     static __device__ __forceinline__ R dev(R v, R w) { return w * v; }
     static __device__ __forceinline__ R relax(R v, R omb, R x, R, R) { return fmaf(omb, v, x); }
@@ -130,10 +149,11 @@ struct NodeMoments {
     R drho, jx, jy, jz, dk;
 };
 
-template <class R>
-__device__ __forceinline__ NodeMoments<R> moments_from_dev(const R (&d)[kQ]) {
+// dget(I) returns d_I for a compile-time population index I.
+template <class R, class G>
+__device__ __forceinline__ NodeMoments<R> moments_from(G&& dget) {
     NodeMoments<R> m;
-    m.drho = d[0];
+    m.drho = dget(std::integral_constant<int, 0>{});
     m.jx = R(0);
     m.jy = R(0);
     m.jz = R(0);
@@ -141,8 +161,10 @@ __device__ __forceinline__ NodeMoments<R> moments_from_dev(const R (&d)[kQ]) {
     static_for<20>([&](auto K) {
         constexpr int ip = 2 * K + 1, im = 2 * K + 2;
         constexpr Vel c = vel(ip);
-        const R s = d[ip] + d[im];
-        const R df = d[ip] - d[im];
+        const R dp = dget(std::integral_constant<int, ip>{});
+        const R dm = dget(std::integral_constant<int, im>{});
+        const R s = dp + dm;
+        const R df = dp - dm;
         m.drho += s;
         // c2 components are doubled: c = c2 / 2
         if constexpr (c.x != 0) m.jx = fma(R(0.5 * c.x), df, m.jx);
@@ -152,6 +174,11 @@ __device__ __forceinline__ NodeMoments<R> moments_from_dev(const R (&d)[kQ]) {
         m.dk = fma(R(csq), s, m.dk);
     });
     return m;
+}
+
+template <class R>
+__device__ __forceinline__ NodeMoments<R> moments_from_dev(const R (&d)[kQ]) {
+    return moments_from<R>([&](auto I) { return d[I]; });
 }
 
 // Primitive variables of a node: rho, u, eta = theta / theta_0 - 1.
@@ -187,10 +214,10 @@ __device__ __forceinline__ bool state_ok(const NodeState<R>& st) {
 // relaxation of one node.  v[i] are the working values of the node's incoming
 // populations (f or h, see the codec), tb = 2 beta, omb = 1 - 2 beta.
 // sink(I, value) receives the new working value of population I.
-template <class Codec, bool PROJECT, class Sink>
-__device__ __forceinline__ void equilibrium_relax(const NodeState<typename Codec::R>& st,
-                                                  const Consts<typename Codec::R>& K, typename Codec::R tb,
-                                                  typename Codec::R omb, const typename Codec::R (&v)[kQ], Sink&& sink) {
+template <class Codec, bool PROJECT, class VGet, class Sink>
+__device__ __forceinline__ void equilibrium_relax_g(const NodeState<typename Codec::R>& st,
+                                                    const Consts<typename Codec::R>& K, typename Codec::R tb,
+                                                    typename Codec::R omb, VGet&& vget, Sink&& sink) {
     using R = typename Codec::R;
     const R rho = st.rho, eta = st.eta;
     const R inv_1pe = R(1) / (R(1) + eta);           // theta_0 / theta
@@ -248,7 +275,8 @@ __device__ __forceinline__ void equilibrium_relax(const NodeState<typename Codec
     {
         const R P0 = tb * rR[0];
         const R x0 = fma(P0, Cs[0], tb * rRm1[0]);
-        sink(std::integral_constant<int, 0>{}, Codec::relax(v[0], omb, x0, K.w[0], tb));
+        sink(std::integral_constant<int, 0>{},
+             Codec::relax(vget(std::integral_constant<int, 0>{}), omb, x0, K.w[0], tb));
     }
     static_for<20>([&](auto KK) {
         constexpr int ip = 2 * KK + 1, im = 2 * KK + 2;
@@ -274,9 +302,18 @@ __device__ __forceinline__ void equilibrium_relax(const NodeState<typename Codec
         const R a2 = a * a;
         const R t = fma(R(0.5) * P, a2, B);
         const R o = fma(P * R(1.0 / 6.0), a2 * a, P * q);
-        sink(std::integral_constant<int, ip>{}, Codec::relax(v[ip], omb, t + o, K.w[s], tb));
-        sink(std::integral_constant<int, im>{}, Codec::relax(v[im], omb, t - o, K.w[s], tb));
+        sink(std::integral_constant<int, ip>{},
+             Codec::relax(vget(std::integral_constant<int, ip>{}), omb, t + o, K.w[s], tb));
+        sink(std::integral_constant<int, im>{},
+             Codec::relax(vget(std::integral_constant<int, im>{}), omb, t - o, K.w[s], tb));
     });
+}
+
+template <class Codec, bool PROJECT, class Sink>
+__device__ __forceinline__ void equilibrium_relax(const NodeState<typename Codec::R>& st,
+                                                  const Consts<typename Codec::R>& K, typename Codec::R tb,
+                                                  typename Codec::R omb, const typename Codec::R (&v)[kQ], Sink&& sink) {
+    equilibrium_relax_g<Codec, PROJECT>(st, K, tb, omb, [&](auto I) { return v[I]; }, sink);
 }
 
 // Geometry of one population buffer.

@@ -68,13 +68,14 @@ __global__ void __launch_bounds__(kStepThreads) k_step(const typename Codec::raw
     });
 
     R dv[kQ];
-    static_for<kQ>([&](auto I) { dv[I] = Codec::dev(v[I], K.w[vel(I).shell]); });
+    constexpr R inv_scale = R(1.0 / Codec::kScale);
+    static_for<kQ>([&](auto I) { dv[I] = Codec::dev(v[I], K.w[vel(I).shell] * inv_scale); });
     const NodeMoments<R> m = moments_from_dev(dv);
     const NodeState<R> st = state_from_moments(m, K);
     if (!state_ok(st)) atomicOr(err, 1);
 
     T* out = dst + (int64_t)s * kQ * d.plane + (int64_t)z * nxy + (int64_t)y * d.nx + x;
-    equilibrium_relax<Codec, PROJECT>(st, K, tb, R(1) - tb, v,
+    equilibrium_relax<Codec, PROJECT>(st, K, tb * R(Codec::kScale), R(1) - tb, v,
                                       [&](auto I, R val) { out[(int64_t)I * d.plane] = Codec::to_raw(val); });
 }
 
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(256) k_init(typename Codec::raw_t* __restrict_
 #pragma unroll
     for (int i = 0; i < kQ; ++i) zero[i] = R(0);
     typename Codec::raw_t* out = dst + (int64_t)s * kQ * d.plane + node;
-    equilibrium_relax<Codec, PROJECT>(st, K, R(1), R(0), zero,
+    equilibrium_relax<Codec, PROJECT>(st, K, R(Codec::kScale), R(0), zero,
                                       [&](auto I, R val) { out[(int64_t)I * d.plane] = Codec::to_raw(val); });
 }
 
@@ -117,7 +118,10 @@ __device__ __forceinline__ NodeMoments<typename Codec::R> node_moments_at(const 
     const int64_t node = q - s * d.plane;
     const typename Codec::raw_t* base = src + (int64_t)s * kQ * d.plane + node;
     R dv[kQ];
-    static_for<kQ>([&](auto I) { dv[I] = Codec::dev(Codec::value(base[(int64_t)I * d.plane]), K.w[vel(I).shell]); });
+    constexpr R inv_scale = R(1.0 / Codec::kScale);
+    static_for<kQ>([&](auto I) {
+        dv[I] = Codec::dev(Codec::value(base[(int64_t)I * d.plane]), K.w[vel(I).shell] * inv_scale);
+    });
     return moments_from_dev(dv);
 }
 
@@ -188,7 +192,7 @@ __global__ void __launch_bounds__(256) k_to_f64(const typename Codec::raw_t* __r
     if constexpr (Codec::stores_f)
         f[k] = v;
     else
-        f[k] = w.w[i] * (1.0 + v);
+        f[k] = w.w[i] * (1.0 + v * (1.0 / Codec::kScale));
 }
 
 template <class Codec>
@@ -202,7 +206,7 @@ __global__ void __launch_bounds__(256) k_from_f64(const double* __restrict__ f, 
     if constexpr (Codec::stores_f)
         h = f[k];
     else
-        h = (f[k] - w.w[i]) / w.w[i];
+        h = (f[k] - w.w[i]) / w.w[i] * Codec::kScale;
     dst[e] = Codec::to_raw((typename Codec::R)h);
 }
 

@@ -22,11 +22,17 @@ struct LaunchConsts {
 // Storage precision codes (match lb_precision in gblb.h).
 enum Prec { kF64 = 0, kF32 = 1, kF16 = 2, kBF16 = 3 };
 
+// Step kernel variants: direct global loads, or shared-memory staging by TMA bulk copies.
+enum Variant { kVariantDirect = 0, kVariantStaged = 1 };
+
+// Tile width of the staged kernel for this grid and precision, 0 if it does not apply.
+int tma_tile_width(int prec, const Dims& d);
+
 size_t storage_bytes(int prec);
 
 // One fused pull step src -> dst over the whole grid.
-cudaError_t launch_step(int prec, bool project, const void* src, void* dst, const Dims& d, const LaunchConsts& c,
-                        double twobeta, int* err, cudaStream_t st);
+cudaError_t launch_step(int prec, bool project, int variant, const void* src, void* dst, const Dims& d,
+                        const LaunchConsts& c, double twobeta, int* err, cudaStream_t st);
 
 // Equilibrium of float64 fields for nodes [q0, q0 + count).
 cudaError_t launch_init(int prec, bool project, void* dst, const Dims& d, const LaunchConsts& c, int64_t q0,
@@ -50,8 +56,8 @@ cudaError_t launch_from_f64(int prec, const double* f, void* dst, const Dims& d,
 // Per-precision step launchers (defined in the per-precision translation units).
 cudaError_t launch_step_f64(bool project, const void* src, void* dst, const Dims& d, const LaunchConsts& c,
                             double twobeta, int* err, cudaStream_t st);
-cudaError_t launch_step_f32(int prec, bool project, const void* src, void* dst, const Dims& d, const LaunchConsts& c,
-                            double twobeta, int* err, cudaStream_t st);
+cudaError_t launch_step_f32(int prec, bool project, int variant, const void* src, void* dst, const Dims& d,
+                            const LaunchConsts& c, double twobeta, int* err, cudaStream_t st);
 
 inline dim3 step_grid(const Dims& d, int threads) {
     return dim3((unsigned)d.rows, (unsigned)((d.nx + threads - 1) / threads), 1);

@@ -24,6 +24,7 @@ PRECISION = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 LB_RD3Q41 = 41
 LB_FLAG_PAPER_LITERAL = 1
+LB_FLAG_NO_STAGING = 2
 
 
 class LbError(RuntimeError):
@@ -62,6 +63,8 @@ def lib():
         L.lb_state_bytes.restype = i64
         L.lb_get_state.argtypes = [vp, vp, ctypes.c_int]
         L.lb_set_state.argtypes = [vp, vp, ctypes.c_int]
+        L.lb_step_variant.argtypes = [vp]
+        L.lb_step_variant.restype = ctypes.c_int
         L.lb_time.argtypes = [vp]
         L.lb_time.restype = i64
         L.lb_sync.argtypes = [vp]
@@ -192,6 +195,10 @@ def lb_get_state(ctx, raw):
 def lb_set_state(ctx, raw):
     p, d = _ptr(raw)
     _check(lib().lb_set_state(ctx, p, d), ctx)
+
+
+def lb_step_variant(ctx):
+    return int(lib().lb_step_variant(ctx))
 
 
 def lb_time(ctx):

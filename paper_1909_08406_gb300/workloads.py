@@ -104,12 +104,15 @@ def fourier_box_field(nx, ny, nz, seed, kmax=8, device="cpu"):
     ks = np.arange(-kmax, kmax)
     coef = torch.from_numpy(a - 1j * b).to(device)  # field = Re sum c_k e^{i k.x}
     coef[kmax, kmax, kmax] = 0
-    kz, ky, kx = [torch.from_numpy(ks).to(device)] * 3
+    k = torch.from_numpy(ks.astype(np.float64)).to(device)
     out = []
+
+    def phase(n, shift):
+        pos = torch.arange(n, dtype=F64, device=device) + shift
+        return torch.exp(1j * (2 * math.pi / n) * k[:, None] * pos[None, :])  # complex128 [nk, n]
+
     for shift in (0.0, 0.5):
-        ex = torch.exp(2j * math.pi * kx[:, None] * (torch.arange(nx, device=device)[None, :] + shift) / nx)
-        ey = torch.exp(2j * math.pi * ky[:, None] * (torch.arange(ny, device=device)[None, :] + shift) / ny)
-        ez = torch.exp(2j * math.pi * kz[:, None] * (torch.arange(nz, device=device)[None, :] + shift) / nz)
+        ex, ey, ez = phase(nx, shift), phase(ny, shift), phase(nz, shift)
         # coef[kz, ky, kx] -> field[z, y, x]
         g = torch.einsum("abc,cx->abx", coef, ex)
         g = torch.einsum("abx,by->ayx", g, ey)

@@ -9,6 +9,10 @@ import oracle
 TORCH_DTYPE = {"f64": torch.float64, "f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}
 # unit roundoff of each storage type (half the spacing at 1)
 STORE_EPS = {"f64": 2.0 ** -53, "f32": 2.0 ** -24, "f16": 2.0 ** -11, "bf16": 2.0 ** -8}
+# scale of the stored value: f16 stores 2^8 h (documented in gblb.h)
+STORE_SCALE = {"f64": 1.0, "f32": 1.0, "f16": 256.0, "bf16": 1.0}
+# largest rounding error near zero, in units of h: half the smallest subnormal spacing
+STORE_TINY = {"f64": 0.0, "f32": 2.0 ** -150, "f16": 2.0 ** -25 / 256.0, "bf16": 2.0 ** -134}
 
 
 def lib_to_oracle_perm():
@@ -38,4 +42,4 @@ def decode(raw, prec, w_lib):
     if prec == "f64":
         return v
     w = np.asarray(w_lib)[None, :, None, None, None]
-    return w * (1.0 + v)
+    return w * (1.0 + v / STORE_SCALE[prec])

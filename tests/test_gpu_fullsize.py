@@ -1,0 +1,191 @@
+"""Parity at the full benchmark sizes, in the launch configuration bench.py times.
+
+The oracle cannot run 256^3 or 512^3 grids for many steps, so the check is
+one step on sampled nodes: the GPU state at step t is read back through the
+C ABI, the test gathers each sampled node's 41 incoming populations with its
+own index arithmetic (real node positions, as in the oracle's streaming pins),
+the oracle collides them in FP64, and the result is compared with the GPU
+state at step t + 1 at that node.  Per-population bound on h = f/w - 1:
+    |h_gpu - h_oracle| <= eps_store |h_oracle| + tiny_store + 2e-6 max_i |h_oracle| + 1e-12
+(one rounding to the storage type -- relative half-spacing eps_store, or half
+the smallest subnormal spacing tiny_store near zero -- plus FP32 evaluation of
+the equilibrium in deviation form).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import STORE_EPS, STORE_SCALE, STORE_TINY, TORCH_DTYPE
+from paper_1909_08406_gb300 import lb
+from paper_1909_08406_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+NU = 0.01
+
+
+def _sample_nodes(n, count, seed):
+    rng = np.random.default_rng(seed)
+    s = rng.integers(0, 2, count)
+    z = rng.integers(0, n, count)
+    y = rng.integers(0, n, count)
+    x = rng.integers(0, n, count)
+    # always include the faces and corners, where the periodic wrap happens
+    edge = np.array([[0, 0, 0, 0], [1, n - 1, n - 1, n - 1], [0, n - 1, 0, 1], [1, 0, n - 1, n - 2],
+                     [1, 1, 0, n - 1], [0, n - 2, n - 1, 0]])
+    return np.concatenate([np.stack([s, z, y, x], 1), edge])
+
+
+def _upwind(nodes, c, n):
+    """Source (s', z', y', x') of each population of each node: position p - c_i, periodic."""
+    s, z, y, x = nodes.T
+    p = np.stack([x, y, z], 1).astype(np.float64) + 0.5 * s[:, None]  # [m, 3]
+    q = np.mod(p[:, None, :] - c[None, :, :], n)  # [m, 41, 3]
+    frac = q - np.floor(q)
+    sp = (frac[..., 0] == 0.5).astype(np.int64)
+    cell = np.floor(q).astype(np.int64)
+    return sp, cell[..., 2], cell[..., 1], cell[..., 0]
+
+
+def _decode(vals, prec, w):
+    v = vals.to(torch.float64).cpu().numpy()
+    return v if prec == "f64" else w * (1.0 + v / STORE_SCALE[prec])
+
+
+def _one_step_sampled(n, prec, fields, steps_before, seed):
+    th0 = lb.lb_theta0()
+    tau = NU / th0
+    c2, w = lb.lb_velocity_set()
+    c = c2.astype(np.float64) / 2.0
+    ctx = lb.lb_init((n, n, n), tau, prec)
+    try:
+        lb.lb_set_fields(ctx, fields["rho"], fields["u"], fields["theta"])
+        lb.lb_step(ctx, steps_before)
+        shape = (2, 41, n, n, n)
+        a = torch.empty(shape, dtype=TORCH_DTYPE[prec], device="cuda")
+        lb.lb_get_state(ctx, a)
+        lb.lb_step(ctx, 1)
+        b = torch.empty_like(a)
+        lb.lb_get_state(ctx, b)
+        lb.lb_sync(ctx)
+    finally:
+        lb.lb_destroy(ctx)
+    nodes = _sample_nodes(n, 3000, seed)
+    sp, zs, ys, xs = _upwind(nodes, c, n)
+    ii = np.broadcast_to(np.arange(41), sp.shape)
+    t = lambda v: torch.from_numpy(np.ascontiguousarray(v)).cuda()
+    fin = _decode(a[t(sp), t(ii), t(zs), t(ys), t(xs)], prec, w)  # [m, 41] library order
+    s, z, y, x = nodes.T
+    out = _decode(b[t(s)[:, None], t(ii), t(z)[:, None], t(y)[:, None], t(x)[:, None]], prec, w)
+    del a, b
+    torch.cuda.empty_cache()
+    # oracle collision in its own velocity order
+    c2o = oracle.velocities_doubled()
+    perm = np.array([int(np.where((c2o == v).all(1))[0][0]) for v in c2])
+    worst = 0.0
+    for k in range(len(nodes)):
+        fo = np.empty(41)
+        fo[perm] = fin[k]
+        ref = oracle.collide(fo, tau)[perm]
+        h_ref = ref / w - 1
+        h_got = out[k] / w - 1
+        tol = STORE_EPS[prec] * np.abs(h_ref) + STORE_TINY[prec] + 2e-6 * np.abs(h_ref).max() + 1e-12
+        worst = max(worst, float(np.max(np.abs(h_got - h_ref) / tol)))
+    return worst
+
+
+def test_config2_f32_256_sampled_step():
+    n = 256
+    fields = wl.acoustic_thermal(n, lb.lb_theta0(), device="cuda")
+    assert _one_step_sampled(n, "f32", fields, 3, seed=1) <= 1.0
+
+
+@pytest.mark.parametrize("prec", ["f16", "bf16"])
+def test_config3_16bit_512_sampled_step(prec):
+    n = 512
+    fields = wl.thermoacoustic_pulse(n, lb.lb_theta0(), device="cuda")
+    assert _one_step_sampled(n, prec, fields, 3, seed=2) <= 1.0
+
+
+def _mode_series(prec, n, steps, every, fields, kx_mode, ky_mode):
+    """GPU run; projections of rho-1 on sin(2 pi kx x/n) and of theta/theta0-1 on cos(2 pi ky y/n)."""
+    th0 = lb.lb_theta0()
+    ctx = lb.lb_init((n, n, n), NU / th0, prec)
+    X, Y, _ = wl.node_positions(n, n, n, device="cuda")
+    Sx = torch.sin(2 * math.pi * kx_mode * X / n)
+    Cy = torch.cos(2 * math.pi * ky_mode * Y / n)
+    rho = torch.empty((2, n, n, n), dtype=torch.float64, device="cuda")
+    th = torch.empty_like(rho)
+    ts, ra, ta = [], [], []
+    try:
+        lb.lb_set_fields(ctx, fields["rho"], fields["u"], fields["theta"])
+        for t in range(0, steps + 1, every):
+            if t:
+                lb.lb_step(ctx, every)
+            lb.lb_get_moments(ctx, rho, None, th)
+            ts.append(t)
+            ra.append(float(((rho - 1) * Sx).sum() / (Sx * Sx).sum()))
+            ta.append(float(((th / th0 - 1) * Cy).sum() / (Cy * Cy).sum()))
+        lb.lb_sync(ctx)
+        final_rho = rho.clone()
+    finally:
+        lb.lb_destroy(ctx)
+    return np.array(ts, float), np.array(ra), np.array(ta), final_rho
+
+
+def _fit(t, a, k, cs0, g0):
+    from scipy.optimize import curve_fit
+
+    def model(t, As, w, phi, G, Ae, X):
+        return As * np.cos(w * t + phi) * np.exp(-G * t) + Ae * np.exp(-X * t)
+
+    p, _ = curve_fit(model, t, a, p0=[0.6 * a[0], cs0 * k, 0.0, g0, 0.4 * a[0], g0], maxfev=20000)
+    return {"w": p[1], "G": p[3], "X": p[5]}
+
+
+def test_config2_f32_physics_and_error_vs_f64():
+    """256^3 FP32, 1000 steps: sound speed and both decay rates of the acoustic (k = 4 along x) and
+    thermal (k = 2 along y) waves against the FP64 oracle (quasi-1D runs of the same modes), within
+    0.1%; density L2 error against the GPU FP64 mode <= 1e-4 of the wave amplitude."""
+    n, steps, every = 256, 1000, 5
+    th0 = lb.lb_theta0()
+    fields = wl.acoustic_thermal(n, th0, device="cuda")
+    t, ra, ta, rho32 = _mode_series("f32", n, steps, every, fields, 4, 2)
+    _, _, _, rho64 = _mode_series("f64", n, steps, 250, fields, 4, 2)
+    err = float(torch.sqrt(((rho32 - rho64) ** 2).mean())) / 1e-3
+    assert err <= 1e-4, err
+
+    cs = math.sqrt(5 * th0 / 3)
+    tau = NU / th0
+    # oracle: the same modes on quasi-1D grids (a wave along x with k = 4 on 256 cells is one
+    # wavelength on 64 cells; the y wave with k = 2 is one wavelength on 128 cells)
+    fa = wl.standing_wave(64, 1, 1, th0, amplitude=1e-3)
+    fo = oracle.init_fields(fa["rho"].numpy(), fa["u"].numpy(), fa["theta"].numpy())
+    Xa, _, _ = wl.node_positions(64, 1, 1)
+    Sa = np.sin(2 * math.pi * Xa.numpy() / 64)
+    Yb = wl.node_positions(1, 128, 1)[1].numpy()
+    Cb = np.cos(2 * math.pi * Yb / 128)
+    fb_fields = {"rho": torch.ones((2, 1, 128, 1), dtype=torch.float64),
+                 "u": torch.zeros((3, 2, 1, 128, 1), dtype=torch.float64),
+                 "theta": torch.from_numpy(th0 * (1 + 1e-3 * Cb))}
+    fb = oracle.init_fields(fb_fields["rho"].numpy(), fb_fields["u"].numpy(), fb_fields["theta"].numpy())
+    oa, ob = [], []
+    for k in range(len(t)):
+        r, _, _ = oracle.get_moments(fo)
+        oa.append(np.sum((r - 1) * Sa) / np.sum(Sa * Sa))
+        _, _, thb = oracle.get_moments(fb)
+        ob.append(np.sum((thb / th0 - 1) * Cb) / np.sum(Cb * Cb))
+        if k + 1 < len(t):
+            fo = oracle.step(fo, tau, every)
+            fb = oracle.step(fb, tau, every)
+    ka, kb = 2 * math.pi / 64, 2 * math.pi / 128
+    g_a, g_b = NU * ka * ka, NU * kb * kb
+    for (gpu, ora, k, g) in ((ra, np.array(oa), ka, g_a), (ta, np.array(ob), kb, g_b)):
+        fg = _fit(t, gpu, k, cs, g)
+        fr = _fit(t, ora, k, cs, g)
+        assert fg["w"] == pytest.approx(fr["w"], rel=1e-3)
+        assert fg["G"] == pytest.approx(fr["G"], rel=1e-3)
+        assert fg["X"] == pytest.approx(fr["X"], rel=1e-3)

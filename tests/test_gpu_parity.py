@@ -57,8 +57,13 @@ def _run_gpu(shape, tau, prec, fields, steps, flags=0):
     return f
 
 
+# (133,...) and the small grids run the direct-load kernel; nx = 128 / 256 / 384 run the
+# shared-memory-staged kernel (one tile per row, and first/middle/last tiles of a row)
+STAGED_SHAPES = [(128, 3, 2), (256, 1, 1), (384, 2, 3)]
+
+
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("shape", [(4, 4, 4), (3, 5, 7), (1, 2, 5), (133, 3, 2)])
+@pytest.mark.parametrize("shape", [(4, 4, 4), (3, 5, 7), (1, 2, 5), (133, 3, 2)] + STAGED_SHAPES)
 def test_streaming_is_bit_exact(prec, shape, perm, w_lib):
     nx, ny, nz = shape
     rng = np.random.default_rng(100 + nx)
@@ -97,8 +102,10 @@ def test_config1_f64_standing_wave_200_steps(perm):
 
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("project", [True, False])
-def test_random_fields_parity(prec, project, perm):
-    shape = (133, 5, 3)  # two x-blocks with a ragged tail, odd y/z
+@pytest.mark.parametrize("shape", [(133, 5, 3), (384, 3, 2), (128, 4, 3)])
+def test_random_fields_parity(prec, project, shape, perm):
+    # (133, 5, 3): direct kernel, two x-blocks with a ragged tail, odd y/z;
+    # (384, 3, 2) and (128, 4, 3): staged kernel (3 tiles per row; one tile per row)
     th0 = lb.lb_theta0()
     amp = 0.05 if prec in ("f64", "f32") else 0.02
     fl = wl.random_fields(*shape, th0, seed=7, du=amp, drho=amp, dtheta=amp)
@@ -218,6 +225,37 @@ def test_unstable_state_is_reported():
         assert e.value.status == -5
     finally:
         lb.lb_destroy(ctx)
+
+
+def test_step_variant_selection():
+    for shape, prec, flags, expect in [((256, 2, 2), "f16", 0, 256), ((384, 2, 2), "f32", 0, 128),
+                                       ((130, 2, 2), "f32", 0, 0), ((256, 2, 2), "f64", 0, 0),
+                                       ((256, 2, 2), "bf16", lb.LB_FLAG_NO_STAGING, 0)]:
+        ctx = lb.lb_init(shape, 0.5, prec, flags=flags)
+        try:
+            assert lb.lb_step_variant(ctx) == expect, (shape, prec, flags)
+        finally:
+            lb.lb_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
+def test_staged_and_direct_kernels_agree(prec):
+    shape = (256, 4, 3)
+    th0 = lb.lb_theta0()
+    fl = wl.random_fields(*shape, th0, seed=13, du=0.02, drho=0.02, dtheta=0.02)
+    outs = []
+    for flags in (0, lb.LB_FLAG_NO_STAGING):
+        ctx = lb.lb_init(shape, 0.3, prec, flags=flags)
+        try:
+            lb.lb_set_fields(ctx, fl["rho"], fl["u"], fl["theta"])
+            lb.lb_step(ctx, 10)
+            f = np.empty((2, 41, 3, 4, 256))
+            lb.lb_get_populations(ctx, f)
+        finally:
+            lb.lb_destroy(ctx)
+        outs.append(f)
+    rel = np.abs(outs[0] - outs[1]) / outs[1]
+    assert rel.max() <= RANDOM_FIELD_TOL[prec] / 4, rel.max()
 
 
 def test_free_streaming_time_counter():
