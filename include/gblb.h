@@ -75,7 +75,7 @@ typedef enum {
 
 /* lb_init flags */
 #define LB_FLAG_PAPER_LITERAL 1u /* equilibrium exactly as printed (no momentum projection) */
-#define LB_FLAG_NO_STAGING 2u    /* always use the direct-load step kernel (see lb_step_variant) */
+#define LB_FLAG_STAGED 2u        /* use the shared-memory-staged step kernel where it applies (see lb_step_variant) */
 
 typedef struct {
     int64_t nx, ny, nz; /* simple-cubic cells per axis, each >= 1; nodes = 2 nx ny nz */
@@ -142,7 +142,7 @@ lb_status lb_set_state(lb_ctx *ctx, const void *raw, int on_device);
 /* Step kernel used by this context: the tile width (128 or 256) of the
  * shared-memory-staged kernel, whose rows are fetched by TMA bulk copies
  * (FP32/FP16/BF16 storage, nx a multiple of 128 and of 16 bytes), or 0 for the
- * direct-load kernel (FP64, other grids, or LB_FLAG_NO_STAGING).  Both compute
+ * direct-load kernel (the default; FP64 and other grids always).  Both compute
  * the same update. */
 int lb_step_variant(const lb_ctx *ctx);
 
@@ -156,6 +156,43 @@ lb_status lb_destroy(lb_ctx *ctx);
 
 /* Message for the last failing call on ctx (or for a failing lb_init when ctx is NULL). */
 const char *lb_last_error(const lb_ctx *ctx);
+
+/* ------------------------------------------------------------------------
+ * Batched sweep of independent simulations (uneven grids, per-simulation tau).
+ * Not in the paper: many small simulations advanced in one launch so that
+ * the GPU is filled.  Each simulation is an lb_ctx owned by the batch
+ * (lb_batch_sim); use it with lb_set_fields / lb_get_moments / lb_conserved /
+ * lb_get_populations, but never lb_destroy it or lb_step it alone.
+ * ------------------------------------------------------------------------ */
+typedef struct lb_batch lb_batch;
+
+#define LB_BATCH_GRAPH 0      /* one batched launch per step, n steps replayed as one CUDA graph */
+#define LB_BATCH_PERSISTENT 1 /* one cooperative launch for all n steps, grid barrier between steps */
+#define LB_BATCH_SEQUENTIAL 2 /* each simulation stepped by its own launches (baseline) */
+
+/* nsims simulations, grids[k] and tau[k] each; precision and flags as lb_init. */
+lb_status lb_batch_init(lb_batch **out, int nsims, const lb_grid *grids, const double *tau, lb_precision precision,
+                        unsigned flags, void *cuda_stream);
+int lb_batch_size(const lb_batch *b);
+/* Context of simulation sim (0 <= sim < size), owned by the batch; NULL if out of range. */
+lb_ctx *lb_batch_sim(lb_batch *b, int sim);
+/* Autotuner: times every tile shape (TX x-nodes by RY rows per CTA) on this
+ * batch for reps steps each (the state is not advanced), keeps the fastest,
+ * and reports it and its time per step in ms.  Any output may be NULL. */
+lb_status lb_batch_tune(lb_batch *b, int reps, int *tx, int *ry, double *ms_per_step);
+/* Tile shape in use; lb_batch_set_tile accepts (16,4) (16,8) (32,2) (32,4) (64,1) (64,2) (128,1). */
+lb_status lb_batch_get_tile(const lb_batch *b, int *tx, int *ry);
+lb_status lb_batch_set_tile(lb_batch *b, int tx, int ry);
+/* Advance every simulation by n steps in the given mode (LB_BATCH_*).  Asynchronous. */
+lb_status lb_batch_step(lb_batch *b, int64_t n, int mode);
+/* Cycle budget of each grid-barrier wait of the persistent mode (default 4e9) and, for
+ * diagnostics, extra arrivals the barrier waits for (0 in normal use; > 0 makes every
+ * wait run out, which must end in LB_ERR_TIMEOUT, never a hang). */
+lb_status lb_batch_set_wait(lb_batch *b, long long limit_cycles, unsigned extra_arrivals);
+/* Wait for the batch's work; reports LB_ERR_TIMEOUT / LB_ERR_UNSTABLE from the device error words. */
+lb_status lb_batch_sync(lb_batch *b);
+lb_status lb_batch_destroy(lb_batch *b);
+const char *lb_batch_last_error(const lb_batch *b);
 
 #ifdef __cplusplus
 }

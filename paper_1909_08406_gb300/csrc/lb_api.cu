@@ -7,6 +7,7 @@
 #include <string>
 
 #include "gblb.h"
+#include "lb_ctx.h"
 #include "lb_launch.h"
 
 using namespace gblb;
@@ -24,6 +25,7 @@ struct Lattice {
     LaunchConsts lc;
     double theta0;
 };
+
 
 // Lattice constants from Table I.  w_0 = 1 - sum of the other weights and
 // theta_0 = sum_i w_i c_ix^2 (Sec. III, Eq. allWeights).  The rest-state
@@ -117,27 +119,9 @@ static const Lattice& lattice() {
     return L;
 }
 
-struct lb_ctx {
-    lb_grid g;
-    Dims d;
-    int prec;
-    bool project;
-    int variant;
-    double tau, twobeta;
-    cudaStream_t stream;
-    int device;
-    void* buf[2];
-    int cur;
-    size_t esize;
-    int* d_err;
-    double* d_partials;
-    int nblocks;
-    double* d_out5;
-    double* d_stage;
-    int64_t stage_doubles;
-    int64_t time;
-    std::string msg;
-};
+namespace gblb {
+const LaunchConsts& lattice_consts() { return lattice().lc; }
+}  // namespace gblb
 
 static std::string g_init_msg;
 
@@ -203,7 +187,7 @@ lb_status lb_init(lb_ctx** out, lb_grid grid, int velocity_set, double theta0, d
     if ((int)precision < LB_F64 || (int)precision > LB_F32_S16B)
         return fail(nullptr, LB_ERR_ARG, "lb_init: unknown precision");
     if (!(tau > 0.0)) return fail(nullptr, LB_ERR_ARG, "lb_init: tau must be > 0 (or +inf)");
-    if (flags & ~(LB_FLAG_PAPER_LITERAL | LB_FLAG_NO_STAGING)) return fail(nullptr, LB_ERR_ARG, "lb_init: unknown flag bits");
+    if (flags & ~(LB_FLAG_PAPER_LITERAL | LB_FLAG_STAGED)) return fail(nullptr, LB_ERR_ARG, "lb_init: unknown flag bits");
     const Lattice& L = lattice();
     if (theta0 > 0.0 && fabs(theta0 / L.theta0 - 1.0) > 1e-12)
         return fail(nullptr, LB_ERR_THETA0, "lb_init: theta0 differs from sum_i w_i c_ix^2 of the Table I weights");
@@ -217,7 +201,7 @@ lb_status lb_init(lb_ctx** out, lb_grid grid, int velocity_set, double theta0, d
     c->d.rows = 2 * grid.ny * grid.nz;
     c->prec = (int)precision;
     c->project = !(flags & LB_FLAG_PAPER_LITERAL);
-    c->variant = (flags & LB_FLAG_NO_STAGING) ? kVariantDirect : kVariantStaged;
+    c->variant = (flags & LB_FLAG_STAGED) ? kVariantStaged : kVariantDirect;
     c->tau = tau;
     c->twobeta = isinf(tau) ? 0.0 : 2.0 / (2.0 * tau + 1.0);
     c->stream = (cudaStream_t)cuda_stream;

@@ -1,0 +1,491 @@
+// Batched sweep: many independent RD3Q41 simulations of uneven grid sizes
+// and relaxation times advanced together.
+//
+// Work list: every simulation's nodes are cut into tiles of TX consecutive x
+// by RY consecutive rows; the tiles of all simulations are numbered
+// back to back (tile0[k] is the first tile of simulation k) and a CTA finds
+// its simulation by binary search.  Modes:
+//   LB_BATCH_GRAPH       one batched launch per time step, the n launches
+//                        captured once into a CUDA graph and replayed;
+//   LB_BATCH_PERSISTENT  one cooperative launch for all n steps: CTAs stride
+//                        over the work list and meet at a grid barrier between
+//                        steps (bounded spin; expiry -> LB_ERR_TIMEOUT);
+//   LB_BATCH_SEQUENTIAL  per simulation, one lb_step-style launch per step
+//                        (the baseline).
+// The tile shape (TX, RY) is chosen by lb_batch_tune, which times each
+// candidate shape on the batch itself.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "gblb.h"
+#include "lb_ctx.h"
+#include "lb_kernels.cuh"
+
+namespace gblb {
+
+struct BatchSim {
+    void* buf[2];
+    Dims d;
+    float tbf;
+    double tbd;
+    int64_t tile0;  // first tile of this simulation in the work list
+    int tiles_x;    // x-chunks per row group
+    int pad;
+};
+
+template <class R>
+__device__ __forceinline__ R tb_of(const BatchSim& s);
+template <>
+__device__ __forceinline__ float tb_of<float>(const BatchSim& s) {
+    return s.tbf;
+}
+template <>
+__device__ __forceinline__ double tb_of<double>(const BatchSim& s) {
+    return s.tbd;
+}
+
+// One tile of the work list.  Ld selects the load path: the read-only path for
+// one-step launches, L2-coherent loads inside the persistent kernel (a CTA may
+// read, in step k + 1, lines another CTA wrote in step k).
+template <class Codec, bool PROJECT, class Ld>
+__device__ __forceinline__ void batch_tile(const BatchSim* __restrict__ sims, int nsims, int64_t t, int parity,
+                                           const Consts<typename Codec::R>& K, int tx, int ry, int* err) {
+    using R = typename Codec::R;
+    using T = typename Codec::raw_t;
+    int lo = 0, hi = nsims - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sims[mid].tile0 <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const BatchSim& S = sims[lo];
+    const int64_t local = t - S.tile0;
+    const int64_t rg = local / S.tiles_x;
+    const int xc = (int)(local - rg * S.tiles_x);
+    const int x = xc * tx + (int)(threadIdx.x % tx);
+    const int64_t row = rg * ry + (int64_t)(threadIdx.x / tx);
+    if (x >= S.d.nx || row >= S.d.rows) return;
+    const int y = (int)(row % S.d.ny);
+    const int64_t zr = row / S.d.ny;
+    const int z = (int)(zr % S.d.nz);
+    const int s = (int)(zr / S.d.nz);
+    step_node<Codec, PROJECT, Ld>(static_cast<const T*>(S.buf[parity]), static_cast<T*>(S.buf[parity ^ 1]), S.d, K,
+                                  tb_of<R>(S), err, s, z, y, x);
+}
+
+template <class Codec, bool PROJECT>
+__global__ void __launch_bounds__(128) k_batch_step(const BatchSim* __restrict__ sims, int nsims, int parity,
+                                                    Consts<typename Codec::R> K, int tx, int ry, int* err) {
+    batch_tile<Codec, PROJECT, LoadNC>(sims, nsims, blockIdx.x, parity, K, tx, ry, err);
+}
+
+struct GridBar {
+    unsigned count;
+    unsigned gen;
+};
+
+// Grid-wide barrier for a cooperative launch.  Thread 0 of each CTA arrives
+// on a counter; the last arrival resets it and advances the generation; the
+// others spin on the generation with a cycle budget.  Returns false (for the
+// whole CTA) if the budget ran out.
+__device__ __forceinline__ bool grid_sync(GridBar* bar, unsigned expected, long long limit) {
+    __syncthreads();
+    int ok = 1;
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = &bar->gen;
+        const unsigned g = *vgen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&bar->count, 1u) + 1u;
+        if (arrived == expected) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*vgen == g) {
+                if (clock64() - t0 > limit) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    return __syncthreads_and(ok) != 0;
+}
+
+template <class Codec, bool PROJECT>
+__global__ void __launch_bounds__(128) k_batch_persistent(const BatchSim* __restrict__ sims, int nsims, int64_t ntiles,
+                                                          int64_t nsteps, int parity0, Consts<typename Codec::R> K,
+                                                          int tx, int ry, int* err, GridBar* bar, unsigned expected,
+                                                          long long limit) {
+    for (int64_t step = 0; step < nsteps; ++step) {
+        const int parity = (int)((parity0 + step) & 1);
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x)
+            batch_tile<Codec, PROJECT, LoadCG>(sims, nsims, t, parity, K, tx, ry, err);
+        if (step + 1 < nsteps && !grid_sync(bar, expected, limit)) {
+            if (threadIdx.x == 0) atomicOr(err, 2);
+            return;
+        }
+    }
+}
+
+template <class F>
+static cudaError_t dispatch_codec(int prec, F&& f) {
+    switch (prec) {
+        case kF64: return f(CodecF64{});
+        case kF32: return f(CodecF32{});
+        case kF16: return f(CodecF16{});
+        case kBF16: return f(CodecBF16{});
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class Codec>
+static const Consts<typename Codec::R>& consts_of(const LaunchConsts& c) {
+    if constexpr (std::is_same<typename Codec::R, double>::value)
+        return c.kd;
+    else
+        return c.kf;
+}
+
+}  // namespace gblb
+
+using namespace gblb;
+
+static const int kTileShapes[][2] = {{16, 4}, {16, 8}, {32, 2}, {32, 4}, {64, 1}, {64, 2}, {128, 1}};
+
+struct lb_batch {
+    int n = 0;
+    std::vector<lb_ctx*> ctx;
+    int prec = 0;
+    bool project = true;
+    int device = 0;
+    int sms = 0;
+    cudaStream_t user = nullptr;
+    cudaStream_t ps = nullptr;  // private stream (graph capture needs a non-legacy stream)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
+    BatchSim* d_sims = nullptr;
+    std::vector<BatchSim> h_sims;
+    int tx = 32, ry = 4;
+    int64_t ntiles = 0;
+    int* d_err = nullptr;
+    GridBar* d_bar = nullptr;
+    long long wait_limit = 4000000000LL;
+    unsigned extra_arrivals = 0;
+    struct GraphEntry {
+        int64_t steps;
+        int parity, tx, ry;
+        cudaGraphExec_t exec;
+    };
+    std::vector<GraphEntry> graphs;
+    int persistent_graph = -1;  // -1 untried, 0 direct launch, 1 captured in a graph
+    std::string msg;
+};
+
+static std::string g_batch_init_msg;
+
+static lb_status bfail(lb_batch* b, lb_status s, const std::string& m) {
+    if (b)
+        b->msg = m;
+    else
+        g_batch_init_msg = m;
+    return s;
+}
+
+#define BCK(b, call)                                                                                  \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return bfail(b, e_ == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA,               \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));                         \
+    } while (0)
+
+// Lay out the work list for tile shape (tx, ry) and upload it.
+static lb_status plan(lb_batch* b, int tx, int ry) {
+    int64_t t = 0;
+    for (int k = 0; k < b->n; ++k) {
+        BatchSim& s = b->h_sims[k];
+        const lb_ctx* c = b->ctx[k];
+        s.buf[0] = c->buf[0];
+        s.buf[1] = c->buf[1];
+        s.d = c->d;
+        s.tbd = c->twobeta;
+        s.tbf = (float)c->twobeta;
+        s.tiles_x = (int)((c->d.nx + tx - 1) / tx);
+        s.tile0 = t;
+        t += (int64_t)s.tiles_x * ((c->d.rows + ry - 1) / ry);
+    }
+    if (t > 0x7fffffffLL) return bfail(b, LB_ERR_ARG, "batch work list too long for one launch");
+    b->ntiles = t;
+    b->tx = tx;
+    b->ry = ry;
+    BCK(b, cudaMemcpyAsync(b->d_sims, b->h_sims.data(), sizeof(BatchSim) * b->n, cudaMemcpyHostToDevice, b->ps));
+    BCK(b, cudaStreamSynchronize(b->ps));
+    for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
+    b->graphs.clear();
+    return LB_OK;
+}
+
+static cudaError_t launch_batch_step(lb_batch* b, int parity, cudaStream_t st) {
+    const LaunchConsts& lc = lattice_consts();
+    return dispatch_codec(b->prec, [&](auto codec) {
+        using C = decltype(codec);
+        if (b->project)
+            k_batch_step<C, true><<<(unsigned)b->ntiles, b->tx * b->ry, 0, st>>>(b->d_sims, b->n, parity,
+                                                                                   consts_of<C>(lc), b->tx, b->ry,
+                                                                                   b->d_err);
+        else
+            k_batch_step<C, false><<<(unsigned)b->ntiles, b->tx * b->ry, 0, st>>>(b->d_sims, b->n, parity,
+                                                                                    consts_of<C>(lc), b->tx, b->ry,
+                                                                                    b->d_err);
+        return cudaGetLastError();
+    });
+}
+
+static cudaError_t launch_persistent(lb_batch* b, int64_t nsteps, int parity, cudaStream_t st, int* grid_out) {
+    const LaunchConsts& lc = lattice_consts();
+    return dispatch_codec(b->prec, [&](auto codec) -> cudaError_t {
+        using C = decltype(codec);
+        void (*kern)(const BatchSim*, int, int64_t, int64_t, int, Consts<typename C::R>, int, int, int*, GridBar*,
+                     unsigned, long long) =
+            b->project ? k_batch_persistent<C, true> : k_batch_persistent<C, false>;
+        int per_sm = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, b->tx * b->ry, 0);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        int64_t grid = (int64_t)per_sm * b->sms;
+        if (grid > b->ntiles) grid = b->ntiles;
+        *grid_out = (int)grid;
+        unsigned expected = (unsigned)grid + b->extra_arrivals;
+        e = cudaMemsetAsync(b->d_bar, 0, sizeof(GridBar), st);
+        if (e != cudaSuccess) return e;
+        const BatchSim* sims = b->d_sims;
+        int nsims = b->n;
+        int64_t ntiles = b->ntiles;
+        Consts<typename C::R> K = consts_of<C>(lc);
+        int tx = b->tx, ry = b->ry;
+        int* err = b->d_err;
+        GridBar* bar = b->d_bar;
+        long long limit = b->wait_limit;
+        void* args[] = {(void*)&sims, (void*)&nsims, (void*)&ntiles, (void*)&nsteps, (void*)&parity, (void*)&K,
+                        (void*)&tx, (void*)&ry, (void*)&err, (void*)&bar, (void*)&expected, (void*)&limit};
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)grid);
+        cfg.blockDim = dim3((unsigned)(tx * ry));
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelExC(&cfg, (const void*)kern, args);
+    });
+}
+
+extern "C" {
+
+lb_status lb_batch_init(lb_batch** out, int nsims, const lb_grid* grids, const double* tau, lb_precision precision,
+                        unsigned flags, void* cuda_stream) {
+    if (!out || nsims < 1 || !grids || !tau) return bfail(nullptr, LB_ERR_ARG, "lb_batch_init: bad argument");
+    *out = nullptr;
+    lb_batch* b = new lb_batch();
+    b->n = nsims;
+    b->prec = (int)precision;
+    b->project = !(flags & LB_FLAG_PAPER_LITERAL);
+    b->user = (cudaStream_t)cuda_stream;
+    for (int k = 0; k < nsims; ++k) {
+        lb_ctx* c = nullptr;
+        lb_status s = lb_init(&c, grids[k], LB_RD3Q41, 0.0, tau[k], precision, flags, cuda_stream);
+        if (s != LB_OK) {
+            std::string m = std::string("lb_batch_init: simulation ") + std::to_string(k) + ": " + lb_last_error(nullptr);
+            for (auto* p : b->ctx) lb_destroy(p);
+            delete b;
+            return bfail(nullptr, s, m);
+        }
+        b->ctx.push_back(c);
+    }
+    b->h_sims.resize(nsims);
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->ps, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->t1);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_sims, sizeof(BatchSim) * nsims);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_bar, sizeof(GridBar));
+    if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        lb_batch_destroy(b);
+        return bfail(nullptr, LB_ERR_CUDA, std::string("lb_batch_init: ") + cudaGetErrorString(e));
+    }
+    lb_status s = plan(b, 32, 4);
+    if (s != LB_OK) {
+        std::string m = b->msg;
+        lb_batch_destroy(b);
+        return bfail(nullptr, s, m);
+    }
+    *out = b;
+    return LB_OK;
+}
+
+int lb_batch_size(const lb_batch* b) { return b ? b->n : -1; }
+
+lb_ctx* lb_batch_sim(lb_batch* b, int sim) { return (b && sim >= 0 && sim < b->n) ? b->ctx[sim] : nullptr; }
+
+lb_status lb_batch_set_tile(lb_batch* b, int tx, int ry) {
+    if (!b) return LB_ERR_ARG;
+    bool known = false;
+    for (auto& t : kTileShapes) known |= (t[0] == tx && t[1] == ry);
+    if (!known) return bfail(b, LB_ERR_ARG, "lb_batch_set_tile: not one of the tile shapes");
+    BCK(b, cudaSetDevice(b->device));
+    return plan(b, tx, ry);
+}
+
+lb_status lb_batch_get_tile(const lb_batch* b, int* tx, int* ry) {
+    if (!b) return LB_ERR_ARG;
+    if (tx) *tx = b->tx;
+    if (ry) *ry = b->ry;
+    return LB_OK;
+}
+
+lb_status lb_batch_tune(lb_batch* b, int reps, int* tx_out, int* ry_out, double* ms_out) {
+    if (!b) return LB_ERR_ARG;
+    BCK(b, cudaSetDevice(b->device));
+    if (reps < 1) reps = 3;
+    // the trial steps read buf[cur] and write buf[1 - cur] without flipping: the state is unchanged
+    BCK(b, cudaEventRecord(b->ev_in, b->user));
+    BCK(b, cudaStreamWaitEvent(b->ps, b->ev_in, 0));
+    const int parity = b->ctx[0]->cur;
+    float best = 1e30f;
+    int bt = b->tx, br = b->ry;
+    for (auto& shape : kTileShapes) {
+        lb_status s = plan(b, shape[0], shape[1]);
+        if (s != LB_OK) return s;
+        BCK(b, launch_batch_step(b, parity, b->ps));  // warm-up
+        BCK(b, cudaEventRecord(b->t0, b->ps));
+        for (int r = 0; r < reps; ++r) BCK(b, launch_batch_step(b, parity, b->ps));
+        BCK(b, cudaEventRecord(b->t1, b->ps));
+        BCK(b, cudaEventSynchronize(b->t1));
+        float ms = 0.f;
+        BCK(b, cudaEventElapsedTime(&ms, b->t0, b->t1));
+        ms /= reps;
+        if (ms < best) {
+            best = ms;
+            bt = shape[0];
+            br = shape[1];
+        }
+    }
+    lb_status s = plan(b, bt, br);
+    if (s != LB_OK) return s;
+    if (tx_out) *tx_out = bt;
+    if (ry_out) *ry_out = br;
+    if (ms_out) *ms_out = best;
+    return LB_OK;
+}
+
+lb_status lb_batch_set_wait(lb_batch* b, long long limit_cycles, unsigned extra_arrivals) {
+    if (!b || limit_cycles < 1) return LB_ERR_ARG;
+    b->wait_limit = limit_cycles;
+    b->extra_arrivals = extra_arrivals;
+    return LB_OK;
+}
+
+lb_status lb_batch_step(lb_batch* b, int64_t nsteps, int mode) {
+    if (!b || nsteps < 0) return bfail(b, LB_ERR_ARG, "lb_batch_step: bad argument");
+    if (nsteps == 0) return LB_OK;
+    BCK(b, cudaSetDevice(b->device));
+    const int parity = b->ctx[0]->cur;
+    if (mode == LB_BATCH_SEQUENTIAL) {
+        for (auto* c : b->ctx) {
+            lb_status s = lb_step(c, nsteps);
+            if (s != LB_OK) return bfail(b, s, lb_last_error(c));
+        }
+        return LB_OK;
+    }
+    BCK(b, cudaEventRecord(b->ev_in, b->user));
+    BCK(b, cudaStreamWaitEvent(b->ps, b->ev_in, 0));
+    if (mode == LB_BATCH_GRAPH) {
+        cudaGraphExec_t exec = nullptr;
+        for (auto& g : b->graphs)
+            if (g.steps == nsteps && g.parity == parity && g.tx == b->tx && g.ry == b->ry) exec = g.exec;
+        if (!exec) {
+            cudaGraph_t graph = nullptr;
+            BCK(b, cudaStreamBeginCapture(b->ps, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaSuccess;
+            for (int64_t t = 0; t < nsteps && e == cudaSuccess; ++t) e = launch_batch_step(b, parity ^ (int)(t & 1), b->ps);
+            cudaError_t e2 = cudaStreamEndCapture(b->ps, &graph);
+            if (e != cudaSuccess) return bfail(b, LB_ERR_CUDA, std::string("batched launch during capture: ") + cudaGetErrorString(e));
+            if (e2 != cudaSuccess) return bfail(b, LB_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e2));
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return bfail(b, LB_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+            if (b->graphs.size() >= 8) {
+                cudaGraphExecDestroy(b->graphs.front().exec);
+                b->graphs.erase(b->graphs.begin());
+            }
+            b->graphs.push_back({nsteps, parity, b->tx, b->ry, exec});
+        }
+        BCK(b, cudaGraphLaunch(exec, b->ps));
+    } else if (mode == LB_BATCH_PERSISTENT) {
+        int grid = 0;
+        BCK(b, launch_persistent(b, nsteps, parity, b->ps, &grid));
+    } else {
+        return bfail(b, LB_ERR_ARG, "lb_batch_step: unknown mode");
+    }
+    BCK(b, cudaEventRecord(b->ev_out, b->ps));
+    BCK(b, cudaStreamWaitEvent(b->user, b->ev_out, 0));
+    for (auto* c : b->ctx) {
+        c->cur ^= (int)(nsteps & 1);
+        c->time += nsteps;
+    }
+    return LB_OK;
+}
+
+lb_status lb_batch_sync(lb_batch* b) {
+    if (!b) return LB_ERR_ARG;
+    BCK(b, cudaSetDevice(b->device));
+    BCK(b, cudaStreamSynchronize(b->ps));
+    BCK(b, cudaStreamSynchronize(b->user));
+    int h = 0;
+    BCK(b, cudaMemcpy(&h, b->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h & 2) return bfail(b, LB_ERR_TIMEOUT, "a grid barrier of the persistent batch kernel gave up waiting");
+    if (h) return bfail(b, LB_ERR_UNSTABLE, "a node reached rho <= 0, theta <= 0 or a non-finite moment");
+    for (auto* c : b->ctx) {
+        lb_status s = lb_sync(c);
+        if (s != LB_OK) return bfail(b, s, lb_last_error(c));
+    }
+    return LB_OK;
+}
+
+lb_status lb_batch_destroy(lb_batch* b) {
+    if (!b) return LB_OK;
+    cudaSetDevice(b->device);
+    if (b->ps) cudaStreamSynchronize(b->ps);
+    for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
+    for (auto* c : b->ctx) lb_destroy(c);
+    if (b->ps) cudaStreamDestroy(b->ps);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->t0) cudaEventDestroy(b->t0);
+    if (b->t1) cudaEventDestroy(b->t1);
+    cudaFree(b->d_sims);
+    cudaFree(b->d_err);
+    cudaFree(b->d_bar);
+    delete b;
+    return LB_OK;
+}
+
+const char* lb_batch_last_error(const lb_batch* b) { return b ? b->msg.c_str() : g_batch_init_msg.c_str(); }
+
+}  // extern "C"

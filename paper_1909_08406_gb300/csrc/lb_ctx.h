@@ -1,0 +1,37 @@
+// Internal definition of the solver context (opaque in gblb.h), shared by the
+// single-grid API and the batched API.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "gblb.h"
+#include "lb_launch.h"
+
+struct lb_ctx {
+    lb_grid g;
+    gblb::Dims d;
+    int prec;
+    bool project;
+    int variant;
+    double tau, twobeta;
+    cudaStream_t stream;
+    int device;
+    void* buf[2];  // ping-pong population buffers; buf[cur] holds the current state
+    int cur;
+    size_t esize;
+    int* d_err;    // sticky device error word: bit 0 unstable node, bit 1 wait timeout
+    double* d_partials;
+    int nblocks;
+    double* d_out5;
+    double* d_stage;
+    int64_t stage_doubles;
+    int64_t time;
+    std::string msg;
+};
+
+namespace gblb {
+const LaunchConsts& lattice_consts();
+}

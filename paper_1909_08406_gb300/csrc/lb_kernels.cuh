@@ -10,32 +10,35 @@ namespace gblb {
 
 constexpr int kStepThreads = 128;
 
-template <class T>
-__device__ __forceinline__ T ld_stream(const T* p) {
-    return __ldg(p);
-}
+// Load paths: the read-only (non-coherent) path for kernels whose inputs no
+// thread of the same launch writes, and L2-coherent loads for persistent
+// kernels that read, after a grid barrier, what other CTAs wrote.
+struct LoadNC {
+    template <class T>
+    static __device__ __forceinline__ T load(const T* p) {
+        return __ldg(p);
+    }
+};
+struct LoadCG {
+    template <class T>
+    static __device__ __forceinline__ T load(const T* p) {
+        return __ldcg(p);
+    }
+};
 
-// Fused pull update (Sec. II): node (s, z, y, x) gathers f*_i(x - c_i, t) for
-// all 41 velocities, computes its moments, the equilibrium and the BGK
-// relaxation, and writes its 41 post-collision values.  Integer links stay on
+// Fused pull update (Sec. II) of one node (s, z, y, x): gather f*_i(x - c_i, t)
+// for all 41 velocities, compute the moments, the equilibrium and the BGK
+// relaxation, and write the 41 post-collision values.  Integer links stay on
 // the sub-lattice (shifts 0, +-1, +-2 cells); the bcc-1/2 links come from the
 // other sub-lattice: for A (s = 0) a component +1/2 reads cell r - 1 and -1/2
 // reads cell r; for B (s = 1) +1/2 reads cell r and -1/2 reads cell r + 1.
-// Grid: blockIdx.x = row (s, z, y), blockIdx.y * blockDim.x + threadIdx.x = x.
-template <class Codec, bool PROJECT>
-__global__ void __launch_bounds__(kStepThreads) k_step(const typename Codec::raw_t* __restrict__ src,
-                                                       typename Codec::raw_t* __restrict__ dst, Dims d,
-                                                       Consts<typename Codec::R> K, typename Codec::R tb,
-                                                       int* __restrict__ err) {
+template <class Codec, bool PROJECT, class Ld = LoadNC>
+__device__ __forceinline__ void step_node(const typename Codec::raw_t* __restrict__ src,
+                                          typename Codec::raw_t* __restrict__ dst, const Dims& d,
+                                          const Consts<typename Codec::R>& K, typename Codec::R tb,
+                                          int* __restrict__ err, int s, int z, int y, int x) {
     using R = typename Codec::R;
     using T = typename Codec::raw_t;
-    const int x = blockIdx.y * blockDim.x + threadIdx.x;
-    if (x >= d.nx) return;
-    const int64_t row = blockIdx.x;
-    const int y = (int)(row % d.ny);
-    const int64_t zr = row / d.ny;
-    const int z = (int)(zr % d.nz);
-    const int s = (int)(zr / d.nz);
     const int64_t nxy = (int64_t)d.nx * d.ny;
 
     // coordinate / offset of the upwind cell for a shift delta = k - 2 (source = x - delta)
@@ -60,10 +63,10 @@ __global__ void __launch_bounds__(kStepThreads) k_step(const typename Codec::raw
         constexpr Vel c = vel(I);
         if constexpr (c.shell == 5) {
             const int64_t off = (c.z > 0 ? hzp : hzm) + (c.y > 0 ? hyp : hym) + (c.x > 0 ? hxp : hxm);
-            v[I] = Codec::value(ld_stream(other + (int64_t)I * d.plane + off));
+            v[I] = Codec::value(Ld::load(other + (int64_t)I * d.plane + off));
         } else {
             const int64_t off = zo[c.z / 2 + 2] + yo[c.y / 2 + 2] + xs[c.x / 2 + 2];
-            v[I] = Codec::value(ld_stream(same + (int64_t)I * d.plane + off));
+            v[I] = Codec::value(Ld::load(same + (int64_t)I * d.plane + off));
         }
     });
 
@@ -77,6 +80,23 @@ __global__ void __launch_bounds__(kStepThreads) k_step(const typename Codec::raw
     T* out = dst + (int64_t)s * kQ * d.plane + (int64_t)z * nxy + (int64_t)y * d.nx + x;
     equilibrium_relax<Codec, PROJECT>(st, K, tb * R(Codec::kScale), R(1) - tb, v,
                                       [&](auto I, R val) { out[(int64_t)I * d.plane] = Codec::to_raw(val); });
+}
+
+// Direct-load step kernel.  Grid: blockIdx.x = row (s, z, y),
+// blockIdx.y * blockDim.x + threadIdx.x = x.
+template <class Codec, bool PROJECT>
+__global__ void __launch_bounds__(kStepThreads) k_step(const typename Codec::raw_t* __restrict__ src,
+                                                       typename Codec::raw_t* __restrict__ dst, Dims d,
+                                                       Consts<typename Codec::R> K, typename Codec::R tb,
+                                                       int* __restrict__ err) {
+    const int x = blockIdx.y * blockDim.x + threadIdx.x;
+    if (x >= d.nx) return;
+    const int64_t row = blockIdx.x;
+    const int y = (int)(row % d.ny);
+    const int64_t zr = row / d.ny;
+    const int z = (int)(zr % d.nz);
+    const int s = (int)(zr / d.nz);
+    step_node<Codec, PROJECT>(src, dst, d, K, tb, err, s, z, y, x);
 }
 
 // Populations = equilibrium of the given float64 fields, for nodes

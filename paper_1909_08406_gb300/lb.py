@@ -24,7 +24,7 @@ PRECISION = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
 STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 LB_RD3Q41 = 41
 LB_FLAG_PAPER_LITERAL = 1
-LB_FLAG_NO_STAGING = 2
+LB_FLAG_STAGED = 2
 
 
 class LbError(RuntimeError):
@@ -216,3 +216,104 @@ def lb_destroy(ctx):
 def lb_last_error(ctx=None):
     m = lib().lb_last_error(ctx)
     return m.decode() if m else ""
+
+
+# ---------------------------------------------------------------------------
+# Batched sweep of independent simulations
+# ---------------------------------------------------------------------------
+LB_BATCH_GRAPH = 0
+LB_BATCH_PERSISTENT = 1
+LB_BATCH_SEQUENTIAL = 2
+_batch_bound = False
+
+
+def _bind_batch():
+    global _batch_bound
+    if _batch_bound:
+        return lib()
+    L = lib()
+    vp, i64 = ctypes.c_void_p, ctypes.c_int64
+    L.lb_batch_init.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_uint, vp]
+    L.lb_batch_size.argtypes = [vp]
+    L.lb_batch_size.restype = ctypes.c_int
+    L.lb_batch_sim.argtypes = [vp, ctypes.c_int]
+    L.lb_batch_sim.restype = vp
+    L.lb_batch_tune.argtypes = [vp, ctypes.c_int, vp, vp, vp]
+    L.lb_batch_get_tile.argtypes = [vp, vp, vp]
+    L.lb_batch_set_tile.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.lb_batch_step.argtypes = [vp, i64, ctypes.c_int]
+    L.lb_batch_set_wait.argtypes = [vp, ctypes.c_longlong, ctypes.c_uint]
+    L.lb_batch_sync.argtypes = [vp]
+    L.lb_batch_destroy.argtypes = [vp]
+    L.lb_batch_last_error.argtypes = [vp]
+    L.lb_batch_last_error.restype = ctypes.c_char_p
+    for name in ("lb_batch_init", "lb_batch_tune", "lb_batch_get_tile", "lb_batch_set_tile", "lb_batch_step",
+                 "lb_batch_set_wait", "lb_batch_sync", "lb_batch_destroy"):
+        getattr(L, name).restype = ctypes.c_int
+    _batch_bound = True
+    return L
+
+
+def _bcheck(status, b):
+    if status != LB_OK:
+        msg = _bind_batch().lb_batch_last_error(b)
+        raise LbError(status, msg.decode() if msg else "")
+
+
+def lb_batch_init(grids, taus, precision="f32", flags=0, stream=None):
+    """grids: list of (nx, ny, nz); taus: list of tau.  Returns an opaque batch handle."""
+    L = _bind_batch()
+    n = len(grids)
+    garr = (_Grid * n)(*[_Grid(*(int(v) for v in g)) for g in grids])
+    tarr = (ctypes.c_double * n)(*[float(t) for t in taus])
+    h = ctypes.c_void_p()
+    st = L.lb_batch_init(ctypes.byref(h), n, ctypes.cast(garr, ctypes.c_void_p), ctypes.cast(tarr, ctypes.c_void_p),
+                         PRECISION[precision] if isinstance(precision, str) else int(precision), int(flags),
+                         _stream(stream))
+    _bcheck(st, None)
+    return h.value
+
+
+def lb_batch_size(b):
+    return int(_bind_batch().lb_batch_size(b))
+
+
+def lb_batch_sim(b, sim):
+    """Context handle of simulation `sim` (owned by the batch: use with lb_set_fields etc., never lb_destroy)."""
+    h = _bind_batch().lb_batch_sim(b, int(sim))
+    if not h:
+        raise IndexError(sim)
+    return h
+
+
+def lb_batch_tune(b, reps=3):
+    """Autotune the tile shape; returns (tx, ry, ms_per_step)."""
+    tx, ry, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _bcheck(_bind_batch().lb_batch_tune(b, int(reps), ctypes.byref(tx), ctypes.byref(ry), ctypes.byref(ms)), b)
+    return tx.value, ry.value, ms.value
+
+
+def lb_batch_get_tile(b):
+    tx, ry = ctypes.c_int(), ctypes.c_int()
+    _bcheck(_bind_batch().lb_batch_get_tile(b, ctypes.byref(tx), ctypes.byref(ry)), b)
+    return tx.value, ry.value
+
+
+def lb_batch_set_tile(b, tx, ry):
+    _bcheck(_bind_batch().lb_batch_set_tile(b, int(tx), int(ry)), b)
+
+
+def lb_batch_step(b, n, mode=LB_BATCH_GRAPH):
+    _bcheck(_bind_batch().lb_batch_step(b, int(n), int(mode)), b)
+
+
+def lb_batch_set_wait(b, limit_cycles, extra_arrivals=0):
+    _bcheck(_bind_batch().lb_batch_set_wait(b, int(limit_cycles), int(extra_arrivals)), b)
+
+
+def lb_batch_sync(b):
+    _bcheck(_bind_batch().lb_batch_sync(b), b)
+
+
+def lb_batch_destroy(b):
+    _bcheck(_bind_batch().lb_batch_destroy(b), b)

@@ -1,0 +1,103 @@
+"""Batched sweep (many independent simulations, uneven grids, per-simulation tau):
+every mode against the FP64 oracle per simulation, the modes against each
+other, the autotuner, and the bounded grid barrier of the persistent mode."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import lib_to_oracle_perm, to_oracle_order
+from paper_1909_08406_gb300 import lb
+from paper_1909_08406_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+GRIDS = [(12, 8, 6), (16, 16, 16), (20, 10, 8), (8, 8, 8), (33, 5, 4)]
+TAUS = [0.55, 0.9, 0.6, 0.75, 1.0]
+TOL = {"f64": 1e-12, "f32": 2e-7}
+
+
+def _fields(k):
+    th0 = lb.lb_theta0()
+    return wl.random_fields(*GRIDS[k], th0, seed=40 + k, du=0.03, drho=0.03, dtheta=0.03)
+
+
+def _run(prec, mode, steps, tile=None):
+    b = lb.lb_batch_init(GRIDS, TAUS, prec)
+    try:
+        for k in range(len(GRIDS)):
+            fl = _fields(k)
+            lb.lb_set_fields(lb.lb_batch_sim(b, k), fl["rho"].cuda(), fl["u"].cuda(), fl["theta"].cuda())
+        if tile:
+            lb.lb_batch_set_tile(b, *tile)
+        lb.lb_batch_step(b, steps, mode)
+        lb.lb_batch_sync(b)
+        out = []
+        for k, (nx, ny, nz) in enumerate(GRIDS):
+            f = np.empty((2, 41, nz, ny, nx))
+            lb.lb_get_populations(lb.lb_batch_sim(b, k), f)
+            out.append(f)
+    finally:
+        lb.lb_batch_destroy(b)
+    return out
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("mode", [lb.LB_BATCH_GRAPH, lb.LB_BATCH_PERSISTENT, lb.LB_BATCH_SEQUENTIAL])
+def test_batch_modes_match_oracle(prec, mode):
+    steps = 9  # odd: exercises the buffer parity bookkeeping
+    perm = lib_to_oracle_perm()
+    got = _run(prec, mode, steps)
+    for k in range(len(GRIDS)):
+        fl = _fields(k)
+        ref = oracle.step(oracle.init_fields(fl["rho"].numpy(), fl["u"].numpy(), fl["theta"].numpy()), TAUS[k], steps)
+        rel = np.abs(to_oracle_order(got[k], perm) - ref) / ref
+        assert rel.max() <= TOL[prec], (k, rel.max())
+
+
+@pytest.mark.parametrize("tile", [(16, 4), (16, 8), (32, 2), (32, 4), (64, 1), (64, 2), (128, 1)])
+def test_batch_tile_shapes_agree(tile):
+    a = _run("f32", lb.LB_BATCH_GRAPH, 4, tile=tile)
+    b = _run("f32", lb.LB_BATCH_SEQUENTIAL, 4)
+    for x, y in zip(a, b):
+        assert np.max(np.abs(x - y) / y) <= 1e-7
+
+
+def test_autotuner_keeps_state_and_picks_a_shape():
+    b = lb.lb_batch_init(GRIDS, TAUS, "f32")
+    try:
+        for k in range(len(GRIDS)):
+            fl = _fields(k)
+            lb.lb_set_fields(lb.lb_batch_sim(b, k), fl["rho"].cuda(), fl["u"].cuda(), fl["theta"].cuda())
+        lb.lb_batch_step(b, 3, lb.LB_BATCH_GRAPH)
+        before = [torch.empty(lb.lb_state_bytes(lb.lb_batch_sim(b, k)), dtype=torch.uint8, device="cuda")
+                  for k in range(len(GRIDS))]
+        for k, t in enumerate(before):
+            lb.lb_get_state(lb.lb_batch_sim(b, k), t)
+        tx, ry, ms = lb.lb_batch_tune(b, reps=2)
+        assert (tx, ry) == lb.lb_batch_get_tile(b)
+        assert ms > 0
+        for k, t in enumerate(before):
+            after = torch.empty_like(t)
+            lb.lb_get_state(lb.lb_batch_sim(b, k), after)
+            assert torch.equal(after, t)
+        lb.lb_batch_sync(b)
+    finally:
+        lb.lb_batch_destroy(b)
+
+
+def test_persistent_barrier_timeout_is_reported_not_hung():
+    """A grid barrier waiting for an arrival that never comes gives LB_ERR_TIMEOUT within its
+    cycle budget, and the GPU stays usable."""
+    b = lb.lb_batch_init(GRIDS[:2], TAUS[:2], "f32")
+    try:
+        lb.lb_batch_set_wait(b, 2_000_000, extra_arrivals=1)  # ~1 ms budget, barrier can never complete
+        lb.lb_batch_step(b, 3, lb.LB_BATCH_PERSISTENT)
+        with pytest.raises(lb.LbError) as e:
+            lb.lb_batch_sync(b)
+        assert e.value.status == -6
+    finally:
+        lb.lb_batch_destroy(b)
+    # a fresh batch still runs normally
+    out = _run("f32", lb.LB_BATCH_PERSISTENT, 2)
+    assert all(np.isfinite(f).all() for f in out)

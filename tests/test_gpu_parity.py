@@ -57,14 +57,15 @@ def _run_gpu(shape, tau, prec, fields, steps, flags=0):
     return f
 
 
-# (133,...) and the small grids run the direct-load kernel; nx = 128 / 256 / 384 run the
-# shared-memory-staged kernel (one tile per row, and first/middle/last tiles of a row)
+# With LB_FLAG_STAGED, nx = 128 / 256 / 384 run the shared-memory-staged kernel (one tile per
+# row, and first/middle/last tiles of a row); every other case runs the direct-load kernel.
 STAGED_SHAPES = [(128, 3, 2), (256, 1, 1), (384, 2, 3)]
 
 
+@pytest.mark.parametrize("staged", [False, True])
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("shape", [(4, 4, 4), (3, 5, 7), (1, 2, 5), (133, 3, 2)] + STAGED_SHAPES)
-def test_streaming_is_bit_exact(prec, shape, perm, w_lib):
+def test_streaming_is_bit_exact(prec, shape, staged, perm, w_lib):
     nx, ny, nz = shape
     rng = np.random.default_rng(100 + nx)
     h = 0.1 * rng.uniform(-1, 1, size=(2, 41, nz, ny, nx))
@@ -73,7 +74,7 @@ def test_streaming_is_bit_exact(prec, shape, perm, w_lib):
     else:
         stored = h
     raw = torch.from_numpy(stored).to(TORCH_DTYPE[prec]).cuda().contiguous()
-    ctx = lb.lb_init(shape, math.inf, prec)
+    ctx = lb.lb_init(shape, math.inf, prec, flags=lb.LB_FLAG_STAGED if staged else 0)
     try:
         lb.lb_set_state(ctx, raw)
         lb.lb_step(ctx, 1)
@@ -100,10 +101,11 @@ def test_config1_f64_standing_wave_200_steps(perm):
     assert rel.max() <= 1e-12, rel.max()
 
 
+@pytest.mark.parametrize("staged", [False, True])
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("project", [True, False])
 @pytest.mark.parametrize("shape", [(133, 5, 3), (384, 3, 2), (128, 4, 3)])
-def test_random_fields_parity(prec, project, shape, perm):
+def test_random_fields_parity(prec, project, shape, staged, perm):
     # (133, 5, 3): direct kernel, two x-blocks with a ragged tail, odd y/z;
     # (384, 3, 2) and (128, 4, 3): staged kernel (3 tiles per row; one tile per row)
     th0 = lb.lb_theta0()
@@ -111,8 +113,8 @@ def test_random_fields_parity(prec, project, shape, perm):
     fl = wl.random_fields(*shape, th0, seed=7, du=amp, drho=amp, dtheta=amp)
     tau = 0.3
     steps = 20
-    got = to_oracle_order(_run_gpu(shape, tau, prec, fl, steps, flags=0 if project else lb.LB_FLAG_PAPER_LITERAL),
-                          perm)
+    flags = (0 if project else lb.LB_FLAG_PAPER_LITERAL) | (lb.LB_FLAG_STAGED if staged else 0)
+    got = to_oracle_order(_run_gpu(shape, tau, prec, fl, steps, flags=flags), perm)
     ref = oracle.step(oracle.init_fields(*_fields_np(fl), project=project), tau, steps, project=project)
     rel = np.abs(got - ref) / np.abs(ref)
     assert rel.max() <= RANDOM_FIELD_TOL[prec], rel.max()
@@ -228,9 +230,10 @@ def test_unstable_state_is_reported():
 
 
 def test_step_variant_selection():
-    for shape, prec, flags, expect in [((256, 2, 2), "f16", 0, 256), ((384, 2, 2), "f32", 0, 128),
-                                       ((130, 2, 2), "f32", 0, 0), ((256, 2, 2), "f64", 0, 0),
-                                       ((256, 2, 2), "bf16", lb.LB_FLAG_NO_STAGING, 0)]:
+    S = lb.LB_FLAG_STAGED
+    for shape, prec, flags, expect in [((256, 2, 2), "f16", S, 256), ((384, 2, 2), "f32", S, 128),
+                                       ((130, 2, 2), "f32", S, 0), ((256, 2, 2), "f64", S, 0),
+                                       ((256, 2, 2), "bf16", 0, 0)]:
         ctx = lb.lb_init(shape, 0.5, prec, flags=flags)
         try:
             assert lb.lb_step_variant(ctx) == expect, (shape, prec, flags)
@@ -244,7 +247,7 @@ def test_staged_and_direct_kernels_agree(prec):
     th0 = lb.lb_theta0()
     fl = wl.random_fields(*shape, th0, seed=13, du=0.02, drho=0.02, dtheta=0.02)
     outs = []
-    for flags in (0, lb.LB_FLAG_NO_STAGING):
+    for flags in (lb.LB_FLAG_STAGED, 0):
         ctx = lb.lb_init(shape, 0.3, prec, flags=flags)
         try:
             lb.lb_set_fields(ctx, fl["rho"], fl["u"], fl["theta"])
