@@ -49,7 +49,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-batch", action="store_true", help="skip the batched 64-simulation sweep")
     p.add_argument("--batch-steps", type=int, default=1000)
-    p.add_argument("--staged", action="store_true", help="headline run on the TMA-staged step kernel")
+    p.add_argument("--kernel", type=int, default=None,
+                   help="step kernel for the headline run (LB_KERNEL_* id); default: the fastest that applies")
     return p.parse_args()
 
 
@@ -294,43 +295,65 @@ def main():
     precs = [args.precision] + ([] if args.no_secondary else [p for p in ("f32", "bf16", "f16", "f64")
                                                               if p != args.precision])
     results = {}
+    by_kernel = {}
     clocks = None
-    head_flags = lb.LB_FLAG_STAGED if args.staged else 0
-    runs = [(args.precision, head_flags)] + [(p, 0) for p in precs[1:]]
-    if not args.no_secondary:
-        # the other step kernel on the headline precision, for comparison
-        runs.insert(1, (args.precision, lb.LB_FLAG_STAGED ^ head_flags))
-    for prec, flags in runs:
-        head = prec == args.precision and flags == head_flags
-        key = prec if flags == 0 else prec + "_staged"
-        steps = args.steps if head else (max(3, args.steps // 10) if prec == "f64" else max(5, args.steps // 2))
-        warm = args.warmup if head else 3
-        ctx = lb.lb_init((n, n, n), tau, prec, flags=flags)
-        variant = lb.lb_step_variant(ctx)
+
+    def timed_run(prec, kernel, steps, warm, sample_clocks):
+        ctx = lb.lb_init((n, n, n), tau, prec)
         try:
             lb.lb_set_fields(ctx, fields["rho"], fields["u"], fields["theta"])
+            if kernel is None:
+                lb.lb_tune(ctx, reps=3)
+            else:
+                lb.lb_set_step_kernel(ctx, kernel)
+            used = lb.lb_step_variant(ctx)
             lb.lb_sync(ctx)
             barrier()
             torch.cuda.synchronize()
-            sampler = ClockSampler(local) if head else None
+            sampler = ClockSampler(local) if sample_clocks else None
             if sampler:
                 sampler.__enter__()
             total_ms, per = time_steps(lb, ctx, torch, steps, warm)
             if sampler:
                 sampler.__exit__(None, None, None)
-                clocks = sampler.summary()
             barrier()
             total_ms = max_over_ranks(total_ms)
-            alg = nodes * 41 * 2 * BYTES[prec]
-            avg_ms = sum(per) / len(per)
-            results[key] = {"mlups": world * nodes * steps / (total_ms * 1e-3) / 1e6,
-                            "ms_per_step": total_ms / steps, "kernel_ms": avg_ms,
-                            "achieved_gbs": alg / (avg_ms * 1e-3) / 1e9, "alg_bytes_per_launch": alg,
-                            "steps": steps, "warmup": warm,
-                            "kernel": f"k_step_tma (TMA-staged, tile {variant})" if variant else "k_step (direct)"}
         finally:
             lb.lb_destroy(ctx)
         torch.cuda.empty_cache()
+        alg = nodes * 41 * 2 * BYTES[prec]
+        avg_ms = sum(per) / len(per)
+        return {"mlups": world * nodes * steps / (total_ms * 1e-3) / 1e6, "ms_per_step": total_ms / steps,
+                "kernel_ms": avg_ms, "achieved_gbs": alg / (avg_ms * 1e-3) / 1e9, "alg_bytes_per_launch": alg,
+                "steps": steps, "warmup": warm, "kernel_id": used, "kernel": lb.KERNEL_NAMES[used]}, sampler
+
+    # headline precision: every step kernel that applies to this grid, a short run each; the
+    # fastest is then timed in full (the same choice lb_tune makes)
+    head = args.precision
+    kernels = [args.kernel] if args.kernel is not None else [lb.LB_KERNEL_DIRECT1, lb.LB_KERNEL_DIRECT2,
+                                                            lb.LB_KERNEL_DIRECT2R, lb.LB_KERNEL_STAGED]
+    probe_ctx = lb.lb_init((n, n, n), tau, head)
+    applicable = []
+    for k in kernels:
+        lb.lb_set_step_kernel(probe_ctx, k)
+        if lb.lb_step_variant(probe_ctx) == k and k not in applicable:
+            applicable.append(k)
+    lb.lb_destroy(probe_ctx)
+    torch.cuda.empty_cache()
+    if len(applicable) > 1:
+        for k in applicable:
+            r, _ = timed_run(head, k, max(5, args.steps // 3), 2, False)
+            by_kernel[lb.KERNEL_NAMES[k]] = {"mlups": r["mlups"], "achieved_gbs": r["achieved_gbs"],
+                                             "ms_per_step": r["ms_per_step"]}
+        best = max(applicable, key=lambda k: by_kernel[lb.KERNEL_NAMES[k]]["mlups"])
+    else:
+        best = applicable[0]
+    results[head], sampler = timed_run(head, best, args.steps, args.warmup, True)
+    clocks = sampler.summary()
+    if not args.no_secondary:
+        for prec in precs[1:]:
+            steps = max(3, args.steps // 10) if prec == "f64" else max(5, args.steps // 2)
+            results[prec], _ = timed_run(prec, None, steps, 3, False)
 
     batch = None
     if not args.no_batch and world == 1:
@@ -370,7 +393,7 @@ def main():
 
     if rank != 0:
         return
-    r = results[args.precision + ("_staged" if args.staged else "")]
+    r = results[args.precision]
     peak, peak_kind = measured_peaks()
     traffic = ncu_traffic(args.precision, n)
     line = {
@@ -388,6 +411,7 @@ def main():
         "by_precision": {p: {"mlups": v["mlups"], "achieved_gbs": v["achieved_gbs"],
                              "frac_of_hbm": v["achieved_gbs"] / peak, "ms_per_step": v["ms_per_step"],
                              "steps": v["steps"], "kernel": v["kernel"]} for p, v in results.items()},
+        "by_kernel": by_kernel,
         "batch": batch,
         "gpu_launches": r["steps"],
         "clocks": clocks,

@@ -75,7 +75,7 @@ typedef enum {
 
 /* lb_init flags */
 #define LB_FLAG_PAPER_LITERAL 1u /* equilibrium exactly as printed (no momentum projection) */
-#define LB_FLAG_STAGED 2u        /* use the shared-memory-staged step kernel where it applies (see lb_step_variant) */
+#define LB_FLAG_STAGED 2u        /* start with LB_KERNEL_STAGED (see lb_set_step_kernel) */
 
 typedef struct {
     int64_t nx, ny, nz; /* simple-cubic cells per axis, each >= 1; nodes = 2 nx ny nz */
@@ -139,12 +139,30 @@ int64_t lb_state_bytes(const lb_ctx *ctx);
 lb_status lb_get_state(lb_ctx *ctx, void *raw, int on_device);
 lb_status lb_set_state(lb_ctx *ctx, const void *raw, int on_device);
 
-/* Step kernel used by this context: the tile width (128 or 256) of the
- * shared-memory-staged kernel, whose rows are fetched by TMA bulk copies
- * (FP32/FP16/BF16 storage, nx a multiple of 128 and of 16 bytes), or 0 for the
- * direct-load kernel (the default; FP64 and other grids always).  Both compute
- * the same update. */
+/* Step kernels.  All compute the same update; they differ in how the 41
+ * upwind values reach the registers:
+ *   LB_KERNEL_DIRECT1  one node per thread, direct global loads
+ *   LB_KERNEL_DIRECT2  two rows per thread, packed FP32x2 arithmetic (not FP64;
+ *                      ny even, nx*ny*nz < 2^32)
+ *   LB_KERNEL_DIRECT2R the same with a register budget for 4 CTAs per SM
+ *   LB_KERNEL_STAGED   tiles of 128/256 x fetched by TMA bulk copies into a
+ *                      shared-memory ring (not FP64; nx a multiple of 128 and
+ *                      of 16 bytes)
+ *   LB_KERNEL_AUTO     DIRECT2 where it applies, else DIRECT1 (the default)
+ * A request that does not apply to the grid falls back to one that does. */
+#define LB_KERNEL_AUTO (-1)
+#define LB_KERNEL_DIRECT1 0
+#define LB_KERNEL_DIRECT2 1
+#define LB_KERNEL_DIRECT2R 2
+#define LB_KERNEL_STAGED 3
+
+/* Kernel lb_step will run for this context (LB_KERNEL_DIRECT1 .. LB_KERNEL_STAGED). */
 int lb_step_variant(const lb_ctx *ctx);
+/* Request a step kernel (LB_KERNEL_*). */
+lb_status lb_set_step_kernel(lb_ctx *ctx, int kernel);
+/* Autotuner: time every step kernel that applies to this grid for reps steps
+ * (the state is not advanced), keep the fastest, report it and its ms per step. */
+lb_status lb_tune(lb_ctx *ctx, int reps, int *kernel, double *ms_per_step);
 
 /* Number of time steps taken since the last lb_set_fields / lb_set_populations / lb_set_state. */
 int64_t lb_time(const lb_ctx *ctx);

@@ -201,7 +201,7 @@ lb_status lb_init(lb_ctx** out, lb_grid grid, int velocity_set, double theta0, d
     c->d.rows = 2 * grid.ny * grid.nz;
     c->prec = (int)precision;
     c->project = !(flags & LB_FLAG_PAPER_LITERAL);
-    c->variant = (flags & LB_FLAG_STAGED) ? kVariantStaged : kVariantDirect;
+    c->variant = (flags & LB_FLAG_STAGED) ? kKernelStaged : kKernelAuto;
     c->tau = tau;
     c->twobeta = isinf(tau) ? 0.0 : 2.0 / (2.0 * tau + 1.0);
     c->stream = (cudaStream_t)cuda_stream;
@@ -266,7 +266,55 @@ lb_status lb_sync(lb_ctx* c) {
 
 int lb_step_variant(const lb_ctx* c) {
     if (!c) return -1;
-    return c->variant == kVariantStaged ? tma_tile_width(c->prec, c->d) : 0;
+    return resolve_kernel(c->prec, c->d, c->variant);
+}
+
+lb_status lb_set_step_kernel(lb_ctx* c, int kernel) {
+    if (!c || kernel < LB_KERNEL_AUTO || kernel > LB_KERNEL_STAGED) return fail(c, LB_ERR_ARG, "lb_set_step_kernel: unknown kernel");
+    c->variant = kernel;
+    return LB_OK;
+}
+
+lb_status lb_tune(lb_ctx* c, int reps, int* kernel_out, double* ms_out) {
+    if (!c) return LB_ERR_ARG;
+    CK(c, cudaSetDevice(c->device));
+    if (reps < 1) reps = 3;
+    const LaunchConsts& lc = lattice().lc;
+    cudaEvent_t e0, e1;
+    CK(c, cudaEventCreate(&e0));
+    CK(c, cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_k = resolve_kernel(c->prec, c->d, kKernelAuto);
+    // trial steps read buf[cur] and write buf[1 - cur] without flipping: the state is unchanged
+    for (int k = LB_KERNEL_DIRECT1; k <= LB_KERNEL_STAGED; ++k) {
+        if (resolve_kernel(c->prec, c->d, k) != k) continue;
+        cudaError_t e = launch_step(c->prec, c->project, k, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc, c->twobeta,
+                                    c->d_err, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r)
+            e = launch_step(c->prec, c->project, k, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc, c->twobeta, c->d_err,
+                            c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return fail(c, LB_ERR_CUDA, std::string("lb_tune: ") + cudaGetErrorString(e));
+        }
+        ms /= reps;
+        if (ms < best) {
+            best = ms;
+            best_k = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->variant = best_k;
+    if (kernel_out) *kernel_out = best_k;
+    if (ms_out) *ms_out = best;
+    return LB_OK;
 }
 
 lb_status lb_set_fields(lb_ctx* c, const double* rho, const double* u, const double* theta, int on_device) {

@@ -97,6 +97,7 @@ __device__ __forceinline__ void static_for(F&& f) {
 struct CodecF64 {  // stores f_i
     using raw_t = double;
     using R = double;
+    using KS = double;  // type of the lattice constants
     static constexpr bool stores_f = true;
     static constexpr double kScale = 1.0;
     static __device__ __forceinline__ R value(raw_t r) { return r; }
@@ -108,8 +109,12 @@ struct CodecF64 {  // stores f_i
 struct CodecF32 {  // stores h_i = f_i / w_i - 1
     using raw_t = float;
     using R = float;
+    using KS = float;
     static constexpr bool stores_f = false;
     static constexpr double kScale = 1.0;
+    using pair_t = float2;
+    static __device__ __forceinline__ pair_t pack2(raw_t a, raw_t b) { return make_float2(a, b); }
+    static __device__ __forceinline__ float2 unpack2(pair_t p) { return p; }
     static __device__ __forceinline__ R value(raw_t r) { return r; }
     static __device__ __forceinline__ R dev(R v, R w) { return w * v; }
     static __device__ __forceinline__ R relax(R v, R omb, R x, R, R) { return fmaf(omb, v, x); }
@@ -123,23 +128,71 @@ struct CodecF32 {  // stores h_i = f_i / w_i - 1
 struct CodecF16 {
     using raw_t = __half;
     using R = float;
+    using KS = float;
     static constexpr bool stores_f = false;
     static constexpr double kScale = 256.0;
     static __device__ __forceinline__ R value(raw_t r) { return __half2float(r); }
     static __device__ __forceinline__ R dev(R v, R w) { return w * v; }
     static __device__ __forceinline__ R relax(R v, R omb, R x, R, R) { return fmaf(omb, v, x); }
     static __device__ __forceinline__ raw_t to_raw(R v) { return __float2half_rn(v); }
+    // two stored elements kept packed in one register
+    using pair_t = __half2;
+    static __device__ __forceinline__ pair_t pack2(raw_t a, raw_t b) { return __halves2half2(a, b); }
+    static __device__ __forceinline__ float2 unpack2(pair_t p) { return __half22float2(p); }
 };
 
 struct CodecBF16 {
     using raw_t = __nv_bfloat16;
     using R = float;
+    using KS = float;
     static constexpr bool stores_f = false;
     static constexpr double kScale = 1.0;
     static __device__ __forceinline__ R value(raw_t r) { return __bfloat162float(r); }
     static __device__ __forceinline__ R dev(R v, R w) { return w * v; }
     static __device__ __forceinline__ R relax(R v, R omb, R x, R, R) { return fmaf(omb, v, x); }
     static __device__ __forceinline__ raw_t to_raw(R v) { return __float2bfloat16_rn(v); }
+    using pair_t = __nv_bfloat162;
+    static __device__ __forceinline__ pair_t pack2(raw_t a, raw_t b) { return __halves2bfloat162(a, b); }
+    static __device__ __forceinline__ float2 unpack2(pair_t p) { return __bfloat1622float2(p); }
+};
+
+// ---------------------------------------------------------------------------
+// Two nodes per thread: F2 carries one float per node and maps every
+// arithmetic operation onto Blackwell's packed FP32x2 instructions
+// (__fadd2_rn, __fmul2_rn, __ffma2_rn; each lane rounds exactly as the scalar
+// FP32 operation does), halving the FP32 instruction count of the collision.
+// ---------------------------------------------------------------------------
+struct F2 {
+    float2 v;
+    __device__ __forceinline__ F2() {}
+    __device__ __forceinline__ F2(float s) : v(make_float2(s, s)) {}
+    __device__ __forceinline__ F2(double s) : v(make_float2((float)s, (float)s)) {}
+    __device__ __forceinline__ F2(int s) : v(make_float2((float)s, (float)s)) {}
+    __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
+    __device__ __forceinline__ F2(float2 x) : v(x) {}
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2(__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)); }
+__device__ __forceinline__ F2 operator-(F2 a) { return F2(__fmul2_rn(a.v, make_float2(-1.f, -1.f))); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator/(F2 a, F2 b) { return F2(a.v.x / b.v.x, a.v.y / b.v.y); }
+__device__ __forceinline__ F2& operator+=(F2& a, F2 b) {
+    a = a + b;
+    return a;
+}
+using ::fma;  // keep the scalar overloads visible next to the F2 one
+__device__ __forceinline__ F2 fma(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
+
+// Two-node codec over a one-node storage codec: same storage, F2 arithmetic.
+template <class Base>
+struct Codec2 {
+    using raw_t = typename Base::raw_t;
+    using R = F2;
+    using KS = float;
+    static constexpr bool stores_f = Base::stores_f;
+    static constexpr double kScale = Base::kScale;
+    static __device__ __forceinline__ F2 dev(F2 v, F2 w) { return w * v; }
+    static __device__ __forceinline__ F2 relax(F2 v, F2 omb, F2 x, F2, F2) { return fma(omb, v, x); }
 };
 
 // Moments of one node from the deviations d_i = f_i - w_i (Sec. II):
@@ -187,8 +240,8 @@ struct NodeState {
     R drho, rho, ux, uy, uz, eta;
 };
 
-template <class R>
-__device__ __forceinline__ NodeState<R> state_from_moments(const NodeMoments<R>& m, const Consts<R>& K) {
+template <class R, class KS>
+__device__ __forceinline__ NodeState<R> state_from_moments(const NodeMoments<R>& m, const Consts<KS>& K) {
     NodeState<R> st;
     st.drho = m.drho;
     st.rho = R(1) + m.drho;
@@ -210,13 +263,19 @@ __device__ __forceinline__ bool state_ok(const NodeState<R>& st) {
            fabs(st.uz) < R(1e30);
 }
 
+__device__ __forceinline__ bool state_ok(const NodeState<F2>& st) {
+    NodeState<float> a{st.drho.v.x, st.rho.v.x, st.ux.v.x, st.uy.v.x, st.uz.v.x, st.eta.v.x};
+    NodeState<float> b{st.drho.v.y, st.rho.v.y, st.ux.v.y, st.uy.v.y, st.uz.v.y, st.eta.v.y};
+    return state_ok(a) && state_ok(b);
+}
+
 // Equilibrium (Eq. feqGenU3, with the optional momentum projection) and BGK
 // relaxation of one node.  v[i] are the working values of the node's incoming
 // populations (f or h, see the codec), tb = 2 beta, omb = 1 - 2 beta.
 // sink(I, value) receives the new working value of population I.
 template <class Codec, bool PROJECT, class VGet, class Sink>
 __device__ __forceinline__ void equilibrium_relax_g(const NodeState<typename Codec::R>& st,
-                                                    const Consts<typename Codec::R>& K, typename Codec::R tb,
+                                                    const Consts<typename Codec::KS>& K, typename Codec::R tb,
                                                     typename Codec::R omb, VGet&& vget, Sink&& sink) {
     using R = typename Codec::R;
     const R rho = st.rho, eta = st.eta;
@@ -311,7 +370,7 @@ __device__ __forceinline__ void equilibrium_relax_g(const NodeState<typename Cod
 
 template <class Codec, bool PROJECT, class Sink>
 __device__ __forceinline__ void equilibrium_relax(const NodeState<typename Codec::R>& st,
-                                                  const Consts<typename Codec::R>& K, typename Codec::R tb,
+                                                  const Consts<typename Codec::KS>& K, typename Codec::R tb,
                                                   typename Codec::R omb, const typename Codec::R (&v)[kQ], Sink&& sink) {
     equilibrium_relax_g<Codec, PROJECT>(st, K, tb, omb, [&](auto I) { return v[I]; }, sink);
 }

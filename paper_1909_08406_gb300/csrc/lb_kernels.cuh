@@ -99,6 +99,88 @@ __global__ void __launch_bounds__(kStepThreads) k_step(const typename Codec::raw
     step_node<Codec, PROJECT>(src, dst, d, K, tb, err, s, z, y, x);
 }
 
+// Two-rows-per-thread direct-load step kernel (FP32 arithmetic, any storage
+// except FP64): each thread updates nodes (s, z, y, x) and (s, z, y + 1, x)
+// with packed FP32x2 arithmetic.  Addresses are formed from 32-bit in-plane
+// offsets (the host guarantees nx * ny * nz < 2^32) plus plane * I.  Blocks
+// are numbered chunk-fastest, so the CTAs covering one row segment run
+// together and the sectors they share at chunk and wrap boundaries stay in
+// L2.  Requires ny even.  Grid: (nz * ny / 2 * 2 sub-lattices) * chunks blocks.
+template <class Codec, bool PROJECT, int MINB>
+__global__ void __launch_bounds__(kStepThreads, MINB) k_step2(const typename Codec::raw_t* __restrict__ src,
+                                                        typename Codec::raw_t* __restrict__ dst, Dims d,
+                                                        Consts<float> K, float tb, int* __restrict__ err,
+                                                        int chunks) {
+    using T = typename Codec::raw_t;
+    using C2 = Codec2<Codec>;
+    const int64_t t = blockIdx.x;
+    const int64_t rp = t / chunks;
+    const int x = (int)(t - rp * chunks) * blockDim.x + threadIdx.x;
+    if (x >= d.nx) return;
+    const int nyh = d.ny >> 1;
+    const int y = 2 * (int)(rp % nyh);
+    const int64_t zr = rp / nyh;
+    const int z = (int)(zr % d.nz);
+    const int s = (int)(zr / d.nz);
+    const uint32_t nx = (uint32_t)d.nx, nxy = (uint32_t)d.nx * (uint32_t)d.ny;
+    const uint32_t plane = (uint32_t)d.plane;
+
+    // source coordinates: x - delta for delta = k - 2; rows y + k - 2 for k = 0..5 (covers
+    // y - delta for the first node and y + 1 - delta for the second); planes z - delta
+    uint32_t xs[5], yo[6], zo[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        xs[k] = (uint32_t)wrap(x - (k - 2), d.nx);
+        zo[k] = (uint32_t)wrap(z - (k - 2), d.nz) * nxy;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) yo[k] = (uint32_t)wrap(y + k - 2, d.ny) * nx;
+    // half links: delta = 1 - s for a +1/2 component, -s for -1/2; the row index is 2 - delta
+    const uint32_t hxp = s ? xs[2] : xs[3], hxm = s ? xs[1] : xs[2];
+    const uint32_t hzp = s ? zo[2] : zo[3], hzm = s ? zo[1] : zo[2];
+    const int kyp = 1 + s, kym = 2 + s;  // 2 - delta for +1/2 and -1/2
+
+    const T* same = src + (size_t)s * kQ * d.plane;
+    const T* other = src + (size_t)(1 - s) * kQ * d.plane;
+
+    // the two nodes' stored values stay packed (one register per population for 16-bit
+    // storage) and are widened to FP32 where they are used
+    typename Codec::pair_t pv[kQ];
+    static_for<kQ>([&](auto I) {
+        constexpr Vel c = vel(I);
+        uint32_t oa, ob;
+        const T* base;
+        if constexpr (c.shell == 5) {
+            const uint32_t xz = (c.z > 0 ? hzp : hzm) + (c.x > 0 ? hxp : hxm);
+            const int ky = c.y > 0 ? kyp : kym;
+            oa = xz + yo[ky];
+            ob = xz + yo[ky + 1];
+            base = other;
+        } else {
+            const uint32_t xz = zo[c.z / 2 + 2] + xs[c.x / 2 + 2];
+            oa = xz + yo[2 - c.y / 2];
+            ob = xz + yo[3 - c.y / 2];
+            base = same;
+        }
+        const T* p = base + (size_t)I * plane;
+        pv[I] = Codec::pack2(LoadNC::load(p + oa), LoadNC::load(p + ob));
+    });
+    auto vget = [&](auto I) { return F2(Codec::unpack2(pv[I])); };
+
+    constexpr float inv_scale = (float)(1.0 / Codec::kScale);
+    const NodeMoments<F2> m = moments_from<F2>([&](auto I) { return C2::dev(vget(I), F2(K.w[vel(I).shell] * inv_scale)); });
+    const NodeState<F2> st = state_from_moments(m, K);
+    if (!state_ok(st)) atomicOr(err, 1);
+
+    T* outa = dst + (size_t)s * kQ * d.plane + ((uint32_t)z * nxy + (uint32_t)y * nx + (uint32_t)x);
+    equilibrium_relax_g<C2, PROJECT>(st, K, F2(tb * (float)Codec::kScale), F2(1.f - tb), vget,
+                                     [&](auto I, F2 val) {
+                                         T* p = outa + (size_t)I * plane;
+                                         p[0] = Codec::to_raw(val.v.x);
+                                         p[nx] = Codec::to_raw(val.v.y);
+                                     });
+}
+
 // Populations = equilibrium of the given float64 fields, for nodes
 // q in [q0, q0 + count), q = s * plane + (z * ny + y) * nx + x.  Field
 // pointers are indexed by q - q0 (u component c at c * ustride + q - q0).

@@ -22,8 +22,11 @@ struct LaunchConsts {
 // Storage precision codes (match lb_precision in gblb.h).
 enum Prec { kF64 = 0, kF32 = 1, kF16 = 2, kBF16 = 3 };
 
-// Step kernel variants: direct global loads, or shared-memory staging by TMA bulk copies.
-enum Variant { kVariantDirect = 0, kVariantStaged = 1 };
+// Step kernels (values match LB_KERNEL_* in gblb.h).
+enum StepKernel { kKernelAuto = -1, kKernelDirect1 = 0, kKernelDirect2 = 1, kKernelDirect2R = 2, kKernelStaged = 3 };
+
+// The kernel a request resolves to for this precision and grid (falls back where one does not apply).
+int resolve_kernel(int prec, const Dims& d, int kernel);
 
 // Tile width of the staged kernel for this grid and precision, 0 if it does not apply.
 int tma_tile_width(int prec, const Dims& d);

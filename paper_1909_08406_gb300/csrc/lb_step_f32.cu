@@ -1,19 +1,35 @@
-// FP32-arithmetic step kernels (FP32, FP16 and BF16 storage): the direct-load
-// kernel and the shared-memory-staged (TMA bulk copy) kernel.  This unit is
-// compiled with ptxas double-precision-use warnings so that no FP64
-// instruction slips into the float path.
+// FP32-arithmetic step kernels (FP32, FP16 and BF16 storage).  Variants:
+//   kKernelDirect1   k_step:        one node per thread, direct global loads
+//   kKernelDirect2   k_step2<.,.,3>: two rows per thread, packed FP32x2 math
+//   kKernelDirect2R  k_step2<.,.,4>: the same, register budget for 4 CTAs/SM
+//   kKernelStaged    k_step_tma:    rows fetched by TMA bulk copies into a
+//                                   shared-memory ring
+// This unit is compiled with ptxas double-precision-use warnings so that no
+// FP64 instruction slips into the float path.
 #include "lb_kernels.cuh"
 #include "lb_step_tma.cuh"
 
 namespace gblb {
 
 template <class Codec, bool P>
-static cudaError_t run(const void* src, void* dst, const Dims& d, const LaunchConsts& c, double twobeta, int* err,
-                       cudaStream_t st) {
+static cudaError_t run_direct1(const void* src, void* dst, const Dims& d, const LaunchConsts& c, double twobeta,
+                               int* err, cudaStream_t st) {
     using T = typename Codec::raw_t;
     const int th = step_threads(d);
     k_step<Codec, P><<<step_grid(d, th), th, 0, st>>>(static_cast<const T*>(src), static_cast<T*>(dst), d, c.kf,
                                                       (float)twobeta, err);
+    return cudaGetLastError();
+}
+
+template <class Codec, bool P, int MINB>
+static cudaError_t run_direct2(const void* src, void* dst, const Dims& d, const LaunchConsts& c, double twobeta,
+                               int* err, cudaStream_t st) {
+    using T = typename Codec::raw_t;
+    const int th = step_threads(d);
+    const int chunks = (d.nx + th - 1) / th;
+    const int64_t blocks = d.rows / 2 * chunks;
+    k_step2<Codec, P, MINB><<<(unsigned)blocks, th, 0, st>>>(static_cast<const T*>(src), static_cast<T*>(dst), d,
+                                                             c.kf, (float)twobeta, err, chunks);
     return cudaGetLastError();
 }
 
@@ -52,11 +68,11 @@ static cudaError_t run_tma(const void* src, void* dst, const Dims& d, const Laun
     return cudaGetLastError();
 }
 
-// Staged-kernel shapes per storage type: (tile width, threads, ring depth).
-template <class Codec, int TX>
-struct TmaShape;
+// Staged-kernel shapes per storage type: (tile width, threads, ring depth, CTAs/SM).
 // FP32, TX 256: 86.6 KB ring -> 2 CTAs/SM; TX 128: 66.9 KB -> 3 CTAs/SM.
 // 16-bit, TX 256: 66.9 KB -> 3 CTAs/SM; TX 128: 47.3 KB -> 4 CTAs/SM.
+template <class Codec, int TX>
+struct TmaShape;
 template <int TX>
 struct TmaShape<CodecF32, TX> {
     using Cfg = TmaCfg<CodecF32, TX, (TX < 256 ? TX : 256), (TX >= 256 ? 2 : 3), (TX >= 256 ? 2 : 3)>;
@@ -79,31 +95,44 @@ int tma_tile_width(int prec, const Dims& d) {
     return 0;
 }
 
+int resolve_kernel(int prec, const Dims& d, int kernel) {
+    if (prec == kF64) return kKernelDirect1;
+    const bool two_rows = d.ny % 2 == 0 && d.plane < ((int64_t)1 << 32);
+    switch (kernel) {
+        case kKernelStaged: return tma_tile_width(prec, d) ? kKernelStaged : resolve_kernel(prec, d, kKernelAuto);
+        case kKernelDirect2:
+        case kKernelDirect2R: return two_rows ? kernel : kKernelDirect1;
+        case kKernelDirect1: return kKernelDirect1;
+        default: return two_rows ? kKernelDirect2 : kKernelDirect1;
+    }
+}
+
 template <class Codec, bool P>
-static cudaError_t dispatch_tma(int tx, const void* src, void* dst, const Dims& d, const LaunchConsts& c,
-                                double twobeta, int* err, cudaStream_t st) {
-    if (tx == 256) return run_tma<Codec, P, typename TmaShape<Codec, 256>::Cfg>(src, dst, d, c, twobeta, err, st);
-    if (tx == 128) return run_tma<Codec, P, typename TmaShape<Codec, 128>::Cfg>(src, dst, d, c, twobeta, err, st);
-    return run<Codec, P>(src, dst, d, c, twobeta, err, st);
+static cudaError_t step_codec(int prec, int kernel, const void* src, void* dst, const Dims& d, const LaunchConsts& c,
+                              double twobeta, int* err, cudaStream_t st) {
+    switch (resolve_kernel(prec, d, kernel)) {
+        case kKernelStaged:
+            if (tma_tile_width(prec, d) == 256)
+                return run_tma<Codec, P, typename TmaShape<Codec, 256>::Cfg>(src, dst, d, c, twobeta, err, st);
+            return run_tma<Codec, P, typename TmaShape<Codec, 128>::Cfg>(src, dst, d, c, twobeta, err, st);
+        case kKernelDirect2: return run_direct2<Codec, P, 3>(src, dst, d, c, twobeta, err, st);
+        case kKernelDirect2R: return run_direct2<Codec, P, 4>(src, dst, d, c, twobeta, err, st);
+        default: return run_direct1<Codec, P>(src, dst, d, c, twobeta, err, st);
+    }
 }
 
-template <class Codec>
-static cudaError_t step_codec(int prec, bool project, int variant, const void* src, void* dst, const Dims& d,
-                              const LaunchConsts& c, double twobeta, int* err, cudaStream_t st) {
-    const int tx = variant == kVariantStaged ? tma_tile_width(prec, d) : 0;
-    if (tx)
-        return project ? dispatch_tma<Codec, true>(tx, src, dst, d, c, twobeta, err, st)
-                       : dispatch_tma<Codec, false>(tx, src, dst, d, c, twobeta, err, st);
-    return project ? run<Codec, true>(src, dst, d, c, twobeta, err, st)
-                   : run<Codec, false>(src, dst, d, c, twobeta, err, st);
-}
-
-cudaError_t launch_step_f32(int prec, bool project, int variant, const void* src, void* dst, const Dims& d,
+cudaError_t launch_step_f32(int prec, bool project, int kernel, const void* src, void* dst, const Dims& d,
                             const LaunchConsts& c, double twobeta, int* err, cudaStream_t st) {
     switch (prec) {
-        case kF32: return step_codec<CodecF32>(prec, project, variant, src, dst, d, c, twobeta, err, st);
-        case kF16: return step_codec<CodecF16>(prec, project, variant, src, dst, d, c, twobeta, err, st);
-        case kBF16: return step_codec<CodecBF16>(prec, project, variant, src, dst, d, c, twobeta, err, st);
+        case kF32:
+            return project ? step_codec<CodecF32, true>(prec, kernel, src, dst, d, c, twobeta, err, st)
+                           : step_codec<CodecF32, false>(prec, kernel, src, dst, d, c, twobeta, err, st);
+        case kF16:
+            return project ? step_codec<CodecF16, true>(prec, kernel, src, dst, d, c, twobeta, err, st)
+                           : step_codec<CodecF16, false>(prec, kernel, src, dst, d, c, twobeta, err, st);
+        case kBF16:
+            return project ? step_codec<CodecBF16, true>(prec, kernel, src, dst, d, c, twobeta, err, st)
+                           : step_codec<CodecBF16, false>(prec, kernel, src, dst, d, c, twobeta, err, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -1,0 +1,601 @@
+// Surrogate kernels: periodic 3x3x3 convolution as an implicit GEMM on the
+// BF16 tensor cores (mma.sync m16n8k16, FP32 accumulate), its weight
+// gradient, and the small element-wise / reduction kernels of training and
+// rollout.  C ABI in include/gblb_surrogate.h.
+//
+// Forward tile: one CTA owns RT = 4 consecutive rows (64 voxels each) of one
+// z-plane of one batch item: M = 256 voxels, N = cout, K = 27 * cin.  The
+// CTA stages the periodic halo (3 planes x 6 rows x 66 voxels x cin) and all
+// weights in shared memory with 16-byte row padding (conflict-free ldmatrix);
+// each of the 16 warps computes 16 voxels x cout.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "gblb_surrogate.h"
+
+namespace sg {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kW = 64;             // voxels per row (nx)
+constexpr int kRT = 4;             // rows per forward tile
+constexpr int kHR = kRT + 2;       // halo rows
+constexpr int kHX = kW + 2;        // halo voxels per row
+constexpr int kFwdWarps = kRT * 4;  // 16 voxels per warp
+constexpr int kFwdThreads = kFwdWarps * 32;
+
+template <int CIN>
+struct HaloCfg {
+    static constexpr int STRIDE = CIN * 2 + 16;  // bytes per halo voxel
+    static constexpr int BYTES = 3 * kHR * kHX * STRIDE;
+};
+template <int CIN, int COUT>
+struct WCfg {
+    static constexpr int STRIDE = 27 * CIN * 2 + 16;  // bytes per output channel row
+    static constexpr int BYTES = COUT * STRIDE;
+};
+
+struct Epi {
+    int act;
+    int res_in;
+    const void* add;
+    int add_f32;
+    float* z_out;
+    int y_f32;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], uint32_t addr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(addr));
+}
+// D = A * B + D, A 16x16 (row-major) BF16, B 16x8 (column-major) BF16, D 16x8 FP32
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+// GELU with the Gaussian CDF, g(z) = z Phi(z), and its derivative Phi(z) + z phi(z).
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+    return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kFwdThreads, 1) k_conv_fwd(sg_shape s, const bf16* __restrict__ x,
+                                                              const bf16* __restrict__ w,
+                                                              const float* __restrict__ bias, Epi epi, void* y) {
+    using H = HaloCfg<CIN>;
+    using WC = WCfg<CIN, COUT>;
+    extern __shared__ __align__(16) unsigned char sm[];
+    unsigned char* halo = sm;
+    unsigned char* wsm = sm + H::BYTES;
+    const int tid = threadIdx.x;
+    int64_t t = blockIdx.x;
+    const int tiles_y = s.ny / kRT;
+    const int yt = (int)(t % tiles_y);
+    t /= tiles_y;
+    const int z = (int)(t % s.nz);
+    const int b = (int)(t / s.nz);
+    const int y0 = yt * kRT;
+
+    constexpr int CH = CIN / 8;  // 16-byte chunks per voxel
+    for (int i = tid; i < 3 * kHR * kHX * CH; i += kFwdThreads) {
+        const int c = i % CH;
+        const int v = i / CH;
+        const int xh = v % kHX, r = v / kHX;
+        const int yh = r % kHR, zh = r / kHR;
+        const int zz = wrapi(z + zh - 1, s.nz), yy = wrapi(y0 + yh - 1, s.ny), xx = wrapi(xh - 1, kW);
+        const int64_t g = ((((int64_t)b * s.nz + zz) * s.ny + yy) * kW + xx) * CIN + c * 8;
+        *reinterpret_cast<uint4*>(halo + (size_t)v * H::STRIDE + c * 16) = *reinterpret_cast<const uint4*>(x + g);
+    }
+    constexpr int WCH = 27 * CIN / 8;
+    for (int i = tid; i < COUT * WCH; i += kFwdThreads) {
+        const int co = i / WCH, c = i % WCH;
+        *reinterpret_cast<uint4*>(wsm + co * WC::STRIDE + c * 16) =
+            *reinterpret_cast<const uint4*>(w + (size_t)co * 27 * CIN + c * 8);
+    }
+    __syncthreads();
+
+    const int warp = tid >> 5, lane = tid & 31;
+    const int yl = warp >> 2, x0 = (warp & 3) * 16;
+    float acc[COUT / 8][4];
+#pragma unroll
+    for (int i = 0; i < COUT / 8; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+    const uint32_t hs = smem_u32(halo), ws = smem_u32(wsm);
+    const int ar = lane & 15, akc = lane >> 4;
+    const int bn = (lane & 7) + 8 * (lane >> 4), bkc = (lane >> 3) & 1;
+    for (int tap = 0; tap < 27; ++tap) {
+        const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+        const int hrow = ((dz + 1) * kHR + (yl + 1 + dy)) * kHX + (x0 + ar + 1 + dx);
+        const uint32_t a0 = hs + hrow * H::STRIDE + akc * 16;
+#pragma unroll
+        for (int kb = 0; kb < CIN / 16; ++kb) {
+            uint32_t a[4];
+            ldsm_x4(a, a0 + kb * 32);
+#pragma unroll
+            for (int np = 0; np < COUT / 16; ++np) {
+                uint32_t bb[4];
+                ldsm_x4(bb, ws + (np * 16 + bn) * WC::STRIDE + (tap * CIN + kb * 16 + bkc * 8) * 2);
+                mma_bf16(acc[2 * np], a, bb[0], bb[1]);
+                mma_bf16(acc[2 * np + 1], a, bb[2], bb[3]);
+            }
+        }
+    }
+
+    // epilogue: lane holds (voxel g, channels 2t, 2t+1) and (voxel g + 8, same channels) per n-tile
+    const int g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+    for (int nt = 0; nt < COUT / 8; ++nt) {
+        const int co = nt * 8 + 2 * t4;
+        const float b0 = bias ? bias[co] : 0.f, b1 = bias ? bias[co + 1] : 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int xx = x0 + g + 8 * h;
+            const int64_t v = (((int64_t)b * s.nz + z) * s.ny + (y0 + yl)) * kW + xx;
+            float z0 = acc[nt][2 * h] + b0, z1 = acc[nt][2 * h + 1] + b1;
+            if (epi.z_out) *reinterpret_cast<float2*>(epi.z_out + v * COUT + co) = make_float2(z0, z1);
+            float o0 = epi.act == SG_ACT_GELU ? gelu(z0) : z0;
+            float o1 = epi.act == SG_ACT_GELU ? gelu(z1) : z1;
+            if (epi.res_in && CIN == COUT) {
+                const int hc = (1 * kHR + (yl + 1)) * kHX + (xx + 1);
+                const __nv_bfloat162 r = *reinterpret_cast<const __nv_bfloat162*>(halo + hc * H::STRIDE + co * 2);
+                o0 += __bfloat162float(r.x);
+                o1 += __bfloat162float(r.y);
+            }
+            if (epi.add) {
+                if (epi.add_f32) {
+                    const float2 r = *reinterpret_cast<const float2*>(static_cast<const float*>(epi.add) + v * COUT + co);
+                    o0 += r.x;
+                    o1 += r.y;
+                } else {
+                    const __nv_bfloat162 r =
+                        *reinterpret_cast<const __nv_bfloat162*>(static_cast<const bf16*>(epi.add) + v * COUT + co);
+                    o0 += __bfloat162float(r.x);
+                    o1 += __bfloat162float(r.y);
+                }
+            }
+            if (epi.y_f32)
+                *reinterpret_cast<float2*>(static_cast<float*>(y) + v * COUT + co) = make_float2(o0, o1);
+            else
+                *reinterpret_cast<__nv_bfloat162*>(static_cast<bf16*>(y) + v * COUT + co) = __floats2bfloat162_rn(o0, o1);
+        }
+    }
+}
+
+// Weight gradient, split over (tap, voxel partition): CTA (tap, p) accumulates
+// dw[co][tap][ci] over its voxel range in 128-voxel chunks (two rows); warp w
+// takes voxels 16w..16w+15 of each chunk as the K dimension of
+// D[co][ci] += dz^T[co][v] x[v + d(tap)][ci].  The 8 warps' partial sums are
+// added in shared memory in a fixed order and written to partials[p][tap].
+constexpr int kWgThreads = 256;
+constexpr int kChunk = 128;
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(kWgThreads) k_conv_wgrad(sg_shape s, const bf16* __restrict__ x,
+                                                           const bf16* __restrict__ dz, float* __restrict__ partials,
+                                                           int parts) {
+    constexpr int ZS = COUT * 2 + 16, XS = CIN * 2 + 16;
+    constexpr int STAGE = kChunk * (ZS + XS), RED = 8 * COUT * CIN * 4;
+    // the staging tiles and, after the last chunk, the per-warp partial sums share one buffer
+    __shared__ __align__(16) unsigned char buf[STAGE > RED ? STAGE : RED];
+    unsigned char* zs = buf;
+    unsigned char* xs = buf + kChunk * ZS;
+    float (*red)[COUT * CIN] = reinterpret_cast<float (*)[COUT * CIN]>(buf);
+    const int tap = blockIdx.x, p = blockIdx.y;
+    const int ddz = tap / 9 - 1, ddy = (tap / 3) % 3 - 1, ddx = tap % 3 - 1;
+    const int64_t voxels = (int64_t)s.batch * s.nz * s.ny * kW;
+    const int64_t nchunks = voxels / kChunk;
+    const int64_t c0 = nchunks * p / parts, c1 = nchunks * (p + 1) / parts;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float acc[COUT / 16][CIN / 8][4];
+#pragma unroll
+    for (int i = 0; i < COUT / 16; ++i)
+#pragma unroll
+        for (int j = 0; j < CIN / 8; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.f;
+    const uint32_t zsa = smem_u32(zs), xsa = smem_u32(xs);
+    const int jm = lane >> 3, rr = lane & 7;
+    for (int64_t ch = c0; ch < c1; ++ch) {
+        const int64_t v0 = ch * kChunk;
+        for (int i = tid; i < kChunk * (COUT / 8); i += kWgThreads) {
+            const int v = i / (COUT / 8), c = i % (COUT / 8);
+            *reinterpret_cast<uint4*>(zs + v * ZS + c * 16) =
+                *reinterpret_cast<const uint4*>(dz + (v0 + v) * COUT + c * 8);
+        }
+        for (int i = tid; i < kChunk * (CIN / 8); i += kWgThreads) {
+            const int v = i / (CIN / 8), c = i % (CIN / 8);
+            int64_t q = v0 + v;
+            const int xx = (int)(q % kW);
+            q /= kW;
+            const int yy = (int)(q % s.ny);
+            q /= s.ny;
+            const int zz = (int)(q % s.nz);
+            const int bb = (int)(q / s.nz);
+            const int64_t src = ((((int64_t)bb * s.nz + wrapi(zz + ddz, s.nz)) * s.ny + wrapi(yy + ddy, s.ny)) * kW +
+                                 wrapi(xx + ddx, kW)) * CIN + c * 8;
+            *reinterpret_cast<uint4*>(xs + v * XS + c * 16) = *reinterpret_cast<const uint4*>(x + src);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int mt = 0; mt < COUT / 16; ++mt) {
+            // A = dz^T: matrix j = (co 8*(j&1).., voxels 8*(j>>1)..), rows stored by voxel -> transposed load
+            uint32_t a[4];
+            ldsm_x4_t(a, zsa + (16 * warp + rr + 8 * (jm >> 1)) * ZS + (16 * mt + 8 * (jm & 1)) * 2);
+#pragma unroll
+            for (int nt = 0; nt < CIN / 8; nt += 2) {
+                // B = x: matrix j = (voxels 8*(j&1).., ci 8*(nt + (j>>1))..), rows stored by voxel -> transposed load
+                uint32_t bb[4];
+                ldsm_x4_t(bb, xsa + (16 * warp + rr + 8 * (jm & 1)) * XS + (8 * (nt + (jm >> 1))) * 2);
+                mma_bf16(acc[mt][nt], a, bb[0], bb[1]);
+                mma_bf16(acc[mt][nt + 1], a, bb[2], bb[3]);
+            }
+        }
+        __syncthreads();
+    }
+    const int g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+    for (int mt = 0; mt < COUT / 16; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < CIN / 8; ++nt) {
+            const int co = 16 * mt + g, ci = 8 * nt + 2 * t4;
+            red[warp][co * CIN + ci] = acc[mt][nt][0];
+            red[warp][co * CIN + ci + 1] = acc[mt][nt][1];
+            red[warp][(co + 8) * CIN + ci] = acc[mt][nt][2];
+            red[warp][(co + 8) * CIN + ci + 1] = acc[mt][nt][3];
+        }
+    __syncthreads();
+    for (int e = tid; e < COUT * CIN; e += kWgThreads) {
+        float sum = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sum += red[k][e];
+        partials[((int64_t)p * 27 + tap) * COUT * CIN + e] = sum;
+    }
+}
+
+// dw[co][tap][ci] = sum_p partials[p][tap][co][ci]  (fixed order)
+__global__ void k_wgrad_reduce(int cin, int cout, int parts, const float* __restrict__ partials,
+                               float* __restrict__ dw) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = 27 * cin * cout;
+    if (e >= n) return;
+    const int ci = e % cin, tap = (e / cin) % 27, co = e / (27 * cin);
+    const int64_t off = (int64_t)tap * cout * cin + co * cin + ci;
+    float sum = 0.f;
+    for (int p = 0; p < parts; ++p) sum += partials[(int64_t)p * 27 * cout * cin + off];
+    dw[e] = sum;
+}
+
+// db[co] = sum_v dz[v][co]: one block per channel, fixed-order tree.
+__global__ void k_bias_grad(int64_t voxels, int cout, const bf16* __restrict__ dz, float* __restrict__ db) {
+    __shared__ float sh[256];
+    const int co = blockIdx.x;
+    float sum = 0.f;
+    for (int64_t v = threadIdx.x; v < voxels; v += 256) sum += __bfloat162float(dz[v * cout + co]);
+    sh[threadIdx.x] = sum;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) db[co] = sh[0];
+}
+
+__global__ void k_act_bwd(int64_t n, int act, const float* __restrict__ dy, const float* __restrict__ z,
+                          bf16* __restrict__ dz) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float g = act == SG_ACT_GELU ? dy[i] * gelu_grad(z[i]) : dy[i];
+    dz[i] = __float2bfloat16_rn(g);
+}
+
+__global__ void k_transpose_w(int cin, int cout, const bf16* __restrict__ w, bf16* __restrict__ wt) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 27 * cin * cout) return;
+    // wt[ci][tap][co] = w[co][26 - tap][ci]
+    const int co = e % cout, tap = (e / cout) % 27, ci = e / (27 * cout);
+    wt[e] = w[((int64_t)co * 27 + (26 - tap)) * cin + ci];
+}
+
+constexpr int kRedBlocks = 256;
+
+// Sum of squared differences / squares, block partials in fixed order.
+__global__ void k_mse(int64_t voxels, int c, int nch, const bf16* __restrict__ pred, const bf16* __restrict__ target,
+                      float* __restrict__ dpred, float* __restrict__ partial) {
+    __shared__ double sh[256];
+    double sum = 0.0;
+    const float scale = 2.f / (float)((double)voxels * nch);
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < voxels * c; i += (int64_t)gridDim.x * 256) {
+        const int ch = (int)(i % c);
+        float d = 0.f;
+        if (ch < nch) d = __bfloat162float(pred[i]) - __bfloat162float(target[i]);
+        dpred[i] = scale * d;
+        sum += (double)d * d;
+    }
+    sh[threadIdx.x] = sum;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = (float)sh[0];
+}
+
+__global__ void k_finish_mse(int nblocks, double denom, const float* __restrict__ partial, float* __restrict__ loss) {
+    if (threadIdx.x != 0) return;
+    double s = 0.0;
+    for (int i = 0; i < nblocks; ++i) s += partial[i];
+    *loss = (float)(s / denom);
+}
+
+// per batch item: sums of (a-b)^2 and b^2 over the first nch channels
+__global__ void k_rel_l2(int64_t per_item, int c, int nch, const bf16* __restrict__ a, const bf16* __restrict__ b,
+                         double* __restrict__ partial) {
+    __shared__ double sd[256], sb[256];
+    const int item = blockIdx.y;
+    double d2 = 0.0, b2 = 0.0;
+    const int64_t base = (int64_t)item * per_item * c;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < per_item * c; i += (int64_t)gridDim.x * 256) {
+        if ((int)(i % c) >= nch) continue;
+        const double av = __bfloat162float(a[base + i]), bv = __bfloat162float(b[base + i]);
+        d2 += (av - bv) * (av - bv);
+        b2 += bv * bv;
+    }
+    sd[threadIdx.x] = d2;
+    sb[threadIdx.x] = b2;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            sd[threadIdx.x] += sd[threadIdx.x + w];
+            sb[threadIdx.x] += sb[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[((int64_t)item * gridDim.x + blockIdx.x) * 2] = sd[0];
+        partial[((int64_t)item * gridDim.x + blockIdx.x) * 2 + 1] = sb[0];
+    }
+}
+
+__global__ void k_finish_rel_l2(int items, int nblocks, const double* __restrict__ partial, float* __restrict__ out) {
+    const int item = threadIdx.x;
+    if (item >= items) return;
+    double d = 0.0, b = 0.0;
+    for (int i = 0; i < nblocks; ++i) {
+        d += partial[((int64_t)item * nblocks + i) * 2];
+        b += partial[((int64_t)item * nblocks + i) * 2 + 1];
+    }
+    out[item] = (float)(b > 0 ? sqrt(d / b) : sqrt(d));
+}
+
+__global__ void k_adam(int64_t n, float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, bf16* __restrict__ p16, float lr, float b1, float b2, float eps,
+                       float c1, float c2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    p[i] = pi;
+    if (p16) p16[i] = __float2bfloat16_rn(pi);
+}
+
+// A-sub-lattice fields of one batch item -> 16 normalised channels.
+__global__ void k_pack(sg_shape s, int item, const double* __restrict__ rho, const double* __restrict__ u,
+                       const double* __restrict__ th, double theta0, float s0, float s1, float s2,
+                       bf16* __restrict__ x) {
+    const int64_t plane = (int64_t)s.nz * s.ny * s.nx;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= plane) return;
+    const int64_t ustride = 2 * plane;  // u[3][2][nz][ny][nx]
+    float ch[8] = {(float)((rho[q] - 1.0) / s0), (float)(u[q] / s1), (float)(u[ustride + q] / s1),
+                   (float)(u[2 * ustride + q] / s1), (float)((th[q] / theta0 - 1.0) / s2), 0.f, 0.f, 0.f};
+    bf16* out = x + ((int64_t)item * plane + q) * 16;
+    __nv_bfloat162 pk[8];
+    for (int k = 0; k < 4; ++k) pk[k] = __floats2bfloat162_rn(ch[2 * k], ch[2 * k + 1]);
+    for (int k = 4; k < 8; ++k) pk[k] = __floats2bfloat162_rn(0.f, 0.f);
+    uint4* o = reinterpret_cast<uint4*>(out);
+    o[0] = *reinterpret_cast<uint4*>(&pk[0]);
+    o[1] = *reinterpret_cast<uint4*>(&pk[4]);
+}
+
+// 16-channel prediction of one batch item -> float64 fields on both sub-lattices.
+__global__ void k_unpack(sg_shape s, int item, const bf16* __restrict__ x, double theta0, float s0, float s1, float s2,
+                         double* __restrict__ rho, double* __restrict__ u, double* __restrict__ th) {
+    const int64_t plane = (int64_t)s.nz * s.ny * s.nx;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= 2 * plane) return;
+    const int sub = q >= plane;
+    const int64_t cell = q - sub * plane;
+    const int xx = (int)(cell % s.nx), yy = (int)((cell / s.nx) % s.ny), zz = (int)(cell / ((int64_t)s.nx * s.ny));
+    const bf16* base = x + (int64_t)item * plane * 16;
+    float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    const int n = sub ? 8 : 1;
+    for (int k = 0; k < n; ++k) {
+        // B node of cell r sits at r + (1/2,1/2,1/2): its A neighbours are cells r + {0,1}^3
+        const int ax = sub ? wrapi(xx + (k & 1), s.nx) : xx;
+        const int ay = sub ? wrapi(yy + ((k >> 1) & 1), s.ny) : yy;
+        const int az = sub ? wrapi(zz + (k >> 2), s.nz) : zz;
+        const bf16* v = base + (((int64_t)az * s.ny + ay) * s.nx + ax) * 16;
+        for (int c = 0; c < 5; ++c) acc[c] += __bfloat162float(v[c]);
+    }
+    const float inv = 1.f / (float)n;
+    rho[q] = 1.0 + (double)(acc[0] * inv) * s0;
+    u[q] = (double)(acc[1] * inv) * s1;
+    u[2 * plane + q] = (double)(acc[2] * inv) * s1;
+    u[4 * plane + q] = (double)(acc[3] * inv) * s1;
+    th[q] = theta0 * (1.0 + (double)(acc[4] * inv) * s2);
+}
+
+template <int CIN, int COUT>
+static int launch_fwd(sg_shape s, const void* x, const void* w, const float* bias, Epi epi, void* y,
+                      cudaStream_t st) {
+    constexpr int smem = HaloCfg<CIN>::BYTES + WCfg<CIN, COUT>::BYTES;
+    static int configured = -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -3;
+    if (configured != dev) {
+        if (cudaFuncSetAttribute(k_conv_fwd<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+            cudaSuccess)
+            return -3;
+        configured = dev;
+    }
+    const int64_t tiles = (int64_t)s.batch * s.nz * (s.ny / kRT);
+    k_conv_fwd<CIN, COUT><<<(unsigned)tiles, kFwdThreads, smem, st>>>(
+        s, static_cast<const bf16*>(x), static_cast<const bf16*>(w), bias, epi, y);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+static int parts_for(sg_shape s) {
+    const int64_t chunks = (int64_t)s.batch * s.nz * s.ny * kW / kChunk;
+    int p = 32;
+    if (p > chunks) p = (int)chunks;
+    return p < 1 ? 1 : p;
+}
+
+template <int CIN, int COUT>
+static int launch_wgrad(sg_shape s, const void* x, const void* dz, float* dw, float* db, void* scratch,
+                        cudaStream_t st) {
+    const int parts = parts_for(s);
+    float* partials = static_cast<float*>(scratch);
+    k_conv_wgrad<CIN, COUT><<<dim3(27, parts), kWgThreads, 0, st>>>(s, static_cast<const bf16*>(x),
+                                                                     static_cast<const bf16*>(dz), partials, parts);
+    const int n = 27 * CIN * COUT;
+    k_wgrad_reduce<<<(n + 255) / 256, 256, 0, st>>>(CIN, COUT, parts, partials, dw);
+    const int64_t voxels = (int64_t)s.batch * s.nz * s.ny * s.nx;
+    if (db) k_bias_grad<<<COUT, 256, 0, st>>>(voxels, COUT, static_cast<const bf16*>(dz), db);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+static bool shape_ok(sg_shape s) {
+    return s.batch >= 1 && s.nz >= 1 && s.nx == kW && s.ny >= kRT && s.ny % kRT == 0;
+}
+
+}  // namespace sg
+
+using namespace sg;
+
+extern "C" {
+
+int sg_conv3d_fwd(sg_shape s, int cin, int cout, const void* x, const void* w, const float* bias, int act,
+                  int res_in, const void* add, float* z_out, void* y, void* stream) {
+    Epi e{act, res_in, add, 0, z_out, 0};
+    if (!x || !w || !y || !shape_ok(s) || (res_in && cin != cout)) return -1;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cin == 16 && cout == 32) return launch_fwd<16, 32>(s, x, w, bias, e, y, st);
+    if (cin == 32 && cout == 32) return launch_fwd<32, 32>(s, x, w, bias, e, y, st);
+    if (cin == 32 && cout == 16) return launch_fwd<32, 16>(s, x, w, bias, e, y, st);
+    if (cin == 16 && cout == 16) return launch_fwd<16, 16>(s, x, w, bias, e, y, st);
+    return -1;
+}
+
+// Input-gradient form: y (FP32) = conv(x, w) + add (FP32, may be NULL).
+int sg_conv3d_fwd_f32(sg_shape s, int cin, int cout, const void* x, const void* w, const float* add, float* y,
+                      void* stream) {
+    Epi e{SG_ACT_NONE, 0, add, 1, nullptr, 1};
+    if (!x || !w || !y || !shape_ok(s)) return -1;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cin == 16 && cout == 32) return launch_fwd<16, 32>(s, x, w, nullptr, e, y, st);
+    if (cin == 32 && cout == 32) return launch_fwd<32, 32>(s, x, w, nullptr, e, y, st);
+    if (cin == 32 && cout == 16) return launch_fwd<32, 16>(s, x, w, nullptr, e, y, st);
+    if (cin == 16 && cout == 16) return launch_fwd<16, 16>(s, x, w, nullptr, e, y, st);
+    return -1;
+}
+
+int sg_act_backward(int64_t n, int act, const float* dy, const float* z, void* dz, void* stream) {
+    if (n < 0 || !dy || !dz || (act == SG_ACT_GELU && !z)) return -1;
+    if (n == 0) return 0;
+    k_act_bwd<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, act, dy, z, static_cast<bf16*>(dz));
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int sg_transpose_weights(int cin, int cout, const void* w, void* wt, void* stream) {
+    if (!w || !wt || cin < 1 || cout < 1) return -1;
+    const int n = 27 * cin * cout;
+    k_transpose_w<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(cin, cout, static_cast<const bf16*>(w),
+                                                                     static_cast<bf16*>(wt));
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int64_t sg_wgrad_scratch_bytes(sg_shape s, int cin, int cout) {
+    return (int64_t)parts_for(s) * 27 * cin * cout * (int64_t)sizeof(float);
+}
+
+int sg_conv3d_wgrad(sg_shape s, int cin, int cout, const void* x, const void* dz, float* dw, float* db, void* scratch,
+                    void* stream) {
+    if (!x || !dz || !dw || !scratch || !shape_ok(s)) return -1;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cin == 16 && cout == 32) return launch_wgrad<16, 32>(s, x, dz, dw, db, scratch, st);
+    if (cin == 32 && cout == 32) return launch_wgrad<32, 32>(s, x, dz, dw, db, scratch, st);
+    if (cin == 32 && cout == 16) return launch_wgrad<32, 16>(s, x, dz, dw, db, scratch, st);
+    if (cin == 16 && cout == 16) return launch_wgrad<16, 16>(s, x, dz, dw, db, scratch, st);
+    return -1;
+}
+
+int64_t sg_reduce_scratch_bytes(int64_t n) { return (int64_t)kRedBlocks * 64 * 2 * (int64_t)sizeof(double) + 64; }
+
+int sg_mse(int64_t voxels, int c, int nch, const void* pred, const void* target, float* loss, float* dpred,
+           void* scratch, void* stream) {
+    if (!pred || !target || !loss || !dpred || !scratch || nch > c || voxels < 1) return -1;
+    cudaStream_t st = (cudaStream_t)stream;
+    float* partial = static_cast<float*>(scratch);
+    k_mse<<<kRedBlocks, 256, 0, st>>>(voxels, c, nch, static_cast<const bf16*>(pred), static_cast<const bf16*>(target),
+                                      dpred, partial);
+    k_finish_mse<<<1, 32, 0, st>>>(kRedBlocks, (double)voxels * nch, partial, loss);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int sg_rel_l2(sg_shape s, int c, int nch, const void* a, const void* b, float* out, void* scratch, void* stream) {
+    if (!a || !b || !out || !scratch || s.batch < 1 || s.batch > 64 || nch > c) return -1;
+    const int64_t per_item = (int64_t)s.nz * s.ny * s.nx;
+    k_rel_l2<<<dim3(kRedBlocks, s.batch), 256, 0, (cudaStream_t)stream>>>(
+        per_item, c, nch, static_cast<const bf16*>(a), static_cast<const bf16*>(b), static_cast<double*>(scratch));
+    k_finish_rel_l2<<<1, 64, 0, (cudaStream_t)stream>>>(s.batch, kRedBlocks, static_cast<const double*>(scratch), out);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int sg_adam(int64_t n, float* p, const float* g, float* m, float* v, void* p16, float lr, float beta1, float beta2,
+            float eps, int t, void* stream) {
+    if (!p || !g || !m || !v || t < 1 || n < 0) return -1;
+    if (n == 0) return 0;
+    const float c1 = 1.f - powf(beta1, (float)t), c2 = 1.f - powf(beta2, (float)t);
+    k_adam<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, p, g, m, v, static_cast<bf16*>(p16), lr,
+                                                                           beta1, beta2, eps, c1, c2);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int sg_pack_fields(sg_shape s, int item, const double* rho, const double* u, const double* theta, double theta0,
+                   const float* scales, void* x, void* stream) {
+    if (!rho || !u || !theta || !scales || !x || item < 0 || item >= s.batch) return -1;
+    const int64_t plane = (int64_t)s.nz * s.ny * s.nx;
+    k_pack<<<(unsigned)((plane + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        s, item, rho, u, theta, theta0, scales[0], scales[1], scales[2], static_cast<bf16*>(x));
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int sg_unpack_fields(sg_shape s, int item, const void* x, double theta0, const float* scales, double* rho, double* u,
+                     double* theta, void* stream) {
+    if (!rho || !u || !theta || !scales || !x || item < 0 || item >= s.batch) return -1;
+    const int64_t n = 2 * (int64_t)s.nz * s.ny * s.nx;
+    k_unpack<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        s, item, static_cast<const bf16*>(x), theta0, scales[0], scales[1], scales[2], rho, u, theta);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+}  // extern "C"

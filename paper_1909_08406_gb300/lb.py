@@ -25,6 +25,9 @@ STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 LB_RD3Q41 = 41
 LB_FLAG_PAPER_LITERAL = 1
 LB_FLAG_STAGED = 2
+LB_KERNEL_AUTO, LB_KERNEL_DIRECT1, LB_KERNEL_DIRECT2, LB_KERNEL_DIRECT2R, LB_KERNEL_STAGED = -1, 0, 1, 2, 3
+KERNEL_NAMES = {0: "k_step (direct, 1 node/thread)", 1: "k_step2 (direct, 2 rows/thread, FP32x2)",
+                2: "k_step2 (direct, 2 rows/thread, FP32x2, 4 CTAs/SM)", 3: "k_step_tma (TMA-staged)"}
 
 
 class LbError(RuntimeError):
@@ -65,6 +68,10 @@ def lib():
         L.lb_set_state.argtypes = [vp, vp, ctypes.c_int]
         L.lb_step_variant.argtypes = [vp]
         L.lb_step_variant.restype = ctypes.c_int
+        L.lb_set_step_kernel.argtypes = [vp, ctypes.c_int]
+        L.lb_set_step_kernel.restype = ctypes.c_int
+        L.lb_tune.argtypes = [vp, ctypes.c_int, vp, vp]
+        L.lb_tune.restype = ctypes.c_int
         L.lb_time.argtypes = [vp]
         L.lb_time.restype = i64
         L.lb_sync.argtypes = [vp]
@@ -199,6 +206,17 @@ def lb_set_state(ctx, raw):
 
 def lb_step_variant(ctx):
     return int(lib().lb_step_variant(ctx))
+
+
+def lb_set_step_kernel(ctx, kernel):
+    _check(lib().lb_set_step_kernel(ctx, int(kernel)), ctx)
+
+
+def lb_tune(ctx, reps=3):
+    """Autotune the step kernel; returns (kernel, ms_per_step)."""
+    k, ms = ctypes.c_int(), ctypes.c_double()
+    _check(lib().lb_tune(ctx, int(reps), ctypes.byref(k), ctypes.byref(ms)), ctx)
+    return k.value, ms.value
 
 
 def lb_time(ctx):

@@ -43,9 +43,10 @@ def _fields_np(fl):
     return fl["rho"].numpy(), fl["u"].numpy(), fl["theta"].numpy()
 
 
-def _run_gpu(shape, tau, prec, fields, steps, flags=0):
+def _run_gpu(shape, tau, prec, fields, steps, flags=0, kernel=lb.LB_KERNEL_AUTO):
     ctx = lb.lb_init(shape, tau, prec, flags=flags)
     try:
+        lb.lb_set_step_kernel(ctx, kernel)
         lb.lb_set_fields(ctx, fields["rho"].cuda(), fields["u"].cuda(), fields["theta"].cuda())
         lb.lb_step(ctx, steps)
         nx, ny, nz = shape
@@ -57,15 +58,18 @@ def _run_gpu(shape, tau, prec, fields, steps, flags=0):
     return f
 
 
-# With LB_FLAG_STAGED, nx = 128 / 256 / 384 run the shared-memory-staged kernel (one tile per
-# row, and first/middle/last tiles of a row); every other case runs the direct-load kernel.
-STAGED_SHAPES = [(128, 3, 2), (256, 1, 1), (384, 2, 3)]
+# Every step kernel on every shape it applies to: DIRECT2/DIRECT2R need ny even (odd ny falls back
+# to DIRECT1); STAGED needs nx a multiple of 128 (nx = 128: one tile per row; 256, 384: first,
+# middle and last tiles of a row) and falls back to DIRECT2/DIRECT1 elsewhere; FP64 always runs
+# DIRECT1.
+KERNELS = [lb.LB_KERNEL_DIRECT1, lb.LB_KERNEL_DIRECT2, lb.LB_KERNEL_DIRECT2R, lb.LB_KERNEL_STAGED]
+STREAM_SHAPES = [(4, 4, 4), (3, 5, 7), (1, 2, 5), (133, 4, 3), (128, 2, 3), (256, 2, 1), (384, 2, 3)]
 
 
-@pytest.mark.parametrize("staged", [False, True])
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("shape", [(4, 4, 4), (3, 5, 7), (1, 2, 5), (133, 3, 2)] + STAGED_SHAPES)
-def test_streaming_is_bit_exact(prec, shape, staged, perm, w_lib):
+@pytest.mark.parametrize("shape", STREAM_SHAPES)
+def test_streaming_is_bit_exact(prec, shape, kernel, perm, w_lib):
     nx, ny, nz = shape
     rng = np.random.default_rng(100 + nx)
     h = 0.1 * rng.uniform(-1, 1, size=(2, 41, nz, ny, nx))
@@ -74,8 +78,9 @@ def test_streaming_is_bit_exact(prec, shape, staged, perm, w_lib):
     else:
         stored = h
     raw = torch.from_numpy(stored).to(TORCH_DTYPE[prec]).cuda().contiguous()
-    ctx = lb.lb_init(shape, math.inf, prec, flags=lb.LB_FLAG_STAGED if staged else 0)
+    ctx = lb.lb_init(shape, math.inf, prec)
     try:
+        lb.lb_set_step_kernel(ctx, kernel)
         lb.lb_set_state(ctx, raw)
         lb.lb_step(ctx, 1)
         out = torch.empty_like(raw)
@@ -101,20 +106,20 @@ def test_config1_f64_standing_wave_200_steps(perm):
     assert rel.max() <= 1e-12, rel.max()
 
 
-@pytest.mark.parametrize("staged", [False, True])
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("project", [True, False])
-@pytest.mark.parametrize("shape", [(133, 5, 3), (384, 3, 2), (128, 4, 3)])
-def test_random_fields_parity(prec, project, shape, staged, perm):
-    # (133, 5, 3): direct kernel, two x-blocks with a ragged tail, odd y/z;
-    # (384, 3, 2) and (128, 4, 3): staged kernel (3 tiles per row; one tile per row)
+@pytest.mark.parametrize("shape", [(133, 5, 3), (133, 4, 3), (384, 2, 3), (128, 4, 3)])
+def test_random_fields_parity(prec, project, shape, kernel, perm):
+    # (133, *, 3): two x-blocks with a ragged tail, odd and even ny; (384, 2, 3): three tiles
+    # per row for the staged kernel; (128, 4, 3): one tile per row
     th0 = lb.lb_theta0()
     amp = 0.05 if prec in ("f64", "f32") else 0.02
     fl = wl.random_fields(*shape, th0, seed=7, du=amp, drho=amp, dtheta=amp)
     tau = 0.3
     steps = 20
-    flags = (0 if project else lb.LB_FLAG_PAPER_LITERAL) | (lb.LB_FLAG_STAGED if staged else 0)
-    got = to_oracle_order(_run_gpu(shape, tau, prec, fl, steps, flags=flags), perm)
+    flags = 0 if project else lb.LB_FLAG_PAPER_LITERAL
+    got = to_oracle_order(_run_gpu(shape, tau, prec, fl, steps, flags=flags, kernel=kernel), perm)
     ref = oracle.step(oracle.init_fields(*_fields_np(fl), project=project), tau, steps, project=project)
     rel = np.abs(got - ref) / np.abs(ref)
     assert rel.max() <= RANDOM_FIELD_TOL[prec], rel.max()
@@ -229,27 +234,56 @@ def test_unstable_state_is_reported():
         lb.lb_destroy(ctx)
 
 
-def test_step_variant_selection():
-    S = lb.LB_FLAG_STAGED
-    for shape, prec, flags, expect in [((256, 2, 2), "f16", S, 256), ((384, 2, 2), "f32", S, 128),
-                                       ((130, 2, 2), "f32", S, 0), ((256, 2, 2), "f64", S, 0),
-                                       ((256, 2, 2), "bf16", 0, 0)]:
-        ctx = lb.lb_init(shape, 0.5, prec, flags=flags)
+def test_step_kernel_selection_and_fallbacks():
+    K = lb
+    cases = [((256, 2, 2), "f16", K.LB_KERNEL_STAGED, K.LB_KERNEL_STAGED),
+             ((256, 2, 2), "f16", K.LB_KERNEL_AUTO, K.LB_KERNEL_DIRECT2),
+             ((256, 3, 2), "f32", K.LB_KERNEL_DIRECT2, K.LB_KERNEL_DIRECT1),   # odd ny
+             ((130, 2, 2), "f32", K.LB_KERNEL_STAGED, K.LB_KERNEL_DIRECT2),    # nx not a multiple of 128
+             ((256, 2, 2), "f64", K.LB_KERNEL_STAGED, K.LB_KERNEL_DIRECT1),
+             ((256, 2, 2), "bf16", K.LB_KERNEL_DIRECT2R, K.LB_KERNEL_DIRECT2R)]
+    for shape, prec, req, expect in cases:
+        ctx = lb.lb_init(shape, 0.5, prec)
         try:
-            assert lb.lb_step_variant(ctx) == expect, (shape, prec, flags)
+            lb.lb_set_step_kernel(ctx, req)
+            assert lb.lb_step_variant(ctx) == expect, (shape, prec, req)
         finally:
             lb.lb_destroy(ctx)
+    ctx = lb.lb_init((256, 2, 2), 0.5, "f16", flags=lb.LB_FLAG_STAGED)
+    try:
+        assert lb.lb_step_variant(ctx) == K.LB_KERNEL_STAGED
+    finally:
+        lb.lb_destroy(ctx)
+
+
+def test_step_autotuner_keeps_state():
+    shape = (256, 4, 3)
+    fl = wl.random_fields(*shape, lb.lb_theta0(), seed=14, du=0.02, drho=0.02, dtheta=0.02)
+    ctx = lb.lb_init(shape, 0.3, "f16")
+    try:
+        lb.lb_set_fields(ctx, fl["rho"], fl["u"], fl["theta"])
+        lb.lb_step(ctx, 2)
+        a = np.empty(lb.lb_state_bytes(ctx), dtype=np.uint8)
+        lb.lb_get_state(ctx, a)
+        k, ms = lb.lb_tune(ctx, reps=2)
+        assert k == lb.lb_step_variant(ctx) and ms > 0
+        b = np.empty_like(a)
+        lb.lb_get_state(ctx, b)
+        assert np.array_equal(a, b)
+    finally:
+        lb.lb_destroy(ctx)
 
 
 @pytest.mark.parametrize("prec", ["f32", "f16", "bf16"])
-def test_staged_and_direct_kernels_agree(prec):
+def test_step_kernels_agree(prec):
     shape = (256, 4, 3)
     th0 = lb.lb_theta0()
     fl = wl.random_fields(*shape, th0, seed=13, du=0.02, drho=0.02, dtheta=0.02)
     outs = []
-    for flags in (lb.LB_FLAG_STAGED, 0):
-        ctx = lb.lb_init(shape, 0.3, prec, flags=flags)
+    for kernel in KERNELS:
+        ctx = lb.lb_init(shape, 0.3, prec)
         try:
+            lb.lb_set_step_kernel(ctx, kernel)
             lb.lb_set_fields(ctx, fl["rho"], fl["u"], fl["theta"])
             lb.lb_step(ctx, 10)
             f = np.empty((2, 41, 3, 4, 256))
@@ -257,8 +291,11 @@ def test_staged_and_direct_kernels_agree(prec):
         finally:
             lb.lb_destroy(ctx)
         outs.append(f)
-    rel = np.abs(outs[0] - outs[1]) / outs[1]
-    assert rel.max() <= RANDOM_FIELD_TOL[prec] / 4, rel.max()
+    # every kernel meets the oracle bound; they may differ from each other by as much (different
+    # but equally valid FP32 evaluation orders, each rounded to the storage type)
+    for o in outs[1:]:
+        rel = np.abs(o - outs[0]) / outs[0]
+        assert rel.max() <= RANDOM_FIELD_TOL[prec], rel.max()
 
 
 def test_free_streaming_time_counter():
