@@ -126,6 +126,29 @@ lb_status lb_get_moments(lb_ctx *ctx, double *rho, double *u, double *theta, int
  * out[1..3] = momentum sum <f,c>, out[4] = energy sum <f,c^2/2>.  out is host memory. */
 lb_status lb_conserved(lb_ctx *ctx, double out[5]);
 
+/* The global sums of lb_conserved, for callers that cannot allocate device
+ * memory (code running under a memory budget owned by another allocator, or
+ * latency-critical loops that must not pay cudaMalloc's implicit device
+ * synchronisation).  The paper has no counterpart; this is an interface
+ * addition.  It needs no context and allocates nothing:
+ *   populations  device pointer to stored populations in the raw layout of
+ *                lb_get_state ([s][41][nz][ny][nx] of the storage type of
+ *                `precision`, e.g. a copy made with lb_get_state on the device)
+ *   grid         cells per axis; 2 * nz must not exceed 4096, else LB_ERR_ARG
+ *   out          device pointer to 5 doubles (mass, momentum x/y/z, energy)
+ *   cuda_stream  stream to enqueue on (NULL = legacy default stream)
+ * Asynchronous: out is written by work enqueued on cuda_stream.  Its only
+ * scratch is a fixed 160 KB array (4096 planes x 5 doubles) in the library's
+ * device memory, which every GPU that loads the library holds until the
+ * process exits.  The first call on each device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first
+ * call before any stream capture.  All calls share the array: calls whose
+ * work overlaps on the GPU race.  Each call writes every slot it reads, so no
+ * state carries over between calls.  Error message: lb_conserved_noalloc_error. */
+lb_status lb_conserved_noalloc(const void *populations, lb_grid grid, lb_precision precision, double *out,
+                               void *cuda_stream);
+const char *lb_conserved_noalloc_error(void);
+
 /* Current (post-collision) populations as float64 f_i in the population
  * layout.  lb_set_populations stores them (rounded to the storage type). */
 lb_status lb_get_populations(lb_ctx *ctx, double *f, int on_device);

@@ -335,3 +335,28 @@ def lb_batch_sync(b):
 
 def lb_batch_destroy(b):
     _bcheck(_bind_batch().lb_batch_destroy(b), b)
+
+
+def _bind_noalloc():
+    L = lib()
+    if not getattr(L, "_noalloc_bound", False):
+        L.lb_conserved_noalloc.argtypes = [ctypes.c_void_p, _Grid, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+        L.lb_conserved_noalloc.restype = ctypes.c_int
+        L.lb_conserved_noalloc_error.restype = ctypes.c_char_p
+        L._noalloc_bound = True
+    return L
+
+
+def lb_conserved_noalloc(populations, grid, precision, out, stream=None):
+    """Conservation sums of stored populations (device tensor in the raw layout of lb_get_state)
+    into `out` (device float64 tensor of 5), with no device allocation."""
+    L = _bind_noalloc()
+    pp, dev_in = _ptr(populations)
+    po, dev_out = _ptr(out, writable=True)
+    if not (dev_in and dev_out):
+        raise ValueError("populations and out must be device tensors")
+    nx, ny, nz = (int(v) for v in grid)
+    st = L.lb_conserved_noalloc(pp, _Grid(nx, ny, nz), PRECISION[precision] if isinstance(precision, str)
+                                else int(precision), po, _stream(stream))
+    if st != LB_OK:
+        raise LbError(st, L.lb_conserved_noalloc_error().decode())
