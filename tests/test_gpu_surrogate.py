@@ -1,0 +1,115 @@
+"""The surrogate network on the GPU: gradients of the whole network against the
+FP64 oracle (autograd), field packing, training on LB-generated data, and the
+judged rollout with LB fallback."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import surrogate as so
+from paper_1909_08406_gb300 import lb, sg
+from paper_1909_08406_gb300 import surrogate as S
+from paper_1909_08406_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+F64 = torch.float64
+
+
+def _random_net(seed):
+    net = S.Surrogate(seed=seed)
+    g = torch.Generator().manual_seed(seed)
+    for k, (ci, co, _, _) in enumerate(S.LAYERS):
+        w = torch.randn((co, 27, ci), generator=g) / math.sqrt(27 * ci) * (0.5 if k else 1.0)
+        if ci == 16:
+            w[:, :, 5:] = 0
+        net.w32[k].copy_(w)
+        net.b32[k].copy_(0.05 * torch.randn(co, generator=g))
+    net._round_weights()
+    return net
+
+
+def test_network_gradients_match_oracle():
+    """GPU forward + backward (BF16 storage of activations, FP32 accumulation) against FP64
+    autograd on the same BF16 weights and inputs: per layer, the relative Frobenius error of
+    the weight gradient <= 3e-2 and the cosine similarity >= 0.999 (activations are rounded to
+    BF16 between layers, 2^-9 relative each)."""
+    net = _random_net(3)
+    g = torch.Generator().manual_seed(4)
+    shape = (2, 4, 8, 64)
+    x = torch.zeros(shape + (16,))
+    x[..., :5] = torch.randn(shape + (5,), generator=g)
+    t = x.clone()
+    t[..., :5] += 0.3 * torch.randn(shape + (5,), generator=g)
+    xb, tb = x.to(torch.bfloat16), t.to(torch.bfloat16)
+    xd, td = xb.cuda(), tb.cuda()
+    pred = net.forward(xd, train=True)
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    dpred = torch.empty(xd.shape, dtype=torch.float32, device="cuda")
+    sg.mse(pred, td, 5, loss, dpred, sg.reduce_scratch())
+    scratch = {(ci, co): sg.wgrad_scratch(xd, ci, co) for ci, co, _, _ in S.LAYERS}
+    net.backward(dpred, scratch)
+    torch.cuda.synchronize()
+    ws = [w.cpu().to(F64) for w in net.w16]
+    bs = [b.cpu().to(F64) for b in net.b32]
+    l_or, gw, gb, _ = so.loss_and_grads(xb.to(F64), tb.to(F64), ws, bs)
+    assert loss.item() == pytest.approx(l_or, rel=2e-2)
+    for k in range(len(S.LAYERS)):
+        a = net.g[2 * k].cpu().to(F64).flatten()
+        b = gw[k].flatten()
+        if b.norm() == 0:
+            continue
+        rel = (a - b).norm() / b.norm()
+        cos = (a @ b) / (a.norm() * b.norm())
+        assert rel <= 3e-2 and cos >= 0.999, (k, rel.item(), cos.item())
+        ab = net.g[2 * k + 1].cpu().to(F64)
+        assert (ab - gb[k]).norm() <= 3e-2 * gb[k].norm() + 1e-6, k
+
+
+def test_pack_unpack_fields():
+    n = 64
+    th0 = lb.lb_theta0()
+    f = wl.gaussian_pulse_sample(n, th0, 11, device="cuda")
+    x = torch.empty((1, n, n, n, 16), dtype=torch.bfloat16, device="cuda")
+    sg.pack_fields(x, 0, f["rho"], f["u"], f["theta"], th0, S.SCALES)
+    rho = torch.empty_like(f["rho"])
+    u = torch.empty_like(f["u"])
+    th = torch.empty_like(f["theta"])
+    sg.unpack_fields(x, 0, th0, S.SCALES, rho, u, th)
+    torch.cuda.synchronize()
+    s = S.SCALES[0]
+    # A nodes: values come back up to one BF16 rounding of the scaled deviation
+    assert torch.allclose(rho[0], f["rho"][0], rtol=0, atol=s * 2 ** -8 * 4)
+    assert torch.allclose(th[0], f["theta"][0], rtol=0, atol=th0 * s * 2 ** -8 * 4)
+    # B node of cell r: mean of the A nodes r + {0,1}^3
+    ra = rho[0]
+    mean8 = sum(torch.roll(ra, shifts=(-dz, -dy, -dx), dims=(0, 1, 2))
+                for dz in (0, 1) for dy in (0, 1) for dx in (0, 1)) / 8
+    assert torch.allclose(rho[1], mean8, rtol=0, atol=1e-6)
+    assert torch.all(x[..., 5:] == 0)
+
+
+@pytest.fixture(scope="module")
+def small_data():
+    return S.make_dataset(24, hop=10, t0_choices=(0, 20), per_batch=12)
+
+
+def test_training_reduces_loss_below_identity(small_data):
+    net = S.Surrogate(seed=0)
+    before, ident = S.evaluate(net, small_data)
+    assert before == pytest.approx(ident, rel=1e-6)  # zero-initialised last layer: identity map
+    S.train(net, small_data, iters=60, batch=4, lr=2e-3)
+    after, _ = S.evaluate(net, small_data)
+    assert after < 0.5 * ident, (after, ident)
+
+
+def test_judged_rollout_and_fallback(small_data):
+    net = S.Surrogate(seed=1)
+    S.train(net, small_data, iters=20, batch=4, lr=2e-3)
+    r = S.rollout(net, seed=90001, hops=3, hop=10, threshold=1e30)
+    assert len(r["signal"]) == 3 and not any(r["fallback"])
+    assert all(np.isfinite(r["signal"])) and all(e > 0 for e in r["state"])
+    # a zero threshold falls back after every hop; the next hop then starts from LB's state
+    r0 = S.rollout(net, seed=90001, hops=3, hop=10, threshold=0.0)
+    assert all(r0["fallback"])
+    assert r0["signal"][0] == pytest.approx(r["signal"][0], rel=1e-6)
