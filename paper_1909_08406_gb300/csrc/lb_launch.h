@@ -23,7 +23,14 @@ struct LaunchConsts {
 enum Prec { kF64 = 0, kF32 = 1, kF16 = 2, kBF16 = 3 };
 
 // Step kernels (values match LB_KERNEL_* in gblb.h).
-enum StepKernel { kKernelAuto = -1, kKernelDirect1 = 0, kKernelDirect2 = 1, kKernelDirect2R = 2, kKernelStaged = 3 };
+enum StepKernel {
+    kKernelAuto = -1,
+    kKernelDirect1 = 0,
+    kKernelDirect2 = 1,
+    kKernelDirect2R = 2,
+    kKernelStaged = 3,
+    kKernelWarpSpec = 4
+};
 
 // The kernel a request resolves to for this precision and grid (falls back where one does not apply).
 int resolve_kernel(int prec, const Dims& d, int kernel);

@@ -4,10 +4,14 @@
 //   kKernelDirect2R  k_step2<.,.,4>: the same, register budget for 4 CTAs/SM
 //   kKernelStaged    k_step_tma:    rows fetched by TMA bulk copies into a
 //                                   shared-memory ring
+//   kKernelWarpSpec  k_step_ws:     the same staging with a dedicated producer
+//                                   warp, full/empty mbarriers, and consumers
+//                                   updating two rows per thread (FP32x2)
 // This unit is compiled with ptxas double-precision-use warnings so that no
 // FP64 instruction slips into the float path.
 #include "lb_kernels.cuh"
 #include "lb_step_tma.cuh"
+#include "lb_step_ws.cuh"
 
 namespace gblb {
 
@@ -68,6 +72,43 @@ static cudaError_t run_tma(const void* src, void* dst, const Dims& d, const Laun
     return cudaGetLastError();
 }
 
+template <class Codec, bool P, class Cfg>
+static cudaError_t run_ws(const void* src, void* dst, const Dims& d, const LaunchConsts& c, double twobeta, int* err,
+                          cudaStream_t st) {
+    using T = typename Codec::raw_t;
+    static TmaLaunchInfo info;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    auto kern = k_step_ws<Codec, P, Cfg>;
+    if (info.device != dev) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::THREADS, Cfg::SMEM);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        info.grid = per_sm * sms;
+        info.device = dev;
+    }
+    const int64_t ntiles = d.rows / 2 * (d.nx / Cfg::TX);
+    const int grid = (int)(ntiles < info.grid ? ntiles : info.grid);
+    const long long wait_limit = 4000000000LL;  // ~2 s of SM clock
+    kern<<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(static_cast<const T*>(src), static_cast<T*>(dst), d, c.kf,
+                                                 (float)twobeta, err, wait_limit);
+    return cudaGetLastError();
+}
+
+// Warp-specialised shapes: 128 x per tile, 4 consumer warps.  16-bit: 70.8 KB ring
+// (3 stages) -> up to 3 CTAs/SM; FP32: 89.3 KB ring (2 stages) -> 2 CTAs/SM.
+template <class Codec>
+struct WsShape {
+    using Cfg = WsCfg<Codec, 128, 4, (sizeof(typename Codec::raw_t) == 2 ? 3 : 2),
+                      (sizeof(typename Codec::raw_t) == 2 ? 3 : 2)>;
+};
+
 // Staged-kernel shapes per storage type: (tile width, threads, ring depth, CTAs/SM).
 // FP32, TX 256: 86.6 KB ring -> 2 CTAs/SM; TX 128: 66.9 KB -> 3 CTAs/SM.
 // 16-bit, TX 256: 66.9 KB -> 3 CTAs/SM; TX 128: 47.3 KB -> 4 CTAs/SM.
@@ -99,6 +140,9 @@ int resolve_kernel(int prec, const Dims& d, int kernel) {
     if (prec == kF64) return kKernelDirect1;
     const bool two_rows = d.ny % 2 == 0 && d.plane < ((int64_t)1 << 32);
     switch (kernel) {
+        case kKernelWarpSpec:
+            return (two_rows && d.nx % 128 == 0 && tma_tile_width(prec, d)) ? kKernelWarpSpec
+                                                                             : resolve_kernel(prec, d, kKernelAuto);
         case kKernelStaged: return tma_tile_width(prec, d) ? kKernelStaged : resolve_kernel(prec, d, kKernelAuto);
         case kKernelDirect2:
         case kKernelDirect2R: return two_rows ? kernel : kKernelDirect1;
@@ -115,6 +159,7 @@ static cudaError_t step_codec(int prec, int kernel, const void* src, void* dst, 
             if (tma_tile_width(prec, d) == 256)
                 return run_tma<Codec, P, typename TmaShape<Codec, 256>::Cfg>(src, dst, d, c, twobeta, err, st);
             return run_tma<Codec, P, typename TmaShape<Codec, 128>::Cfg>(src, dst, d, c, twobeta, err, st);
+        case kKernelWarpSpec: return run_ws<Codec, P, typename WsShape<Codec>::Cfg>(src, dst, d, c, twobeta, err, st);
         case kKernelDirect2: return run_direct2<Codec, P, 3>(src, dst, d, c, twobeta, err, st);
         case kKernelDirect2R: return run_direct2<Codec, P, 4>(src, dst, d, c, twobeta, err, st);
         default: return run_direct1<Codec, P>(src, dst, d, c, twobeta, err, st);

@@ -62,7 +62,8 @@ def _run_gpu(shape, tau, prec, fields, steps, flags=0, kernel=lb.LB_KERNEL_AUTO)
 # to DIRECT1); STAGED needs nx a multiple of 128 (nx = 128: one tile per row; 256, 384: first,
 # middle and last tiles of a row) and falls back to DIRECT2/DIRECT1 elsewhere; FP64 always runs
 # DIRECT1.
-KERNELS = [lb.LB_KERNEL_DIRECT1, lb.LB_KERNEL_DIRECT2, lb.LB_KERNEL_DIRECT2R, lb.LB_KERNEL_STAGED]
+KERNELS = [lb.LB_KERNEL_DIRECT1, lb.LB_KERNEL_DIRECT2, lb.LB_KERNEL_DIRECT2R, lb.LB_KERNEL_STAGED,
+           lb.LB_KERNEL_WARPSPEC]
 STREAM_SHAPES = [(4, 4, 4), (3, 5, 7), (1, 2, 5), (133, 4, 3), (128, 2, 3), (256, 2, 1), (384, 2, 3)]
 
 
