@@ -79,10 +79,43 @@ __device__ __forceinline__ void batch_tile(const BatchSim* __restrict__ sims, in
                                   tb_of<R>(S), err, s, z, y, x);
 }
 
-template <class Codec, bool PROJECT>
-__global__ void __launch_bounds__(128) k_batch_step(const BatchSim* __restrict__ sims, int nsims, int parity,
-                                                    Consts<typename Codec::R> K, int tx, int ry, int* err) {
-    batch_tile<Codec, PROJECT, LoadNC>(sims, nsims, blockIdx.x, parity, K, tx, ry, err);
+// Two-row tiles (FP32 arithmetic, every simulation with ny even): a tile is TX x-nodes by RY
+// row pairs; each thread updates (y, x) and (y + 1, x) with packed FP32x2 arithmetic.
+template <class Codec, bool PROJECT, class Ld>
+__device__ __forceinline__ void batch_tile2(const BatchSim* __restrict__ sims, int nsims, int64_t t, int parity,
+                                            const Consts<float>& K, int tx, int ry, int* err) {
+    using T = typename Codec::raw_t;
+    int lo = 0, hi = nsims - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sims[mid].tile0 <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const BatchSim& S = sims[lo];
+    const int64_t local = t - S.tile0;
+    const int64_t rg = local / S.tiles_x;
+    const int xc = (int)(local - rg * S.tiles_x);
+    const int x = xc * tx + (int)(threadIdx.x % tx);
+    const int64_t rp = rg * ry + (int64_t)(threadIdx.x / tx);
+    if (x >= S.d.nx || rp >= S.d.rows / 2) return;
+    const int nyh = S.d.ny >> 1;
+    const int y = 2 * (int)(rp % nyh);
+    const int64_t zr = rp / nyh;
+    const int z = (int)(zr % S.d.nz);
+    const int s = (int)(zr / S.d.nz);
+    step_node2<Codec, PROJECT, Ld>(static_cast<const T*>(S.buf[parity]), static_cast<T*>(S.buf[parity ^ 1]), S.d, K,
+                                   S.tbf, err, s, z, y, x);
+}
+
+template <class Codec, bool PROJECT, bool TWO>
+__global__ void __launch_bounds__(128, 3) k_batch_step(const BatchSim* __restrict__ sims, int nsims, int parity,
+                                                    Consts<typename Codec::KS> K, int tx, int ry, int* err) {
+    if constexpr (TWO)
+        batch_tile2<Codec, PROJECT, LoadNC>(sims, nsims, blockIdx.x, parity, K, tx, ry, err);
+    else
+        batch_tile<Codec, PROJECT, LoadNC>(sims, nsims, blockIdx.x, parity, K, tx, ry, err);
 }
 
 struct GridBar {
@@ -121,15 +154,19 @@ __device__ __forceinline__ bool grid_sync(GridBar* bar, unsigned expected, long 
     return __syncthreads_and(ok) != 0;
 }
 
-template <class Codec, bool PROJECT>
-__global__ void __launch_bounds__(128) k_batch_persistent(const BatchSim* __restrict__ sims, int nsims, int64_t ntiles,
-                                                          int64_t nsteps, int parity0, Consts<typename Codec::R> K,
+template <class Codec, bool PROJECT, bool TWO>
+__global__ void __launch_bounds__(128, 3) k_batch_persistent(const BatchSim* __restrict__ sims, int nsims, int64_t ntiles,
+                                                          int64_t nsteps, int parity0, Consts<typename Codec::KS> K,
                                                           int tx, int ry, int* err, GridBar* bar, unsigned expected,
                                                           long long limit) {
     for (int64_t step = 0; step < nsteps; ++step) {
         const int parity = (int)((parity0 + step) & 1);
-        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x)
-            batch_tile<Codec, PROJECT, LoadCG>(sims, nsims, t, parity, K, tx, ry, err);
+        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            if constexpr (TWO)
+                batch_tile2<Codec, PROJECT, LoadCG>(sims, nsims, t, parity, K, tx, ry, err);
+            else
+                batch_tile<Codec, PROJECT, LoadCG>(sims, nsims, t, parity, K, tx, ry, err);
+        }
         if (step + 1 < nsteps && !grid_sync(bar, expected, limit)) {
             if (threadIdx.x == 0) atomicOr(err, 2);
             return;
@@ -149,8 +186,8 @@ static cudaError_t dispatch_codec(int prec, F&& f) {
 }
 
 template <class Codec>
-static const Consts<typename Codec::R>& consts_of(const LaunchConsts& c) {
-    if constexpr (std::is_same<typename Codec::R, double>::value)
+static const Consts<typename Codec::KS>& consts_of(const LaunchConsts& c) {
+    if constexpr (std::is_same<typename Codec::KS, double>::value)
         return c.kd;
     else
         return c.kf;
@@ -175,6 +212,7 @@ struct lb_batch {
     BatchSim* d_sims = nullptr;
     std::vector<BatchSim> h_sims;
     int tx = 32, ry = 4;
+    bool two_rows = false;  // FP32 arithmetic and every simulation with ny even: two rows per thread
     int64_t ntiles = 0;
     int* d_err = nullptr;
     GridBar* d_bar = nullptr;
@@ -221,7 +259,8 @@ static lb_status plan(lb_batch* b, int tx, int ry) {
         s.tbf = (float)c->twobeta;
         s.tiles_x = (int)((c->d.nx + tx - 1) / tx);
         s.tile0 = t;
-        t += (int64_t)s.tiles_x * ((c->d.rows + ry - 1) / ry);
+        const int64_t rows = b->two_rows ? c->d.rows / 2 : c->d.rows;
+        t += (int64_t)s.tiles_x * ((rows + ry - 1) / ry);
     }
     if (t > 0x7fffffffLL) return bfail(b, LB_ERR_ARG, "batch work list too long for one launch");
     b->ntiles = t;
@@ -238,14 +277,24 @@ static cudaError_t launch_batch_step(lb_batch* b, int parity, cudaStream_t st) {
     const LaunchConsts& lc = lattice_consts();
     return dispatch_codec(b->prec, [&](auto codec) {
         using C = decltype(codec);
+        const unsigned grid = (unsigned)b->ntiles, block = (unsigned)(b->tx * b->ry);
+        if constexpr (std::is_same<typename C::R, float>::value) {
+            if (b->two_rows) {
+                if (b->project)
+                    k_batch_step<C, true, true><<<grid, block, 0, st>>>(b->d_sims, b->n, parity, consts_of<C>(lc),
+                                                                        b->tx, b->ry, b->d_err);
+                else
+                    k_batch_step<C, false, true><<<grid, block, 0, st>>>(b->d_sims, b->n, parity, consts_of<C>(lc),
+                                                                         b->tx, b->ry, b->d_err);
+                return cudaGetLastError();
+            }
+        }
         if (b->project)
-            k_batch_step<C, true><<<(unsigned)b->ntiles, b->tx * b->ry, 0, st>>>(b->d_sims, b->n, parity,
-                                                                                   consts_of<C>(lc), b->tx, b->ry,
-                                                                                   b->d_err);
+            k_batch_step<C, true, false><<<grid, block, 0, st>>>(b->d_sims, b->n, parity, consts_of<C>(lc), b->tx,
+                                                                 b->ry, b->d_err);
         else
-            k_batch_step<C, false><<<(unsigned)b->ntiles, b->tx * b->ry, 0, st>>>(b->d_sims, b->n, parity,
-                                                                                    consts_of<C>(lc), b->tx, b->ry,
-                                                                                    b->d_err);
+            k_batch_step<C, false, false><<<grid, block, 0, st>>>(b->d_sims, b->n, parity, consts_of<C>(lc), b->tx,
+                                                                  b->ry, b->d_err);
         return cudaGetLastError();
     });
 }
@@ -254,9 +303,12 @@ static cudaError_t launch_persistent(lb_batch* b, int64_t nsteps, int parity, cu
     const LaunchConsts& lc = lattice_consts();
     return dispatch_codec(b->prec, [&](auto codec) -> cudaError_t {
         using C = decltype(codec);
-        void (*kern)(const BatchSim*, int, int64_t, int64_t, int, Consts<typename C::R>, int, int, int*, GridBar*,
+        void (*kern)(const BatchSim*, int, int64_t, int64_t, int, Consts<typename C::KS>, int, int, int*, GridBar*,
                      unsigned, long long) =
-            b->project ? k_batch_persistent<C, true> : k_batch_persistent<C, false>;
+            b->project ? k_batch_persistent<C, true, false> : k_batch_persistent<C, false, false>;
+        if constexpr (std::is_same<typename C::R, float>::value) {
+            if (b->two_rows) kern = b->project ? k_batch_persistent<C, true, true> : k_batch_persistent<C, false, true>;
+        }
         int per_sm = 0;
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, b->tx * b->ry, 0);
         if (e != cudaSuccess) return e;
@@ -270,7 +322,7 @@ static cudaError_t launch_persistent(lb_batch* b, int64_t nsteps, int parity, cu
         const BatchSim* sims = b->d_sims;
         int nsims = b->n;
         int64_t ntiles = b->ntiles;
-        Consts<typename C::R> K = consts_of<C>(lc);
+        Consts<typename C::KS> K = consts_of<C>(lc);
         int tx = b->tx, ry = b->ry;
         int* err = b->d_err;
         GridBar* bar = b->d_bar;
@@ -314,6 +366,8 @@ lb_status lb_batch_init(lb_batch** out, int nsims, const lb_grid* grids, const d
         b->ctx.push_back(c);
     }
     b->h_sims.resize(nsims);
+    b->two_rows = precision != LB_F64;
+    for (auto* c : b->ctx) b->two_rows = b->two_rows && c->d.ny % 2 == 0 && c->d.plane < ((int64_t)1 << 32);
     cudaError_t e = cudaGetDevice(&b->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->ps, cudaStreamNonBlocking);

@@ -99,6 +99,12 @@ __global__ void __launch_bounds__(kStepThreads) k_step(const typename Codec::raw
     step_node<Codec, PROJECT>(src, dst, d, K, tb, err, s, z, y, x);
 }
 
+template <class Codec, bool PROJECT, class Ld>
+__device__ __forceinline__ void step_node2(const typename Codec::raw_t* __restrict__ src,
+                                           typename Codec::raw_t* __restrict__ dst, const Dims& d,
+                                           const Consts<float>& K, float tb, int* __restrict__ err, int s, int z,
+                                           int y, int x);
+
 // Two-rows-per-thread direct-load step kernel (FP32 arithmetic, any storage
 // except FP64): each thread updates nodes (s, z, y, x) and (s, z, y + 1, x)
 // with packed FP32x2 arithmetic.  Addresses are formed from 32-bit in-plane
@@ -111,8 +117,6 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2(const typename Cod
                                                         typename Codec::raw_t* __restrict__ dst, Dims d,
                                                         Consts<float> K, float tb, int* __restrict__ err,
                                                         int chunks) {
-    using T = typename Codec::raw_t;
-    using C2 = Codec2<Codec>;
     const int64_t t = blockIdx.x;
     const int64_t rp = t / chunks;
     const int x = (int)(t - rp * chunks) * blockDim.x + threadIdx.x;
@@ -122,6 +126,17 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2(const typename Cod
     const int64_t zr = rp / nyh;
     const int z = (int)(zr % d.nz);
     const int s = (int)(zr / d.nz);
+    step_node2<Codec, PROJECT, LoadNC>(src, dst, d, K, tb, err, s, z, y, x);
+}
+
+// Nodes (s, z, y, x) and (s, z, y + 1, x) (y even), packed FP32x2 arithmetic; see k_step2.
+template <class Codec, bool PROJECT, class Ld>
+__device__ __forceinline__ void step_node2(const typename Codec::raw_t* __restrict__ src,
+                                           typename Codec::raw_t* __restrict__ dst, const Dims& d,
+                                           const Consts<float>& K, float tb, int* __restrict__ err, int s, int z,
+                                           int y, int x) {
+    using T = typename Codec::raw_t;
+    using C2 = Codec2<Codec>;
     const uint32_t nx = (uint32_t)d.nx, nxy = (uint32_t)d.nx * (uint32_t)d.ny;
     const uint32_t plane = (uint32_t)d.plane;
 
@@ -163,7 +178,7 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2(const typename Cod
             base = same;
         }
         const T* p = base + (size_t)I * plane;
-        pv[I] = Codec::pack2(LoadNC::load(p + oa), LoadNC::load(p + ob));
+        pv[I] = Codec::pack2(Ld::load(p + oa), Ld::load(p + ob));
     });
     auto vget = [&](auto I) { return F2(Codec::unpack2(pv[I])); };
 
