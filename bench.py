@@ -33,7 +33,8 @@ sys.path.insert(0, ROOT)
 BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 DTYPE_NAME = {"f64": "f64", "f32": "f32", "f16": "f32 (f16 storage)", "bf16": "f32 (bf16 storage)"}
 NU = 0.01
-STEP_KERNEL_SOURCES = ["lb_common.cuh", "lb_kernels.cuh", "lb_step_tma.cuh", "lb_step_f32.cu", "lb_step_f64.cu"]
+STEP_KERNEL_SOURCES = ["lb_common.cuh", "lb_kernels.cuh", "lb_step_tma.cuh", "lb_step_ws.cuh", "lb_step_f32.cu",
+                       "lb_step_f64.cu"]
 
 
 def parse():
@@ -332,7 +333,7 @@ def main():
     head = args.precision
     kernels = [args.kernel] if args.kernel is not None else [lb.LB_KERNEL_DIRECT1, lb.LB_KERNEL_DIRECT2,
                                                             lb.LB_KERNEL_DIRECT2R, lb.LB_KERNEL_STAGED,
-                                                            lb.LB_KERNEL_WARPSPEC]
+                                                            lb.LB_KERNEL_WARPSPEC, lb.LB_KERNEL_DIRECT2X]
     probe_ctx = lb.lb_init((n, n, n), tau, head)
     applicable = []
     for k in kernels:

@@ -174,6 +174,8 @@ lb_status lb_set_state(lb_ctx *ctx, const void *raw, int on_device);
  *   LB_KERNEL_WARPSPEC the staging done by one producer warp through a ring of
  *                      full/empty mbarriers, consumer warps updating two rows
  *                      per thread (not FP64; nx a multiple of 128, ny even)
+ *   LB_KERNEL_DIRECT2X two x-adjacent nodes per thread, FP32x2 arithmetic,
+ *                      32-bit paired loads and stores (FP16/BF16 storage; nx even)
  *   LB_KERNEL_AUTO     DIRECT2 where it applies, else DIRECT1 (the default)
  * A request that does not apply to the grid falls back to one that does. */
 #define LB_KERNEL_AUTO (-1)
@@ -182,8 +184,9 @@ lb_status lb_set_state(lb_ctx *ctx, const void *raw, int on_device);
 #define LB_KERNEL_DIRECT2R 2
 #define LB_KERNEL_STAGED 3
 #define LB_KERNEL_WARPSPEC 4
+#define LB_KERNEL_DIRECT2X 5
 
-/* Kernel lb_step will run for this context (LB_KERNEL_DIRECT1 .. LB_KERNEL_WARPSPEC). */
+/* Kernel lb_step will run for this context (LB_KERNEL_DIRECT1 .. LB_KERNEL_DIRECT2X). */
 int lb_step_variant(const lb_ctx *ctx);
 /* Request a step kernel (LB_KERNEL_*). */
 lb_status lb_set_step_kernel(lb_ctx *ctx, int kernel);

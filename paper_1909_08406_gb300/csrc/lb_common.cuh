@@ -139,6 +139,11 @@ struct CodecF16 {
     using pair_t = __half2;
     static __device__ __forceinline__ pair_t pack2(raw_t a, raw_t b) { return __halves2half2(a, b); }
     static __device__ __forceinline__ float2 unpack2(pair_t p) { return __half22float2(p); }
+    // (hi of a, lo of b): the pair that starts at an odd element between two aligned pairs
+    static __device__ __forceinline__ pair_t straddle(pair_t a, pair_t b) {
+        return __halves2half2(__high2half(a), __low2half(b));
+    }
+    static __device__ __forceinline__ pair_t to_raw2(float2 v) { return __float22half2_rn(v); }
 };
 
 struct CodecBF16 {
@@ -154,6 +159,10 @@ struct CodecBF16 {
     using pair_t = __nv_bfloat162;
     static __device__ __forceinline__ pair_t pack2(raw_t a, raw_t b) { return __halves2bfloat162(a, b); }
     static __device__ __forceinline__ float2 unpack2(pair_t p) { return __bfloat1622float2(p); }
+    static __device__ __forceinline__ pair_t straddle(pair_t a, pair_t b) {
+        return __halves2bfloat162(__high2bfloat16(a), __low2bfloat16(b));
+    }
+    static __device__ __forceinline__ pair_t to_raw2(float2 v) { return __float22bfloat162_rn(v); }
 };
 
 // ---------------------------------------------------------------------------
@@ -182,6 +191,13 @@ __device__ __forceinline__ F2& operator+=(F2& a, F2 b) {
 }
 using ::fma;  // keep the scalar overloads visible next to the F2 one
 __device__ __forceinline__ F2 fma(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
+
+// Reciprocals of the node scalars (1/rho, theta0/theta, ...).  FP64 keeps the IEEE
+// division; the FP32 paths use the hardware reciprocal approximation (within 2 ulp),
+// far below the FP32 rounding of the populations themselves.
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ F2 recip(F2 x) { return F2(__fdividef(1.0f, x.v.x), __fdividef(1.0f, x.v.y)); }
 
 // Two-node codec over a one-node storage codec: same storage, F2 arithmetic.
 template <class Base>
@@ -245,7 +261,7 @@ __device__ __forceinline__ NodeState<R> state_from_moments(const NodeMoments<R>&
     NodeState<R> st;
     st.drho = m.drho;
     st.rho = R(1) + m.drho;
-    const R inv_rho = R(1) / st.rho;
+    const R inv_rho = recip(st.rho);
     st.ux = m.jx * inv_rho;
     st.uy = m.jy * inv_rho;
     st.uz = m.jz * inv_rho;
@@ -279,7 +295,7 @@ __device__ __forceinline__ void equilibrium_relax_g(const NodeState<typename Cod
                                                     typename Codec::R omb, VGet&& vget, Sink&& sink) {
     using R = typename Codec::R;
     const R rho = st.rho, eta = st.eta;
-    const R inv_1pe = R(1) / (R(1) + eta);           // theta_0 / theta
+    const R inv_1pe = recip(R(1) + eta);             // theta_0 / theta
     const R inv_theta = inv_1pe / K.theta0;          // 1 / theta
     const R usq = st.ux * st.ux + st.uy * st.uy + st.uz * st.uz;
     const R g = usq * inv_theta;                     // u^2 / theta
@@ -287,7 +303,7 @@ __device__ __forceinline__ void equilibrium_relax_g(const NodeState<typename Cod
     const R r2 = inv_1pe * inv_1pe;
     const R M2 = (K.m2[0] + eta * (K.m2[1] + eta * (K.m2[2] + eta * K.m2[3]))) * r2;
     const R M2p = (K.m2p[0] + eta * (K.m2p[1] + eta * (K.m2p[2] + eta * K.m2p[3]))) * r2;
-    const R A1 = R(2.5) * M2 / (R(1) + R(2.5) * M2);
+    const R A1 = R(2.5) * M2 * recip(R(1) + R(2.5) * M2);
     const R A2 = R(5) * A1 * (R(1) - M2) - (R(3) + M2p - R(5) * M2);
     // rest-state factors per shell: f~_s = w_s rho R_s, R_s - 1 = eta (p1 + eta (p2 + eta p3))
     R rR[kShells], rRm1[kShells];
@@ -325,7 +341,7 @@ __device__ __forceinline__ void equilibrium_relax_g(const NodeState<typename Cod
         const R djx = -upx * S - it3 * st.ux * (S4 * ux2 + R(3) * S22 * (usq - ux2));
         const R djy = -upy * S - it3 * st.uy * (S4 * uy2 + R(3) * S22 * (usq - uy2));
         const R djz = -upz * S - it3 * st.uz * (S4 * uz2 + R(3) * S22 * (usq - uz2));
-        const R k = inv_theta / rho;
+        const R k = inv_theta * recip(rho);
         vx = djx * k;
         vy = djy * k;
         vz = djz * k;

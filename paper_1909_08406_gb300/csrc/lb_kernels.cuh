@@ -196,6 +196,83 @@ __device__ __forceinline__ void step_node2(const typename Codec::raw_t* __restri
                                      });
 }
 
+// Two x-adjacent nodes per thread (16-bit storage): nodes (s, z, y, x) and
+// (s, z, y, x + 1), x even, packed FP32x2 arithmetic.  Each plane is read as
+// aligned pairs of 16-bit values: one 32-bit load when the plane's x shift is
+// even, two loads and a byte permute when it is odd; the two results of a
+// plane are written with one 32-bit store.  Requires nx even and
+// nx * ny * nz < 2^32.  Blocks are numbered chunk-fastest over rows.
+template <class Codec, bool PROJECT, int MINB>
+__global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Codec::raw_t* __restrict__ src,
+                                                         typename Codec::raw_t* __restrict__ dst, Dims d,
+                                                         Consts<float> K, float tb, int* __restrict__ err,
+                                                         int chunks) {
+    using T = typename Codec::raw_t;
+    using P = typename Codec::pair_t;
+    using C2 = Codec2<Codec>;
+    const int64_t t = blockIdx.x;
+    const int64_t row = t / chunks;
+    const int x = 2 * ((int)(t - row * chunks) * blockDim.x + threadIdx.x);
+    if (x >= d.nx) return;
+    const int y = (int)(row % d.ny);
+    const int64_t zr = row / d.ny;
+    const int z = (int)(zr % d.nz);
+    const int s = (int)(zr / d.nz);
+    const uint32_t nx = (uint32_t)d.nx, nxy = (uint32_t)d.nx * (uint32_t)d.ny;
+    const uint32_t plane = (uint32_t)d.plane;
+
+    // aligned pair starts: x - 2, x, x + 2 (periodic; nx even keeps them even)
+    const uint32_t xm = (uint32_t)wrap(x - 2, d.nx), x0 = (uint32_t)x, xq = (uint32_t)wrap(x + 2, d.nx);
+    uint32_t yo[5], zo[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        yo[k] = (uint32_t)wrap(y - (k - 2), d.ny) * nx;
+        zo[k] = (uint32_t)wrap(z - (k - 2), d.nz) * nxy;
+    }
+    const uint32_t hyp = s ? yo[2] : yo[3], hym = s ? yo[1] : yo[2];
+    const uint32_t hzp = s ? zo[2] : zo[3], hzm = s ? zo[1] : zo[2];
+    const T* same = src + (size_t)s * kQ * d.plane;
+    const T* other = src + (size_t)(1 - s) * kQ * d.plane;
+
+    auto ld = [&](const T* p, uint32_t off) { return LoadNC::load(reinterpret_cast<const P*>(p + off)); };
+    // values at (x - dx, x + 1 - dx) of the row at p, for a shift dx in {-2, ..., 2}
+    auto pair_at = [&](const T* p, int dx) -> P {
+        switch (dx) {
+            case 2: return ld(p, xm);
+            case 1: return Codec::straddle(ld(p, xm), ld(p, x0));
+            case 0: return ld(p, x0);
+            case -1: return Codec::straddle(ld(p, x0), ld(p, xq));
+            default: return ld(p, xq);
+        }
+    };
+    P pv[kQ];
+    static_for<kQ>([&](auto I) {
+        constexpr Vel c = vel(I);
+        if constexpr (c.shell == 5) {
+            const T* p = other + (size_t)I * plane + ((c.z > 0 ? hzp : hzm) + (c.y > 0 ? hyp : hym));
+            // x shift 1 - s for a +1/2 component, -s for -1/2
+            if constexpr (c.x > 0)
+                pv[I] = s ? pair_at(p, 0) : pair_at(p, 1);
+            else
+                pv[I] = s ? pair_at(p, -1) : pair_at(p, 0);
+        } else {
+            const T* p = same + (size_t)I * plane + (zo[c.z / 2 + 2] + yo[c.y / 2 + 2]);
+            pv[I] = pair_at(p, c.x / 2);
+        }
+    });
+    auto vget = [&](auto I) { return F2(Codec::unpack2(pv[I])); };
+
+    constexpr float inv_scale = (float)(1.0 / Codec::kScale);
+    const NodeMoments<F2> m =
+        moments_from<F2>([&](auto I) { return C2::dev(vget(I), F2(K.w[vel(I).shell] * inv_scale)); });
+    const NodeState<F2> st = state_from_moments(m, K);
+    if (!state_ok(st)) atomicOr(err, 1);
+
+    P* outp = reinterpret_cast<P*>(dst + (size_t)s * kQ * d.plane + ((uint32_t)z * nxy + (uint32_t)y * nx + x0));
+    equilibrium_relax_g<C2, PROJECT>(st, K, F2(tb * (float)Codec::kScale), F2(1.f - tb), vget,
+                                     [&](auto I, F2 val) { outp[(size_t)I * (plane / 2)] = Codec::to_raw2(val.v); });
+}
+
 // Populations = equilibrium of the given float64 fields, for nodes
 // q in [q0, q0 + count), q = s * plane + (z * ny + y) * nx + x.  Field
 // pointers are indexed by q - q0 (u component c at c * ustride + q - q0).

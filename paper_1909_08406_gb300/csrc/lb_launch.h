@@ -29,7 +29,8 @@ enum StepKernel {
     kKernelDirect2 = 1,
     kKernelDirect2R = 2,
     kKernelStaged = 3,
-    kKernelWarpSpec = 4
+    kKernelWarpSpec = 4,
+    kKernelDirect2X = 5
 };
 
 // The kernel a request resolves to for this precision and grid (falls back where one does not apply).
