@@ -268,18 +268,13 @@ def main():
     from paper_1909_08406_gb300 import lb
     from paper_1909_08406_gb300 import workloads as wl
 
+    from paper_1909_08406_gb300 import decomp
+
     def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
+        decomp.barrier()
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return decomp.max_over_ranks(x, device="cuda")
 
     n = args.n
     nodes = 2 * n ** 3

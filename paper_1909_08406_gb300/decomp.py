@@ -1,0 +1,115 @@
+"""Host-side logic for spreading the update over several ranks (one process per GPU).
+
+Two splits of the periodic bcc grid are described here.
+
+* Replicas: every rank advances its own independent grid (or its share of a
+  batch of independent simulations).  There is no data-path exchange; the
+  ranks meet only to time the run (``barrier``, ``max_over_ranks``) and to
+  add up the work done (``aggregate_rate``).
+
+* z slabs of one grid: rank r owns the sc-cell planes ``slab_bounds(nz, W, r)``
+  of both sub-lattices.  The update of a node pulls from at most two cells
+  away along z (integer links of the sc-2 shell shift by +-2 cells; the
+  bcc-1/2 links shift by 0 or 1 cell, Sec. III), so a halo of ``HALO = 2``
+  planes on each side, refreshed once per step, makes the slab's interior
+  update identical to the whole grid's.  A slab padded with its halos can be
+  stepped by the periodic kernel as it is: the wrap only touches halo planes,
+  and those are overwritten by the next exchange.  The global conserved sums
+  are the FP64 sums of the ranks' interior sums.
+
+The functions take array-like tensors in the population layout
+``f[s][i][z][y][x]`` and a ``torch.distributed`` process group; with NCCL they
+move device tensors, with gloo host tensors.
+"""
+from __future__ import annotations
+
+HALO = 2
+
+
+def slab_bounds(nz: int, world: int, rank: int) -> tuple[int, int]:
+    """Planes [z0, z1) of rank `rank` when nz planes are split over `world` ranks as evenly as
+    possible (the first nz % world ranks get one plane more).  Every slab must hold at least
+    HALO planes so that a halo comes from one neighbour only."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("bad rank/world")
+    base, extra = divmod(nz, world)
+    if base < HALO:
+        raise ValueError(f"nz = {nz} over {world} ranks leaves slabs thinner than the halo ({HALO})")
+    z0 = rank * base + min(rank, extra)
+    return z0, z0 + base + (1 if rank < extra else 0)
+
+
+def pad(f_slab, halo: int = HALO):
+    """A new tensor [2][Q][nz_local + 2 halo][ny][nx] with the slab in the middle and the halo
+    planes zero; ``exchange_halos`` fills them."""
+    import torch
+    s, q, nzl, ny, nx = f_slab.shape
+    out = torch.zeros((s, q, nzl + 2 * halo, ny, nx), dtype=f_slab.dtype, device=f_slab.device)
+    out[:, :, halo:halo + nzl] = f_slab
+    return out
+
+
+def interior(f_padded, halo: int = HALO):
+    return f_padded[:, :, halo:f_padded.shape[2] - halo]
+
+
+def exchange_halos(f_padded, group=None, halo: int = HALO):
+    """Refresh the halo planes of a padded slab from the periodic neighbours' interiors: the
+    lower halo receives the top `halo` interior planes of rank - 1, the upper halo the bottom
+    `halo` interior planes of rank + 1.  One exchange per step; with one rank the slab is its
+    own neighbour (the periodic wrap)."""
+    import torch
+    import torch.distributed as dist
+    nzp = f_padded.shape[2]
+    lo_send = f_padded[:, :, halo:2 * halo].contiguous()            # to rank - 1 (its upper halo)
+    hi_send = f_padded[:, :, nzp - 2 * halo:nzp - halo].contiguous()  # to rank + 1 (its lower halo)
+    world = dist.get_world_size(group) if dist.is_initialized() else 1
+    if world == 1:
+        f_padded[:, :, :halo] = hi_send
+        f_padded[:, :, nzp - halo:] = lo_send
+        return f_padded
+    rank = dist.get_rank(group)
+    down, up = (rank - 1) % world, (rank + 1) % world
+    lo_recv = torch.empty_like(lo_send)
+    hi_recv = torch.empty_like(hi_send)
+    # tag 0: planes going up (they land in the receiver's lower halo); tag 1: going down
+    ops = [dist.P2POp(dist.isend, hi_send, up, group, 0), dist.P2POp(dist.isend, lo_send, down, group, 1),
+           dist.P2POp(dist.irecv, lo_recv, down, group, 0), dist.P2POp(dist.irecv, hi_recv, up, group, 1)]
+    for r in dist.batch_isend_irecv(ops):
+        r.wait()
+    f_padded[:, :, :halo] = lo_recv
+    f_padded[:, :, nzp - halo:] = hi_recv
+    return f_padded
+
+
+def allreduce_sum_f64(values, group=None, device="cpu"):
+    """Sum of a few FP64 numbers over the ranks (the global conserved quantities)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    if dist.is_initialized() and dist.get_world_size(group) > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    return [float(v) for v in t.cpu()]
+
+
+def barrier(group=None):
+    import torch.distributed as dist
+    if dist.is_initialized() and dist.get_world_size(group) > 1:
+        dist.barrier(group)
+
+
+def max_over_ranks(x: float, group=None, device="cpu") -> float:
+    """The largest of the ranks' values (the time of the slowest rank bounds the job)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_initialized() or dist.get_world_size(group) == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    return float(t.item())
+
+
+def aggregate_rate(units_this_rank: float, seconds_this_rank: float, group=None, device="cpu") -> float:
+    """Whole-job throughput: the units all ranks processed divided by the slowest rank's time."""
+    total = allreduce_sum_f64([units_this_rank], group, device)[0]
+    return total / max_over_ranks(seconds_this_rank, group, device)
