@@ -175,7 +175,9 @@ lb_status lb_set_state(lb_ctx *ctx, const void *raw, int on_device);
  *                      full/empty mbarriers, consumer warps updating two rows
  *                      per thread (not FP64; nx a multiple of 128, ny even)
  *   LB_KERNEL_DIRECT2X two x-adjacent nodes per thread, FP32x2 arithmetic,
- *                      32-bit paired loads and stores (FP16/BF16 storage; nx even)
+ *                      32-bit paired loads and stores, next row's loads overlapped
+ *                      with the current row's relaxation (FP16/BF16 storage; nx even)
+ *   LB_KERNEL_DIRECT2XW the same with a register budget of 2 CTAs per SM
  *   LB_KERNEL_AUTO     DIRECT2 where it applies, else DIRECT1 (the default)
  * A request that does not apply to the grid falls back to one that does. */
 #define LB_KERNEL_AUTO (-1)
@@ -185,8 +187,9 @@ lb_status lb_set_state(lb_ctx *ctx, const void *raw, int on_device);
 #define LB_KERNEL_STAGED 3
 #define LB_KERNEL_WARPSPEC 4
 #define LB_KERNEL_DIRECT2X 5
+#define LB_KERNEL_DIRECT2XW 6
 
-/* Kernel lb_step will run for this context (LB_KERNEL_DIRECT1 .. LB_KERNEL_DIRECT2X). */
+/* Kernel lb_step will run for this context (LB_KERNEL_DIRECT1 .. LB_KERNEL_DIRECT2XW). */
 int lb_step_variant(const lb_ctx *ctx);
 /* Request a step kernel (LB_KERNEL_*). */
 lb_status lb_set_step_kernel(lb_ctx *ctx, int kernel);

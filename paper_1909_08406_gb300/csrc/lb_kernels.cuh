@@ -200,42 +200,49 @@ __device__ __forceinline__ void step_node2(const typename Codec::raw_t* __restri
 // (s, z, y, x + 1), x even, packed FP32x2 arithmetic.  Each plane is read as
 // aligned pairs of 16-bit values: one 32-bit load when the plane's x shift is
 // even, two loads and a byte permute when it is odd; the two results of a
-// plane are written with one 32-bit store.  Requires nx even and
-// nx * ny * nz < 2^32.  Blocks are numbered chunk-fastest over rows.
-template <class Codec, bool PROJECT, int MINB>
-__global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Codec::raw_t* __restrict__ src,
-                                                         typename Codec::raw_t* __restrict__ dst, Dims d,
-                                                         Consts<float> K, float tb, int* __restrict__ err,
-                                                         int chunks) {
+// plane are written with one 32-bit store.
+//
+// A block covers one chunk of x for `rpb` consecutive rows (s, z, y), y
+// fastest.  The loads of the next row are software-pipelined into the
+// registers of the current one: as soon as population I of the current row
+// has been relaxed and stored, its register receives population I of the next
+// row, so a row's loads are in flight while the previous row is still being
+// relaxed.  Requires nx even and nx * ny * nz < 2^32.
+template <class Codec>
+struct RowAddr2x {
+    using T = typename Codec::raw_t;
+    const T* same;   // population 0 of the node's own sub-lattice
+    const T* other;  // population 0 of the other sub-lattice
+    uint32_t yo[5], zo[5];
+    uint32_t hyp, hym, hzp, hzm;
+    int s;
+    __device__ __forceinline__ void set(const T* src, const Dims& d, int s_, int z, int y) {
+        s = s_;
+        const uint32_t nx = (uint32_t)d.nx, nxy = (uint32_t)d.nx * (uint32_t)d.ny;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            yo[k] = (uint32_t)wrap(y - (k - 2), d.ny) * nx;
+            zo[k] = (uint32_t)wrap(z - (k - 2), d.nz) * nxy;
+        }
+        // half links: delta = 1 - s for a +1/2 component, -s for -1/2
+        hyp = s ? yo[2] : yo[3];
+        hym = s ? yo[1] : yo[2];
+        hzp = s ? zo[2] : zo[3];
+        hzm = s ? zo[1] : zo[2];
+        same = src + (size_t)s * kQ * d.plane;
+        other = src + (size_t)(1 - s) * kQ * d.plane;
+    }
+};
+
+// The pair of upwind values of population I for the nodes x, x + 1 of the row
+// described by `a` (source x - delta for a shift delta in {-2, ..., 2}).
+template <class Codec, int I>
+__device__ __forceinline__ typename Codec::pair_t load_pair2x(const RowAddr2x<Codec>& a, uint32_t plane,
+                                                              uint32_t xm, uint32_t x0, uint32_t xq) {
     using T = typename Codec::raw_t;
     using P = typename Codec::pair_t;
-    using C2 = Codec2<Codec>;
-    const int64_t t = blockIdx.x;
-    const int64_t row = t / chunks;
-    const int x = 2 * ((int)(t - row * chunks) * blockDim.x + threadIdx.x);
-    if (x >= d.nx) return;
-    const int y = (int)(row % d.ny);
-    const int64_t zr = row / d.ny;
-    const int z = (int)(zr % d.nz);
-    const int s = (int)(zr / d.nz);
-    const uint32_t nx = (uint32_t)d.nx, nxy = (uint32_t)d.nx * (uint32_t)d.ny;
-    const uint32_t plane = (uint32_t)d.plane;
-
-    // aligned pair starts: x - 2, x, x + 2 (periodic; nx even keeps them even)
-    const uint32_t xm = (uint32_t)wrap(x - 2, d.nx), x0 = (uint32_t)x, xq = (uint32_t)wrap(x + 2, d.nx);
-    uint32_t yo[5], zo[5];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        yo[k] = (uint32_t)wrap(y - (k - 2), d.ny) * nx;
-        zo[k] = (uint32_t)wrap(z - (k - 2), d.nz) * nxy;
-    }
-    const uint32_t hyp = s ? yo[2] : yo[3], hym = s ? yo[1] : yo[2];
-    const uint32_t hzp = s ? zo[2] : zo[3], hzm = s ? zo[1] : zo[2];
-    const T* same = src + (size_t)s * kQ * d.plane;
-    const T* other = src + (size_t)(1 - s) * kQ * d.plane;
-
+    constexpr Vel c = vel(I);
     auto ld = [&](const T* p, uint32_t off) { return LoadNC::load(reinterpret_cast<const P*>(p + off)); };
-    // values at (x - dx, x + 1 - dx) of the row at p, for a shift dx in {-2, ..., 2}
     auto pair_at = [&](const T* p, int dx) -> P {
         switch (dx) {
             case 2: return ld(p, xm);
@@ -245,32 +252,78 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Co
             default: return ld(p, xq);
         }
     };
+    if constexpr (c.shell == 5) {
+        const T* p = a.other + (size_t)I * plane + ((c.z > 0 ? a.hzp : a.hzm) + (c.y > 0 ? a.hyp : a.hym));
+        if constexpr (c.x > 0)
+            return a.s ? pair_at(p, 0) : pair_at(p, 1);
+        else
+            return a.s ? pair_at(p, -1) : pair_at(p, 0);
+    } else {
+        const T* p = a.same + (size_t)I * plane + (a.zo[c.z / 2 + 2] + a.yo[c.y / 2 + 2]);
+        return pair_at(p, c.x / 2);
+    }
+}
+
+template <class Codec, bool PROJECT, int MINB>
+__global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Codec::raw_t* __restrict__ src,
+                                                         typename Codec::raw_t* __restrict__ dst, Dims d,
+                                                         Consts<float> K, float tb, int* __restrict__ err,
+                                                         int chunks, int rpb) {
+    using T = typename Codec::raw_t;
+    using P = typename Codec::pair_t;
+    using C2 = Codec2<Codec>;
+    const uint32_t t = blockIdx.x;
+    const uint32_t grp = t / (uint32_t)chunks;
+    const int x = 2 * ((int)(t - grp * (uint32_t)chunks) * (int)blockDim.x + (int)threadIdx.x);
+    if (x >= d.nx) return;
+    const uint32_t r0 = grp * (uint32_t)rpb;
+    const uint32_t r1 = min(r0 + (uint32_t)rpb, (uint32_t)d.rows);
+    int y = (int)(r0 % (uint32_t)d.ny);
+    const uint32_t zr = r0 / (uint32_t)d.ny;
+    int z = (int)(zr % (uint32_t)d.nz);
+    int s = (int)(zr / (uint32_t)d.nz);
+    const uint32_t nx = (uint32_t)d.nx, nxy = (uint32_t)d.nx * (uint32_t)d.ny;
+    const uint32_t plane = (uint32_t)d.plane;
+
+    // aligned pair starts: x - 2, x, x + 2 (periodic; nx even keeps them even)
+    const uint32_t xm = (uint32_t)wrap(x - 2, d.nx), x0 = (uint32_t)x, xq = (uint32_t)wrap(x + 2, d.nx);
+
+    RowAddr2x<Codec> a;
+    a.set(src, d, s, z, y);
     P pv[kQ];
-    static_for<kQ>([&](auto I) {
-        constexpr Vel c = vel(I);
-        if constexpr (c.shell == 5) {
-            const T* p = other + (size_t)I * plane + ((c.z > 0 ? hzp : hzm) + (c.y > 0 ? hyp : hym));
-            // x shift 1 - s for a +1/2 component, -s for -1/2
-            if constexpr (c.x > 0)
-                pv[I] = s ? pair_at(p, 0) : pair_at(p, 1);
-            else
-                pv[I] = s ? pair_at(p, -1) : pair_at(p, 0);
-        } else {
-            const T* p = same + (size_t)I * plane + (zo[c.z / 2 + 2] + yo[c.y / 2 + 2]);
-            pv[I] = pair_at(p, c.x / 2);
-        }
-    });
+    static_for<kQ>([&](auto I) { pv[I] = load_pair2x<Codec, I>(a, plane, xm, x0, xq); });
     auto vget = [&](auto I) { return F2(Codec::unpack2(pv[I])); };
-
     constexpr float inv_scale = (float)(1.0 / Codec::kScale);
-    const NodeMoments<F2> m =
-        moments_from<F2>([&](auto I) { return C2::dev(vget(I), F2(K.w[vel(I).shell] * inv_scale)); });
-    const NodeState<F2> st = state_from_moments(m, K);
-    if (!state_ok(st)) atomicOr(err, 1);
 
-    P* outp = reinterpret_cast<P*>(dst + (size_t)s * kQ * d.plane + ((uint32_t)z * nxy + (uint32_t)y * nx + x0));
-    equilibrium_relax_g<C2, PROJECT>(st, K, F2(tb * (float)Codec::kScale), F2(1.f - tb), vget,
-                                     [&](auto I, F2 val) { outp[(size_t)I * (plane / 2)] = Codec::to_raw2(val.v); });
+    for (uint32_t r = r0; r < r1; ++r) {
+        // the next row, in (s, z, y) order
+        int yn = y + 1, zn = z, sn = s;
+        if (yn == d.ny) {
+            yn = 0;
+            if (++zn == d.nz) {
+                zn = 0;
+                ++sn;
+            }
+        }
+        const bool more = r + 1 < r1;
+        RowAddr2x<Codec> an;
+        an.set(src, d, more ? sn : s, more ? zn : z, more ? yn : y);
+
+        const NodeMoments<F2> m =
+            moments_from<F2>([&](auto I) { return C2::dev(vget(I), F2(K.w[vel(I).shell] * inv_scale)); });
+        const NodeState<F2> st = state_from_moments(m, K);
+        if (!state_ok(st)) atomicOr(err, 1);
+
+        P* outp = reinterpret_cast<P*>(dst + (size_t)s * kQ * d.plane + ((uint32_t)z * nxy + (uint32_t)y * nx + x0));
+        equilibrium_relax_g<C2, PROJECT>(st, K, F2(tb * (float)Codec::kScale), F2(1.f - tb), vget,
+                                         [&](auto I, F2 val) {
+                                             outp[(size_t)I * (plane / 2)] = Codec::to_raw2(val.v);
+                                             if (more) pv[I] = load_pair2x<Codec, I>(an, plane, xm, x0, xq);
+                                         });
+        s = sn;
+        z = zn;
+        y = yn;
+    }
 }
 
 // Populations = equilibrium of the given float64 fields, for nodes

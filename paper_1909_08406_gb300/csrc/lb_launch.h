@@ -30,7 +30,8 @@ enum StepKernel {
     kKernelDirect2R = 2,
     kKernelStaged = 3,
     kKernelWarpSpec = 4,
-    kKernelDirect2X = 5
+    kKernelDirect2X = 5,
+    kKernelDirect2XW = 6
 };
 
 // The kernel a request resolves to for this precision and grid (falls back where one does not apply).

@@ -37,7 +37,10 @@ static cudaError_t run_direct2(const void* src, void* dst, const Dims& d, const 
     return cudaGetLastError();
 }
 
-template <class Codec, bool P>
+// rows per block of the x-pair kernel (the next row's loads overlap the current row's relaxation)
+static constexpr int kRowsPerBlock2x = 4;
+
+template <class Codec, bool P, int MINB>
 static cudaError_t run_direct2x(const void* src, void* dst, const Dims& d, const LaunchConsts& c, double twobeta,
                                 int* err, cudaStream_t st) {
     using T = typename Codec::raw_t;
@@ -47,9 +50,10 @@ static cudaError_t run_direct2x(const void* src, void* dst, const Dims& d, const
         const int half = d.nx / 2;
         const int th = half >= 128 ? 128 : ((half + 31) / 32) * 32;
         const int chunks = (half + th - 1) / th;
-        const int64_t blocks = d.rows * chunks;
-        k_step2x<Codec, P, 3><<<(unsigned)blocks, th, 0, st>>>(static_cast<const T*>(src), static_cast<T*>(dst), d,
-                                                               c.kf, (float)twobeta, err, chunks);
+        const int rpb = kRowsPerBlock2x;
+        const int64_t blocks = ((d.rows + rpb - 1) / rpb) * chunks;
+        k_step2x<Codec, P, MINB><<<(unsigned)blocks, th, 0, st>>>(static_cast<const T*>(src), static_cast<T*>(dst), d,
+                                                               c.kf, (float)twobeta, err, chunks, rpb);
         return cudaGetLastError();
     }
 }
@@ -158,8 +162,9 @@ int resolve_kernel(int prec, const Dims& d, int kernel) {
     const bool two_rows = d.ny % 2 == 0 && d.plane < ((int64_t)1 << 32);
     switch (kernel) {
         case kKernelDirect2X:
+        case kKernelDirect2XW:
             return (storage_bytes(prec) == 2 && d.nx % 2 == 0 && d.plane < ((int64_t)1 << 32))
-                       ? kKernelDirect2X
+                       ? kernel
                        : resolve_kernel(prec, d, kKernelAuto);
         case kKernelWarpSpec:
             return (two_rows && d.nx % 128 == 0 && tma_tile_width(prec, d)) ? kKernelWarpSpec
@@ -181,7 +186,8 @@ static cudaError_t step_codec(int prec, int kernel, const void* src, void* dst, 
                 return run_tma<Codec, P, typename TmaShape<Codec, 256>::Cfg>(src, dst, d, c, twobeta, err, st);
             return run_tma<Codec, P, typename TmaShape<Codec, 128>::Cfg>(src, dst, d, c, twobeta, err, st);
         case kKernelWarpSpec: return run_ws<Codec, P, typename WsShape<Codec>::Cfg>(src, dst, d, c, twobeta, err, st);
-        case kKernelDirect2X: return run_direct2x<Codec, P>(src, dst, d, c, twobeta, err, st);
+        case kKernelDirect2X: return run_direct2x<Codec, P, 3>(src, dst, d, c, twobeta, err, st);
+        case kKernelDirect2XW: return run_direct2x<Codec, P, 2>(src, dst, d, c, twobeta, err, st);
         case kKernelDirect2: return run_direct2<Codec, P, 3>(src, dst, d, c, twobeta, err, st);
         case kKernelDirect2R: return run_direct2<Codec, P, 4>(src, dst, d, c, twobeta, err, st);
         default: return run_direct1<Codec, P>(src, dst, d, c, twobeta, err, st);
