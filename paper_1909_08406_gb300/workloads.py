@@ -22,6 +22,9 @@ thermal tests, Secs. VI-VIII):
                            along y + seeded uniform density noise
   * ``thermoacoustic_pulse`` Gaussian pressure pulse at the centre + seeded
                            random temperature field from a 16^3 Fourier box
+  * ``spherical_pulse``    the 3D acoustic pulse of Sec. VII: rho' = eps exp(-alpha r^2),
+                           alpha = ln 2 / b^2, isentropic (all of it acoustic) or
+                           isothermal
   * ``shear_wave``         transverse velocity wave u_y = U sin(2 pi x / nx)
   * ``batch_sweep``        per-simulation grid edges, tau and amplitudes
   * ``random_fields``      seeded smooth-ish random fields for parity tests
@@ -141,6 +144,39 @@ def thermoacoustic_pulse(n, theta0, amplitude=1e-2, sigma=8.0, theta_amplitude=1
     theta = theta0 * (1.0 + theta_amplitude * g)
     zero = torch.zeros_like(rho)
     return _fields(rho, zero, zero, zero, theta)
+
+
+def spherical_pulse(n, theta0, b=4.0, eps=1e-3, isentropic=True, device="cpu"):
+    """The 3D acoustic spherical pulse (Sec. VII): rho = 1 + eps exp(-alpha r^2) with
+    alpha = ln 2 / b^2 (b is the half-width at half maximum, in sc cells), u = 0, centred in
+    the periodic n^3 box (minimum-image distance).  With `isentropic` the temperature follows
+    the density adiabatically for a monatomic gas, theta = theta0 rho^(2/3), so the whole
+    pulse is an acoustic disturbance; otherwise theta = theta0 (the isothermal pulse, which
+    also carries an entropy mode)."""
+    X, Y, Z = node_positions(n, n, n, device)
+    c = n / 2.0
+
+    def d(P):
+        r = P - c
+        return r - n * torch.round(r / n)
+
+    r2 = d(X) ** 2 + d(Y) ** 2 + d(Z) ** 2
+    rho = 1.0 + eps * torch.exp(-(math.log(2.0) / (b * b)) * r2)
+    theta = theta0 * rho ** (2.0 / 3.0) if isentropic else torch.full_like(rho, theta0)
+    zero = torch.zeros_like(rho)
+    return _fields(rho, zero, zero, zero, theta)
+
+
+def pulse_radius(n, device="cpu"):
+    """Distance of every node from the centre of the n^3 box used by `spherical_pulse`."""
+    X, Y, Z = node_positions(n, n, n, device)
+    c = n / 2.0
+
+    def d(P):
+        r = P - c
+        return r - n * torch.round(r / n)
+
+    return torch.sqrt(d(X) ** 2 + d(Y) ** 2 + d(Z) ** 2)
 
 
 def gaussian_pulse_sample(n, theta0, seed, device="cpu"):
