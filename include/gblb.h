@@ -175,9 +175,12 @@ lb_status lb_set_state(lb_ctx *ctx, const void *raw, int on_device);
  *                      full/empty mbarriers, consumer warps updating two rows
  *                      per thread (not FP64; nx a multiple of 128, ny even)
  *   LB_KERNEL_DIRECT2X two x-adjacent nodes per thread, FP32x2 arithmetic,
- *                      32-bit paired loads and stores, next row's loads overlapped
- *                      with the current row's relaxation (FP16/BF16 storage; nx even)
- *   LB_KERNEL_DIRECT2XW the same with a register budget of 2 CTAs per SM
+ *                      32-bit paired loads and stores (FP16/BF16 storage; nx even)
+ *   LB_KERNEL_DIRECT2XL the same over 4 rows per block, the next row's source
+ *                      rows prefetched into L2 by bulk prefetches
+ *   LB_KERNEL_DIRECT2XA the same over 8 rows per block, each thread copying the
+ *                      next row's values into its own shared-memory slots with
+ *                      cp.async while it computes the current row
  *   LB_KERNEL_AUTO     DIRECT2 where it applies, else DIRECT1 (the default)
  * A request that does not apply to the grid falls back to one that does. */
 #define LB_KERNEL_AUTO (-1)
@@ -187,9 +190,10 @@ lb_status lb_set_state(lb_ctx *ctx, const void *raw, int on_device);
 #define LB_KERNEL_STAGED 3
 #define LB_KERNEL_WARPSPEC 4
 #define LB_KERNEL_DIRECT2X 5
-#define LB_KERNEL_DIRECT2XW 6
+#define LB_KERNEL_DIRECT2XL 6
+#define LB_KERNEL_DIRECT2XA 7
 
-/* Kernel lb_step will run for this context (LB_KERNEL_DIRECT1 .. LB_KERNEL_DIRECT2XW). */
+/* Kernel lb_step will run for this context (LB_KERNEL_DIRECT1 .. LB_KERNEL_DIRECT2XA). */
 int lb_step_variant(const lb_ctx *ctx);
 /* Request a step kernel (LB_KERNEL_*). */
 lb_status lb_set_step_kernel(lb_ctx *ctx, int kernel);

@@ -305,24 +305,17 @@ __device__ __forceinline__ void equilibrium_relax_g(const NodeState<typename Cod
     const R M2p = (K.m2p[0] + eta * (K.m2p[1] + eta * (K.m2p[2] + eta * K.m2p[3]))) * r2;
     const R A1 = R(2.5) * M2 * recip(R(1) + R(2.5) * M2);
     const R A2 = R(5) * A1 * (R(1) - M2) - (R(3) + M2p - R(5) * M2);
-    // rest-state factors per shell: f~_s = w_s rho R_s, R_s - 1 = eta (p1 + eta (p2 + eta p3))
-    R rR[kShells], rRm1[kShells];
-#pragma unroll
-    for (int s = 0; s < kShells; ++s) {
-        const R Rm1 = eta * (K.p1[s] + eta * (K.p2[s] + eta * K.p3[s]));
-        rR[s] = rho + rho * Rm1;       // rho R_s
-        rRm1[s] = st.drho + rho * Rm1; // rho R_s - 1
-    }
+    // rest-state factors per shell: f~_s = w_s rho R_s, R_s - 1 = eta (p1 + eta (p2 + eta p3));
     // per-shell even constant C_s and odd factor D_s of the series
     //   X_i = C_s + a^2/2 + a D_s + a^3/6,  a = u.c/theta
     //   C_s = -g (1 - A1)/2 - g c_s^2 A1 / (6 theta),  D_s = 1 + g A2 / 6 - g c_s^2 A1 / (6 theta)
-    R Cs[kShells], Dm1[kShells];
+    // They are formed where a shell is used (the populations are ordered by shell), which keeps
+    // only one shell's factors live at a time.
     const R gA1_6t = g * A1 * inv_theta * R(1.0 / 6.0);
-#pragma unroll
-    for (int s = 0; s < kShells; ++s) {
-        Cs[s] = R(-0.5) * g * (R(1) - A1) - gA1_6t * K.c2[s];
-        Dm1[s] = g * A2 * R(1.0 / 6.0) - gA1_6t * K.c2[s];
-    }
+    const R cg = R(-0.5) * g * (R(1) - A1);
+    const R dg = g * A2 * R(1.0 / 6.0);
+    auto rest_m1 = [&](int s) { return eta * (K.p1[s] + eta * (K.p2[s] + eta * K.p3[s])); };
+    auto dm1 = [&](int s) { return dg - gA1_6t * K.c2[s]; };
     const R upx = st.ux * inv_theta, upy = st.uy * inv_theta, upz = st.uz * inv_theta;
     // momentum projection v = dj / (rho theta), dj = rho u - sum_i f^eq_i c_i in closed form:
     //   dj_a = -(u_a/theta) sum_s f~_s n2_s (D_s - 1) - [S4 u_a^3 + 3 S22 u_a (u^2 - u_a^2)] / (6 theta^3)
@@ -331,8 +324,8 @@ __device__ __forceinline__ void equilibrium_relax_g(const NodeState<typename Cod
         R S = R(0), S4 = R(0), S22 = R(0);
 #pragma unroll
         for (int s = 1; s < kShells; ++s) {
-            const R ft = K.w[s] * rR[s];
-            S = fma(ft * K.n2[s], Dm1[s], S);
+            const R ft = K.w[s] * (rho + rho * rest_m1(s));
+            S = fma(ft * K.n2[s], dm1(s), S);
             S4 = fma(ft, K.n4[s], S4);
             S22 = fma(ft, K.n22[s], S22);
         }
@@ -348,18 +341,23 @@ __device__ __forceinline__ void equilibrium_relax_g(const NodeState<typename Cod
     }
     // rest population: a = 0
     {
-        const R P0 = tb * rR[0];
-        const R x0 = fma(P0, Cs[0], tb * rRm1[0]);
+        const R rm1 = rest_m1(0);
+        const R P0 = tb * (rho + rho * rm1);
+        const R x0 = fma(P0, cg - gA1_6t * K.c2[0], tb * (st.drho + rho * rm1));
         sink(std::integral_constant<int, 0>{},
              Codec::relax(vget(std::integral_constant<int, 0>{}), omb, x0, K.w[0], tb));
     }
+    R P, B, Ds;  // factors of the current shell
     static_for<20>([&](auto KK) {
         constexpr int ip = 2 * KK + 1, im = 2 * KK + 2;
         constexpr Vel c = vel(ip);
         constexpr int s = c.shell;
-        const R P = tb * rR[s];
-        const R B = fma(P, Cs[s], tb * rRm1[s]);
-        const R Ds = R(1) + Dm1[s];
+        if constexpr (KK == 0 || vel(ip - 2).shell != s) {
+            const R rm1 = rest_m1(s);
+            P = tb * (rho + rho * rm1);
+            B = fma(P, cg - gA1_6t * K.c2[s], tb * (st.drho + rho * rm1));
+            Ds = R(1) + dm1(s);
+        }
         // p_s = D_s u / theta + v
         R a = R(0), q = R(0);
         if constexpr (c.x != 0) {

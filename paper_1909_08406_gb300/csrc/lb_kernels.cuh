@@ -25,7 +25,6 @@ struct LoadCG {
         return __ldcg(p);
     }
 };
-
 // Fused pull update (Sec. II) of one node (s, z, y, x): gather f*_i(x - c_i, t)
 // for all 41 velocities, compute the moments, the equilibrium and the BGK
 // relaxation, and write the 41 post-collision values.  Integer links stay on
@@ -264,7 +263,83 @@ __device__ __forceinline__ typename Codec::pair_t load_pair2x(const RowAddr2x<Co
     }
 }
 
-template <class Codec, bool PROJECT, int MINB>
+// Shared-memory slots of the asynchronous-copy pipeline (MODE 4 below): the
+// aligned pairs that population I's upwind pair is made of, one 32-bit slot
+// each -- two for a plane whose x shift is odd, and for every bcc-1/2 plane
+// (whose shift parity depends on the sub-lattice), else one.
+__host__ __device__ constexpr int x2_nslots(int I) {
+    return (vel(I).shell == 5 || ((vel(I).x / 2) & 1)) ? 2 : 1;
+}
+__host__ __device__ constexpr int x2_slot(int I) {
+    int k = 0;
+    for (int j = 0; j < I; ++j) k += x2_nslots(j);
+    return k;
+}
+constexpr int kX2Slots = x2_slot(kQ);  // 67
+constexpr int kX2Stages = 2;
+
+__device__ __forceinline__ void cp_async4(uint32_t saddr, const void* g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// x shift of population I's source for sub-lattice s (source x - dx).
+template <int I>
+__device__ __forceinline__ int x2_shift(int s) {
+    constexpr Vel c = vel(I);
+    if constexpr (c.shell == 5)
+        return c.x > 0 ? 1 - s : -s;  // delta = 1 - s for +1/2, -s for -1/2
+    else
+        return c.x / 2;
+}
+
+// Row pointer of population I's source row for the row described by `a`.
+template <class Codec, int I>
+__device__ __forceinline__ const typename Codec::raw_t* x2_row(const RowAddr2x<Codec>& a, uint32_t plane) {
+    constexpr Vel c = vel(I);
+    if constexpr (c.shell == 5)
+        return a.other + (size_t)I * plane + ((c.z > 0 ? a.hzp : a.hzm) + (c.y > 0 ? a.hyp : a.hym));
+    else
+        return a.same + (size_t)I * plane + (a.zo[c.z / 2 + 2] + a.yo[c.y / 2 + 2]);
+}
+
+// Prefetch into L2 the part of population I's source row that the nodes
+// [xa, xb) of the row (s, z, y) will read (x - 2 .. x + 2, not wrapped),
+// trimmed inward to whole 16-byte units of that row.
+template <class Codec>
+__device__ __forceinline__ void prefetch_row_l2(const typename Codec::raw_t* src, const Dims& d, int I, int s, int z,
+                                                int y, int xa, int xb) {
+    using T = typename Codec::raw_t;
+    const Vel c = c_vel.v[I];
+    int sp, dz, dy;
+    if (c.shell == 5) {  // half link: delta = 1 - s for +1/2, -s for -1/2; other sub-lattice
+        sp = 1 - s;
+        dz = c.z > 0 ? 1 - s : -s;
+        dy = c.y > 0 ? 1 - s : -s;
+    } else {
+        sp = s;
+        dz = c.z / 2;
+        dy = c.y / 2;
+    }
+    const int zz = wrap(z - dz, d.nz), yy = wrap(y - dy, d.ny);
+    const int lo = max(xa - 2, 0), hi = min(xb + 2, d.nx);
+    const T* row = src + ((size_t)sp * kQ + I) * d.plane + ((size_t)zz * d.ny + yy) * d.nx;
+    const uintptr_t b0 = ((uintptr_t)(row + lo) + 15) & ~(uintptr_t)15;
+    const uintptr_t b1 = ((uintptr_t)(row + hi)) & ~(uintptr_t)15;
+    if (b1 > b0)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b0), "r"((uint32_t)(b1 - b0)) : "memory");
+}
+
+// How a block of the x-pair kernel gets a row's upwind values:
+// MODE 0: direct loads at the start of the row.
+// MODE 2: as MODE 0, plus an L2 bulk prefetch of the next row's source rows
+//         (one per population, by threads 0..40) at the start of the current row.
+// MODE 4: each thread copies the aligned pairs of the next row into its own
+//         shared-memory slots with cp.async (no registers held, no block
+//         barrier: a thread reads only what it copied) while it computes the
+//         current row; cp.async.wait_group orders the two.
+template <class Codec, bool PROJECT, int MINB, int MODE>
 __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Codec::raw_t* __restrict__ src,
                                                          typename Codec::raw_t* __restrict__ dst, Dims d,
                                                          Consts<float> K, float tb, int* __restrict__ err,
@@ -274,26 +349,71 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Co
     using C2 = Codec2<Codec>;
     const uint32_t t = blockIdx.x;
     const uint32_t grp = t / (uint32_t)chunks;
-    const int x = 2 * ((int)(t - grp * (uint32_t)chunks) * (int)blockDim.x + (int)threadIdx.x);
-    if (x >= d.nx) return;
+    const int chunk = (int)(t - grp * (uint32_t)chunks);
+    const int x = 2 * (chunk * (int)blockDim.x + (int)threadIdx.x);
+    const int xa = 2 * chunk * (int)blockDim.x, xb = min(xa + 2 * (int)blockDim.x, d.nx);
     const uint32_t r0 = grp * (uint32_t)rpb;
     const uint32_t r1 = min(r0 + (uint32_t)rpb, (uint32_t)d.rows);
     int y = (int)(r0 % (uint32_t)d.ny);
     const uint32_t zr = r0 / (uint32_t)d.ny;
     int z = (int)(zr % (uint32_t)d.nz);
     int s = (int)(zr / (uint32_t)d.nz);
+    const bool active = x < d.nx;
+    if (!active && (MODE != 2 || threadIdx.x >= kQ)) return;
     const uint32_t nx = (uint32_t)d.nx, nxy = (uint32_t)d.nx * (uint32_t)d.ny;
     const uint32_t plane = (uint32_t)d.plane;
 
     // aligned pair starts: x - 2, x, x + 2 (periodic; nx even keeps them even)
     const uint32_t xm = (uint32_t)wrap(x - 2, d.nx), x0 = (uint32_t)x, xq = (uint32_t)wrap(x + 2, d.nx);
 
-    RowAddr2x<Codec> a;
-    a.set(src, d, s, z, y);
+    extern __shared__ uint32_t x2_smem[];
+    // slot k of stage g of this thread: word (g * kX2Slots + k) * blockDim.x + threadIdx.x
+    auto slot_word = [&](int g, int k) { return (g * kX2Slots + k) * (int)blockDim.x + (int)threadIdx.x; };
+    auto issue_row = [&](int g, const RowAddr2x<Codec>& a) {
+        static_for<kQ>([&](auto I) {
+            constexpr int k = x2_slot(I);
+            const T* p = x2_row<Codec, I>(a, plane);
+            const int dx = x2_shift<I>(a.s);
+            const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(&x2_smem[slot_word(g, k)]);
+            const uint32_t s1 = s0 + 4u * blockDim.x;
+            if (dx == 2) {
+                cp_async4(s0, p + xm);
+            } else if (dx == 1) {
+                cp_async4(s0, p + xm);
+                cp_async4(s1, p + x0);
+            } else if (dx == 0) {
+                cp_async4(s0, p + x0);
+            } else if (dx == -1) {
+                cp_async4(s0, p + x0);
+                cp_async4(s1, p + xq);
+            } else {
+                cp_async4(s0, p + xq);
+            }
+        });
+    };
+    auto read_pair = [&](int g, auto I, int s_) -> P {
+        constexpr int k = x2_slot(I);
+        const int dx = x2_shift<I>(s_);
+        auto word = [&](int kk) {
+            P v;
+            const uint32_t r = x2_smem[slot_word(g, kk)];
+            memcpy(&v, &r, 4);
+            return v;
+        };
+        if (dx == 1 || dx == -1) return Codec::straddle(word(k), word(k + 1));
+        return word(k);
+    };
+
     P pv[kQ];
-    static_for<kQ>([&](auto I) { pv[I] = load_pair2x<Codec, I>(a, plane, xm, x0, xq); });
     auto vget = [&](auto I) { return F2(Codec::unpack2(pv[I])); };
     constexpr float inv_scale = (float)(1.0 / Codec::kScale);
+    int stage = 0;
+    if constexpr (MODE == 4) {
+        RowAddr2x<Codec> a;
+        a.set(src, d, s, z, y);
+        issue_row(0, a);
+        cp_async_commit();
+    }
 
     for (uint32_t r = r0; r < r1; ++r) {
         // the next row, in (s, z, y) order
@@ -306,8 +426,29 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Co
             }
         }
         const bool more = r + 1 < r1;
-        RowAddr2x<Codec> an;
-        an.set(src, d, more ? sn : s, more ? zn : z, more ? yn : y);
+        if constexpr (MODE == 2) {
+            if (more && threadIdx.x < kQ) prefetch_row_l2<Codec>(src, d, (int)threadIdx.x, sn, zn, yn, xa, xb);
+            if (!active) {
+                s = sn;
+                z = zn;
+                y = yn;
+                continue;
+            }
+        }
+        if constexpr (MODE == 4) {
+            if (more) {
+                RowAddr2x<Codec> an;
+                an.set(src, d, sn, zn, yn);
+                issue_row(stage ^ 1, an);
+            }
+            cp_async_commit();
+            cp_async_wait1();  // every group but the newest: this row's copies have landed
+            static_for<kQ>([&](auto I) { pv[I] = read_pair(stage, I, s); });
+        } else {
+            RowAddr2x<Codec> a;
+            a.set(src, d, s, z, y);
+            static_for<kQ>([&](auto I) { pv[I] = load_pair2x<Codec, I>(a, plane, xm, x0, xq); });
+        }
 
         const NodeMoments<F2> m =
             moments_from<F2>([&](auto I) { return C2::dev(vget(I), F2(K.w[vel(I).shell] * inv_scale)); });
@@ -316,13 +457,11 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Co
 
         P* outp = reinterpret_cast<P*>(dst + (size_t)s * kQ * d.plane + ((uint32_t)z * nxy + (uint32_t)y * nx + x0));
         equilibrium_relax_g<C2, PROJECT>(st, K, F2(tb * (float)Codec::kScale), F2(1.f - tb), vget,
-                                         [&](auto I, F2 val) {
-                                             outp[(size_t)I * (plane / 2)] = Codec::to_raw2(val.v);
-                                             if (more) pv[I] = load_pair2x<Codec, I>(an, plane, xm, x0, xq);
-                                         });
+                                         [&](auto I, F2 val) { outp[(size_t)I * (plane / 2)] = Codec::to_raw2(val.v); });
         s = sn;
         z = zn;
         y = yn;
+        stage ^= 1;
     }
 }
 
