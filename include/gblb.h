@@ -76,6 +76,15 @@ typedef enum {
 /* lb_init flags */
 #define LB_FLAG_PAPER_LITERAL 1u /* equilibrium exactly as printed (no momentum projection) */
 #define LB_FLAG_STAGED 2u        /* start with LB_KERNEL_STAGED (see lb_set_step_kernel) */
+/* Exact entropic equilibrium instead of the series (Eqs. (discreteentropiceq),
+ * (fivelagrangemultipliersystem)): f^eq_i = w_i rho exp(-alpha - beta.c_i -
+ * gamma c_i^2), the five multipliers solved per node by Newton's method (FP64
+ * in LB_F64, else FP32), so mass, momentum and energy are exact collision
+ * invariants for any u and theta.  The update then always runs
+ * LB_KERNEL_DIRECT1; a node whose Newton residual stays above tolerance is
+ * reported as LB_ERR_UNSTABLE.  Excludes LB_FLAG_PAPER_LITERAL; not for
+ * lb_batch_init. */
+#define LB_FLAG_ENTROPIC 4u
 
 typedef struct {
     int64_t nx, ny, nz; /* simple-cubic cells per axis, each >= 1; nodes = 2 nx ny nz */
@@ -176,12 +185,10 @@ lb_status lb_set_state(lb_ctx *ctx, const void *raw, int on_device);
  *                      per thread (not FP64; nx a multiple of 128, ny even)
  *   LB_KERNEL_DIRECT2X two x-adjacent nodes per thread, FP32x2 arithmetic,
  *                      32-bit paired loads and stores (FP16/BF16 storage; nx even)
- *   LB_KERNEL_DIRECT2XL the same over 4 rows per block, the next row's source
+ *   LB_KERNEL_DIRECT2XL the same over 2 rows per block, the next row's source
  *                      rows prefetched into L2 by bulk prefetches
- *   LB_KERNEL_DIRECT2XA the same over 8 rows per block, each thread copying the
- *                      next row's values into its own shared-memory slots with
- *                      cp.async while it computes the current row
- *   LB_KERNEL_AUTO     DIRECT2 where it applies, else DIRECT1 (the default)
+ *   LB_KERNEL_AUTO     DIRECT2XL for 16-bit storage with nx even, else DIRECT2 where
+ *                      it applies, else DIRECT1 (the default)
  * A request that does not apply to the grid falls back to one that does. */
 #define LB_KERNEL_AUTO (-1)
 #define LB_KERNEL_DIRECT1 0
@@ -191,9 +198,8 @@ lb_status lb_set_state(lb_ctx *ctx, const void *raw, int on_device);
 #define LB_KERNEL_WARPSPEC 4
 #define LB_KERNEL_DIRECT2X 5
 #define LB_KERNEL_DIRECT2XL 6
-#define LB_KERNEL_DIRECT2XA 7
 
-/* Kernel lb_step will run for this context (LB_KERNEL_DIRECT1 .. LB_KERNEL_DIRECT2XA). */
+/* Kernel lb_step will run for this context (LB_KERNEL_DIRECT1 .. LB_KERNEL_DIRECT2XL). */
 int lb_step_variant(const lb_ctx *ctx);
 /* Request a step kernel (LB_KERNEL_*). */
 lb_status lb_set_step_kernel(lb_ctx *ctx, int kernel);

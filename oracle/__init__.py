@@ -42,6 +42,15 @@ def _p(a):
     return a.ctypes.data_as(_dp)
 
 
+def _kind(project):
+    """Equilibrium used by collide/step/init_fields: project=True (series with the momentum
+    projection), False (the series as printed) or "entropic" (the exact entropic equilibrium,
+    Eq. (discreteentropiceq), by Newton's method)."""
+    if project == "entropic":
+        return ctypes.c_int(2)
+    return ctypes.c_int(1 if project else 0)
+
+
 def _threads(n):
     return ctypes.c_int(0 if n is None else int(n))
 
@@ -115,7 +124,7 @@ def moments(f):
 def collide(f, tau, project=True):
     f = np.ascontiguousarray(f, dtype=np.float64)
     out = np.zeros(NV)
-    lib().or_collide(_p(f), ctypes.c_double(tau), ctypes.c_int(int(project)), _p(out))
+    lib().or_collide(_p(f), ctypes.c_double(tau), _kind(project), _p(out))
     return out
 
 
@@ -132,7 +141,7 @@ def step(f, tau, nsteps, project=True, nthreads=None):
     f = np.array(f, dtype=np.float64, order="C", copy=True)
     _, _, nz, ny, nx = f.shape
     work = np.empty_like(f)
-    lib().or_step(_i64(nx), _i64(ny), _i64(nz), ctypes.c_double(tau), ctypes.c_int(int(project)), _i64(nsteps),
+    lib().or_step(_i64(nx), _i64(ny), _i64(nz), ctypes.c_double(tau), _kind(project), _i64(nsteps),
                   _p(f), _p(work), _threads(nthreads))
     return f
 
@@ -143,7 +152,7 @@ def step_nodes(fpost, tau, nodes, project=True, nthreads=None):
     _, _, nz, ny, nx = fpost.shape
     nodes = np.ascontiguousarray(nodes, dtype=np.int64)
     out = np.zeros((len(nodes), NV))
-    lib().or_step_nodes(_i64(nx), _i64(ny), _i64(nz), ctypes.c_double(tau), ctypes.c_int(int(project)), _p(fpost),
+    lib().or_step_nodes(_i64(nx), _i64(ny), _i64(nz), ctypes.c_double(tau), _kind(project), _p(fpost),
                         nodes.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _i64(len(nodes)), _p(out),
                         _threads(nthreads))
     return out
@@ -156,7 +165,7 @@ def init_fields(rho, u, theta, project=True, nthreads=None):
     theta = np.ascontiguousarray(theta, dtype=np.float64)
     _, nz, ny, nx = rho.shape
     f = np.zeros((2, NV, nz, ny, nx))
-    lib().or_init_fields(_i64(nx), _i64(ny), _i64(nz), _p(rho), _p(u), _p(theta), ctypes.c_int(int(project)), _p(f),
+    lib().or_init_fields(_i64(nx), _i64(ny), _i64(nz), _p(rho), _p(u), _p(theta), _kind(project), _p(f),
                          _threads(nthreads))
     return f
 

@@ -347,12 +347,25 @@ void or_moments(const double *f, double *rho, double *u, double *theta) {
 
 static double beta_of_tau(double tau) { return isinf(tau) ? 0.0 : 1.0 / (2.0 * tau + 1.0); }
 
-/* Discrete BGK collision f* = f + 2 beta (f^eq(rho(f), u(f), theta(f)) - f). */
+/* The equilibrium used by the update.  kind 0: Eq. (feqGenU3) as printed;
+ * 1: Eq. (feqGenU3) with the momentum projection; 2: the exact entropic
+ * equilibrium, Eq. (discreteentropiceq) (NaN if Newton fails). */
+static void equilibrium_of_kind(double rho, const double *u, double theta, int kind, double *feq) {
+    if (kind == 2) {
+        if (or_entropic_equilibrium(rho, u, theta, feq) < 0)
+            for (int i = 0; i < NV; ++i) feq[i] = NAN;
+    } else {
+        or_equilibrium(rho, u, theta, kind, feq);
+    }
+}
+
+/* Discrete BGK collision f* = f + 2 beta (f^eq(rho(f), u(f), theta(f)) - f),
+ * with the equilibrium of the given kind (see equilibrium_of_kind). */
 void or_collide(const double *f, double tau, int project, double *out) {
     init_lattice();
     double rho, u[3], theta, feq[NV];
     or_moments(f, &rho, u, &theta);
-    or_equilibrium(rho, u, theta, project, feq);
+    equilibrium_of_kind(rho, u, theta, project, feq);
     double b2 = 2.0 * beta_of_tau(tau);
     for (int i = 0; i < NV; ++i) out[i] = f[i] + b2 * (feq[i] - f[i]);
 }
@@ -465,7 +478,7 @@ void or_init_fields(int64_t nx, int64_t ny, int64_t nz, const double *rho, const
     for (int64_t q = 0; q < nn; ++q) {
         double uu[3] = {u[q], u[nn + q], u[2 * nn + q]};
         double feq[NV];
-        or_equilibrium(rho[q], uu, theta[q], project, feq);
+        equilibrium_of_kind(rho[q], uu, theta[q], project, feq);
         int64_t x = q % nx, r = q / nx;
         int64_t y = r % ny;
         r /= ny;

@@ -24,7 +24,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC", "-I", INCLUDE,
           "-I", CSRC]
 # Units whose kernels must stay free of FP64 instructions.
-NO_FP64 = {"lb_step_f32.cu"}
+NO_FP64 = {"lb_step_f32.cu", "lb_step_entropic.cu"}
 
 
 def nvcc() -> str:

@@ -187,7 +187,10 @@ lb_status lb_init(lb_ctx** out, lb_grid grid, int velocity_set, double theta0, d
     if ((int)precision < LB_F64 || (int)precision > LB_F32_S16B)
         return fail(nullptr, LB_ERR_ARG, "lb_init: unknown precision");
     if (!(tau > 0.0)) return fail(nullptr, LB_ERR_ARG, "lb_init: tau must be > 0 (or +inf)");
-    if (flags & ~(LB_FLAG_PAPER_LITERAL | LB_FLAG_STAGED)) return fail(nullptr, LB_ERR_ARG, "lb_init: unknown flag bits");
+    if (flags & ~(LB_FLAG_PAPER_LITERAL | LB_FLAG_STAGED | LB_FLAG_ENTROPIC))
+        return fail(nullptr, LB_ERR_ARG, "lb_init: unknown flag bits");
+    if ((flags & LB_FLAG_ENTROPIC) && (flags & LB_FLAG_PAPER_LITERAL))
+        return fail(nullptr, LB_ERR_ARG, "lb_init: LB_FLAG_ENTROPIC and LB_FLAG_PAPER_LITERAL exclude each other");
     const Lattice& L = lattice();
     if (theta0 > 0.0 && fabs(theta0 / L.theta0 - 1.0) > 1e-12)
         return fail(nullptr, LB_ERR_THETA0, "lb_init: theta0 differs from sum_i w_i c_ix^2 of the Table I weights");
@@ -200,7 +203,7 @@ lb_status lb_init(lb_ctx** out, lb_grid grid, int velocity_set, double theta0, d
     c->d.plane = grid.nx * grid.ny * grid.nz;
     c->d.rows = 2 * grid.ny * grid.nz;
     c->prec = (int)precision;
-    c->project = !(flags & LB_FLAG_PAPER_LITERAL);
+    c->eq = (flags & LB_FLAG_ENTROPIC) ? 2 : (flags & LB_FLAG_PAPER_LITERAL) ? 0 : 1;
     c->variant = (flags & LB_FLAG_STAGED) ? kKernelStaged : kKernelAuto;
     c->tau = tau;
     c->twobeta = isinf(tau) ? 0.0 : 2.0 / (2.0 * tau + 1.0);
@@ -266,11 +269,12 @@ lb_status lb_sync(lb_ctx* c) {
 
 int lb_step_variant(const lb_ctx* c) {
     if (!c) return -1;
+    if (c->eq == 2) return kKernelDirect1;  // the exact entropic equilibrium runs in k_step only
     return resolve_kernel(c->prec, c->d, c->variant);
 }
 
 lb_status lb_set_step_kernel(lb_ctx* c, int kernel) {
-    if (!c || kernel < LB_KERNEL_AUTO || kernel > LB_KERNEL_DIRECT2XA) return fail(c, LB_ERR_ARG, "lb_set_step_kernel: unknown kernel");
+    if (!c || kernel < LB_KERNEL_AUTO || kernel > LB_KERNEL_DIRECT2XL) return fail(c, LB_ERR_ARG, "lb_set_step_kernel: unknown kernel");
     c->variant = kernel;
     return LB_OK;
 }
@@ -286,13 +290,13 @@ lb_status lb_tune(lb_ctx* c, int reps, int* kernel_out, double* ms_out) {
     float best = 1e30f;
     int best_k = resolve_kernel(c->prec, c->d, kKernelAuto);
     // trial steps read buf[cur] and write buf[1 - cur] without flipping: the state is unchanged
-    for (int k = LB_KERNEL_DIRECT1; k <= LB_KERNEL_DIRECT2XA; ++k) {
+    for (int k = LB_KERNEL_DIRECT1; k <= LB_KERNEL_DIRECT2XL; ++k) {
         if (resolve_kernel(c->prec, c->d, k) != k) continue;
-        cudaError_t e = launch_step(c->prec, c->project, k, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc, c->twobeta,
+        cudaError_t e = launch_step(c->prec, c->eq, k, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc, c->twobeta,
                                     c->d_err, c->stream);
         if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
         for (int r = 0; r < reps && e == cudaSuccess; ++r)
-            e = launch_step(c->prec, c->project, k, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc, c->twobeta, c->d_err,
+            e = launch_step(c->prec, c->eq, k, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc, c->twobeta, c->d_err,
                             c->stream);
         if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -324,7 +328,7 @@ lb_status lb_set_fields(lb_ctx* c, const double* rho, const double* u, const dou
     const LaunchConsts& lc = lattice().lc;
     void* dst = c->buf[c->cur];
     if (on_device) {
-        CK(c, launch_init(c->prec, c->project, dst, c->d, lc, 0, n, rho, u, n, theta, c->d_err, c->stream));
+        CK(c, launch_init(c->prec, c->eq, dst, c->d, lc, 0, n, rho, u, n, theta, c->d_err, c->stream));
     } else {
         lb_status s = ensure_stage(c);
         if (s != LB_OK) return s;
@@ -339,7 +343,7 @@ lb_status lb_set_fields(lb_ctx* c, const double* rho, const double* u, const dou
             for (int k = 0; k < 3; ++k)
                 CK(c, cudaMemcpyAsync(su + k * cnt, u + k * n + q0, b, cudaMemcpyHostToDevice, c->stream));
             CK(c, cudaMemcpyAsync(st, theta + q0, b, cudaMemcpyHostToDevice, c->stream));
-            CK(c, launch_init(c->prec, c->project, dst, c->d, lc, q0, cnt, sr, su, cnt, st, c->d_err, c->stream));
+            CK(c, launch_init(c->prec, c->eq, dst, c->d, lc, q0, cnt, sr, su, cnt, st, c->d_err, c->stream));
         }
         CK(c, cudaStreamSynchronize(c->stream));
     }
@@ -352,7 +356,7 @@ lb_status lb_step(lb_ctx* c, int64_t n) {
     CK(c, cudaSetDevice(c->device));
     const LaunchConsts& lc = lattice().lc;
     for (int64_t t = 0; t < n; ++t) {
-        CK(c, launch_step(c->prec, c->project, c->variant, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc, c->twobeta,
+        CK(c, launch_step(c->prec, c->eq, c->variant, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc, c->twobeta,
                           c->d_err, c->stream));
         c->cur ^= 1;
         c->time += 1;

@@ -36,25 +36,28 @@ static cudaError_t dispatch(int prec, F&& f) {
 
 static unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-cudaError_t launch_step(int prec, bool project, int variant, const void* src, void* dst, const Dims& d,
+cudaError_t launch_step(int prec, int eq, int variant, const void* src, void* dst, const Dims& d,
                         const LaunchConsts& c, double twobeta, int* err, cudaStream_t st) {
-    if (prec == kF64) return launch_step_f64(project, src, dst, d, c, twobeta, err, st);
-    return launch_step_f32(prec, project, variant, src, dst, d, c, twobeta, err, st);
+    if (prec == kF64) return launch_step_f64(eq, src, dst, d, c, twobeta, err, st);
+    if (eq == 2) return launch_step_entropic(prec, src, dst, d, c, twobeta, err, st);
+    return launch_step_f32(prec, eq == 1, variant, src, dst, d, c, twobeta, err, st);
 }
 
-cudaError_t launch_init(int prec, bool project, void* dst, const Dims& d, const LaunchConsts& c, int64_t q0,
+cudaError_t launch_init(int prec, int eq, void* dst, const Dims& d, const LaunchConsts& c, int64_t q0,
                         int64_t count, const double* rho, const double* u, int64_t ustride, const double* theta,
                         int* err, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
     return dispatch(prec, [&](auto codec) {
         using C = decltype(codec);
         using T = typename C::raw_t;
-        if (project)
-            k_init<C, true><<<blocks_for(count, 256), 256, 0, st>>>(static_cast<T*>(dst), d, consts_for<C>(c), c.theta0,
-                                                                     q0, count, rho, u, ustride, theta, err);
+        const unsigned nb = blocks_for(count, 256);
+        T* o = static_cast<T*>(dst);
+        if (eq == 2)
+            k_init<C, 2><<<nb, 256, 0, st>>>(o, d, consts_for<C>(c), c.theta0, q0, count, rho, u, ustride, theta, err);
+        else if (eq == 1)
+            k_init<C, 1><<<nb, 256, 0, st>>>(o, d, consts_for<C>(c), c.theta0, q0, count, rho, u, ustride, theta, err);
         else
-            k_init<C, false><<<blocks_for(count, 256), 256, 0, st>>>(static_cast<T*>(dst), d, consts_for<C>(c),
-                                                                      c.theta0, q0, count, rho, u, ustride, theta, err);
+            k_init<C, 0><<<nb, 256, 0, st>>>(o, d, consts_for<C>(c), c.theta0, q0, count, rho, u, ustride, theta, err);
         return cudaGetLastError();
     });
 }

@@ -349,6 +349,8 @@ lb_status lb_batch_init(lb_batch** out, int nsims, const lb_grid* grids, const d
                         unsigned flags, void* cuda_stream) {
     if (!out || nsims < 1 || !grids || !tau) return bfail(nullptr, LB_ERR_ARG, "lb_batch_init: bad argument");
     *out = nullptr;
+    if (flags & LB_FLAG_ENTROPIC)
+        return bfail(nullptr, LB_ERR_ARG, "lb_batch_init: the exact entropic equilibrium is a single-grid mode");
     lb_batch* b = new lb_batch();
     b->n = nsims;
     b->prec = (int)precision;

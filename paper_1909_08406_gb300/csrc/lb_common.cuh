@@ -382,11 +382,163 @@ __device__ __forceinline__ void equilibrium_relax_g(const NodeState<typename Cod
     });
 }
 
-template <class Codec, bool PROJECT, class Sink>
+__device__ __forceinline__ double expm1_of(double x) { return expm1(x); }
+__device__ __forceinline__ float expm1_of(float x) { return expm1f(x); }
+
+// Exact entropic equilibrium (Eqs. (discreteentropiceq) and
+// (fivelagrangemultipliersystem)) and BGK relaxation of one node.
+//   f^eq_i = w_i rho exp(X_i),  X_i = l0 + l.c_i + l4 (c_i^2 - 3 theta_0),
+// with the five multipliers fixed by <f^eq, (1, c, c^2)> = (rho, rho u,
+// rho u^2 + 3 rho theta).  Divided by rho and written for the deviations this
+// is  sum_i w_i expm1(X_i) phi_i = t,  phi = (1, c, c^2 - 3 theta_0),
+// t = (0, u, u^2 + 3 theta_0 eta), which keeps full relative precision of the
+// small deviations in FP32.  Newton's method starts from the solution of the
+// linearised system (J = diag(1, theta_0, theta_0, theta_0, 6 theta_0^2) at
+// rest); once the residual is below `tol` one more step is taken (quadratic
+// convergence then leaves round-off), and `ok` is cleared if that does not
+// happen within MAXIT steps.  The working value passed on is x_i = tb h^eq_i
+// with h^eq_i = rho expm1(X_i) + (rho - 1).
+template <class Codec, class VGet, class Sink>
+__device__ __forceinline__ void entropic_relax(const NodeState<typename Codec::R>& st,
+                                               const Consts<typename Codec::KS>& K, typename Codec::R tb,
+                                               typename Codec::R omb, VGet&& vget, Sink&& sink, bool& ok) {
+    using R = typename Codec::R;
+    constexpr bool kDouble = sizeof(R) == 8;
+    constexpr int MAXIT = kDouble ? 20 : 12;
+    const R tol = kDouble ? R(1e-10) : R(3e-5);
+    const R th0 = K.theta0;
+    const R usq = st.ux * st.ux + st.uy * st.uy + st.uz * st.uz;
+    const R t4 = usq + R(3) * th0 * st.eta;
+    R l[5] = {R(0), st.ux / th0, st.uy / th0, st.uz / th0, t4 / (R(6) * th0 * th0)};
+    const R tgt[5] = {R(0), st.ux, st.uy, st.uz, t4};
+    bool conv = false;
+#pragma unroll 1
+    for (int it = 0; it < MAXIT; ++it) {
+        // residual F and Jacobian J (upper triangle, row-major) at l
+        R F[5] = {R(0), R(0), R(0), R(0), R(0)};
+        R J[15] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+        {
+            const R p4 = K.c2[0] - R(3) * th0;
+            const R em = expm1_of(l[0] + l[4] * p4);
+            const R w = K.w[0], ex = em + R(1);
+            F[0] += w * em;
+            F[4] += w * p4 * em;
+            J[0] += w * ex;
+            J[4] += w * p4 * ex;
+            J[14] += w * p4 * p4 * ex;
+        }
+        static_for<20>([&](auto KK) {
+            constexpr Vel c = vel(2 * KK + 1);
+            constexpr double cx = 0.5 * c.x, cy = 0.5 * c.y, cz = 0.5 * c.z;
+            const R w = K.w[c.shell], p4 = K.c2[c.shell] - R(3) * th0;
+            const R E = l[0] + l[4] * p4;
+            R O = R(0);
+            if constexpr (cx != 0) O += R(cx) * l[1];
+            if constexpr (cy != 0) O += R(cy) * l[2];
+            if constexpr (cz != 0) O += R(cz) * l[3];
+            const R ep = expm1_of(E + O), emn = expm1_of(E - O);
+            const R se = w * (ep + emn), de = w * (ep - emn);  // even / odd parts
+            const R sx = se + R(2) * w;                        // w (exp(E+O) + exp(E-O))
+            const R cc[3] = {R(cx), R(cy), R(cz)};
+            F[0] += se;
+            F[4] += p4 * se;
+            J[0] += sx;
+            J[4] += p4 * sx;
+            J[14] += p4 * p4 * sx;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                F[1 + a] += cc[a] * de;
+                J[1 + a] += cc[a] * de;          // (0, 1+a)
+                J[(a == 0 ? 8 : a == 1 ? 11 : 13)] += cc[a] * p4 * de;  // (1+a, 4)
+            }
+            // (1+a, 1+b), b >= a: 5 6 7 / 9 10 / 12
+            J[5] += cc[0] * cc[0] * sx;
+            J[6] += cc[0] * cc[1] * sx;
+            J[7] += cc[0] * cc[2] * sx;
+            J[9] += cc[1] * cc[1] * sx;
+            J[10] += cc[1] * cc[2] * sx;
+            J[12] += cc[2] * cc[2] * sx;
+        });
+        R res = R(0);
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            F[k] -= tgt[k];
+            res = fmax(res, fabs(F[k]));
+        }
+        conv = res <= tol;  // false for NaN
+        // solve J d = -F (symmetric positive definite: elimination without pivoting)
+        R A[5][5];
+        {
+            int q = 0;
+#pragma unroll
+            for (int r = 0; r < 5; ++r)
+#pragma unroll
+                for (int cix = r; cix < 5; ++cix) {
+                    A[r][cix] = J[q];
+                    A[cix][r] = J[q];
+                    ++q;
+                }
+        }
+        R b[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) b[k] = -F[k];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const R inv = R(1) / A[k][k];
+#pragma unroll
+            for (int r = k + 1; r < 5; ++r) {
+                const R f = A[r][k] * inv;
+#pragma unroll
+                for (int cix = k; cix < 5; ++cix) A[r][cix] -= f * A[k][cix];
+                b[r] -= f * b[k];
+            }
+        }
+#pragma unroll
+        for (int k = 4; k >= 0; --k) {
+            R sum = b[k];
+#pragma unroll
+            for (int cix = k + 1; cix < 5; ++cix) sum -= A[k][cix] * b[cix];
+            b[k] = sum / A[k][k];
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) l[k] += b[k];
+        if (conv) break;
+    }
+    if (!conv) ok = false;
+    // relaxation towards h^eq = rho expm1(X) + drho
+    {
+        const R em = expm1_of(l[0] + l[4] * (K.c2[0] - R(3) * th0));
+        sink(std::integral_constant<int, 0>{},
+             Codec::relax(vget(std::integral_constant<int, 0>{}), omb, tb * (st.rho * em + st.drho), K.w[0], tb));
+    }
+    static_for<20>([&](auto KK) {
+        constexpr int ip = 2 * KK + 1, im = 2 * KK + 2;
+        constexpr Vel c = vel(ip);
+        const R E = l[0] + l[4] * (K.c2[c.shell] - R(3) * th0);
+        R O = R(0);
+        if constexpr (c.x != 0) O += R(0.5 * c.x) * l[1];
+        if constexpr (c.y != 0) O += R(0.5 * c.y) * l[2];
+        if constexpr (c.z != 0) O += R(0.5 * c.z) * l[3];
+        sink(std::integral_constant<int, ip>{},
+             Codec::relax(vget(std::integral_constant<int, ip>{}), omb, tb * (st.rho * expm1_of(E + O) + st.drho),
+                          K.w[c.shell], tb));
+        sink(std::integral_constant<int, im>{},
+             Codec::relax(vget(std::integral_constant<int, im>{}), omb, tb * (st.rho * expm1_of(E - O) + st.drho),
+                          K.w[c.shell], tb));
+    });
+}
+
+// Equilibrium kinds: 0 = Eq. (feqGenU3) as printed, 1 = with the momentum
+// projection, 2 = the exact entropic equilibrium (clears `ok` if Newton fails).
+template <class Codec, int EQ, class Sink>
 __device__ __forceinline__ void equilibrium_relax(const NodeState<typename Codec::R>& st,
                                                   const Consts<typename Codec::KS>& K, typename Codec::R tb,
-                                                  typename Codec::R omb, const typename Codec::R (&v)[kQ], Sink&& sink) {
-    equilibrium_relax_g<Codec, PROJECT>(st, K, tb, omb, [&](auto I) { return v[I]; }, sink);
+                                                  typename Codec::R omb, const typename Codec::R (&v)[kQ], Sink&& sink,
+                                                  bool& ok) {
+    if constexpr (EQ == 2)
+        entropic_relax<Codec>(st, K, tb, omb, [&](auto I) { return v[I]; }, sink, ok);
+    else
+        equilibrium_relax_g<Codec, EQ == 1>(st, K, tb, omb, [&](auto I) { return v[I]; }, sink);
 }
 
 // Geometry of one population buffer.

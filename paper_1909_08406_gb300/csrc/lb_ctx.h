@@ -14,7 +14,7 @@ struct lb_ctx {
     lb_grid g;
     gblb::Dims d;
     int prec;
-    bool project;
+    int eq;  // equilibrium kind: 0 as printed, 1 with the momentum projection, 2 exact entropic
     int variant;
     double tau, twobeta;
     cudaStream_t stream;

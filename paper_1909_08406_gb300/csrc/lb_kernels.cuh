@@ -31,7 +31,7 @@ struct LoadCG {
 // the sub-lattice (shifts 0, +-1, +-2 cells); the bcc-1/2 links come from the
 // other sub-lattice: for A (s = 0) a component +1/2 reads cell r - 1 and -1/2
 // reads cell r; for B (s = 1) +1/2 reads cell r and -1/2 reads cell r + 1.
-template <class Codec, bool PROJECT, class Ld = LoadNC>
+template <class Codec, int EQ, class Ld = LoadNC>
 __device__ __forceinline__ void step_node(const typename Codec::raw_t* __restrict__ src,
                                           typename Codec::raw_t* __restrict__ dst, const Dims& d,
                                           const Consts<typename Codec::R>& K, typename Codec::R tb,
@@ -74,16 +74,18 @@ __device__ __forceinline__ void step_node(const typename Codec::raw_t* __restric
     static_for<kQ>([&](auto I) { dv[I] = Codec::dev(v[I], K.w[vel(I).shell] * inv_scale); });
     const NodeMoments<R> m = moments_from_dev(dv);
     const NodeState<R> st = state_from_moments(m, K);
-    if (!state_ok(st)) atomicOr(err, 1);
+    bool ok = state_ok(st);
 
     T* out = dst + (int64_t)s * kQ * d.plane + (int64_t)z * nxy + (int64_t)y * d.nx + x;
-    equilibrium_relax<Codec, PROJECT>(st, K, tb * R(Codec::kScale), R(1) - tb, v,
-                                      [&](auto I, R val) { out[(int64_t)I * d.plane] = Codec::to_raw(val); });
+    equilibrium_relax<Codec, EQ>(st, K, tb * R(Codec::kScale), R(1) - tb, v,
+                                 [&](auto I, R val) { out[(int64_t)I * d.plane] = Codec::to_raw(val); }, ok);
+    if (!ok) atomicOr(err, 1);
 }
 
 // Direct-load step kernel.  Grid: blockIdx.x = row (s, z, y),
-// blockIdx.y * blockDim.x + threadIdx.x = x.
-template <class Codec, bool PROJECT>
+// blockIdx.y * blockDim.x + threadIdx.x = x.  EQ: equilibrium kind (see
+// equilibrium_relax).
+template <class Codec, int EQ>
 __global__ void __launch_bounds__(kStepThreads) k_step(const typename Codec::raw_t* __restrict__ src,
                                                        typename Codec::raw_t* __restrict__ dst, Dims d,
                                                        Consts<typename Codec::R> K, typename Codec::R tb,
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(kStepThreads) k_step(const typename Codec::raw
     const int64_t zr = row / d.ny;
     const int z = (int)(zr % d.nz);
     const int s = (int)(zr / d.nz);
-    step_node<Codec, PROJECT>(src, dst, d, K, tb, err, s, z, y, x);
+    step_node<Codec, EQ>(src, dst, d, K, tb, err, s, z, y, x);
 }
 
 template <class Codec, bool PROJECT, class Ld>
@@ -263,47 +265,6 @@ __device__ __forceinline__ typename Codec::pair_t load_pair2x(const RowAddr2x<Co
     }
 }
 
-// Shared-memory slots of the asynchronous-copy pipeline (MODE 4 below): the
-// aligned pairs that population I's upwind pair is made of, one 32-bit slot
-// each -- two for a plane whose x shift is odd, and for every bcc-1/2 plane
-// (whose shift parity depends on the sub-lattice), else one.
-__host__ __device__ constexpr int x2_nslots(int I) {
-    return (vel(I).shell == 5 || ((vel(I).x / 2) & 1)) ? 2 : 1;
-}
-__host__ __device__ constexpr int x2_slot(int I) {
-    int k = 0;
-    for (int j = 0; j < I; ++j) k += x2_nslots(j);
-    return k;
-}
-constexpr int kX2Slots = x2_slot(kQ);  // 67
-constexpr int kX2Stages = 2;
-
-__device__ __forceinline__ void cp_async4(uint32_t saddr, const void* g) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-
-// x shift of population I's source for sub-lattice s (source x - dx).
-template <int I>
-__device__ __forceinline__ int x2_shift(int s) {
-    constexpr Vel c = vel(I);
-    if constexpr (c.shell == 5)
-        return c.x > 0 ? 1 - s : -s;  // delta = 1 - s for +1/2, -s for -1/2
-    else
-        return c.x / 2;
-}
-
-// Row pointer of population I's source row for the row described by `a`.
-template <class Codec, int I>
-__device__ __forceinline__ const typename Codec::raw_t* x2_row(const RowAddr2x<Codec>& a, uint32_t plane) {
-    constexpr Vel c = vel(I);
-    if constexpr (c.shell == 5)
-        return a.other + (size_t)I * plane + ((c.z > 0 ? a.hzp : a.hzm) + (c.y > 0 ? a.hyp : a.hym));
-    else
-        return a.same + (size_t)I * plane + (a.zo[c.z / 2 + 2] + a.yo[c.y / 2 + 2]);
-}
-
 // Prefetch into L2 the part of population I's source row that the nodes
 // [xa, xb) of the row (s, z, y) will read (x - 2 .. x + 2, not wrapped),
 // trimmed inward to whole 16-byte units of that row.
@@ -334,11 +295,8 @@ __device__ __forceinline__ void prefetch_row_l2(const typename Codec::raw_t* src
 // How a block of the x-pair kernel gets a row's upwind values:
 // MODE 0: direct loads at the start of the row.
 // MODE 2: as MODE 0, plus an L2 bulk prefetch of the next row's source rows
-//         (one per population, by threads 0..40) at the start of the current row.
-// MODE 4: each thread copies the aligned pairs of the next row into its own
-//         shared-memory slots with cp.async (no registers held, no block
-//         barrier: a thread reads only what it copied) while it computes the
-//         current row; cp.async.wait_group orders the two.
+//         (one per population, by threads 0..40) at the start of the current
+//         row, so that the next row's loads hit in L2.
 template <class Codec, bool PROJECT, int MINB, int MODE>
 __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Codec::raw_t* __restrict__ src,
                                                          typename Codec::raw_t* __restrict__ dst, Dims d,
@@ -366,54 +324,9 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Co
     // aligned pair starts: x - 2, x, x + 2 (periodic; nx even keeps them even)
     const uint32_t xm = (uint32_t)wrap(x - 2, d.nx), x0 = (uint32_t)x, xq = (uint32_t)wrap(x + 2, d.nx);
 
-    extern __shared__ uint32_t x2_smem[];
-    // slot k of stage g of this thread: word (g * kX2Slots + k) * blockDim.x + threadIdx.x
-    auto slot_word = [&](int g, int k) { return (g * kX2Slots + k) * (int)blockDim.x + (int)threadIdx.x; };
-    auto issue_row = [&](int g, const RowAddr2x<Codec>& a) {
-        static_for<kQ>([&](auto I) {
-            constexpr int k = x2_slot(I);
-            const T* p = x2_row<Codec, I>(a, plane);
-            const int dx = x2_shift<I>(a.s);
-            const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(&x2_smem[slot_word(g, k)]);
-            const uint32_t s1 = s0 + 4u * blockDim.x;
-            if (dx == 2) {
-                cp_async4(s0, p + xm);
-            } else if (dx == 1) {
-                cp_async4(s0, p + xm);
-                cp_async4(s1, p + x0);
-            } else if (dx == 0) {
-                cp_async4(s0, p + x0);
-            } else if (dx == -1) {
-                cp_async4(s0, p + x0);
-                cp_async4(s1, p + xq);
-            } else {
-                cp_async4(s0, p + xq);
-            }
-        });
-    };
-    auto read_pair = [&](int g, auto I, int s_) -> P {
-        constexpr int k = x2_slot(I);
-        const int dx = x2_shift<I>(s_);
-        auto word = [&](int kk) {
-            P v;
-            const uint32_t r = x2_smem[slot_word(g, kk)];
-            memcpy(&v, &r, 4);
-            return v;
-        };
-        if (dx == 1 || dx == -1) return Codec::straddle(word(k), word(k + 1));
-        return word(k);
-    };
-
     P pv[kQ];
     auto vget = [&](auto I) { return F2(Codec::unpack2(pv[I])); };
     constexpr float inv_scale = (float)(1.0 / Codec::kScale);
-    int stage = 0;
-    if constexpr (MODE == 4) {
-        RowAddr2x<Codec> a;
-        a.set(src, d, s, z, y);
-        issue_row(0, a);
-        cp_async_commit();
-    }
 
     for (uint32_t r = r0; r < r1; ++r) {
         // the next row, in (s, z, y) order
@@ -435,16 +348,7 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Co
                 continue;
             }
         }
-        if constexpr (MODE == 4) {
-            if (more) {
-                RowAddr2x<Codec> an;
-                an.set(src, d, sn, zn, yn);
-                issue_row(stage ^ 1, an);
-            }
-            cp_async_commit();
-            cp_async_wait1();  // every group but the newest: this row's copies have landed
-            static_for<kQ>([&](auto I) { pv[I] = read_pair(stage, I, s); });
-        } else {
+        {
             RowAddr2x<Codec> a;
             a.set(src, d, s, z, y);
             static_for<kQ>([&](auto I) { pv[I] = load_pair2x<Codec, I>(a, plane, xm, x0, xq); });
@@ -461,14 +365,13 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Co
         s = sn;
         z = zn;
         y = yn;
-        stage ^= 1;
     }
 }
 
 // Populations = equilibrium of the given float64 fields, for nodes
 // q in [q0, q0 + count), q = s * plane + (z * ny + y) * nx + x.  Field
 // pointers are indexed by q - q0 (u component c at c * ustride + q - q0).
-template <class Codec, bool PROJECT>
+template <class Codec, int EQ>
 __global__ void __launch_bounds__(256) k_init(typename Codec::raw_t* __restrict__ dst, Dims d, Consts<typename Codec::R> K,
                                               double theta0, int64_t q0, int64_t count, const double* __restrict__ rho,
                                               const double* __restrict__ u, int64_t ustride,
@@ -486,13 +389,14 @@ __global__ void __launch_bounds__(256) k_init(typename Codec::raw_t* __restrict_
     st.uy = (R)u[ustride + k];
     st.uz = (R)u[2 * ustride + k];
     st.eta = (R)(theta[k] / theta0 - 1.0);
-    if (!state_ok(st)) atomicOr(err, 1);
+    bool ok = state_ok(st);
     R zero[kQ];
 #pragma unroll
     for (int i = 0; i < kQ; ++i) zero[i] = R(0);
     typename Codec::raw_t* out = dst + (int64_t)s * kQ * d.plane + node;
-    equilibrium_relax<Codec, PROJECT>(st, K, R(Codec::kScale), R(0), zero,
-                                      [&](auto I, R val) { out[(int64_t)I * d.plane] = Codec::to_raw(val); });
+    equilibrium_relax<Codec, EQ>(st, K, R(Codec::kScale), R(0), zero,
+                                 [&](auto I, R val) { out[(int64_t)I * d.plane] = Codec::to_raw(val); }, ok);
+    if (!ok) atomicOr(err, 1);
 }
 
 template <class Codec>

@@ -31,8 +31,7 @@ enum StepKernel {
     kKernelStaged = 3,
     kKernelWarpSpec = 4,
     kKernelDirect2X = 5,
-    kKernelDirect2XL = 6,
-    kKernelDirect2XA = 7
+    kKernelDirect2XL = 6
 };
 
 // The kernel a request resolves to for this precision and grid (falls back where one does not apply).
@@ -44,11 +43,11 @@ int tma_tile_width(int prec, const Dims& d);
 size_t storage_bytes(int prec);
 
 // One fused pull step src -> dst over the whole grid.
-cudaError_t launch_step(int prec, bool project, int variant, const void* src, void* dst, const Dims& d,
+cudaError_t launch_step(int prec, int eq, int variant, const void* src, void* dst, const Dims& d,
                         const LaunchConsts& c, double twobeta, int* err, cudaStream_t st);
 
 // Equilibrium of float64 fields for nodes [q0, q0 + count).
-cudaError_t launch_init(int prec, bool project, void* dst, const Dims& d, const LaunchConsts& c, int64_t q0,
+cudaError_t launch_init(int prec, int eq, void* dst, const Dims& d, const LaunchConsts& c, int64_t q0,
                         int64_t count, const double* rho, const double* u, int64_t ustride, const double* theta,
                         int* err, cudaStream_t st);
 
@@ -67,10 +66,13 @@ cudaError_t launch_from_f64(int prec, const double* f, void* dst, const Dims& d,
                             int64_t count, cudaStream_t st);
 
 // Per-precision step launchers (defined in the per-precision translation units).
-cudaError_t launch_step_f64(bool project, const void* src, void* dst, const Dims& d, const LaunchConsts& c,
+cudaError_t launch_step_f64(int eq, const void* src, void* dst, const Dims& d, const LaunchConsts& c,
                             double twobeta, int* err, cudaStream_t st);
 cudaError_t launch_step_f32(int prec, bool project, int variant, const void* src, void* dst, const Dims& d,
                             const LaunchConsts& c, double twobeta, int* err, cudaStream_t st);
+// The exact-entropic-equilibrium update (FP32 arithmetic, any storage but FP64), k_step only.
+cudaError_t launch_step_entropic(int prec, const void* src, void* dst, const Dims& d, const LaunchConsts& c,
+                                 double twobeta, int* err, cudaStream_t st);
 
 inline dim3 step_grid(const Dims& d, int threads) {
     return dim3((unsigned)d.rows, (unsigned)((d.nx + threads - 1) / threads), 1);

@@ -49,21 +49,7 @@ static cudaError_t run_direct2x(const void* src, void* dst, const Dims& d, const
         const int chunks = (half + th - 1) / th;
         const int64_t blocks = ((d.rows + rpb - 1) / rpb) * chunks;
         auto kern = k_step2x<Codec, P, MINB, MODE>;
-        size_t smem = 0;
-        if constexpr (MODE == 4) {
-            smem = (size_t)kX2Stages * kX2Slots * 4 * th;
-            static int opted_in_device = -1;  // the attribute is per device
-            int dev = 0;
-            cudaError_t e = cudaGetDevice(&dev);
-            if (e != cudaSuccess) return e;
-            if (opted_in_device != dev) {
-                e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(kX2Stages * kX2Slots * 4 * kStepThreads));
-                if (e != cudaSuccess) return e;
-                opted_in_device = dev;
-            }
-        }
-        kern<<<(unsigned)blocks, th, smem, st>>>(static_cast<const T*>(src), static_cast<T*>(dst), d, c.kf,
+        kern<<<(unsigned)blocks, th, 0, st>>>(static_cast<const T*>(src), static_cast<T*>(dst), d, c.kf,
                                                  (float)twobeta, err, chunks, rpb);
         return cudaGetLastError();
     }
@@ -174,7 +160,6 @@ int resolve_kernel(int prec, const Dims& d, int kernel) {
     switch (kernel) {
         case kKernelDirect2X:
         case kKernelDirect2XL:
-        case kKernelDirect2XA:
             return (storage_bytes(prec) == 2 && d.nx % 2 == 0 && d.plane < ((int64_t)1 << 32))
                        ? kernel
                        : resolve_kernel(prec, d, kKernelAuto);
@@ -185,7 +170,9 @@ int resolve_kernel(int prec, const Dims& d, int kernel) {
         case kKernelDirect2:
         case kKernelDirect2R: return two_rows ? kernel : kKernelDirect1;
         case kKernelDirect1: return kKernelDirect1;
-        default: return two_rows ? kKernelDirect2 : kKernelDirect1;
+        default:
+            if (storage_bytes(prec) == 2 && d.nx % 2 == 0 && d.plane < ((int64_t)1 << 32)) return kKernelDirect2XL;
+            return two_rows ? kKernelDirect2 : kKernelDirect1;
     }
 }
 
@@ -199,8 +186,8 @@ static cudaError_t step_codec(int prec, int kernel, const void* src, void* dst, 
             return run_tma<Codec, P, typename TmaShape<Codec, 128>::Cfg>(src, dst, d, c, twobeta, err, st);
         case kKernelWarpSpec: return run_ws<Codec, P, typename WsShape<Codec>::Cfg>(src, dst, d, c, twobeta, err, st);
         case kKernelDirect2X: return run_direct2x<Codec, P, 3, 0>(src, dst, d, c, twobeta, err, st, 1);
-        case kKernelDirect2XL: return run_direct2x<Codec, P, 3, 2>(src, dst, d, c, twobeta, err, st, 4);
-        case kKernelDirect2XA: return run_direct2x<Codec, P, 3, 4>(src, dst, d, c, twobeta, err, st, 8);
+        case kKernelDirect2XL: return run_direct2x<Codec, P, 3, 2>(src, dst, d, c, twobeta, err, st, 2);
+
         case kKernelDirect2: return run_direct2<Codec, P, 3>(src, dst, d, c, twobeta, err, st);
         case kKernelDirect2R: return run_direct2<Codec, P, 4>(src, dst, d, c, twobeta, err, st);
         default: return run_direct1<Codec, P>(src, dst, d, c, twobeta, err, st);

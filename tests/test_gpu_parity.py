@@ -64,8 +64,7 @@ def _run_gpu(shape, tau, prec, fields, steps, flags=0, kernel=lb.LB_KERNEL_AUTO)
 # storage and nx even (nx = 2: the x-2 and x+2 pairs coincide; 262: a ragged second block of
 # pairs); FP64 always runs DIRECT1.
 KERNELS = [lb.LB_KERNEL_DIRECT1, lb.LB_KERNEL_DIRECT2, lb.LB_KERNEL_DIRECT2R, lb.LB_KERNEL_STAGED,
-           lb.LB_KERNEL_WARPSPEC, lb.LB_KERNEL_DIRECT2X, lb.LB_KERNEL_DIRECT2XL,
-           lb.LB_KERNEL_DIRECT2XA]
+           lb.LB_KERNEL_WARPSPEC, lb.LB_KERNEL_DIRECT2X, lb.LB_KERNEL_DIRECT2XL]
 STREAM_SHAPES = [(4, 4, 4), (3, 5, 7), (1, 2, 5), (133, 4, 3), (128, 2, 3), (256, 2, 1), (384, 2, 3),
                  (2, 3, 2), (262, 2, 3)]
 
@@ -242,13 +241,16 @@ def test_unstable_state_is_reported():
 def test_step_kernel_selection_and_fallbacks():
     K = lb
     cases = [((256, 2, 2), "f16", K.LB_KERNEL_STAGED, K.LB_KERNEL_STAGED),
-             ((256, 2, 2), "f16", K.LB_KERNEL_AUTO, K.LB_KERNEL_DIRECT2),
+             ((256, 2, 2), "f16", K.LB_KERNEL_AUTO, K.LB_KERNEL_DIRECT2XL),
+             ((256, 2, 2), "f32", K.LB_KERNEL_AUTO, K.LB_KERNEL_DIRECT2),
+             ((255, 2, 2), "bf16", K.LB_KERNEL_AUTO, K.LB_KERNEL_DIRECT2),  # odd nx
              ((256, 3, 2), "f32", K.LB_KERNEL_DIRECT2, K.LB_KERNEL_DIRECT1),   # odd ny
              ((130, 2, 2), "f32", K.LB_KERNEL_STAGED, K.LB_KERNEL_DIRECT2),    # nx not a multiple of 128
              ((256, 2, 2), "f64", K.LB_KERNEL_STAGED, K.LB_KERNEL_DIRECT1),
              ((256, 2, 2), "bf16", K.LB_KERNEL_DIRECT2R, K.LB_KERNEL_DIRECT2R),
              ((130, 3, 2), "f16", K.LB_KERNEL_DIRECT2X, K.LB_KERNEL_DIRECT2X),
              ((133, 2, 2), "bf16", K.LB_KERNEL_DIRECT2X, K.LB_KERNEL_DIRECT2),  # odd nx
+             ((256, 2, 2), "f16", K.LB_KERNEL_DIRECT2XL, K.LB_KERNEL_DIRECT2XL),
              ((256, 2, 2), "f32", K.LB_KERNEL_DIRECT2X, K.LB_KERNEL_DIRECT2)]   # 32-bit storage
     for shape, prec, req, expect in cases:
         ctx = lb.lb_init(shape, 0.5, prec)

@@ -182,3 +182,18 @@ def test_second_moment_at_reference_temperature(lat, theta0):
     f = oracle.equilibrium(1.2, u, theta0, True)
     P = (f[:, None, None] * c[:, :, None] * c[:, None, :]).sum(0)
     assert np.allclose(P, 1.2 * np.outer(u, u) + 1.2 * theta0 * np.eye(3), rtol=0, atol=1e-15)
+
+
+def test_entropic_collision_conserves_and_fixes_equilibrium():
+    """With the exact entropic equilibrium the collision keeps rho, rho u and the energy to
+    round-off for states far from rest, and leaves an entropic equilibrium unchanged."""
+    rng = np.random.default_rng(41)
+    c, w, _ = oracle.velocities()
+    for _ in range(5):
+        f = w * (1.0 + 0.3 * rng.uniform(-1, 1, size=41))
+        out = oracle.collide(f, 0.4, project="entropic")
+        m0, m1 = oracle.moments(f), oracle.moments(out)
+        for a, b in zip(m0, m1):
+            assert np.allclose(a, b, rtol=0, atol=1e-14)
+    feq = oracle.entropic_equilibrium(1.05, np.array([0.1, -0.05, 0.02]), 1.1 * oracle.theta0())
+    assert np.allclose(oracle.collide(feq, 0.4, project="entropic"), feq, rtol=1e-13, atol=0)
