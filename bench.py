@@ -76,15 +76,16 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def ncu_traffic(precision, n):
-    """dram read+write bytes per launch of the step kernel from the committed ncu
-    summary, if it was taken on the current kernel sources; else None."""
+def ncu_traffic(precision, kernel_id, n):
+    """dram read+write bytes per launch of the step kernel that ran, from the committed ncu
+    summary (keyed "<precision>/<kernel id>"), if it was taken on the current kernel sources;
+    else None."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as fh:
         d = json.load(fh)
-    e = d.get(precision)
+    e = d.get(f"{precision}/{kernel_id}")
     if not e or e.get("kernel_hash") != kernel_hash():
         return None
     # scale a smaller capture to this grid by the node count (traffic ~ nodes)
@@ -393,7 +394,7 @@ def main():
         return
     r = results[args.precision]
     peak, peak_kind = measured_peaks()
-    traffic = ncu_traffic(args.precision, n)
+    traffic = ncu_traffic(args.precision, r["kernel_id"], n)
     line = {
         "metric": "MLUPS", "value": r["mlups"], "unit": "MLUPS", "n_gpus": world, "steps": r["steps"],
         "warmup": r["warmup"], "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
