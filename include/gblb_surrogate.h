@@ -48,6 +48,24 @@ typedef struct {
 int sg_conv3d_fwd(sg_shape s, int cin, int cout, const void *x, const void *w, const float *bias, int act,
                   int res_in, const void *add, float *z_out, void *y, void *stream);
 
+/* Kernel of the two convolution entry points above:
+ *   SG_CONV_TCGEN05  (default) 5th-generation tensor cores: tcgen05.mma with
+ *                    the FP32 accumulator in tensor memory, M = 128 voxels,
+ *                    N = cout, K = 16 per instruction; persistent CTAs with the
+ *                    weights resident in shared memory.  A wait for the tensor
+ *                    cores that runs out of time (~1 s) ends the kernel and
+ *                    is reported by sg_status.
+ *   SG_CONV_MMA_SYNC warp-level mma.sync.m16n8k16.
+ * Returns the previous setting, or -1 for an unknown value.  Process-wide. */
+#define SG_CONV_MMA_SYNC 0
+#define SG_CONV_TCGEN05 1
+int sg_set_conv_impl(int impl);
+
+/* Synchronises `stream` and returns 0, or -6 if a tensor-core wait of a
+ * convolution ran out of time since the last call (the flag is then
+ * cleared), or -3 for a CUDA error. */
+int sg_status(void *stream);
+
 /* Input-gradient form of the convolution: y = conv(x, w) + add, with y and
  * add (may be NULL) FP32 [voxels][cout]. */
 int sg_conv3d_fwd_f32(sg_shape s, int cin, int cout, const void *x, const void *w, const float *add, float *y,

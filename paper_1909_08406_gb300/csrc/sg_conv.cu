@@ -1,9 +1,10 @@
 // Surrogate kernels: periodic 3x3x3 convolution as an implicit GEMM on the
-// BF16 tensor cores (mma.sync m16n8k16, FP32 accumulate), its weight
-// gradient, and the small element-wise / reduction kernels of training and
-// rollout.  C ABI in include/gblb_surrogate.h.
+// BF16 tensor cores -- tcgen05 with the accumulator in tensor memory (the
+// default), or warp-level mma.sync m16n8k16 -- with FP32 accumulation, its
+// weight gradient, and the small element-wise / reduction kernels of training
+// and rollout.  C ABI in include/gblb_surrogate.h.
 //
-// Forward tile: one CTA owns RT = 4 consecutive rows (64 voxels each) of one
+// mma.sync forward tile: one CTA owns RT = 4 consecutive rows (64 voxels each) of one
 // z-plane of one batch item: M = 256 voxels, N = cout, K = 27 * cin.  The
 // CTA stages the periodic halo (3 planes x 6 rows x 66 voxels x cin) and all
 // weights in shared memory with 16-byte row padding (conflict-free ldmatrix);
@@ -443,9 +444,290 @@ __global__ void k_unpack(sg_shape s, int item, const bf16* __restrict__ x, doubl
     th[q] = theta0 * (1.0 + (double)(acc[4] * inv) * s2);
 }
 
+// ---------------------------------------------------------------------------
+// Forward convolution on the 5th-generation tensor cores (tcgen05, TMEM).
+//
+// Implicit GEMM per tile of M = 128 output voxels (two 64-voxel rows of one
+// z-plane): D[128][cout] (FP32, in tensor memory) = sum over the 27 taps and
+// the cin/16 K-slices of A_tap[128][16] x B_tap[16][cout], one
+// tcgen05.mma.kind::f16 (BF16 in, FP32 accumulate, M=128, N=cout, K=16) each,
+// issued by one thread.  Operands sit in shared memory in the canonical
+// no-swizzle K-major layout: 8 x 16-byte "core matrices", stride 128 B along
+// M (or N) and LBO along K.  The halo (3 planes x 4 rows x 64 voxels) is kept
+// in three copies shifted by dx = -1, 0, +1 in x (periodic), with the 64
+// voxels of a row unpadded, so that the 128 rows of A for any tap are
+// uniformly 16 bytes apart and a tap is only a different descriptor start
+// address: + (dz+1) planes + (dy+1) rows in the copy of its dx.  The weights
+// of all 27 taps stay resident in shared memory; a persistent CTA walks its
+// tiles, refills the halo, issues the MMAs, waits on an mbarrier that
+// tcgen05.commit arrives on (bounded wait), and runs the fused epilogue from
+// tensor memory (tcgen05.ld, one voxel per thread).
+// ---------------------------------------------------------------------------
+__device__ int g_sg_status;  // bit 0: a tensor-core wait ran out of time
+
+template <int CIN, int COUT>
+struct TcCfg {
+    static constexpr int K8 = CIN / 8;                 // 16-byte channel groups
+    static constexpr int HZ = 3, HY = 4;               // halo planes / rows of a 2-row tile
+    static constexpr int PLANE = HZ * HY * kW * 16;    // one channel group of one shifted copy
+    static constexpr int COPY = K8 * PLANE;
+    static constexpr int A_BYTES = 3 * COPY;
+    static constexpr int WTAP = K8 * COUT * 16;
+    static constexpr int B_BYTES = 27 * WTAP;
+    static constexpr int SMEM = A_BYTES + B_BYTES;
+    static constexpr int THREADS = 128;
+    // instruction descriptor: F32 accumulate, BF16 A and B, both K-major, N = COUT, M = 128
+    static constexpr uint32_t IDESC =
+        (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(COUT >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    static_assert(COUT % 16 == 0 && COUT <= 32, "N = cout: 16 or 32");
+    static_assert(SMEM <= 232448, "shared memory");
+};
+
+// Shared-memory matrix descriptor (no swizzle): start address, leading (K)
+// and stride (M/N) byte offsets, descriptor version 1.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity, long long limit) {
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.b32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > limit) return false;
+    }
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128, 1) k_conv_fwd_tc(sg_shape s, const bf16* __restrict__ x,
+                                                        const bf16* __restrict__ w, const float* __restrict__ bias,
+                                                        Epi epi, void* y, long long wait_limit) {
+    using C = TcCfg<CIN, COUT>;
+    extern __shared__ __align__(128) unsigned char sm_tc[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_holder;
+    unsigned char* A = sm_tc;
+    unsigned char* Bw = sm_tc + C::A_BYTES;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // weights of all taps: B[tap][k8][co][8 channels] <- w[co][tap][k8 * 8 ..]
+    for (int i = tid; i < 27 * C::K8 * COUT; i += C::THREADS) {
+        const int co = i % COUT, r = i / COUT;
+        const int k8 = r % C::K8, tap = r / C::K8;
+        *reinterpret_cast<uint4*>(Bw + (size_t)((tap * C::K8 + k8) * COUT + co) * 16) =
+            *reinterpret_cast<const uint4*>(w + ((size_t)co * 27 + tap) * CIN + k8 * 8);
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
+                     "r"(32));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_holder;
+    const uint32_t a_s = smem_u32(A), b_s = smem_u32(Bw), bar_s = smem_u32(&bar);
+
+    const int tiles_y = s.ny / 2;
+    const int64_t ntiles = (int64_t)s.batch * s.nz * tiles_y;
+    uint32_t phase = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int yt = (int)(tile % tiles_y);
+        const int64_t t2 = tile / tiles_y;
+        const int z = (int)(t2 % s.nz);
+        const int b = (int)(t2 / s.nz);
+        const int y0 = 2 * yt;
+        // halo: copy dx holds in[x + dx] at position x, so source voxel xs lands at xs - dx
+        for (int i = tid; i < C::HZ * C::HY * kW * C::K8; i += C::THREADS) {
+            const int k8 = i % C::K8, v = i / C::K8;
+            const int xs = v % kW, r = v / kW;
+            const int yh = r % C::HY, zh = r / C::HY;
+            const int zz = wrapi(z + zh - 1, s.nz), yy = wrapi(y0 + yh - 1, s.ny);
+            const uint4 val =
+                *reinterpret_cast<const uint4*>(x + ((((int64_t)b * s.nz + zz) * s.ny + yy) * kW + xs) * CIN + k8 * 8);
+            const size_t row = (size_t)k8 * C::PLANE + (size_t)((zh * C::HY + yh) * kW) * 16;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const int xd = wrapi(xs - (d - 1), kW);
+                *reinterpret_cast<uint4*>(A + (size_t)d * C::COPY + row + (size_t)xd * 16) = val;
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+            for (int tap = 0; tap < 27; ++tap) {
+                const int dz = tap / 9, dy = (tap / 3) % 3, dxi = tap % 3;  // each + 1
+                const uint32_t a0 = a_s + dxi * C::COPY + ((dz * C::HY + dy) * kW) * 16;
+                const uint32_t b0 = b_s + tap * C::WTAP;
+#pragma unroll
+                for (int kk = 0; kk < CIN / 16; ++kk) {
+                    const uint64_t ad = umma_desc(a0 + 2 * kk * C::PLANE, C::PLANE, 128);
+                    const uint64_t bd = umma_desc(b0 + 2 * kk * COUT * 16, COUT * 16, 128);
+                    tc_mma(tmem, ad, bd, C::IDESC, (tap | kk) != 0);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_s)
+                         : "memory");
+        }
+        const bool ok = tc_wait(bar_s, phase, wait_limit);
+        phase ^= 1;
+        if (__syncthreads_or(!ok)) {
+            // give the MMAs in flight a second bounded chance to finish before tensor memory is freed
+            if (tid == 0) {
+                atomicOr(&g_sg_status, 1);
+                tc_wait(bar_s, phase ^ 1, wait_limit);
+            }
+            __syncthreads();
+            break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+        // epilogue: thread = voxel m = 32 warp + lane (tensor-memory lane m), all cout channels
+        const int m = 32 * warp + lane;
+        const int yl = m >> 6, xx = m & 63;
+        const int64_t v = (((int64_t)b * s.nz + z) * s.ny + (y0 + yl)) * kW + xx;
+#pragma unroll
+        for (int c0 = 0; c0 < COUT; c0 += 16) {
+            float acc[16];
+            tc_ld16(tmem + ((uint32_t)(32 * warp) << 16) + c0, acc);
+            float o[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float zj = acc[j] + (bias ? bias[c0 + j] : 0.f);
+                acc[j] = zj;
+                o[j] = epi.act == SG_ACT_GELU ? gelu(zj) : zj;
+            }
+            if (epi.z_out) {
+                float4* zo = reinterpret_cast<float4*>(epi.z_out + v * COUT + c0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) zo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+            }
+            if (epi.res_in && CIN == COUT) {
+                // centre voxel of the tile from the unshifted copy (dx = 0): channels c0 .. c0 + 15
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int k8 = c0 / 8 + h;
+                    const uint4 raw = *reinterpret_cast<const uint4*>(
+                        A + (size_t)C::COPY + (size_t)k8 * C::PLANE + (size_t)((1 * C::HY + yl + 1) * kW + xx) * 16);
+                    const __nv_bfloat162* p = reinterpret_cast<const __nv_bfloat162*>(&raw);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        o[8 * h + 2 * q] += __bfloat162float(p[q].x);
+                        o[8 * h + 2 * q + 1] += __bfloat162float(p[q].y);
+                    }
+                }
+            }
+            if (epi.add) {
+                if (epi.add_f32) {
+                    const float4* ad = reinterpret_cast<const float4*>(static_cast<const float*>(epi.add) + v * COUT + c0);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 r = ad[q];
+                        o[4 * q] += r.x;
+                        o[4 * q + 1] += r.y;
+                        o[4 * q + 2] += r.z;
+                        o[4 * q + 3] += r.w;
+                    }
+                } else {
+                    const uint4* ad = reinterpret_cast<const uint4*>(static_cast<const bf16*>(epi.add) + v * COUT + c0);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const uint4 raw = ad[h];
+                        const __nv_bfloat162* p = reinterpret_cast<const __nv_bfloat162*>(&raw);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            o[8 * h + 2 * q] += __bfloat162float(p[q].x);
+                            o[8 * h + 2 * q + 1] += __bfloat162float(p[q].y);
+                        }
+                    }
+                }
+            }
+            if (epi.y_f32) {
+                float4* yo = reinterpret_cast<float4*>(static_cast<float*>(y) + v * COUT + c0);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) yo[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
+            } else {
+                uint4 pk[2];
+                __nv_bfloat162* p = reinterpret_cast<__nv_bfloat162*>(pk);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) p[q] = __floats2bfloat162_rn(o[2 * q], o[2 * q + 1]);
+                uint4* yo = reinterpret_cast<uint4*>(static_cast<bf16*>(y) + v * COUT + c0);
+                yo[0] = pk[0];
+                yo[1] = pk[1];
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();  // halo and accumulator free for the next tile
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32));
+}
+
+static int g_fwd_impl = SG_CONV_TCGEN05;  // forward convolution kernel (sg_set_conv_impl)
+
+template <int CIN, int COUT>
+static int launch_fwd_tc(sg_shape s, const void* x, const void* w, const float* bias, Epi epi, void* y,
+                         cudaStream_t st) {
+    using C = TcCfg<CIN, COUT>;
+    static int configured = -1, grid_max = 0;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -3;
+    if (configured != dev) {
+        if (cudaFuncSetAttribute(k_conv_fwd_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
+            cudaSuccess)
+            return -3;
+        int per_sm = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_fwd_tc<CIN, COUT>, C::THREADS, C::SMEM) !=
+                cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1)
+            return -3;
+        grid_max = per_sm * sms;
+        configured = dev;
+    }
+    const int64_t tiles = (int64_t)s.batch * s.nz * (s.ny / 2);
+    const int grid = (int)(tiles < grid_max ? tiles : grid_max);
+    const long long wait_limit = 2000000000LL;  // ~1 s of SM clock per tile
+    k_conv_fwd_tc<CIN, COUT><<<grid, C::THREADS, C::SMEM, st>>>(s, static_cast<const bf16*>(x),
+                                                               static_cast<const bf16*>(w), bias, epi, y, wait_limit);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
 template <int CIN, int COUT>
 static int launch_fwd(sg_shape s, const void* x, const void* w, const float* bias, Epi epi, void* y,
                       cudaStream_t st) {
+    if (g_fwd_impl == SG_CONV_TCGEN05) return launch_fwd_tc<CIN, COUT>(s, x, w, bias, epi, y, st);
     constexpr int smem = HaloCfg<CIN>::BYTES + WCfg<CIN, COUT>::BYTES;
     static int configured = -1;
     int dev = 0;
@@ -516,6 +798,25 @@ int sg_conv3d_fwd_f32(sg_shape s, int cin, int cout, const void* x, const void* 
     if (cin == 32 && cout == 16) return launch_fwd<32, 16>(s, x, w, nullptr, e, y, st);
     if (cin == 16 && cout == 16) return launch_fwd<16, 16>(s, x, w, nullptr, e, y, st);
     return -1;
+}
+
+int sg_set_conv_impl(int impl) {
+    if (impl != SG_CONV_MMA_SYNC && impl != SG_CONV_TCGEN05) return -1;
+    const int prev = g_fwd_impl;
+    g_fwd_impl = impl;
+    return prev;
+}
+
+int sg_status(void* stream) {
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return -3;
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_sg_status, sizeof(int)) != cudaSuccess) return -3;
+    if (v) {
+        const int zero = 0;
+        if (cudaMemcpyToSymbol(g_sg_status, &zero, sizeof(int)) != cudaSuccess) return -3;
+        return -6;
+    }
+    return 0;
 }
 
 int sg_act_backward(int64_t n, int act, const float* dy, const float* z, void* dz, void* stream) {

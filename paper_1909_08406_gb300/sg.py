@@ -20,6 +20,7 @@ class SgShape(ctypes.Structure):
 
 
 ACT_NONE, ACT_GELU = 0, 1
+CONV_MMA_SYNC, CONV_TCGEN05 = 0, 1
 
 
 def _L():
@@ -41,6 +42,8 @@ def _L():
                         ctypes.c_int, vp],
             "sg_pack_fields": [SgShape, ctypes.c_int, vp, vp, vp, ctypes.c_double, vp, vp, vp],
             "sg_unpack_fields": [SgShape, ctypes.c_int, vp, ctypes.c_double, vp, vp, vp, vp, vp],
+            "sg_set_conv_impl": [ctypes.c_int],
+            "sg_status": [vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -61,6 +64,20 @@ def _stream():
 def _ok(rc, name):
     if rc != 0:
         raise RuntimeError(f"{name} failed with status {rc}")
+
+
+def set_conv_impl(impl):
+    """Select the forward-convolution kernel (CONV_TCGEN05, the default, or CONV_MMA_SYNC);
+    returns the previous one."""
+    prev = _L().sg_set_conv_impl(int(impl))
+    if prev < 0:
+        raise ValueError(f"unknown convolution kernel {impl}")
+    return prev
+
+
+def status():
+    """Synchronise the current stream; raise if a tensor-core wait of a convolution ran out of time."""
+    _ok(_L().sg_status(_stream()), "sg_status")
 
 
 def shape_of(t):

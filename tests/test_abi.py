@@ -1,6 +1,6 @@
 """C ABI checks that need no GPU: the library loads, exports every entry point
-declared in include/gblb.h, reports the paper's velocity set, and rejects bad
-arguments before touching the device."""
+declared in include/*.h (lb_* and sg_*), reports the paper's velocity set, and
+rejects bad arguments before touching the device."""
 import ctypes
 import os
 import re
@@ -21,7 +21,7 @@ def _declared_symbols():
         text = open(os.path.join(ROOT, "include", hdr)).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         text = re.sub(r"//[^\n]*", "", text)
-        for m in re.finditer(r"\b(lb_\w+)\s*\(", text):
+        for m in re.finditer(r"\b((?:lb|sg)_\w+)\s*\(", text):
             names.add(m.group(1))
     return sorted(names)
 
@@ -35,7 +35,7 @@ def L():
 
 def test_library_exports_every_declared_symbol(L):
     names = _declared_symbols()
-    assert "lb_init" in names and "lb_step" in names
+    assert "lb_init" in names and "lb_step" in names and "sg_conv3d_fwd" in names and "sg_set_conv_impl" in names
     missing = [n for n in names if not hasattr(L, n)]
     assert not missing, missing
 
@@ -79,3 +79,11 @@ def test_null_context_is_rejected(L):
     assert L.lb_step(None, ctypes.c_int64(1)) == -1
     assert L.lb_sync(None) == -1
     assert L.lb_destroy(None) == 0
+
+
+def test_conv_impl_switch(L):
+    from paper_1909_08406_gb300 import sg
+    prev = sg.set_conv_impl(sg.CONV_MMA_SYNC)
+    assert sg.set_conv_impl(prev) == sg.CONV_MMA_SYNC
+    with pytest.raises(ValueError):
+        sg.set_conv_impl(7)

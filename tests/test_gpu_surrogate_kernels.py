@@ -22,9 +22,17 @@ def _rand(shape, g, scale=1.0):
     return (scale * torch.randn(shape, generator=g, dtype=torch.float32)).to(torch.bfloat16)
 
 
+@pytest.fixture(params=[sg.CONV_TCGEN05, sg.CONV_MMA_SYNC], ids=["tcgen05", "mma_sync"])
+def impl(request):
+    prev = sg.set_conv_impl(request.param)
+    yield request.param
+    sg.set_conv_impl(prev)
+
+
+# (1, 16, 64, 64): 512 tiles of the tcgen05 kernel, more than its persistent grid
 @pytest.mark.parametrize("cin,cout", [(16, 32), (32, 32), (32, 16), (16, 16)])
-@pytest.mark.parametrize("shape", [(1, 4, 8, 64), (2, 3, 4, 64)])
-def test_conv_forward_matches_oracle(cin, cout, shape):
+@pytest.mark.parametrize("shape", [(1, 4, 8, 64), (2, 3, 4, 64), (1, 16, 64, 64)])
+def test_conv_forward_matches_oracle(cin, cout, shape, impl):
     g = torch.Generator().manual_seed(cin + cout + shape[0])
     x = _rand(shape + (cin,), g)
     w = _rand((cout, 27, cin), g, 1 / math.sqrt(27 * cin))
@@ -38,16 +46,17 @@ def test_conv_forward_matches_oracle(cin, cout, shape):
     assert torch.all((z.cpu().to(F64) - zr).abs() <= 1e-5 * absum + 1e-7)
     yr = so.gelu(zr) + (x.to(F64) if cin == cout else 0)
     assert torch.allclose(y.cpu().to(F64), yr, rtol=2 ** -7, atol=1e-6 * (1 + absum.max().item()))
+    sg.status()
 
 
-def test_conv_forward_f32_with_add():
+def test_conv_forward_f32_with_add(impl):
     g = torch.Generator().manual_seed(3)
     shape = (1, 2, 4, 64)
     x = _rand(shape + (32,), g)
     w = _rand((16, 27, 32), g, 0.05)
     add = torch.randn(shape + (16,), generator=g, dtype=torch.float32)
     y = sg.conv3d_fwd_f32(x.cuda(), w.cuda(), add=add.cuda())
-    torch.cuda.synchronize()
+    sg.status()
     ref = so.conv3d_periodic(x.to(F64), w.to(F64)) + add.to(F64)
     assert torch.allclose(y.cpu().to(F64), ref, rtol=1e-5, atol=1e-5)
 
@@ -73,7 +82,7 @@ def test_weight_and_bias_gradient_matches_oracle(cin, cout):
 
 
 @pytest.mark.parametrize("cin,cout", [(32, 32), (32, 16)])
-def test_input_gradient_is_conv_with_transposed_weights(cin, cout):
+def test_input_gradient_is_conv_with_transposed_weights(cin, cout, impl):
     g = torch.Generator().manual_seed(20 + cout)
     shape = (1, 4, 4, 64)
     x = _rand(shape + (cin,), g)
