@@ -559,48 +559,70 @@ __global__ void __launch_bounds__(128, 1) k_conv_fwd_tc(sg_shape s, const bf16* 
 
     const int tiles_y = s.ny / 2;
     const int64_t ntiles = (int64_t)s.batch * s.nz * tiles_y;
-    uint32_t phase = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int yt = (int)(tile % tiles_y);
-        const int64_t t2 = tile / tiles_y;
-        const int z = (int)(t2 % s.nz);
-        const int b = (int)(t2 / s.nz);
-        const int y0 = 2 * yt;
-        // halo: copy dx holds in[x + dx] at position x, so source voxel xs lands at xs - dx
+    struct Tile {
+        int b, z, y0;
+    };
+    auto tile_of = [&](int64_t t) {
+        const int yt = (int)(t % tiles_y);
+        const int64_t t2 = t / tiles_y;
+        return Tile{(int)(t2 / s.nz), (int)(t2 % s.nz), 2 * yt};
+    };
+    // halo: copy dx holds in[x + dx] at position x, so source voxel xs lands at xs - dx.
+    // Asynchronous 16-byte copies (the second and third read of a chunk hit L1), so all of a
+    // thread's loads are in flight at once; completed by cp.async.wait_group.
+    auto fill = [&](const Tile& T) {
         for (int i = tid; i < C::HZ * C::HY * kW * C::K8; i += C::THREADS) {
             const int k8 = i % C::K8, v = i / C::K8;
             const int xs = v % kW, r = v / kW;
             const int yh = r % C::HY, zh = r / C::HY;
-            const int zz = wrapi(z + zh - 1, s.nz), yy = wrapi(y0 + yh - 1, s.ny);
-            const uint4 val =
-                *reinterpret_cast<const uint4*>(x + ((((int64_t)b * s.nz + zz) * s.ny + yy) * kW + xs) * CIN + k8 * 8);
-            const size_t row = (size_t)k8 * C::PLANE + (size_t)((zh * C::HY + yh) * kW) * 16;
+            const int zz = wrapi(T.z + zh - 1, s.nz), yy = wrapi(T.y0 + yh - 1, s.ny);
+            const bf16* src = x + ((((int64_t)T.b * s.nz + zz) * s.ny + yy) * kW + xs) * CIN + k8 * 8;
+            const uint32_t row = a_s + (uint32_t)(k8 * C::PLANE + (zh * C::HY + yh) * kW * 16);
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const int xd = wrapi(xs - (d - 1), kW);
-                *reinterpret_cast<uint4*>(A + (size_t)d * C::COPY + row + (size_t)xd * 16) = val;
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(row + (uint32_t)(d * C::COPY + xd * 16)),
+                             "l"(src)
+                             : "memory");
             }
         }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    // 27 taps x cin/16 K-slices into the accumulator, then a commit to the mbarrier (one thread)
+    auto issue = [&]() {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+        for (int tap = 0; tap < 27; ++tap) {
+            const int dz = tap / 9, dy = (tap / 3) % 3, dxi = tap % 3;  // each + 1
+            const uint32_t a0 = a_s + dxi * C::COPY + ((dz * C::HY + dy) * kW) * 16;
+            const uint32_t b0 = b_s + tap * C::WTAP;
+#pragma unroll
+            for (int kk = 0; kk < CIN / 16; ++kk) {
+                const uint64_t ad = umma_desc(a0 + 2 * kk * C::PLANE, C::PLANE, 128);
+                const uint64_t bd = umma_desc(b0 + 2 * kk * COUT * 16, COUT * 16, 128);
+                tc_mma(tmem, ad, bd, C::IDESC, (tap | kk) != 0);
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_s)
+                     : "memory");
+    };
+    // operands of the tile are in shared memory: make them visible to the tensor cores
+    auto operands_ready = [&]() {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll 1
-            for (int tap = 0; tap < 27; ++tap) {
-                const int dz = tap / 9, dy = (tap / 3) % 3, dxi = tap % 3;  // each + 1
-                const uint32_t a0 = a_s + dxi * C::COPY + ((dz * C::HY + dy) * kW) * 16;
-                const uint32_t b0 = b_s + tap * C::WTAP;
-#pragma unroll
-                for (int kk = 0; kk < CIN / 16; ++kk) {
-                    const uint64_t ad = umma_desc(a0 + 2 * kk * C::PLANE, C::PLANE, 128);
-                    const uint64_t bd = umma_desc(b0 + 2 * kk * COUT * 16, COUT * 16, 128);
-                    tc_mma(tmem, ad, bd, C::IDESC, (tap | kk) != 0);
-                }
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_s)
-                         : "memory");
-        }
+    };
+
+    uint32_t phase = 0;
+    int64_t tile = blockIdx.x;
+    if (tile < ntiles) {
+        fill(tile_of(tile));
+        operands_ready();
+        if (tid == 0) issue();
+    }
+    for (; tile < ntiles; tile += gridDim.x) {
+        const Tile T = tile_of(tile);
         const bool ok = tc_wait(bar_s, phase, wait_limit);
         phase ^= 1;
         if (__syncthreads_or(!ok)) {
@@ -613,11 +635,15 @@ __global__ void __launch_bounds__(128, 1) k_conv_fwd_tc(sg_shape s, const bf16* 
             break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // the tensor cores are done with the halo: start filling it for the next tile while
+        // this tile's epilogue runs
+        const int64_t next = tile + gridDim.x;
+        if (next < ntiles) fill(tile_of(next));
 
         // epilogue: thread = voxel m = 32 warp + lane (tensor-memory lane m), all cout channels
         const int m = 32 * warp + lane;
         const int yl = m >> 6, xx = m & 63;
-        const int64_t v = (((int64_t)b * s.nz + z) * s.ny + (y0 + yl)) * kW + xx;
+        const int64_t v = (((int64_t)T.b * s.nz + T.z) * s.ny + (T.y0 + yl)) * kW + xx;
 #pragma unroll
         for (int c0 = 0; c0 < COUT; c0 += 16) {
             float acc[16];
@@ -635,12 +661,11 @@ __global__ void __launch_bounds__(128, 1) k_conv_fwd_tc(sg_shape s, const bf16* 
                 for (int q = 0; q < 4; ++q) zo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
             }
             if (epi.res_in && CIN == COUT) {
-                // centre voxel of the tile from the unshifted copy (dx = 0): channels c0 .. c0 + 15
+                // the voxel's own input channels c0 .. c0 + 15 (the halo is being refilled)
+                const uint4* rp = reinterpret_cast<const uint4*>(x + v * CIN + c0);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const int k8 = c0 / 8 + h;
-                    const uint4 raw = *reinterpret_cast<const uint4*>(
-                        A + (size_t)C::COPY + (size_t)k8 * C::PLANE + (size_t)((1 * C::HY + yl + 1) * kW + xx) * 16);
+                    const uint4 raw = rp[h];
                     const __nv_bfloat162* p = reinterpret_cast<const __nv_bfloat162*>(&raw);
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
@@ -688,9 +713,15 @@ __global__ void __launch_bounds__(128, 1) k_conv_fwd_tc(sg_shape s, const bf16* 
                 yo[1] = pk[1];
             }
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();  // halo and accumulator free for the next tile
+        // next tile: its halo has landed and the accumulator has been read out
+        if (next < ntiles) {
+            operands_ready();
+            if (tid == 0) issue();
+        }
     }
+    // every warp has finished reading tensor memory before it is freed
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32));
 }
