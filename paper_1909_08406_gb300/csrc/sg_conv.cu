@@ -475,7 +475,8 @@ struct TcCfg {
     static constexpr int WTAP = K8 * COUT * 16;
     static constexpr int B_BYTES = 27 * WTAP;
     static constexpr int SMEM = A_BYTES + B_BYTES;
-    static constexpr int THREADS = 128;
+    static constexpr int THREADS = 256;  // 8 warps: two per tensor-memory lane quarter in the epilogue
+    static constexpr int CPW = 16;  // accumulator columns read out per warp (warps 4-7 idle when cout = 16)
     // instruction descriptor: F32 accumulate, BF16 A and B, both K-major, N = COUT, M = 128
     static constexpr uint32_t IDESC =
         (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(COUT >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
@@ -524,7 +525,7 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
 }
 
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(128, 1) k_conv_fwd_tc(sg_shape s, const bf16* __restrict__ x,
+__global__ void __launch_bounds__(256, 1) k_conv_fwd_tc(sg_shape s, const bf16* __restrict__ x,
                                                         const bf16* __restrict__ w, const float* __restrict__ bias,
                                                         Epi epi, void* y, long long wait_limit) {
     using C = TcCfg<CIN, COUT>;
@@ -571,9 +572,10 @@ __global__ void __launch_bounds__(128, 1) k_conv_fwd_tc(sg_shape s, const bf16* 
     // Asynchronous 16-byte copies (the second and third read of a chunk hit L1), so all of a
     // thread's loads are in flight at once; completed by cp.async.wait_group.
     auto fill = [&](const Tile& T) {
+        // x fastest: a warp writes 32 consecutive 16-byte chunks of one row (no bank conflicts)
         for (int i = tid; i < C::HZ * C::HY * kW * C::K8; i += C::THREADS) {
-            const int k8 = i % C::K8, v = i / C::K8;
-            const int xs = v % kW, r = v / kW;
+            const int xs = i % kW, q = i / kW;
+            const int k8 = q % C::K8, r = q / C::K8;
             const int yh = r % C::HY, zh = r / C::HY;
             const int zz = wrapi(T.z + zh - 1, s.nz), yy = wrapi(T.y0 + yh - 1, s.ny);
             const bf16* src = x + ((((int64_t)T.b * s.nz + zz) * s.ny + yy) * kW + xs) * CIN + k8 * 8;
@@ -640,14 +642,16 @@ __global__ void __launch_bounds__(128, 1) k_conv_fwd_tc(sg_shape s, const bf16* 
         const int64_t next = tile + gridDim.x;
         if (next < ntiles) fill(tile_of(next));
 
-        // epilogue: thread = voxel m = 32 warp + lane (tensor-memory lane m), all cout channels
-        const int m = 32 * warp + lane;
+        // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (voxel m = lane index) and
+        // accumulator columns 16 (w / 4) .. + 15 (none for w >= 4 when cout = 16)
+        const int quarter = warp & 3;
+        const int m = 32 * quarter + lane;
         const int yl = m >> 6, xx = m & 63;
         const int64_t v = (((int64_t)T.b * s.nz + T.z) * s.ny + (T.y0 + yl)) * kW + xx;
 #pragma unroll
-        for (int c0 = 0; c0 < COUT; c0 += 16) {
+        for (int c0 = (warp >> 2) * C::CPW; c0 < COUT && c0 < (warp >> 2) * C::CPW + C::CPW; c0 += 16) {
             float acc[16];
-            tc_ld16(tmem + ((uint32_t)(32 * warp) << 16) + c0, acc);
+            tc_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + c0, acc);
             float o[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
@@ -726,7 +730,7 @@ __global__ void __launch_bounds__(128, 1) k_conv_fwd_tc(sg_shape s, const bf16* 
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32));
 }
 
-static int g_fwd_impl = SG_CONV_TCGEN05;  // forward convolution kernel (sg_set_conv_impl)
+static int g_fwd_impl = SG_CONV_MMA_SYNC;  // forward convolution kernel (sg_set_conv_impl)
 
 template <int CIN, int COUT>
 static int launch_fwd_tc(sg_shape s, const void* x, const void* w, const float* bias, Epi epi, void* y,
