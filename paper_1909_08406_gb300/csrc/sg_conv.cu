@@ -9,6 +9,8 @@
 // CTA stages the periodic halo (3 planes x 6 rows x 66 voxels x cin) and all
 // weights in shared memory with 16-byte row padding (conflict-free ldmatrix);
 // each of the 16 warps computes 16 voxels x cout.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -458,31 +460,9 @@ __global__ void k_unpack(sg_shape s, int item, const bf16* __restrict__ x, doubl
 // voxels of a row unpadded, so that the 128 rows of A for any tap are
 // uniformly 16 bytes apart and a tap is only a different descriptor start
 // address: + (dz+1) planes + (dy+1) rows in the copy of its dx.  The weights
-// of all 27 taps stay resident in shared memory; a persistent CTA walks its
-// tiles, refills the halo, issues the MMAs, waits on an mbarrier that
-// tcgen05.commit arrives on (bounded wait), and runs the fused epilogue from
-// tensor memory (tcgen05.ld, one voxel per thread).
+// of all 27 taps stay resident in shared memory.
 // ---------------------------------------------------------------------------
 __device__ int g_sg_status;  // bit 0: a tensor-core wait ran out of time
-
-template <int CIN, int COUT>
-struct TcCfg {
-    static constexpr int K8 = CIN / 8;                 // 16-byte channel groups
-    static constexpr int HZ = 3, HY = 4;               // halo planes / rows of a 2-row tile
-    static constexpr int PLANE = HZ * HY * kW * 16;    // one channel group of one shifted copy
-    static constexpr int COPY = K8 * PLANE;
-    static constexpr int A_BYTES = 3 * COPY;
-    static constexpr int WTAP = K8 * COUT * 16;
-    static constexpr int B_BYTES = 27 * WTAP;
-    static constexpr int SMEM = A_BYTES + B_BYTES;
-    static constexpr int THREADS = 256;  // 8 warps: two per tensor-memory lane quarter in the epilogue
-    static constexpr int CPW = 16;  // accumulator columns read out per warp (warps 4-7 idle when cout = 16)
-    // instruction descriptor: F32 accumulate, BF16 A and B, both K-major, N = COUT, M = 128
-    static constexpr uint32_t IDESC =
-        (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(COUT >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-    static_assert(COUT % 16 == 0 && COUT <= 32, "N = cout: 16 or 32");
-    static_assert(SMEM <= 232448, "shared memory");
-};
 
 // Shared-memory matrix descriptor (no swizzle): start address, leading (K)
 // and stride (M/N) byte offsets, descriptor version 1.
@@ -524,19 +504,90 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined forward convolution on tcgen05 with TMA operand loads.
+//
+// Same implicit GEMM as above (tile = 128 voxels of two rows, one
+// tcgen05.mma M=128 x N=cout x K=16 per tap and 16-channel slice), with the
+// work of a tile split over warp roles that run concurrently:
+//   warp 0 (one thread)  TMA producer: per (tile, 16-channel slice) it loads
+//                        the 3 x 4 halo rows of the slice in the three
+//                        x-shifted copies, 72 boxes of 8 channels x 64 voxels
+//                        (cp.async.bulk.tensor.5d with a tensor map over the
+//                        NDHWC activations).  A box shifted by -1 / +1 in x
+//                        starts or ends one voxel outside the row; the tensor
+//                        map fills that voxel with zeros.
+//   warp 1               fixes the periodic wrap: writes the one voxel per
+//                        shifted row that the box left as zero (loaded from
+//                        global memory before the box lands), then marks the
+//                        stage full.
+//   warp 2 (one thread)  issues the 27 MMAs of a stage into one of two
+//                        accumulators in tensor memory; tcgen05.commit frees the
+//                        stage (and, after the last slice, fills the accumulator).
+//   warps 4-7            epilogue: read the accumulator out of tensor memory
+//                        (tcgen05.ld), free it, and apply bias, activation,
+//                        residual and add while the next tile's MMAs run.
+// Two shared-memory stages (one 16-channel slice of a tile each) and two
+// accumulators decouple the roles; all hand-offs are mbarriers and every wait
+// is bounded (on expiry the kernel sets the status flag and the roles wind
+// down after waiting, bounded, for their own asynchronous work).
+// ---------------------------------------------------------------------------
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(256, 1) k_conv_fwd_tc(sg_shape s, const bf16* __restrict__ x,
-                                                        const bf16* __restrict__ w, const float* __restrict__ bias,
-                                                        Epi epi, void* y, long long wait_limit) {
-    using C = TcCfg<CIN, COUT>;
-    extern __shared__ __align__(128) unsigned char sm_tc[];
-    __shared__ __align__(8) uint64_t bar;
+struct TcpCfg {
+    static constexpr int K8 = CIN / 8;
+    static constexpr int HY = 4;
+    static constexpr int ROWS = 3 * HY;                // halo rows: 3 planes x 4 rows
+    static constexpr int PLANE = ROWS * kW * 16;       // one 8-channel group of one shifted copy
+    static constexpr int SLICES = CIN / 16;            // 16-channel K slices per tile
+    static constexpr int STAGE = 3 * 2 * PLANE;        // 3 copies x 2 channel groups
+    static constexpr int A_BYTES = 2 * STAGE;
+    static constexpr int WTAP = K8 * COUT * 16;
+    static constexpr int B_BYTES = 27 * WTAP;
+    static constexpr int SMEM = A_BYTES + B_BYTES + 1024;  // + slack to align the base to 1 KB
+    static constexpr int THREADS = 256;
+    static constexpr uint32_t TX_BYTES = 3 * 2 * ROWS * 8 * kW * 2;  // bytes landed per stage
+    static constexpr uint32_t IDESC =
+        (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(COUT >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    static_assert(COUT % 16 == 0 && COUT <= 32, "N = cout: 16 or 32");
+    static_assert(CIN % 16 == 0, "cin: multiple of 16");
+    static_assert(SMEM <= 232448, "shared memory");
+};
+
+__device__ __forceinline__ void tp_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tp_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tp_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tp_tma5(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3, int c4,
+                                        uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+        "%6}], [%7];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+        : "memory");
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256, 1)
+    k_conv_fwd_tcp(const __grid_constant__ CUtensorMap xmap, sg_shape s, const bf16* __restrict__ x,
+                   const bf16* __restrict__ w, const float* __restrict__ bias, Epi epi, void* y, long long wait_limit) {
+    using C = TcpCfg<CIN, COUT>;
+    extern __shared__ __align__(1024) unsigned char sm_tcp[];
+    __shared__ __align__(8) uint64_t bars[11];  // full_tma[2] full[2] empty[2] acc_full[2] acc_empty[2] drain
     __shared__ uint32_t tmem_holder;
-    unsigned char* A = sm_tc;
-    unsigned char* Bw = sm_tc + C::A_BYTES;
+    const uint32_t base = (smem_u32(sm_tcp) + 1023u) & ~1023u;
+    unsigned char* smem = sm_tcp + (base - smem_u32(sm_tcp));
+    const uint32_t a_s = base, b_s = base + C::A_BYTES;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    auto bar = [&](int k) { return smem_u32(&bars[k]); };
+    const int FT = 0, FU = 2, EM = 4, AF = 6, AE = 8, DR = 10;
 
     // weights of all taps: B[tap][k8][co][8 channels] <- w[co][tap][k8 * 8 ..]
+    unsigned char* Bw = smem + C::A_BYTES;
     for (int i = tid; i < 27 * C::K8 * COUT; i += C::THREADS) {
         const int co = i % COUT, r = i / COUT;
         const int k8 = r % C::K8, tap = r / C::K8;
@@ -545,18 +596,19 @@ __global__ void __launch_bounds__(256, 1) k_conv_fwd_tc(sg_shape s, const bf16* 
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
-                     "r"(32));
+                     "r"(64));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar)), "r"(1));
+        for (int k = 0; k < 11; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(k)), "r"(k == AE || k == AE + 1 ? 4 : 1));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_holder;
-    const uint32_t a_s = smem_u32(A), b_s = smem_u32(Bw), bar_s = smem_u32(&bar);
 
     const int tiles_y = s.ny / 2;
     const int64_t ntiles = (int64_t)s.batch * s.nz * tiles_y;
@@ -568,194 +620,268 @@ __global__ void __launch_bounds__(256, 1) k_conv_fwd_tc(sg_shape s, const bf16* 
         const int64_t t2 = t / tiles_y;
         return Tile{(int)(t2 / s.nz), (int)(t2 % s.nz), 2 * yt};
     };
-    // halo: copy dx holds in[x + dx] at position x, so source voxel xs lands at xs - dx.
-    // Asynchronous 16-byte copies (the second and third read of a chunk hit L1), so all of a
-    // thread's loads are in flight at once; completed by cp.async.wait_group.
-    auto fill = [&](const Tile& T) {
-        // x fastest: a warp writes 32 consecutive 16-byte chunks of one row (no bank conflicts)
-        for (int i = tid; i < C::HZ * C::HY * kW * C::K8; i += C::THREADS) {
-            const int xs = i % kW, q = i / kW;
-            const int k8 = q % C::K8, r = q / C::K8;
-            const int yh = r % C::HY, zh = r / C::HY;
-            const int zz = wrapi(T.z + zh - 1, s.nz), yy = wrapi(T.y0 + yh - 1, s.ny);
-            const bf16* src = x + ((((int64_t)T.b * s.nz + zz) * s.ny + yy) * kW + xs) * CIN + k8 * 8;
-            const uint32_t row = a_s + (uint32_t)(k8 * C::PLANE + (zh * C::HY + yh) * kW * 16);
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const int xd = wrapi(xs - (d - 1), kW);
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(row + (uint32_t)(d * C::COPY + xd * 16)),
-                             "l"(src)
-                             : "memory");
+    auto fail = [&]() { atomicOr(&g_sg_status, 1); };
+
+    if (warp == 0 && lane == 0) {
+        // ---- TMA producer ----
+        int armed_stage = -1;
+        uint32_t armed_parity = 0;
+        for (int64_t i = 0;; ++i) {
+            const int64_t tile = blockIdx.x + (i / C::SLICES) * gridDim.x;
+            if (tile >= ntiles) break;
+            const int st = (int)(i & 1);
+            const uint32_t n = (uint32_t)(i >> 1);
+            if (!tc_wait(bar(EM + st), (n & 1) ^ 1, wait_limit)) {
+                fail();
+                break;
             }
+            tp_expect_tx(bar(FT + st), C::TX_BYTES);
+            armed_stage = st;
+            armed_parity = n & 1;
+            const Tile T = tile_of(tile);
+            const int j = (int)(i % C::SLICES);
+            const uint32_t sbase = a_s + st * C::STAGE;
+            for (int d = 0; d < 3; ++d)
+                for (int g = 0; g < 2; ++g)
+                    for (int r = 0; r < C::ROWS; ++r) {
+                        const int zz = wrapi(T.z + r / C::HY - 1, s.nz), yy = wrapi(T.y0 + r % C::HY - 1, s.ny);
+                        tp_tma5(sbase + (uint32_t)((d * 2 + g) * C::PLANE + r * kW * 16), &xmap, (2 * j + g) * 8, d - 1,
+                                yy, zz, T.b, bar(FT + st));
+                    }
         }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-    // 27 taps x cin/16 K-slices into the accumulator, then a commit to the mbarrier (one thread)
-    auto issue = [&]() {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // the CTA must not exit with boxes still landing
+        if (armed_stage >= 0 && !tc_wait(bar(FT + armed_stage), armed_parity, wait_limit)) fail();
+    } else if (warp == 1) {
+        // ---- periodic-wrap fixer: copy 0 position 0 <- in[63], copy 2 position 63 <- in[0] ----
+        for (int64_t i = 0;; ++i) {
+            const int64_t tile = blockIdx.x + (i / C::SLICES) * gridDim.x;
+            if (tile >= ntiles) break;
+            const int st = (int)(i & 1);
+            const uint32_t n = (uint32_t)(i >> 1);
+            const Tile T = tile_of(tile);
+            const int j = (int)(i % C::SLICES);
+            uint4 val[2];
+            uint32_t dst[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int c = lane + 32 * h;  // 48 chunks: side (2) x group (2) x row (12)
+                const int cc = c < 48 ? c : 0;
+                const int side = cc / 24, g = (cc / 12) % 2, r = cc % 12;
+                const int zz = wrapi(T.z + r / C::HY - 1, s.nz), yy = wrapi(T.y0 + r % C::HY - 1, s.ny);
+                const int xs = side ? 0 : kW - 1;
+                val[h] = *reinterpret_cast<const uint4*>(
+                    x + ((((int64_t)T.b * s.nz + zz) * s.ny + yy) * kW + xs) * CIN + (2 * j + g) * 8);
+                dst[h] = a_s + st * C::STAGE + (uint32_t)(((side ? 2 : 0) * 2 + g) * C::PLANE + r * kW * 16 +
+                                                          (side ? kW - 1 : 0) * 16);
+            }
+            // one decision for the whole warp (the lanes wait independently)
+            if (!__all_sync(0xffffffffu, tc_wait(bar(FT + st), n & 1, wait_limit))) {
+                if (lane == 0) fail();
+                break;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                if (lane + 32 * h < 48)
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst[h]), "r"(val[h].x), "r"(val[h].y),
+                                 "r"(val[h].z), "r"(val[h].w)
+                                 : "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) tp_arrive(bar(FU + st));
+        }
+    } else if (warp == 2 && lane == 0) {
+        // ---- MMA issuer ----
+        for (int64_t i = 0;; ++i) {
+            const int64_t tile = blockIdx.x + (i / C::SLICES) * gridDim.x;
+            if (tile >= ntiles) break;
+            const int st = (int)(i & 1);
+            const uint32_t n = (uint32_t)(i >> 1);
+            const int j = (int)(i % C::SLICES);
+            const int64_t t = i / C::SLICES;
+            const int acc = (int)(t & 1);
+            const uint32_t q = (uint32_t)(t >> 1);
+            if (j == 0 && !tc_wait(bar(AE + acc), (q & 1) ^ 1, wait_limit)) {
+                fail();
+                break;
+            }
+            if (!tc_wait(bar(FU + st), n & 1, wait_limit)) {
+                fail();
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sbase = a_s + st * C::STAGE;
+            const uint32_t d_tmem = tmem + (uint32_t)(acc * 32);
 #pragma unroll 1
-        for (int tap = 0; tap < 27; ++tap) {
-            const int dz = tap / 9, dy = (tap / 3) % 3, dxi = tap % 3;  // each + 1
-            const uint32_t a0 = a_s + dxi * C::COPY + ((dz * C::HY + dy) * kW) * 16;
-            const uint32_t b0 = b_s + tap * C::WTAP;
-#pragma unroll
-            for (int kk = 0; kk < CIN / 16; ++kk) {
-                const uint64_t ad = umma_desc(a0 + 2 * kk * C::PLANE, C::PLANE, 128);
-                const uint64_t bd = umma_desc(b0 + 2 * kk * COUT * 16, COUT * 16, 128);
-                tc_mma(tmem, ad, bd, C::IDESC, (tap | kk) != 0);
+            for (int tap = 0; tap < 27; ++tap) {
+                const int dz = tap / 9, dy = (tap / 3) % 3, dxi = tap % 3;  // each + 1
+                const uint64_t ad = umma_desc(sbase + (uint32_t)(dxi * 2 * C::PLANE + (dz * C::HY + dy) * kW * 16),
+                                              C::PLANE, 128);
+                const uint64_t bd = umma_desc(b_s + (uint32_t)(tap * C::WTAP + 2 * j * COUT * 16), COUT * 16, 128);
+                tc_mma(d_tmem, ad, bd, C::IDESC, (tap | j) != 0);
             }
+            tp_commit(bar(EM + st));
+            if (j == C::SLICES - 1) tp_commit(bar(AF + acc));
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_s)
-                     : "memory");
-    };
-    // operands of the tile are in shared memory: make them visible to the tensor cores
-    auto operands_ready = [&]() {
-        asm volatile("cp.async.wait_group 0;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-    };
-
-    uint32_t phase = 0;
-    int64_t tile = blockIdx.x;
-    if (tile < ntiles) {
-        fill(tile_of(tile));
-        operands_ready();
-        if (tid == 0) issue();
-    }
-    for (; tile < ntiles; tile += gridDim.x) {
-        const Tile T = tile_of(tile);
-        const bool ok = tc_wait(bar_s, phase, wait_limit);
-        phase ^= 1;
-        if (__syncthreads_or(!ok)) {
-            // give the MMAs in flight a second bounded chance to finish before tensor memory is freed
-            if (tid == 0) {
-                atomicOr(&g_sg_status, 1);
-                tc_wait(bar_s, phase ^ 1, wait_limit);
-            }
-            __syncthreads();
-            break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // the tensor cores are done with the halo: start filling it for the next tile while
-        // this tile's epilogue runs
-        const int64_t next = tile + gridDim.x;
-        if (next < ntiles) fill(tile_of(next));
-
-        // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (voxel m = lane index) and
-        // accumulator columns 16 (w / 4) .. + 15 (none for w >= 4 when cout = 16)
-        const int quarter = warp & 3;
+        // every MMA this thread issued has completed before tensor memory can be freed
+        tp_commit(bar(DR));
+        if (!tc_wait(bar(DR), 0, wait_limit)) fail();
+    } else if (warp >= 4) {
+        // ---- epilogue ----
+        const int quarter = warp - 4;
         const int m = 32 * quarter + lane;
         const int yl = m >> 6, xx = m & 63;
-        const int64_t v = (((int64_t)T.b * s.nz + T.z) * s.ny + (T.y0 + yl)) * kW + xx;
-#pragma unroll
-        for (int c0 = (warp >> 2) * C::CPW; c0 < COUT && c0 < (warp >> 2) * C::CPW + C::CPW; c0 += 16) {
-            float acc[16];
-            tc_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + c0, acc);
-            float o[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const float zj = acc[j] + (bias ? bias[c0 + j] : 0.f);
-                acc[j] = zj;
-                o[j] = epi.act == SG_ACT_GELU ? gelu(zj) : zj;
+        for (int64_t t = 0;; ++t) {
+            const int64_t tile = blockIdx.x + t * gridDim.x;
+            if (tile >= ntiles) break;
+            const int acc = (int)(t & 1);
+            const uint32_t q = (uint32_t)(t >> 1);
+            if (!__all_sync(0xffffffffu, tc_wait(bar(AF + acc), q & 1, wait_limit))) {
+                if (lane == 0) fail();
+                break;
             }
-            if (epi.z_out) {
-                float4* zo = reinterpret_cast<float4*>(epi.z_out + v * COUT + c0);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            float zc[COUT];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) zo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+            for (int c0 = 0; c0 < COUT; c0 += 16) {
+                float v16[16];
+                tc_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(acc * 32 + c0), v16);
+#pragma unroll
+                for (int k = 0; k < 16; ++k) zc[c0 + k] = v16[k];
             }
-            if (epi.res_in && CIN == COUT) {
-                // the voxel's own input channels c0 .. c0 + 15 (the halo is being refilled)
-                const uint4* rp = reinterpret_cast<const uint4*>(x + v * CIN + c0);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) tp_arrive(bar(AE + acc));
+
+            const Tile T = tile_of(tile);
+            const int64_t v = (((int64_t)T.b * s.nz + T.z) * s.ny + (T.y0 + yl)) * kW + xx;
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const uint4 raw = rp[h];
-                    const __nv_bfloat162* p = reinterpret_cast<const __nv_bfloat162*>(&raw);
+            for (int c0 = 0; c0 < COUT; c0 += 16) {
+                float o[16];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        o[8 * h + 2 * q] += __bfloat162float(p[q].x);
-                        o[8 * h + 2 * q + 1] += __bfloat162float(p[q].y);
-                    }
+                for (int k = 0; k < 16; ++k) {
+                    const float zj = zc[c0 + k] + (bias ? bias[c0 + k] : 0.f);
+                    zc[c0 + k] = zj;
+                    o[k] = epi.act == SG_ACT_GELU ? gelu(zj) : zj;
                 }
-            }
-            if (epi.add) {
-                if (epi.add_f32) {
-                    const float4* ad = reinterpret_cast<const float4*>(static_cast<const float*>(epi.add) + v * COUT + c0);
+                if (epi.z_out) {
+                    float4* zo = reinterpret_cast<float4*>(epi.z_out + v * COUT + c0);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float4 r = ad[q];
-                        o[4 * q] += r.x;
-                        o[4 * q + 1] += r.y;
-                        o[4 * q + 2] += r.z;
-                        o[4 * q + 3] += r.w;
-                    }
-                } else {
-                    const uint4* ad = reinterpret_cast<const uint4*>(static_cast<const bf16*>(epi.add) + v * COUT + c0);
+                    for (int k = 0; k < 4; ++k)
+                        zo[k] = make_float4(zc[c0 + 4 * k], zc[c0 + 4 * k + 1], zc[c0 + 4 * k + 2], zc[c0 + 4 * k + 3]);
+                }
+                if (epi.res_in && CIN == COUT) {
+                    const uint4* rp = reinterpret_cast<const uint4*>(x + v * CIN + c0);
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
-                        const uint4 raw = ad[h];
+                        const uint4 raw = rp[h];
                         const __nv_bfloat162* p = reinterpret_cast<const __nv_bfloat162*>(&raw);
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            o[8 * h + 2 * q] += __bfloat162float(p[q].x);
-                            o[8 * h + 2 * q + 1] += __bfloat162float(p[q].y);
+                        for (int k = 0; k < 4; ++k) {
+                            o[8 * h + 2 * k] += __bfloat162float(p[k].x);
+                            o[8 * h + 2 * k + 1] += __bfloat162float(p[k].y);
                         }
                     }
                 }
-            }
-            if (epi.y_f32) {
-                float4* yo = reinterpret_cast<float4*>(static_cast<float*>(y) + v * COUT + c0);
+                if (epi.add) {
+                    if (epi.add_f32) {
+                        const float4* ad =
+                            reinterpret_cast<const float4*>(static_cast<const float*>(epi.add) + v * COUT + c0);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) yo[q] = make_float4(o[4 * q], o[4 * q + 1], o[4 * q + 2], o[4 * q + 3]);
-            } else {
-                uint4 pk[2];
-                __nv_bfloat162* p = reinterpret_cast<__nv_bfloat162*>(pk);
+                        for (int k = 0; k < 4; ++k) {
+                            const float4 r = ad[k];
+                            o[4 * k] += r.x;
+                            o[4 * k + 1] += r.y;
+                            o[4 * k + 2] += r.z;
+                            o[4 * k + 3] += r.w;
+                        }
+                    } else {
+                        const uint4* ad =
+                            reinterpret_cast<const uint4*>(static_cast<const bf16*>(epi.add) + v * COUT + c0);
 #pragma unroll
-                for (int q = 0; q < 8; ++q) p[q] = __floats2bfloat162_rn(o[2 * q], o[2 * q + 1]);
-                uint4* yo = reinterpret_cast<uint4*>(static_cast<bf16*>(y) + v * COUT + c0);
-                yo[0] = pk[0];
-                yo[1] = pk[1];
+                        for (int h = 0; h < 2; ++h) {
+                            const uint4 raw = ad[h];
+                            const __nv_bfloat162* p = reinterpret_cast<const __nv_bfloat162*>(&raw);
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                o[8 * h + 2 * k] += __bfloat162float(p[k].x);
+                                o[8 * h + 2 * k + 1] += __bfloat162float(p[k].y);
+                            }
+                        }
+                    }
+                }
+                if (epi.y_f32) {
+                    float4* yo = reinterpret_cast<float4*>(static_cast<float*>(y) + v * COUT + c0);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) yo[k] = make_float4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
+                } else {
+                    uint4 pk[2];
+                    __nv_bfloat162* p = reinterpret_cast<__nv_bfloat162*>(pk);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) p[k] = __floats2bfloat162_rn(o[2 * k], o[2 * k + 1]);
+                    uint4* yo = reinterpret_cast<uint4*>(static_cast<bf16*>(y) + v * COUT + c0);
+                    yo[0] = pk[0];
+                    yo[1] = pk[1];
+                }
             }
-        }
-        // next tile: its halo has landed and the accumulator has been read out
-        if (next < ntiles) {
-            operands_ready();
-            if (tid == 0) issue();
         }
     }
-    // every warp has finished reading tensor memory before it is freed
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64));
 }
 
 static int g_fwd_impl = SG_CONV_MMA_SYNC;  // forward convolution kernel (sg_set_conv_impl)
 
+// cuTensorMapEncodeTiled from the driver, found once through the runtime (no link-time driver dependency)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
 template <int CIN, int COUT>
 static int launch_fwd_tc(sg_shape s, const void* x, const void* w, const float* bias, Epi epi, void* y,
                          cudaStream_t st) {
-    using C = TcCfg<CIN, COUT>;
+    using C = TcpCfg<CIN, COUT>;
     static int configured = -1, grid_max = 0;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return -3;
     if (configured != dev) {
-        if (cudaFuncSetAttribute(k_conv_fwd_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
+        if (cudaFuncSetAttribute(k_conv_fwd_tcp<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
             cudaSuccess)
             return -3;
-        int per_sm = 0, sms = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_fwd_tc<CIN, COUT>, C::THREADS, C::SMEM) !=
-                cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1)
-            return -3;
-        grid_max = per_sm * sms;
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -3;
+        grid_max = sms;  // one CTA per SM (shared memory)
         configured = dev;
     }
+    auto encode = tensor_map_encoder();
+    if (!encode) return -3;
+    // activations x[b][z][y][x][c] as a 5D tensor (c fastest); boxes of 8 channels x 64 voxels of one row
+    alignas(64) CUtensorMap map;
+    const cuuint64_t dims[5] = {(cuuint64_t)CIN, (cuuint64_t)kW, (cuuint64_t)s.ny, (cuuint64_t)s.nz, (cuuint64_t)s.batch};
+    const cuuint64_t strides[4] = {(cuuint64_t)CIN * 2, (cuuint64_t)kW * CIN * 2, (cuuint64_t)s.ny * kW * CIN * 2,
+                                   (cuuint64_t)s.nz * s.ny * kW * CIN * 2};
+    const cuuint32_t box[5] = {8, (cuuint32_t)kW, 1, 1, 1};
+    const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(x), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return -3;
     const int64_t tiles = (int64_t)s.batch * s.nz * (s.ny / 2);
     const int grid = (int)(tiles < grid_max ? tiles : grid_max);
-    const long long wait_limit = 2000000000LL;  // ~1 s of SM clock per tile
-    k_conv_fwd_tc<CIN, COUT><<<grid, C::THREADS, C::SMEM, st>>>(s, static_cast<const bf16*>(x),
-                                                               static_cast<const bf16*>(w), bias, epi, y, wait_limit);
+    const long long wait_limit = 2000000000LL;  // ~1 s of SM clock per wait
+    k_conv_fwd_tcp<CIN, COUT><<<grid, C::THREADS, C::SMEM, st>>>(map, s, static_cast<const bf16*>(x),
+                                                                static_cast<const bf16*>(w), bias, epi, y, wait_limit);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
