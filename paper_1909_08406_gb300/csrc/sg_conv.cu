@@ -512,11 +512,14 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
 // work of a tile split over warp roles that run concurrently:
 //   warp 0 (one thread)  TMA producer: per (tile, 16-channel slice) it loads
 //                        the 3 x 4 halo rows of the slice in the three
-//                        x-shifted copies, 72 boxes of 8 channels x 64 voxels
-//                        (cp.async.bulk.tensor.5d with a tensor map over the
-//                        NDHWC activations).  A box shifted by -1 / +1 in x
-//                        starts or ends one voxel outside the row; the tensor
-//                        map fills that voxel with zeros.
+//                        x-shifted copies (cp.async.bulk.tensor.5d with tensor
+//                        maps over the NDHWC activations): one box of 8
+//                        channels x 64 voxels x 4 rows x 3 planes per copy and
+//                        channel group, or, where the halo wraps around the
+//                        periodic y or z boundary, one box per row.  A box
+//                        shifted by -1 / +1 in x starts or ends one voxel
+//                        outside the row; the tensor map fills that voxel with
+//                        zeros.
 //   warp 1               fixes the periodic wrap: writes the one voxel per
 //                        shifted row that the box left as zero (loaded from
 //                        global memory before the box lands), then marks the
@@ -573,7 +576,8 @@ __device__ __forceinline__ void tp_tma5(uint32_t dst, const CUtensorMap* map, in
 
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(256, 1)
-    k_conv_fwd_tcp(const __grid_constant__ CUtensorMap xmap, sg_shape s, const bf16* __restrict__ x,
+    k_conv_fwd_tcp(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap xblk, sg_shape s,
+                   const bf16* __restrict__ x,
                    const bf16* __restrict__ w, const float* __restrict__ bias, Epi epi, void* y, long long wait_limit) {
     using C = TcpCfg<CIN, COUT>;
     extern __shared__ __align__(1024) unsigned char sm_tcp[];
@@ -641,13 +645,22 @@ __global__ void __launch_bounds__(256, 1)
             const Tile T = tile_of(tile);
             const int j = (int)(i % C::SLICES);
             const uint32_t sbase = a_s + st * C::STAGE;
+            const bool interior = T.y0 >= 1 && T.y0 + 2 < s.ny && T.z >= 1 && T.z + 1 < s.nz;
             for (int d = 0; d < 3; ++d)
-                for (int g = 0; g < 2; ++g)
-                    for (int r = 0; r < C::ROWS; ++r) {
-                        const int zz = wrapi(T.z + r / C::HY - 1, s.nz), yy = wrapi(T.y0 + r % C::HY - 1, s.ny);
-                        tp_tma5(sbase + (uint32_t)((d * 2 + g) * C::PLANE + r * kW * 16), &xmap, (2 * j + g) * 8, d - 1,
-                                yy, zz, T.b, bar(FT + st));
+                for (int g = 0; g < 2; ++g) {
+                    const uint32_t dst = sbase + (uint32_t)((d * 2 + g) * C::PLANE);
+                    if (interior) {
+                        // the whole 3-plane x 4-row halo of the copy in one box
+                        tp_tma5(dst, &xblk, (2 * j + g) * 8, d - 1, T.y0 - 1, T.z - 1, T.b, bar(FT + st));
+                    } else {
+                        // periodic wrap in y or z: one box per halo row
+                        for (int r = 0; r < C::ROWS; ++r) {
+                            const int zz = wrapi(T.z + r / C::HY - 1, s.nz), yy = wrapi(T.y0 + r % C::HY - 1, s.ny);
+                            tp_tma5(dst + (uint32_t)(r * kW * 16), &xmap, (2 * j + g) * 8, d - 1, yy, zz, T.b,
+                                    bar(FT + st));
+                        }
                     }
+                }
         }
         // the CTA must not exit with boxes still landing
         if (armed_stage >= 0 && !tc_wait(bar(FT + armed_stage), armed_parity, wait_limit)) fail();
@@ -877,10 +890,18 @@ static int launch_fwd_tc(sg_shape s, const void* x, const void* w, const float* 
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return -3;
+    // the same tensor with boxes of 8 channels x 64 voxels x 4 rows x 3 planes (a tile's whole halo
+    // of one channel group, for tiles away from the periodic y and z boundaries)
+    alignas(64) CUtensorMap blk;
+    const cuuint32_t box_blk[5] = {8, (cuuint32_t)kW, (cuuint32_t)C::HY, 3, 1};
+    if (encode(&blk, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(x), dims, strides, box_blk, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return -3;
     const int64_t tiles = (int64_t)s.batch * s.nz * (s.ny / 2);
     const int grid = (int)(tiles < grid_max ? tiles : grid_max);
     const long long wait_limit = 2000000000LL;  // ~1 s of SM clock per wait
-    k_conv_fwd_tcp<CIN, COUT><<<grid, C::THREADS, C::SMEM, st>>>(map, s, static_cast<const bf16*>(x),
+    k_conv_fwd_tcp<CIN, COUT><<<grid, C::THREADS, C::SMEM, st>>>(map, blk, s, static_cast<const bf16*>(x),
                                                                 static_cast<const bf16*>(w), bias, epi, y, wait_limit);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
