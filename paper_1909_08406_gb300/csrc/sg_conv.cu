@@ -508,53 +508,63 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
 // Pipelined forward convolution on tcgen05 with TMA operand loads.
 //
 // Same implicit GEMM as above (tile = 128 voxels of two rows, one
-// tcgen05.mma M=128 x N=cout x K=16 per tap and 16-channel slice), with the
-// work of a tile split over warp roles that run concurrently:
-//   warp 0 (one thread)  TMA producer: per (tile, 16-channel slice) it loads
-//                        the 3 x 4 halo rows of the slice in the three
-//                        x-shifted copies (cp.async.bulk.tensor.5d with tensor
-//                        maps over the NDHWC activations): one box of 8
-//                        channels x 64 voxels x 4 rows x 3 planes per copy and
-//                        channel group, or, where the halo wraps around the
-//                        periodic y or z boundary, one box per row.  A box
-//                        shifted by -1 / +1 in x starts or ends one voxel
-//                        outside the row; the tensor map fills that voxel with
-//                        zeros.
-//   warp 1               fixes the periodic wrap: writes the one voxel per
-//                        shifted row that the box left as zero (loaded from
-//                        global memory before the box lands), then marks the
-//                        stage full.
-//   warp 2 (one thread)  issues the 27 MMAs of a stage into one of two
-//                        accumulators in tensor memory; tcgen05.commit frees the
-//                        stage (and, after the last slice, fills the accumulator).
-//   warps 4-7            epilogue: read the accumulator out of tensor memory
-//                        (tcgen05.ld), free it, and apply bias, activation,
-//                        residual and add while the next tile's MMAs run.
-// Two shared-memory stages (one 16-channel slice of a tile each) and two
-// accumulators decouple the roles; all hand-offs are mbarriers and every wait
-// is bounded (on expiry the kernel sets the status flag and the roles wind
-// down after waiting, bounded, for their own asynchronous work).
+// tcgen05.mma M=128 x N=cout x K=16 per tap and 16-channel slice).  A CTA
+// walks columns of ZC tiles along z (same batch item and row pair); for each
+// 16-channel slice it streams the column's ZC + 2 halo planes (4 rows x 64
+// voxels x 16 channels, in the three x-shifted copies) through a ring of 4
+// plane slots, so each plane is loaded once per column instead of once per
+// tile, and tile k of the column uses the slots of planes k, k+1, k+2.
+// Operand A uses the 32-byte-swizzled K-major layout (rows of 16 channels =
+// 32 B, 8-row atoms of 256 B), which the TMA writes directly
+// (CU_TENSOR_MAP_SWIZZLE_32B); B stays in the no-swizzle layout.  Warp roles:
+//   warp 0 (one thread)  TMA producer: per plane slot one box of 16 channels x
+//                        64 voxels x 4 rows per x-shifted copy (or one box per
+//                        row where the rows wrap around the periodic y
+//                        boundary; z wraps per plane).  A box shifted by -1 /
+//                        +1 in x starts or ends one voxel outside the row; the
+//                        tensor map fills that voxel with zeros.
+//   warp 1               periodic-wrap fixer: writes those voxels (loaded from
+//                        global memory before the box lands) and marks the slot
+//                        full.
+//   warp 2 (one thread)  MMA issuer: 27 MMAs per tile and slice into one of
+//                        2 x ZC accumulators in tensor memory; tcgen05.commit
+//                        frees plane slots and fills accumulators.
+//   warps 4-7            epilogue: tcgen05.ld of an accumulator, free it, bias,
+//                        activation, residual and add, store -- concurrently
+//                        with the MMAs of the next tiles.
+// All hand-offs are mbarriers; every wait is bounded (on expiry the kernel
+// sets the status flag and the roles wind down after waiting, bounded, for
+// their own asynchronous work).
 // ---------------------------------------------------------------------------
 template <int CIN, int COUT>
-struct TcpCfg {
+struct TczCfg {
     static constexpr int K8 = CIN / 8;
-    static constexpr int HY = 4;
-    static constexpr int ROWS = 3 * HY;                // halo rows: 3 planes x 4 rows
-    static constexpr int PLANE = ROWS * kW * 16;       // one 8-channel group of one shifted copy
-    static constexpr int SLICES = CIN / 16;            // 16-channel K slices per tile
-    static constexpr int STAGE = 3 * 2 * PLANE;        // 3 copies x 2 channel groups
-    static constexpr int A_BYTES = 2 * STAGE;
+    static constexpr int SL = CIN / 16;                 // 16-channel K slices
+    static constexpr int HY = 4;                        // halo rows of a 2-row tile
+    static constexpr int ZC = 4;                        // tiles per column along z
+    static constexpr int NSLOT = 4;                     // plane slots in the ring
+    static constexpr int COPYB = HY * kW * 32;          // one x-shifted copy of one plane: 8 KB
+    static constexpr int SLOT = 3 * COPYB;              // 24 KB
+    static constexpr int A_BYTES = NSLOT * SLOT;
     static constexpr int WTAP = K8 * COUT * 16;
     static constexpr int B_BYTES = 27 * WTAP;
-    static constexpr int SMEM = A_BYTES + B_BYTES + 1024;  // + slack to align the base to 1 KB
+    static constexpr int SMEM = A_BYTES + B_BYTES + 1024;
     static constexpr int THREADS = 256;
-    static constexpr uint32_t TX_BYTES = 3 * 2 * ROWS * 8 * kW * 2;  // bytes landed per stage
+    static constexpr int NACC = 2 * ZC;                 // accumulators of 32 columns
+    static constexpr int TMEM_COLS = NACC * 32;         // 256
     static constexpr uint32_t IDESC =
         (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(COUT >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
     static_assert(COUT % 16 == 0 && COUT <= 32, "N = cout: 16 or 32");
     static_assert(CIN % 16 == 0, "cin: multiple of 16");
     static_assert(SMEM <= 232448, "shared memory");
 };
+
+// Shared-memory descriptor of a 32-byte-swizzled K-major operand: 8-row atoms
+// of 256 B (SBO), layout type 6; the leading offset is unused for K = 16.
+__device__ __forceinline__ uint64_t umma_desc_sw32(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(256 >> 4) << 32) | (1ull << 46) |
+           (6ull << 61);
+}
 
 __device__ __forceinline__ void tp_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -576,19 +586,20 @@ __device__ __forceinline__ void tp_tma5(uint32_t dst, const CUtensorMap* map, in
 
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(256, 1)
-    k_conv_fwd_tcp(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap xblk, sg_shape s,
-                   const bf16* __restrict__ x,
-                   const bf16* __restrict__ w, const float* __restrict__ bias, Epi epi, void* y, long long wait_limit) {
-    using C = TcpCfg<CIN, COUT>;
-    extern __shared__ __align__(1024) unsigned char sm_tcp[];
-    __shared__ __align__(8) uint64_t bars[11];  // full_tma[2] full[2] empty[2] acc_full[2] acc_empty[2] drain
+    k_conv_fwd_tcz(const __grid_constant__ CUtensorMap xrows, const __grid_constant__ CUtensorMap xrow, sg_shape s,
+                   const bf16* __restrict__ x, const bf16* __restrict__ w, const float* __restrict__ bias, Epi epi,
+                   void* y, long long wait_limit) {
+    using C = TczCfg<CIN, COUT>;
+    extern __shared__ __align__(1024) unsigned char sm_tcz[];
+    // barriers: TMA landed [4], slot full [4], slot empty [4], accumulator full [8], accumulator empty [8], drain
+    __shared__ __align__(8) uint64_t bars[4 + 4 + 4 + 2 * C::NACC + 1];
     __shared__ uint32_t tmem_holder;
-    const uint32_t base = (smem_u32(sm_tcp) + 1023u) & ~1023u;
-    unsigned char* smem = sm_tcp + (base - smem_u32(sm_tcp));
+    const uint32_t base = (smem_u32(sm_tcz) + 1023u) & ~1023u;
+    unsigned char* smem = sm_tcz + (base - smem_u32(sm_tcz));
     const uint32_t a_s = base, b_s = base + C::A_BYTES;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr int LT = 0, FU = 4, EM = 8, AF = 12, AE = 12 + C::NACC, DR = 12 + 2 * C::NACC;
     auto bar = [&](int k) { return smem_u32(&bars[k]); };
-    const int FT = 0, FU = 2, EM = 4, AF = 6, AE = 8, DR = 10;
 
     // weights of all taps: B[tap][k8][co][8 channels] <- w[co][tap][k8 * 8 ..]
     unsigned char* Bw = smem + C::A_BYTES;
@@ -600,12 +611,12 @@ __global__ void __launch_bounds__(256, 1)
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
-                     "r"(64));
+                     "r"(C::TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int k = 0; k < 11; ++k)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(k)), "r"(k == AE || k == AE + 1 ? 4 : 1));
+        for (int k = 0; k <= DR; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(k)), "r"(k >= AE && k < DR ? 4 : 1));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -614,126 +625,150 @@ __global__ void __launch_bounds__(256, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_holder;
 
+    // columns: (batch item, row pair, chunk of ZC planes); consecutive columns are neighbouring row pairs
     const int tiles_y = s.ny / 2;
-    const int64_t ntiles = (int64_t)s.batch * s.nz * tiles_y;
-    struct Tile {
-        int b, z, y0;
+    const int nchunks = (s.nz + C::ZC - 1) / C::ZC;
+    const int64_t ncols = (int64_t)s.batch * nchunks * tiles_y;
+    struct Col {
+        int b, z0, len, y0;
     };
-    auto tile_of = [&](int64_t t) {
-        const int yt = (int)(t % tiles_y);
-        const int64_t t2 = t / tiles_y;
-        return Tile{(int)(t2 / s.nz), (int)(t2 % s.nz), 2 * yt};
+    auto col_of = [&](int64_t c) {
+        const int yt = (int)(c % tiles_y);
+        const int64_t r = c / tiles_y;
+        const int ch = (int)(r % nchunks);
+        const int b = (int)(r / nchunks);
+        const int z0 = ch * C::ZC;
+        return Col{b, z0, min(C::ZC, s.nz - z0), 2 * yt};
     };
     auto fail = [&]() { atomicOr(&g_sg_status, 1); };
 
     if (warp == 0 && lane == 0) {
-        // ---- TMA producer ----
-        int armed_stage = -1;
-        uint32_t armed_parity = 0;
-        for (int64_t i = 0;; ++i) {
-            const int64_t tile = blockIdx.x + (i / C::SLICES) * gridDim.x;
-            if (tile >= ntiles) break;
-            const int st = (int)(i & 1);
-            const uint32_t n = (uint32_t)(i >> 1);
-            if (!tc_wait(bar(EM + st), (n & 1) ^ 1, wait_limit)) {
-                fail();
-                break;
-            }
-            tp_expect_tx(bar(FT + st), C::TX_BYTES);
-            armed_stage = st;
-            armed_parity = n & 1;
-            const Tile T = tile_of(tile);
-            const int j = (int)(i % C::SLICES);
-            const uint32_t sbase = a_s + st * C::STAGE;
-            const bool interior = T.y0 >= 1 && T.y0 + 2 < s.ny && T.z >= 1 && T.z + 1 < s.nz;
-            for (int d = 0; d < 3; ++d)
-                for (int g = 0; g < 2; ++g) {
-                    const uint32_t dst = sbase + (uint32_t)((d * 2 + g) * C::PLANE);
-                    if (interior) {
-                        // the whole 3-plane x 4-row halo of the copy in one box
-                        tp_tma5(dst, &xblk, (2 * j + g) * 8, d - 1, T.y0 - 1, T.z - 1, T.b, bar(FT + st));
-                    } else {
-                        // periodic wrap in y or z: one box per halo row
-                        for (int r = 0; r < C::ROWS; ++r) {
-                            const int zz = wrapi(T.z + r / C::HY - 1, s.nz), yy = wrapi(T.y0 + r % C::HY - 1, s.ny);
-                            tp_tma5(dst + (uint32_t)(r * kW * 16), &xmap, (2 * j + g) * 8, d - 1, yy, zz, T.b,
-                                    bar(FT + st));
+        // ---- TMA producer: plane loads in order (column, slice, plane) ----
+        uint32_t q = 0;  // plane-load sequence number
+        int last_slot = -1;
+        uint32_t last_parity = 0;
+        bool ok = true;
+        for (int64_t c = blockIdx.x; c < ncols && ok; c += gridDim.x) {
+            const Col K = col_of(c);
+            const bool y_inside = K.y0 >= 1 && K.y0 + 2 < s.ny;
+            for (int j = 0; j < C::SL && ok; ++j)
+                for (int p = 0; p < K.len + 2; ++p, ++q) {
+                    const int slot = (int)(q % C::NSLOT);
+                    const uint32_t use = q / C::NSLOT;
+                    if (!tc_wait(bar(EM + slot), (use & 1) ^ 1, wait_limit)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    tp_expect_tx(bar(LT + slot), C::SLOT);
+                    last_slot = slot;
+                    last_parity = use & 1;
+                    const int zz = wrapi(K.z0 - 1 + p, s.nz);
+                    for (int d = 0; d < 3; ++d) {
+                        const uint32_t dst = a_s + (uint32_t)(slot * C::SLOT + d * C::COPYB);
+                        if (y_inside) {
+                            tp_tma5(dst, &xrows, 16 * j, d - 1, K.y0 - 1, zz, K.b, bar(LT + slot));
+                        } else {
+                            for (int r = 0; r < C::HY; ++r)
+                                tp_tma5(dst + (uint32_t)(r * kW * 32), &xrow, 16 * j, d - 1, wrapi(K.y0 + r - 1, s.ny),
+                                        zz, K.b, bar(LT + slot));
                         }
                     }
                 }
         }
         // the CTA must not exit with boxes still landing
-        if (armed_stage >= 0 && !tc_wait(bar(FT + armed_stage), armed_parity, wait_limit)) fail();
+        if (last_slot >= 0 && !tc_wait(bar(LT + last_slot), last_parity, wait_limit)) fail();
     } else if (warp == 1) {
-        // ---- periodic-wrap fixer: copy 0 position 0 <- in[63], copy 2 position 63 <- in[0] ----
-        for (int64_t i = 0;; ++i) {
-            const int64_t tile = blockIdx.x + (i / C::SLICES) * gridDim.x;
-            if (tile >= ntiles) break;
-            const int st = (int)(i & 1);
-            const uint32_t n = (uint32_t)(i >> 1);
-            const Tile T = tile_of(tile);
-            const int j = (int)(i % C::SLICES);
-            uint4 val[2];
-            uint32_t dst[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int c = lane + 32 * h;  // 48 chunks: side (2) x group (2) x row (12)
-                const int cc = c < 48 ? c : 0;
-                const int side = cc / 24, g = (cc / 12) % 2, r = cc % 12;
-                const int zz = wrapi(T.z + r / C::HY - 1, s.nz), yy = wrapi(T.y0 + r % C::HY - 1, s.ny);
-                const int xs = side ? 0 : kW - 1;
-                val[h] = *reinterpret_cast<const uint4*>(
-                    x + ((((int64_t)T.b * s.nz + zz) * s.ny + yy) * kW + xs) * CIN + (2 * j + g) * 8);
-                dst[h] = a_s + st * C::STAGE + (uint32_t)(((side ? 2 : 0) * 2 + g) * C::PLANE + r * kW * 16 +
-                                                          (side ? kW - 1 : 0) * 16);
-            }
-            // one decision for the whole warp (the lanes wait independently)
-            if (!__all_sync(0xffffffffu, tc_wait(bar(FT + st), n & 1, wait_limit))) {
-                if (lane == 0) fail();
-                break;
-            }
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-                if (lane + 32 * h < 48)
-                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst[h]), "r"(val[h].x), "r"(val[h].y),
-                                 "r"(val[h].z), "r"(val[h].w)
-                                 : "memory");
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) tp_arrive(bar(FU + st));
+        // ---- periodic-wrap fixer: copy 0 voxel 0 <- in[63], copy 2 voxel 63 <- in[0], 4 rows ----
+        uint32_t q = 0;
+        bool ok = true;
+        for (int64_t c = blockIdx.x; c < ncols && ok; c += gridDim.x) {
+            const Col K = col_of(c);
+            for (int j = 0; j < C::SL && ok; ++j)
+                for (int p = 0; p < K.len + 2; ++p, ++q) {
+                    const int slot = (int)(q % C::NSLOT);
+                    const uint32_t use = q / C::NSLOT;
+                    // lane < 16: side (2) x row (4) x 16-byte half of the voxel (2)
+                    const int l = lane & 15;
+                    const int side = l >> 3, r = (l >> 1) & 3, h = l & 1;
+                    const int zz = wrapi(K.z0 - 1 + p, s.nz), yy = wrapi(K.y0 + r - 1, s.ny);
+                    const int xs = side ? 0 : kW - 1, pos = side ? kW - 1 : 0;
+                    const uint4 val = *reinterpret_cast<const uint4*>(
+                        x + ((((int64_t)K.b * s.nz + zz) * s.ny + yy) * kW + xs) * CIN + 16 * j + 8 * h);
+                    // 32-byte swizzle: the two 16-byte halves of rows 4..7 of an 8-row atom trade places
+                    const uint32_t dst = a_s + (uint32_t)(slot * C::SLOT + (side ? 2 : 0) * C::COPYB + r * kW * 32 +
+                                                          pos * 32 + ((h ^ ((pos >> 2) & 1)) * 16));
+                    if (!__all_sync(0xffffffffu, tc_wait(bar(LT + slot), use & 1, wait_limit))) {
+                        if (lane == 0) fail();
+                        ok = false;
+                        break;
+                    }
+                    if (lane < 16)
+                        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(val.x), "r"(val.y),
+                                     "r"(val.z), "r"(val.w)
+                                     : "memory");
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) tp_arrive(bar(FU + slot));
+                }
         }
     } else if (warp == 2 && lane == 0) {
         // ---- MMA issuer ----
-        for (int64_t i = 0;; ++i) {
-            const int64_t tile = blockIdx.x + (i / C::SLICES) * gridDim.x;
-            if (tile >= ntiles) break;
-            const int st = (int)(i & 1);
-            const uint32_t n = (uint32_t)(i >> 1);
-            const int j = (int)(i % C::SLICES);
-            const int64_t t = i / C::SLICES;
-            const int acc = (int)(t & 1);
-            const uint32_t q = (uint32_t)(t >> 1);
-            if (j == 0 && !tc_wait(bar(AE + acc), (q & 1) ^ 1, wait_limit)) {
-                fail();
-                break;
-            }
-            if (!tc_wait(bar(FU + st), n & 1, wait_limit)) {
-                fail();
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t sbase = a_s + st * C::STAGE;
-            const uint32_t d_tmem = tmem + (uint32_t)(acc * 32);
+        uint32_t q = 0;  // sequence number of the first plane of the current (column, slice)
+        int64_t u = 0;   // column ordinal of this CTA
+        bool ok = true;
+        for (int64_t c = blockIdx.x; c < ncols && ok; c += gridDim.x, ++u) {
+            const Col K = col_of(c);
+            for (int j = 0; j < C::SL && ok; ++j) {
+                for (int k = 0; k < C::ZC && ok; ++k) {
+                    const int acc = (int)(u & 1) * C::ZC + k;
+                    const uint32_t au = (uint32_t)(u >> 1);
+                    if (k >= K.len) {
+                        // a short last chunk: keep every accumulator's barrier phases in step
+                        if (j == 0 && !tc_wait(bar(AE + acc), (au & 1) ^ 1, wait_limit)) {
+                            fail();
+                            ok = false;
+                            break;
+                        }
+                        if (j == C::SL - 1) tp_commit(bar(AF + acc));
+                        continue;
+                    }
+                    // planes k, k + 1, k + 2 of this slice must be in their slots
+                    for (int p = (k == 0 ? 0 : k + 2); p <= k + 2; ++p) {
+                        const uint32_t qq = q + p;
+                        if (!tc_wait(bar(FU + (int)(qq % C::NSLOT)), (qq / C::NSLOT) & 1, wait_limit)) {
+                            fail();
+                            ok = false;
+                            break;
+                        }
+                    }
+                    if (!ok) break;
+                    if (j == 0 && !tc_wait(bar(AE + acc), (au & 1) ^ 1, wait_limit)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t d_tmem = tmem + (uint32_t)(acc * 32);
 #pragma unroll 1
-            for (int tap = 0; tap < 27; ++tap) {
-                const int dz = tap / 9, dy = (tap / 3) % 3, dxi = tap % 3;  // each + 1
-                const uint64_t ad = umma_desc(sbase + (uint32_t)(dxi * 2 * C::PLANE + (dz * C::HY + dy) * kW * 16),
-                                              C::PLANE, 128);
-                const uint64_t bd = umma_desc(b_s + (uint32_t)(tap * C::WTAP + 2 * j * COUT * 16), COUT * 16, 128);
-                tc_mma(d_tmem, ad, bd, C::IDESC, (tap | j) != 0);
+                    for (int tap = 0; tap < 27; ++tap) {
+                        const int dz = tap / 9, dy = (tap / 3) % 3, dxi = tap % 3;  // each + 1
+                        const uint32_t slot = (q + k + dz) % C::NSLOT;
+                        const uint64_t ad = umma_desc_sw32(a_s + slot * C::SLOT + dxi * C::COPYB + dy * kW * 32);
+                        const uint64_t bd =
+                            umma_desc(b_s + (uint32_t)(tap * C::WTAP + 2 * j * COUT * 16), COUT * 16, 128);
+                        tc_mma(d_tmem, ad, bd, C::IDESC, (tap | j) != 0);
+                    }
+                    // plane k is not used by later tiles of this slice; the last tile frees all three
+                    tp_commit(bar(EM + (int)((q + k) % C::NSLOT)));
+                    if (k == K.len - 1) {
+                        tp_commit(bar(EM + (int)((q + k + 1) % C::NSLOT)));
+                        tp_commit(bar(EM + (int)((q + k + 2) % C::NSLOT)));
+                    }
+                    if (j == C::SL - 1) tp_commit(bar(AF + acc));
+                }
+                q += K.len + 2;
             }
-            tp_commit(bar(EM + st));
-            if (j == C::SLICES - 1) tp_commit(bar(AF + acc));
         }
         // every MMA this thread issued has completed before tensor memory can be freed
         tp_commit(bar(DR));
@@ -743,97 +778,105 @@ __global__ void __launch_bounds__(256, 1)
         const int quarter = warp - 4;
         const int m = 32 * quarter + lane;
         const int yl = m >> 6, xx = m & 63;
-        for (int64_t t = 0;; ++t) {
-            const int64_t tile = blockIdx.x + t * gridDim.x;
-            if (tile >= ntiles) break;
-            const int acc = (int)(t & 1);
-            const uint32_t q = (uint32_t)(t >> 1);
-            if (!__all_sync(0xffffffffu, tc_wait(bar(AF + acc), q & 1, wait_limit))) {
-                if (lane == 0) fail();
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            float zc[COUT];
+        int64_t u = 0;
+        bool ok = true;
+        for (int64_t c = blockIdx.x; c < ncols && ok; c += gridDim.x, ++u) {
+            const Col K = col_of(c);
+            for (int k = 0; k < C::ZC; ++k) {
+                const int acc = (int)(u & 1) * C::ZC + k;
+                const uint32_t au = (uint32_t)(u >> 1);
+                if (!__all_sync(0xffffffffu, tc_wait(bar(AF + acc), au & 1, wait_limit))) {
+                    if (lane == 0) fail();
+                    ok = false;
+                    break;
+                }
+                if (k >= K.len) {  // ghost tile of a short chunk
+                    __syncwarp();
+                    if (lane == 0) tp_arrive(bar(AE + acc));
+                    continue;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                float zc[COUT];
 #pragma unroll
-            for (int c0 = 0; c0 < COUT; c0 += 16) {
-                float v16[16];
-                tc_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(acc * 32 + c0), v16);
+                for (int c0 = 0; c0 < COUT; c0 += 16) {
+                    float v16[16];
+                    tc_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(acc * 32 + c0), v16);
 #pragma unroll
-                for (int k = 0; k < 16; ++k) zc[c0 + k] = v16[k];
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) tp_arrive(bar(AE + acc));
+                    for (int e = 0; e < 16; ++e) zc[c0 + e] = v16[e];
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) tp_arrive(bar(AE + acc));
 
-            const Tile T = tile_of(tile);
-            const int64_t v = (((int64_t)T.b * s.nz + T.z) * s.ny + (T.y0 + yl)) * kW + xx;
+                const int64_t v = (((int64_t)K.b * s.nz + (K.z0 + k)) * s.ny + (K.y0 + yl)) * kW + xx;
 #pragma unroll
-            for (int c0 = 0; c0 < COUT; c0 += 16) {
-                float o[16];
+                for (int c0 = 0; c0 < COUT; c0 += 16) {
+                    float o[16];
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    const float zj = zc[c0 + k] + (bias ? bias[c0 + k] : 0.f);
-                    zc[c0 + k] = zj;
-                    o[k] = epi.act == SG_ACT_GELU ? gelu(zj) : zj;
-                }
-                if (epi.z_out) {
-                    float4* zo = reinterpret_cast<float4*>(epi.z_out + v * COUT + c0);
-#pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        zo[k] = make_float4(zc[c0 + 4 * k], zc[c0 + 4 * k + 1], zc[c0 + 4 * k + 2], zc[c0 + 4 * k + 3]);
-                }
-                if (epi.res_in && CIN == COUT) {
-                    const uint4* rp = reinterpret_cast<const uint4*>(x + v * CIN + c0);
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const uint4 raw = rp[h];
-                        const __nv_bfloat162* p = reinterpret_cast<const __nv_bfloat162*>(&raw);
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            o[8 * h + 2 * k] += __bfloat162float(p[k].x);
-                            o[8 * h + 2 * k + 1] += __bfloat162float(p[k].y);
-                        }
+                    for (int e = 0; e < 16; ++e) {
+                        const float zj = zc[c0 + e] + (bias ? bias[c0 + e] : 0.f);
+                        zc[c0 + e] = zj;
+                        o[e] = epi.act == SG_ACT_GELU ? gelu(zj) : zj;
                     }
-                }
-                if (epi.add) {
-                    if (epi.add_f32) {
-                        const float4* ad =
-                            reinterpret_cast<const float4*>(static_cast<const float*>(epi.add) + v * COUT + c0);
+                    if (epi.z_out) {
+                        float4* zo = reinterpret_cast<float4*>(epi.z_out + v * COUT + c0);
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const float4 r = ad[k];
-                            o[4 * k] += r.x;
-                            o[4 * k + 1] += r.y;
-                            o[4 * k + 2] += r.z;
-                            o[4 * k + 3] += r.w;
-                        }
-                    } else {
-                        const uint4* ad =
-                            reinterpret_cast<const uint4*>(static_cast<const bf16*>(epi.add) + v * COUT + c0);
+                        for (int e = 0; e < 4; ++e)
+                            zo[e] = make_float4(zc[c0 + 4 * e], zc[c0 + 4 * e + 1], zc[c0 + 4 * e + 2], zc[c0 + 4 * e + 3]);
+                    }
+                    if (epi.res_in && CIN == COUT) {
+                        const uint4* rp = reinterpret_cast<const uint4*>(x + v * CIN + c0);
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
-                            const uint4 raw = ad[h];
-                            const __nv_bfloat162* p = reinterpret_cast<const __nv_bfloat162*>(&raw);
+                            const uint4 raw = rp[h];
+                            const __nv_bfloat162* pr = reinterpret_cast<const __nv_bfloat162*>(&raw);
 #pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                o[8 * h + 2 * k] += __bfloat162float(p[k].x);
-                                o[8 * h + 2 * k + 1] += __bfloat162float(p[k].y);
+                            for (int e = 0; e < 4; ++e) {
+                                o[8 * h + 2 * e] += __bfloat162float(pr[e].x);
+                                o[8 * h + 2 * e + 1] += __bfloat162float(pr[e].y);
                             }
                         }
                     }
-                }
-                if (epi.y_f32) {
-                    float4* yo = reinterpret_cast<float4*>(static_cast<float*>(y) + v * COUT + c0);
+                    if (epi.add) {
+                        if (epi.add_f32) {
+                            const float4* ad =
+                                reinterpret_cast<const float4*>(static_cast<const float*>(epi.add) + v * COUT + c0);
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) yo[k] = make_float4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
-                } else {
-                    uint4 pk[2];
-                    __nv_bfloat162* p = reinterpret_cast<__nv_bfloat162*>(pk);
+                            for (int e = 0; e < 4; ++e) {
+                                const float4 r = ad[e];
+                                o[4 * e] += r.x;
+                                o[4 * e + 1] += r.y;
+                                o[4 * e + 2] += r.z;
+                                o[4 * e + 3] += r.w;
+                            }
+                        } else {
+                            const uint4* ad =
+                                reinterpret_cast<const uint4*>(static_cast<const bf16*>(epi.add) + v * COUT + c0);
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) p[k] = __floats2bfloat162_rn(o[2 * k], o[2 * k + 1]);
-                    uint4* yo = reinterpret_cast<uint4*>(static_cast<bf16*>(y) + v * COUT + c0);
-                    yo[0] = pk[0];
-                    yo[1] = pk[1];
+                            for (int h = 0; h < 2; ++h) {
+                                const uint4 raw = ad[h];
+                                const __nv_bfloat162* pr = reinterpret_cast<const __nv_bfloat162*>(&raw);
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    o[8 * h + 2 * e] += __bfloat162float(pr[e].x);
+                                    o[8 * h + 2 * e + 1] += __bfloat162float(pr[e].y);
+                                }
+                            }
+                        }
+                    }
+                    if (epi.y_f32) {
+                        float4* yo = reinterpret_cast<float4*>(static_cast<float*>(y) + v * COUT + c0);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) yo[e] = make_float4(o[4 * e], o[4 * e + 1], o[4 * e + 2], o[4 * e + 3]);
+                    } else {
+                        uint4 pk[2];
+                        __nv_bfloat162* pp = reinterpret_cast<__nv_bfloat162*>(pk);
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) pp[e] = __floats2bfloat162_rn(o[2 * e], o[2 * e + 1]);
+                        uint4* yo = reinterpret_cast<uint4*>(static_cast<bf16*>(y) + v * COUT + c0);
+                        yo[0] = pk[0];
+                        yo[1] = pk[1];
+                    }
                 }
             }
         }
@@ -841,7 +884,8 @@ __global__ void __launch_bounds__(256, 1)
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64));
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS));
 }
 
 static int g_fwd_impl = SG_CONV_MMA_SYNC;  // forward convolution kernel (sg_set_conv_impl)
@@ -864,44 +908,41 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 template <int CIN, int COUT>
 static int launch_fwd_tc(sg_shape s, const void* x, const void* w, const float* bias, Epi epi, void* y,
                          cudaStream_t st) {
-    using C = TcpCfg<CIN, COUT>;
+    using C = TczCfg<CIN, COUT>;
     static int configured = -1, grid_max = 0;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return -3;
     if (configured != dev) {
-        if (cudaFuncSetAttribute(k_conv_fwd_tcp<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
+        if (cudaFuncSetAttribute(k_conv_fwd_tcz<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
             cudaSuccess)
             return -3;
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -3;
-        grid_max = sms;  // one CTA per SM (shared memory)
+        grid_max = sms;  // one CTA per SM (shared memory, tensor memory)
         configured = dev;
     }
     auto encode = tensor_map_encoder();
     if (!encode) return -3;
-    // activations x[b][z][y][x][c] as a 5D tensor (c fastest); boxes of 8 channels x 64 voxels of one row
-    alignas(64) CUtensorMap map;
+    // activations x[b][z][y][x][c] as a 5D tensor (c fastest); boxes of 16 channels (32 bytes, the
+    // swizzle span) x 64 voxels x 4 rows or x 1 row, written 32-byte swizzled
     const cuuint64_t dims[5] = {(cuuint64_t)CIN, (cuuint64_t)kW, (cuuint64_t)s.ny, (cuuint64_t)s.nz, (cuuint64_t)s.batch};
     const cuuint64_t strides[4] = {(cuuint64_t)CIN * 2, (cuuint64_t)kW * CIN * 2, (cuuint64_t)s.ny * kW * CIN * 2,
                                    (cuuint64_t)s.nz * s.ny * kW * CIN * 2};
-    const cuuint32_t box[5] = {8, (cuuint32_t)kW, 1, 1, 1};
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(x), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+    alignas(64) CUtensorMap rows, row;
+    const cuuint32_t box_rows[5] = {16, (cuuint32_t)kW, (cuuint32_t)C::HY, 1, 1};
+    const cuuint32_t box_row[5] = {16, (cuuint32_t)kW, 1, 1, 1};
+    if (encode(&rows, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(x), dims, strides, box_rows, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+        encode(&row, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(x), dims, strides, box_row, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return -3;
-    // the same tensor with boxes of 8 channels x 64 voxels x 4 rows x 3 planes (a tile's whole halo
-    // of one channel group, for tiles away from the periodic y and z boundaries)
-    alignas(64) CUtensorMap blk;
-    const cuuint32_t box_blk[5] = {8, (cuuint32_t)kW, (cuuint32_t)C::HY, 3, 1};
-    if (encode(&blk, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(x), dims, strides, box_blk, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return -3;
-    const int64_t tiles = (int64_t)s.batch * s.nz * (s.ny / 2);
-    const int grid = (int)(tiles < grid_max ? tiles : grid_max);
+    const int64_t cols = (int64_t)s.batch * ((s.nz + C::ZC - 1) / C::ZC) * (s.ny / 2);
+    const int grid = (int)(cols < grid_max ? cols : grid_max);
     const long long wait_limit = 2000000000LL;  // ~1 s of SM clock per wait
-    k_conv_fwd_tcp<CIN, COUT><<<grid, C::THREADS, C::SMEM, st>>>(map, blk, s, static_cast<const bf16*>(x),
+    k_conv_fwd_tcz<CIN, COUT><<<grid, C::THREADS, C::SMEM, st>>>(rows, row, s, static_cast<const bf16*>(x),
                                                                 static_cast<const bf16*>(w), bias, epi, y, wait_limit);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

@@ -29,9 +29,11 @@ def impl(request):
     sg.set_conv_impl(prev)
 
 
-# (1, 16, 64, 64): 512 tiles of the tcgen05 kernel, more than its persistent grid
+# tcgen05 kernel: (2, 3, 4, 64) a short z chunk (3 of 4 tiles) and rows wrapping in y;
+# (1, 4, 8, 64) interior and wrapping row pairs; (4, 6, 64, 64) 256 columns of tiles for at most
+# 152 CTAs (several columns per CTA, both accumulator sets) with chunks of 4 and 2 planes
 @pytest.mark.parametrize("cin,cout", [(16, 32), (32, 32), (32, 16), (16, 16)])
-@pytest.mark.parametrize("shape", [(1, 4, 8, 64), (2, 3, 4, 64), (1, 16, 64, 64)])
+@pytest.mark.parametrize("shape", [(1, 4, 8, 64), (2, 3, 4, 64), (4, 6, 64, 64)])
 def test_conv_forward_matches_oracle(cin, cout, shape, impl):
     g = torch.Generator().manual_seed(cin + cout + shape[0])
     x = _rand(shape + (cin,), g)
