@@ -16,6 +16,9 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+#include <utility>
+
 #include "gblb_surrogate.h"
 
 namespace sg {
@@ -71,6 +74,16 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
 }
 
 __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+// f(std::integral_constant<int, I>{}) for I = 0 .. N-1, unrolled at compile time
+template <int... Is, class F>
+__device__ __forceinline__ void sg_static_for_impl(std::integer_sequence<int, Is...>, F&& f) {
+    (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+    sg_static_for_impl(std::make_integer_sequence<int, N>{}, f);
+}
 
 // GELU with the Gaussian CDF, g(z) = z Phi(z), and its derivative Phi(z) + z phi(z).
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
@@ -750,15 +763,20 @@ __global__ void __launch_bounds__(256, 1)
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const uint32_t d_tmem = tmem + (uint32_t)(acc * 32);
-#pragma unroll 1
-                    for (int tap = 0; tap < 27; ++tap) {
-                        const int dz = tap / 9, dy = (tap / 3) % 3, dxi = tap % 3;  // each + 1
-                        const uint32_t slot = (q + k + dz) % C::NSLOT;
-                        const uint64_t ad = umma_desc_sw32(a_s + slot * C::SLOT + dxi * C::COPYB + dy * kW * 32);
-                        const uint64_t bd =
-                            umma_desc(b_s + (uint32_t)(tap * C::WTAP + 2 * j * COUT * 16), COUT * 16, 128);
-                        tc_mma(d_tmem, ad, bd, C::IDESC, (tap | j) != 0);
-                    }
+                    // descriptors of the three planes' slots and of the slice's weights; a tap adds a
+                    // compile-time offset to the start-address field (addresses stay below 2^18 bytes,
+                    // so the 14-bit field never carries)
+                    const uint64_t a_pl[3] = {umma_desc_sw32(a_s + ((q + k) % C::NSLOT) * C::SLOT),
+                                              umma_desc_sw32(a_s + ((q + k + 1) % C::NSLOT) * C::SLOT),
+                                              umma_desc_sw32(a_s + ((q + k + 2) % C::NSLOT) * C::SLOT)};
+                    const uint64_t b0 = umma_desc(b_s + (uint32_t)(2 * j * COUT * 16), COUT * 16, 128);
+                    const uint32_t first = j == 0 ? 0u : 1u;
+                    static_for<27>([&](auto TAP) {
+                        constexpr int dz = TAP / 9, dy = (TAP / 3) % 3, dxi = TAP % 3;  // each + 1
+                        constexpr uint64_t aoff = (uint64_t)((dxi * C::COPYB + dy * kW * 32) >> 4);
+                        constexpr uint64_t boff = (uint64_t)((TAP * C::WTAP) >> 4);
+                        tc_mma(d_tmem, a_pl[dz] + aoff, b0 + boff, C::IDESC, TAP == 0 ? first : 1u);
+                    });
                     // plane k is not used by later tiles of this slice; the last tile frees all three
                     tp_commit(bar(EM + (int)((q + k) % C::NSLOT)));
                     if (k == K.len - 1) {
