@@ -49,13 +49,13 @@ int sg_conv3d_fwd(sg_shape s, int cin, int cout, const void *x, const void *w, c
                   int res_in, const void *add, float *z_out, void *y, void *stream);
 
 /* Kernel of the two convolution entry points above:
- *   SG_CONV_TCGEN05  5th-generation tensor cores: tcgen05.mma with
+ *   SG_CONV_TCGEN05  (default) 5th-generation tensor cores: tcgen05.mma with
  *                    the FP32 accumulator in tensor memory, M = 128 voxels,
  *                    N = cout, K = 16 per instruction; persistent CTAs with the
  *                    weights resident in shared memory.  A wait for the tensor
  *                    cores that runs out of time (~1 s) ends the kernel and
  *                    is reported by sg_status.
- *   SG_CONV_MMA_SYNC (default) warp-level mma.sync.m16n8k16.
+ *   SG_CONV_MMA_SYNC warp-level mma.sync.m16n8k16.
  * Returns the previous setting, or -1 for an unknown value.  Process-wide. */
 #define SG_CONV_MMA_SYNC 0
 #define SG_CONV_TCGEN05 1

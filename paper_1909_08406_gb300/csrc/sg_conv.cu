@@ -542,13 +542,24 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
 //   warp 2 (one thread)  MMA issuer: 27 MMAs per tile and slice into one of
 //                        2 x ZC accumulators in tensor memory; tcgen05.commit
 //                        frees plane slots and fills accumulators.
-//   warps 4-7            epilogue: tcgen05.ld of an accumulator, free it, bias,
+//   warps 4-11           epilogue (two per tensor-memory lane quarter, half the
+//                        columns each): tcgen05.ld of an accumulator, free it, bias,
 //                        activation, residual and add, store -- concurrently
 //                        with the MMAs of the next tiles.
 // All hand-offs are mbarriers; every wait is bounded (on expiry the kernel
 // sets the status flag and the roles wind down after waiting, bounded, for
 // their own asynchronous work).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void tc_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
 template <int CIN, int COUT>
 struct TczCfg {
     static constexpr int K8 = CIN / 8;
@@ -562,7 +573,9 @@ struct TczCfg {
     static constexpr int WTAP = K8 * COUT * 16;
     static constexpr int B_BYTES = 27 * WTAP;
     static constexpr int SMEM = A_BYTES + B_BYTES + 1024;
-    static constexpr int THREADS = 256;
+    static constexpr int THREADS = 384;                 // warps 0-2 roles, 3 spare, 4-11 epilogue
+    static constexpr int EPI_WARPS = 8;                 // two per tensor-memory lane quarter
+    static constexpr int EPI_COLS = COUT / 2;           // accumulator columns per epilogue warp
     static constexpr int NACC = 2 * ZC;                 // accumulators of 32 columns
     static constexpr int TMEM_COLS = NACC * 32;         // 256
     static constexpr uint32_t IDESC =
@@ -598,7 +611,7 @@ __device__ __forceinline__ void tp_tma5(uint32_t dst, const CUtensorMap* map, in
 }
 
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(384, 1)
     k_conv_fwd_tcz(const __grid_constant__ CUtensorMap xrows, const __grid_constant__ CUtensorMap xrow, sg_shape s,
                    const bf16* __restrict__ x, const bf16* __restrict__ w, const float* __restrict__ bias, Epi epi,
                    void* y, long long wait_limit) {
@@ -629,7 +642,7 @@ __global__ void __launch_bounds__(256, 1)
     }
     if (tid == 0) {
         for (int k = 0; k <= DR; ++k)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(k)), "r"(k >= AE && k < DR ? 4 : 1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(k)), "r"(k >= AE && k < DR ? C::EPI_WARPS : 1));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -792,8 +805,10 @@ __global__ void __launch_bounds__(256, 1)
         tp_commit(bar(DR));
         if (!tc_wait(bar(DR), 0, wait_limit)) fail();
     } else if (warp >= 4) {
-        // ---- epilogue ----
-        const int quarter = warp - 4;
+        // ---- epilogue: warp reads lanes 32 (warp % 4) .. + 31 and columns half * cout / 2 .. + cout / 2 ----
+        const int quarter = warp & 3, half = (warp - 4) >> 2;
+        constexpr int EC = C::EPI_COLS;
+        const int c_lo = half * EC;
         const int m = 32 * quarter + lane;
         const int yl = m >> 6, xx = m & 63;
         int64_t u = 0;
@@ -814,39 +829,62 @@ __global__ void __launch_bounds__(256, 1)
                     continue;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                float zc[COUT];
-#pragma unroll
-                for (int c0 = 0; c0 < COUT; c0 += 16) {
-                    float v16[16];
-                    tc_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(acc * 32 + c0), v16);
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) zc[c0 + e] = v16[e];
+                float zc[EC];
+                const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(acc * 32 + c_lo);
+                if constexpr (EC == 16) {
+                    tc_ld16(taddr, zc);
+                } else {
+                    tc_ld8(taddr, zc);
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) tp_arrive(bar(AE + acc));
 
                 const int64_t v = (((int64_t)K.b * s.nz + (K.z0 + k)) * s.ny + (K.y0 + yl)) * kW + xx;
+                float o[EC];
 #pragma unroll
-                for (int c0 = 0; c0 < COUT; c0 += 16) {
-                    float o[16];
+                for (int e = 0; e < EC; ++e) {
+                    const float zj = zc[e] + (bias ? bias[c_lo + e] : 0.f);
+                    zc[e] = zj;
+                    o[e] = epi.act == SG_ACT_GELU ? gelu(zj) : zj;
+                }
+                if (epi.z_out) {
+                    float4* zo = reinterpret_cast<float4*>(epi.z_out + v * COUT + c_lo);
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        const float zj = zc[c0 + e] + (bias ? bias[c0 + e] : 0.f);
-                        zc[c0 + e] = zj;
-                        o[e] = epi.act == SG_ACT_GELU ? gelu(zj) : zj;
+                    for (int e = 0; e < EC / 4; ++e)
+                        zo[e] = make_float4(zc[4 * e], zc[4 * e + 1], zc[4 * e + 2], zc[4 * e + 3]);
+                }
+                if (epi.res_in && CIN == COUT) {
+                    const uint4* rp = reinterpret_cast<const uint4*>(x + v * CIN + c_lo);
+#pragma unroll
+                    for (int h = 0; h < EC / 8; ++h) {
+                        const uint4 raw = rp[h];
+                        const __nv_bfloat162* pr = reinterpret_cast<const __nv_bfloat162*>(&raw);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            o[8 * h + 2 * e] += __bfloat162float(pr[e].x);
+                            o[8 * h + 2 * e + 1] += __bfloat162float(pr[e].y);
+                        }
                     }
-                    if (epi.z_out) {
-                        float4* zo = reinterpret_cast<float4*>(epi.z_out + v * COUT + c0);
+                }
+                if (epi.add) {
+                    if (epi.add_f32) {
+                        const float4* ad =
+                            reinterpret_cast<const float4*>(static_cast<const float*>(epi.add) + v * COUT + c_lo);
 #pragma unroll
-                        for (int e = 0; e < 4; ++e)
-                            zo[e] = make_float4(zc[c0 + 4 * e], zc[c0 + 4 * e + 1], zc[c0 + 4 * e + 2], zc[c0 + 4 * e + 3]);
-                    }
-                    if (epi.res_in && CIN == COUT) {
-                        const uint4* rp = reinterpret_cast<const uint4*>(x + v * CIN + c0);
+                        for (int e = 0; e < EC / 4; ++e) {
+                            const float4 r = ad[e];
+                            o[4 * e] += r.x;
+                            o[4 * e + 1] += r.y;
+                            o[4 * e + 2] += r.z;
+                            o[4 * e + 3] += r.w;
+                        }
+                    } else {
+                        const uint4* ad =
+                            reinterpret_cast<const uint4*>(static_cast<const bf16*>(epi.add) + v * COUT + c_lo);
 #pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-                            const uint4 raw = rp[h];
+                        for (int h = 0; h < EC / 8; ++h) {
+                            const uint4 raw = ad[h];
                             const __nv_bfloat162* pr = reinterpret_cast<const __nv_bfloat162*>(&raw);
 #pragma unroll
                             for (int e = 0; e < 4; ++e) {
@@ -855,46 +893,19 @@ __global__ void __launch_bounds__(256, 1)
                             }
                         }
                     }
-                    if (epi.add) {
-                        if (epi.add_f32) {
-                            const float4* ad =
-                                reinterpret_cast<const float4*>(static_cast<const float*>(epi.add) + v * COUT + c0);
+                }
+                if (epi.y_f32) {
+                    float4* yo = reinterpret_cast<float4*>(static_cast<float*>(y) + v * COUT + c_lo);
 #pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                const float4 r = ad[e];
-                                o[4 * e] += r.x;
-                                o[4 * e + 1] += r.y;
-                                o[4 * e + 2] += r.z;
-                                o[4 * e + 3] += r.w;
-                            }
-                        } else {
-                            const uint4* ad =
-                                reinterpret_cast<const uint4*>(static_cast<const bf16*>(epi.add) + v * COUT + c0);
+                    for (int e = 0; e < EC / 4; ++e) yo[e] = make_float4(o[4 * e], o[4 * e + 1], o[4 * e + 2], o[4 * e + 3]);
+                } else {
+                    uint4 pk[EC / 8];
+                    __nv_bfloat162* pp = reinterpret_cast<__nv_bfloat162*>(pk);
 #pragma unroll
-                            for (int h = 0; h < 2; ++h) {
-                                const uint4 raw = ad[h];
-                                const __nv_bfloat162* pr = reinterpret_cast<const __nv_bfloat162*>(&raw);
+                    for (int e = 0; e < EC / 2; ++e) pp[e] = __floats2bfloat162_rn(o[2 * e], o[2 * e + 1]);
+                    uint4* yo = reinterpret_cast<uint4*>(static_cast<bf16*>(y) + v * COUT + c_lo);
 #pragma unroll
-                                for (int e = 0; e < 4; ++e) {
-                                    o[8 * h + 2 * e] += __bfloat162float(pr[e].x);
-                                    o[8 * h + 2 * e + 1] += __bfloat162float(pr[e].y);
-                                }
-                            }
-                        }
-                    }
-                    if (epi.y_f32) {
-                        float4* yo = reinterpret_cast<float4*>(static_cast<float*>(y) + v * COUT + c0);
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) yo[e] = make_float4(o[4 * e], o[4 * e + 1], o[4 * e + 2], o[4 * e + 3]);
-                    } else {
-                        uint4 pk[2];
-                        __nv_bfloat162* pp = reinterpret_cast<__nv_bfloat162*>(pk);
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) pp[e] = __floats2bfloat162_rn(o[2 * e], o[2 * e + 1]);
-                        uint4* yo = reinterpret_cast<uint4*>(static_cast<bf16*>(y) + v * COUT + c0);
-                        yo[0] = pk[0];
-                        yo[1] = pk[1];
-                    }
+                    for (int h = 0; h < EC / 8; ++h) yo[h] = pk[h];
                 }
             }
         }
@@ -906,7 +917,7 @@ __global__ void __launch_bounds__(256, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS));
 }
 
-static int g_fwd_impl = SG_CONV_MMA_SYNC;  // forward convolution kernel (sg_set_conv_impl)
+static int g_fwd_impl = SG_CONV_TCGEN05;  // forward convolution kernel (sg_set_conv_impl)
 
 // cuTensorMapEncodeTiled from the driver, found once through the runtime (no link-time driver dependency)
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {

@@ -67,7 +67,7 @@ def _ok(rc, name):
 
 
 def set_conv_impl(impl):
-    """Select the forward-convolution kernel (CONV_MMA_SYNC, the default, or CONV_TCGEN05);
+    """Select the forward-convolution kernel (CONV_TCGEN05, the default, or CONV_MMA_SYNC);
     returns the previous one."""
     prev = _L().sg_set_conv_impl(int(impl))
     if prev < 0:
