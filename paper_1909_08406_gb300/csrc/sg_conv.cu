@@ -524,9 +524,10 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
 // tcgen05.mma M=128 x N=cout x K=16 per tap and 16-channel slice).  A CTA
 // walks columns of ZC tiles along z (same batch item and row pair); for each
 // 16-channel slice it streams the column's ZC + 2 halo planes (4 rows x 64
-// voxels x 16 channels, in the three x-shifted copies) through a ring of 4
+// voxels x 16 channels, in the three x-shifted copies) through a ring of 6
 // plane slots, so each plane is loaded once per column instead of once per
-// tile, and tile k of the column uses the slots of planes k, k+1, k+2.
+// tile, tile k of the column uses the slots of planes k, k+1, k+2, and the
+// producer runs up to three planes ahead of the MMAs.
 // Operand A uses the 32-byte-swizzled K-major layout (rows of 16 channels =
 // 32 B, 8-row atoms of 256 B), which the TMA writes directly
 // (CU_TENSOR_MAP_SWIZZLE_32B); B stays in the no-swizzle layout.  Warp roles:
@@ -566,7 +567,7 @@ struct TczCfg {
     static constexpr int SL = CIN / 16;                 // 16-channel K slices
     static constexpr int HY = 4;                        // halo rows of a 2-row tile
     static constexpr int ZC = 4;                        // tiles per column along z
-    static constexpr int NSLOT = 4;                     // plane slots in the ring
+    static constexpr int NSLOT = 6;                     // plane slots in the ring (3 in use, 3 ahead)
     static constexpr int COPYB = HY * kW * 32;          // one x-shifted copy of one plane: 8 KB
     static constexpr int SLOT = 3 * COPYB;              // 24 KB
     static constexpr int A_BYTES = NSLOT * SLOT;
@@ -617,14 +618,14 @@ __global__ void __launch_bounds__(384, 1)
                    void* y, long long wait_limit) {
     using C = TczCfg<CIN, COUT>;
     extern __shared__ __align__(1024) unsigned char sm_tcz[];
-    // barriers: TMA landed [4], slot full [4], slot empty [4], accumulator full [8], accumulator empty [8], drain
-    __shared__ __align__(8) uint64_t bars[4 + 4 + 4 + 2 * C::NACC + 1];
+    // barriers: TMA landed, slot full, slot empty [NSLOT each], accumulator full, accumulator empty [NACC each], drain
+    __shared__ __align__(8) uint64_t bars[3 * C::NSLOT + 2 * C::NACC + 1];
     __shared__ uint32_t tmem_holder;
     const uint32_t base = (smem_u32(sm_tcz) + 1023u) & ~1023u;
     unsigned char* smem = sm_tcz + (base - smem_u32(sm_tcz));
     const uint32_t a_s = base, b_s = base + C::A_BYTES;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    constexpr int LT = 0, FU = 4, EM = 8, AF = 12, AE = 12 + C::NACC, DR = 12 + 2 * C::NACC;
+    constexpr int LT = 0, FU = C::NSLOT, EM = 2 * C::NSLOT, AF = 3 * C::NSLOT, AE = AF + C::NACC, DR = AE + C::NACC;
     auto bar = [&](int k) { return smem_u32(&bars[k]); };
 
     // weights of all taps: B[tap][k8][co][8 channels] <- w[co][tap][k8 * 8 ..]
@@ -811,6 +812,9 @@ __global__ void __launch_bounds__(384, 1)
         const int c_lo = half * EC;
         const int m = 32 * quarter + lane;
         const int yl = m >> 6, xx = m & 63;
+        float bv[EC];
+#pragma unroll
+        for (int e = 0; e < EC; ++e) bv[e] = bias ? bias[c_lo + e] : 0.f;
         int64_t u = 0;
         bool ok = true;
         for (int64_t c = blockIdx.x; c < ncols && ok; c += gridDim.x, ++u) {
@@ -844,7 +848,7 @@ __global__ void __launch_bounds__(384, 1)
                 float o[EC];
 #pragma unroll
                 for (int e = 0; e < EC; ++e) {
-                    const float zj = zc[e] + (bias ? bias[c_lo + e] : 0.f);
+                    const float zj = zc[e] + bv[e];
                     zc[e] = zj;
                     o[e] = epi.act == SG_ACT_GELU ? gelu(zj) : zj;
                 }
