@@ -491,6 +491,21 @@ __device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t a, uint64_t b, ui
         "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+// Warp-uniform issue: every lane forms the same operands (so they live in uniform registers) and
+// one elected lane issues the instruction.
+__device__ __forceinline__ void tc_mma_elect(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p, e;\n\tsetp.ne.u32 p, %4, 0;\n\telect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void tc_commit_elect(uint32_t bar) {
+    asm volatile(
+        "{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}" ::"r"(bar)
+        : "memory");
+}
+
 __device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity, long long limit) {
     const long long t0 = clock64();
     for (;;) {
@@ -540,7 +555,8 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
 //   warp 1               periodic-wrap fixer: writes those voxels (loaded from
 //                        global memory before the box lands) and marks the slot
 //                        full.
-//   warp 2 (one thread)  MMA issuer: 27 MMAs per tile and slice into one of
+//   warp 2               MMA issuer (warp-uniform loop, one elected lane issues):
+//                        27 MMAs per tile and slice into one of
 //                        2 x ZC accumulators in tensor memory; tcgen05.commit
 //                        frees plane slots and fills accumulators.
 //   warps 4-11           epilogue (two per tensor-memory lane quarter, half the
@@ -739,8 +755,8 @@ __global__ void __launch_bounds__(384, 1)
                     if (lane == 0) tp_arrive(bar(FU + slot));
                 }
         }
-    } else if (warp == 2 && lane == 0) {
-        // ---- MMA issuer ----
+    } else if (warp == 2) {
+        // ---- MMA issuer: the whole warp runs the loop (warp-uniform operands), one lane issues ----
         uint32_t q = 0;  // sequence number of the first plane of the current (column, slice)
         int64_t u = 0;   // column ordinal of this CTA
         bool ok = true;
@@ -752,26 +768,27 @@ __global__ void __launch_bounds__(384, 1)
                     const uint32_t au = (uint32_t)(u >> 1);
                     if (k >= K.len) {
                         // a short last chunk: keep every accumulator's barrier phases in step
-                        if (j == 0 && !tc_wait(bar(AE + acc), (au & 1) ^ 1, wait_limit)) {
-                            fail();
+                        if (j == 0 && !__all_sync(0xffffffffu, tc_wait(bar(AE + acc), (au & 1) ^ 1, wait_limit))) {
+                            if (lane == 0) fail();
                             ok = false;
                             break;
                         }
-                        if (j == C::SL - 1) tp_commit(bar(AF + acc));
+                        if (j == C::SL - 1) tc_commit_elect(bar(AF + acc));
                         continue;
                     }
                     // planes k, k + 1, k + 2 of this slice must be in their slots
                     for (int p = (k == 0 ? 0 : k + 2); p <= k + 2; ++p) {
                         const uint32_t qq = q + p;
-                        if (!tc_wait(bar(FU + (int)(qq % C::NSLOT)), (qq / C::NSLOT) & 1, wait_limit)) {
-                            fail();
+                        if (!__all_sync(0xffffffffu, tc_wait(bar(FU + (int)(qq % C::NSLOT)), (qq / C::NSLOT) & 1,
+                                                             wait_limit))) {
+                            if (lane == 0) fail();
                             ok = false;
                             break;
                         }
                     }
                     if (!ok) break;
-                    if (j == 0 && !tc_wait(bar(AE + acc), (au & 1) ^ 1, wait_limit)) {
-                        fail();
+                    if (j == 0 && !__all_sync(0xffffffffu, tc_wait(bar(AE + acc), (au & 1) ^ 1, wait_limit))) {
+                        if (lane == 0) fail();
                         ok = false;
                         break;
                     }
@@ -789,22 +806,22 @@ __global__ void __launch_bounds__(384, 1)
                         constexpr int dz = TAP / 9, dy = (TAP / 3) % 3, dxi = TAP % 3;  // each + 1
                         constexpr uint64_t aoff = (uint64_t)((dxi * C::COPYB + dy * kW * 32) >> 4);
                         constexpr uint64_t boff = (uint64_t)((TAP * C::WTAP) >> 4);
-                        tc_mma(d_tmem, a_pl[dz] + aoff, b0 + boff, C::IDESC, TAP == 0 ? first : 1u);
+                        tc_mma_elect(d_tmem, a_pl[dz] + aoff, b0 + boff, C::IDESC, TAP == 0 ? first : 1u);
                     });
                     // plane k is not used by later tiles of this slice; the last tile frees all three
-                    tp_commit(bar(EM + (int)((q + k) % C::NSLOT)));
+                    tc_commit_elect(bar(EM + (int)((q + k) % C::NSLOT)));
                     if (k == K.len - 1) {
-                        tp_commit(bar(EM + (int)((q + k + 1) % C::NSLOT)));
-                        tp_commit(bar(EM + (int)((q + k + 2) % C::NSLOT)));
+                        tc_commit_elect(bar(EM + (int)((q + k + 1) % C::NSLOT)));
+                        tc_commit_elect(bar(EM + (int)((q + k + 2) % C::NSLOT)));
                     }
-                    if (j == C::SL - 1) tp_commit(bar(AF + acc));
+                    if (j == C::SL - 1) tc_commit_elect(bar(AF + acc));
                 }
                 q += K.len + 2;
             }
         }
-        // every MMA this thread issued has completed before tensor memory can be freed
-        tp_commit(bar(DR));
-        if (!tc_wait(bar(DR), 0, wait_limit)) fail();
+        // every MMA this warp issued has completed before tensor memory can be freed
+        tc_commit_elect(bar(DR));
+        if (!__all_sync(0xffffffffu, tc_wait(bar(DR), 0, wait_limit)) && lane == 0) fail();
     } else if (warp >= 4) {
         // ---- epilogue: warp reads lanes 32 (warp % 4) .. + 31 and columns half * cout / 2 .. + cout / 2 ----
         const int quarter = warp & 3, half = (warp - 4) >> 2;
