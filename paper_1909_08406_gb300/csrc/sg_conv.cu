@@ -506,6 +506,13 @@ __device__ __forceinline__ void tc_commit_elect(uint32_t bar) {
         : "memory");
 }
 
+// true in exactly one lane of the (converged) warp
+__device__ __forceinline__ bool elect_one() {
+    uint32_t e;
+    asm volatile("{\n\t.reg .pred p;\n\telect.sync _|p, 0xffffffff;\n\tselp.b32 %0, 1, 0, p;\n}" : "=r"(e));
+    return e != 0;
+}
+
 __device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity, long long limit) {
     const long long t0 = clock64();
     for (;;) {
@@ -546,7 +553,8 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
 // Operand A uses the 32-byte-swizzled K-major layout (rows of 16 channels =
 // 32 B, 8-row atoms of 256 B), which the TMA writes directly
 // (CU_TENSOR_MAP_SWIZZLE_32B); B stays in the no-swizzle layout.  Warp roles:
-//   warp 0 (one thread)  TMA producer: per plane slot one box of 16 channels x
+//   warp 0               TMA producer (warp-uniform loop, one elected lane issues):
+//                        per plane slot one box of 16 channels x
 //                        64 voxels x 4 rows per x-shifted copy (or one box per
 //                        row where the rows wrap around the periodic y
 //                        boundary; z wraps per plane).  A box shifted by -1 /
@@ -685,8 +693,9 @@ __global__ void __launch_bounds__(384, 1)
     };
     auto fail = [&]() { atomicOr(&g_sg_status, 1); };
 
-    if (warp == 0 && lane == 0) {
-        // ---- TMA producer: plane loads in order (column, slice, plane) ----
+    if (warp == 0) {
+        // ---- TMA producer: plane loads in order (column, slice, plane); the whole warp runs the
+        // loop (warp-uniform coordinates), one elected lane issues ----
         uint32_t q = 0;  // plane-load sequence number
         int last_slot = -1;
         uint32_t last_parity = 0;
@@ -698,29 +707,34 @@ __global__ void __launch_bounds__(384, 1)
                 for (int p = 0; p < K.len + 2; ++p, ++q) {
                     const int slot = (int)(q % C::NSLOT);
                     const uint32_t use = q / C::NSLOT;
-                    if (!tc_wait(bar(EM + slot), (use & 1) ^ 1, wait_limit)) {
-                        fail();
+                    if (!__all_sync(0xffffffffu, tc_wait(bar(EM + slot), (use & 1) ^ 1, wait_limit))) {
+                        if (lane == 0) fail();
                         ok = false;
                         break;
                     }
-                    tp_expect_tx(bar(LT + slot), C::SLOT);
                     last_slot = slot;
                     last_parity = use & 1;
                     const int zz = wrapi(K.z0 - 1 + p, s.nz);
-                    for (int d = 0; d < 3; ++d) {
-                        const uint32_t dst = a_s + (uint32_t)(slot * C::SLOT + d * C::COPYB);
-                        if (y_inside) {
-                            tp_tma5(dst, &xrows, 16 * j, d - 1, K.y0 - 1, zz, K.b, bar(LT + slot));
-                        } else {
-                            for (int r = 0; r < C::HY; ++r)
-                                tp_tma5(dst + (uint32_t)(r * kW * 32), &xrow, 16 * j, d - 1, wrapi(K.y0 + r - 1, s.ny),
-                                        zz, K.b, bar(LT + slot));
+                    if (elect_one()) {
+                        tp_expect_tx(bar(LT + slot), C::SLOT);
+                        for (int d = 0; d < 3; ++d) {
+                            const uint32_t dst = a_s + (uint32_t)(slot * C::SLOT + d * C::COPYB);
+                            if (y_inside) {
+                                tp_tma5(dst, &xrows, 16 * j, d - 1, K.y0 - 1, zz, K.b, bar(LT + slot));
+                            } else {
+                                for (int r = 0; r < C::HY; ++r)
+                                    tp_tma5(dst + (uint32_t)(r * kW * 32), &xrow, 16 * j, d - 1,
+                                            wrapi(K.y0 + r - 1, s.ny), zz, K.b, bar(LT + slot));
+                            }
                         }
                     }
+                    __syncwarp();
                 }
         }
         // the CTA must not exit with boxes still landing
-        if (last_slot >= 0 && !tc_wait(bar(LT + last_slot), last_parity, wait_limit)) fail();
+        if (last_slot >= 0 && !__all_sync(0xffffffffu, tc_wait(bar(LT + last_slot), last_parity, wait_limit)) &&
+            lane == 0)
+            fail();
     } else if (warp == 1) {
         // ---- periodic-wrap fixer: copy 0 voxel 0 <- in[63], copy 2 voxel 63 <- in[0], 4 rows ----
         uint32_t q = 0;
