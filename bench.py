@@ -387,8 +387,9 @@ def main():
         io = 5 * nodes * 8
         e2e = {"value": world * nodes * args.steps / el / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": io / args.steps, "d2h_bytes_per_step": io / args.steps,
-               "seconds": el, "note": "lb_set_fields from pinned host (rho,u,theta f64), "
-                                      "K x lb_step, lb_get_moments to pinned host"}
+               "seconds": el, "note": "lb_set_fields from pinned host (rho,u,theta f64, read by the "
+                                      "kernel over the host link), K x lb_step, lb_get_moments to pinned "
+                                      "host"}
 
     if rank != 0:
         return

@@ -119,7 +119,10 @@ lb_status lb_set_stream(lb_ctx *ctx, void *cuda_stream);
 
 /* Set the populations to the equilibrium (Eq. feqGenU3) of the given fields:
  * rho[s][z][y][x], u[3][s][z][y][x], theta[s][z][y][x] (float64).  The stored
- * state is then the post-collision state at t = 0. */
+ * state is then the post-collision state at t = 0.  on_device = 0: host arrays.
+ * Page-locked (pinned) host arrays are read by the kernel directly over the
+ * host link; pageable ones are copied through a device staging buffer in
+ * chunks.  Returns after the host arrays have been read. */
 lb_status lb_set_fields(lb_ctx *ctx, const double *rho, const double *u, const double *theta, int on_device);
 
 /* Advance n >= 0 time steps: each step streams (pull) and collides every node
@@ -128,7 +131,9 @@ lb_status lb_step(lb_ctx *ctx, int64_t n);
 
 /* Node moments of the current state: rho, u = j/rho, theta = (<f,c^2>/rho - u^2)/3
  * (Sec. II), into caller arrays in the field layouts above.  Any output
- * pointer may be NULL. */
+ * pointer may be NULL.  Host outputs (on_device = 0) are complete on return;
+ * page-locked ones are written by the kernel directly, pageable ones through
+ * the staging buffer. */
 lb_status lb_get_moments(lb_ctx *ctx, double *rho, double *u, double *theta, int on_device);
 
 /* Global sums in FP64, deterministic order: out[0] = mass sum <f,1>,

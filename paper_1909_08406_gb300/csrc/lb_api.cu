@@ -143,6 +143,19 @@ static lb_status fail(lb_ctx* c, lb_status s, const std::string& m) {
 
 static int64_t nodes_of(const lb_ctx* c) { return 2 * c->d.plane; }
 
+// Device address of a host array that kernels can read and write directly: page-locked
+// (pinned) host memory, mapped into the device's address space.  nullptr for pageable memory,
+// which goes through the staging buffer instead.
+static const void* mapped_host_view(const void* p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();  // clear the error of an unknown pointer
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // Staging buffer for host transfers (float64), allocated on first use.
 static lb_status ensure_stage(lb_ctx* c) {
     if (c->d_stage) return LB_OK;
@@ -327,8 +340,15 @@ lb_status lb_set_fields(lb_ctx* c, const double* rho, const double* u, const dou
     const int64_t n = nodes_of(c);
     const LaunchConsts& lc = lattice().lc;
     void* dst = c->buf[c->cur];
+    const double* mr = on_device ? nullptr : static_cast<const double*>(mapped_host_view(rho));
+    const double* mu = on_device ? nullptr : static_cast<const double*>(mapped_host_view(u));
+    const double* mt = on_device ? nullptr : static_cast<const double*>(mapped_host_view(theta));
     if (on_device) {
         CK(c, launch_init(c->prec, c->eq, dst, c->d, lc, 0, n, rho, u, n, theta, c->d_err, c->stream));
+    } else if (mr && mu && mt) {
+        // pinned host arrays: the kernel reads them over the host link, no staging copies
+        CK(c, launch_init(c->prec, c->eq, dst, c->d, lc, 0, n, mr, mu, n, mt, c->d_err, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
     } else {
         lb_status s = ensure_stage(c);
         if (s != LB_OK) return s;
@@ -373,6 +393,16 @@ lb_status lb_get_moments(lb_ctx* c, double* rho, double* u, double* theta, int o
     if (on_device) {
         CK(c, launch_moments(c->prec, src, c->d, lc, 0, n, rho, u, n, theta, c->stream));
         return LB_OK;
+    }
+    {
+        // pinned host arrays (every one that is requested): the kernel writes them directly
+        double* mr = static_cast<double*>(const_cast<void*>(mapped_host_view(rho)));
+        double* mu = static_cast<double*>(const_cast<void*>(mapped_host_view(u)));
+        double* mt = static_cast<double*>(const_cast<void*>(mapped_host_view(theta)));
+        if ((!rho || mr) && (!u || mu) && (!theta || mt)) {
+            CK(c, launch_moments(c->prec, src, c->d, lc, 0, n, mr, mu, n, mt, c->stream));
+            return lb_sync(c);
+        }
     }
     lb_status s = ensure_stage(c);
     if (s != LB_OK) return s;

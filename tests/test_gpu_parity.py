@@ -316,3 +316,39 @@ def test_free_streaming_time_counter():
         assert lb.lb_time(ctx) == 3
     finally:
         lb.lb_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f16"])
+def test_pinned_host_fields_match_device_path(prec):
+    """lb_set_fields / lb_get_moments with page-locked host arrays (read and written by the kernels
+    over the host link), pageable host arrays (staging buffer) and device arrays give the same
+    state and the same moments, bit for bit."""
+    shape = (20, 6, 5)
+    th0 = lb.lb_theta0()
+    fl = wl.random_fields(*shape, th0, seed=44, du=0.02, drho=0.02, dtheta=0.02)
+    pinned = {k: v.clone().pin_memory() for k, v in fl.items()}
+    pageable = {k: v.clone() for k, v in fl.items()}
+    device = {k: v.cuda() for k, v in fl.items()}
+    outs = []
+    for src, where in ((pinned, "host"), (pageable, "host"), (device, "device")):
+        ctx = lb.lb_init(shape, 0.3, prec)
+        try:
+            lb.lb_set_fields(ctx, src["rho"], src["u"], src["theta"])
+            lb.lb_step(ctx, 3)
+            state = np.empty(lb.lb_state_bytes(ctx), dtype=np.uint8)
+            lb.lb_get_state(ctx, state)
+            if where == "device":
+                m = {k: torch.empty_like(v) for k, v in device.items()}
+            elif src is pinned:
+                m = {k: torch.empty_like(v).pin_memory() for k, v in fl.items()}
+            else:
+                m = {k: torch.empty_like(v) for k, v in fl.items()}
+            lb.lb_get_moments(ctx, m["rho"], m["u"], m["theta"])
+            lb.lb_sync(ctx)
+        finally:
+            lb.lb_destroy(ctx)
+        outs.append((state, {k: v.cpu() for k, v in m.items()}))
+    for state, m in outs[1:]:
+        assert np.array_equal(state, outs[0][0])
+        for k in m:
+            assert torch.equal(m[k], outs[0][1][k]), k
