@@ -201,9 +201,14 @@ __device__ __forceinline__ void step_node2(const typename Codec::raw_t* __restri
 // (s, z, y, x + 1), x even, packed FP32x2 arithmetic.  Each plane is read as
 // aligned pairs of 16-bit values: one 32-bit load when the plane's x shift is
 // even, two loads and a byte permute when it is odd; the two results of a
-// plane are written with one 32-bit store.  RowAddr2x holds the row offsets of
-// one row (s, z, y); load_pair2x forms population I's upwind pair from them.
-// Requires nx even and nx * ny * nz < 2^32.
+// plane are written with one 32-bit store.
+//
+// A block covers one chunk of x for `rpb` consecutive rows (s, z, y), y
+// fastest.  The loads of the next row are software-pipelined into the
+// registers of the current one: as soon as population I of the current row
+// has been relaxed and stored, its register receives population I of the next
+// row, so a row's loads are in flight while the previous row is still being
+// relaxed.  Requires nx even and nx * ny * nz < 2^32.
 template <class Codec>
 struct RowAddr2x {
     using T = typename Codec::raw_t;
@@ -357,123 +362,6 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Co
         P* outp = reinterpret_cast<P*>(dst + (size_t)s * kQ * d.plane + ((uint32_t)z * nxy + (uint32_t)y * nx + x0));
         equilibrium_relax_g<C2, PROJECT>(st, K, F2(tb * (float)Codec::kScale), F2(1.f - tb), vget,
                                          [&](auto I, F2 val) { outp[(size_t)I * (plane / 2)] = Codec::to_raw2(val.v); });
-        s = sn;
-        z = zn;
-        y = yn;
-    }
-}
-
-// Upwind pairs of population I for rows y (out_a) and y + 1 (out_b) of the
-// same plane.  FAST: no source row of either row wraps around the periodic y
-// boundary, so row y + 1's source rows are row y's shifted by one row (nx
-// elements); otherwise b holds row y + 1's own offsets.
-template <class Codec, int I, bool FAST>
-__device__ __forceinline__ void load_pair2x_rows(const RowAddr2x<Codec>& a, const RowAddr2x<Codec>& b,
-                                                 uint32_t plane, uint32_t nx, uint32_t xm, uint32_t x0, uint32_t xq,
-                                                 typename Codec::pair_t& out_a, typename Codec::pair_t& out_b) {
-    using T = typename Codec::raw_t;
-    using P = typename Codec::pair_t;
-    constexpr Vel c = vel(I);
-    auto ld = [&](const T* p, uint32_t off) { return LoadNC::load(reinterpret_cast<const P*>(p + off)); };
-    auto pair_at = [&](const T* p, int dx) -> P {
-        switch (dx) {
-            case 2: return ld(p, xm);
-            case 1: return Codec::straddle(ld(p, xm), ld(p, x0));
-            case 0: return ld(p, x0);
-            case -1: return Codec::straddle(ld(p, x0), ld(p, xq));
-            default: return ld(p, xq);
-        }
-    };
-    const T* pa;
-    const T* pb;
-    int dx;
-    if constexpr (c.shell == 5) {
-        pa = a.other + (size_t)I * plane + ((c.z > 0 ? a.hzp : a.hzm) + (c.y > 0 ? a.hyp : a.hym));
-        pb = FAST ? pa + nx : b.other + (size_t)I * plane + ((c.z > 0 ? b.hzp : b.hzm) + (c.y > 0 ? b.hyp : b.hym));
-        dx = c.x > 0 ? 1 - a.s : -a.s;  // x shift 1 - s for a +1/2 component, -s for -1/2
-    } else {
-        pa = a.same + (size_t)I * plane + (a.zo[c.z / 2 + 2] + a.yo[c.y / 2 + 2]);
-        pb = FAST ? pa + nx : b.same + (size_t)I * plane + (b.zo[c.z / 2 + 2] + b.yo[c.y / 2 + 2]);
-        dx = c.x / 2;
-    }
-    out_a = pair_at(pa, dx);
-    out_b = pair_at(pb, dx);
-}
-
-// x pairs in two rows per thread: nodes (x, x + 1) of rows y and y + 1 (y
-// even) of one plane, FP32x2 arithmetic per row.  The uniform bookkeeping of
-// the row addresses is shared by the two rows (row y + 1's source rows are row
-// y's shifted by one row wherever nothing wraps in y), and both rows' loads
-// are in flight together.  A block covers one chunk of x for `rpb`
-// consecutive row pairs; at the start of a pair, threads 0..81 issue L2 bulk
-// prefetches of the next pair's source rows.  Requires nx and ny even and
-// nx * ny * nz < 2^32.
-template <class Codec, bool PROJECT, int MINB>
-__global__ void __launch_bounds__(kStepThreads, MINB) k_step2x2(const typename Codec::raw_t* __restrict__ src,
-                                                          typename Codec::raw_t* __restrict__ dst, Dims d,
-                                                          Consts<float> K, float tb, int* __restrict__ err,
-                                                          int chunks, int rpb) {
-    using T = typename Codec::raw_t;
-    using P = typename Codec::pair_t;
-    using C2 = Codec2<Codec>;
-    const uint32_t t = blockIdx.x;
-    const uint32_t grp = t / (uint32_t)chunks;
-    const int chunk = (int)(t - grp * (uint32_t)chunks);
-    const int x = 2 * (chunk * (int)blockDim.x + (int)threadIdx.x);
-    const int xa = 2 * chunk * (int)blockDim.x, xb = min(xa + 2 * (int)blockDim.x, d.nx);
-    const uint32_t npairs = (uint32_t)d.rows / 2;
-    const uint32_t p0 = grp * (uint32_t)rpb;
-    const uint32_t p1 = min(p0 + (uint32_t)rpb, npairs);
-    const uint32_t r0 = 2 * p0;
-    int y = (int)(r0 % (uint32_t)d.ny);
-    const uint32_t zr = r0 / (uint32_t)d.ny;
-    int z = (int)(zr % (uint32_t)d.nz);
-    int s = (int)(zr / (uint32_t)d.nz);
-    const bool active = x < d.nx;
-    if (!active && threadIdx.x >= 2 * kQ) return;
-    const uint32_t nx = (uint32_t)d.nx, nxy = (uint32_t)d.nx * (uint32_t)d.ny;
-    const uint32_t plane = (uint32_t)d.plane;
-    const uint32_t xm = (uint32_t)wrap(x - 2, d.nx), x0 = (uint32_t)x, xq = (uint32_t)wrap(x + 2, d.nx);
-    constexpr float inv_scale = (float)(1.0 / Codec::kScale);
-
-    P pa[kQ], pb[kQ];
-    // moments, equilibrium, relaxation and store of one row from its upwind pairs
-    auto update_row = [&](P(&pv)[kQ], int yy) {
-        auto vget = [&](auto I) { return F2(Codec::unpack2(pv[I])); };
-        const NodeMoments<F2> m =
-            moments_from<F2>([&](auto I) { return C2::dev(vget(I), F2(K.w[vel(I).shell] * inv_scale)); });
-        const NodeState<F2> st = state_from_moments(m, K);
-        if (!state_ok(st)) atomicOr(err, 1);
-        P* outp = reinterpret_cast<P*>(dst + (size_t)s * kQ * d.plane + ((uint32_t)z * nxy + (uint32_t)yy * nx + x0));
-        equilibrium_relax_g<C2, PROJECT>(st, K, F2(tb * (float)Codec::kScale), F2(1.f - tb), vget,
-                                         [&](auto I, F2 val) { outp[(size_t)I * (plane / 2)] = Codec::to_raw2(val.v); });
-    };
-
-    for (uint32_t p = p0; p < p1; ++p) {
-        // the next row pair, in (s, z, y) order
-        int yn = y + 2, zn = z, sn = s;
-        if (yn >= d.ny) {
-            yn = 0;
-            if (++zn == d.nz) {
-                zn = 0;
-                ++sn;
-            }
-        }
-        const bool more = p + 1 < p1;
-        if (more && threadIdx.x < 2 * kQ)
-            prefetch_row_l2<Codec>(src, d, (int)threadIdx.x % kQ, sn, zn, yn + (int)threadIdx.x / kQ, xa, xb);
-        if (active) {
-            RowAddr2x<Codec> a, b;
-            a.set(src, d, s, z, y);
-            if (y >= 2 && y + 3 < d.ny) {
-                static_for<kQ>([&](auto I) { load_pair2x_rows<Codec, I, true>(a, a, plane, nx, xm, x0, xq, pa[I], pb[I]); });
-            } else {
-                b.set(src, d, s, z, y + 1);
-                static_for<kQ>([&](auto I) { load_pair2x_rows<Codec, I, false>(a, b, plane, nx, xm, x0, xq, pa[I], pb[I]); });
-            }
-            update_row(pa, y);
-            update_row(pb, y + 1);
-        }
         s = sn;
         z = zn;
         y = yn;

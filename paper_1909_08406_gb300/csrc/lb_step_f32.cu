@@ -55,25 +55,6 @@ static cudaError_t run_direct2x(const void* src, void* dst, const Dims& d, const
     }
 }
 
-template <class Codec, bool P, int MINB>
-static cudaError_t run_direct2x2(const void* src, void* dst, const Dims& d, const LaunchConsts& c, double twobeta,
-                                 int* err, cudaStream_t st, int rpb) {
-    using T = typename Codec::raw_t;
-    if constexpr (sizeof(T) != 2) {
-        return cudaErrorInvalidValue;
-    } else {
-        const int half = d.nx / 2;
-        // at least 96 threads: threads 0 .. 81 issue the prefetches of the next row pair
-        const int th = half >= 128 ? 128 : (half <= 96 ? 96 : 128);
-        const int chunks = (half + th - 1) / th;
-        const int64_t npairs = d.rows / 2;
-        const int64_t blocks = ((npairs + rpb - 1) / rpb) * chunks;
-        k_step2x2<Codec, P, MINB><<<(unsigned)blocks, th, 0, st>>>(
-            static_cast<const T*>(src), static_cast<T*>(dst), d, c.kf, (float)twobeta, err, chunks, rpb);
-        return cudaGetLastError();
-    }
-}
-
 // Per-instance launch data: dynamic shared memory opt-in and the persistent grid size.
 struct TmaLaunchInfo {
     int device = -1;
@@ -182,9 +163,6 @@ int resolve_kernel(int prec, const Dims& d, int kernel) {
             return (storage_bytes(prec) == 2 && d.nx % 2 == 0 && d.plane < ((int64_t)1 << 32))
                        ? kernel
                        : resolve_kernel(prec, d, kKernelAuto);
-        case kKernelDirect2X2:
-            return (storage_bytes(prec) == 2 && d.nx % 2 == 0 && two_rows) ? kernel
-                                                                           : resolve_kernel(prec, d, kKernelAuto);
         case kKernelWarpSpec:
             return (two_rows && d.nx % 128 == 0 && tma_tile_width(prec, d)) ? kKernelWarpSpec
                                                                              : resolve_kernel(prec, d, kKernelAuto);
@@ -209,7 +187,6 @@ static cudaError_t step_codec(int prec, int kernel, const void* src, void* dst, 
         case kKernelWarpSpec: return run_ws<Codec, P, typename WsShape<Codec>::Cfg>(src, dst, d, c, twobeta, err, st);
         case kKernelDirect2X: return run_direct2x<Codec, P, 3, 0>(src, dst, d, c, twobeta, err, st, 1);
         case kKernelDirect2XL: return run_direct2x<Codec, P, 3, 2>(src, dst, d, c, twobeta, err, st, 2);
-        case kKernelDirect2X2: return run_direct2x2<Codec, P, 2>(src, dst, d, c, twobeta, err, st, 2);
 
         case kKernelDirect2: return run_direct2<Codec, P, 3>(src, dst, d, c, twobeta, err, st);
         case kKernelDirect2R: return run_direct2<Codec, P, 4>(src, dst, d, c, twobeta, err, st);
