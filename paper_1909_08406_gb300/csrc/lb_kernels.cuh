@@ -265,16 +265,16 @@ __device__ __forceinline__ typename Codec::pair_t load_pair2x(const RowAddr2x<Co
     }
 }
 
-// Prefetch into L2 the part of population I's source row that the nodes
-// [xa, xb) of the row (s, z, y) will read (x - 2 .. x + 2, not wrapped),
-// trimmed inward to whole 16-byte units of that row.
+// Start of population I's source row (element x = 0) for the nodes of row
+// (s, z, y): integer links stay on the sub-lattice and shift by c / 2 cells;
+// bcc-1/2 links read the other sub-lattice with delta = 1 - s for a +1/2
+// component and -s for -1/2.
 template <class Codec>
-__device__ __forceinline__ void prefetch_row_l2(const typename Codec::raw_t* src, const Dims& d, int I, int s, int z,
-                                                int y, int xa, int xb) {
-    using T = typename Codec::raw_t;
+__device__ __forceinline__ const typename Codec::raw_t* source_row(const typename Codec::raw_t* src, const Dims& d,
+                                                                   int I, int s, int z, int y) {
     const Vel c = c_vel.v[I];
     int sp, dz, dy;
-    if (c.shell == 5) {  // half link: delta = 1 - s for +1/2, -s for -1/2; other sub-lattice
+    if (c.shell == 5) {
         sp = 1 - s;
         dz = c.z > 0 ? 1 - s : -s;
         dy = c.y > 0 ? 1 - s : -s;
@@ -284,12 +284,26 @@ __device__ __forceinline__ void prefetch_row_l2(const typename Codec::raw_t* src
         dy = c.y / 2;
     }
     const int zz = wrap(z - dz, d.nz), yy = wrap(y - dy, d.ny);
-    const int lo = max(xa - 2, 0), hi = min(xb + 2, d.nx);
-    const T* row = src + ((size_t)sp * kQ + I) * d.plane + ((size_t)zz * d.ny + yy) * d.nx;
+    return src + ((size_t)sp * kQ + I) * d.plane + ((size_t)zz * d.ny + yy) * d.nx;
+}
+
+// Prefetch into L2 the part [xa - 2, xb + 2) of a source row (not wrapped),
+// trimmed inward to whole 16-byte units of that row.
+template <class T>
+__device__ __forceinline__ void prefetch_span_l2(const T* row, int xa, int xb, int nx) {
+    const int lo = max(xa - 2, 0), hi = min(xb + 2, nx);
     const uintptr_t b0 = ((uintptr_t)(row + lo) + 15) & ~(uintptr_t)15;
     const uintptr_t b1 = ((uintptr_t)(row + hi)) & ~(uintptr_t)15;
     if (b1 > b0)
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b0), "r"((uint32_t)(b1 - b0)) : "memory");
+}
+
+// Prefetch into L2 the part of population I's source row that the nodes
+// [xa, xb) of the row (s, z, y) will read.
+template <class Codec>
+__device__ __forceinline__ void prefetch_row_l2(const typename Codec::raw_t* src, const Dims& d, int I, int s, int z,
+                                                int y, int xa, int xb) {
+    prefetch_span_l2(source_row<Codec>(src, d, I, s, z, y), xa, xb, d.nx);
 }
 
 // How a block of the x-pair kernel gets a row's upwind values:
@@ -297,6 +311,10 @@ __device__ __forceinline__ void prefetch_row_l2(const typename Codec::raw_t* src
 // MODE 2: as MODE 0, plus an L2 bulk prefetch of the next row's source rows
 //         (one per population, by threads 0..40) at the start of the current
 //         row, so that the next row's loads hit in L2.
+// MODE 3: as MODE 2, and the same threads 0..40 also write the next row's 41
+//         source-row pointers into a shared table (double-buffered, one block
+//         barrier per row); every warp reads its row's pointers from there
+//         instead of forming them itself.
 template <class Codec, bool PROJECT, int MINB, int MODE>
 __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Codec::raw_t* __restrict__ src,
                                                          typename Codec::raw_t* __restrict__ dst, Dims d,
@@ -317,7 +335,9 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Co
     int z = (int)(zr % (uint32_t)d.nz);
     int s = (int)(zr / (uint32_t)d.nz);
     const bool active = x < d.nx;
-    if (!active && (MODE != 2 || threadIdx.x >= kQ)) return;
+    if constexpr (MODE != 3) {  // MODE 3 keeps every thread for the block barriers
+        if (!active && (MODE != 2 || threadIdx.x >= kQ)) return;
+    }
     const uint32_t nx = (uint32_t)d.nx, nxy = (uint32_t)d.nx * (uint32_t)d.ny;
     const uint32_t plane = (uint32_t)d.plane;
 
@@ -327,6 +347,13 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Co
     P pv[kQ];
     auto vget = [&](auto I) { return F2(Codec::unpack2(pv[I])); };
     constexpr float inv_scale = (float)(1.0 / Codec::kScale);
+
+    __shared__ const T* s_row[MODE == 3 ? 2 : 1][kQ];  // MODE 3: source-row pointers of the row (and the next)
+    if constexpr (MODE == 3) {
+        if (threadIdx.x < kQ) s_row[0][threadIdx.x] = source_row<Codec>(src, d, (int)threadIdx.x, s, z, y);
+        __syncthreads();
+    }
+    auto ld = [&](const T* p, uint32_t off) { return LoadNC::load(reinterpret_cast<const P*>(p + off)); };
 
     for (uint32_t r = r0; r < r1; ++r) {
         // the next row, in (s, z, y) order
@@ -339,6 +366,7 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Co
             }
         }
         const bool more = r + 1 < r1;
+        const int buf = (int)((r - r0) & 1);
         if constexpr (MODE == 2) {
             if (more && threadIdx.x < kQ) prefetch_row_l2<Codec>(src, d, (int)threadIdx.x, sn, zn, yn, xa, xb);
             if (!active) {
@@ -348,20 +376,46 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Co
                 continue;
             }
         }
-        {
+        if constexpr (MODE == 3) {
+            if (more && threadIdx.x < kQ) {
+                const T* row = source_row<Codec>(src, d, (int)threadIdx.x, sn, zn, yn);
+                s_row[buf ^ 1][threadIdx.x] = row;
+                prefetch_span_l2(row, xa, xb, d.nx);
+            }
+        }
+        if constexpr (MODE == 3) {
+            if (active) {
+                static_for<kQ>([&](auto I) {
+                    constexpr Vel c = vel(I);
+                    const T* p = s_row[buf][I];
+                    // x shift: c / 2 cells on the sub-lattice; 1 - s (+1/2) or -s (-1/2) across it
+                    const int dx = c.shell == 5 ? (c.x > 0 ? 1 - s : -s) : c.x / 2;
+                    switch (dx) {
+                        case 2: pv[I] = ld(p, xm); break;
+                        case 1: pv[I] = Codec::straddle(ld(p, xm), ld(p, x0)); break;
+                        case 0: pv[I] = ld(p, x0); break;
+                        case -1: pv[I] = Codec::straddle(ld(p, x0), ld(p, xq)); break;
+                        default: pv[I] = ld(p, xq); break;
+                    }
+                });
+            }
+        } else {
             RowAddr2x<Codec> a;
             a.set(src, d, s, z, y);
             static_for<kQ>([&](auto I) { pv[I] = load_pair2x<Codec, I>(a, plane, xm, x0, xq); });
         }
+        if (MODE != 3 || active) {
 
-        const NodeMoments<F2> m =
-            moments_from<F2>([&](auto I) { return C2::dev(vget(I), F2(K.w[vel(I).shell] * inv_scale)); });
-        const NodeState<F2> st = state_from_moments(m, K);
-        if (!state_ok(st)) atomicOr(err, 1);
+            const NodeMoments<F2> m =
+                moments_from<F2>([&](auto I) { return C2::dev(vget(I), F2(K.w[vel(I).shell] * inv_scale)); });
+            const NodeState<F2> st = state_from_moments(m, K);
+            if (!state_ok(st)) atomicOr(err, 1);
 
-        P* outp = reinterpret_cast<P*>(dst + (size_t)s * kQ * d.plane + ((uint32_t)z * nxy + (uint32_t)y * nx + x0));
-        equilibrium_relax_g<C2, PROJECT>(st, K, F2(tb * (float)Codec::kScale), F2(1.f - tb), vget,
-                                         [&](auto I, F2 val) { outp[(size_t)I * (plane / 2)] = Codec::to_raw2(val.v); });
+            P* outp = reinterpret_cast<P*>(dst + (size_t)s * kQ * d.plane + ((uint32_t)z * nxy + (uint32_t)y * nx + x0));
+            equilibrium_relax_g<C2, PROJECT>(st, K, F2(tb * (float)Codec::kScale), F2(1.f - tb), vget,
+                                             [&](auto I, F2 val) { outp[(size_t)I * (plane / 2)] = Codec::to_raw2(val.v); });
+        }
+        if constexpr (MODE == 3) __syncthreads();  // the next row's table is complete; this row's is free
         s = sn;
         z = zn;
         y = yn;
