@@ -309,9 +309,9 @@ __device__ __forceinline__ void prefetch_row_l2(const typename Codec::raw_t* src
 // How a block of the x-pair kernel gets a row's upwind values:
 // MODE 0: direct loads at the start of the row.
 // MODE 2: as MODE 0, plus an L2 bulk prefetch of the next row's source rows
-//         (one per population, by threads 0..40) at the start of the current
-//         row, so that the next row's loads hit in L2.
-// MODE 3: as MODE 2, and the same threads 0..40 also write the next row's 41
+//         (one per population, by the first threads of the block) at the start
+//         of the current row, so that the next row's loads hit in L2.
+// MODE 3: as MODE 2, and the same threads also write the next row's 41
 //         source-row pointers into a shared table (double-buffered, one block
 //         barrier per row); every warp reads its row's pointers from there
 //         instead of forming them itself.
@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Co
     int s = (int)(zr / (uint32_t)d.nz);
     const bool active = x < d.nx;
     if constexpr (MODE != 3) {  // MODE 3 keeps every thread for the block barriers
-        if (!active && (MODE != 2 || threadIdx.x >= kQ)) return;
+        if (!active && (MODE != 2 || threadIdx.x >= kQ)) return;  // threads < 41 issue prefetches
     }
     const uint32_t nx = (uint32_t)d.nx, nxy = (uint32_t)d.nx * (uint32_t)d.ny;
     const uint32_t plane = (uint32_t)d.plane;
@@ -350,7 +350,8 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Co
 
     __shared__ const T* s_row[MODE == 3 ? 2 : 1][kQ];  // MODE 3: source-row pointers of the row (and the next)
     if constexpr (MODE == 3) {
-        if (threadIdx.x < kQ) s_row[0][threadIdx.x] = source_row<Codec>(src, d, (int)threadIdx.x, s, z, y);
+        // all 41 entries, whatever the block size (a block may have only 32 threads)
+        for (int i = (int)threadIdx.x; i < kQ; i += (int)blockDim.x) s_row[0][i] = source_row<Codec>(src, d, i, s, z, y);
         __syncthreads();
     }
     auto ld = [&](const T* p, uint32_t off) { return LoadNC::load(reinterpret_cast<const P*>(p + off)); };
@@ -368,7 +369,9 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Co
         const bool more = r + 1 < r1;
         const int buf = (int)((r - r0) & 1);
         if constexpr (MODE == 2) {
-            if (more && threadIdx.x < kQ) prefetch_row_l2<Codec>(src, d, (int)threadIdx.x, sn, zn, yn, xa, xb);
+            if (more)
+                for (int i = (int)threadIdx.x; i < kQ; i += (int)blockDim.x)
+                    prefetch_row_l2<Codec>(src, d, i, sn, zn, yn, xa, xb);
             if (!active) {
                 s = sn;
                 z = zn;
@@ -377,11 +380,12 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Co
             }
         }
         if constexpr (MODE == 3) {
-            if (more && threadIdx.x < kQ) {
-                const T* row = source_row<Codec>(src, d, (int)threadIdx.x, sn, zn, yn);
-                s_row[buf ^ 1][threadIdx.x] = row;
-                prefetch_span_l2(row, xa, xb, d.nx);
-            }
+            if (more)
+                for (int i = (int)threadIdx.x; i < kQ; i += (int)blockDim.x) {
+                    const T* row = source_row<Codec>(src, d, i, sn, zn, yn);
+                    s_row[buf ^ 1][i] = row;
+                    prefetch_span_l2(row, xa, xb, d.nx);
+                }
         }
         if constexpr (MODE == 3) {
             if (active) {
