@@ -311,10 +311,6 @@ __device__ __forceinline__ void prefetch_row_l2(const typename Codec::raw_t* src
 // MODE 2: as MODE 0, plus an L2 bulk prefetch of the next row's source rows
 //         (one per population, by the first threads of the block) at the start
 //         of the current row, so that the next row's loads hit in L2.
-// MODE 3: as MODE 2, and the same threads also write the next row's 41
-//         source-row pointers into a shared table (double-buffered, one block
-//         barrier per row); every warp reads its row's pointers from there
-//         instead of forming them itself.
 template <class Codec, bool PROJECT, int MINB, int MODE>
 __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Codec::raw_t* __restrict__ src,
                                                          typename Codec::raw_t* __restrict__ dst, Dims d,
@@ -335,9 +331,7 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Co
     int z = (int)(zr % (uint32_t)d.nz);
     int s = (int)(zr / (uint32_t)d.nz);
     const bool active = x < d.nx;
-    if constexpr (MODE != 3) {  // MODE 3 keeps every thread for the block barriers
-        if (!active && (MODE != 2 || threadIdx.x >= kQ)) return;  // threads < 41 issue prefetches
-    }
+    if (!active && (MODE != 2 || threadIdx.x >= kQ)) return;  // threads < 41 issue prefetches
     const uint32_t nx = (uint32_t)d.nx, nxy = (uint32_t)d.nx * (uint32_t)d.ny;
     const uint32_t plane = (uint32_t)d.plane;
 
@@ -347,14 +341,6 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Co
     P pv[kQ];
     auto vget = [&](auto I) { return F2(Codec::unpack2(pv[I])); };
     constexpr float inv_scale = (float)(1.0 / Codec::kScale);
-
-    __shared__ const T* s_row[MODE == 3 ? 2 : 1][kQ];  // MODE 3: source-row pointers of the row (and the next)
-    if constexpr (MODE == 3) {
-        // all 41 entries, whatever the block size (a block may have only 32 threads)
-        for (int i = (int)threadIdx.x; i < kQ; i += (int)blockDim.x) s_row[0][i] = source_row<Codec>(src, d, i, s, z, y);
-        __syncthreads();
-    }
-    auto ld = [&](const T* p, uint32_t off) { return LoadNC::load(reinterpret_cast<const P*>(p + off)); };
 
     for (uint32_t r = r0; r < r1; ++r) {
         // the next row, in (s, z, y) order
@@ -367,11 +353,13 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Co
             }
         }
         const bool more = r + 1 < r1;
-        const int buf = (int)((r - r0) & 1);
         if constexpr (MODE == 2) {
-            if (more)
-                for (int i = (int)threadIdx.x; i < kQ; i += (int)blockDim.x)
+            if (more) {
+                if (threadIdx.x < kQ) prefetch_row_l2<Codec>(src, d, (int)threadIdx.x, sn, zn, yn, xa, xb);
+                // blocks of fewer than 41 threads (narrow grids) cover the remaining populations
+                for (int i = (int)(threadIdx.x + blockDim.x); i < kQ; i += (int)blockDim.x)
                     prefetch_row_l2<Codec>(src, d, i, sn, zn, yn, xa, xb);
+            }
             if (!active) {
                 s = sn;
                 z = zn;
@@ -379,47 +367,20 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Co
                 continue;
             }
         }
-        if constexpr (MODE == 3) {
-            if (more)
-                for (int i = (int)threadIdx.x; i < kQ; i += (int)blockDim.x) {
-                    const T* row = source_row<Codec>(src, d, i, sn, zn, yn);
-                    s_row[buf ^ 1][i] = row;
-                    prefetch_span_l2(row, xa, xb, d.nx);
-                }
-        }
-        if constexpr (MODE == 3) {
-            if (active) {
-                static_for<kQ>([&](auto I) {
-                    constexpr Vel c = vel(I);
-                    const T* p = s_row[buf][I];
-                    // x shift: c / 2 cells on the sub-lattice; 1 - s (+1/2) or -s (-1/2) across it
-                    const int dx = c.shell == 5 ? (c.x > 0 ? 1 - s : -s) : c.x / 2;
-                    switch (dx) {
-                        case 2: pv[I] = ld(p, xm); break;
-                        case 1: pv[I] = Codec::straddle(ld(p, xm), ld(p, x0)); break;
-                        case 0: pv[I] = ld(p, x0); break;
-                        case -1: pv[I] = Codec::straddle(ld(p, x0), ld(p, xq)); break;
-                        default: pv[I] = ld(p, xq); break;
-                    }
-                });
-            }
-        } else {
+        {
             RowAddr2x<Codec> a;
             a.set(src, d, s, z, y);
             static_for<kQ>([&](auto I) { pv[I] = load_pair2x<Codec, I>(a, plane, xm, x0, xq); });
         }
-        if (MODE != 3 || active) {
 
-            const NodeMoments<F2> m =
-                moments_from<F2>([&](auto I) { return C2::dev(vget(I), F2(K.w[vel(I).shell] * inv_scale)); });
-            const NodeState<F2> st = state_from_moments(m, K);
-            if (!state_ok(st)) atomicOr(err, 1);
+        const NodeMoments<F2> m =
+            moments_from<F2>([&](auto I) { return C2::dev(vget(I), F2(K.w[vel(I).shell] * inv_scale)); });
+        const NodeState<F2> st = state_from_moments(m, K);
+        if (!state_ok(st)) atomicOr(err, 1);
 
-            P* outp = reinterpret_cast<P*>(dst + (size_t)s * kQ * d.plane + ((uint32_t)z * nxy + (uint32_t)y * nx + x0));
-            equilibrium_relax_g<C2, PROJECT>(st, K, F2(tb * (float)Codec::kScale), F2(1.f - tb), vget,
-                                             [&](auto I, F2 val) { outp[(size_t)I * (plane / 2)] = Codec::to_raw2(val.v); });
-        }
-        if constexpr (MODE == 3) __syncthreads();  // the next row's table is complete; this row's is free
+        P* outp = reinterpret_cast<P*>(dst + (size_t)s * kQ * d.plane + ((uint32_t)z * nxy + (uint32_t)y * nx + x0));
+        equilibrium_relax_g<C2, PROJECT>(st, K, F2(tb * (float)Codec::kScale), F2(1.f - tb), vget,
+                                         [&](auto I, F2 val) { outp[(size_t)I * (plane / 2)] = Codec::to_raw2(val.v); });
         s = sn;
         z = zn;
         y = yn;

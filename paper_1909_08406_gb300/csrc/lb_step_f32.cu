@@ -160,7 +160,6 @@ int resolve_kernel(int prec, const Dims& d, int kernel) {
     switch (kernel) {
         case kKernelDirect2X:
         case kKernelDirect2XL:
-        case kKernelDirect2XS:
             return (storage_bytes(prec) == 2 && d.nx % 2 == 0 && d.plane < ((int64_t)1 << 32))
                        ? kernel
                        : resolve_kernel(prec, d, kKernelAuto);
@@ -188,7 +187,6 @@ static cudaError_t step_codec(int prec, int kernel, const void* src, void* dst, 
         case kKernelWarpSpec: return run_ws<Codec, P, typename WsShape<Codec>::Cfg>(src, dst, d, c, twobeta, err, st);
         case kKernelDirect2X: return run_direct2x<Codec, P, 3, 0>(src, dst, d, c, twobeta, err, st, 1);
         case kKernelDirect2XL: return run_direct2x<Codec, P, 3, 2>(src, dst, d, c, twobeta, err, st, 2);
-        case kKernelDirect2XS: return run_direct2x<Codec, P, 3, 3>(src, dst, d, c, twobeta, err, st, 4);
 
         case kKernelDirect2: return run_direct2<Codec, P, 3>(src, dst, d, c, twobeta, err, st);
         case kKernelDirect2R: return run_direct2<Codec, P, 4>(src, dst, d, c, twobeta, err, st);
