@@ -265,16 +265,16 @@ __device__ __forceinline__ typename Codec::pair_t load_pair2x(const RowAddr2x<Co
     }
 }
 
-// Start of population I's source row (element x = 0) for the nodes of row
-// (s, z, y): integer links stay on the sub-lattice and shift by c / 2 cells;
-// bcc-1/2 links read the other sub-lattice with delta = 1 - s for a +1/2
-// component and -s for -1/2.
+// Prefetch into L2 the part of population I's source row that the nodes
+// [xa, xb) of the row (s, z, y) will read (x - 2 .. x + 2, not wrapped),
+// trimmed inward to whole 16-byte units of that row.
 template <class Codec>
-__device__ __forceinline__ const typename Codec::raw_t* source_row(const typename Codec::raw_t* src, const Dims& d,
-                                                                   int I, int s, int z, int y) {
+__device__ __forceinline__ void prefetch_row_l2(const typename Codec::raw_t* src, const Dims& d, int I, int s, int z,
+                                                int y, int xa, int xb) {
+    using T = typename Codec::raw_t;
     const Vel c = c_vel.v[I];
     int sp, dz, dy;
-    if (c.shell == 5) {
+    if (c.shell == 5) {  // half link: delta = 1 - s for +1/2, -s for -1/2; other sub-lattice
         sp = 1 - s;
         dz = c.z > 0 ? 1 - s : -s;
         dy = c.y > 0 ? 1 - s : -s;
@@ -284,26 +284,12 @@ __device__ __forceinline__ const typename Codec::raw_t* source_row(const typenam
         dy = c.y / 2;
     }
     const int zz = wrap(z - dz, d.nz), yy = wrap(y - dy, d.ny);
-    return src + ((size_t)sp * kQ + I) * d.plane + ((size_t)zz * d.ny + yy) * d.nx;
-}
-
-// Prefetch into L2 the part [xa - 2, xb + 2) of a source row (not wrapped),
-// trimmed inward to whole 16-byte units of that row.
-template <class T>
-__device__ __forceinline__ void prefetch_span_l2(const T* row, int xa, int xb, int nx) {
-    const int lo = max(xa - 2, 0), hi = min(xb + 2, nx);
+    const int lo = max(xa - 2, 0), hi = min(xb + 2, d.nx);
+    const T* row = src + ((size_t)sp * kQ + I) * d.plane + ((size_t)zz * d.ny + yy) * d.nx;
     const uintptr_t b0 = ((uintptr_t)(row + lo) + 15) & ~(uintptr_t)15;
     const uintptr_t b1 = ((uintptr_t)(row + hi)) & ~(uintptr_t)15;
     if (b1 > b0)
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b0), "r"((uint32_t)(b1 - b0)) : "memory");
-}
-
-// Prefetch into L2 the part of population I's source row that the nodes
-// [xa, xb) of the row (s, z, y) will read.
-template <class Codec>
-__device__ __forceinline__ void prefetch_row_l2(const typename Codec::raw_t* src, const Dims& d, int I, int s, int z,
-                                                int y, int xa, int xb) {
-    prefetch_span_l2(source_row<Codec>(src, d, I, s, z, y), xa, xb, d.nx);
 }
 
 // How a block of the x-pair kernel gets a row's upwind values:
