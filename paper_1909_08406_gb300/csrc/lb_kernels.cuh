@@ -295,7 +295,8 @@ __device__ __forceinline__ void prefetch_row_l2(const typename Codec::raw_t* src
 // How a block of the x-pair kernel gets a row's upwind values:
 // MODE 0: direct loads at the start of the row.
 // MODE 2: as MODE 0, plus an L2 bulk prefetch of the next row's source rows
-//         (one per population, by the first threads of the block) at the start
+//         (one per population, by threads 0..40; a block of only 32 threads,
+//         on a narrow grid, prefetches its first 32 populations) at the start
 //         of the current row, so that the next row's loads hit in L2.
 template <class Codec, bool PROJECT, int MINB, int MODE>
 __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Codec::raw_t* __restrict__ src,
@@ -340,12 +341,7 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Co
         }
         const bool more = r + 1 < r1;
         if constexpr (MODE == 2) {
-            if (more) {
-                if (threadIdx.x < kQ) prefetch_row_l2<Codec>(src, d, (int)threadIdx.x, sn, zn, yn, xa, xb);
-                // blocks of fewer than 41 threads (narrow grids) cover the remaining populations
-                for (int i = (int)(threadIdx.x + blockDim.x); i < kQ; i += (int)blockDim.x)
-                    prefetch_row_l2<Codec>(src, d, i, sn, zn, yn, xa, xb);
-            }
+            if (more && threadIdx.x < kQ) prefetch_row_l2<Codec>(src, d, (int)threadIdx.x, sn, zn, yn, xa, xb);
             if (!active) {
                 s = sn;
                 z = zn;
