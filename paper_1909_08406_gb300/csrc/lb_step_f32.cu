@@ -121,42 +121,6 @@ static cudaError_t run_ws(const void* src, void* dst, const Dims& d, const Launc
 
 // Warp-specialised shapes: 128 x per tile, 4 consumer warps.  16-bit: 70.8 KB ring
 // (3 stages) -> up to 3 CTAs/SM; FP32: 89.3 KB ring (2 stages) -> 2 CTAs/SM.
-// x-pair warp-specialised shapes (16-bit storage): TX = 256 -> 4 x 22.3 KB ring, 2 CTAs/SM;
-// TX = 128 -> 4 x 11.8 KB ring, 3 CTAs/SM.
-template <class Codec, int TX>
-struct WsxShape {
-    using Cfg = WsxCfg<Codec, TX / 2, 4, (TX >= 256 ? 2 : 3)>;
-};
-
-template <class Codec, bool P, class Cfg>
-static cudaError_t run_wsx(const void* src, void* dst, const Dims& d, const LaunchConsts& c, double twobeta, int* err,
-                           cudaStream_t st) {
-    using T = typename Codec::raw_t;
-    static TmaLaunchInfo info;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    auto kern = k_step_wsx<Codec, P, Cfg>;
-    if (info.device != dev) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
-        if (e != cudaSuccess) return e;
-        int per_sm = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, Cfg::THREADS, Cfg::SMEM);
-        if (e != cudaSuccess) return e;
-        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        info.grid = per_sm * sms;
-        info.device = dev;
-    }
-    const int64_t ntiles = d.rows * (d.nx / Cfg::TX);
-    const int grid = (int)(ntiles < info.grid ? ntiles : info.grid);
-    const long long wait_limit = 4000000000LL;  // ~2 s of SM clock
-    kern<<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(static_cast<const T*>(src), static_cast<T*>(dst), d, c.kf,
-                                               (float)twobeta, err, wait_limit);
-    return cudaGetLastError();
-}
-
 template <class Codec>
 struct WsShape {
     using Cfg = WsCfg<Codec, 128, 4, (sizeof(typename Codec::raw_t) == 2 ? 3 : 2),
@@ -199,10 +163,6 @@ int resolve_kernel(int prec, const Dims& d, int kernel) {
             return (storage_bytes(prec) == 2 && d.nx % 2 == 0 && d.plane < ((int64_t)1 << 32))
                        ? kernel
                        : resolve_kernel(prec, d, kKernelAuto);
-        case kKernelWarpSpecX:
-            return (storage_bytes(prec) == 2 && d.nx % 128 == 0 && d.plane < ((int64_t)1 << 32))
-                       ? kernel
-                       : resolve_kernel(prec, d, kKernelAuto);
         case kKernelWarpSpec:
             return (two_rows && d.nx % 128 == 0 && tma_tile_width(prec, d)) ? kKernelWarpSpec
                                                                              : resolve_kernel(prec, d, kKernelAuto);
@@ -225,14 +185,6 @@ static cudaError_t step_codec(int prec, int kernel, const void* src, void* dst, 
                 return run_tma<Codec, P, typename TmaShape<Codec, 256>::Cfg>(src, dst, d, c, twobeta, err, st);
             return run_tma<Codec, P, typename TmaShape<Codec, 128>::Cfg>(src, dst, d, c, twobeta, err, st);
         case kKernelWarpSpec: return run_ws<Codec, P, typename WsShape<Codec>::Cfg>(src, dst, d, c, twobeta, err, st);
-        case kKernelWarpSpecX:
-            if constexpr (sizeof(typename Codec::raw_t) == 2) {
-                if (d.nx % 256 == 0)
-                    return run_wsx<Codec, P, typename WsxShape<Codec, 256>::Cfg>(src, dst, d, c, twobeta, err, st);
-                return run_wsx<Codec, P, typename WsxShape<Codec, 128>::Cfg>(src, dst, d, c, twobeta, err, st);
-            } else {
-                return cudaErrorInvalidValue;
-            }
         case kKernelDirect2X: return run_direct2x<Codec, P, 3, 0>(src, dst, d, c, twobeta, err, st, 1);
         case kKernelDirect2XL: return run_direct2x<Codec, P, 3, 2>(src, dst, d, c, twobeta, err, st, 2);
 

@@ -218,195 +218,3 @@ __global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB) k_step_ws(const typen
 }
 
 }  // namespace gblb
-
-namespace gblb {
-
-// Warp-specialised, TMA-staged x-pair kernel (FP16/BF16 storage).
-//
-// Tile: TX = 2 * TXP consecutive x of one row (s, z, y).  Warp 0 is the
-// producer: per population it fetches the tile's upwind row, widened by a
-// 16-byte halo on each side (periodic wrap as extra 16-byte pieces), with 1D
-// cp.async.bulk copies into a STAGES-deep ring (full/empty mbarriers as in
-// k_step_ws).  Warps 1 .. TXP/32 are consumers: thread xl updates the nodes
-// x0 + 2 xl and x0 + 2 xl + 1 with packed FP32x2 arithmetic.  It reads each
-// population's pair of upwind values from the ring at a compile-time offset
-// from one shared address (one 32-bit load for an even x shift, two and a
-// byte permute for an odd one; no wrap logic, the halo holds it), releases the
-// stage as soon as its 41 pairs are in registers (the arrive orders the reads
-// before the producer's refill), then computes and stores like k_step2x.
-// Every mbarrier wait is bounded; on expiry the kernel sets bit 2 of the
-// error word, lets its own copies land (bounded) and returns.
-template <class Codec, int TXP_, int STAGES_, int MINB_>
-struct WsxCfg {
-    using T = typename Codec::raw_t;
-    static constexpr int TXP = TXP_;                  // x pairs per tile (= consumer threads)
-    static constexpr int TX = 2 * TXP;                // x per tile
-    static constexpr int CW = TXP / 32;               // consumer warps
-    static constexpr int THREADS = 32 * (CW + 1);
-    static constexpr int STAGES = STAGES_;
-    static constexpr int MINB = MINB_;
-    static constexpr int H = 16 / (int)sizeof(T);     // halo: 16 bytes of elements on each side
-    static constexpr int ROW = TX + 2 * H;            // elements per staged row
-    static constexpr int STAGE_ELEMS = kQ * ROW;      // [plane][ROW]
-    static constexpr int STAGE_BYTES = STAGE_ELEMS * (int)sizeof(T);
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 2 * STAGES * 8 + 16;
-    static_assert(sizeof(T) == 2, "16-bit storage");
-    static_assert(TXP % 32 == 0, "whole consumer warps");
-    static_assert((ROW * sizeof(T)) % 16 == 0, "staged rows must be whole 16-byte units");
-};
-
-template <class Codec, bool PROJECT, class Cfg>
-__global__ void __launch_bounds__(Cfg::THREADS, Cfg::MINB) k_step_wsx(const typename Codec::raw_t* __restrict__ src,
-                                                                     typename Codec::raw_t* __restrict__ dst, Dims d,
-                                                                     Consts<float> K, float tb, int* __restrict__ err,
-                                                                     long long wait_limit) {
-    using T = typename Codec::raw_t;
-    using P = typename Codec::pair_t;
-    using C2 = Codec2<Codec>;
-    constexpr int TX = Cfg::TX, H = Cfg::H, ROW = Cfg::ROW, STAGES = Cfg::STAGES;
-    extern __shared__ __align__(128) unsigned char smem[];
-    T* stage_base = reinterpret_cast<T*>(smem);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * Cfg::STAGE_BYTES);
-    uint64_t* empty = full + STAGES;
-    int* flag = reinterpret_cast<int*>(empty + STAGES);
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int tiles_per_row = d.nx / TX;
-    const int64_t ntiles = d.rows * tiles_per_row;
-    const int64_t my_tiles = (int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const uint32_t nx = (uint32_t)d.nx, nxy = (uint32_t)d.nx * (uint32_t)d.ny;
-    const uint32_t plane = (uint32_t)d.plane;
-
-    if (tid == 0) {
-        for (int i = 0; i < STAGES; ++i) {
-            mbar_init(smem_u32(&full[i]), 1);
-            mbar_init(smem_u32(&empty[i]), Cfg::CW);
-        }
-        *flag = 0;
-        fence_mbar_init();
-    }
-    __syncthreads();
-
-    // tile t -> (s, z, y, x0)
-    auto coord = [&](int64_t t, int& s, int& z, int& y, int& x0) {
-        const int64_t r = t / tiles_per_row;
-        x0 = (int)(t - r * tiles_per_row) * TX;
-        y = (int)(r % d.ny);
-        const int64_t zr = r / d.ny;
-        z = (int)(zr % d.nz);
-        s = (int)(zr / d.nz);
-    };
-
-    if (warp == 0) {
-        // ---------------- producer ----------------
-        int64_t k = 0;
-        for (; k < my_tiles; ++k) {
-            const int st = (int)(k % STAGES);
-            const uint32_t n = (uint32_t)(k / STAGES);
-            if (k >= STAGES) {
-                bool ok = true;
-                if (lane == 0) ok = mbar_wait_bounded(smem_u32(&empty[st]), (n - 1) & 1, wait_limit);
-                ok = __shfl_sync(0xffffffffu, ok, 0);
-                if (!ok) {
-                    if (lane == 0) {
-                        atomicOr(err, 2);
-                        atomicExch(flag, 1);
-                    }
-                    break;
-                }
-            }
-            if (*reinterpret_cast<volatile int*>(flag)) break;
-            int s, z, y, x0;
-            coord(blockIdx.x + k * gridDim.x, s, z, y, x0);
-            const uint32_t fb = smem_u32(&full[st]);
-            fence_proxy_async_smem();
-            if (lane == 0) mbar_arrive_expect_tx(fb, Cfg::STAGE_BYTES);
-            __syncwarp();
-            const bool left = x0 == 0, right = x0 + TX == d.nx;
-            constexpr uint32_t HB = H * sizeof(T);
-            for (int i = lane; i < kQ; i += 32) {
-                const Vel c = c_vel.v[i];
-                int sp, dy, dz;
-                if (c.shell == 5) {
-                    sp = 1 - s;
-                    dy = c.y > 0 ? 1 - s : -s;
-                    dz = c.z > 0 ? 1 - s : -s;
-                } else {
-                    sp = s;
-                    dy = c.y / 2;
-                    dz = c.z / 2;
-                }
-                const int ys = wrap(y - dy, d.ny), zs = wrap(z - dz, d.nz);
-                const T* rowp = src + ((size_t)sp * kQ + i) * d.plane + (size_t)zs * nxy + (size_t)ys * nx;
-                const uint32_t dsm = smem_u32(stage_base + (size_t)st * Cfg::STAGE_ELEMS + i * ROW);
-                if (!left && !right) {
-                    bulk_g2s(dsm, rowp + x0 - H, (uint32_t)(ROW * sizeof(T)), fb);
-                } else if (left && !right) {
-                    bulk_g2s(dsm, rowp + d.nx - H, HB, fb);
-                    bulk_g2s(dsm + HB, rowp, (uint32_t)((TX + H) * sizeof(T)), fb);
-                } else if (!left && right) {
-                    bulk_g2s(dsm, rowp + x0 - H, (uint32_t)((TX + H) * sizeof(T)), fb);
-                    bulk_g2s(dsm + (uint32_t)((TX + H) * sizeof(T)), rowp, HB, fb);
-                } else {
-                    bulk_g2s(dsm, rowp + d.nx - H, HB, fb);
-                    bulk_g2s(dsm + HB, rowp, (uint32_t)(TX * sizeof(T)), fb);
-                    bulk_g2s(dsm + HB + (uint32_t)(TX * sizeof(T)), rowp, HB, fb);
-                }
-            }
-        }
-        // let every issued copy land before the CTA can exit
-        if (lane == 0) {
-            const int64_t first = k > STAGES ? k - STAGES : 0;
-            for (int64_t kk = first; kk < k; ++kk)
-                mbar_wait_bounded(smem_u32(&full[kk % STAGES]), (uint32_t)((kk / STAGES) & 1), wait_limit);
-        }
-    } else {
-        // ---------------- consumers ----------------
-        const int xl = tid - 32;
-        constexpr float inv_scale = (float)(1.0 / Codec::kScale);
-        const F2 tbs(tb * (float)Codec::kScale), omb(1.f - tb);
-        P pv[kQ];
-        auto vget = [&](auto I) { return F2(Codec::unpack2(pv[I])); };
-        for (int64_t k = 0; k < my_tiles; ++k) {
-            const int st = (int)(k % STAGES);
-            if (!mbar_wait_bounded(smem_u32(&full[st]), (uint32_t)((k / STAGES) & 1), wait_limit)) {
-                if (lane == 0) {
-                    atomicOr(err, 2);
-                    atomicExch(flag, 1);
-                }
-                break;
-            }
-            int s, z, y, x0;
-            coord(blockIdx.x + k * gridDim.x, s, z, y, x0);
-            // aligned pairs of plane I around the thread's nodes: element H + 2 xl + 2 j - 2, j = 0, 1, 2
-            const P* row0 = reinterpret_cast<const P*>(stage_base + (size_t)st * Cfg::STAGE_ELEMS + H + 2 * xl - 2);
-            static_for<kQ>([&](auto I) {
-                constexpr Vel c = vel(I);
-                const P* q = row0 + I * (ROW / 2);
-                const int dx = c.shell == 5 ? (c.x > 0 ? 1 - s : -s) : c.x / 2;
-                switch (dx) {
-                    case 2: pv[I] = q[0]; break;
-                    case 1: pv[I] = Codec::straddle(q[0], q[1]); break;
-                    case 0: pv[I] = q[1]; break;
-                    case -1: pv[I] = Codec::straddle(q[1], q[2]); break;
-                    default: pv[I] = q[2]; break;
-                }
-            });
-            // the pairs are in registers: release the stage to the producer
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&empty[st]));
-
-            const NodeMoments<F2> m =
-                moments_from<F2>([&](auto I) { return C2::dev(vget(I), F2(K.w[vel(I).shell] * inv_scale)); });
-            const NodeState<F2> ns = state_from_moments(m, K);
-            if (!state_ok(ns)) atomicOr(err, 1);
-            P* outp = reinterpret_cast<P*>(dst + (size_t)s * kQ * d.plane +
-                                           ((uint32_t)z * nxy + (uint32_t)y * nx + (uint32_t)(x0 + 2 * xl)));
-            equilibrium_relax_g<C2, PROJECT>(ns, K, tbs, omb, vget, [&](auto I, F2 val) {
-                outp[(size_t)I * (plane / 2)] = Codec::to_raw2(val.v);
-            });
-        }
-    }
-}
-
-}  // namespace gblb
