@@ -330,7 +330,7 @@ def main():
     kernels = [args.kernel] if args.kernel is not None else [lb.LB_KERNEL_DIRECT1, lb.LB_KERNEL_DIRECT2,
                                                             lb.LB_KERNEL_DIRECT2R, lb.LB_KERNEL_STAGED,
                                                             lb.LB_KERNEL_WARPSPEC, lb.LB_KERNEL_DIRECT2X,
-                                                            lb.LB_KERNEL_DIRECT2XL, lb.LB_KERNEL_DIRECT2H]
+                                                            lb.LB_KERNEL_DIRECT2XL]
     probe_ctx = lb.lb_init((n, n, n), tau, head)
     applicable = []
     for k in kernels:

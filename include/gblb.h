@@ -192,9 +192,6 @@ lb_status lb_set_state(lb_ctx *ctx, const void *raw, int on_device);
  *                      32-bit paired loads and stores (FP16/BF16 storage; nx even)
  *   LB_KERNEL_DIRECT2XL the same over 2 rows per block, the next row's source
  *                      rows prefetched into L2 by bulk prefetches
- *   LB_KERNEL_DIRECT2H x pairs with the 41 populations split over two warps
- *                      (partial moments exchanged through shared memory), for
- *                      fewer registers per thread and more resident warps
  *   LB_KERNEL_AUTO     DIRECT2XL for 16-bit storage with nx even, else DIRECT2 where
  *                      it applies, else DIRECT1 (the default)
  * A request that does not apply to the grid falls back to one that does. */
@@ -206,9 +203,8 @@ lb_status lb_set_state(lb_ctx *ctx, const void *raw, int on_device);
 #define LB_KERNEL_WARPSPEC 4
 #define LB_KERNEL_DIRECT2X 5
 #define LB_KERNEL_DIRECT2XL 6
-#define LB_KERNEL_DIRECT2H 7
 
-/* Kernel lb_step will run for this context (LB_KERNEL_DIRECT1 .. LB_KERNEL_DIRECT2H). */
+/* Kernel lb_step will run for this context (LB_KERNEL_DIRECT1 .. LB_KERNEL_DIRECT2XL). */
 int lb_step_variant(const lb_ctx *ctx);
 /* Request a step kernel (LB_KERNEL_*). */
 lb_status lb_set_step_kernel(lb_ctx *ctx, int kernel);

@@ -287,7 +287,7 @@ int lb_step_variant(const lb_ctx* c) {
 }
 
 lb_status lb_set_step_kernel(lb_ctx* c, int kernel) {
-    if (!c || kernel < LB_KERNEL_AUTO || kernel > LB_KERNEL_DIRECT2H) return fail(c, LB_ERR_ARG, "lb_set_step_kernel: unknown kernel");
+    if (!c || kernel < LB_KERNEL_AUTO || kernel > LB_KERNEL_DIRECT2XL) return fail(c, LB_ERR_ARG, "lb_set_step_kernel: unknown kernel");
     c->variant = kernel;
     return LB_OK;
 }
@@ -303,7 +303,7 @@ lb_status lb_tune(lb_ctx* c, int reps, int* kernel_out, double* ms_out) {
     float best = 1e30f;
     int best_k = resolve_kernel(c->prec, c->d, kKernelAuto);
     // trial steps read buf[cur] and write buf[1 - cur] without flipping: the state is unchanged
-    for (int k = LB_KERNEL_DIRECT1; k <= LB_KERNEL_DIRECT2H; ++k) {
+    for (int k = LB_KERNEL_DIRECT1; k <= LB_KERNEL_DIRECT2XL; ++k) {
         if (resolve_kernel(c->prec, c->d, k) != k) continue;
         cudaError_t e = launch_step(c->prec, c->eq, k, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc, c->twobeta,
                                     c->d_err, c->stream);

@@ -218,22 +218,16 @@ struct NodeMoments {
     R drho, jx, jy, jz, dk;
 };
 
-// dget(I) returns d_I for a compile-time population index I.  With a pair
-// range [K0, K1) and REST, only those +-pairs (populations 2K+1, 2K+2) and the
-// rest population contribute: a partial sum over a subset of the velocities.
-template <class R, int K0 = 0, int K1 = 20, bool REST = true, class G>
+// dget(I) returns d_I for a compile-time population index I.
+template <class R, class G>
 __device__ __forceinline__ NodeMoments<R> moments_from(G&& dget) {
     NodeMoments<R> m;
-    if constexpr (REST)
-        m.drho = dget(std::integral_constant<int, 0>{});
-    else
-        m.drho = R(0);
+    m.drho = dget(std::integral_constant<int, 0>{});
     m.jx = R(0);
     m.jy = R(0);
     m.jz = R(0);
     m.dk = R(0);
     static_for<20>([&](auto K) {
-        if constexpr (K < K0 || K >= K1) return;
         constexpr int ip = 2 * K + 1, im = 2 * K + 2;
         constexpr Vel c = vel(ip);
         const R dp = dget(std::integral_constant<int, ip>{});
@@ -294,10 +288,8 @@ __device__ __forceinline__ bool state_ok(const NodeState<F2>& st) {
 // Equilibrium (Eq. feqGenU3, with the optional momentum projection) and BGK
 // relaxation of one node.  v[i] are the working values of the node's incoming
 // populations (f or h, see the codec), tb = 2 beta, omb = 1 - 2 beta.
-// sink(I, value) receives the new working value of population I.  With a pair
-// range [K0, K1) and REST, only those +-pairs and the rest population are
-// relaxed (the node's state must still be the full one).
-template <class Codec, bool PROJECT, int K0 = 0, int K1 = 20, bool REST = true, class VGet, class Sink>
+// sink(I, value) receives the new working value of population I.
+template <class Codec, bool PROJECT, class VGet, class Sink>
 __device__ __forceinline__ void equilibrium_relax_g(const NodeState<typename Codec::R>& st,
                                                     const Consts<typename Codec::KS>& K, typename Codec::R tb,
                                                     typename Codec::R omb, VGet&& vget, Sink&& sink) {
@@ -348,7 +340,7 @@ __device__ __forceinline__ void equilibrium_relax_g(const NodeState<typename Cod
         vz = djz * k;
     }
     // rest population: a = 0
-    if constexpr (REST) {
+    {
         const R rm1 = rest_m1(0);
         const R P0 = tb * (rho + rho * rm1);
         const R x0 = fma(P0, cg - gA1_6t * K.c2[0], tb * (st.drho + rho * rm1));
@@ -357,11 +349,10 @@ __device__ __forceinline__ void equilibrium_relax_g(const NodeState<typename Cod
     }
     R P, B, Ds;  // factors of the current shell
     static_for<20>([&](auto KK) {
-        if constexpr (KK < K0 || KK >= K1) return;
         constexpr int ip = 2 * KK + 1, im = 2 * KK + 2;
         constexpr Vel c = vel(ip);
         constexpr int s = c.shell;
-        if constexpr (KK == K0 || vel(KK == 0 ? 0 : ip - 2).shell != s) {
+        if constexpr (KK == 0 || vel(ip - 2).shell != s) {
             const R rm1 = rest_m1(s);
             P = tb * (rho + rho * rm1);
             B = fma(P, cg - gA1_6t * K.c2[s], tb * (st.drho + rho * rm1));

@@ -369,123 +369,6 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Co
     }
 }
 
-// x pairs with the populations split over two warps: warps 2p and 2p + 1 of a
-// block update the same 32 x pairs (x, x + 1) of a row, warp 2p the rest
-// population and +-pairs 1..10, warp 2p + 1 the +-pairs 11..20.  Each loads and
-// relaxes only its half, so it holds half the values; the two partial moment
-// sums are exchanged through shared memory (one named barrier per warp pair
-// and row, double-buffered by row) and added in a fixed order, so both warps
-// form the identical node state.  Rows per block `rpb`, with an L2 bulk
-// prefetch of the next row's source rows (threads 0..40).  Requires nx even
-// and nx * ny * nz < 2^32.
-template <class Codec, bool PROJECT, int MINB>
-__global__ void __launch_bounds__(kStepThreads, MINB) k_step2h(const typename Codec::raw_t* __restrict__ src,
-                                                         typename Codec::raw_t* __restrict__ dst, Dims d,
-                                                         Consts<float> K, float tb, int* __restrict__ err,
-                                                         int chunks, int rpb) {
-    using T = typename Codec::raw_t;
-    using P = typename Codec::pair_t;
-    using C2 = Codec2<Codec>;
-    const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
-    const int wp = warp >> 1, half = warp & 1;          // warp pair, population half
-    const int npairs_blk = (int)(blockDim.x >> 6) * 32;  // x pairs per block
-    const uint32_t t = blockIdx.x;
-    const uint32_t grp = t / (uint32_t)chunks;
-    const int chunk = (int)(t - grp * (uint32_t)chunks);
-    const int xa = 2 * chunk * npairs_blk, xb = min(xa + 2 * npairs_blk, d.nx);
-    const int x = xa + 2 * (wp * 32 + lane);
-    const uint32_t r0 = grp * (uint32_t)rpb;
-    const uint32_t r1 = min(r0 + (uint32_t)rpb, (uint32_t)d.rows);
-    int y = (int)(r0 % (uint32_t)d.ny);
-    const uint32_t zr = r0 / (uint32_t)d.ny;
-    int z = (int)(zr % (uint32_t)d.nz);
-    int s = (int)(zr / (uint32_t)d.nz);
-    const bool active = x < d.nx;  // inactive threads stay for the barriers
-    const uint32_t nx = (uint32_t)d.nx, nxy = (uint32_t)d.nx * (uint32_t)d.ny;
-    const uint32_t plane = (uint32_t)d.plane;
-    const uint32_t xm = (uint32_t)wrap(min(x, d.nx - 2) - 2, d.nx), x0 = (uint32_t)min(x, d.nx - 2),
-                   xq = (uint32_t)wrap(min(x, d.nx - 2) + 2, d.nx);
-    constexpr float inv_scale = (float)(1.0 / Codec::kScale);
-    // partial moments of each warp, per row parity: [parity][warp][value][lane]
-    __shared__ float2 s_part[2][kStepThreads / 32][5][32];
-
-    P pv[kQ];
-    auto vget = [&](auto I) { return F2(Codec::unpack2(pv[I])); };
-
-    auto run = [&](auto HALF) {
-        constexpr int H = decltype(HALF)::value;
-        constexpr int K0 = H ? 10 : 0, K1 = H ? 20 : 10;
-        constexpr bool REST = H == 0;
-        int par = 0;
-        for (uint32_t r = r0; r < r1; ++r, par ^= 1) {
-            int yn = y + 1, zn = z, sn = s;
-            if (yn == d.ny) {
-                yn = 0;
-                if (++zn == d.nz) {
-                    zn = 0;
-                    ++sn;
-                }
-            }
-            if (r + 1 < r1 && threadIdx.x < kQ) prefetch_row_l2<Codec>(src, d, (int)threadIdx.x, sn, zn, yn, xa, xb);
-            NodeMoments<F2> m;
-            if (active) {
-                RowAddr2x<Codec> a;
-                a.set(src, d, s, z, y);
-                if constexpr (REST) pv[0] = load_pair2x<Codec, 0>(a, plane, xm, x0, xq);
-                static_for<20>([&](auto KK) {
-                    if constexpr (KK < K0 || KK >= K1) return;
-                    pv[2 * KK + 1] = load_pair2x<Codec, 2 * KK + 1>(a, plane, xm, x0, xq);
-                    pv[2 * KK + 2] = load_pair2x<Codec, 2 * KK + 2>(a, plane, xm, x0, xq);
-                });
-                m = moments_from<F2, K0, K1, REST>(
-                    [&](auto I) { return C2::dev(vget(I), F2(K.w[vel(I).shell] * inv_scale)); });
-            } else {
-                m.drho = m.jx = m.jy = m.jz = m.dk = F2(0.f);
-            }
-            // exchange the partial sums with the partner warp; total = half 0 + half 1 in both
-            float2* mine = &s_part[par][warp][0][lane];
-            mine[0] = m.drho.v;
-            mine[32] = m.jx.v;
-            mine[64] = m.jy.v;
-            mine[96] = m.jz.v;
-            mine[128] = m.dk.v;
-            asm volatile("bar.sync %0, 64;" ::"r"(1 + wp) : "memory");
-            const float2* other = &s_part[par][warp ^ 1][0][lane];
-            const F2 o0(other[0]), o1(other[32]), o2(other[64]), o3(other[96]), o4(other[128]);
-            NodeMoments<F2> tot;
-            if constexpr (H == 0) {
-                tot.drho = m.drho + o0;
-                tot.jx = m.jx + o1;
-                tot.jy = m.jy + o2;
-                tot.jz = m.jz + o3;
-                tot.dk = m.dk + o4;
-            } else {
-                tot.drho = o0 + m.drho;
-                tot.jx = o1 + m.jx;
-                tot.jy = o2 + m.jy;
-                tot.jz = o3 + m.jz;
-                tot.dk = o4 + m.dk;
-            }
-            if (active) {
-                const NodeState<F2> st = state_from_moments(tot, K);
-                if (!state_ok(st)) atomicOr(err, 1);
-                P* outp =
-                    reinterpret_cast<P*>(dst + (size_t)s * kQ * d.plane + ((uint32_t)z * nxy + (uint32_t)y * nx + x0));
-                equilibrium_relax_g<C2, PROJECT, K0, K1, REST>(
-                    st, K, F2(tb * (float)Codec::kScale), F2(1.f - tb), vget,
-                    [&](auto I, F2 val) { outp[(size_t)I * (plane / 2)] = Codec::to_raw2(val.v); });
-            }
-            s = sn;
-            z = zn;
-            y = yn;
-        }
-    };
-    if (half == 0)
-        run(std::integral_constant<int, 0>{});
-    else
-        run(std::integral_constant<int, 1>{});
-}
-
 // Populations = equilibrium of the given float64 fields, for nodes
 // q in [q0, q0 + count), q = s * plane + (z * ny + y) * nx + x.  Field
 // pointers are indexed by q - q0 (u component c at c * ustride + q - q0).

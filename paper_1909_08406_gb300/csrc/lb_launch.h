@@ -31,8 +31,7 @@ enum StepKernel {
     kKernelStaged = 3,
     kKernelWarpSpec = 4,
     kKernelDirect2X = 5,
-    kKernelDirect2XL = 6,
-    kKernelDirect2H = 7
+    kKernelDirect2XL = 6
 };
 
 // The kernel a request resolves to for this precision and grid (falls back where one does not apply).

@@ -55,25 +55,6 @@ static cudaError_t run_direct2x(const void* src, void* dst, const Dims& d, const
     }
 }
 
-template <class Codec, bool P, int MINB>
-static cudaError_t run_direct2h(const void* src, void* dst, const Dims& d, const LaunchConsts& c, double twobeta,
-                                int* err, cudaStream_t st, int rpb) {
-    using T = typename Codec::raw_t;
-    if constexpr (sizeof(T) != 2) {
-        return cudaErrorInvalidValue;
-    } else {
-        const int half = d.nx / 2;  // x pairs per row
-        // 128 threads = 2 warp pairs = 64 x pairs per block; 64 threads (one warp pair) for narrow rows
-        const int th = half > 32 ? 128 : 64;
-        const int pairs_blk = (th / 64) * 32;
-        const int chunks = (half + pairs_blk - 1) / pairs_blk;
-        const int64_t blocks = ((d.rows + rpb - 1) / rpb) * chunks;
-        k_step2h<Codec, P, MINB><<<(unsigned)blocks, th, 0, st>>>(static_cast<const T*>(src), static_cast<T*>(dst), d,
-                                                                 c.kf, (float)twobeta, err, chunks, rpb);
-        return cudaGetLastError();
-    }
-}
-
 // Per-instance launch data: dynamic shared memory opt-in and the persistent grid size.
 struct TmaLaunchInfo {
     int device = -1;
@@ -179,7 +160,6 @@ int resolve_kernel(int prec, const Dims& d, int kernel) {
     switch (kernel) {
         case kKernelDirect2X:
         case kKernelDirect2XL:
-        case kKernelDirect2H:
             return (storage_bytes(prec) == 2 && d.nx % 2 == 0 && d.plane < ((int64_t)1 << 32))
                        ? kernel
                        : resolve_kernel(prec, d, kKernelAuto);
@@ -207,7 +187,6 @@ static cudaError_t step_codec(int prec, int kernel, const void* src, void* dst, 
         case kKernelWarpSpec: return run_ws<Codec, P, typename WsShape<Codec>::Cfg>(src, dst, d, c, twobeta, err, st);
         case kKernelDirect2X: return run_direct2x<Codec, P, 3, 0>(src, dst, d, c, twobeta, err, st, 1);
         case kKernelDirect2XL: return run_direct2x<Codec, P, 3, 2>(src, dst, d, c, twobeta, err, st, 2);
-        case kKernelDirect2H: return run_direct2h<Codec, P, 4>(src, dst, d, c, twobeta, err, st, 2);
 
         case kKernelDirect2: return run_direct2<Codec, P, 3>(src, dst, d, c, twobeta, err, st);
         case kKernelDirect2R: return run_direct2<Codec, P, 4>(src, dst, d, c, twobeta, err, st);

@@ -27,13 +27,12 @@ LB_FLAG_PAPER_LITERAL = 1
 LB_FLAG_STAGED = 2
 LB_FLAG_ENTROPIC = 4
 LB_KERNEL_AUTO, LB_KERNEL_DIRECT1, LB_KERNEL_DIRECT2, LB_KERNEL_DIRECT2R, LB_KERNEL_STAGED, LB_KERNEL_WARPSPEC = -1, 0, 1, 2, 3, 4
-LB_KERNEL_DIRECT2X, LB_KERNEL_DIRECT2XL, LB_KERNEL_DIRECT2H = 5, 6, 7
+LB_KERNEL_DIRECT2X, LB_KERNEL_DIRECT2XL = 5, 6
 KERNEL_NAMES = {0: "k_step (direct, 1 node/thread)", 1: "k_step2 (direct, 2 rows/thread, FP32x2)",
                 2: "k_step2 (direct, 2 rows/thread, FP32x2, 4 CTAs/SM)", 3: "k_step_tma (TMA-staged)",
                 4: "k_step_ws (TMA-staged, warp-specialised, FP32x2)",
                 5: "k_step2x (direct, 2 x-adjacent nodes/thread, FP32x2, paired 16-bit access)",
-                6: "k_step2x (x pairs, 2 rows/block, next row prefetched into L2)",
-                7: "k_step2h (x pairs, populations split over two warps, L2 prefetch)"}
+                6: "k_step2x (x pairs, 2 rows/block, next row prefetched into L2)"}
 
 
 class LbError(RuntimeError):

@@ -64,8 +64,7 @@ def _run_gpu(shape, tau, prec, fields, steps, flags=0, kernel=lb.LB_KERNEL_AUTO)
 # storage and nx even (nx = 2: the x-2 and x+2 pairs coincide; 262: a ragged second block of
 # pairs); FP64 always runs DIRECT1.
 KERNELS = [lb.LB_KERNEL_DIRECT1, lb.LB_KERNEL_DIRECT2, lb.LB_KERNEL_DIRECT2R, lb.LB_KERNEL_STAGED,
-           lb.LB_KERNEL_WARPSPEC, lb.LB_KERNEL_DIRECT2X, lb.LB_KERNEL_DIRECT2XL,
-           lb.LB_KERNEL_DIRECT2H]
+           lb.LB_KERNEL_WARPSPEC, lb.LB_KERNEL_DIRECT2X, lb.LB_KERNEL_DIRECT2XL]
 STREAM_SHAPES = [(4, 4, 4), (3, 5, 7), (1, 2, 5), (133, 4, 3), (128, 2, 3), (256, 2, 1), (384, 2, 3),
                  (2, 3, 2), (262, 2, 3)]
 
