@@ -27,14 +27,18 @@ import torch
 NU = 0.01
 
 
-def run(n, steps, prec, fields):
+def run(n, steps, prec, fields, kernel=None):
+    """Sets the fields, steps and returns (rho, theta, conserved before, conserved after, seconds).
+    `kernel` fixes the step kernel (an LB_KERNEL_* id); None lets the autotuner pick."""
     from . import lb
     th0 = lb.lb_theta0()
     ctx = lb.lb_init((n, n, n), NU / th0, prec)
     try:
         lb.lb_set_fields(ctx, fields["rho"], fields["u"], fields["theta"])
         c0 = lb.lb_conserved(ctx)
-        if prec != "f64":
+        if kernel is not None:
+            lb.lb_set_step_kernel(ctx, kernel)
+        elif prec != "f64":
             lb.lb_tune(ctx, reps=2)
         t0 = time.perf_counter()
         lb.lb_step(ctx, steps)
@@ -50,6 +54,30 @@ def run(n, steps, prec, fields):
     return rho, th, c0, c1, el
 
 
+def compare(n, steps, precs, fields, kernels=None):
+    """Error of each storage precision in `precs` against the GPU FP64 mode after `steps` steps
+    of the same initial fields.  `kernels` maps a precision to a fixed step kernel id."""
+    from . import lb
+    th0 = lb.lb_theta0()
+    ref_rho, ref_th, c0, c1, el = run(n, steps, "f64", fields)
+    nr = float(torch.linalg.vector_norm(ref_rho - 1.0))
+    nt = float(torch.linalg.vector_norm(ref_th - th0))
+    out = {"f64": {"seconds": el, "mass_drift": (c1[0] - c0[0]) / c0[0], "energy_drift": (c1[4] - c0[4]) / c0[4],
+                   "l2_rho_fluct": nr, "l2_theta_fluct": nt}}
+    for prec in precs:
+        rho, th, c0, c1, el = run(n, steps, prec, fields, (kernels or {}).get(prec))
+        out[prec] = {"rel_l2_rho_fluct": float(torch.linalg.vector_norm(rho - ref_rho)) / nr,
+                     "rel_l2_theta_fluct": float(torch.linalg.vector_norm(th - ref_th)) / nt,
+                     "max_abs_rho_err": float((rho - ref_rho).abs().max()),
+                     "mass_drift": (c1[0] - c0[0]) / c0[0], "energy_drift": (c1[4] - c0[4]) / c0[4],
+                     "seconds": el}
+        del rho, th
+        torch.cuda.empty_cache()
+    del ref_rho, ref_th
+    torch.cuda.empty_cache()
+    return out
+
+
 def main(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--n", type=int, default=512)
@@ -58,24 +86,9 @@ def main(argv=None):
     from . import lb
     from . import workloads as wl
     torch.cuda.set_device(0)
-    th0 = lb.lb_theta0()
-    fields = wl.thermoacoustic_pulse(a.n, th0, device="cuda")
+    fields = wl.thermoacoustic_pulse(a.n, lb.lb_theta0(), device="cuda")
     out = {"n": a.n, "steps": a.steps, "workload": "thermoacoustic pulse (1e-2, sigma 8) + theta Fourier box (1e-3)"}
-    ref_rho, ref_th, c0, c1, el = run(a.n, a.steps, "f64", fields)
-    out["f64"] = {"seconds": el, "mass_drift": (c1[0] - c0[0]) / c0[0], "energy_drift": (c1[4] - c0[4]) / c0[4]}
-    dr = ref_rho - 1.0
-    dt = ref_th - th0
-    nr, nt = float(torch.linalg.vector_norm(dr)), float(torch.linalg.vector_norm(dt))
-    for prec in ("f32", "f16", "bf16"):
-        rho, th, c0, c1, el = run(a.n, a.steps, prec, fields)
-        er = float(torch.linalg.vector_norm(rho - ref_rho)) / nr
-        et = float(torch.linalg.vector_norm(th - ref_th)) / nt
-        out[prec] = {"rel_l2_rho_fluct": er, "rel_l2_theta_fluct": et,
-                     "max_abs_rho_err": float((rho - ref_rho).abs().max()),
-                     "mass_drift": (c1[0] - c0[0]) / c0[0], "energy_drift": (c1[4] - c0[4]) / c0[4],
-                     "seconds": el}
-        del rho, th
-        torch.cuda.empty_cache()
+    out.update(compare(a.n, a.steps, ("f32", "f16", "bf16"), fields))
     print(json.dumps(out))
 
 
