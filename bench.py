@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-batch", action="store_true", help="skip the batched 64-simulation sweep")
+    p.add_argument("--no-accuracy", action="store_true",
+                   help="skip the error of the reduced-precision runs against the GPU FP64 mode")
     p.add_argument("--batch-steps", type=int, default=1000)
     p.add_argument("--kernel", type=int, default=None,
                    help="step kernel for the headline run (LB_KERNEL_* id); default: the fastest that applies")
@@ -201,7 +203,10 @@ def run_batch(lb, wl, torch, steps, count=64):
             lb.lb_set_fields(lb.lb_batch_sim(b, k), fl["rho"], fl["u"], fl["theta"])
         lb.lb_batch_sync(b)
         tx, ry, ms = lb.lb_batch_tune(b, reps=3)
-        out["tile"] = [tx, ry]
+        # tuned per mode: [tx, ry, rows per thread]; ry = 0: linear tiles of tx consecutive
+        # nodes (or node pairs)
+        out["plan"] = {"graph": list(lb.lb_batch_get_plan(b, lb.LB_BATCH_GRAPH)),
+                       "persistent": list(lb.lb_batch_get_plan(b, lb.LB_BATCH_PERSISTENT))}
         stream = torch.cuda.current_stream()
         for name, mode in (("graph", lb.LB_BATCH_GRAPH), ("persistent", lb.LB_BATCH_PERSISTENT),
                            ("sequential", lb.LB_BATCH_SEQUENTIAL)):
@@ -354,6 +359,18 @@ def main():
             steps = max(3, args.steps // 10) if prec == "f64" else max(5, args.steps // 2)
             results[prec], _ = timed_run(prec, None, steps, 3, False)
 
+    # the error at which each timed precision runs: the same fields and steps against the GPU FP64
+    # mode (itself matched to the FP64 oracle to 1e-12), with the kernel that was timed
+    accuracy = None
+    if not args.no_accuracy and rank == 0 and world == 1:
+        from paper_1909_08406_gb300 import accuracy_report
+        precs_acc = [p for p in results if p != "f64"]
+        acc = accuracy_report.compare(n, args.steps, precs_acc, fields,
+                                      {p: results[p]["kernel_id"] for p in precs_acc})
+        accuracy = {"vs": "GPU FP64 mode, same fields and steps", "steps": args.steps,
+                    **{p: {k: acc[p][k] for k in ("rel_l2_rho_fluct", "rel_l2_theta_fluct", "max_abs_rho_err",
+                                                  "mass_drift", "energy_drift")} for p in precs_acc}}
+
     batch = None
     if not args.no_batch and world == 1:
         del fields
@@ -412,6 +429,7 @@ def main():
                              "frac_of_hbm": v["achieved_gbs"] / peak, "ms_per_step": v["ms_per_step"],
                              "steps": v["steps"], "kernel": v["kernel"]} for p, v in results.items()},
         "by_kernel": by_kernel,
+        "accuracy": accuracy,
         "batch": batch,
         "gpu_launches": r["steps"],
         "clocks": clocks,

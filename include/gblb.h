@@ -242,13 +242,27 @@ lb_status lb_batch_init(lb_batch **out, int nsims, const lb_grid *grids, const d
 int lb_batch_size(const lb_batch *b);
 /* Context of simulation sim (0 <= sim < size), owned by the batch; NULL if out of range. */
 lb_ctx *lb_batch_sim(lb_batch *b, int sim);
-/* Autotuner: times every tile shape (TX x-nodes by RY rows per CTA) on this
- * batch for reps steps each (the state is not advanced), keeps the fastest,
- * and reports it and its time per step in ms.  Any output may be NULL. */
+/* Autotuner.  For each of the two batched launch modes (LB_BATCH_GRAPH and
+ * LB_BATCH_PERSISTENT, tuned separately) it times every tile shape (TX x-nodes
+ * by RY rows per CTA, or RY = 0: TX consecutive entries of a simulation's
+ * x-fastest node order, crossing row ends), with one and, where allowed, two
+ * rows per thread, on this batch for reps steps each (the state is not
+ * advanced), and keeps the fastest.  Reports the graph mode's shape and time
+ * per step in ms (lb_batch_get_plan gives both modes').  Any output may be NULL. */
 lb_status lb_batch_tune(lb_batch *b, int reps, int *tx, int *ry, double *ms_per_step);
-/* Tile shape in use; lb_batch_set_tile accepts (16,4) (16,8) (32,2) (32,4) (64,1) (64,2) (128,1). */
+/* Tile shape of the graph mode; lb_batch_set_tile sets it for both modes and accepts
+ * (16,4) (16,8) (32,2) (32,4) (64,1) (64,2) (128,1) and the linear shapes (64,0) (128,0). */
 lb_status lb_batch_get_tile(const lb_batch *b, int *tx, int *ry);
 lb_status lb_batch_set_tile(lb_batch *b, int tx, int ry);
+/* Rows updated per thread, for both modes: 1, or 2 (nodes (y, x) and (y + 1, x) with
+ * packed FP32x2 arithmetic; FP32/FP16/BF16 storage with every simulation's ny even,
+ * else LB_ERR_ARG).  Two is the default where allowed; lb_batch_tune may change it.
+ * lb_batch_get_rows reports the graph mode's (-1 for NULL). */
+lb_status lb_batch_set_rows(lb_batch *b, int rows_per_thread);
+int lb_batch_get_rows(const lb_batch *b);
+/* Tile shape and rows per thread of mode LB_BATCH_GRAPH or LB_BATCH_PERSISTENT (else
+ * LB_ERR_ARG).  Any output may be NULL. */
+lb_status lb_batch_get_plan(const lb_batch *b, int mode, int *tx, int *ry, int *rows_per_thread);
 /* Advance every simulation by n steps in the given mode (LB_BATCH_*).  Asynchronous. */
 lb_status lb_batch_step(lb_batch *b, int64_t n, int mode);
 /* Cycle budget of each grid-barrier wait of the persistent mode (default 4e9) and, for

@@ -2,9 +2,13 @@
 // and relaxation times advanced together.
 //
 // Work list: every simulation's nodes are cut into tiles of TX consecutive x
-// by RY consecutive rows; the tiles of all simulations are numbered
-// back to back (tile0[k] is the first tile of simulation k) and a CTA finds
-// its simulation by binary search.  Modes:
+// by RY consecutive rows, or (RY = 0, linear tiles) into runs of TX
+// consecutive entries of its x-fastest node order that cross row ends, so a
+// warp reads 32 consecutive values of each population whatever nx is; the
+// tiles of all simulations are numbered back to back (tile0[k] is the first
+// tile of simulation k) and a CTA finds its simulation by binary search.
+// With FP32 arithmetic a thread may update one node or two (y, y + 1) with
+// packed FP32x2 arithmetic.  Modes:
 //   LB_BATCH_GRAPH       one batched launch per time step, the n launches
 //                        captured once into a CUDA graph and replayed;
 //   LB_BATCH_PERSISTENT  one cooperative launch for all n steps: CTAs stride
@@ -12,8 +16,8 @@
 //                        steps (bounded spin; expiry -> LB_ERR_TIMEOUT);
 //   LB_BATCH_SEQUENTIAL  per simulation, one lb_step-style launch per step
 //                        (the baseline).
-// The tile shape (TX, RY) is chosen by lb_batch_tune, which times each
-// candidate shape on the batch itself.
+// The tile shape (TX, RY) and the rows per thread are chosen by lb_batch_tune,
+// which times each candidate on the batch itself.
 #include <math.h>
 #include <string.h>
 
@@ -33,9 +37,47 @@ struct BatchSim {
     float tbf;
     double tbd;
     int64_t tile0;  // first tile of this simulation in the work list
+    int64_t units;  // linear tiles: nodes (one row per thread) or node pairs (two rows per thread)
     int tiles_x;    // x-chunks per row group
     int pad;
 };
+
+__device__ __forceinline__ int find_sim(const BatchSim* __restrict__ sims, int nsims, int64_t t) {
+    int lo = 0, hi = nsims - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sims[mid].tile0 <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Row (or row pair) and x of this thread's entry of tile t of simulation S; false if the
+// entry lies past the simulation's end.  ry = 0: linear tiles of tx entries.
+__device__ __forceinline__ bool tile_entry(const BatchSim& S, int64_t t, int tx, int ry, int64_t nrows, int64_t& row,
+                                           int& x) {
+    const int64_t local = t - S.tile0;
+    if (ry == 0) {
+        const int64_t i = local * tx + (int64_t)threadIdx.x;
+        if (i >= S.units) return false;
+        if (S.units <= 0xffffffffLL) {
+            const unsigned r = (unsigned)i / (unsigned)S.d.nx;
+            row = r;
+            x = (int)((unsigned)i - r * (unsigned)S.d.nx);
+        } else {
+            row = i / S.d.nx;
+            x = (int)(i - row * S.d.nx);
+        }
+        return true;
+    }
+    const int64_t rg = local / S.tiles_x;
+    const int xc = (int)(local - rg * S.tiles_x);
+    x = xc * tx + (int)(threadIdx.x % tx);
+    row = rg * ry + (int64_t)(threadIdx.x / tx);
+    return x < S.d.nx && row < nrows;
+}
 
 template <class R>
 __device__ __forceinline__ R tb_of(const BatchSim& s);
@@ -56,21 +98,10 @@ __device__ __forceinline__ void batch_tile(const BatchSim* __restrict__ sims, in
                                            const Consts<typename Codec::R>& K, int tx, int ry, int* err) {
     using R = typename Codec::R;
     using T = typename Codec::raw_t;
-    int lo = 0, hi = nsims - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (sims[mid].tile0 <= t)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    const BatchSim& S = sims[lo];
-    const int64_t local = t - S.tile0;
-    const int64_t rg = local / S.tiles_x;
-    const int xc = (int)(local - rg * S.tiles_x);
-    const int x = xc * tx + (int)(threadIdx.x % tx);
-    const int64_t row = rg * ry + (int64_t)(threadIdx.x / tx);
-    if (x >= S.d.nx || row >= S.d.rows) return;
+    const BatchSim& S = sims[find_sim(sims, nsims, t)];
+    int64_t row;
+    int x;
+    if (!tile_entry(S, t, tx, ry, S.d.rows, row, x)) return;
     const int y = (int)(row % S.d.ny);
     const int64_t zr = row / S.d.ny;
     const int z = (int)(zr % S.d.nz);
@@ -80,26 +111,16 @@ __device__ __forceinline__ void batch_tile(const BatchSim* __restrict__ sims, in
 }
 
 // Two-row tiles (FP32 arithmetic, every simulation with ny even): a tile is TX x-nodes by RY
-// row pairs; each thread updates (y, x) and (y + 1, x) with packed FP32x2 arithmetic.
+// row pairs (or TX consecutive (row pair, x) entries); each thread updates (y, x) and
+// (y + 1, x) with packed FP32x2 arithmetic.
 template <class Codec, bool PROJECT, class Ld>
 __device__ __forceinline__ void batch_tile2(const BatchSim* __restrict__ sims, int nsims, int64_t t, int parity,
                                             const Consts<float>& K, int tx, int ry, int* err) {
     using T = typename Codec::raw_t;
-    int lo = 0, hi = nsims - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (sims[mid].tile0 <= t)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    const BatchSim& S = sims[lo];
-    const int64_t local = t - S.tile0;
-    const int64_t rg = local / S.tiles_x;
-    const int xc = (int)(local - rg * S.tiles_x);
-    const int x = xc * tx + (int)(threadIdx.x % tx);
-    const int64_t rp = rg * ry + (int64_t)(threadIdx.x / tx);
-    if (x >= S.d.nx || rp >= S.d.rows / 2) return;
+    const BatchSim& S = sims[find_sim(sims, nsims, t)];
+    int64_t rp;
+    int x;
+    if (!tile_entry(S, t, tx, ry, S.d.rows / 2, rp, x)) return;
     const int nyh = S.d.ny >> 1;
     const int y = 2 * (int)(rp % nyh);
     const int64_t zr = rp / nyh;
@@ -109,8 +130,17 @@ __device__ __forceinline__ void batch_tile2(const BatchSim* __restrict__ sims, i
                                    S.tbf, err, s, z, y, x);
 }
 
+// Resident CTAs per SM the register allocation is sized for.  One node per thread in FP32
+// arithmetic fits 80 registers without spills (6 CTAs of 128 threads, 24 warps per SM); the
+// persistent kernel's loop state needs 96 (5 CTAs); two nodes per thread (packed FP32x2) and
+// FP64 arithmetic need about 168 (3 CTAs).
+template <class Codec, bool TWO>
+constexpr int batch_min_blocks(bool persistent) {
+    return (TWO || sizeof(typename Codec::R) == 8) ? 3 : (persistent ? 5 : 6);
+}
+
 template <class Codec, bool PROJECT, bool TWO>
-__global__ void __launch_bounds__(128, 3) k_batch_step(const BatchSim* __restrict__ sims, int nsims, int parity,
+__global__ void __launch_bounds__(128, batch_min_blocks<Codec, TWO>(false)) k_batch_step(const BatchSim* __restrict__ sims, int nsims, int parity,
                                                     Consts<typename Codec::KS> K, int tx, int ry, int* err) {
     if constexpr (TWO)
         batch_tile2<Codec, PROJECT, LoadNC>(sims, nsims, blockIdx.x, parity, K, tx, ry, err);
@@ -155,7 +185,7 @@ __device__ __forceinline__ bool grid_sync(GridBar* bar, unsigned expected, long 
 }
 
 template <class Codec, bool PROJECT, bool TWO>
-__global__ void __launch_bounds__(128, 3) k_batch_persistent(const BatchSim* __restrict__ sims, int nsims, int64_t ntiles,
+__global__ void __launch_bounds__(128, batch_min_blocks<Codec, TWO>(true)) k_batch_persistent(const BatchSim* __restrict__ sims, int nsims, int64_t ntiles,
                                                           int64_t nsteps, int parity0, Consts<typename Codec::KS> K,
                                                           int tx, int ry, int* err, GridBar* bar, unsigned expected,
                                                           long long limit) {
@@ -197,7 +227,10 @@ static const Consts<typename Codec::KS>& consts_of(const LaunchConsts& c) {
 
 using namespace gblb;
 
-static const int kTileShapes[][2] = {{16, 4}, {16, 8}, {32, 2}, {32, 4}, {64, 1}, {64, 2}, {128, 1}};
+// (TX, RY); RY = 0: linear tiles of TX entries
+static const int kTileShapes[][2] = {{16, 4}, {16, 8}, {32, 2}, {32, 4}, {64, 1}, {64, 2}, {128, 1}, {64, 0}, {128, 0}};
+
+static int tile_threads(int tx, int ry) { return ry == 0 ? tx : tx * ry; }
 
 struct lb_batch {
     int n = 0;
@@ -209,18 +242,24 @@ struct lb_batch {
     cudaStream_t user = nullptr;
     cudaStream_t ps = nullptr;  // private stream (graph capture needs a non-legacy stream)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr, t0 = nullptr, t1 = nullptr;
-    BatchSim* d_sims = nullptr;
+    // One work list per launch mode: the graph-replayed batched launch and the persistent
+    // kernel are tuned separately (they differ in registers, occupancy and load path).
+    struct Plan {
+        int tx = 32, ry = 4;
+        bool two_rows = false;  // two rows per thread (FP32x2)
+        int64_t ntiles = 0;
+        BatchSim* d_sims = nullptr;
+    };
+    Plan gp, pp;  // LB_BATCH_GRAPH, LB_BATCH_PERSISTENT
     std::vector<BatchSim> h_sims;
-    int tx = 32, ry = 4;
-    bool two_rows = false;  // FP32 arithmetic and every simulation with ny even: two rows per thread
-    int64_t ntiles = 0;
+    bool two_rows_ok = false;  // FP32 arithmetic and every simulation with ny even
     int* d_err = nullptr;
     GridBar* d_bar = nullptr;
     long long wait_limit = 4000000000LL;
     unsigned extra_arrivals = 0;
-    struct GraphEntry {
+    struct GraphEntry {  // captured for the graph plan in use; dropped when it changes
         int64_t steps;
-        int parity, tx, ry;
+        int parity;
         cudaGraphExec_t exec;
     };
     std::vector<GraphEntry> graphs;
@@ -246,8 +285,8 @@ static lb_status bfail(lb_batch* b, lb_status s, const std::string& m) {
                          std::string(#call) + ": " + cudaGetErrorString(e_));                         \
     } while (0)
 
-// Lay out the work list for tile shape (tx, ry) and upload it.
-static lb_status plan(lb_batch* b, int tx, int ry) {
+// Lay out the work list of plan P for tile shape (tx, ry) and rows per thread, and upload it.
+static lb_status plan(lb_batch* b, lb_batch::Plan& P, int tx, int ry, bool two_rows) {
     int64_t t = 0;
     for (int k = 0; k < b->n; ++k) {
         BatchSim& s = b->h_sims[k];
@@ -259,17 +298,21 @@ static lb_status plan(lb_batch* b, int tx, int ry) {
         s.tbf = (float)c->twobeta;
         s.tiles_x = (int)((c->d.nx + tx - 1) / tx);
         s.tile0 = t;
-        const int64_t rows = b->two_rows ? c->d.rows / 2 : c->d.rows;
-        t += (int64_t)s.tiles_x * ((rows + ry - 1) / ry);
+        const int64_t rows = two_rows ? c->d.rows / 2 : c->d.rows;
+        s.units = rows * c->d.nx;
+        t += ry == 0 ? (s.units + tx - 1) / tx : (int64_t)s.tiles_x * ((rows + ry - 1) / ry);
     }
     if (t > 0x7fffffffLL) return bfail(b, LB_ERR_ARG, "batch work list too long for one launch");
-    b->ntiles = t;
-    b->tx = tx;
-    b->ry = ry;
-    BCK(b, cudaMemcpyAsync(b->d_sims, b->h_sims.data(), sizeof(BatchSim) * b->n, cudaMemcpyHostToDevice, b->ps));
+    P.ntiles = t;
+    P.tx = tx;
+    P.ry = ry;
+    P.two_rows = two_rows;
+    BCK(b, cudaMemcpyAsync(P.d_sims, b->h_sims.data(), sizeof(BatchSim) * b->n, cudaMemcpyHostToDevice, b->ps));
     BCK(b, cudaStreamSynchronize(b->ps));
-    for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
-    b->graphs.clear();
+    if (&P == &b->gp) {
+        for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
+        b->graphs.clear();
+    }
     return LB_OK;
 }
 
@@ -277,24 +320,25 @@ static cudaError_t launch_batch_step(lb_batch* b, int parity, cudaStream_t st) {
     const LaunchConsts& lc = lattice_consts();
     return dispatch_codec(b->prec, [&](auto codec) {
         using C = decltype(codec);
-        const unsigned grid = (unsigned)b->ntiles, block = (unsigned)(b->tx * b->ry);
+        const lb_batch::Plan& P = b->gp;
+        const unsigned grid = (unsigned)P.ntiles, block = (unsigned)tile_threads(P.tx, P.ry);
         if constexpr (std::is_same<typename C::R, float>::value) {
-            if (b->two_rows) {
+            if (P.two_rows) {
                 if (b->project)
-                    k_batch_step<C, true, true><<<grid, block, 0, st>>>(b->d_sims, b->n, parity, consts_of<C>(lc),
-                                                                        b->tx, b->ry, b->d_err);
+                    k_batch_step<C, true, true><<<grid, block, 0, st>>>(P.d_sims, b->n, parity, consts_of<C>(lc),
+                                                                        P.tx, P.ry, b->d_err);
                 else
-                    k_batch_step<C, false, true><<<grid, block, 0, st>>>(b->d_sims, b->n, parity, consts_of<C>(lc),
-                                                                         b->tx, b->ry, b->d_err);
+                    k_batch_step<C, false, true><<<grid, block, 0, st>>>(P.d_sims, b->n, parity, consts_of<C>(lc),
+                                                                         P.tx, P.ry, b->d_err);
                 return cudaGetLastError();
             }
         }
         if (b->project)
-            k_batch_step<C, true, false><<<grid, block, 0, st>>>(b->d_sims, b->n, parity, consts_of<C>(lc), b->tx,
-                                                                 b->ry, b->d_err);
+            k_batch_step<C, true, false><<<grid, block, 0, st>>>(P.d_sims, b->n, parity, consts_of<C>(lc), P.tx,
+                                                                 P.ry, b->d_err);
         else
-            k_batch_step<C, false, false><<<grid, block, 0, st>>>(b->d_sims, b->n, parity, consts_of<C>(lc), b->tx,
-                                                                  b->ry, b->d_err);
+            k_batch_step<C, false, false><<<grid, block, 0, st>>>(P.d_sims, b->n, parity, consts_of<C>(lc), P.tx,
+                                                                  P.ry, b->d_err);
         return cudaGetLastError();
     });
 }
@@ -307,23 +351,25 @@ static cudaError_t launch_persistent(lb_batch* b, int64_t nsteps, int parity, cu
                      unsigned, long long) =
             b->project ? k_batch_persistent<C, true, false> : k_batch_persistent<C, false, false>;
         if constexpr (std::is_same<typename C::R, float>::value) {
-            if (b->two_rows) kern = b->project ? k_batch_persistent<C, true, true> : k_batch_persistent<C, false, true>;
+            if (b->pp.two_rows)
+                kern = b->project ? k_batch_persistent<C, true, true> : k_batch_persistent<C, false, true>;
         }
         int per_sm = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, b->tx * b->ry, 0);
+        const lb_batch::Plan& P = b->pp;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tile_threads(P.tx, P.ry), 0);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) return cudaErrorInvalidConfiguration;
         int64_t grid = (int64_t)per_sm * b->sms;
-        if (grid > b->ntiles) grid = b->ntiles;
+        if (grid > P.ntiles) grid = P.ntiles;
         *grid_out = (int)grid;
         unsigned expected = (unsigned)grid + b->extra_arrivals;
         e = cudaMemsetAsync(b->d_bar, 0, sizeof(GridBar), st);
         if (e != cudaSuccess) return e;
-        const BatchSim* sims = b->d_sims;
+        const BatchSim* sims = P.d_sims;
         int nsims = b->n;
-        int64_t ntiles = b->ntiles;
+        int64_t ntiles = P.ntiles;
         Consts<typename C::KS> K = consts_of<C>(lc);
-        int tx = b->tx, ry = b->ry;
+        int tx = P.tx, ry = P.ry;
         int* err = b->d_err;
         GridBar* bar = b->d_bar;
         long long limit = b->wait_limit;
@@ -331,7 +377,7 @@ static cudaError_t launch_persistent(lb_batch* b, int64_t nsteps, int parity, cu
                         (void*)&tx, (void*)&ry, (void*)&err, (void*)&bar, (void*)&expected, (void*)&limit};
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)grid);
-        cfg.blockDim = dim3((unsigned)(tx * ry));
+        cfg.blockDim = dim3((unsigned)tile_threads(tx, ry));
         cfg.dynamicSmemBytes = 0;
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
@@ -368,8 +414,8 @@ lb_status lb_batch_init(lb_batch** out, int nsims, const lb_grid* grids, const d
         b->ctx.push_back(c);
     }
     b->h_sims.resize(nsims);
-    b->two_rows = precision != LB_F64;
-    for (auto* c : b->ctx) b->two_rows = b->two_rows && c->d.ny % 2 == 0 && c->d.plane < ((int64_t)1 << 32);
+    b->two_rows_ok = precision != LB_F64;
+    for (auto* c : b->ctx) b->two_rows_ok = b->two_rows_ok && c->d.ny % 2 == 0 && c->d.plane < ((int64_t)1 << 32);
     cudaError_t e = cudaGetDevice(&b->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->ps, cudaStreamNonBlocking);
@@ -377,7 +423,8 @@ lb_status lb_batch_init(lb_batch** out, int nsims, const lb_grid* grids, const d
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreate(&b->t0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->t1);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_sims, sizeof(BatchSim) * nsims);
+    if (e == cudaSuccess) e = cudaMalloc(&b->gp.d_sims, sizeof(BatchSim) * nsims);
+    if (e == cudaSuccess) e = cudaMalloc(&b->pp.d_sims, sizeof(BatchSim) * nsims);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_bar, sizeof(GridBar));
     if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
@@ -385,7 +432,8 @@ lb_status lb_batch_init(lb_batch** out, int nsims, const lb_grid* grids, const d
         lb_batch_destroy(b);
         return bfail(nullptr, LB_ERR_CUDA, std::string("lb_batch_init: ") + cudaGetErrorString(e));
     }
-    lb_status s = plan(b, 32, 4);
+    lb_status s = plan(b, b->gp, 32, 4, b->two_rows_ok);
+    if (s == LB_OK) s = plan(b, b->pp, 32, 4, b->two_rows_ok);
     if (s != LB_OK) {
         std::string m = b->msg;
         lb_batch_destroy(b);
@@ -405,13 +453,51 @@ lb_status lb_batch_set_tile(lb_batch* b, int tx, int ry) {
     for (auto& t : kTileShapes) known |= (t[0] == tx && t[1] == ry);
     if (!known) return bfail(b, LB_ERR_ARG, "lb_batch_set_tile: not one of the tile shapes");
     BCK(b, cudaSetDevice(b->device));
-    return plan(b, tx, ry);
+    lb_status s = plan(b, b->gp, tx, ry, b->gp.two_rows);
+    return s != LB_OK ? s : plan(b, b->pp, tx, ry, b->pp.two_rows);
 }
 
 lb_status lb_batch_get_tile(const lb_batch* b, int* tx, int* ry) {
     if (!b) return LB_ERR_ARG;
-    if (tx) *tx = b->tx;
-    if (ry) *ry = b->ry;
+    if (tx) *tx = b->gp.tx;
+    if (ry) *ry = b->gp.ry;
+    return LB_OK;
+}
+
+lb_status lb_batch_set_rows(lb_batch* b, int rows_per_thread) {
+    if (!b || (rows_per_thread != 1 && rows_per_thread != 2)) return bfail(b, LB_ERR_ARG, "lb_batch_set_rows: 1 or 2");
+    if (rows_per_thread == 2 && !b->two_rows_ok)
+        return bfail(b, LB_ERR_ARG, "lb_batch_set_rows: two rows per thread need FP32 arithmetic and ny even");
+    BCK(b, cudaSetDevice(b->device));
+    lb_status s = plan(b, b->gp, b->gp.tx, b->gp.ry, rows_per_thread == 2);
+    return s != LB_OK ? s : plan(b, b->pp, b->pp.tx, b->pp.ry, rows_per_thread == 2);
+}
+
+int lb_batch_get_rows(const lb_batch* b) { return b ? (b->gp.two_rows ? 2 : 1) : -1; }
+
+lb_status lb_batch_get_plan(const lb_batch* b, int mode, int* tx, int* ry, int* rows_per_thread) {
+    if (!b || (mode != LB_BATCH_GRAPH && mode != LB_BATCH_PERSISTENT)) return LB_ERR_ARG;
+    const lb_batch::Plan& P = mode == LB_BATCH_GRAPH ? b->gp : b->pp;
+    if (tx) *tx = P.tx;
+    if (ry) *ry = P.ry;
+    if (rows_per_thread) *rows_per_thread = P.two_rows ? 2 : 1;
+    return LB_OK;
+}
+
+// Time `reps` launches of one batched step in the given mode with the current plans (after one
+// untimed launch); the trial steps read buf[cur] and write buf[1 - cur] without flipping.
+static lb_status time_trial(lb_batch* b, int mode, int parity, int reps, float* ms) {
+    int grid = 0;
+    auto launch = [&]() {
+        return mode == LB_BATCH_GRAPH ? launch_batch_step(b, parity, b->ps) : launch_persistent(b, 1, parity, b->ps, &grid);
+    };
+    BCK(b, launch());
+    BCK(b, cudaEventRecord(b->t0, b->ps));
+    for (int r = 0; r < reps; ++r) BCK(b, launch());
+    BCK(b, cudaEventRecord(b->t1, b->ps));
+    BCK(b, cudaEventSynchronize(b->t1));
+    BCK(b, cudaEventElapsedTime(ms, b->t0, b->t1));
+    *ms /= reps;
     return LB_OK;
 }
 
@@ -419,34 +505,38 @@ lb_status lb_batch_tune(lb_batch* b, int reps, int* tx_out, int* ry_out, double*
     if (!b) return LB_ERR_ARG;
     BCK(b, cudaSetDevice(b->device));
     if (reps < 1) reps = 3;
-    // the trial steps read buf[cur] and write buf[1 - cur] without flipping: the state is unchanged
+    // the trial steps leave the state unchanged (see time_trial)
     BCK(b, cudaEventRecord(b->ev_in, b->user));
     BCK(b, cudaStreamWaitEvent(b->ps, b->ev_in, 0));
     const int parity = b->ctx[0]->cur;
-    float best = 1e30f;
-    int bt = b->tx, br = b->ry;
-    for (auto& shape : kTileShapes) {
-        lb_status s = plan(b, shape[0], shape[1]);
-        if (s != LB_OK) return s;
-        BCK(b, launch_batch_step(b, parity, b->ps));  // warm-up
-        BCK(b, cudaEventRecord(b->t0, b->ps));
-        for (int r = 0; r < reps; ++r) BCK(b, launch_batch_step(b, parity, b->ps));
-        BCK(b, cudaEventRecord(b->t1, b->ps));
-        BCK(b, cudaEventSynchronize(b->t1));
-        float ms = 0.f;
-        BCK(b, cudaEventElapsedTime(&ms, b->t0, b->t1));
-        ms /= reps;
-        if (ms < best) {
-            best = ms;
-            bt = shape[0];
-            br = shape[1];
+    float best_ms = 0.f;
+    for (int mode : {LB_BATCH_GRAPH, LB_BATCH_PERSISTENT}) {
+        lb_batch::Plan& P = mode == LB_BATCH_GRAPH ? b->gp : b->pp;
+        float best = 1e30f;
+        int bt = P.tx, br = P.ry;
+        bool b2 = P.two_rows;
+        for (int two = 0; two <= (b->two_rows_ok ? 1 : 0); ++two) {
+            for (auto& shape : kTileShapes) {
+                lb_status s = plan(b, P, shape[0], shape[1], two != 0);
+                if (s != LB_OK) return s;
+                float ms = 0.f;
+                s = time_trial(b, mode, parity, reps, &ms);
+                if (s != LB_OK) return s;
+                if (ms < best) {
+                    best = ms;
+                    bt = shape[0];
+                    br = shape[1];
+                    b2 = two != 0;
+                }
+            }
         }
+        lb_status s = plan(b, P, bt, br, b2);
+        if (s != LB_OK) return s;
+        if (mode == LB_BATCH_GRAPH) best_ms = best;
     }
-    lb_status s = plan(b, bt, br);
-    if (s != LB_OK) return s;
-    if (tx_out) *tx_out = bt;
-    if (ry_out) *ry_out = br;
-    if (ms_out) *ms_out = best;
+    if (tx_out) *tx_out = b->gp.tx;
+    if (ry_out) *ry_out = b->gp.ry;
+    if (ms_out) *ms_out = best_ms;
     return LB_OK;
 }
 
@@ -474,7 +564,7 @@ lb_status lb_batch_step(lb_batch* b, int64_t nsteps, int mode) {
     if (mode == LB_BATCH_GRAPH) {
         cudaGraphExec_t exec = nullptr;
         for (auto& g : b->graphs)
-            if (g.steps == nsteps && g.parity == parity && g.tx == b->tx && g.ry == b->ry) exec = g.exec;
+            if (g.steps == nsteps && g.parity == parity) exec = g.exec;
         if (!exec) {
             cudaGraph_t graph = nullptr;
             BCK(b, cudaStreamBeginCapture(b->ps, cudaStreamCaptureModeThreadLocal));
@@ -490,7 +580,7 @@ lb_status lb_batch_step(lb_batch* b, int64_t nsteps, int mode) {
                 cudaGraphExecDestroy(b->graphs.front().exec);
                 b->graphs.erase(b->graphs.begin());
             }
-            b->graphs.push_back({nsteps, parity, b->tx, b->ry, exec});
+            b->graphs.push_back({nsteps, parity, exec});
         }
         BCK(b, cudaGraphLaunch(exec, b->ps));
     } else if (mode == LB_BATCH_PERSISTENT) {
@@ -535,7 +625,8 @@ lb_status lb_batch_destroy(lb_batch* b) {
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     if (b->t0) cudaEventDestroy(b->t0);
     if (b->t1) cudaEventDestroy(b->t1);
-    cudaFree(b->d_sims);
+    cudaFree(b->gp.d_sims);
+    cudaFree(b->pp.d_sims);
     cudaFree(b->d_err);
     cudaFree(b->d_bar);
     delete b;

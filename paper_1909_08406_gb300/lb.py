@@ -264,14 +264,18 @@ def _bind_batch():
     L.lb_batch_tune.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     L.lb_batch_get_tile.argtypes = [vp, vp, vp]
     L.lb_batch_set_tile.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.lb_batch_set_rows.argtypes = [vp, ctypes.c_int]
+    L.lb_batch_get_rows.argtypes = [vp]
+    L.lb_batch_get_rows.restype = ctypes.c_int
+    L.lb_batch_get_plan.argtypes = [vp, ctypes.c_int, vp, vp, vp]
     L.lb_batch_step.argtypes = [vp, i64, ctypes.c_int]
     L.lb_batch_set_wait.argtypes = [vp, ctypes.c_longlong, ctypes.c_uint]
     L.lb_batch_sync.argtypes = [vp]
     L.lb_batch_destroy.argtypes = [vp]
     L.lb_batch_last_error.argtypes = [vp]
     L.lb_batch_last_error.restype = ctypes.c_char_p
-    for name in ("lb_batch_init", "lb_batch_tune", "lb_batch_get_tile", "lb_batch_set_tile", "lb_batch_step",
-                 "lb_batch_set_wait", "lb_batch_sync", "lb_batch_destroy"):
+    for name in ("lb_batch_init", "lb_batch_tune", "lb_batch_get_tile", "lb_batch_set_tile", "lb_batch_set_rows",
+                 "lb_batch_get_plan", "lb_batch_step", "lb_batch_set_wait", "lb_batch_sync", "lb_batch_destroy"):
         getattr(L, name).restype = ctypes.c_int
     _batch_bound = True
     return L
@@ -310,7 +314,8 @@ def lb_batch_sim(b, sim):
 
 
 def lb_batch_tune(b, reps=3):
-    """Autotune the tile shape; returns (tx, ry, ms_per_step)."""
+    """Autotune the tile shape and rows per thread of both batched modes; returns the graph
+    mode's (tx, ry, ms_per_step)."""
     tx, ry, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
     _bcheck(_bind_batch().lb_batch_tune(b, int(reps), ctypes.byref(tx), ctypes.byref(ry), ctypes.byref(ms)), b)
     return tx.value, ry.value, ms.value
@@ -324,6 +329,22 @@ def lb_batch_get_tile(b):
 
 def lb_batch_set_tile(b, tx, ry):
     _bcheck(_bind_batch().lb_batch_set_tile(b, int(tx), int(ry)), b)
+
+
+def lb_batch_set_rows(b, rows_per_thread):
+    """1 or 2 rows per thread (2: packed FP32x2 on (y, y + 1); FP32 arithmetic, every ny even)."""
+    _bcheck(_bind_batch().lb_batch_set_rows(b, int(rows_per_thread)), b)
+
+
+def lb_batch_get_rows(b):
+    return int(_bind_batch().lb_batch_get_rows(b))
+
+
+def lb_batch_get_plan(b, mode):
+    """(tx, ry, rows_per_thread) of LB_BATCH_GRAPH or LB_BATCH_PERSISTENT."""
+    tx, ry, rows = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _bcheck(_bind_batch().lb_batch_get_plan(b, int(mode), ctypes.byref(tx), ctypes.byref(ry), ctypes.byref(rows)), b)
+    return tx.value, ry.value, rows.value
 
 
 def lb_batch_step(b, n, mode=LB_BATCH_GRAPH):

@@ -1,6 +1,7 @@
 """Batched sweep (many independent simulations, uneven grids, per-simulation tau):
-every mode against the FP64 oracle per simulation, the modes against each
-other, the autotuner, and the bounded grid barrier of the persistent mode."""
+every mode against the FP64 oracle per simulation, every tile shape and both
+rows-per-thread choices against the oracle, the modes against each other, the
+autotuner, and the bounded grid barrier of the persistent mode."""
 import numpy as np
 import pytest
 import torch
@@ -13,27 +14,31 @@ from paper_1909_08406_gb300 import workloads as wl
 pytestmark = pytest.mark.gpu
 
 GRIDS = [(12, 8, 6), (16, 16, 16), (20, 10, 8), (8, 8, 8), (33, 5, 4)]
+# every ny even (two rows per thread allowed); nx odd, so linear tiles cross row ends mid-warp
+GRIDS_EVEN = [(12, 8, 6), (16, 16, 16), (20, 10, 8), (8, 8, 8), (33, 6, 4)]
 TAUS = [0.55, 0.9, 0.6, 0.75, 1.0]
 TOL = {"f64": 1e-12, "f32": 2e-7}
 
 
-def _fields(k):
+def _fields(k, grids=GRIDS):
     th0 = lb.lb_theta0()
-    return wl.random_fields(*GRIDS[k], th0, seed=40 + k, du=0.03, drho=0.03, dtheta=0.03)
+    return wl.random_fields(*grids[k], th0, seed=40 + k, du=0.03, drho=0.03, dtheta=0.03)
 
 
-def _run(prec, mode, steps, tile=None):
-    b = lb.lb_batch_init(GRIDS, TAUS, prec)
+def _run(prec, mode, steps, tile=None, rows=None, grids=GRIDS):
+    b = lb.lb_batch_init(grids, TAUS, prec)
     try:
-        for k in range(len(GRIDS)):
-            fl = _fields(k)
+        for k in range(len(grids)):
+            fl = _fields(k, grids)
             lb.lb_set_fields(lb.lb_batch_sim(b, k), fl["rho"].cuda(), fl["u"].cuda(), fl["theta"].cuda())
+        if rows:
+            lb.lb_batch_set_rows(b, rows)
         if tile:
             lb.lb_batch_set_tile(b, *tile)
         lb.lb_batch_step(b, steps, mode)
         lb.lb_batch_sync(b)
         out = []
-        for k, (nx, ny, nz) in enumerate(GRIDS):
+        for k, (nx, ny, nz) in enumerate(grids):
             f = np.empty((2, 41, nz, ny, nx))
             lb.lb_get_populations(lb.lb_batch_sim(b, k), f)
             out.append(f)
@@ -55,12 +60,83 @@ def test_batch_modes_match_oracle(prec, mode):
         assert rel.max() <= TOL[prec], (k, rel.max())
 
 
-@pytest.mark.parametrize("tile", [(16, 4), (16, 8), (32, 2), (32, 4), (64, 1), (64, 2), (128, 1)])
+TILES = [(16, 4), (16, 8), (32, 2), (32, 4), (64, 1), (64, 2), (128, 1), (64, 0), (128, 0)]
+
+
+@pytest.mark.parametrize("tile", TILES)
 def test_batch_tile_shapes_agree(tile):
     a = _run("f32", lb.LB_BATCH_GRAPH, 4, tile=tile)
     b = _run("f32", lb.LB_BATCH_SEQUENTIAL, 4)
     for x, y in zip(a, b):
         assert np.max(np.abs(x - y) / y) <= 1e-7
+
+
+@pytest.mark.parametrize("rows", [1, 2])
+@pytest.mark.parametrize("tile", TILES)
+@pytest.mark.parametrize("mode", [lb.LB_BATCH_GRAPH, lb.LB_BATCH_PERSISTENT])
+def test_batch_rows_and_tiles_match_oracle(mode, tile, rows):
+    steps = 5
+    perm = lib_to_oracle_perm()
+    got = _run("f32", mode, steps, tile=tile, rows=rows, grids=GRIDS_EVEN)
+    for k in range(len(GRIDS_EVEN)):
+        fl = _fields(k, GRIDS_EVEN)
+        ref = oracle.step(oracle.init_fields(fl["rho"].numpy(), fl["u"].numpy(), fl["theta"].numpy()), TAUS[k], steps)
+        rel = np.abs(to_oracle_order(got[k], perm) - ref) / ref
+        assert rel.max() <= TOL["f32"], (k, rel.max())
+
+
+def test_two_rows_need_even_ny():
+    b = lb.lb_batch_init(GRIDS, TAUS, "f32")
+    try:
+        assert lb.lb_batch_get_rows(b) == 1
+        with pytest.raises(lb.LbError):
+            lb.lb_batch_set_rows(b, 2)
+        with pytest.raises(lb.LbError):
+            lb.lb_batch_set_tile(b, 100, 0)
+    finally:
+        lb.lb_batch_destroy(b)
+    b = lb.lb_batch_init(GRIDS_EVEN, TAUS, "f32")
+    try:
+        assert lb.lb_batch_get_rows(b) == 2
+        lb.lb_batch_set_rows(b, 1)
+        assert lb.lb_batch_get_rows(b) == 1
+        lb.lb_batch_set_tile(b, 64, 0)
+        for mode in (lb.LB_BATCH_GRAPH, lb.LB_BATCH_PERSISTENT):
+            assert lb.lb_batch_get_plan(b, mode) == (64, 0, 1)
+        with pytest.raises(lb.LbError):
+            lb.lb_batch_get_plan(b, lb.LB_BATCH_SEQUENTIAL)
+    finally:
+        lb.lb_batch_destroy(b)
+
+
+def test_tuned_plans_keep_results():
+    """After tuning, both batched modes (each with its own plan) still match the sequential mode."""
+    b = lb.lb_batch_init(GRIDS_EVEN, TAUS, "f32")
+    outs = []
+    try:
+        for k in range(len(GRIDS_EVEN)):
+            fl = _fields(k, GRIDS_EVEN)
+            lb.lb_set_fields(lb.lb_batch_sim(b, k), fl["rho"].cuda(), fl["u"].cuda(), fl["theta"].cuda())
+        lb.lb_batch_tune(b, reps=1)
+        for mode in (lb.LB_BATCH_GRAPH, lb.LB_BATCH_PERSISTENT, lb.LB_BATCH_SEQUENTIAL):
+            lb.lb_batch_step(b, 3, mode)
+            lb.lb_batch_sync(b)
+            outs.append([])
+            for k, (nx, ny, nz) in enumerate(GRIDS_EVEN):
+                f = np.empty((2, 41, nz, ny, nx))
+                lb.lb_get_populations(lb.lb_batch_sim(b, k), f)
+                outs[-1].append(f)
+    finally:
+        lb.lb_batch_destroy(b)
+    # three consecutive 3-step advances of the same batch: compare against the oracle instead
+    perm = lib_to_oracle_perm()
+    for k in range(len(GRIDS_EVEN)):
+        fl = _fields(k, GRIDS_EVEN)
+        f = oracle.init_fields(fl["rho"].numpy(), fl["u"].numpy(), fl["theta"].numpy())
+        for m in range(3):
+            f = oracle.step(f, TAUS[k], 3)
+            rel = np.abs(to_oracle_order(outs[m][k], perm) - f) / f
+            assert rel.max() <= TOL["f32"], (m, k, rel.max())
 
 
 def test_autotuner_keeps_state_and_picks_a_shape():
@@ -77,6 +153,9 @@ def test_autotuner_keeps_state_and_picks_a_shape():
         tx, ry, ms = lb.lb_batch_tune(b, reps=2)
         assert (tx, ry) == lb.lb_batch_get_tile(b)
         assert ms > 0
+        assert lb.lb_batch_get_plan(b, lb.LB_BATCH_GRAPH) == (tx, ry, lb.lb_batch_get_rows(b))
+        ptx, pry, prows = lb.lb_batch_get_plan(b, lb.LB_BATCH_PERSISTENT)
+        assert [ptx, pry] in [list(t) for t in TILES] and prows == 1  # GRIDS has an odd ny
         for k, t in enumerate(before):
             after = torch.empty_like(t)
             lb.lb_get_state(lb.lb_batch_sim(b, k), after)
