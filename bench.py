@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--no-accuracy", action="store_true",
                    help="skip the error of the reduced-precision runs against the GPU FP64 mode")
     p.add_argument("--batch-steps", type=int, default=1000)
+    p.add_argument("--batch-sims", type=int, default=64, help="simulations in the batched sweep")
     p.add_argument("--kernel", type=int, default=None,
                    help="step kernel for the headline run (LB_KERNEL_* id); default: the fastest that applies")
     return p.parse_args()
@@ -375,7 +376,7 @@ def main():
     if not args.no_batch and world == 1:
         del fields
         torch.cuda.empty_cache()
-        batch = run_batch(lb, wl, torch, args.batch_steps)
+        batch = run_batch(lb, wl, torch, args.batch_steps, count=args.batch_sims)
         fields = wl.thermoacoustic_pulse(n, th0, device="cuda")
 
     # end to end through the C ABI with host buffers: upload fields, K steps, read back all fields

@@ -236,7 +236,8 @@ typedef struct lb_batch lb_batch;
 #define LB_BATCH_PERSISTENT 1 /* one cooperative launch for all n steps, grid barrier between steps */
 #define LB_BATCH_SEQUENTIAL 2 /* each simulation stepped by its own launches (baseline) */
 
-/* nsims simulations, grids[k] and tau[k] each; precision and flags as lb_init. */
+/* nsims simulations, grids[k] and tau[k] each; precision and flags as lb_init.  Each
+ * simulation must have fewer than 2^31 nodes (LB_ERR_ARG otherwise). */
 lb_status lb_batch_init(lb_batch **out, int nsims, const lb_grid *grids, const double *tau, lb_precision precision,
                         unsigned flags, void *cuda_stream);
 int lb_batch_size(const lb_batch *b);

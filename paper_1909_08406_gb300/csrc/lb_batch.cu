@@ -31,15 +31,39 @@
 
 namespace gblb {
 
+// Division of n < 2^31 by a run-time constant d >= 1 as one multiply and shift
+// (Granlund and Montgomery, division by invariant integers using
+// multiplication, 1994): with 2^k >= d and m = ceil(2^(31+k) / d),
+// floor(n / d) = (n m) >> (31 + k).  Proof: write n = q d + r and
+// m d = 2^(31+k) + e with 0 <= e < d <= 2^k; then
+// n m / 2^(31+k) = q + (r + n e / 2^(31+k)) / d, and n e / 2^(31+k) < 1,
+// so the bracket stays below d.  m < 2^32 because d > 2^(k-1) for the
+// smallest such k.
+struct FastDiv {
+    uint32_t m, sh;
+};
+
+static FastDiv make_fastdiv(uint32_t d) {
+    uint32_t k = 0;
+    while ((1ull << k) < d) ++k;
+    FastDiv f;
+    f.m = (uint32_t)(((1ull << (31 + k)) + d - 1) / d);
+    f.sh = 31 + k;
+    return f;
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, FastDiv f) { return (uint32_t)(((uint64_t)n * f.m) >> f.sh); }
+
 struct BatchSim {
     void* buf[2];
     Dims d;
     float tbf;
     double tbd;
-    int64_t tile0;  // first tile of this simulation in the work list
-    int64_t units;  // linear tiles: nodes (one row per thread) or node pairs (two rows per thread)
-    int tiles_x;    // x-chunks per row group
-    int pad;
+    int64_t tile0;   // first tile of this simulation in the work list
+    uint32_t units;  // entries: nodes (one row per thread) or node pairs (two rows per thread)
+    uint32_t nrows;  // rows (one row per thread) or row pairs (two)
+    int tiles_x;     // x-chunks per row group
+    FastDiv fx, fy, fz, ft;  // division by nx, by ny (or ny / 2), by nz, by tiles_x
 };
 
 __device__ __forceinline__ int find_sim(const BatchSim* __restrict__ sims, int nsims, int64_t t) {
@@ -54,29 +78,33 @@ __device__ __forceinline__ int find_sim(const BatchSim* __restrict__ sims, int n
     return lo;
 }
 
-// Row (or row pair) and x of this thread's entry of tile t of simulation S; false if the
-// entry lies past the simulation's end.  ry = 0: linear tiles of tx entries.
-__device__ __forceinline__ bool tile_entry(const BatchSim& S, int64_t t, int tx, int ry, int64_t nrows, int64_t& row,
-                                           int& x) {
-    const int64_t local = t - S.tile0;
+// Node (s, z, y, x) of this thread's entry of tile t of simulation S (with two rows per thread,
+// y is the first row of the pair); false past the simulation's end.  Tiles: tx x-nodes by ry
+// rows (tx = 2^txs), or ry = 0: tx consecutive entries of the x-fastest order.  Every index
+// is below 2^31 (lb_batch_init rejects larger simulations).
+template <bool TWO>
+__device__ __forceinline__ bool tile_node(const BatchSim& S, int64_t t, int tx, int txs, int ry, int& s, int& z,
+                                          int& y, int& x) {
+    const uint32_t local = (uint32_t)(t - S.tile0);
+    uint32_t row;
     if (ry == 0) {
-        const int64_t i = local * tx + (int64_t)threadIdx.x;
+        const uint32_t i = local * (uint32_t)tx + threadIdx.x;
         if (i >= S.units) return false;
-        if (S.units <= 0xffffffffLL) {
-            const unsigned r = (unsigned)i / (unsigned)S.d.nx;
-            row = r;
-            x = (int)((unsigned)i - r * (unsigned)S.d.nx);
-        } else {
-            row = i / S.d.nx;
-            x = (int)(i - row * S.d.nx);
-        }
-        return true;
+        row = fdiv(i, S.fx);
+        x = (int)(i - row * (uint32_t)S.d.nx);
+    } else {
+        const uint32_t rg = fdiv(local, S.ft);
+        x = (int)((local - rg * (uint32_t)S.tiles_x) * (uint32_t)tx + (threadIdx.x & (uint32_t)(tx - 1)));
+        row = rg * (uint32_t)ry + (threadIdx.x >> txs);
+        if (x >= S.d.nx || row >= S.nrows) return false;
     }
-    const int64_t rg = local / S.tiles_x;
-    const int xc = (int)(local - rg * S.tiles_x);
-    x = xc * tx + (int)(threadIdx.x % tx);
-    row = rg * ry + (int64_t)(threadIdx.x / tx);
-    return x < S.d.nx && row < nrows;
+    const uint32_t zr = fdiv(row, S.fy);
+    const uint32_t nyr = TWO ? (uint32_t)S.d.ny >> 1 : (uint32_t)S.d.ny;
+    y = (int)(row - zr * nyr) * (TWO ? 2 : 1);
+    const uint32_t sz = fdiv(zr, S.fz);
+    z = (int)(zr - sz * (uint32_t)S.d.nz);
+    s = (int)sz;
+    return true;
 }
 
 template <class R>
@@ -95,17 +123,12 @@ __device__ __forceinline__ double tb_of<double>(const BatchSim& s) {
 // read, in step k + 1, lines another CTA wrote in step k).
 template <class Codec, bool PROJECT, class Ld>
 __device__ __forceinline__ void batch_tile(const BatchSim* __restrict__ sims, int nsims, int64_t t, int parity,
-                                           const Consts<typename Codec::R>& K, int tx, int ry, int* err) {
+                                           const Consts<typename Codec::R>& K, int tx, int txs, int ry, int* err) {
     using R = typename Codec::R;
     using T = typename Codec::raw_t;
     const BatchSim& S = sims[find_sim(sims, nsims, t)];
-    int64_t row;
-    int x;
-    if (!tile_entry(S, t, tx, ry, S.d.rows, row, x)) return;
-    const int y = (int)(row % S.d.ny);
-    const int64_t zr = row / S.d.ny;
-    const int z = (int)(zr % S.d.nz);
-    const int s = (int)(zr / S.d.nz);
+    int s, z, y, x;
+    if (!tile_node<false>(S, t, tx, txs, ry, s, z, y, x)) return;
     step_node<Codec, PROJECT, Ld>(static_cast<const T*>(S.buf[parity]), static_cast<T*>(S.buf[parity ^ 1]), S.d, K,
                                   tb_of<R>(S), err, s, z, y, x);
 }
@@ -115,17 +138,11 @@ __device__ __forceinline__ void batch_tile(const BatchSim* __restrict__ sims, in
 // (y + 1, x) with packed FP32x2 arithmetic.
 template <class Codec, bool PROJECT, class Ld>
 __device__ __forceinline__ void batch_tile2(const BatchSim* __restrict__ sims, int nsims, int64_t t, int parity,
-                                            const Consts<float>& K, int tx, int ry, int* err) {
+                                            const Consts<float>& K, int tx, int txs, int ry, int* err) {
     using T = typename Codec::raw_t;
     const BatchSim& S = sims[find_sim(sims, nsims, t)];
-    int64_t rp;
-    int x;
-    if (!tile_entry(S, t, tx, ry, S.d.rows / 2, rp, x)) return;
-    const int nyh = S.d.ny >> 1;
-    const int y = 2 * (int)(rp % nyh);
-    const int64_t zr = rp / nyh;
-    const int z = (int)(zr % S.d.nz);
-    const int s = (int)(zr / S.d.nz);
+    int s, z, y, x;
+    if (!tile_node<true>(S, t, tx, txs, ry, s, z, y, x)) return;
     step_node2<Codec, PROJECT, Ld>(static_cast<const T*>(S.buf[parity]), static_cast<T*>(S.buf[parity ^ 1]), S.d, K,
                                    S.tbf, err, s, z, y, x);
 }
@@ -136,16 +153,16 @@ __device__ __forceinline__ void batch_tile2(const BatchSim* __restrict__ sims, i
 // FP64 arithmetic need about 168 (3 CTAs).
 template <class Codec, bool TWO>
 constexpr int batch_min_blocks(bool persistent) {
-    return (TWO || sizeof(typename Codec::R) == 8) ? 3 : (persistent ? 5 : 6);
+    return (TWO || sizeof(typename Codec::R) == 8) ? 3 : (persistent ? 6 : 6);
 }
 
 template <class Codec, bool PROJECT, bool TWO>
 __global__ void __launch_bounds__(128, batch_min_blocks<Codec, TWO>(false)) k_batch_step(const BatchSim* __restrict__ sims, int nsims, int parity,
-                                                    Consts<typename Codec::KS> K, int tx, int ry, int* err) {
+                                                    Consts<typename Codec::KS> K, int tx, int txs, int ry, int* err) {
     if constexpr (TWO)
-        batch_tile2<Codec, PROJECT, LoadNC>(sims, nsims, blockIdx.x, parity, K, tx, ry, err);
+        batch_tile2<Codec, PROJECT, LoadNC>(sims, nsims, blockIdx.x, parity, K, tx, txs, ry, err);
     else
-        batch_tile<Codec, PROJECT, LoadNC>(sims, nsims, blockIdx.x, parity, K, tx, ry, err);
+        batch_tile<Codec, PROJECT, LoadNC>(sims, nsims, blockIdx.x, parity, K, tx, txs, ry, err);
 }
 
 struct GridBar {
@@ -185,17 +202,18 @@ __device__ __forceinline__ bool grid_sync(GridBar* bar, unsigned expected, long 
 }
 
 template <class Codec, bool PROJECT, bool TWO>
-__global__ void __launch_bounds__(128, batch_min_blocks<Codec, TWO>(true)) k_batch_persistent(const BatchSim* __restrict__ sims, int nsims, int64_t ntiles,
-                                                          int64_t nsteps, int parity0, Consts<typename Codec::KS> K,
-                                                          int tx, int ry, int* err, GridBar* bar, unsigned expected,
-                                                          long long limit) {
+__global__ void __launch_bounds__(128, batch_min_blocks<Codec, TWO>(true))
+    k_batch_persistent(const BatchSim* __restrict__ sims, int nsims, int64_t ntiles, int64_t nsteps, int parity0,
+                       Consts<typename Codec::KS> K, int tx, int txs, int ry, int* err, GridBar* bar,
+                       unsigned expected, long long limit) {
+    const int nt = (int)ntiles;  // < 2^31 (the work list is checked when it is laid out)
     for (int64_t step = 0; step < nsteps; ++step) {
         const int parity = (int)((parity0 + step) & 1);
-        for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        for (int t = blockIdx.x; t < nt; t += gridDim.x) {
             if constexpr (TWO)
-                batch_tile2<Codec, PROJECT, LoadCG>(sims, nsims, t, parity, K, tx, ry, err);
+                batch_tile2<Codec, PROJECT, LoadCG>(sims, nsims, t, parity, K, tx, txs, ry, err);
             else
-                batch_tile<Codec, PROJECT, LoadCG>(sims, nsims, t, parity, K, tx, ry, err);
+                batch_tile<Codec, PROJECT, LoadCG>(sims, nsims, t, parity, K, tx, txs, ry, err);
         }
         if (step + 1 < nsteps && !grid_sync(bar, expected, limit)) {
             if (threadIdx.x == 0) atomicOr(err, 2);
@@ -231,6 +249,12 @@ using namespace gblb;
 static const int kTileShapes[][2] = {{16, 4}, {16, 8}, {32, 2}, {32, 4}, {64, 1}, {64, 2}, {128, 1}, {64, 0}, {128, 0}};
 
 static int tile_threads(int tx, int ry) { return ry == 0 ? tx : tx * ry; }
+
+static int log2i(int v) {  // tile widths are powers of two
+    int k = 0;
+    while ((1 << k) < v) ++k;
+    return k;
+}
 
 struct lb_batch {
     int n = 0;
@@ -299,8 +323,13 @@ static lb_status plan(lb_batch* b, lb_batch::Plan& P, int tx, int ry, bool two_r
         s.tiles_x = (int)((c->d.nx + tx - 1) / tx);
         s.tile0 = t;
         const int64_t rows = two_rows ? c->d.rows / 2 : c->d.rows;
-        s.units = rows * c->d.nx;
-        t += ry == 0 ? (s.units + tx - 1) / tx : (int64_t)s.tiles_x * ((rows + ry - 1) / ry);
+        s.units = (uint32_t)(rows * c->d.nx);  // < 2^31 (lb_batch_init)
+        s.nrows = (uint32_t)rows;
+        s.fx = make_fastdiv((uint32_t)c->d.nx);
+        s.fy = make_fastdiv((uint32_t)(two_rows ? c->d.ny / 2 : c->d.ny));
+        s.fz = make_fastdiv((uint32_t)c->d.nz);
+        s.ft = make_fastdiv((uint32_t)s.tiles_x);
+        t += ry == 0 ? ((int64_t)s.units + tx - 1) / tx : (int64_t)s.tiles_x * ((rows + ry - 1) / ry);
     }
     if (t > 0x7fffffffLL) return bfail(b, LB_ERR_ARG, "batch work list too long for one launch");
     P.ntiles = t;
@@ -326,19 +355,19 @@ static cudaError_t launch_batch_step(lb_batch* b, int parity, cudaStream_t st) {
             if (P.two_rows) {
                 if (b->project)
                     k_batch_step<C, true, true><<<grid, block, 0, st>>>(P.d_sims, b->n, parity, consts_of<C>(lc),
-                                                                        P.tx, P.ry, b->d_err);
+                                                                        P.tx, log2i(P.tx), P.ry, b->d_err);
                 else
                     k_batch_step<C, false, true><<<grid, block, 0, st>>>(P.d_sims, b->n, parity, consts_of<C>(lc),
-                                                                         P.tx, P.ry, b->d_err);
+                                                                         P.tx, log2i(P.tx), P.ry, b->d_err);
                 return cudaGetLastError();
             }
         }
         if (b->project)
             k_batch_step<C, true, false><<<grid, block, 0, st>>>(P.d_sims, b->n, parity, consts_of<C>(lc), P.tx,
-                                                                 P.ry, b->d_err);
+                                                                 log2i(P.tx), P.ry, b->d_err);
         else
             k_batch_step<C, false, false><<<grid, block, 0, st>>>(P.d_sims, b->n, parity, consts_of<C>(lc), P.tx,
-                                                                  P.ry, b->d_err);
+                                                                  log2i(P.tx), P.ry, b->d_err);
         return cudaGetLastError();
     });
 }
@@ -347,8 +376,8 @@ static cudaError_t launch_persistent(lb_batch* b, int64_t nsteps, int parity, cu
     const LaunchConsts& lc = lattice_consts();
     return dispatch_codec(b->prec, [&](auto codec) -> cudaError_t {
         using C = decltype(codec);
-        void (*kern)(const BatchSim*, int, int64_t, int64_t, int, Consts<typename C::KS>, int, int, int*, GridBar*,
-                     unsigned, long long) =
+        void (*kern)(const BatchSim*, int, int64_t, int64_t, int, Consts<typename C::KS>, int, int, int, int*,
+                     GridBar*, unsigned, long long) =
             b->project ? k_batch_persistent<C, true, false> : k_batch_persistent<C, false, false>;
         if constexpr (std::is_same<typename C::R, float>::value) {
             if (b->pp.two_rows)
@@ -369,12 +398,13 @@ static cudaError_t launch_persistent(lb_batch* b, int64_t nsteps, int parity, cu
         int nsims = b->n;
         int64_t ntiles = P.ntiles;
         Consts<typename C::KS> K = consts_of<C>(lc);
-        int tx = P.tx, ry = P.ry;
+        int tx = P.tx, txs = log2i(P.tx), ry = P.ry;
         int* err = b->d_err;
         GridBar* bar = b->d_bar;
         long long limit = b->wait_limit;
         void* args[] = {(void*)&sims, (void*)&nsims, (void*)&ntiles, (void*)&nsteps, (void*)&parity, (void*)&K,
-                        (void*)&tx, (void*)&ry, (void*)&err, (void*)&bar, (void*)&expected, (void*)&limit};
+                        (void*)&tx, (void*)&txs, (void*)&ry, (void*)&err, (void*)&bar, (void*)&expected,
+                        (void*)&limit};
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)grid);
         cfg.blockDim = dim3((unsigned)tile_threads(tx, ry));
@@ -397,6 +427,13 @@ lb_status lb_batch_init(lb_batch** out, int nsims, const lb_grid* grids, const d
     *out = nullptr;
     if (flags & LB_FLAG_ENTROPIC)
         return bfail(nullptr, LB_ERR_ARG, "lb_batch_init: the exact entropic equilibrium is a single-grid mode");
+    for (int k = 0; k < nsims; ++k) {
+        const lb_grid& g = grids[k];
+        if (g.nx >= 1 && g.ny >= 1 && g.nz >= 1 && g.nx < (1 << 30) && g.ny < (1 << 30) && g.nz < (1 << 30) &&
+            2.0 * (double)g.nx * (double)g.ny * (double)g.nz >= 2147483648.0)
+            return bfail(nullptr, LB_ERR_ARG,
+                         "lb_batch_init: simulation " + std::to_string(k) + " has 2^31 nodes or more (single-grid only)");
+    }
     lb_batch* b = new lb_batch();
     b->n = nsims;
     b->prec = (int)precision;

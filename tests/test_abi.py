@@ -87,3 +87,15 @@ def test_conv_impl_switch(L):
     assert sg.set_conv_impl(prev) == sg.CONV_MMA_SYNC
     with pytest.raises(ValueError):
         sg.set_conv_impl(7)
+
+
+def test_batch_rejects_members_of_2_31_nodes(L):
+    """The batched kernels index a simulation's nodes in 32 bits: a member of 2^31 nodes or
+    more is refused before anything is allocated."""
+    from paper_1909_08406_gb300 import lb
+    with pytest.raises(lb.LbError) as e:
+        lb.lb_batch_init([(8, 8, 8), (1024, 1024, 1024)], [0.6, 0.7], "f32")
+    assert e.value.status == -1
+    assert "2^31" in str(e.value)
+    assert L.lb_batch_get_rows(None) == -1
+    assert L.lb_batch_get_plan(None, 0, None, None, None) == -1
