@@ -204,11 +204,9 @@ __device__ __forceinline__ void step_node2(const typename Codec::raw_t* __restri
 // plane are written with one 32-bit store.
 //
 // A block covers one chunk of x for `rpb` consecutive rows (s, z, y), y
-// fastest.  The loads of the next row are software-pipelined into the
-// registers of the current one: as soon as population I of the current row
-// has been relaxed and stored, its register receives population I of the next
-// row, so a row's loads are in flight while the previous row is still being
-// relaxed.  Requires nx even and nx * ny * nz < 2^32.
+// fastest, and each thread loads a row's 41 pairs at the start of that row
+// (MODE below says how the next row is brought closer meanwhile).  Requires
+// nx even and nx * ny * nz < 2^32.
 template <class Codec>
 struct RowAddr2x {
     using T = typename Codec::raw_t;
