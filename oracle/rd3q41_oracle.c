@@ -45,6 +45,10 @@
  *   - beta = 1 / (2 tau + 1) (Delta t = 1); tau = +inf gives beta = 0.
  *   - The grid "N^3" has N^3 simple-cubic cells and 2 N^3 nodes: sub-lattice
  *     A at integer positions r, sub-lattice B at r + (1/2, 1/2, 1/2).
+ *   - The kinetic wall condition the paper cites (Ansumali and Karlin 2002) is
+ *     not restated there; or_step_walls writes it for this lattice as diffuse
+ *     reflection with the walls a quarter cell beyond the outermost node planes
+ *     and one wall density per wall and step (see that function).
  *
  * Array layout used by every grid routine here (the oracle's own velocity
  * order, given by or_velocities):
@@ -463,6 +467,79 @@ void or_step_nodes(int64_t nx, int64_t ny, int64_t nz, double tau, int project, 
         double fin[NV];
         for (int i = 0; i < NV; ++i) fin[i] = fpost[upwind(nx, ny, nz, s, i, z, y, x)];
         or_collide(fin, tau, project, out + k * NV);
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Kinetic (diffuse) walls normal to z                                 */
+/* ------------------------------------------------------------------ */
+
+/* n time steps with two kinetic walls normal to z instead of the periodic
+ * wrap in z (x and y stay periodic).  In doubled coordinates the nodes occupy
+ * z2 = 2z + s in [0, 2 nz); the bottom wall lies at z2 = -1/2 and the top
+ * wall at z2 = 2 nz - 1/2, a quarter cell beyond the outermost node planes,
+ * so the channel height is nz cells.  The paper applies the kinetic boundary
+ * condition of Ansumali and Karlin (2002) without restating it; this is that
+ * condition (diffuse reflection) written for the crystallographic lattice:
+ *   - a post-collision population whose destination z2 + 2 c_iz lies beyond a
+ *     wall is absorbed by that wall;
+ *   - a population whose upwind position z2 - 2 c_iz lies beyond a wall is
+ *     emitted by it: f_i = rho_w f^eq_i(1, u_w, theta_w), the model's own
+ *     equilibrium at the wall's velocity and temperature;
+ *   - rho_w makes the emitted mass equal to the absorbed mass, so the wall
+ *     neither creates nor destroys mass.  rho_w is one value per wall and
+ *     step, the balance taken over the whole wall plane: this is the local
+ *     condition for flows that are uniform along the wall.
+ * wall[8] = {u_x, u_y, u_z, theta} of the bottom wall, then of the top wall
+ * (u_z must be 0).  wall_rho[2 * nsteps] receives rho_w of both walls per
+ * step if it is not NULL. */
+void or_step_walls(int64_t nx, int64_t ny, int64_t nz, double tau, int project, int64_t nsteps, double *f,
+                   double *work, const double wall[8], double *wall_rho, int nthreads) {
+    init_lattice();
+    set_threads(nthreads);
+    double eb[NV], et[NV];
+    equilibrium_of_kind(1.0, wall, wall[3], project, eb);
+    equilibrium_of_kind(1.0, wall + 4, wall[7], project, et);
+    for (int64_t t = 0; t < nsteps; ++t) {
+        /* mass absorbed by each wall, and the emission of a unit-density wall */
+        double absorbed[2] = {0.0, 0.0}, emitted[2] = {0.0, 0.0};
+        for (int s = 0; s < 2; ++s)
+            for (int i = 0; i < NV; ++i)
+                for (int64_t z = 0; z < nz; ++z)
+                    for (int64_t y = 0; y < ny; ++y)
+                        for (int64_t x = 0; x < nx; ++x) {
+                            int64_t z2 = 2 * z + s;
+                            int64_t dest = z2 + C2[i][2], src = z2 - C2[i][2];
+                            double v = f[pidx(nx, ny, nz, s, i, z, y, x)];
+                            if (dest < 0) absorbed[0] += v;
+                            if (dest >= 2 * nz) absorbed[1] += v;
+                            if (src < 0) emitted[0] += eb[i];
+                            if (src >= 2 * nz) emitted[1] += et[i];
+                        }
+        double rb = absorbed[0] / emitted[0], rt = absorbed[1] / emitted[1];
+        if (wall_rho) {
+            wall_rho[2 * t] = rb;
+            wall_rho[2 * t + 1] = rt;
+        }
+#pragma omp parallel for collapse(3) schedule(static)
+        for (int s = 0; s < 2; ++s)
+            for (int64_t z = 0; z < nz; ++z)
+                for (int64_t y = 0; y < ny; ++y)
+                    for (int64_t x = 0; x < nx; ++x) {
+                        double fin[NV], fout[NV];
+                        for (int i = 0; i < NV; ++i) {
+                            int64_t src = 2 * z + s - C2[i][2];
+                            if (src < 0)
+                                fin[i] = rb * eb[i];
+                            else if (src >= 2 * nz)
+                                fin[i] = rt * et[i];
+                            else
+                                fin[i] = f[upwind(nx, ny, nz, s, i, z, y, x)];
+                        }
+                        or_collide(fin, tau, project, fout);
+                        for (int i = 0; i < NV; ++i) work[pidx(nx, ny, nz, s, i, z, y, x)] = fout[i];
+                    }
+        memcpy(f, work, sizeof(double) * (size_t)(2 * NV * nx * ny * nz));
     }
 }
 

@@ -1,0 +1,117 @@
+"""Kinetic (diffuse) walls normal to z in the oracle (Sec. "Viscous heat
+dissipation": kinetic boundary conditions at the walls, periodic in the other
+two directions).
+
+Pins, none of which restates the oracle's formula:
+  - a gas at rest at the walls' temperature stays exactly at rest, with the
+    walls' density 1 (every absorbed population comes back as the same
+    equilibrium value);
+  - the walls conserve mass to round-off while they exchange momentum and
+    energy with the gas;
+  - mirroring the channel (z -> -z with the half-cell shift that keeps the bcc
+    grid on itself, walls swapped) mirrors the solution, which catches a
+    misplaced top wall;
+  - Couette flow with viscous heating reaches the steady temperature profile of
+    Eq. (eckert), (T - T0)/dT = y/H + Ec/2 (y/H)(1 - y/H), and the linear
+    velocity profile, at first order in 1/H (the kinetic boundary layer: the
+    temperature jump and velocity slip at a diffuse wall are of the order of a
+    mean free path)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_08406_gb300 import workloads as wl
+
+TH0 = oracle.theta0()
+
+
+def _rest(nx, ny, nz):
+    rho = np.ones((2, nz, ny, nx))
+    u = np.zeros((3, 2, nz, ny, nx))
+    th = np.full((2, nz, ny, nx), TH0)
+    return oracle.init_fields(rho, u, th)
+
+
+def test_rest_state_is_a_fixed_point():
+    f0 = _rest(3, 2, 6)
+    f1, rho_w = oracle.step_walls(f0, 0.3, 20, (0.0, 0.0, TH0), (0.0, 0.0, TH0), wall_rho=True)
+    assert np.abs(f1 - f0).max() <= 1e-13 * f0.max()
+    assert np.abs(rho_w - 1.0).max() <= 1e-13
+
+
+def _random(nx, ny, nz, seed):
+    fl = wl.random_fields(nx, ny, nz, TH0, seed=seed, du=0.03, drho=0.03, dtheta=0.03)
+    return oracle.init_fields(fl["rho"].numpy(), fl["u"].numpy(), fl["theta"].numpy())
+
+
+BOTTOM = (0.02, -0.01, TH0 * 1.01)
+TOP = (-0.03, 0.0, TH0 * 0.98)
+
+
+def test_walls_conserve_mass_and_exchange_momentum_and_energy():
+    f0 = _random(3, 2, 6, 3)
+    c0 = oracle.conserved(f0)
+    f1 = oracle.step_walls(f0, 0.3, 50, BOTTOM, TOP)
+    c1 = oracle.conserved(f1)
+    assert abs(c1[0] - c0[0]) <= 1e-13 * c0[0]
+    assert np.abs(c1[1:] - c0[1:]).max() > 1e-3  # the walls push and heat or cool the gas
+    # the same state stepped periodically keeps every invariant
+    c2 = oracle.conserved(oracle.step(f0, 0.3, 50))
+    assert np.abs(c2 - c0).max() <= 1e-12 * c0[0]
+
+
+def _mirror(f):
+    """The channel reflected about its mid-plane: in doubled coordinates
+    (x2, y2, z2) -> (x2 + 1, y2 + 1, 2 nz - 1 - z2), velocities c_z -> -c_z.  A reflection
+    in z alone would send a node of one sub-lattice to no node at all; with the half-cell
+    shift in x and y (a symmetry of the periodic bcc grid) A (x, y, z) goes to
+    B (x, y, nz - 1 - z) and B (x, y, z) to A (x + 1, y + 1, nz - 1 - z)."""
+    c2 = oracle.velocities_doubled()
+    refl = np.array([int(np.where((c2 == v * np.array([1, 1, -1])).all(1))[0][0]) for v in c2])
+    g = np.empty_like(f)
+    g[1] = f[0][refl][:, ::-1]
+    g[0] = np.roll(f[1][refl][:, ::-1], (1, 1), axis=(2, 3))
+    return g
+
+
+def test_mirrored_channel_gives_the_mirrored_solution():
+    f0 = _random(4, 3, 5, 7)
+    a = oracle.step_walls(f0, 0.4, 12, BOTTOM, TOP)
+    b = oracle.step_walls(_mirror(f0), 0.4, 12, TOP, BOTTOM)
+    assert np.abs(_mirror(a) - b).max() <= 1e-14 * f0.max()
+
+
+def _couette(H, ec, nu=0.05, u0=0.02):
+    """Steady Couette flow between a still wall at T0 (bottom) and a wall moving at u0 at
+    T1 = T0 + dT (top), dT = u0^2 / (c_p Ec), c_p = 5/2, the walls at theta0 -+ dT/2 as in
+    the paper's runs; returns y/H, (T - T0)/dT and u/u0 at every node plane, and the exact
+    temperature profile."""
+    dT = u0 * u0 / (2.5 * ec)
+    f = _rest(1, 1, H)
+    f = oracle.step_walls(f, nu / TH0, int(3 * H * H / nu), (0.0, 0.0, TH0 - dT / 2), (u0, 0.0, TH0 + dT / 2))
+    _, u, th = oracle.get_moments(f)
+    z2 = np.array([[2 * z + s for z in range(H)] for s in range(2)]).ravel()
+    y = (z2 / 2.0 + 0.25) / H  # walls a quarter cell beyond the outermost node planes
+    o = np.argsort(y)
+    y = y[o]
+    tn = ((th.reshape(2, H) - (TH0 - dT / 2)) / dT).ravel()[o]
+    un = (u[0].reshape(2, H) / u0).ravel()[o]
+    return y, tn, un, y + ec / 2 * y * (1 - y)
+
+
+def test_couette_viscous_heating_converges_to_eq_eckert():
+    errs = []
+    for H in (8, 16):
+        y, tn, un, ex = _couette(H, 2.0)
+        errs.append((np.abs(tn - ex).max(), np.abs(un - y).max()))
+    (t8, u8), (t16, u16) = errs
+    assert t16 <= 0.04 and u16 <= 0.01, errs  # measured 0.037, 0.0079
+    assert t8 / t16 >= 1.8 and u8 / u16 >= 1.8, errs  # first order (measured 1.93, 1.97)
+
+
+@pytest.mark.parametrize("ec,bound", [(0.5, 0.03), (5.0, 0.07)])
+def test_couette_eckert_numbers_of_the_paper(ec, bound):
+    y, tn, un, ex = _couette(16, ec)
+    assert np.abs(tn - ex).max() <= bound, np.abs(tn - ex).max()
+    # at Ec = 5 the viscous heating lifts the gas above the hot wall's temperature
+    assert (tn.max() > 1.1) == (ex.max() > 1.1)
