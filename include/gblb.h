@@ -212,6 +212,31 @@ lb_status lb_set_step_kernel(lb_ctx *ctx, int kernel);
  * (the state is not advanced), keep the fastest, report it and its ms per step. */
 lb_status lb_tune(lb_ctx *ctx, int reps, int *kernel, double *ms_per_step);
 
+/* Kinetic walls normal to z (Sec. "Viscous heat dissipation", which applies
+ * the kinetic boundary condition of Ansumali and Karlin 2002 at the walls and
+ * keeps the other two directions periodic).  With enable != 0 the grid is no
+ * longer periodic in z: a bottom wall lies a quarter cell below the lowest
+ * node plane (A nodes of z = 0) and a top wall a quarter cell above the
+ * highest (B nodes of z = nz - 1), so the channel is nz cells high.  Diffuse
+ * reflection: every post-collision population that would stream through a
+ * wall is absorbed by it, and every population whose upwind position lies
+ * beyond a wall arrives as rho_w f^eq_i(1, u_w, theta_w), the model's
+ * equilibrium at the wall's velocity and temperature, with rho_w the density
+ * that returns the absorbed mass (one value per wall and step, balanced over
+ * the whole wall plane: the local condition for flows uniform along the wall).
+ * Mass is conserved; momentum and energy are exchanged with the walls.
+ *   bottom, top  {u_x, u_y, u_z, theta} of each wall, host arrays read during
+ *                the call; u_z must be 0, theta > 0
+ * Requires nz >= 4 (LB_ERR_ARG otherwise).  enable = 0 restores the periodic
+ * grid.  Each step then runs three small kernels besides the step kernel (the
+ * wall sums and the two outermost cell layers at each wall).  Walls are not
+ * part of lb_get_state; a batch (lb_batch_step) refuses members with walls
+ * (LB_ERR_STATE). */
+lb_status lb_set_walls(lb_ctx *ctx, int enable, const double bottom[4], const double top[4]);
+/* rho_w of the bottom and top wall in the last step (1, 1 before the first); LB_ERR_STATE
+ * without walls.  Synchronises the context's stream. */
+lb_status lb_wall_density(lb_ctx *ctx, double rho_w[2]);
+
 /* Number of time steps taken since the last lb_set_fields / lb_set_populations / lb_set_state. */
 int64_t lb_time(const lb_ctx *ctx);
 

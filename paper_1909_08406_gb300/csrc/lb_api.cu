@@ -376,8 +376,12 @@ lb_status lb_step(lb_ctx* c, int64_t n) {
     CK(c, cudaSetDevice(c->device));
     const LaunchConsts& lc = lattice().lc;
     for (int64_t t = 0; t < n; ++t) {
-        CK(c, launch_step(c->prec, c->eq, c->variant, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc, c->twobeta,
-                          c->d_err, c->stream));
+        if (c->walls)
+            CK(c, launch_wall_step(c->prec, c->eq, c->variant, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc,
+                                   c->twobeta, c->d_wall, c->d_err, c->stream));
+        else
+            CK(c, launch_step(c->prec, c->eq, c->variant, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc,
+                              c->twobeta, c->d_err, c->stream));
         c->cur ^= 1;
         c->time += 1;
     }
@@ -517,8 +521,51 @@ lb_status lb_destroy(lb_ctx* c) {
     cudaFree(c->d_err);
     cudaFree(c->d_partials);
     cudaFree(c->d_stage);
+    cudaFree(c->d_wall);
     delete c;
     return LB_OK;
+}
+
+lb_status lb_set_walls(lb_ctx* c, int enable, const double bottom[4], const double top[4]) {
+    if (!c) return LB_ERR_ARG;
+    if (!enable) {
+        c->walls = 0;
+        return LB_OK;
+    }
+    if (!bottom || !top) return fail(c, LB_ERR_ARG, "lb_set_walls: null wall");
+    if (c->d.nz < 4) return fail(c, LB_ERR_ARG, "lb_set_walls: walls need nz >= 4");
+    if (bottom[2] != 0.0 || top[2] != 0.0) return fail(c, LB_ERR_ARG, "lb_set_walls: a wall cannot move along z");
+    for (const double* w : {bottom, top})
+        if (!(w[3] > 0.0) || !isfinite(w[0]) || !isfinite(w[1]) || !isfinite(w[3]))
+            return fail(c, LB_ERR_ARG, "lb_set_walls: wall velocity must be finite and theta > 0");
+    CK(c, cudaSetDevice(c->device));
+    if (!c->d_wall) {
+        cudaError_t e = cudaMalloc(&c->d_wall, wall_block_bytes());
+        if (e != cudaSuccess) {
+            c->d_wall = nullptr;
+            return fail(c, e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA,
+                        std::string("lb_set_walls: ") + cudaGetErrorString(e));
+        }
+    }
+    const double w[8] = {bottom[0], bottom[1], bottom[2], bottom[3], top[0], top[1], top[2], top[3]};
+    CK(c, launch_wall_setup(c->eq, c->d_wall, c->d, lattice().lc, w, c->stream));
+    double rho[2];
+    CK(c, cudaMemcpyAsync(rho, c->d_wall + wall_rho_offset(), sizeof rho, cudaMemcpyDeviceToHost, c->stream));
+    lb_status s = lb_sync(c);
+    if (s != LB_OK) return s;
+    if (!(rho[0] == 1.0 && rho[1] == 1.0))
+        return fail(c, LB_ERR_ARG, "lb_set_walls: no equilibrium at a wall's velocity and temperature");
+    c->walls = 1;
+    return LB_OK;
+}
+
+lb_status lb_wall_density(lb_ctx* c, double rho_w[2]) {
+    if (!c || !rho_w) return LB_ERR_ARG;
+    if (!c->walls) return fail(c, LB_ERR_STATE, "lb_wall_density: no walls set");
+    CK(c, cudaSetDevice(c->device));
+    CK(c, cudaMemcpyAsync(rho_w, c->d_wall + wall_rho_offset(), 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream));
+    return lb_sync(c);
 }
 
 const char* lb_last_error(const lb_ctx* c) { return c ? c->msg.c_str() : g_init_msg.c_str(); }

@@ -587,6 +587,8 @@ lb_status lb_batch_set_wait(lb_batch* b, long long limit_cycles, unsigned extra_
 lb_status lb_batch_step(lb_batch* b, int64_t nsteps, int mode) {
     if (!b || nsteps < 0) return bfail(b, LB_ERR_ARG, "lb_batch_step: bad argument");
     if (nsteps == 0) return LB_OK;
+    for (auto* c : b->ctx)
+        if (c->walls) return bfail(b, LB_ERR_STATE, "lb_batch_step: a simulation of the batch has walls");
     BCK(b, cudaSetDevice(b->device));
     const int parity = b->ctx[0]->cur;
     if (mode == LB_BATCH_SEQUENTIAL) {

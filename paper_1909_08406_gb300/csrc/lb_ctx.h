@@ -29,6 +29,8 @@ struct lb_ctx {
     double* d_stage;
     int64_t stage_doubles;
     int64_t time;
+    int walls = 0;            // kinetic walls normal to z (lb_set_walls) instead of the periodic wrap
+    double* d_wall = nullptr;  // the walls' device block (lb_walls.cu)
     std::string msg;
 };
 

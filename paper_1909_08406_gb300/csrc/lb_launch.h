@@ -74,6 +74,16 @@ cudaError_t launch_step_f32(int prec, bool project, int variant, const void* src
 cudaError_t launch_step_entropic(int prec, const void* src, void* dst, const Dims& d, const LaunchConsts& c,
                                  double twobeta, int* err, cudaStream_t st);
 
+// Kinetic walls normal to z (lb_walls.cu).  wall[8] = {u_x, u_y, u_z, theta} of the bottom
+// wall, then of the top wall; blk is a device block of wall_block_bytes().
+size_t wall_block_bytes();
+int wall_rho_offset();  // index of rho_w (2 doubles) in the block
+cudaError_t launch_wall_setup(int eq, double* blk, const Dims& d, const LaunchConsts& c, const double wall[8],
+                              cudaStream_t st);
+// One step with the walls: absorbed mass, rho_w, the periodic step, then the wall layers.
+cudaError_t launch_wall_step(int prec, int eq, int variant, const void* src, void* dst, const Dims& d,
+                             const LaunchConsts& c, double twobeta, double* blk, int* err, cudaStream_t st);
+
 inline dim3 step_grid(const Dims& d, int threads) {
     return dim3((unsigned)d.rows, (unsigned)((d.nx + threads - 1) / threads), 1);
 }

@@ -79,6 +79,10 @@ def lib():
         L.lb_tune.restype = ctypes.c_int
         L.lb_time.argtypes = [vp]
         L.lb_time.restype = i64
+        L.lb_set_walls.argtypes = [vp, ctypes.c_int, vp, vp]
+        L.lb_set_walls.restype = ctypes.c_int
+        L.lb_wall_density.argtypes = [vp, vp]
+        L.lb_wall_density.restype = ctypes.c_int
         L.lb_sync.argtypes = [vp]
         L.lb_destroy.argtypes = [vp]
         L.lb_last_error.argtypes = [vp]
@@ -222,6 +226,24 @@ def lb_tune(ctx, reps=3):
     k, ms = ctypes.c_int(), ctypes.c_double()
     _check(lib().lb_tune(ctx, int(reps), ctypes.byref(k), ctypes.byref(ms)), ctx)
     return k.value, ms.value
+
+
+def lb_set_walls(ctx, bottom=None, top=None):
+    """Kinetic walls normal to z: bottom, top = (u_x, u_y, theta) of each wall; None for both
+    restores the periodic grid."""
+    if bottom is None and top is None:
+        _check(lib().lb_set_walls(ctx, 0, None, None), ctx)
+        return
+    b = (ctypes.c_double * 4)(float(bottom[0]), float(bottom[1]), 0.0, float(bottom[2]))
+    t = (ctypes.c_double * 4)(float(top[0]), float(top[1]), 0.0, float(top[2]))
+    _check(lib().lb_set_walls(ctx, 1, ctypes.cast(b, ctypes.c_void_p), ctypes.cast(t, ctypes.c_void_p)), ctx)
+
+
+def lb_wall_density(ctx):
+    """(rho_w bottom, rho_w top) of the last step."""
+    out = (ctypes.c_double * 2)()
+    _check(lib().lb_wall_density(ctx, ctypes.cast(out, ctypes.c_void_p)), ctx)
+    return out[0], out[1]
 
 
 def lb_time(ctx):

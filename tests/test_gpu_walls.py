@@ -1,0 +1,224 @@
+"""Kinetic walls normal to z on the GPU (lb_set_walls) against the oracle's
+or_step_walls, element by element, and the Couette viscous-heating profile of
+Eq. (eckert).
+
+Tolerance (relative, over every population, 20 steps of random fields at
+amplitude 0.03 between a warmer and a cooler moving wall): FP64 1e-12 (only
+summation order differs); otherwise one rounding of each stored deviation
+h = f/w - 1 per step, |dh| <= eps_store |h|, growing like sqrt(steps), at this
+state's largest deviation h_max (about 0.2-0.46 here), plus 2e-7 for the FP32
+evaluation: eps_store h_max sqrt(steps) + 2e-7.  Every step kernel runs the
+bulk of the grid, so the wall pass is checked behind each of them."""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from helpers import lib_to_oracle_perm, to_oracle_order
+from paper_1909_08406_gb300 import lb
+from paper_1909_08406_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+EPS_STORE = {"f32": 2.0 ** -24, "f16": 2.0 ** -11, "bf16": 2.0 ** -8}
+TH0 = lb.lb_theta0()
+BOTTOM = (0.02, -0.01, TH0 * 1.01)
+TOP = (-0.03, 0.0, TH0 * 0.98)
+
+
+@pytest.fixture(scope="module")
+def perm():
+    return lib_to_oracle_perm()
+
+
+def _fields(shape, seed=11):
+    return wl.random_fields(*shape, TH0, seed=seed, du=0.03, drho=0.03, dtheta=0.03)
+
+
+def _gpu(shape, prec, fl, steps, kernel=lb.LB_KERNEL_AUTO, flags=0, tau=0.35):
+    ctx = lb.lb_init(shape, tau, prec, flags=flags)
+    try:
+        lb.lb_set_step_kernel(ctx, kernel)
+        lb.lb_set_fields(ctx, fl["rho"].cuda(), fl["u"].cuda(), fl["theta"].cuda())
+        lb.lb_set_walls(ctx, BOTTOM, TOP)
+        lb.lb_step(ctx, steps)
+        nx, ny, nz = shape
+        f = np.empty((2, 41, nz, ny, nx))
+        lb.lb_get_populations(ctx, f)
+        rho_w = lb.lb_wall_density(ctx)
+        used = lb.lb_step_variant(ctx)
+    finally:
+        lb.lb_destroy(ctx)
+    return f, rho_w, used
+
+
+def _oracle(fl, steps, project=True, tau=0.35):
+    f0 = oracle.init_fields(fl["rho"].numpy(), fl["u"].numpy(), fl["theta"].numpy(), project=project)
+    return oracle.step_walls(f0, tau, steps, BOTTOM, TOP, project=project, wall_rho=True)
+
+
+CASES = [("f64", (12, 6, 8), lb.LB_KERNEL_DIRECT1), ("f64", (7, 5, 4), lb.LB_KERNEL_DIRECT1),
+         ("f32", (12, 6, 8), lb.LB_KERNEL_DIRECT1), ("f32", (12, 6, 8), lb.LB_KERNEL_DIRECT2),
+         ("f32", (7, 5, 4), lb.LB_KERNEL_AUTO), ("f32", (128, 2, 6), lb.LB_KERNEL_STAGED),
+         ("f32", (128, 2, 6), lb.LB_KERNEL_WARPSPEC),
+         ("f16", (12, 6, 8), lb.LB_KERNEL_DIRECT2XL), ("f16", (12, 6, 8), lb.LB_KERNEL_DIRECT2X),
+         ("f16", (7, 5, 4), lb.LB_KERNEL_DIRECT1), ("bf16", (12, 6, 8), lb.LB_KERNEL_DIRECT2XL),
+         ("bf16", (262, 2, 5), lb.LB_KERNEL_AUTO)]
+
+
+@pytest.mark.parametrize("prec,shape,kernel", CASES)
+def test_walls_match_oracle(prec, shape, kernel, perm):
+    steps = 20
+    fl = _fields(shape)
+    got, rho_w, used = _gpu(shape, prec, fl, steps, kernel)
+    ref, ref_rho = _oracle(fl, steps)
+    w = oracle.velocities()[1][None, :, None, None, None]
+    f0 = oracle.init_fields(fl["rho"].numpy(), fl["u"].numpy(), fl["theta"].numpy())
+    h_max = max(np.abs(ref / w - 1).max(), np.abs(f0 / w - 1).max())
+    tol = 1e-12 if prec == "f64" else EPS_STORE[prec] * h_max * np.sqrt(steps) + 2e-7
+    rel = np.abs(to_oracle_order(got, perm) - ref) / np.abs(ref)
+    assert rel.max() <= tol, (prec, shape, lb.KERNEL_NAMES[used], rel.max(), tol)
+    assert np.abs(np.array(rho_w) - ref_rho[-1]).max() <= tol, (rho_w, ref_rho[-1])
+
+
+def test_walls_with_entropic_equilibrium_match_oracle(perm):
+    shape, steps = (8, 4, 6), 10
+    fl = _fields(shape, seed=13)
+    got, _, _ = _gpu(shape, "f64", fl, steps, flags=lb.LB_FLAG_ENTROPIC)
+    ref, _ = _oracle(fl, steps, project="entropic")
+    rel = np.abs(to_oracle_order(got, perm) - ref) / np.abs(ref)
+    assert rel.max() <= 1e-12, rel.max()
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-13), ("f32", 1e-6)])
+def test_walls_conserve_mass(prec, tol):
+    shape = (16, 8, 12)
+    fl = _fields(shape, seed=17)
+    ctx = lb.lb_init(shape, 0.35, prec)
+    try:
+        lb.lb_set_fields(ctx, fl["rho"].cuda(), fl["u"].cuda(), fl["theta"].cuda())
+        c0 = lb.lb_conserved(ctx)
+        lb.lb_set_walls(ctx, BOTTOM, TOP)
+        lb.lb_step(ctx, 100)
+        c1 = lb.lb_conserved(ctx)
+    finally:
+        lb.lb_destroy(ctx)
+    nodes = 2 * 16 * 8 * 12
+    assert abs(c1[0] - c0[0]) <= tol * nodes, (c0[0], c1[0])
+
+
+def test_rest_gas_between_rest_walls_stays_at_rest():
+    shape = (8, 4, 6)
+    ctx = lb.lb_init(shape, 0.3, "f32")
+    try:
+        n = 2 * 8 * 4 * 6
+        rho = torch.ones(n, dtype=torch.float64, device="cuda")
+        u = torch.zeros(3 * n, dtype=torch.float64, device="cuda")
+        th = torch.full((n,), TH0, dtype=torch.float64, device="cuda")
+        lb.lb_set_fields(ctx, rho, u, th)
+        lb.lb_set_walls(ctx, (0.0, 0.0, TH0), (0.0, 0.0, TH0))
+        before = np.empty((2, 41, 6, 4, 8))
+        lb.lb_get_populations(ctx, before)
+        lb.lb_step(ctx, 10)
+        after = np.empty_like(before)
+        lb.lb_get_populations(ctx, after)
+        # every absorbed population comes back as the same rest equilibrium (to the rounding of
+        # the FP64 equilibrium constants)
+        assert np.abs(after - before).max() <= 1e-13 * before.max()
+        rw = lb.lb_wall_density(ctx)
+        assert abs(rw[0] - 1.0) <= 1e-14 and abs(rw[1] - 1.0) <= 1e-14, rw
+    finally:
+        lb.lb_destroy(ctx)
+
+
+def _couette_gpu(H, ec, prec, nu=0.05, u0=0.02, n=4):
+    dT = u0 * u0 / (2.5 * ec)
+    ctx = lb.lb_init((n, n, H), nu / TH0, prec)
+    try:
+        nodes = 2 * n * n * H
+        lb.lb_set_fields(ctx, torch.ones(nodes, dtype=torch.float64, device="cuda"),
+                         torch.zeros(3 * nodes, dtype=torch.float64, device="cuda"),
+                         torch.full((nodes,), TH0, dtype=torch.float64, device="cuda"))
+        lb.lb_set_walls(ctx, (0.0, 0.0, TH0 - dT / 2), (u0, 0.0, TH0 + dT / 2))
+        lb.lb_step(ctx, int(3 * H * H / nu))
+        u = torch.empty((3, 2, H, n, n), dtype=torch.float64, device="cuda")
+        th = torch.empty((2, H, n, n), dtype=torch.float64, device="cuda")
+        lb.lb_get_moments(ctx, None, u, th)
+        lb.lb_sync(ctx)
+    finally:
+        lb.lb_destroy(ctx)
+    th = th.mean(dim=(2, 3)).cpu().numpy()
+    ux = u[0].mean(dim=(2, 3)).cpu().numpy()
+    y = np.array([[(2 * z + s) / 2.0 + 0.25 for z in range(H)] for s in range(2)]) / H
+    o = np.argsort(y.ravel())
+    y = y.ravel()[o]
+    tn = ((th - (TH0 - dT / 2)) / dT).ravel()[o]
+    un = (ux / u0).ravel()[o]
+    return y, tn, un, y + ec / 2 * y * (1 - y)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_couette_viscous_heating_on_gpu(prec):
+    """The steady profile of Eq. (eckert) at H = 16, Ec = 2, as the oracle reaches it (max
+    error 0.037), and agreement with the oracle's own steady profile."""
+    y, tn, un, ex = _couette_gpu(16, 2.0, prec)
+    assert np.abs(tn - ex).max() <= 0.04, np.abs(tn - ex).max()
+    assert np.abs(un - y).max() <= 0.01, np.abs(un - y).max()
+    dT = 0.02 ** 2 / 5.0
+    f = oracle.init_fields(np.ones((2, 16, 1, 1)), np.zeros((3, 2, 16, 1, 1)), np.full((2, 16, 1, 1), TH0))
+    f = oracle.step_walls(f, 0.05 / TH0, int(3 * 16 * 16 / 0.05), (0.0, 0.0, TH0 - dT / 2), (0.02, 0.0, TH0 + dT / 2))
+    _, _, th = oracle.get_moments(f)
+    ref = ((th.reshape(2, 16) - (TH0 - dT / 2)) / dT).ravel()
+    o = np.argsort(np.array([[(2 * z + s) for z in range(16)] for s in range(2)]).ravel())
+    # FP32: the temperature differences are 8e-5 of theta0, so FP32 rounding of h (2^-24 of
+    # order-1 sums) shows as ~1e-3 of dT
+    assert np.abs(tn - ref[o]).max() <= (1e-8 if prec == "f64" else 5e-3), np.abs(tn - ref[o]).max()
+
+
+def test_wall_arguments_and_batch_refusal():
+    ctx = lb.lb_init((4, 4, 3), 0.3, "f32")
+    try:
+        with pytest.raises(lb.LbError) as e:
+            lb.lb_set_walls(ctx, (0.0, 0.0, TH0), (0.0, 0.0, TH0))  # nz < 4
+        assert e.value.status == -1
+        with pytest.raises(lb.LbError) as e:
+            lb.lb_wall_density(ctx)
+        assert e.value.status == -7
+    finally:
+        lb.lb_destroy(ctx)
+    ctx = lb.lb_init((4, 4, 4), 0.3, "f32")
+    try:
+        with pytest.raises(lb.LbError):
+            lb.lb_set_walls(ctx, (0.0, 0.0, -1.0), (0.0, 0.0, TH0))
+        L = lb.lib()
+        b = (ctypes.c_double * 4)(0.0, 0.0, 0.01, TH0)  # moving along z
+        assert L.lb_set_walls(ctx, 1, ctypes.cast(b, ctypes.c_void_p), ctypes.cast(b, ctypes.c_void_p)) == -1
+    finally:
+        lb.lb_destroy(ctx)
+    b = lb.lb_batch_init([(4, 4, 4), (4, 4, 6)], [0.3, 0.4], "f32")
+    try:
+        lb.lb_set_walls(lb.lb_batch_sim(b, 1), (0.0, 0.0, TH0), (0.0, 0.0, TH0))
+        with pytest.raises(lb.LbError) as e:
+            lb.lb_batch_step(b, 1)
+        assert e.value.status == -7
+    finally:
+        lb.lb_batch_destroy(b)
+
+
+def test_walls_off_restores_periodic_update(perm):
+    shape = (8, 4, 6)
+    fl = _fields(shape, seed=19)
+    ctx = lb.lb_init(shape, 0.35, "f64")
+    try:
+        lb.lb_set_fields(ctx, fl["rho"].cuda(), fl["u"].cuda(), fl["theta"].cuda())
+        lb.lb_set_walls(ctx, BOTTOM, TOP)
+        lb.lb_set_walls(ctx)
+        lb.lb_step(ctx, 5)
+        f = np.empty((2, 41, 6, 4, 8))
+        lb.lb_get_populations(ctx, f)
+    finally:
+        lb.lb_destroy(ctx)
+    ref = oracle.step(oracle.init_fields(fl["rho"].numpy(), fl["u"].numpy(), fl["theta"].numpy()), 0.35, 5)
+    assert np.abs(to_oracle_order(f, perm) - ref).max() <= 1e-12 * np.abs(ref).max()
