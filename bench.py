@@ -49,6 +49,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-batch", action="store_true", help="skip the batched 64-simulation sweep")
+    p.add_argument("--no-walls", action="store_true", help="skip the run with kinetic walls normal to z")
     p.add_argument("--no-accuracy", action="store_true",
                    help="skip the error of the reduced-precision runs against the GPU FP64 mode")
     p.add_argument("--batch-steps", type=int, default=1000)
@@ -327,10 +328,12 @@ def main():
     by_kernel = {}
     clocks = None
 
-    def timed_run(prec, kernel, steps, warm, sample_clocks):
+    def timed_run(prec, kernel, steps, warm, sample_clocks, walls=False):
         ctx = lb.lb_init((n, n, n), tau, prec)
         try:
             lb.lb_set_fields(ctx, fields["rho"], fields["u"], fields["theta"])
+            if walls:  # a Couette channel: still wall below, moving wall above, 2e-4 theta0 apart
+                lb.lb_set_walls(ctx, (0.0, 0.0, th0 * (1 - 1e-4)), (0.02, 0.0, th0 * (1 + 1e-4)))
             if kernel is None:
                 lb.lb_tune(ctx, reps=3)
             else:
@@ -381,6 +384,13 @@ def main():
         best = applicable[0]
     results[head], sampler = timed_run(head, best, args.steps, args.warmup, True)
     clocks = sampler.summary()
+    walls = None
+    if not args.no_walls:
+        r, _ = timed_run(head, best, max(5, args.steps // 5), 3, False, walls=True)
+        walls = {"mlups": r["mlups"], "ms_per_step": r["ms_per_step"], "steps": r["steps"],
+                 "vs_periodic": r["mlups"] / results[head]["mlups"],
+                 "note": "kinetic walls normal to z (Couette channel), same grid, precision and step kernel; "
+                         "adds the wall sums and the update of the 2 outermost cell layers at each wall"}
     if not args.no_secondary:
         for prec in precs[1:]:
             steps = max(3, args.steps // 10) if prec == "f64" else max(5, args.steps // 2)
@@ -457,6 +467,7 @@ def main():
                              "steps": v["steps"], "kernel": v["kernel"]} for p, v in results.items()},
         "by_kernel": by_kernel,
         "accuracy": accuracy,
+        "walls": walls,
         "batch": batch,
         "gpu_launches": r["steps"],
         "clocks": clocks,
