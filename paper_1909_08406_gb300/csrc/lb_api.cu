@@ -224,6 +224,7 @@ lb_status lb_init(lb_ctx** out, lb_grid grid, int velocity_set, double theta0, d
     c->esize = storage_bytes(c->prec);
     c->cur = 0;
     c->time = 0;
+    c->wall_sums = 0;
     cudaError_t e = cudaGetDevice(&c->device);
     int sms = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -368,6 +369,7 @@ lb_status lb_set_fields(lb_ctx* c, const double* rho, const double* u, const dou
         CK(c, cudaStreamSynchronize(c->stream));
     }
     c->time = 0;
+    c->wall_sums = 0;
     return LB_OK;
 }
 
@@ -376,9 +378,12 @@ lb_status lb_step(lb_ctx* c, int64_t n) {
     CK(c, cudaSetDevice(c->device));
     const LaunchConsts& lc = lattice().lc;
     for (int64_t t = 0; t < n; ++t) {
-        if (c->walls)
+        if (c->walls) {
             CK(c, launch_wall_step(c->prec, c->eq, c->variant, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc,
-                                   c->twobeta, c->d_wall, c->d_err, c->stream));
+                                   c->twobeta, c->d_wall, c->d_wall_part, c->wall_sums != 0, c->d_err,
+                                   c->stream));
+            c->wall_sums = 1;
+        }
         else
             CK(c, launch_step(c->prec, c->eq, c->variant, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc,
                               c->twobeta, c->d_err, c->stream));
@@ -486,6 +491,7 @@ lb_status lb_set_populations(lb_ctx* c, const double* f, int on_device) {
         CK(c, cudaStreamSynchronize(c->stream));
     }
     c->time = 0;
+    c->wall_sums = 0;
     return LB_OK;
 }
 
@@ -507,6 +513,7 @@ lb_status lb_set_state(lb_ctx* c, const void* raw, int on_device) {
                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     if (!on_device) CK(c, cudaStreamSynchronize(c->stream));
     c->time = 0;
+    c->wall_sums = 0;
     return LB_OK;
 }
 
@@ -522,6 +529,7 @@ lb_status lb_destroy(lb_ctx* c) {
     cudaFree(c->d_partials);
     cudaFree(c->d_stage);
     cudaFree(c->d_wall);
+    cudaFree(c->d_wall_part);
     delete c;
     return LB_OK;
 }
@@ -541,12 +549,16 @@ lb_status lb_set_walls(lb_ctx* c, int enable, const double bottom[4], const doub
     CK(c, cudaSetDevice(c->device));
     if (!c->d_wall) {
         cudaError_t e = cudaMalloc(&c->d_wall, wall_block_bytes());
+        if (e == cudaSuccess) e = cudaMalloc(&c->d_wall_part, sizeof(double) * wall_part_doubles(c->d));
         if (e != cudaSuccess) {
+            cudaFree(c->d_wall);
             c->d_wall = nullptr;
+            c->d_wall_part = nullptr;
             return fail(c, e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA,
                         std::string("lb_set_walls: ") + cudaGetErrorString(e));
         }
     }
+    c->wall_sums = 0;
     const double w[8] = {bottom[0], bottom[1], bottom[2], bottom[3], top[0], top[1], top[2], top[3]};
     CK(c, launch_wall_setup(c->eq, c->d_wall, c->d, lattice().lc, w, c->stream));
     double rho[2];

@@ -80,9 +80,13 @@ size_t wall_block_bytes();
 int wall_rho_offset();  // index of rho_w (2 doubles) in the block
 cudaError_t launch_wall_setup(int eq, double* blk, const Dims& d, const LaunchConsts& c, const double wall[8],
                               cudaStream_t st);
-// One step with the walls: absorbed mass, rho_w, the periodic step, then the wall layers.
+// Doubles of the absorbed-mass partials buffer for this grid.
+size_t wall_part_doubles(const Dims& d);
+// One step with the walls: rho_w (from the partials the last wall step left, or from src when
+// sums_valid is false), the periodic step, then the wall layers, which leave the next partials.
 cudaError_t launch_wall_step(int prec, int eq, int variant, const void* src, void* dst, const Dims& d,
-                             const LaunchConsts& c, double twobeta, double* blk, int* err, cudaStream_t st);
+                             const LaunchConsts& c, double twobeta, double* blk, double* part, bool sums_valid,
+                             int* err, cudaStream_t st);
 
 inline dim3 step_grid(const Dims& d, int threads) {
     return dim3((unsigned)d.rows, (unsigned)((d.nx + threads - 1) / threads), 1);

@@ -13,13 +13,18 @@
 // step, the balance taken over the whole wall plane).
 //
 // Per step, around the ordinary periodic step kernel (src -> dst):
-//   k_wall_absorb   absorbed mass per wall, FP64, from src (partials per block)
-//   k_wall_density  rho_w per wall and the 2 x 41 emitted working values
+//   k_wall_density  rho_w per wall from the absorbed-mass partials, and the
+//                   2 x 41 emitted working values
 //   <periodic step> every node; nodes next to a wall pull wrapped values here
 //   k_step_walls    recomputes the nodes of the 2 outermost cell layers at
 //                   each wall (the only ones with upwind positions beyond a
-//                   wall: links reach 2 cells), src -> dst, overwriting them.
-// The sums are taken in a fixed order, so a step is deterministic.
+//                   wall: links reach 2 cells), src -> dst, overwriting them,
+//                   and sums, per block, the mass that the next step's walls
+//                   absorb from what it stores (those layers are the only
+//                   ones with populations leaving through a wall).
+// After the state is set from outside (fields, populations, a checkpoint,
+// new walls), k_wall_absorb forms the same partials from the stored state once.
+// Every sum is taken in a fixed order, so a step is deterministic.
 #include <math.h>
 
 #include "lb_ctx.h"
@@ -27,21 +32,21 @@
 
 namespace gblb {
 
-constexpr int kWallBlocks = 64;     // absorb partials per wall
-constexpr int kWallThreads = 256;
+constexpr int kDensityThreads = 512;
 
 // Device block of one context's walls (doubles unless noted):
 //   e[2][kQ]        f^eq_i(1, u_w, theta_w) of the bottom and top wall
 //   emit[2]         sum over the (node, i) pairs a unit-density wall feeds
-//   part[2][kWallBlocks]  absorbed-mass partials
+//   wsum[2]         sum of w_i over the (node, i) pairs a wall absorbs: the rest-state part of
+//                   the absorbed mass, which the deviation codecs do not sum per node
 //   rho[2]          rho_w of the last step
 //   vd[2][kQ]       emitted working values (FP64 codec)
 //   vf[2][kQ]       emitted working values as float (FP32 arithmetic codecs)
 struct WallLayout {
     static constexpr int e = 0;
     static constexpr int emit = e + 2 * kQ;
-    static constexpr int part = emit + 2;
-    static constexpr int rho = part + 2 * kWallBlocks;
+    static constexpr int wsum = emit + 2;
+    static constexpr int rho = wsum + 2;
     static constexpr int vd = rho + 2;
     static constexpr int vf = vd + 2 * kQ;  // float[2 * kQ] from here
     static constexpr int doubles = vf + kQ;  // 2 * kQ floats fit in kQ doubles
@@ -69,65 +74,102 @@ __global__ void k_wall_setup(double* __restrict__ blk, Dims d, Consts<double> K,
     equilibrium_relax<CodecF64, EQ>(st, K, 1.0, 0.0, zero, [&](auto I, double val) { e[I] = val; }, ok);
     // a unit-density wall feeds population i (c_iz > 0 for the bottom, < 0 for the top) into
     // the node planes z2 with z2 - 2 c_iz beyond it: |2 c_iz| planes of nx * ny nodes
-    double sum = 0.0;
+    // and absorbs population i (c_iz < 0 at the bottom, > 0 at the top) from |2 c_iz| planes
+    double sum = 0.0, wsum = 0.0;
     for (int i = 0; i < kQ; ++i) {
         const int cz = c_vel.v[i].z;
         const int planes = side ? (cz < 0 ? -cz : 0) : (cz > 0 ? cz : 0);
+        const int out_planes = side ? (cz > 0 ? cz : 0) : (cz < 0 ? -cz : 0);
         sum += (double)planes * e[i];
+        wsum += (double)out_planes * K.w[c_vel.v[i].shell];
     }
     blk[WallLayout::emit + side] = sum * (double)d.nx * (double)d.ny;
+    blk[WallLayout::wsum + side] = wsum * (double)d.nx * (double)d.ny;
     blk[WallLayout::rho + side] = ok ? 1.0 : nan("");
 }
 
-// Absorbed mass: sum of f over the populations of the two outermost cell layers at the wall
-// whose destination z2 + 2 c_iz lies beyond it.  blockIdx.y: 0 bottom, 1 top.
+// Block sum in a fixed order (warp trees, then the warps' sums in order); every thread of
+// the block must call it.  The result is valid in thread 0.
+__device__ __forceinline__ double block_sum_fixed(double v) {
+    __shared__ double warp_sums[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) warp_sums[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < (int)(blockDim.x + 31) / 32; ++k) t += warp_sums[k];
+    return t;
+}
+
+// Absorbed mass of the stored state, in the partial layout and summation order of
+// k_step_walls (one partial per block of its grid, each node's populations in index order,
+// block_sum_fixed), so that a state set from outside gives the same wall densities as the
+// same state reached by stepping.
+// A stored value's share of the absorbed mass: f itself for the FP64 codec; for the deviation
+// codecs w h (the rest-state part w is added once per wall, from wsum), in the compute type.
 template <class Codec>
-__global__ void __launch_bounds__(kWallThreads) k_wall_absorb(const typename Codec::raw_t* __restrict__ src, Dims d,
-                                                              Consts<double> K, double* __restrict__ blk) {
-    const int side = blockIdx.y;
-    const int64_t nxy = (int64_t)d.nx * d.ny;
-    const int64_t items = 4 * nxy;  // (layer, s) x (y, x)
-    const int64_t nz2 = 2 * (int64_t)d.nz;
+__device__ __forceinline__ typename Codec::R absorbed_part(typename Codec::R v, typename Codec::R w) {
+    using R = typename Codec::R;
+    if constexpr (Codec::stores_f)
+        return v;
+    else
+        return w * (v * R(1.0 / Codec::kScale));
+}
+
+template <class Codec>
+__global__ void __launch_bounds__(kStepThreads) k_wall_absorb(const typename Codec::raw_t* __restrict__ src, Dims d,
+                                                              Consts<typename Codec::R> K,
+                                                              double* __restrict__ part) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
     double acc = 0.0;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < items;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const int ls = (int)(k / nxy);
-        const int64_t xy = k - ls * nxy;
+    if (x < d.nx) {
+        const int row = blockIdx.y;  // (layer * 2 + s) * ny + y
+        const int y = row % d.ny;
+        const int ls = row / d.ny;
         const int layer = ls >> 1, s = ls & 1;
-        const int z = side ? d.nz - 2 + layer : layer;
-        const int64_t z2 = 2 * (int64_t)z + s;
-        const typename Codec::raw_t* p = src + ((int64_t)s * kQ * d.plane + (int64_t)z * nxy + xy);
+        const int z = layer < 2 ? layer : d.nz - 4 + layer;
+        const int z2 = 2 * z + s, nz2 = 2 * d.nz;
+        const bool bottom = layer < 2;
+        const typename Codec::raw_t* p =
+            src + ((int64_t)s * kQ * d.plane + ((int64_t)z * d.ny + y) * d.nx + x);
+        typename Codec::R a = 0;
         static_for<kQ>([&](auto I) {
             constexpr Vel c = vel(I);
             if constexpr (c.z != 0) {
-                const int64_t dest = z2 + c.z;
-                if (side ? dest >= nz2 : dest < 0) {
-                    const double v = (double)Codec::value(p[(int64_t)I * d.plane]);
-                    const double w = K.w[c.shell];
-                    acc += Codec::stores_f ? v : w * (1.0 + v * (1.0 / Codec::kScale));
-                }
+                const int dest = z2 + c.z;
+                if (bottom ? dest < 0 : dest >= nz2)
+                    a += absorbed_part<Codec>(Codec::value(p[(int64_t)I * d.plane]), K.w[c.shell]);
             }
         });
+        acc = (double)a;
     }
-    __shared__ double red[kWallThreads];
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int h = kWallThreads / 2; h > 0; h >>= 1) {
-        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) blk[WallLayout::part + side * kWallBlocks + blockIdx.x] = red[0];
+    const double t = block_sum_fixed(acc);
+    if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = t;
 }
 
-// rho_w = absorbed / emitted-at-unit-density per wall, and the working values the wall
-// emits: f for the FP64 codec, (f / w - 1) * scale for the deviation codecs.
+// part[side * nper + k], k < nper: the absorbed-mass partials of each wall.
 template <class Codec>
-__global__ void k_wall_density(double* __restrict__ blk, Consts<double> K) {
+__global__ void __launch_bounds__(kDensityThreads) k_wall_density(double* __restrict__ blk, Consts<double> K,
+                                                                  const double* __restrict__ part, int nper) {
+    __shared__ double red[2][kDensityThreads];
     __shared__ double rho[2];
-    if (threadIdx.x < 2) {
+    for (int side = 0; side < 2; ++side) {
         double a = 0.0;
-        for (int b = 0; b < kWallBlocks; ++b) a += blk[WallLayout::part + threadIdx.x * kWallBlocks + b];
-        rho[threadIdx.x] = a / blk[WallLayout::emit + threadIdx.x];
+        for (int k = threadIdx.x; k < nper; k += kDensityThreads) a += part[side * nper + k];
+        red[side][threadIdx.x] = a;
+    }
+    __syncthreads();
+    for (int h = kDensityThreads / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + h];
+            red[1][threadIdx.x] += red[1][threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 2) {
+        const double absorbed = red[threadIdx.x][0] + (Codec::stores_f ? 0.0 : blk[WallLayout::wsum + threadIdx.x]);
+        rho[threadIdx.x] = absorbed / blk[WallLayout::emit + threadIdx.x];
         blk[WallLayout::rho + threadIdx.x] = rho[threadIdx.x];
     }
     __syncthreads();
@@ -144,19 +186,16 @@ __global__ void k_wall_density(double* __restrict__ blk, Consts<double> K) {
     }
 }
 
-// The update of the nodes in the two outermost cell layers at each wall: the gather of
-// step_node with every upwind position beyond a wall replaced by that wall's emission.
-// Grid: x = x chunks, y = (layer 0..3, s, y) rows; layers 0, 1 at the bottom, 2, 3 at the top.
+
+// One node of k_step_walls; returns the mass its stored values send through the wall.
 template <class Codec, int EQ>
-__global__ void __launch_bounds__(kStepThreads) k_step_walls(const typename Codec::raw_t* __restrict__ src,
-                                                             typename Codec::raw_t* __restrict__ dst, Dims d,
-                                                             Consts<typename Codec::R> K, typename Codec::R tb,
-                                                             const typename Codec::R* __restrict__ vwall,
-                                                             int* __restrict__ err) {
+__device__ __forceinline__ double wall_node(const typename Codec::raw_t* __restrict__ src,
+                                            typename Codec::raw_t* __restrict__ dst, const Dims& d,
+                                            const Consts<typename Codec::R>& K, typename Codec::R tb,
+                                            const typename Codec::R* __restrict__ vwall, int* __restrict__ err,
+                                            int x) {
     using R = typename Codec::R;
     using T = typename Codec::raw_t;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= d.nx) return;
     const int row = blockIdx.y;  // (layer * 2 + s) * ny + y
     const int y = row % d.ny;
     const int ls = row / d.ny;
@@ -202,9 +241,40 @@ __global__ void __launch_bounds__(kStepThreads) k_step_walls(const typename Code
     const NodeState<R> st = state_from_moments(moments_from_dev(dv), K);
     bool ok = state_ok(st);
     T* out = dst + (int64_t)s * kQ * d.plane + (int64_t)z * nxy + (int64_t)y * d.nx + x;
+    R absorbed = 0;
+    const bool bottom = layer < 2;
     equilibrium_relax<Codec, EQ>(st, K, tb * R(Codec::kScale), R(1) - tb, v,
-                                 [&](auto I, R val) { out[(int64_t)I * d.plane] = Codec::to_raw(val); }, ok);
+                                 [&](auto I, R val) {
+                                     const T raw = Codec::to_raw(val);
+                                     out[(int64_t)I * d.plane] = raw;
+                                     constexpr Vel c = vel(I);
+                                     if constexpr (c.z != 0) {
+                                         const int dest = z2 + c.z;
+                                         if (bottom ? dest < 0 : dest >= nz2)
+                                             absorbed += absorbed_part<Codec>(Codec::value(raw), K.w[c.shell]);
+                                     }
+                                 },
+                                 ok);
     if (!ok) atomicOr(err, 1);
+    return (double)absorbed;
+}
+
+// The update of the nodes in the two outermost cell layers at each wall: the gather of
+// step_node with every upwind position beyond a wall replaced by that wall's emission.
+// Grid: x = x chunks, y = (layer 0..3, s, y) rows; layers 0, 1 at the bottom, 2, 3 at the top.
+// part[blockIdx.y * gridDim.x + blockIdx.x] receives the mass that the stored values will
+// send through the block's wall in the next step (bottom partials first, then top).
+template <class Codec, int EQ>
+__global__ void __launch_bounds__(kStepThreads) k_step_walls(const typename Codec::raw_t* __restrict__ src,
+                                                             typename Codec::raw_t* __restrict__ dst, Dims d,
+                                                             Consts<typename Codec::R> K, typename Codec::R tb,
+                                                             const typename Codec::R* __restrict__ vwall,
+                                                             double* __restrict__ part, int* __restrict__ err) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    double absorbed = 0.0;
+    if (x < d.nx) absorbed = wall_node<Codec, EQ>(src, dst, d, K, tb, vwall, err, x);
+    const double t = block_sum_fixed(absorbed);
+    if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = t;
 }
 
 template <class F>
@@ -237,13 +307,31 @@ cudaError_t launch_wall_setup(int eq, double* blk, const Dims& d, const LaunchCo
     });
 }
 
+// Blocks of k_step_walls along x for this grid (and the step kernels' row width).
+static int wall_chunks(const Dims& d) {
+    const int th = step_threads(d);
+    return (d.nx + th - 1) / th;
+}
+
+size_t wall_part_doubles(const Dims& d) { return (size_t)8 * d.ny * wall_chunks(d); }
+
 cudaError_t launch_wall_step(int prec, int eq, int variant, const void* src, void* dst, const Dims& d,
-                             const LaunchConsts& c, double twobeta, double* blk, int* err, cudaStream_t st) {
+                             const LaunchConsts& c, double twobeta, double* blk, double* part, bool sums_valid,
+                             int* err, cudaStream_t st) {
+    const int chunks = wall_chunks(d);
     cudaError_t e = with_codec(prec, [&](auto codec) {
         using C = decltype(codec);
-        k_wall_absorb<C><<<dim3(kWallBlocks, 2), kWallThreads, 0, st>>>(static_cast<const typename C::raw_t*>(src),
-                                                                         d, c.kd, blk);
-        k_wall_density<C><<<1, 96, 0, st>>>(blk, c.kd);
+        using R = typename C::R;
+        const int nper = 4 * d.ny * chunks;  // partials per wall (k_step_walls' blocks)
+        const Consts<R>* K;
+        if constexpr (sizeof(R) == 8)
+            K = &c.kd;
+        else
+            K = &c.kf;
+        if (!sums_valid)
+            k_wall_absorb<C><<<dim3((unsigned)chunks, (unsigned)(8 * d.ny)), step_threads(d), 0, st>>>(
+                static_cast<const typename C::raw_t*>(src), d, *K, part);
+        k_wall_density<C><<<1, kDensityThreads, 0, st>>>(blk, c.kd, part, nper);
         return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;
@@ -253,7 +341,7 @@ cudaError_t launch_wall_step(int prec, int eq, int variant, const void* src, voi
         using C = decltype(codec);
         using R = typename C::R;
         const int th = step_threads(d);
-        const dim3 grid((unsigned)((d.nx + th - 1) / th), (unsigned)(8 * d.ny));
+        const dim3 grid((unsigned)chunks, (unsigned)(8 * d.ny));
         const R* vw;
         if constexpr (sizeof(R) == 8)
             vw = reinterpret_cast<const R*>(blk + WallLayout::vd);
@@ -267,7 +355,7 @@ cudaError_t launch_wall_step(int prec, int eq, int variant, const void* src, voi
         return with_eq(eq, [&](auto E) {
             k_step_walls<C, decltype(E)::value><<<grid, th, 0, st>>>(
                 static_cast<const typename C::raw_t*>(src), static_cast<typename C::raw_t*>(dst), d, *K,
-                (R)twobeta, vw, err);
+                (R)twobeta, vw, part, err);
             return cudaGetLastError();
         });
     });
