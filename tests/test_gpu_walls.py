@@ -255,3 +255,33 @@ def test_checkpoint_restart_with_walls_is_bitwise(prec):
         lb.lb_destroy(ctx)
     assert torch.equal(a, b)
     assert rho_a == rho_b
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_thermoacoustic_column_on_gpu_follows_nsf(prec):
+    """The thermoacoustic column of the oracle's test (H = 64, nu = 0.05, top wall heated by
+    0.01 theta0) on the GPU, against the linearised NSF solution, with the oracle's bounds."""
+    from oracle import nsf1d
+    H, nu, dT, n = 64, 0.05, 0.01 * TH0, 2
+    nodes = 2 * n * n * H
+    ctx = lb.lb_init((n, n, H), nu / TH0, prec)
+    out, t = {}, 0
+    try:
+        lb.lb_set_fields(ctx, torch.ones(nodes, dtype=torch.float64, device="cuda"),
+                         torch.zeros(3 * nodes, dtype=torch.float64, device="cuda"),
+                         torch.full((nodes,), TH0, dtype=torch.float64, device="cuda"))
+        lb.lb_set_walls(ctx, (0.0, 0.0, TH0), (0.0, 0.0, TH0 + dT))
+        for tt in (90, 400):
+            lb.lb_step(ctx, tt - t)
+            t = tt
+            th = torch.empty((2, H, n, n), dtype=torch.float64, device="cuda")
+            lb.lb_get_moments(ctx, None, None, th)
+            lb.lb_sync(ctx)
+            out[tt] = th.mean(dim=(2, 3)).cpu().numpy().ravel() - TH0
+    finally:
+        lb.lb_destroy(ctx)
+    y = np.array([[(2 * z + s) / 2.0 + 0.25 for z in range(H)] for s in range(2)]).ravel()
+    ref = nsf1d.column(float(H), nu, dT, TH0, [90, 400])
+    err = {tt: np.abs(out[tt] - np.interp(y, ref[tt][0], ref[tt][2])).max() / dT for tt in (90, 400)}
+    assert err[90] <= 0.09 and err[400] <= 0.04, err
+    assert err[90] / err[400] >= 1.8, err
