@@ -265,6 +265,17 @@ def run_batch(lb, wl, torch, steps, count=64):
     return out
 
 
+def workload_config(args, world):
+    """The `config` of both arms' JSON lines: the workload the main arm times."""
+    n = args.n
+    nodes = 2 * n ** 3
+    return {"workload": f"thermoacoustic pulse, {n}^3 periodic bcc grid ({nodes} nodes), nu = {NU}, "
+                        f"{args.precision} storage", "grid": n, "nodes": nodes, "precision": args.precision,
+            "l2": "inputs larger than L2 (population buffers of "
+                  f"{nodes * 41 * BYTES[args.precision] / 1e9:.1f} GB each)",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -282,12 +293,12 @@ def run_reference(args, rank, world):
     el = time.perf_counter() - t0
     nodes = 2 * box ** 3
     v = nodes * steps / el / 1e6
-    sample = (f"{box}^3 periodic box of the thermoacoustic recipe (sigma 2 cells), FP64 oracle, "
-              f"{steps} steps after {args.warmup} warm-up steps")
+    sample = (f"bounded sample of the workload: a {box}^3 periodic box of the thermoacoustic recipe (pulse "
+              f"sigma 2 cells), FP64 oracle, {steps} steps after {args.warmup} warm-up steps, MLUPS of that box")
     line = {"impl": "reference", "metric": "MLUPS", "value": v, "unit": "MLUPS", "n_gpus": world, "steps": steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"thermoacoustic {args.n}^3 (reference arm: bounded {box}^3 sample)"},
+            "config": workload_config(args, world),
             "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": oracle.max_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -462,11 +473,7 @@ def main():
         "metric": "MLUPS", "value": r["mlups"], "unit": "MLUPS", "n_gpus": world, "steps": r["steps"],
         "warmup": r["warmup"], "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPE_NAME[args.precision], "data": "synthetic",
-        "config": {"workload": f"thermoacoustic pulse, {n}^3 periodic bcc grid ({nodes} nodes), nu = {NU}, "
-                               f"{args.precision} storage", "grid": n, "nodes": nodes, "precision": args.precision,
-                   "l2": "inputs larger than L2 (population buffers of "
-                         f"{nodes * 41 * BYTES[args.precision] / 1e9:.1f} GB each)",
-                   "parallelism": f"replicas x{world}"},
+        "config": workload_config(args, world),
         "roofline": {"bound": "hbm", "achieved": r["achieved_gbs"], "peak": peak, "unit": "GB/s",
                      "frac": r["achieved_gbs"] / peak, "traffic": traffic, "peak_kind": peak_kind,
                      "kernel": r["kernel"], "alg_bytes_per_launch": r["alg_bytes_per_launch"]},
