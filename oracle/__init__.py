@@ -148,14 +148,18 @@ def step(f, tau, nsteps, project=True, nthreads=None):
 
 def step_walls(f, tau, nsteps, bottom, top, project=True, nthreads=None, wall_rho=False):
     """Advance f by nsteps with kinetic (diffuse) walls normal to z (x, y periodic).
-    bottom, top: (u_x, u_y, theta) of each wall; the walls sit a quarter cell beyond the
-    outermost node planes (channel height nz cells).  With wall_rho=True also returns the
-    walls' densities per step, shape (nsteps, 2)."""
+    bottom, top: (u_x, u_y, theta) of each wall, each a number (the same for every cell column
+    of the wall) or an array [ny][nx]; the walls sit a quarter cell beyond the outermost node
+    planes (channel height nz cells).  With wall_rho=True also returns the walls' densities per
+    step and column, shape (nsteps, 2, ny, nx)."""
     f = np.array(f, dtype=np.float64, order="C", copy=True)
     _, _, nz, ny, nx = f.shape
     work = np.empty_like(f)
-    w = np.array([bottom[0], bottom[1], 0.0, bottom[2], top[0], top[1], 0.0, top[2]], dtype=np.float64)
-    rho_w = np.zeros((int(nsteps), 2))
+    w = np.zeros((2, 4, ny, nx))
+    for side, (ux, uy, th) in enumerate((bottom, top)):
+        w[side, 0], w[side, 1], w[side, 3] = ux, uy, th
+    w = np.ascontiguousarray(w)
+    rho_w = np.zeros((int(nsteps), 2, ny, nx))
     lib().or_step_walls(_i64(nx), _i64(ny), _i64(nz), ctypes.c_double(tau), _kind(project), _i64(nsteps),
                         _p(f), _p(work), _p(w), _p(rho_w), _threads(nthreads))
     return (f, rho_w) if wall_rho else f

@@ -48,7 +48,8 @@
  *   - The kinetic wall condition the paper cites (Ansumali and Karlin 2002) is
  *     not restated there; or_step_walls writes it for this lattice as diffuse
  *     reflection with the walls a quarter cell beyond the outermost node planes
- *     and one wall density per wall and step (see that function).
+ *     and one wall density per cell column of the wall and step (see that
+ *     function).
  *
  * Array layout used by every grid routine here (the oracle's own velocity
  * order, given by or_velocities):
@@ -474,35 +475,53 @@ void or_step_nodes(int64_t nx, int64_t ny, int64_t nz, double tau, int project, 
 /* Kinetic (diffuse) walls normal to z                                 */
 /* ------------------------------------------------------------------ */
 
+/* Wall column of a doubled lateral coordinate q (periodic, n cells).  The bottom wall's
+ * column x holds q in {2x, 2x + 1}, the top wall's {2x - 1, 2x}: the bottom wall faces the A
+ * plane z = 0 and the top wall the B plane z = nz - 1, and the mirror that exchanges the walls
+ * shifts x and y by half a cell, so it carries the one partition onto the other. */
+static int64_t column_of(int64_t q, int64_t n, int side) {
+    q += side;
+    return mod(q >= 0 ? q / 2 : -((-q + 1) / 2), n);
+}
+
 /* n time steps with two kinetic walls normal to z instead of the periodic
  * wrap in z (x and y stay periodic).  In doubled coordinates the nodes occupy
  * z2 = 2z + s in [0, 2 nz); the bottom wall lies at z2 = -1/2 and the top
  * wall at z2 = 2 nz - 1/2, a quarter cell beyond the outermost node planes,
  * so the channel height is nz cells.  The paper applies the kinetic boundary
  * condition of Ansumali and Karlin (2002) without restating it; this is that
- * condition (diffuse reflection) written for the crystallographic lattice:
+ * condition (diffuse reflection) written for the crystallographic lattice,
+ * point by point along the wall, the wall being divided into the cell
+ * columns (x, y) of the grid:
  *   - a post-collision population whose destination z2 + 2 c_iz lies beyond a
- *     wall is absorbed by that wall;
+ *     wall is absorbed by the wall column that contains its destination's
+ *     (x, y) (see column_of for how a wall is cut into columns);
  *   - a population whose upwind position z2 - 2 c_iz lies beyond a wall is
- *     emitted by it: f_i = rho_w f^eq_i(1, u_w, theta_w), the model's own
- *     equilibrium at the wall's velocity and temperature;
- *   - rho_w makes the emitted mass equal to the absorbed mass, so the wall
- *     neither creates nor destroys mass.  rho_w is one value per wall and
- *     step, the balance taken over the whole wall plane: this is the local
- *     condition for flows that are uniform along the wall.
- * wall[8] = {u_x, u_y, u_z, theta} of the bottom wall, then of the top wall
- * (u_z must be 0).  wall_rho[2 * nsteps] receives rho_w of both walls per
- * step if it is not NULL. */
+ *     emitted by the wall column that contains the upwind position's (x, y):
+ *     f_i = rho_w f^eq_i(1, u_w, theta_w), the model's own equilibrium at that
+ *     column's velocity and temperature;
+ *   - rho_w of each column makes the mass it emits equal to the mass it
+ *     absorbs, so no column creates or destroys mass.
+ * wall[2][4][ny][nx]: {u_x, u_y, u_z, theta} of every column of the bottom
+ * wall, then of the top wall (u_z must be 0).  wall_rho[nsteps][2][ny][nx]
+ * receives the columns' rho_w per step if it is not NULL. */
 void or_step_walls(int64_t nx, int64_t ny, int64_t nz, double tau, int project, int64_t nsteps, double *f,
-                   double *work, const double wall[8], double *wall_rho, int nthreads) {
+                   double *work, const double *wall, double *wall_rho, int nthreads) {
     init_lattice();
     set_threads(nthreads);
-    double eb[NV], et[NV];
-    equilibrium_of_kind(1.0, wall, wall[3], project, eb);
-    equilibrium_of_kind(1.0, wall + 4, wall[7], project, et);
+    const int64_t ncol = nx * ny;
+    double *e = (double *)malloc(sizeof(double) * (size_t)(2 * ncol * NV));  /* [side][col][i] */
+    double *emitted = (double *)malloc(sizeof(double) * (size_t)(2 * ncol));
+    double *absorbed = (double *)malloc(sizeof(double) * (size_t)(2 * ncol));
+    double *rho_w = (double *)malloc(sizeof(double) * (size_t)(2 * ncol));
+    for (int side = 0; side < 2; ++side)
+        for (int64_t col = 0; col < ncol; ++col) {
+            const double *w = wall + side * 4 * ncol;
+            double u[3] = {w[col], w[ncol + col], w[2 * ncol + col]};
+            equilibrium_of_kind(1.0, u, w[3 * ncol + col], project, e + (side * ncol + col) * NV);
+        }
     for (int64_t t = 0; t < nsteps; ++t) {
-        /* mass absorbed by each wall, and the emission of a unit-density wall */
-        double absorbed[2] = {0.0, 0.0}, emitted[2] = {0.0, 0.0};
+        for (int64_t k = 0; k < 2 * ncol; ++k) absorbed[k] = emitted[k] = 0.0;
         for (int s = 0; s < 2; ++s)
             for (int i = 0; i < NV; ++i)
                 for (int64_t z = 0; z < nz; ++z)
@@ -510,17 +529,21 @@ void or_step_walls(int64_t nx, int64_t ny, int64_t nz, double tau, int project, 
                         for (int64_t x = 0; x < nx; ++x) {
                             int64_t z2 = 2 * z + s;
                             int64_t dest = z2 + C2[i][2], src = z2 - C2[i][2];
-                            double v = f[pidx(nx, ny, nz, s, i, z, y, x)];
-                            if (dest < 0) absorbed[0] += v;
-                            if (dest >= 2 * nz) absorbed[1] += v;
-                            if (src < 0) emitted[0] += eb[i];
-                            if (src >= 2 * nz) emitted[1] += et[i];
+                            if (dest < 0 || dest >= 2 * nz) {
+                                int side = dest < 0 ? 0 : 1;
+                                int64_t col = column_of(2 * y + s + C2[i][1], ny, side) * nx +
+                                              column_of(2 * x + s + C2[i][0], nx, side);
+                                absorbed[side * ncol + col] += f[pidx(nx, ny, nz, s, i, z, y, x)];
+                            }
+                            if (src < 0 || src >= 2 * nz) {
+                                int side = src < 0 ? 0 : 1;
+                                int64_t col = column_of(2 * y + s - C2[i][1], ny, side) * nx +
+                                              column_of(2 * x + s - C2[i][0], nx, side);
+                                emitted[side * ncol + col] += e[(side * ncol + col) * NV + i];
+                            }
                         }
-        double rb = absorbed[0] / emitted[0], rt = absorbed[1] / emitted[1];
-        if (wall_rho) {
-            wall_rho[2 * t] = rb;
-            wall_rho[2 * t + 1] = rt;
-        }
+        for (int64_t k = 0; k < 2 * ncol; ++k) rho_w[k] = absorbed[k] / emitted[k];
+        if (wall_rho) memcpy(wall_rho + t * 2 * ncol, rho_w, sizeof(double) * (size_t)(2 * ncol));
 #pragma omp parallel for collapse(3) schedule(static)
         for (int s = 0; s < 2; ++s)
             for (int64_t z = 0; z < nz; ++z)
@@ -529,18 +552,24 @@ void or_step_walls(int64_t nx, int64_t ny, int64_t nz, double tau, int project, 
                         double fin[NV], fout[NV];
                         for (int i = 0; i < NV; ++i) {
                             int64_t src = 2 * z + s - C2[i][2];
-                            if (src < 0)
-                                fin[i] = rb * eb[i];
-                            else if (src >= 2 * nz)
-                                fin[i] = rt * et[i];
-                            else
+                            if (src < 0 || src >= 2 * nz) {
+                                int side = src < 0 ? 0 : 1;
+                                int64_t col = column_of(2 * y + s - C2[i][1], ny, side) * nx +
+                                              column_of(2 * x + s - C2[i][0], nx, side);
+                                fin[i] = rho_w[side * ncol + col] * e[(side * ncol + col) * NV + i];
+                            } else {
                                 fin[i] = f[upwind(nx, ny, nz, s, i, z, y, x)];
+                            }
                         }
                         or_collide(fin, tau, project, fout);
                         for (int i = 0; i < NV; ++i) work[pidx(nx, ny, nz, s, i, z, y, x)] = fout[i];
                     }
         memcpy(f, work, sizeof(double) * (size_t)(2 * NV * nx * ny * nz));
     }
+    free(e);
+    free(emitted);
+    free(absorbed);
+    free(rho_w);
 }
 
 /* Populations set to the equilibrium of the given fields (rho[s][z][y][x],
