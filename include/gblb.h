@@ -173,6 +173,8 @@ lb_status lb_set_populations(lb_ctx *ctx, const double *f, int on_device);
  * bf16 h_i, with h_i = f_i/w_i - 1.  Restoring a saved state reproduces the
  * run bit for bit. */
 int64_t lb_state_bytes(const lb_ctx *ctx);
+/* The grid the context was created with (LB_ERR_ARG for a NULL argument). */
+lb_status lb_get_grid(const lb_ctx *ctx, lb_grid *grid);
 lb_status lb_get_state(lb_ctx *ctx, void *raw, int on_device);
 lb_status lb_set_state(lb_ctx *ctx, const void *raw, int on_device);
 
@@ -217,25 +219,29 @@ lb_status lb_tune(lb_ctx *ctx, int reps, int *kernel, double *ms_per_step);
  * keeps the other two directions periodic).  With enable != 0 the grid is no
  * longer periodic in z: a bottom wall lies a quarter cell below the lowest
  * node plane (A nodes of z = 0) and a top wall a quarter cell above the
- * highest (B nodes of z = nz - 1), so the channel is nz cells high.  Diffuse
- * reflection: every post-collision population that would stream through a
- * wall is absorbed by it, and every population whose upwind position lies
- * beyond a wall arrives as rho_w f^eq_i(1, u_w, theta_w), the model's
- * equilibrium at the wall's velocity and temperature, with rho_w the density
- * that returns the absorbed mass (one value per wall and step, balanced over
- * the whole wall plane: the local condition for flows uniform along the wall).
+ * highest (B nodes of z = nz - 1), so the channel is nz cells high.  Each wall
+ * is cut into the grid's cell columns (x, y).  Diffuse reflection, column by
+ * column: every post-collision population that would stream through a wall
+ * is absorbed by the column it lands in, and every population whose upwind
+ * position lies beyond a wall arrives as rho_w f^eq_i(1, u_w, theta_w), the
+ * model's equilibrium at the velocity and temperature of the column it comes
+ * from, with rho_w the density that returns that column's absorbed mass.
  * Mass is conserved; momentum and energy are exchanged with the walls.
- *   bottom, top  {u_x, u_y, u_z, theta} of each wall, host arrays read during
- *                the call; u_z must be 0, theta > 0
+ *   bottom, top  {u_x, u_y, u_z, theta} of every column of each wall, host
+ *                arrays read during the call; u_z must be 0, theta > 0
  * Requires nz >= 4 (LB_ERR_ARG otherwise).  enable = 0 restores the periodic
- * grid.  Each step then runs three small kernels besides the step kernel (the
- * wall sums and the two outermost cell layers at each wall).  Walls are not
- * part of lb_get_state; a batch (lb_batch_step) refuses members with walls
- * (LB_ERR_STATE). */
+ * grid.  Each step then runs two small kernels besides the step kernel (the
+ * columns' densities and the two outermost cell layers at each wall).  Walls
+ * are not part of lb_get_state; a batch (lb_batch_step) refuses members with
+ * walls (LB_ERR_STATE). */
 lb_status lb_set_walls(lb_ctx *ctx, int enable, const double bottom[4], const double top[4]);
-/* rho_w of the bottom and top wall in the last step (1, 1 before the first); LB_ERR_STATE
- * without walls.  Synchronises the context's stream. */
-lb_status lb_wall_density(lb_ctx *ctx, double rho_w[2]);
+/* Walls as lb_set_walls, with a velocity and temperature per cell column:
+ * bottom, top  host arrays [3][ny][nx]: u_x, u_y and theta of every column
+ *              (finite, theta > 0), read during the call. */
+lb_status lb_set_wall_columns(lb_ctx *ctx, const double *bottom, const double *top);
+/* rho_w of every column of the bottom then the top wall in the last step (1 before the
+ * first): host array [2][ny][nx].  LB_ERR_STATE without walls.  Synchronises the stream. */
+lb_status lb_wall_density(lb_ctx *ctx, double *rho_w);
 
 /* Number of time steps taken since the last lb_set_fields / lb_set_populations / lb_set_state. */
 int64_t lb_time(const lb_ctx *ctx);

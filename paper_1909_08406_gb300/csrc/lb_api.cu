@@ -4,7 +4,9 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
+#include <vector>
 
 #include "gblb.h"
 #include "lb_ctx.h"
@@ -224,7 +226,6 @@ lb_status lb_init(lb_ctx** out, lb_grid grid, int velocity_set, double theta0, d
     c->esize = storage_bytes(c->prec);
     c->cur = 0;
     c->time = 0;
-    c->wall_sums = 0;
     cudaError_t e = cudaGetDevice(&c->device);
     int sms = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
@@ -369,7 +370,6 @@ lb_status lb_set_fields(lb_ctx* c, const double* rho, const double* u, const dou
         CK(c, cudaStreamSynchronize(c->stream));
     }
     c->time = 0;
-    c->wall_sums = 0;
     return LB_OK;
 }
 
@@ -378,12 +378,9 @@ lb_status lb_step(lb_ctx* c, int64_t n) {
     CK(c, cudaSetDevice(c->device));
     const LaunchConsts& lc = lattice().lc;
     for (int64_t t = 0; t < n; ++t) {
-        if (c->walls) {
+        if (c->walls)
             CK(c, launch_wall_step(c->prec, c->eq, c->variant, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc,
-                                   c->twobeta, c->d_wall, c->d_wall_part, c->wall_sums != 0, c->d_err,
-                                   c->stream));
-            c->wall_sums = 1;
-        }
+                                   c->twobeta, c->d_wall, c->d_err, c->stream));
         else
             CK(c, launch_step(c->prec, c->eq, c->variant, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc,
                               c->twobeta, c->d_err, c->stream));
@@ -491,11 +488,16 @@ lb_status lb_set_populations(lb_ctx* c, const double* f, int on_device) {
         CK(c, cudaStreamSynchronize(c->stream));
     }
     c->time = 0;
-    c->wall_sums = 0;
     return LB_OK;
 }
 
 int64_t lb_state_bytes(const lb_ctx* c) { return c ? (int64_t)(2 * kQ) * c->d.plane * (int64_t)c->esize : -1; }
+
+lb_status lb_get_grid(const lb_ctx* c, lb_grid* grid) {
+    if (!c || !grid) return LB_ERR_ARG;
+    *grid = c->g;
+    return LB_OK;
+}
 
 lb_status lb_get_state(lb_ctx* c, void* raw, int on_device) {
     if (!c || !raw) return fail(c, LB_ERR_ARG, "lb_get_state: null argument");
@@ -513,7 +515,6 @@ lb_status lb_set_state(lb_ctx* c, const void* raw, int on_device) {
                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     if (!on_device) CK(c, cudaStreamSynchronize(c->stream));
     c->time = 0;
-    c->wall_sums = 0;
     return LB_OK;
 }
 
@@ -529,9 +530,41 @@ lb_status lb_destroy(lb_ctx* c) {
     cudaFree(c->d_partials);
     cudaFree(c->d_stage);
     cudaFree(c->d_wall);
-    cudaFree(c->d_wall_part);
     delete c;
     return LB_OK;
+}
+
+// Upload per-column wall parameters ([2][3][ncol] doubles, host) and derive the walls.
+static lb_status set_wall_columns(lb_ctx* c, const double* params) {
+    const int64_t ncol = (int64_t)c->d.nx * c->d.ny;
+    CK(c, cudaSetDevice(c->device));
+    if (!c->d_wall) {
+        cudaError_t e = cudaMalloc(&c->d_wall, wall_block_bytes(ncol, c->prec));
+        if (e != cudaSuccess) {
+            c->d_wall = nullptr;
+            return fail(c, e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA,
+                        std::string("lb_set_walls: ") + cudaGetErrorString(e));
+        }
+    }
+    CK(c, cudaMemcpyAsync(wall_params(c->d_wall), params, sizeof(double) * 6 * ncol, cudaMemcpyHostToDevice,
+                          c->stream));
+    CK(c, launch_wall_setup(c->prec, c->eq, c->d_wall, c->d, lattice().lc, c->stream));
+    int bad = 0;
+    CK(c, cudaMemcpyAsync(&bad, wall_bad_flag(c->d_wall, ncol, c->prec), sizeof bad, cudaMemcpyDeviceToHost,
+                          c->stream));
+    lb_status s = lb_sync(c);
+    if (s != LB_OK) return s;
+    if (bad) return fail(c, LB_ERR_ARG, "lb_set_walls: no equilibrium at a wall column's velocity and temperature");
+    c->walls = 1;
+    return LB_OK;
+}
+
+static bool wall_checks(lb_ctx* c) {
+    if (c->d.nz < 4) {
+        fail(c, LB_ERR_ARG, "lb_set_walls: walls need nz >= 4");
+        return false;
+    }
+    return true;
 }
 
 lb_status lb_set_walls(lb_ctx* c, int enable, const double bottom[4], const double top[4]) {
@@ -541,41 +574,45 @@ lb_status lb_set_walls(lb_ctx* c, int enable, const double bottom[4], const doub
         return LB_OK;
     }
     if (!bottom || !top) return fail(c, LB_ERR_ARG, "lb_set_walls: null wall");
-    if (c->d.nz < 4) return fail(c, LB_ERR_ARG, "lb_set_walls: walls need nz >= 4");
+    if (!wall_checks(c)) return LB_ERR_ARG;
     if (bottom[2] != 0.0 || top[2] != 0.0) return fail(c, LB_ERR_ARG, "lb_set_walls: a wall cannot move along z");
     for (const double* w : {bottom, top})
         if (!(w[3] > 0.0) || !isfinite(w[0]) || !isfinite(w[1]) || !isfinite(w[3]))
             return fail(c, LB_ERR_ARG, "lb_set_walls: wall velocity must be finite and theta > 0");
-    CK(c, cudaSetDevice(c->device));
-    if (!c->d_wall) {
-        cudaError_t e = cudaMalloc(&c->d_wall, wall_block_bytes());
-        if (e == cudaSuccess) e = cudaMalloc(&c->d_wall_part, sizeof(double) * wall_part_doubles(c->d));
-        if (e != cudaSuccess) {
-            cudaFree(c->d_wall);
-            c->d_wall = nullptr;
-            c->d_wall_part = nullptr;
-            return fail(c, e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA,
-                        std::string("lb_set_walls: ") + cudaGetErrorString(e));
-        }
+    const int64_t ncol = (int64_t)c->d.nx * c->d.ny;
+    std::vector<double> p((size_t)(6 * ncol));
+    for (int side = 0; side < 2; ++side) {
+        const double* w = side ? top : bottom;
+        for (int k = 0; k < 3; ++k)
+            std::fill(p.begin() + (side * 3 + k) * ncol, p.begin() + (side * 3 + k + 1) * ncol, w[k == 2 ? 3 : k]);
     }
-    c->wall_sums = 0;
-    const double w[8] = {bottom[0], bottom[1], bottom[2], bottom[3], top[0], top[1], top[2], top[3]};
-    CK(c, launch_wall_setup(c->eq, c->d_wall, c->d, lattice().lc, w, c->stream));
-    double rho[2];
-    CK(c, cudaMemcpyAsync(rho, c->d_wall + wall_rho_offset(), sizeof rho, cudaMemcpyDeviceToHost, c->stream));
-    lb_status s = lb_sync(c);
-    if (s != LB_OK) return s;
-    if (!(rho[0] == 1.0 && rho[1] == 1.0))
-        return fail(c, LB_ERR_ARG, "lb_set_walls: no equilibrium at a wall's velocity and temperature");
-    c->walls = 1;
-    return LB_OK;
+    return set_wall_columns(c, p.data());
 }
 
-lb_status lb_wall_density(lb_ctx* c, double rho_w[2]) {
+lb_status lb_set_wall_columns(lb_ctx* c, const double* bottom, const double* top) {
+    if (!c) return LB_ERR_ARG;
+    if (!bottom || !top) return fail(c, LB_ERR_ARG, "lb_set_wall_columns: null wall");
+    if (!wall_checks(c)) return LB_ERR_ARG;
+    const int64_t ncol = (int64_t)c->d.nx * c->d.ny;
+    std::vector<double> p((size_t)(6 * ncol));
+    for (int side = 0; side < 2; ++side) {
+        const double* w = side ? top : bottom;
+        for (int64_t k = 0; k < 3 * ncol; ++k) {
+            const double v = w[k];
+            if (!isfinite(v) || (k >= 2 * ncol && !(v > 0.0)))
+                return fail(c, LB_ERR_ARG, "lb_set_wall_columns: wall velocity must be finite and theta > 0");
+            p[(size_t)(side * 3 * ncol + k)] = v;
+        }
+    }
+    return set_wall_columns(c, p.data());
+}
+
+lb_status lb_wall_density(lb_ctx* c, double* rho_w) {
     if (!c || !rho_w) return LB_ERR_ARG;
     if (!c->walls) return fail(c, LB_ERR_STATE, "lb_wall_density: no walls set");
     CK(c, cudaSetDevice(c->device));
-    CK(c, cudaMemcpyAsync(rho_w, c->d_wall + wall_rho_offset(), 2 * sizeof(double), cudaMemcpyDeviceToHost,
+    const int64_t ncol = (int64_t)c->d.nx * c->d.ny;
+    CK(c, cudaMemcpyAsync(rho_w, wall_rho(c->d_wall, ncol), sizeof(double) * 2 * ncol, cudaMemcpyDeviceToHost,
                           c->stream));
     return lb_sync(c);
 }

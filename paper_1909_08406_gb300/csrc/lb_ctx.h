@@ -29,10 +29,8 @@ struct lb_ctx {
     double* d_stage;
     int64_t stage_doubles;
     int64_t time;
-    int walls = 0;            // kinetic walls normal to z (lb_set_walls) instead of the periodic wrap
-    double* d_wall = nullptr;  // the walls' device block (lb_walls.cu)
-    double* d_wall_part = nullptr;  // absorbed-mass partials (lb_walls.cu)
-    int wall_sums = 0;          // d_wall_part holds the partials of the current state
+    int walls = 0;           // kinetic walls normal to z (lb_set_walls) instead of the periodic wrap
+    void* d_wall = nullptr;  // the walls' device block (lb_walls.cu)
     std::string msg;
 };
 

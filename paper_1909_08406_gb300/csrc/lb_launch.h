@@ -74,19 +74,19 @@ cudaError_t launch_step_f32(int prec, bool project, int variant, const void* src
 cudaError_t launch_step_entropic(int prec, const void* src, void* dst, const Dims& d, const LaunchConsts& c,
                                  double twobeta, int* err, cudaStream_t st);
 
-// Kinetic walls normal to z (lb_walls.cu).  wall[8] = {u_x, u_y, u_z, theta} of the bottom
-// wall, then of the top wall; blk is a device block of wall_block_bytes().
-size_t wall_block_bytes();
-int wall_rho_offset();  // index of rho_w (2 doubles) in the block
-cudaError_t launch_wall_setup(int eq, double* blk, const Dims& d, const LaunchConsts& c, const double wall[8],
-                              cudaStream_t st);
-// Doubles of the absorbed-mass partials buffer for this grid.
-size_t wall_part_doubles(const Dims& d);
-// One step with the walls: rho_w (from the partials the last wall step left, or from src when
-// sums_valid is false), the periodic step, then the wall layers, which leave the next partials.
+// Kinetic walls normal to z (lb_walls.cu), one device block per context of
+// wall_block_bytes(nx * ny, prec): per-column parameters (wall_params: [2][3][ny][nx] doubles,
+// u_x, u_y, theta of the bottom then the top wall's cell columns), the columns' rho_w of the
+// last step (wall_rho: [2][ny][nx] doubles) and the derived data of lb_walls.cu.
+size_t wall_block_bytes(int64_t ncol, int prec);
+double* wall_params(void* blk);
+double* wall_rho(void* blk, int64_t ncol);
+int* wall_bad_flag(void* blk, int64_t ncol, int prec);
+// Derive the columns' equilibria from the parameters (sets the bad flag if one has none).
+cudaError_t launch_wall_setup(int prec, int eq, void* blk, const Dims& d, const LaunchConsts& c, cudaStream_t st);
+// One step with the walls: the columns' rho_w from src, the periodic step, then the wall layers.
 cudaError_t launch_wall_step(int prec, int eq, int variant, const void* src, void* dst, const Dims& d,
-                             const LaunchConsts& c, double twobeta, double* blk, double* part, bool sums_valid,
-                             int* err, cudaStream_t st);
+                             const LaunchConsts& c, double twobeta, void* blk, int* err, cudaStream_t st);
 
 inline dim3 step_grid(const Dims& d, int threads) {
     return dim3((unsigned)d.rows, (unsigned)((d.nx + threads - 1) / threads), 1);

@@ -5,26 +5,25 @@
 // Placement: in doubled coordinates the nodes occupy z2 = 2z + s in [0, 2 nz);
 // the bottom wall lies at z2 = -1/2 and the top wall at z2 = 2 nz - 1/2, a
 // quarter cell beyond the outermost node planes (channel height nz cells).
-// Diffuse reflection: a post-collision population whose destination lies
-// beyond a wall is absorbed by it; a population whose upwind position lies
-// beyond a wall is emitted by it as rho_w f^eq_i(1, u_w, theta_w), the model's
-// own equilibrium (linear in rho) at the wall's velocity and temperature, with
-// rho_w the density that returns the absorbed mass (one value per wall and
-// step, the balance taken over the whole wall plane).
+// Each wall is cut into the cell columns (x, y) of the grid: the bottom wall's
+// column x holds the doubled lateral positions {2x, 2x + 1}, the top wall's
+// {2x - 1, 2x} (the walls face the A and the B outermost plane, and the
+// half-cell-shifted mirror that exchanges the walls carries one partition onto
+// the other).  Diffuse reflection, column by column: a post-collision
+// population whose destination lies beyond a wall is absorbed by the column
+// that contains the destination; a population whose upwind position lies
+// beyond a wall is emitted by the column that contains that position, as
+// rho_w f^eq_i(1, u_w, theta_w), the model's own equilibrium (linear in rho)
+// at the column's velocity and temperature, with rho_w the density that
+// returns the column's absorbed mass.
 //
 // Per step, around the ordinary periodic step kernel (src -> dst):
-//   k_wall_density  rho_w per wall from the absorbed-mass partials, and the
-//                   2 x 41 emitted working values
+//   k_wall_columns  absorbed mass and rho_w of every wall column, gathered
+//                   from src in a fixed order
 //   <periodic step> every node; nodes next to a wall pull wrapped values here
 //   k_step_walls    recomputes the nodes of the 2 outermost cell layers at
 //                   each wall (the only ones with upwind positions beyond a
-//                   wall: links reach 2 cells), src -> dst, overwriting them,
-//                   and sums, per block, the mass that the next step's walls
-//                   absorb from what it stores (those layers are the only
-//                   ones with populations leaving through a wall).
-// After the state is set from outside (fields, populations, a checkpoint,
-// new walls), k_wall_absorb forms the same partials from the stored state once.
-// Every sum is taken in a fixed order, so a step is deterministic.
+//                   wall: links reach 2 cells), src -> dst, overwriting them.
 #include <math.h>
 
 #include "lb_ctx.h"
@@ -32,170 +31,158 @@
 
 namespace gblb {
 
-constexpr int kDensityThreads = 512;
+// floor(v / 2) for the small integers of the column arithmetic (v >= -8)
+__host__ __device__ __forceinline__ int half_floor(int v) { return (v + 8) / 2 - 4; }
 
-// Device block of one context's walls (doubles unless noted):
-//   e[2][kQ]        f^eq_i(1, u_w, theta_w) of the bottom and top wall
-//   emit[2]         sum over the (node, i) pairs a unit-density wall feeds
-//   wsum[2]         sum of w_i over the (node, i) pairs a wall absorbs: the rest-state part of
-//                   the absorbed mass, which the deviation codecs do not sum per node
-//   rho[2]          rho_w of the last step
-//   vd[2][kQ]       emitted working values (FP64 codec)
-//   vf[2][kQ]       emitted working values as float (FP32 arithmetic codecs)
-struct WallLayout {
-    static constexpr int e = 0;
-    static constexpr int emit = e + 2 * kQ;
-    static constexpr int wsum = emit + 2;
-    static constexpr int rho = wsum + 2;
-    static constexpr int vd = rho + 2;
-    static constexpr int vf = vd + 2 * kQ;  // float[2 * kQ] from here
-    static constexpr int doubles = vf + kQ;  // 2 * kQ floats fit in kQ doubles
+// Node planes (doubled z) next to a wall from beyond which population i arrives (in) or
+// through which it leaves (out): |2 c_iz| of them when c_iz points the right way, else 0.
+__host__ __device__ __forceinline__ int planes_in(int cz, int side) { return side ? (cz < 0 ? -cz : 0) : (cz > 0 ? cz : 0); }
+__host__ __device__ __forceinline__ int planes_out(int cz, int side) { return side ? (cz > 0 ? cz : 0) : (cz < 0 ? -cz : 0); }
+
+// The walls' device data (one allocation; R is the compute type of the storage codec):
+//   param[2][3][ncol]  u_x, u_y, theta of every column (double)
+//   emit[2][ncol]      sum_i planes_in_i e_i of the column: what it emits at unit density
+//   rho[2][ncol]       rho_w of every column in the last step (double)
+//   wsum[2]            sum_i planes_out_i w_i: the rest-state part of a column's absorbed mass,
+//                      which the deviation codecs do not sum per population
+//   e[2][kQ][ncol]     e_i = f^eq_i(1, u_w, theta_w) (FP64 codec) or e_i / w_i - 1 (deviation
+//                      codecs), in R
+//   dr[2][ncol]        rho_w (FP64 codec) or rho_w - 1 (deviation codecs), in R
+//   bad                set by the set-up if a column has no equilibrium
+struct WallPtrs {
+    double *param, *emit, *rho, *wsum;
+    void *e, *dr;
+    int* bad;
 };
 
-// f^eq_i(1, u_w, theta_w) of both walls and the unit emission sums, in FP64.
-// wall[8] = {u_x, u_y, u_z, theta} of the bottom wall, then of the top wall.
-template <int EQ>
-__global__ void k_wall_setup(double* __restrict__ blk, Dims d, Consts<double> K, double theta0, double wx0,
-                             double wy0, double wz0, double t0, double w1x, double w1y, double w1z, double t1) {
-    if (threadIdx.x >= 2) return;
-    const int side = threadIdx.x;
+static size_t round16(size_t b) { return (b + 15) / 16 * 16; }
+
+static WallPtrs wall_ptrs(void* blk, int64_t ncol, size_t rsize) {
+    char* p = static_cast<char*>(blk);
+    WallPtrs w;
+    w.param = reinterpret_cast<double*>(p);
+    w.emit = w.param + 6 * ncol;
+    w.rho = w.emit + 2 * ncol;
+    w.wsum = w.rho + 2 * ncol;
+    size_t off = sizeof(double) * (size_t)(10 * ncol + 2);
+    off = round16(off);
+    w.e = p + off;
+    off += round16((size_t)(2 * kQ * ncol) * rsize);
+    w.dr = p + off;
+    off += round16((size_t)(2 * ncol) * rsize);
+    w.bad = reinterpret_cast<int*>(p + off);
+    return w;
+}
+
+static size_t rsize_of(int prec) { return prec == kF64 ? 8 : 4; }
+
+size_t wall_block_bytes(int64_t ncol, int prec) {
+    const size_t rs = rsize_of(prec);
+    return round16(sizeof(double) * (size_t)(10 * ncol + 2)) + round16((size_t)(2 * kQ * ncol) * rs) +
+           round16((size_t)(2 * ncol) * rs) + 16;
+}
+
+double* wall_params(void* blk) { return static_cast<double*>(blk); }
+double* wall_rho(void* blk, int64_t ncol) { return static_cast<double*>(blk) + 8 * ncol; }
+int* wall_bad_flag(void* blk, int64_t ncol, int prec) { return wall_ptrs(blk, ncol, rsize_of(prec)).bad; }
+
+// Per column: f^eq(1, u_w, theta_w) in FP64, its unit emission, and the codec's copy of it.
+template <class Codec, int EQ>
+__global__ void k_wall_setup(WallPtrs w, Dims d, Consts<double> K, double theta0) {
+    using R = typename Codec::R;
+    const int64_t ncol = (int64_t)d.nx * d.ny;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 2 * ncol) return;
+    const int side = (int)(k / ncol);
+    const int64_t col = k - side * ncol;
+    const double* pr = w.param + side * 3 * ncol;
     NodeState<double> st;
     st.drho = 0.0;
     st.rho = 1.0;
-    st.ux = side ? w1x : wx0;
-    st.uy = side ? w1y : wy0;
-    st.uz = side ? w1z : wz0;
-    st.eta = (side ? t1 : t0) / theta0 - 1.0;
-    double zero[kQ];
+    st.ux = pr[col];
+    st.uy = pr[ncol + col];
+    st.uz = 0.0;
+    st.eta = pr[2 * ncol + col] / theta0 - 1.0;
+    double zero[kQ], e[kQ];
 #pragma unroll
     for (int i = 0; i < kQ; ++i) zero[i] = 0.0;
-    double* e = blk + WallLayout::e + side * kQ;
-    bool ok = true;
+    bool ok = state_ok(st);
     equilibrium_relax<CodecF64, EQ>(st, K, 1.0, 0.0, zero, [&](auto I, double val) { e[I] = val; }, ok);
-    // a unit-density wall feeds population i (c_iz > 0 for the bottom, < 0 for the top) into
-    // the node planes z2 with z2 - 2 c_iz beyond it: |2 c_iz| planes of nx * ny nodes
-    // and absorbs population i (c_iz < 0 at the bottom, > 0 at the top) from |2 c_iz| planes
-    double sum = 0.0, wsum = 0.0;
+    double emit = 0.0;
+    R* ec = static_cast<R*>(w.e) + (int64_t)side * kQ * ncol + col;
+#pragma unroll
     for (int i = 0; i < kQ; ++i) {
-        const int cz = c_vel.v[i].z;
-        const int planes = side ? (cz < 0 ? -cz : 0) : (cz > 0 ? cz : 0);
-        const int out_planes = side ? (cz > 0 ? cz : 0) : (cz < 0 ? -cz : 0);
-        sum += (double)planes * e[i];
-        wsum += (double)out_planes * K.w[c_vel.v[i].shell];
+        emit += (double)planes_in(c_vel.v[i].z, side) * e[i];
+        const double wi = K.w[c_vel.v[i].shell];
+        ec[(int64_t)i * ncol] = (R)(Codec::stores_f ? e[i] : e[i] / wi - 1.0);
+        ok = ok && isfinite(e[i]) && e[i] > 0.0;
     }
-    blk[WallLayout::emit + side] = sum * (double)d.nx * (double)d.ny;
-    blk[WallLayout::wsum + side] = wsum * (double)d.nx * (double)d.ny;
-    blk[WallLayout::rho + side] = ok ? 1.0 : nan("");
+    w.emit[k] = emit;
+    w.rho[k] = 1.0;
+    static_cast<R*>(w.dr)[k] = (R)(Codec::stores_f ? 1.0 : 0.0);
+    if (col == 0) {
+        double ws = 0.0;
+        for (int i = 0; i < kQ; ++i) ws += (double)planes_out(c_vel.v[i].z, side) * K.w[c_vel.v[i].shell];
+        w.wsum[side] = ws;
+    }
+    if (!ok) atomicOr(w.bad, 1);
 }
 
-// Block sum in a fixed order (warp trees, then the warps' sums in order); every thread of
-// the block must call it.  The result is valid in thread 0.
-__device__ __forceinline__ double block_sum_fixed(double v) {
-    __shared__ double warp_sums[32];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) warp_sums[wid] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x == 0)
-        for (int k = 0; k < (int)(blockDim.x + 31) / 32; ++k) t += warp_sums[k];
-    return t;
-}
-
-// Absorbed mass of the stored state, in the partial layout and summation order of
-// k_step_walls (one partial per block of its grid, each node's populations in index order,
-// block_sum_fixed), so that a state set from outside gives the same wall densities as the
-// same state reached by stepping.
-// A stored value's share of the absorbed mass: f itself for the FP64 codec; for the deviation
-// codecs w h (the rest-state part w is added once per wall, from wsum), in the compute type.
+// Absorbed mass and rho_w of every wall column.  Column (cx, cy) of a wall absorbs population
+// i from the node planes z2 it leaves through the wall, from the source cell whose destination
+// falls in the column: x = cx - floor((s + 2 c_ix + side) / 2), likewise y.  The sum runs in a
+// fixed order (population, then plane), so a step is deterministic and a state set from outside
+// gives the same densities as the same state reached by stepping.
 template <class Codec>
-__device__ __forceinline__ typename Codec::R absorbed_part(typename Codec::R v, typename Codec::R w) {
+__global__ void __launch_bounds__(128) k_wall_columns(const typename Codec::raw_t* __restrict__ src, Dims d,
+                                                      Consts<typename Codec::R> K, WallPtrs w) {
     using R = typename Codec::R;
-    if constexpr (Codec::stores_f)
-        return v;
-    else
-        return w * (v * R(1.0 / Codec::kScale));
-}
-
-template <class Codec>
-__global__ void __launch_bounds__(kStepThreads) k_wall_absorb(const typename Codec::raw_t* __restrict__ src, Dims d,
-                                                              Consts<typename Codec::R> K,
-                                                              double* __restrict__ part) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    double acc = 0.0;
-    if (x < d.nx) {
-        const int row = blockIdx.y;  // (layer * 2 + s) * ny + y
-        const int y = row % d.ny;
-        const int ls = row / d.ny;
-        const int layer = ls >> 1, s = ls & 1;
-        const int z = layer < 2 ? layer : d.nz - 4 + layer;
-        const int z2 = 2 * z + s, nz2 = 2 * d.nz;
-        const bool bottom = layer < 2;
-        const typename Codec::raw_t* p =
-            src + ((int64_t)s * kQ * d.plane + ((int64_t)z * d.ny + y) * d.nx + x);
-        typename Codec::R a = 0;
-        static_for<kQ>([&](auto I) {
-            constexpr Vel c = vel(I);
-            if constexpr (c.z != 0) {
-                const int dest = z2 + c.z;
-                if (bottom ? dest < 0 : dest >= nz2)
-                    a += absorbed_part<Codec>(Codec::value(p[(int64_t)I * d.plane]), K.w[c.shell]);
+    const int64_t ncol = (int64_t)d.nx * d.ny;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= 2 * ncol) return;
+    const int side = (int)(k / ncol);
+    const int64_t col = k - side * ncol;
+    const int cy = (int)(col / d.nx), cx = (int)(col - (int64_t)cy * d.nx);
+    const int nz2 = 2 * d.nz;
+    R acc = 0;
+    static_for<kQ>([&](auto I) {
+        constexpr Vel c = vel(I);
+        if constexpr (c.z != 0) {
+            const int np = planes_out(c.z, side);
+            for (int j = 0; j < np; ++j) {
+                const int z2 = side ? nz2 - np + j : j;
+                const int s = z2 & 1, z = z2 >> 1;
+                int x = cx - half_floor(s + c.x + side), y = cy - half_floor(s + c.y + side);
+                x = x < 0 ? x + d.nx : (x >= d.nx ? x - d.nx : x);
+                y = y < 0 ? y + d.ny : (y >= d.ny ? y - d.ny : y);
+                const R v =
+                    Codec::value(src[((int64_t)s * kQ + I) * d.plane + ((int64_t)z * d.ny + y) * d.nx + x]);
+                if constexpr (Codec::stores_f)
+                    acc += v;
+                else
+                    acc += K.w[c.shell] * (v * R(1.0 / Codec::kScale));
             }
-        });
-        acc = (double)a;
-    }
-    const double t = block_sum_fixed(acc);
-    if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = t;
-}
-
-// part[side * nper + k], k < nper: the absorbed-mass partials of each wall.
-template <class Codec>
-__global__ void __launch_bounds__(kDensityThreads) k_wall_density(double* __restrict__ blk, Consts<double> K,
-                                                                  const double* __restrict__ part, int nper) {
-    __shared__ double red[2][kDensityThreads];
-    __shared__ double rho[2];
-    for (int side = 0; side < 2; ++side) {
-        double a = 0.0;
-        for (int k = threadIdx.x; k < nper; k += kDensityThreads) a += part[side * nper + k];
-        red[side][threadIdx.x] = a;
-    }
-    __syncthreads();
-    for (int h = kDensityThreads / 2; h > 0; h >>= 1) {
-        if ((int)threadIdx.x < h) {
-            red[0][threadIdx.x] += red[0][threadIdx.x + h];
-            red[1][threadIdx.x] += red[1][threadIdx.x + h];
         }
-        __syncthreads();
-    }
-    if (threadIdx.x < 2) {
-        const double absorbed = red[threadIdx.x][0] + (Codec::stores_f ? 0.0 : blk[WallLayout::wsum + threadIdx.x]);
-        rho[threadIdx.x] = absorbed / blk[WallLayout::emit + threadIdx.x];
-        blk[WallLayout::rho + threadIdx.x] = rho[threadIdx.x];
-    }
-    __syncthreads();
-    float* vf = reinterpret_cast<float*>(blk + WallLayout::vf);
-    for (int k = threadIdx.x; k < 2 * kQ; k += blockDim.x) {
-        const int side = k / kQ, i = k - side * kQ;
-        const double e = blk[WallLayout::e + k];
-        const double w = K.w[c_vel.v[i].shell];
-        const double r = rho[side];
-        // deviation of rho_w e_i from the rest weight: (r - 1) + r (e / w - 1)
-        const double v = Codec::stores_f ? r * e : ((r - 1.0) + r * (e / w - 1.0)) * Codec::kScale;
-        blk[WallLayout::vd + k] = v;
-        vf[k] = (float)v;
-    }
+    });
+    const double absorbed = (double)acc + (Codec::stores_f ? 0.0 : w.wsum[side]);
+    const double rho = absorbed / w.emit[k];
+    w.rho[k] = rho;
+    static_cast<R*>(w.dr)[k] = (R)(Codec::stores_f ? rho : rho - 1.0);
 }
 
-
-// One node of k_step_walls; returns the mass its stored values send through the wall.
+// The update of the nodes in the two outermost cell layers at each wall: the gather of
+// step_node with every upwind position beyond a wall replaced by the emission of the wall
+// column that contains it.  Grid: x = x chunks, y = (layer 0..3, s, y) rows; layers 0, 1 at the
+// bottom, 2, 3 at the top.
 template <class Codec, int EQ>
-__device__ __forceinline__ double wall_node(const typename Codec::raw_t* __restrict__ src,
-                                            typename Codec::raw_t* __restrict__ dst, const Dims& d,
-                                            const Consts<typename Codec::R>& K, typename Codec::R tb,
-                                            const typename Codec::R* __restrict__ vwall, int* __restrict__ err,
-                                            int x) {
+__global__ void __launch_bounds__(kStepThreads) k_step_walls(const typename Codec::raw_t* __restrict__ src,
+                                                             typename Codec::raw_t* __restrict__ dst, Dims d,
+                                                             Consts<typename Codec::R> K, typename Codec::R tb,
+                                                             WallPtrs w, int* __restrict__ err) {
     using R = typename Codec::R;
     using T = typename Codec::raw_t;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= d.nx) return;
     const int row = blockIdx.y;  // (layer * 2 + s) * ny + y
     const int y = row % d.ny;
     const int ls = row / d.ny;
@@ -217,15 +204,26 @@ __device__ __forceinline__ double wall_node(const typename Codec::raw_t* __restr
     const int64_t hzp = s ? zo[2] : zo[3], hzm = s ? zo[1] : zo[2];
     const T* same = src + (int64_t)s * kQ * d.plane;
     const T* other = src + (int64_t)(1 - s) * kQ * d.plane;
+    const R* we = static_cast<const R*>(w.e);
+    const R* wdr = static_cast<const R*>(w.dr);
 
     R v[kQ];
     static_for<kQ>([&](auto I) {
         constexpr Vel c = vel(I);
         const int up = z2 - c.z;  // doubled z of the upwind position
-        if (up < 0) {
-            v[I] = vwall[I];
-        } else if (up >= nz2) {
-            v[I] = vwall[kQ + I];
+        if (up < 0 || up >= nz2) {
+            const int side = up < 0 ? 0 : 1;
+            // the wall column containing the upwind position's (x, y)
+            int cx = x + half_floor(s - c.x + side), cy = y + half_floor(s - c.y + side);
+            cx = cx < 0 ? cx + d.nx : (cx >= d.nx ? cx - d.nx : cx);
+            cy = cy < 0 ? cy + d.ny : (cy >= d.ny ? cy - d.ny : cy);
+            const int64_t col = (int64_t)cy * d.nx + cx;
+            const R e = we[((int64_t)side * kQ + I) * nxy + col];
+            const R r = wdr[side * nxy + col];
+            if constexpr (Codec::stores_f)
+                v[I] = r * e;
+            else  // (rho_w e_i / w_i - 1) scaled: dr + he + dr he
+                v[I] = (r + e + r * e) * R(Codec::kScale);
         } else if constexpr (c.shell == 5) {
             const int64_t off = (c.z > 0 ? hzp : hzm) + (c.y > 0 ? hyp : hym) + (c.x > 0 ? hxp : hxm);
             v[I] = Codec::value(other[(int64_t)I * d.plane + off]);
@@ -241,40 +239,9 @@ __device__ __forceinline__ double wall_node(const typename Codec::raw_t* __restr
     const NodeState<R> st = state_from_moments(moments_from_dev(dv), K);
     bool ok = state_ok(st);
     T* out = dst + (int64_t)s * kQ * d.plane + (int64_t)z * nxy + (int64_t)y * d.nx + x;
-    R absorbed = 0;
-    const bool bottom = layer < 2;
     equilibrium_relax<Codec, EQ>(st, K, tb * R(Codec::kScale), R(1) - tb, v,
-                                 [&](auto I, R val) {
-                                     const T raw = Codec::to_raw(val);
-                                     out[(int64_t)I * d.plane] = raw;
-                                     constexpr Vel c = vel(I);
-                                     if constexpr (c.z != 0) {
-                                         const int dest = z2 + c.z;
-                                         if (bottom ? dest < 0 : dest >= nz2)
-                                             absorbed += absorbed_part<Codec>(Codec::value(raw), K.w[c.shell]);
-                                     }
-                                 },
-                                 ok);
+                                 [&](auto I, R val) { out[(int64_t)I * d.plane] = Codec::to_raw(val); }, ok);
     if (!ok) atomicOr(err, 1);
-    return (double)absorbed;
-}
-
-// The update of the nodes in the two outermost cell layers at each wall: the gather of
-// step_node with every upwind position beyond a wall replaced by that wall's emission.
-// Grid: x = x chunks, y = (layer 0..3, s, y) rows; layers 0, 1 at the bottom, 2, 3 at the top.
-// part[blockIdx.y * gridDim.x + blockIdx.x] receives the mass that the stored values will
-// send through the block's wall in the next step (bottom partials first, then top).
-template <class Codec, int EQ>
-__global__ void __launch_bounds__(kStepThreads) k_step_walls(const typename Codec::raw_t* __restrict__ src,
-                                                             typename Codec::raw_t* __restrict__ dst, Dims d,
-                                                             Consts<typename Codec::R> K, typename Codec::R tb,
-                                                             const typename Codec::R* __restrict__ vwall,
-                                                             double* __restrict__ part, int* __restrict__ err) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    double absorbed = 0.0;
-    if (x < d.nx) absorbed = wall_node<Codec, EQ>(src, dst, d, K, tb, vwall, err, x);
-    const double t = block_sum_fixed(absorbed);
-    if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = t;
 }
 
 template <class F>
@@ -298,40 +265,37 @@ static cudaError_t with_eq(int eq, F&& f) {
     }
 }
 
-cudaError_t launch_wall_setup(int eq, double* blk, const Dims& d, const LaunchConsts& c, const double wall[8],
-                              cudaStream_t st) {
-    return with_eq(eq, [&](auto E) {
-        k_wall_setup<decltype(E)::value><<<1, 32, 0, st>>>(blk, d, c.kd, c.theta0, wall[0], wall[1], wall[2], wall[3],
-                                                           wall[4], wall[5], wall[6], wall[7]);
-        return cudaGetLastError();
+template <class C>
+static const Consts<typename C::R>& consts_for(const LaunchConsts& c) {
+    if constexpr (sizeof(typename C::R) == 8)
+        return c.kd;
+    else
+        return c.kf;
+}
+
+cudaError_t launch_wall_setup(int prec, int eq, void* blk, const Dims& d, const LaunchConsts& c, cudaStream_t st) {
+    const int64_t ncol = (int64_t)d.nx * d.ny;
+    return with_codec(prec, [&](auto codec) {
+        using C = decltype(codec);
+        const WallPtrs w = wall_ptrs(blk, ncol, sizeof(typename C::R));
+        cudaError_t e = cudaMemsetAsync(w.bad, 0, sizeof(int), st);
+        if (e != cudaSuccess) return e;
+        return with_eq(eq, [&](auto E) {
+            k_wall_setup<C, decltype(E)::value><<<(unsigned)((2 * ncol + 127) / 128), 128, 0, st>>>(w, d, c.kd,
+                                                                                                  c.theta0);
+            return cudaGetLastError();
+        });
     });
 }
 
-// Blocks of k_step_walls along x for this grid (and the step kernels' row width).
-static int wall_chunks(const Dims& d) {
-    const int th = step_threads(d);
-    return (d.nx + th - 1) / th;
-}
-
-size_t wall_part_doubles(const Dims& d) { return (size_t)8 * d.ny * wall_chunks(d); }
-
 cudaError_t launch_wall_step(int prec, int eq, int variant, const void* src, void* dst, const Dims& d,
-                             const LaunchConsts& c, double twobeta, double* blk, double* part, bool sums_valid,
-                             int* err, cudaStream_t st) {
-    const int chunks = wall_chunks(d);
+                             const LaunchConsts& c, double twobeta, void* blk, int* err, cudaStream_t st) {
+    const int64_t ncol = (int64_t)d.nx * d.ny;
     cudaError_t e = with_codec(prec, [&](auto codec) {
         using C = decltype(codec);
-        using R = typename C::R;
-        const int nper = 4 * d.ny * chunks;  // partials per wall (k_step_walls' blocks)
-        const Consts<R>* K;
-        if constexpr (sizeof(R) == 8)
-            K = &c.kd;
-        else
-            K = &c.kf;
-        if (!sums_valid)
-            k_wall_absorb<C><<<dim3((unsigned)chunks, (unsigned)(8 * d.ny)), step_threads(d), 0, st>>>(
-                static_cast<const typename C::raw_t*>(src), d, *K, part);
-        k_wall_density<C><<<1, kDensityThreads, 0, st>>>(blk, c.kd, part, nper);
+        const WallPtrs w = wall_ptrs(blk, ncol, sizeof(typename C::R));
+        k_wall_columns<C><<<(unsigned)((2 * ncol + 127) / 128), 128, 0, st>>>(
+            static_cast<const typename C::raw_t*>(src), d, consts_for<C>(c), w);
         return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;
@@ -340,28 +304,16 @@ cudaError_t launch_wall_step(int prec, int eq, int variant, const void* src, voi
     return with_codec(prec, [&](auto codec) {
         using C = decltype(codec);
         using R = typename C::R;
+        const WallPtrs w = wall_ptrs(blk, ncol, sizeof(R));
         const int th = step_threads(d);
-        const dim3 grid((unsigned)chunks, (unsigned)(8 * d.ny));
-        const R* vw;
-        if constexpr (sizeof(R) == 8)
-            vw = reinterpret_cast<const R*>(blk + WallLayout::vd);
-        else
-            vw = reinterpret_cast<const R*>(blk + WallLayout::vf);
-        const Consts<R>* K;
-        if constexpr (sizeof(R) == 8)
-            K = &c.kd;
-        else
-            K = &c.kf;
+        const dim3 grid((unsigned)((d.nx + th - 1) / th), (unsigned)(8 * d.ny));
         return with_eq(eq, [&](auto E) {
             k_step_walls<C, decltype(E)::value><<<grid, th, 0, st>>>(
-                static_cast<const typename C::raw_t*>(src), static_cast<typename C::raw_t*>(dst), d, *K,
-                (R)twobeta, vw, part, err);
+                static_cast<const typename C::raw_t*>(src), static_cast<typename C::raw_t*>(dst), d,
+                consts_for<C>(c), (R)twobeta, w, err);
             return cudaGetLastError();
         });
     });
 }
-
-size_t wall_block_bytes() { return sizeof(double) * WallLayout::doubles; }
-int wall_rho_offset() { return WallLayout::rho; }
 
 }  // namespace gblb

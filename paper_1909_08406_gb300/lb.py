@@ -83,6 +83,10 @@ def lib():
         L.lb_set_walls.restype = ctypes.c_int
         L.lb_wall_density.argtypes = [vp, vp]
         L.lb_wall_density.restype = ctypes.c_int
+        L.lb_set_wall_columns.argtypes = [vp, vp, vp]
+        L.lb_set_wall_columns.restype = ctypes.c_int
+        L.lb_get_grid.argtypes = [vp, ctypes.POINTER(_Grid)]
+        L.lb_get_grid.restype = ctypes.c_int
         L.lb_sync.argtypes = [vp]
         L.lb_destroy.argtypes = [vp]
         L.lb_last_error.argtypes = [vp]
@@ -228,22 +232,37 @@ def lb_tune(ctx, reps=3):
     return k.value, ms.value
 
 
+def lb_grid_of(ctx):
+    """(nx, ny, nz) of a context."""
+    g = _Grid()
+    _check(lib().lb_get_grid(ctx, ctypes.byref(g)), ctx)
+    return g.nx, g.ny, g.nz
+
+
 def lb_set_walls(ctx, bottom=None, top=None):
-    """Kinetic walls normal to z: bottom, top = (u_x, u_y, theta) of each wall; None for both
+    """Kinetic walls normal to z: bottom, top = (u_x, u_y, theta) of each wall, each entry a
+    number (the same for every cell column) or an array [ny][nx] (per column); None for both
     restores the periodic grid."""
     if bottom is None and top is None:
         _check(lib().lb_set_walls(ctx, 0, None, None), ctx)
         return
-    b = (ctypes.c_double * 4)(float(bottom[0]), float(bottom[1]), 0.0, float(bottom[2]))
-    t = (ctypes.c_double * 4)(float(top[0]), float(top[1]), 0.0, float(top[2]))
-    _check(lib().lb_set_walls(ctx, 1, ctypes.cast(b, ctypes.c_void_p), ctypes.cast(t, ctypes.c_void_p)), ctx)
+    if all(np.ndim(v) == 0 for v in tuple(bottom) + tuple(top)):
+        b = (ctypes.c_double * 4)(float(bottom[0]), float(bottom[1]), 0.0, float(bottom[2]))
+        t = (ctypes.c_double * 4)(float(top[0]), float(top[1]), 0.0, float(top[2]))
+        _check(lib().lb_set_walls(ctx, 1, ctypes.cast(b, ctypes.c_void_p), ctypes.cast(t, ctypes.c_void_p)), ctx)
+        return
+    nx, ny, _ = lb_grid_of(ctx)
+    arrs = [np.ascontiguousarray(np.stack([np.broadcast_to(np.asarray(v, dtype=np.float64), (ny, nx))
+                                           for v in w])) for w in (bottom, top)]
+    _check(lib().lb_set_wall_columns(ctx, arrs[0].ctypes.data, arrs[1].ctypes.data), ctx)
 
 
 def lb_wall_density(ctx):
-    """(rho_w bottom, rho_w top) of the last step."""
-    out = (ctypes.c_double * 2)()
-    _check(lib().lb_wall_density(ctx, ctypes.cast(out, ctypes.c_void_p)), ctx)
-    return out[0], out[1]
+    """rho_w of every cell column of the bottom and the top wall in the last step, [2][ny][nx]."""
+    nx, ny, _ = lb_grid_of(ctx)
+    out = np.empty((2, ny, nx))
+    _check(lib().lb_wall_density(ctx, out.ctypes.data), ctx)
+    return out
 
 
 def lb_time(ctx):
