@@ -99,3 +99,12 @@ def test_batch_rejects_members_of_2_31_nodes(L):
     assert "2^31" in str(e.value)
     assert L.lb_batch_get_rows(None) == -1
     assert L.lb_batch_get_plan(None, 0, None, None, None) == -1
+
+
+def test_wall_and_grid_entry_points_reject_null(L):
+    from paper_1909_08406_gb300 import lb
+    lb.lib()
+    assert L.lb_set_walls(None, 1, None, None) == -1
+    assert L.lb_set_wall_columns(None, None, None) == -1
+    assert L.lb_wall_density(None, None) == -1
+    assert L.lb_get_grid(None, None) == -1
