@@ -345,3 +345,44 @@ def test_wall_with_varying_temperature_gives_laplace_field_on_gpu(prec):
             exact = a * np.cos(k * X) * np.sinh(k * (H - Y)) / np.sinh(k * H)
             err = max(err, np.abs(th[s, z] / TH0 - 1 - exact[None, :]).max())
     assert err / a <= 0.10, err / a
+
+
+def _cavity_gpu(L, prec, nu=0.1, dT=0.01):
+    """The cavity heated at the top, L = H, side walls by images (see the oracle's test); the
+    largest deviation from the paper's series over the paper's sections, in units of dT."""
+    from oracle.conduction import cavity_series
+    H, nx, ny = L, 2 * L, 2
+    top = TH0 * (1 + dT * np.sign(np.sin(np.pi * (np.arange(nx) - 0.25) / L)))[None, :].repeat(ny, 0)
+    n = 2 * nx * ny * H
+    ctx = lb.lb_init((nx, ny, H), nu / TH0, prec)
+    try:
+        lb.lb_set_fields(ctx, torch.ones(n, dtype=torch.float64, device="cuda"),
+                         torch.zeros(3 * n, dtype=torch.float64, device="cuda"),
+                         torch.full((n,), TH0, dtype=torch.float64, device="cuda"))
+        lb.lb_set_walls(ctx, (0.0, 0.0, TH0), (0.0, 0.0, top))
+        lb.lb_step(ctx, int(4 * H * H / (5.0 / 3.0 * nu)))
+        th = torch.empty((2, H, ny, nx), dtype=torch.float64, device="cuda")
+        lb.lb_get_moments(ctx, None, None, th)
+        lb.lb_sync(ctx)
+    finally:
+        lb.lb_destroy(ctx)
+    T = th[:, :, 0, :].cpu().numpy() / TH0 - 1
+    X = np.array([[np.arange(nx) + 0.5 * s - 0.25 for _ in range(H)] for s in (0, 1)])
+    Y = np.array([[np.full(nx, z + 0.5 * s + 0.25) for z in range(H)] for s in (0, 1)])
+    err = np.abs(T - dT * cavity_series(X, Y, L, H)) / dT
+    xl, yh = X / L, Y / H
+    worst = 0.0
+    for x0 in (0.1, 0.2, 0.5):
+        worst = max(worst, err[(np.abs(xl - x0) <= 0.5 / L + 1e-9) & (yh <= 0.8)].max())
+    for y0 in (0.25, 0.5, 0.75):
+        worst = max(worst, err[(np.abs(yh - y0) <= 0.5 / H + 1e-9) & (xl > 0.05) & (xl < 0.95)].max())
+    return worst
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_cavity_heated_at_the_top_converges_to_the_series(prec):
+    """L = H = 16 as the oracle's test (0.043 dT there), and 32: the kinetic wall's temperature
+    jump shrinks at first order in 1/L."""
+    e16, e32 = _cavity_gpu(16, prec), _cavity_gpu(32, prec)
+    assert e16 <= 0.045 and e32 <= 0.025, (e16, e32)
+    assert e16 / e32 >= 1.7, (e16, e32)
