@@ -472,6 +472,49 @@ void or_step_nodes(int64_t nx, int64_t ny, int64_t nz, double tau, int project, 
 }
 
 /* ------------------------------------------------------------------ */
+/* Isothermal nonideal fluid: BGK with a force (Sec. "Nonideal Fluids")  */
+/* ------------------------------------------------------------------ */
+
+/* One collision with a force density per node, on the pre-collision
+ * (streamed) populations fpre, Eq. (multiphaseEvolution) with alpha = 2
+ * (BGK): rho = sum_i f_i, u = sum_i f_i c_i / rho + g / 2 (the velocity of
+ * the trapezoid-rule variables), f^eq = f^eq(rho, u, theta_0) (isothermal),
+ * F_i = g . (c_i - u) / theta_0 f^eq_i, and
+ *   f_i' = f_i + 2 beta (f^eq_i - f_i) + (1 - beta) F_i.
+ * g[d][node] is the acceleration g^nid of each node (same layout as a
+ * vector field).  fpost receives the post-collision populations. */
+void or_collide_forced(int64_t nx, int64_t ny, int64_t nz, double tau, int project, const double *fpre,
+                       const double *g, double *fpost, int nthreads) {
+    init_lattice();
+    set_threads(nthreads);
+    const int64_t nn = 2 * nx * ny * nz;
+    const double b2 = 2.0 * beta_of_tau(tau);
+#pragma omp parallel for schedule(static)
+    for (int64_t q = 0; q < nn; ++q) {
+        int64_t x = q % nx, r = q / nx;
+        int64_t y = r % ny;
+        r /= ny;
+        int64_t z = r % nz;
+        int s = (int)(r / nz);
+        double fin[NV], feq[NV], rho = 0.0, j[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < NV; ++i) {
+            fin[i] = fpre[pidx(nx, ny, nz, s, i, z, y, x)];
+            rho += fin[i];
+            for (int d = 0; d < 3; ++d) j[d] += fin[i] * CV[i][d];
+        }
+        double gq[3] = {g[q], g[nn + q], g[2 * nn + q]}, u[3];
+        for (int d = 0; d < 3; ++d) u[d] = j[d] / rho + 0.5 * gq[d];
+        equilibrium_of_kind(rho, u, THETA0, project, feq);
+        for (int i = 0; i < NV; ++i) {
+            double gc = 0.0;
+            for (int d = 0; d < 3; ++d) gc += gq[d] * (CV[i][d] - u[d]);
+            const double F = gc / THETA0 * feq[i];
+            fpost[pidx(nx, ny, nz, s, i, z, y, x)] = fin[i] + b2 * (feq[i] - fin[i]) + (1.0 - 0.5 * b2) * F;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ */
 /* Kinetic (diffuse) walls normal to z                                 */
 /* ------------------------------------------------------------------ */
 
