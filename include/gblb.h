@@ -243,6 +243,26 @@ lb_status lb_set_wall_columns(lb_ctx *ctx, const double *bottom, const double *t
  * first): host array [2][ny][nx].  LB_ERR_STATE without walls.  Synchronises the stream. */
 lb_status lb_wall_density(lb_ctx *ctx, double *rho_w);
 
+/* Isothermal nonideal fluid (Sec. "Nonideal Fluids and two-phase flow"): with
+ * enable != 0 each step adds the force of the paper's momentum-conserving
+ * formulation, Eq. (gradientFinal), for the van der Waals equation of state
+ * p = rho theta0 / (1 - b rho) - a rho^2 at the lattice temperature theta0,
+ *   rho g = -[rho d2 mu + mu d2 rho - eta d2 F - (1 - eta) d4 F + kappa d2_b I_ab]
+ * (mu, F: the nonideal chemical potential and free energy; I_ab: the
+ * interfacial stress; d2, d4: the second- and fourth-order gradients of the
+ * 15-velocity bcc stencil of Appendix A), and collides with the forcing of
+ * Eq. (multiphaseEvolution), alpha = 2, at the equilibrium f^eq(rho, u,
+ * theta0) (isothermal: the temperature moment is not kept).  u is then
+ * sum f c / rho + g / 2 (lb_get_moments reports sum f c / rho).
+ *   a >= 0, b > 0   van der Waals constants (theta_c = 8a / (27b), rho_c = 1 / (3b))
+ *   kappa >= 0      interfacial stiffness; eta in [0, 1]: weight of the second-order
+ *                   gradient of F (the paper uses 1/2)
+ * Needs the projected series equilibrium (no LB_FLAG_PAPER_LITERAL or
+ * LB_FLAG_ENTROPIC; LB_ERR_ARG) and no walls (LB_ERR_STATE).  Each step runs
+ * four one-node-per-thread kernels; the work buffer is 88 bytes per node.
+ * enable = 0 restores the energy-conserving update. */
+lb_status lb_set_nonideal(lb_ctx *ctx, int enable, double a, double b, double kappa, double eta);
+
 /* Number of time steps taken since the last lb_set_fields / lb_set_populations / lb_set_state. */
 int64_t lb_time(const lb_ctx *ctx);
 

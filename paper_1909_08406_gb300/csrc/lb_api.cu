@@ -378,7 +378,10 @@ lb_status lb_step(lb_ctx* c, int64_t n) {
     CK(c, cudaSetDevice(c->device));
     const LaunchConsts& lc = lattice().lc;
     for (int64_t t = 0; t < n; ++t) {
-        if (c->walls)
+        if (c->nonideal)
+            CK(c, launch_nonideal_step(c->prec, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc, c->twobeta, c->ni_eos,
+                                       c->d_ni, c->d_err, c->stream));
+        else if (c->walls)
             CK(c, launch_wall_step(c->prec, c->eq, c->variant, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc,
                                    c->twobeta, c->d_wall, c->d_err, c->stream));
         else
@@ -530,6 +533,7 @@ lb_status lb_destroy(lb_ctx* c) {
     cudaFree(c->d_partials);
     cudaFree(c->d_stage);
     cudaFree(c->d_wall);
+    cudaFree(c->d_ni);
     delete c;
     return LB_OK;
 }
@@ -574,6 +578,7 @@ lb_status lb_set_walls(lb_ctx* c, int enable, const double bottom[4], const doub
         return LB_OK;
     }
     if (!bottom || !top) return fail(c, LB_ERR_ARG, "lb_set_walls: null wall");
+    if (c->nonideal) return fail(c, LB_ERR_STATE, "lb_set_walls: not combined with the nonideal mode");
     if (!wall_checks(c)) return LB_ERR_ARG;
     if (bottom[2] != 0.0 || top[2] != 0.0) return fail(c, LB_ERR_ARG, "lb_set_walls: a wall cannot move along z");
     for (const double* w : {bottom, top})
@@ -605,6 +610,35 @@ lb_status lb_set_wall_columns(lb_ctx* c, const double* bottom, const double* top
         }
     }
     return set_wall_columns(c, p.data());
+}
+
+lb_status lb_set_nonideal(lb_ctx* c, int enable, double a, double b, double kappa, double eta) {
+    if (!c) return LB_ERR_ARG;
+    if (!enable) {
+        c->nonideal = 0;
+        return LB_OK;
+    }
+    if (!(a >= 0.0) || !(b > 0.0) || !(kappa >= 0.0) || !(eta >= 0.0 && eta <= 1.0) || !isfinite(a) ||
+        !isfinite(b) || !isfinite(kappa))
+        return fail(c, LB_ERR_ARG, "lb_set_nonideal: need a >= 0, b > 0, kappa >= 0, 0 <= eta <= 1");
+    if (c->eq != 1)
+        return fail(c, LB_ERR_ARG, "lb_set_nonideal: the nonideal mode uses the projected series equilibrium");
+    if (c->walls) return fail(c, LB_ERR_STATE, "lb_set_nonideal: not combined with walls");
+    CK(c, cudaSetDevice(c->device));
+    if (!c->d_ni) {
+        cudaError_t e = cudaMalloc(&c->d_ni, sizeof(double) * nonideal_doubles(c->d));
+        if (e != cudaSuccess) {
+            c->d_ni = nullptr;
+            return fail(c, e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA,
+                        std::string("lb_set_nonideal: ") + cudaGetErrorString(e));
+        }
+    }
+    c->ni_eos[0] = a;
+    c->ni_eos[1] = b;
+    c->ni_eos[2] = kappa;
+    c->ni_eos[3] = eta;
+    c->nonideal = 1;
+    return LB_OK;
 }
 
 lb_status lb_wall_density(lb_ctx* c, double* rho_w) {

@@ -1,0 +1,297 @@
+// Isothermal nonideal (van der Waals) fluid (Sec. "Nonideal Fluids and
+// two-phase flow"; derivative stencil of Appendix A).
+//
+// Per step, from the post-collision state src:
+//   k_ni_density  rho of the streamed populations, sum_i f_i(x - c_i)
+//   k_ni_fields   per node: mu_nid, F_nid, grad2 rho (3), lap rho, lap F_nid
+//   k_ni_force    g^nid of Eq. (gradientFinal):
+//                   rho g = -[rho grad2 mu + mu grad2 rho - eta grad2 F
+//                             - (1 - eta) grad4 F + kappa grad2_b I_ab],
+//                   grad4 = grad2 - (theta_hat / 2) grad2 lap,
+//                   I_ab = [-(1/2)|grad rho|^2 - rho lap rho] delta_ab + grad_a rho grad_b rho
+//   k_ni_step     the pull step with the forced BGK collision of
+//                 Eq. (multiphaseEvolution), alpha = 2: u = j / rho + g / 2,
+//                 f^eq = f^eq(rho, u, theta_0), F_i = g.(c_i - u)/theta_0 f^eq_i,
+//                 f' = f + 2 beta (f^eq - f) + (1 - beta) F_i.
+// The stencil is the 15-velocity bcc set of Appendix A: rest, (+-1, 0, 0) and
+// permutations (on the node's own sub-lattice), (+-1/2, +-1/2, +-1/2) (on the
+// other); weights 14/36, 1/36, 2/36; theta_hat = 1/6.  Fields are FP64.
+#include <math.h>
+
+#include "lb_ctx.h"
+#include "lb_kernels.cuh"
+
+namespace gblb {
+
+struct NiEos {
+    double a, b, theta0, kappa, eta;
+};
+
+__device__ __forceinline__ double ni_F(double r, const NiEos& e) { return -r * e.theta0 * log(1.0 - e.b * r) - e.a * r * r; }
+__device__ __forceinline__ double ni_mu(double r, const NiEos& e) {
+    const double br = e.b * r;
+    return -e.theta0 * log(1.0 - br) + e.theta0 * br / (1.0 - br) - 2.0 * e.a * r;
+}
+
+constexpr double kHatTheta = 1.0 / 6.0;
+constexpr int kStencil = 14;  // moving stencil velocities (the rest one only enters lap)
+
+// Doubled velocity and weight of moving stencil velocity k: 6 sc-1 then 8 bcc-1/2.
+__device__ __forceinline__ void stencil(int k, int& cx, int& cy, int& cz, double& w) {
+    if (k < 6) {
+        cx = cy = cz = 0;
+        const int v = (k & 1) ? -2 : 2;
+        if (k < 2)
+            cx = v;
+        else if (k < 4)
+            cy = v;
+        else
+            cz = v;
+        w = 1.0 / 36.0;
+    } else {
+        const int j = k - 6;
+        cx = (j & 1) ? -1 : 1;
+        cy = (j & 2) ? -1 : 1;
+        cz = (j & 4) ? -1 : 1;
+        w = 2.0 / 36.0;
+    }
+}
+
+// Field index of the node at x + c for node (s, z, y, x), c doubled; periodic.
+__device__ __forceinline__ int64_t ni_neighbor(const Dims& d, int s, int z, int y, int x, int cx, int cy, int cz) {
+    const int t = (s + cx) & 1;
+    int xn = x + (s + cx - t) / 2, yn = y + (s + cy - t) / 2, zn = z + (s + cz - t) / 2;
+    xn = xn < 0 ? xn + d.nx : (xn >= d.nx ? xn - d.nx : xn);
+    yn = yn < 0 ? yn + d.ny : (yn >= d.ny ? yn - d.ny : yn);
+    zn = zn < 0 ? zn + d.nz : (zn >= d.nz ? zn - d.nz : zn);
+    return (((int64_t)t * d.nz + zn) * d.ny + yn) * d.nx + xn;
+}
+
+__device__ __forceinline__ bool ni_node(const Dims& d, int64_t q, int& s, int& z, int& y, int& x) {
+    if (q >= 2 * d.plane) return false;
+    x = (int)(q % d.nx);
+    int64_t r = q / d.nx;
+    y = (int)(r % d.ny);
+    r /= d.ny;
+    z = (int)(r % d.nz);
+    s = (int)(r / d.nz);
+    return true;
+}
+
+// The pull gather of step_node: v[i] = f_i(x - c_i) in the codec's working value.
+template <class Codec>
+__device__ __forceinline__ void ni_gather(const typename Codec::raw_t* __restrict__ src, const Dims& d, int s, int z,
+                                          int y, int x, typename Codec::R (&v)[kQ]) {
+    using T = typename Codec::raw_t;
+    const int64_t nxy = (int64_t)d.nx * d.ny;
+    int xs[5];
+    int64_t yo[5], zo[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        xs[k] = wrap(x - (k - 2), d.nx);
+        yo[k] = (int64_t)wrap(y - (k - 2), d.ny) * d.nx;
+        zo[k] = (int64_t)wrap(z - (k - 2), d.nz) * nxy;
+    }
+    const int hxp = s ? xs[2] : xs[3], hxm = s ? xs[1] : xs[2];
+    const int64_t hyp = s ? yo[2] : yo[3], hym = s ? yo[1] : yo[2];
+    const int64_t hzp = s ? zo[2] : zo[3], hzm = s ? zo[1] : zo[2];
+    const T* same = src + (int64_t)s * kQ * d.plane;
+    const T* other = src + (int64_t)(1 - s) * kQ * d.plane;
+    static_for<kQ>([&](auto I) {
+        constexpr Vel c = vel(I);
+        if constexpr (c.shell == 5) {
+            const int64_t off = (c.z > 0 ? hzp : hzm) + (c.y > 0 ? hyp : hym) + (c.x > 0 ? hxp : hxm);
+            v[I] = Codec::value(other[(int64_t)I * d.plane + off]);
+        } else {
+            const int64_t off = zo[c.z / 2 + 2] + yo[c.y / 2 + 2] + xs[c.x / 2 + 2];
+            v[I] = Codec::value(same[(int64_t)I * d.plane + off]);
+        }
+    });
+}
+
+template <class Codec>
+__global__ void __launch_bounds__(128) k_ni_density(const typename Codec::raw_t* __restrict__ src, Dims d,
+                                                    Consts<double> K, double* __restrict__ rho) {
+    using R = typename Codec::R;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int s, z, y, x;
+    if (!ni_node(d, q, s, z, y, x)) return;
+    R v[kQ];
+    ni_gather<Codec>(src, d, s, z, y, x, v);
+    double dr = 0.0;  // rho - 1 = sum_i (f_i - w_i)
+    static_for<kQ>([&](auto I) {
+        const double w = K.w[vel(I).shell];
+        dr += Codec::stores_f ? (double)v[I] - w : w * ((double)v[I] * (1.0 / Codec::kScale));
+    });
+    rho[q] = 1.0 + dr;
+}
+
+// A[k][node]: 0 mu, 1 F, 2..4 grad2 rho, 5 lap rho, 6 lap F.
+__global__ void __launch_bounds__(128) k_ni_fields(Dims d, NiEos e, const double* __restrict__ rho,
+                                                   double* __restrict__ A) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int s, z, y, x;
+    if (!ni_node(d, q, s, z, y, x)) return;
+    const int64_t n = 2 * d.plane;
+    const double r0 = rho[q], F0 = ni_F(r0, e);
+    double g[3] = {0.0, 0.0, 0.0}, lr = 14.0 / 36.0 * r0, lF = 14.0 / 36.0 * F0;
+    for (int k = 0; k < kStencil; ++k) {
+        int cx, cy, cz;
+        double w;
+        stencil(k, cx, cy, cz, w);
+        const double rn = rho[ni_neighbor(d, s, z, y, x, cx, cy, cz)];
+        g[0] += w * 0.5 * cx * rn;
+        g[1] += w * 0.5 * cy * rn;
+        g[2] += w * 0.5 * cz * rn;
+        lr += w * rn;
+        lF += w * ni_F(rn, e);
+    }
+    A[q] = ni_mu(r0, e);
+    A[n + q] = F0;
+    for (int a = 0; a < 3; ++a) A[(2 + a) * n + q] = g[a] / kHatTheta;
+    A[5 * n + q] = 2.0 / kHatTheta * (lr - r0);
+    A[6 * n + q] = 2.0 / kHatTheta * (lF - F0);
+}
+
+__global__ void __launch_bounds__(128) k_ni_force(Dims d, NiEos e, const double* __restrict__ rho,
+                                                  const double* __restrict__ A, double* __restrict__ g) {
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int s, z, y, x;
+    if (!ni_node(d, q, s, z, y, x)) return;
+    const int64_t n = 2 * d.plane;
+    double dmu[3] = {0, 0, 0}, dF[3] = {0, 0, 0}, dlF[3] = {0, 0, 0}, divI[3] = {0, 0, 0};
+    for (int k = 0; k < kStencil; ++k) {
+        int cx, cy, cz;
+        double w;
+        stencil(k, cx, cy, cz, w);
+        const int64_t m = ni_neighbor(d, s, z, y, x, cx, cy, cz);
+        const double c[3] = {0.5 * cx, 0.5 * cy, 0.5 * cz};
+        const double gr[3] = {A[2 * n + m], A[3 * n + m], A[4 * n + m]};
+        const double iso = -0.5 * (gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]) - rho[m] * A[5 * n + m];
+        for (int a = 0; a < 3; ++a) {
+            if (c[a] == 0.0) continue;
+            const double wc = w * c[a];
+            dmu[a] += wc * A[m];
+            dF[a] += wc * A[n + m];
+            dlF[a] += wc * A[6 * n + m];
+        }
+        // grad2_b I_ab: sum over the stencil of w c_b I_ab(x + c)
+        for (int a = 0; a < 3; ++a) {
+            double t = 0.0;
+            for (int b = 0; b < 3; ++b) {
+                if (c[b] == 0.0) continue;
+                const double I_ab = gr[a] * gr[b] + (a == b ? iso : 0.0);
+                t += w * c[b] * I_ab;
+            }
+            divI[a] += t;
+        }
+    }
+    const double r0 = rho[q], mu0 = A[q];
+    for (int a = 0; a < 3; ++a) {
+        const double g2mu = dmu[a] / kHatTheta, g2F = dF[a] / kHatTheta, g2lF = dlF[a] / kHatTheta;
+        const double g4F = g2F - 0.5 * kHatTheta * g2lF;
+        const double rg = -(r0 * g2mu + mu0 * A[(2 + a) * n + q] - e.eta * g2F - (1.0 - e.eta) * g4F +
+                            e.kappa * divI[a] / kHatTheta);
+        g[a * n + q] = rg / r0;
+    }
+}
+
+template <class Codec>
+__global__ void __launch_bounds__(128) k_ni_step(const typename Codec::raw_t* __restrict__ src,
+                                                 typename Codec::raw_t* __restrict__ dst, Dims d,
+                                                 Consts<typename Codec::R> K, typename Codec::R tb,
+                                                 typename Codec::R inv_theta0, const double* __restrict__ g,
+                                                 int* __restrict__ err) {
+    using R = typename Codec::R;
+    using T = typename Codec::raw_t;
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int s, z, y, x;
+    if (!ni_node(d, q, s, z, y, x)) return;
+    const int64_t n = 2 * d.plane;
+    R v[kQ];
+    ni_gather<Codec>(src, d, s, z, y, x, v);
+    R dv[kQ];
+    constexpr R inv_scale = R(1.0 / Codec::kScale);
+    static_for<kQ>([&](auto I) { dv[I] = Codec::dev(v[I], K.w[vel(I).shell] * inv_scale); });
+    const NodeMoments<R> m = moments_from_dev(dv);
+    NodeState<R> st;
+    st.drho = m.drho;
+    st.rho = R(1) + m.drho;
+    const R gx = (R)g[q], gy = (R)g[n + q], gz = (R)g[2 * n + q];
+    const R inv_rho = R(1) / st.rho;
+    st.ux = m.jx * inv_rho + R(0.5) * gx;
+    st.uy = m.jy * inv_rho + R(0.5) * gy;
+    st.uz = m.jz * inv_rho + R(0.5) * gz;
+    st.eta = R(0);  // isothermal: the equilibrium at theta_0
+    bool ok = state_ok(st);
+    // f^eq in the working representation: f (FP64 codec) or scale * h^eq (deviation codecs)
+    R veq[kQ], zero[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) zero[i] = R(0);
+    equilibrium_relax<Codec, 1>(st, K, R(Codec::kScale), R(0), zero, [&](auto I, R val) { veq[I] = val; }, ok);
+    T* out = dst + (int64_t)s * kQ * d.plane + ((int64_t)z * d.ny + y) * d.nx + x;
+    const R half_f = R(1) - R(0.5) * tb;  // 1 - beta
+    static_for<kQ>([&](auto I) {
+        constexpr Vel c = vel(I);
+        const R gc = gx * (R(0.5 * c.x) - st.ux) + gy * (R(0.5 * c.y) - st.uy) + gz * (R(0.5 * c.z) - st.uz);
+        R val;
+        if constexpr (Codec::stores_f) {
+            const R F = gc * inv_theta0 * veq[I];
+            val = v[I] + tb * (veq[I] - v[I]) + half_f * F;
+        } else {
+            // F_i / w_i = gc / theta0 (1 + h^eq), in units of the stored scale
+            const R F = gc * inv_theta0 * (R(Codec::kScale) + veq[I]);
+            val = v[I] + tb * (veq[I] - v[I]) + half_f * F;
+        }
+        out[(int64_t)I * d.plane] = Codec::to_raw(val);
+    });
+    if (!ok) atomicOr(err, 1);
+}
+
+template <class F>
+static cudaError_t ni_codec(int prec, F&& f) {
+    switch (prec) {
+        case kF64: return f(CodecF64{});
+        case kF32: return f(CodecF32{});
+        case kF16: return f(CodecF16{});
+        case kBF16: return f(CodecBF16{});
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t nonideal_doubles(const Dims& d) { return (size_t)11 * 2 * d.plane; }
+
+cudaError_t launch_nonideal_step(int prec, const void* src, void* dst, const Dims& d, const LaunchConsts& c,
+                                 double twobeta, const double eos[4], double* work, int* err, cudaStream_t st) {
+    const int64_t n = 2 * d.plane;
+    const unsigned blocks = (unsigned)((n + 127) / 128);
+    const NiEos e{eos[0], eos[1], c.theta0, eos[2], eos[3]};
+    double* rho = work;
+    double* A = work + n;
+    double* g = work + 8 * n;
+    cudaError_t r = ni_codec(prec, [&](auto codec) {
+        using C = decltype(codec);
+        k_ni_density<C><<<blocks, 128, 0, st>>>(static_cast<const typename C::raw_t*>(src), d, c.kd, rho);
+        return cudaGetLastError();
+    });
+    if (r != cudaSuccess) return r;
+    k_ni_fields<<<blocks, 128, 0, st>>>(d, e, rho, A);
+    k_ni_force<<<blocks, 128, 0, st>>>(d, e, rho, A, g);
+    r = cudaGetLastError();
+    if (r != cudaSuccess) return r;
+    return ni_codec(prec, [&](auto codec) {
+        using C = decltype(codec);
+        using R = typename C::R;
+        const Consts<R>* K;
+        if constexpr (sizeof(R) == 8)
+            K = &c.kd;
+        else
+            K = &c.kf;
+        k_ni_step<C><<<blocks, 128, 0, st>>>(static_cast<const typename C::raw_t*>(src),
+                                             static_cast<typename C::raw_t*>(dst), d, *K, (R)twobeta,
+                                             (R)(1.0 / c.theta0), g, err);
+        return cudaGetLastError();
+    });
+}
+
+}  // namespace gblb

@@ -87,6 +87,8 @@ def lib():
         L.lb_set_wall_columns.restype = ctypes.c_int
         L.lb_get_grid.argtypes = [vp, ctypes.POINTER(_Grid)]
         L.lb_get_grid.restype = ctypes.c_int
+        L.lb_set_nonideal.argtypes = [vp, ctypes.c_int, dp, dp, dp, dp]
+        L.lb_set_nonideal.restype = ctypes.c_int
         L.lb_sync.argtypes = [vp]
         L.lb_destroy.argtypes = [vp]
         L.lb_last_error.argtypes = [vp]
@@ -230,6 +232,15 @@ def lb_tune(ctx, reps=3):
     k, ms = ctypes.c_int(), ctypes.c_double()
     _check(lib().lb_tune(ctx, int(reps), ctypes.byref(k), ctypes.byref(ms)), ctx)
     return k.value, ms.value
+
+
+def lb_set_nonideal(ctx, a=None, b=None, kappa=0.0, eta=0.5):
+    """Isothermal van der Waals fluid with the paper's momentum-conserving force; a = None
+    restores the energy-conserving update."""
+    if a is None:
+        _check(lib().lb_set_nonideal(ctx, 0, 0.0, 0.0, 0.0, 0.0), ctx)
+        return
+    _check(lib().lb_set_nonideal(ctx, 1, float(a), float(b), float(kappa), float(eta)), ctx)
 
 
 def lb_grid_of(ctx):
