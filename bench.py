@@ -50,6 +50,7 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-batch", action="store_true", help="skip the batched 64-simulation sweep")
     p.add_argument("--no-walls", action="store_true", help="skip the run with kinetic walls normal to z")
+    p.add_argument("--no-nonideal", action="store_true", help="skip the run of the nonideal (van der Waals) fluid")
     p.add_argument("--no-accuracy", action="store_true",
                    help="skip the error of the reduced-precision runs against the GPU FP64 mode")
     p.add_argument("--batch-steps", type=int, default=1000)
@@ -347,12 +348,15 @@ def main():
     by_kernel = {}
     clocks = None
 
-    def timed_run(prec, kernel, steps, warm, sample_clocks, walls=False):
+    def timed_run(prec, kernel, steps, warm, sample_clocks, walls=False, nonideal=False):
         ctx = lb.lb_init((n, n, n), tau, prec)
         try:
             lb.lb_set_fields(ctx, fields["rho"], fields["u"], fields["theta"])
             if walls:  # a Couette channel: still wall below, moving wall above, 2e-4 theta0 apart
                 lb.lb_set_walls(ctx, (0.0, 0.0, th0 * (1 - 1e-4)), (0.02, 0.0, th0 * (1 + 1e-4)))
+            if nonideal:  # van der Waals at theta0 / theta_c = 1.1 (one phase), rho_c = 1
+                theta_c = th0 / 1.1
+                lb.lb_set_nonideal(ctx, 27.0 / 3.0 * theta_c / 8.0, 1.0 / 3.0, 0.05, 0.5)
             if kernel is None:
                 lb.lb_tune(ctx, reps=3)
             else:
@@ -410,6 +414,14 @@ def main():
                  "vs_periodic": r["mlups"] / results[head]["mlups"],
                  "note": "kinetic walls normal to z (Couette channel), same grid, precision and step kernel; "
                          "adds the wall sums and the update of the 2 outermost cell layers at each wall"}
+    nonideal = None
+    if not args.no_nonideal:
+        r, _ = timed_run(head, best, max(5, args.steps // 10), 3, False, nonideal=True)
+        nonideal = {"mlups": r["mlups"], "ms_per_step": r["ms_per_step"], "steps": r["steps"],
+                    "vs_energy_conserving": r["mlups"] / results[head]["mlups"],
+                    "note": "isothermal van der Waals fluid (theta/theta_c = 1.1, kappa 0.05) on the same fields, "
+                            "grid and storage: density, stencil fields and force kernels (FP64) and the forced step, "
+                            "one node per thread"}
     if not args.no_secondary:
         for prec in precs[1:]:
             steps = max(3, args.steps // 10) if prec == "f64" else max(5, args.steps // 2)
@@ -485,6 +497,7 @@ def main():
         "by_kernel": by_kernel,
         "accuracy": accuracy,
         "walls": walls,
+        "nonideal": nonideal,
         "batch": batch,
         "gpu_launches": r["steps"],
         "clocks": clocks,

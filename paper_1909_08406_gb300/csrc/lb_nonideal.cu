@@ -2,8 +2,9 @@
 // two-phase flow"; derivative stencil of Appendix A).
 //
 // Per step, from the post-collision state src:
-//   k_ni_density  rho of the streamed populations, sum_i f_i(x - c_i)
-//   k_ni_fields   per node: mu_nid, F_nid, grad2 rho (3), lap rho, lap F_nid
+//   k_ni_density  rho of the streamed populations, sum_i f_i(x - c_i), and
+//                 mu_nid(rho), F_nid(rho) of each node
+//   k_ni_fields   per node: grad2 rho (3), lap rho, lap F_nid
 //   k_ni_force    g^nid of Eq. (gradientFinal):
 //                   rho g = -[rho grad2 mu + mu grad2 rho - eta grad2 F
 //                             - (1 - eta) grad4 F + kappa grad2_b I_ab],
@@ -111,7 +112,8 @@ __device__ __forceinline__ void ni_gather(const typename Codec::raw_t* __restric
 
 template <class Codec>
 __global__ void __launch_bounds__(128) k_ni_density(const typename Codec::raw_t* __restrict__ src, Dims d,
-                                                    Consts<double> K, double* __restrict__ rho) {
+                                                    Consts<double> K, NiEos e, double* __restrict__ rho,
+                                                    double* __restrict__ A) {
     using R = typename Codec::R;
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int s, z, y, x;
@@ -123,31 +125,32 @@ __global__ void __launch_bounds__(128) k_ni_density(const typename Codec::raw_t*
         const double w = K.w[vel(I).shell];
         dr += Codec::stores_f ? (double)v[I] - w : w * ((double)v[I] * (1.0 / Codec::kScale));
     });
-    rho[q] = 1.0 + dr;
+    const double r = 1.0 + dr;
+    rho[q] = r;
+    A[q] = ni_mu(r, e);
+    A[2 * d.plane + q] = ni_F(r, e);
 }
 
-// A[k][node]: 0 mu, 1 F, 2..4 grad2 rho, 5 lap rho, 6 lap F.
-__global__ void __launch_bounds__(128) k_ni_fields(Dims d, NiEos e, const double* __restrict__ rho,
-                                                   double* __restrict__ A) {
+// A[k][node]: 0 mu, 1 F (both from k_ni_density), 2..4 grad2 rho, 5 lap rho, 6 lap F.
+__global__ void __launch_bounds__(128) k_ni_fields(Dims d, const double* __restrict__ rho, double* __restrict__ A) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int s, z, y, x;
     if (!ni_node(d, q, s, z, y, x)) return;
     const int64_t n = 2 * d.plane;
-    const double r0 = rho[q], F0 = ni_F(r0, e);
+    const double r0 = rho[q], F0 = A[n + q];
     double g[3] = {0.0, 0.0, 0.0}, lr = 14.0 / 36.0 * r0, lF = 14.0 / 36.0 * F0;
     for (int k = 0; k < kStencil; ++k) {
         int cx, cy, cz;
         double w;
         stencil(k, cx, cy, cz, w);
-        const double rn = rho[ni_neighbor(d, s, z, y, x, cx, cy, cz)];
+        const int64_t m = ni_neighbor(d, s, z, y, x, cx, cy, cz);
+        const double rn = rho[m];
         g[0] += w * 0.5 * cx * rn;
         g[1] += w * 0.5 * cy * rn;
         g[2] += w * 0.5 * cz * rn;
         lr += w * rn;
-        lF += w * ni_F(rn, e);
+        lF += w * A[n + m];
     }
-    A[q] = ni_mu(r0, e);
-    A[n + q] = F0;
     for (int a = 0; a < 3; ++a) A[(2 + a) * n + q] = g[a] / kHatTheta;
     A[5 * n + q] = 2.0 / kHatTheta * (lr - r0);
     A[6 * n + q] = 2.0 / kHatTheta * (lF - F0);
@@ -271,11 +274,11 @@ cudaError_t launch_nonideal_step(int prec, const void* src, void* dst, const Dim
     double* g = work + 8 * n;
     cudaError_t r = ni_codec(prec, [&](auto codec) {
         using C = decltype(codec);
-        k_ni_density<C><<<blocks, 128, 0, st>>>(static_cast<const typename C::raw_t*>(src), d, c.kd, rho);
+        k_ni_density<C><<<blocks, 128, 0, st>>>(static_cast<const typename C::raw_t*>(src), d, c.kd, e, rho, A);
         return cudaGetLastError();
     });
     if (r != cudaSuccess) return r;
-    k_ni_fields<<<blocks, 128, 0, st>>>(d, e, rho, A);
+    k_ni_fields<<<blocks, 128, 0, st>>>(d, rho, A);
     k_ni_force<<<blocks, 128, 0, st>>>(d, e, rho, A, g);
     r = cudaGetLastError();
     if (r != cudaSuccess) return r;
