@@ -420,8 +420,8 @@ def main():
         nonideal = {"mlups": r["mlups"], "ms_per_step": r["ms_per_step"], "steps": r["steps"],
                     "vs_energy_conserving": r["mlups"] / results[head]["mlups"],
                     "note": "isothermal van der Waals fluid (theta/theta_c = 1.1, kappa 0.05) on the same fields, "
-                            "grid and storage: density, stencil fields and force kernels (FP64) and the forced step, "
-                            "one node per thread"}
+                            "grid and storage: density, stencil-field and force kernels in the storage's compute type "
+                            "and the forced step, one node per thread"}
     if not args.no_secondary:
         for prec in precs[1:]:
             steps = max(3, args.steps // 10) if prec == "f64" else max(5, args.steps // 2)

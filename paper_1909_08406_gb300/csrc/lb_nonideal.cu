@@ -16,7 +16,8 @@
 //                 f' = f + 2 beta (f^eq - f) + (1 - beta) F_i.
 // The stencil is the 15-velocity bcc set of Appendix A: rest, (+-1, 0, 0) and
 // permutations (on the node's own sub-lattice), (+-1/2, +-1/2, +-1/2) (on the
-// other); weights 14/36, 1/36, 2/36; theta_hat = 1/6.  Fields are FP64.
+// other); weights 14/36, 1/36, 2/36; theta_hat = 1/6.  The fields are in
+// the storage codec's compute type: FP64 for FP64 storage, FP32 otherwise.
 #include <math.h>
 
 #include "lb_ctx.h"
@@ -28,17 +29,26 @@ struct NiEos {
     double a, b, theta0, kappa, eta;
 };
 
-__device__ __forceinline__ double ni_F(double r, const NiEos& e) { return -r * e.theta0 * log(1.0 - e.b * r) - e.a * r * r; }
-__device__ __forceinline__ double ni_mu(double r, const NiEos& e) {
-    const double br = e.b * r;
-    return -e.theta0 * log(1.0 - br) + e.theta0 * br / (1.0 - br) - 2.0 * e.a * r;
+__device__ __forceinline__ double ni_log(double v) { return log(v); }
+__device__ __forceinline__ float ni_log(float v) { return logf(v); }
+
+// F_nid and mu_nid of the van der Waals fluid, in the field type F
+template <class F>
+__device__ __forceinline__ F ni_F(F r, const NiEos& e) {
+    return -r * F(e.theta0) * ni_log(F(1) - F(e.b) * r) - F(e.a) * r * r;
+}
+template <class F>
+__device__ __forceinline__ F ni_mu(F r, const NiEos& e) {
+    const F br = F(e.b) * r;
+    return -F(e.theta0) * ni_log(F(1) - br) + F(e.theta0) * br / (F(1) - br) - F(2) * F(e.a) * r;
 }
 
 constexpr double kHatTheta = 1.0 / 6.0;
 constexpr int kStencil = 14;  // moving stencil velocities (the rest one only enters lap)
 
 // Doubled velocity and weight of moving stencil velocity k: 6 sc-1 then 8 bcc-1/2.
-__device__ __forceinline__ void stencil(int k, int& cx, int& cy, int& cz, double& w) {
+template <class F>
+__device__ __forceinline__ void stencil(int k, int& cx, int& cy, int& cz, F& w) {
     if (k < 6) {
         cx = cy = cz = 0;
         const int v = (k & 1) ? -2 : 2;
@@ -48,13 +58,13 @@ __device__ __forceinline__ void stencil(int k, int& cx, int& cy, int& cz, double
             cy = v;
         else
             cz = v;
-        w = 1.0 / 36.0;
+        w = F(1.0 / 36.0);
     } else {
         const int j = k - 6;
         cx = (j & 1) ? -1 : 1;
         cy = (j & 2) ? -1 : 1;
         cz = (j & 4) ? -1 : 1;
-        w = 2.0 / 36.0;
+        w = F(2.0 / 36.0);
     }
 }
 
@@ -112,89 +122,89 @@ __device__ __forceinline__ void ni_gather(const typename Codec::raw_t* __restric
 
 template <class Codec>
 __global__ void __launch_bounds__(128) k_ni_density(const typename Codec::raw_t* __restrict__ src, Dims d,
-                                                    Consts<double> K, NiEos e, double* __restrict__ rho,
-                                                    double* __restrict__ A) {
+                                                    Consts<typename Codec::R> K, NiEos e,
+                                                    typename Codec::R* __restrict__ rho,
+                                                    typename Codec::R* __restrict__ A) {
     using R = typename Codec::R;
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int s, z, y, x;
     if (!ni_node(d, q, s, z, y, x)) return;
     R v[kQ];
     ni_gather<Codec>(src, d, s, z, y, x, v);
-    double dr = 0.0;  // rho - 1 = sum_i (f_i - w_i)
-    static_for<kQ>([&](auto I) {
-        const double w = K.w[vel(I).shell];
-        dr += Codec::stores_f ? (double)v[I] - w : w * ((double)v[I] * (1.0 / Codec::kScale));
-    });
-    const double r = 1.0 + dr;
+    R dr = 0;  // rho - 1 = sum_i (f_i - w_i)
+    static_for<kQ>([&](auto I) { dr += Codec::dev(v[I], K.w[vel(I).shell] * R(1.0 / Codec::kScale)); });
+    const R r = R(1) + dr;
     rho[q] = r;
-    A[q] = ni_mu(r, e);
-    A[2 * d.plane + q] = ni_F(r, e);
+    A[q] = ni_mu<R>(r, e);
+    A[2 * d.plane + q] = ni_F<R>(r, e);
 }
 
 // A[k][node]: 0 mu, 1 F (both from k_ni_density), 2..4 grad2 rho, 5 lap rho, 6 lap F.
-__global__ void __launch_bounds__(128) k_ni_fields(Dims d, const double* __restrict__ rho, double* __restrict__ A) {
+template <class F>
+__global__ void __launch_bounds__(128) k_ni_fields(Dims d, const F* __restrict__ rho, F* __restrict__ A) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int s, z, y, x;
     if (!ni_node(d, q, s, z, y, x)) return;
     const int64_t n = 2 * d.plane;
-    const double r0 = rho[q], F0 = A[n + q];
-    double g[3] = {0.0, 0.0, 0.0}, lr = 14.0 / 36.0 * r0, lF = 14.0 / 36.0 * F0;
+    const F r0 = rho[q], F0 = A[n + q];
+    F g[3] = {F(0), F(0), F(0)}, lr = F(14.0 / 36.0) * r0, lF = F(14.0 / 36.0) * F0;
     for (int k = 0; k < kStencil; ++k) {
         int cx, cy, cz;
-        double w;
+        F w;
         stencil(k, cx, cy, cz, w);
         const int64_t m = ni_neighbor(d, s, z, y, x, cx, cy, cz);
-        const double rn = rho[m];
-        g[0] += w * 0.5 * cx * rn;
-        g[1] += w * 0.5 * cy * rn;
-        g[2] += w * 0.5 * cz * rn;
+        const F rn = rho[m];
+        g[0] += w * F(0.5 * cx) * rn;
+        g[1] += w * F(0.5 * cy) * rn;
+        g[2] += w * F(0.5 * cz) * rn;
         lr += w * rn;
         lF += w * A[n + m];
     }
-    for (int a = 0; a < 3; ++a) A[(2 + a) * n + q] = g[a] / kHatTheta;
-    A[5 * n + q] = 2.0 / kHatTheta * (lr - r0);
-    A[6 * n + q] = 2.0 / kHatTheta * (lF - F0);
+    for (int a = 0; a < 3; ++a) A[(2 + a) * n + q] = g[a] * F(1.0 / kHatTheta);
+    A[5 * n + q] = F(2.0 / kHatTheta) * (lr - r0);
+    A[6 * n + q] = F(2.0 / kHatTheta) * (lF - F0);
 }
 
-__global__ void __launch_bounds__(128) k_ni_force(Dims d, NiEos e, const double* __restrict__ rho,
-                                                  const double* __restrict__ A, double* __restrict__ g) {
+template <class F>
+__global__ void __launch_bounds__(128) k_ni_force(Dims d, NiEos e, const F* __restrict__ rho, const F* __restrict__ A,
+                                                  F* __restrict__ g) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int s, z, y, x;
     if (!ni_node(d, q, s, z, y, x)) return;
     const int64_t n = 2 * d.plane;
-    double dmu[3] = {0, 0, 0}, dF[3] = {0, 0, 0}, dlF[3] = {0, 0, 0}, divI[3] = {0, 0, 0};
+    F dmu[3] = {0, 0, 0}, dF[3] = {0, 0, 0}, dlF[3] = {0, 0, 0}, divI[3] = {0, 0, 0};
     for (int k = 0; k < kStencil; ++k) {
         int cx, cy, cz;
-        double w;
+        F w;
         stencil(k, cx, cy, cz, w);
         const int64_t m = ni_neighbor(d, s, z, y, x, cx, cy, cz);
-        const double c[3] = {0.5 * cx, 0.5 * cy, 0.5 * cz};
-        const double gr[3] = {A[2 * n + m], A[3 * n + m], A[4 * n + m]};
-        const double iso = -0.5 * (gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]) - rho[m] * A[5 * n + m];
+        const int cc[3] = {cx, cy, cz};
+        const F gr[3] = {A[2 * n + m], A[3 * n + m], A[4 * n + m]};
+        const F iso = F(-0.5) * (gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]) - rho[m] * A[5 * n + m];
         for (int a = 0; a < 3; ++a) {
-            if (c[a] == 0.0) continue;
-            const double wc = w * c[a];
+            if (cc[a] == 0) continue;
+            const F wc = w * F(0.5 * cc[a]);
             dmu[a] += wc * A[m];
             dF[a] += wc * A[n + m];
             dlF[a] += wc * A[6 * n + m];
         }
         // grad2_b I_ab: sum over the stencil of w c_b I_ab(x + c)
         for (int a = 0; a < 3; ++a) {
-            double t = 0.0;
+            F t = 0;
             for (int b = 0; b < 3; ++b) {
-                if (c[b] == 0.0) continue;
-                const double I_ab = gr[a] * gr[b] + (a == b ? iso : 0.0);
-                t += w * c[b] * I_ab;
+                if (cc[b] == 0) continue;
+                const F I_ab = gr[a] * gr[b] + (a == b ? iso : F(0));
+                t += w * F(0.5 * cc[b]) * I_ab;
             }
             divI[a] += t;
         }
     }
-    const double r0 = rho[q], mu0 = A[q];
+    const F r0 = rho[q], mu0 = A[q], inv_th = F(1.0 / kHatTheta);
     for (int a = 0; a < 3; ++a) {
-        const double g2mu = dmu[a] / kHatTheta, g2F = dF[a] / kHatTheta, g2lF = dlF[a] / kHatTheta;
-        const double g4F = g2F - 0.5 * kHatTheta * g2lF;
-        const double rg = -(r0 * g2mu + mu0 * A[(2 + a) * n + q] - e.eta * g2F - (1.0 - e.eta) * g4F +
-                            e.kappa * divI[a] / kHatTheta);
+        const F g2mu = dmu[a] * inv_th, g2F = dF[a] * inv_th, g2lF = dlF[a] * inv_th;
+        const F g4F = g2F - F(0.5 * kHatTheta) * g2lF;
+        const F rg = -(r0 * g2mu + mu0 * A[(2 + a) * n + q] - F(e.eta) * g2F - (F(1) - F(e.eta)) * g4F +
+                       F(e.kappa) * divI[a] * inv_th);
         g[a * n + q] = rg / r0;
     }
 }
@@ -203,7 +213,8 @@ template <class Codec>
 __global__ void __launch_bounds__(128) k_ni_step(const typename Codec::raw_t* __restrict__ src,
                                                  typename Codec::raw_t* __restrict__ dst, Dims d,
                                                  Consts<typename Codec::R> K, typename Codec::R tb,
-                                                 typename Codec::R inv_theta0, const double* __restrict__ g,
+                                                 typename Codec::R inv_theta0,
+                                                 const typename Codec::R* __restrict__ g,
                                                  int* __restrict__ err) {
     using R = typename Codec::R;
     using T = typename Codec::raw_t;
@@ -220,7 +231,7 @@ __global__ void __launch_bounds__(128) k_ni_step(const typename Codec::raw_t* __
     NodeState<R> st;
     st.drho = m.drho;
     st.rho = R(1) + m.drho;
-    const R gx = (R)g[q], gy = (R)g[n + q], gz = (R)g[2 * n + q];
+    const R gx = g[q], gy = g[n + q], gz = g[2 * n + q];
     const R inv_rho = R(1) / st.rho;
     st.ux = m.jx * inv_rho + R(0.5) * gx;
     st.uy = m.jy * inv_rho + R(0.5) * gy;
@@ -269,19 +280,6 @@ cudaError_t launch_nonideal_step(int prec, const void* src, void* dst, const Dim
     const int64_t n = 2 * d.plane;
     const unsigned blocks = (unsigned)((n + 127) / 128);
     const NiEos e{eos[0], eos[1], c.theta0, eos[2], eos[3]};
-    double* rho = work;
-    double* A = work + n;
-    double* g = work + 8 * n;
-    cudaError_t r = ni_codec(prec, [&](auto codec) {
-        using C = decltype(codec);
-        k_ni_density<C><<<blocks, 128, 0, st>>>(static_cast<const typename C::raw_t*>(src), d, c.kd, e, rho, A);
-        return cudaGetLastError();
-    });
-    if (r != cudaSuccess) return r;
-    k_ni_fields<<<blocks, 128, 0, st>>>(d, rho, A);
-    k_ni_force<<<blocks, 128, 0, st>>>(d, e, rho, A, g);
-    r = cudaGetLastError();
-    if (r != cudaSuccess) return r;
     return ni_codec(prec, [&](auto codec) {
         using C = decltype(codec);
         using R = typename C::R;
@@ -290,6 +288,12 @@ cudaError_t launch_nonideal_step(int prec, const void* src, void* dst, const Dim
             K = &c.kd;
         else
             K = &c.kf;
+        R* rho = reinterpret_cast<R*>(work);  // fields in the compute type: rho, A[7], g[3]
+        R* A = rho + n;
+        R* g = rho + 8 * n;
+        k_ni_density<C><<<blocks, 128, 0, st>>>(static_cast<const typename C::raw_t*>(src), d, *K, e, rho, A);
+        k_ni_fields<R><<<blocks, 128, 0, st>>>(d, rho, A);
+        k_ni_force<R><<<blocks, 128, 0, st>>>(d, e, rho, A, g);
         k_ni_step<C><<<blocks, 128, 0, st>>>(static_cast<const typename C::raw_t*>(src),
                                              static_cast<typename C::raw_t*>(dst), d, *K, (R)twobeta,
                                              (R)(1.0 / c.theta0), g, err);
