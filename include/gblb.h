@@ -243,25 +243,45 @@ lb_status lb_set_wall_columns(lb_ctx *ctx, const double *bottom, const double *t
  * first): host array [2][ny][nx].  LB_ERR_STATE without walls.  Synchronises the stream. */
 lb_status lb_wall_density(lb_ctx *ctx, double *rho_w);
 
+/* Equations of state of the nonideal fluid (the eos argument of lb_set_nonideal), at the
+ * lattice temperature theta0, with Z(p) = (1 + p + p^2 - p^3) / (1 - p)^3, p = b rho / 4:
+ *   van der Waals        p = rho theta0 / (1 - b rho) - a rho^2
+ *                        (critical point: theta_c = 8a / (27b), rho_c = 1 / (3b))
+ *   Peng-Robinson type   p = rho theta0 Z - a rho^2 / (1 + 2 b rho - b^2 rho^2), Eq. (cspreos)
+ *                        (a = 1.851427622 theta_c / rho_c, b = 0.353748714 / rho_c)
+ *   Carnahan-Starling    p = rho theta0 Z - a rho^2
+ *                        (a = 1.3828652 theta_c / rho_c, b = 0.52177554 / rho_c: the roots of
+ *                        dp/drho = d2p/drho2 = 0 at (rho_c, theta_c)) */
+#define LB_EOS_VAN_DER_WAALS 1
+#define LB_EOS_PENG_ROBINSON 2
+#define LB_EOS_CARNAHAN_STARLING 3
+
 /* Isothermal nonideal fluid (Sec. "Nonideal Fluids and two-phase flow"): with
- * enable != 0 each step adds the force of the paper's momentum-conserving
- * formulation, Eq. (gradientFinal), for the van der Waals equation of state
- * p = rho theta0 / (1 - b rho) - a rho^2 at the lattice temperature theta0,
+ * eos != 0 (one of LB_EOS_*) each step adds the force of the paper's
+ * momentum-conserving formulation, Eq. (gradientFinal), for that equation of
+ * state at the lattice temperature theta0,
  *   rho g = -[rho d2 mu + mu d2 rho - eta d2 F - (1 - eta) d4 F + kappa d2_b I_ab]
- * (mu, F: the nonideal chemical potential and free energy; I_ab: the
- * interfacial stress; d2, d4: the second- and fourth-order gradients of the
- * 15-velocity bcc stencil of Appendix A), and collides with the forcing of
- * Eq. (multiphaseEvolution), alpha = 2, at the equilibrium f^eq(rho, u,
+ * (mu, F: the nonideal chemical potential and free energy, without the ideal
+ * part theta0 rho (ln rho - 1) that the lattice carries, so that p = rho mu - F;
+ * I_ab: the interfacial stress; d2, d4: the second- and fourth-order gradients
+ * of the 15-velocity bcc stencil of Appendix A), and collides with the forcing
+ * of Eq. (multiphaseEvolution), alpha = 2, at the equilibrium f^eq(rho, u,
  * theta0) (isothermal: the temperature moment is not kept).  u is then
  * sum f c / rho + g / 2 (lb_get_moments reports sum f c / rho).
- *   a >= 0, b > 0   van der Waals constants (theta_c = 8a / (27b), rho_c = 1 / (3b))
+ *   a >= 0, b > 0   the equation of state's constants (above)
  *   kappa >= 0      interfacial stiffness; eta in [0, 1]: weight of the second-order
  *                   gradient of F (the paper uses 1/2)
+ * Densities must stay below the equation of state's singular density (1/b for
+ * van der Waals, 4/b for Carnahan-Starling, (1 + sqrt2)/b for the Peng-Robinson
+ * type).  Beyond it the van der Waals and Peng-Robinson logarithms give NaN,
+ * which the step's state check reports as LB_ERR_UNSTABLE at the next
+ * synchronising call; the Carnahan-Starling form is checked only for
+ * rho > 0 and finite moments.  An eos outside LB_EOS_* gives LB_ERR_ARG.
  * Needs the projected series equilibrium (no LB_FLAG_PAPER_LITERAL or
  * LB_FLAG_ENTROPIC; LB_ERR_ARG) and no walls (LB_ERR_STATE).  Each step runs
  * four one-node-per-thread kernels; the work buffer is 88 bytes per node.
- * enable = 0 restores the energy-conserving update. */
-lb_status lb_set_nonideal(lb_ctx *ctx, int enable, double a, double b, double kappa, double eta);
+ * eos = 0 restores the energy-conserving update. */
+lb_status lb_set_nonideal(lb_ctx *ctx, int eos, double a, double b, double kappa, double eta);
 
 /* Number of time steps taken since the last lb_set_fields / lb_set_populations / lb_set_state. */
 int64_t lb_time(const lb_ctx *ctx);

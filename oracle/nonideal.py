@@ -85,6 +85,14 @@ class VdW:
         self.b = 1.0 / (3.0 * rho_c)
         self.a = 27.0 * self.b * self.theta_c / 8.0
 
+    def rho_scale(self):
+        """The critical density."""
+        return 1.0 / (3.0 * self.b)
+
+    def rho_max(self):
+        """The density where the equation of state becomes singular."""
+        return 1.0 / self.b
+
     def F_nid(self, rho):
         return -rho * self.theta0 * np.log(1.0 - self.b * rho) - self.a * rho * rho
 
@@ -101,22 +109,139 @@ class VdW:
     def maxwell(self):
         """(rho_gas, rho_liquid) with equal chemical potential and pressure."""
         from scipy.optimize import brentq, fsolve
-        # spinodal densities bracket the two phases
-        rs = np.linspace(0.05, 2.9, 20000) / (3 * self.b)
+        # spinodal densities bracket the two phases: the first run of negative slope dp/drho
+        # (the loop below the critical temperature; an equation of state may turn down again
+        # near its own singular density, which is not part of the loop)
+        rmax = 0.95 * self.rho_max()
+        rs = np.linspace(0.02 * self.rho_scale(), rmax, 200000)
         dp = np.gradient(self.p(rs), rs)
         neg = np.where(dp < 0)[0]
-        r1, r2 = rs[neg[0]], rs[neg[-1]]
+        end = neg[0]
+        while end + 1 < len(rs) and dp[end + 1] < 0:
+            end += 1
+        r1, r2 = rs[neg[0]], rs[end]
+        top = end + 1  # the liquid branch: rising pressure after the loop
+        while top + 1 < len(rs) and dp[top + 1] >= 0:
+            top += 1
 
         def eqs(v):
             g, l = v
             return [self.mu(g) - self.mu(l), self.p(g) - self.p(l)]
 
-        # a starting pressure between the spinodal extremes (and above zero, where a gas root exists)
-        p_mid = 0.5 * (self.p(r1) + max(self.p(r2), 0.0))
+        # a starting pressure between the spinodal extremes (and above zero, where a gas root
+        # exists), below the top of the liquid branch
+        lo, hi = max(self.p(r2), 0.0), min(self.p(r1), self.p(rs[top]))
+        if not lo < hi:
+            raise ValueError("no liquid-vapour coexistence at this temperature")
+        p_mid = 0.5 * (lo + hi)
         g0 = brentq(lambda r: self.p(r) - p_mid, 1e-12, r1)
-        l0 = brentq(lambda r: self.p(r) - p_mid, r2, 0.999 / self.b)
+        l0 = brentq(lambda r: self.p(r) - p_mid, r2, rs[top])
         g, l = fsolve(eqs, [g0, l0], xtol=1e-12)
         return float(g), float(l)
+
+
+def _cs_repulsion(eta):
+    """Carnahan-Starling hard-sphere terms at packing eta = b rho / 4: the compressibility
+    Z = (1 + eta + eta^2 - eta^3) / (1 - eta)^3, the excess free energy per particle and
+    theta0, (4 eta - 3 eta^2) / (1 - eta)^2 = int_0^rho (Z - 1) / rho' drho', and its
+    derivative times rho, eta (4 - 2 eta) / (1 - eta)^3."""
+    Z = (1 + eta + eta * eta - eta ** 3) / (1 - eta) ** 3
+    f = (4 * eta - 3 * eta * eta) / (1 - eta) ** 2
+    return Z, f, eta * (4 - 2 * eta) / (1 - eta) ** 3
+
+
+class PengRobinson(VdW):
+    """The Peng-Robinson type equation of state of Eq. (cspreos) (Sec. "Sound propagation in a
+    nonideal gas"): Carnahan-Starling repulsion with a Peng-Robinson attraction,
+        p = rho theta0 Z(b rho / 4) - a rho^2 / (1 + 2 b rho - b^2 rho^2),
+    a = 1.851427622 theta_c / rho_c, b = 0.353748714 / rho_c as printed there.
+    The attraction's free energy is rho int_0^rho p_att / rho'^2 drho'; with
+    1 + 2x - x^2 = (sqrt2 - 1 + x)(sqrt2 + 1 - x) it is
+        F_att = -(a rho / (2 sqrt2 b)) ln[(1 + b rho / (sqrt2 - 1)) / (1 - b rho / (sqrt2 + 1))]."""
+
+    def __init__(self, theta_star, rho_c=1.0, theta0=None):
+        self.theta0 = oracle.theta0() if theta0 is None else theta0
+        self.theta_c = self.theta0 / theta_star
+        self.rho_c = rho_c
+        self.a = 1.851427622 * self.theta_c / rho_c
+        self.b = 0.353748714 / rho_c
+
+    def rho_scale(self):
+        return self.rho_c
+
+    def rho_max(self):
+        return (1.0 + np.sqrt(2.0)) / self.b  # the attraction's pole (before eta = 1)
+
+    def _att_log(self, rho):
+        r2 = np.sqrt(2.0)
+        x = self.b * rho
+        return np.log((r2 - 1 + x) / (r2 + 1 - x)) - np.log((r2 - 1) / (r2 + 1))
+
+    def F_nid(self, rho):
+        _, f, _ = _cs_repulsion(self.b * rho / 4.0)
+        return rho * self.theta0 * f - (self.a * rho / (2 * np.sqrt(2.0) * self.b)) * self._att_log(rho)
+
+    def mu_nid(self, rho):
+        _, f, rdf = _cs_repulsion(self.b * rho / 4.0)
+        x = self.b * rho
+        return (self.theta0 * (f + rdf) - (self.a / (2 * np.sqrt(2.0) * self.b)) * self._att_log(rho)
+                - self.a * rho / (1 + 2 * x - x * x))
+
+    def p(self, rho):
+        Z, _, _ = _cs_repulsion(self.b * rho / 4.0)
+        x = self.b * rho
+        return rho * self.theta0 * Z - self.a * rho * rho / (1 + 2 * x - x * x)
+
+
+class CarnahanStarling(VdW):
+    """The Carnahan-Starling equation of state (Sec. "Quenching of a liquid-gas system" and
+    "Droplet Collision"): Carnahan-Starling repulsion with the van der Waals attraction,
+        p = rho theta0 Z(b rho / 4) - a rho^2,   F_nid = rho theta0 f(b rho / 4) - a rho^2.
+    The paper prints no constants for it; a and b put the critical point at (rho_c, theta_c):
+    with g(eta) = eta Z(eta), dp/drho = d2p/drho2 = 0 there gives g'(eta_c) = eta_c g''(eta_c),
+    b = 4 eta_c / rho_c and a = theta_c g'(eta_c) / (2 rho_c), where
+        g'(eta) = (1 + 4 eta + 4 eta^2 - 4 eta^3 + eta^4) / (1 - eta)^4,
+        g''(eta) = (8 + 20 eta - 4 eta^2) / (1 - eta)^5."""
+
+    @staticmethod
+    def critical_constants():
+        """(b rho_c, a rho_c / theta_c)."""
+        from scipy.optimize import brentq
+
+        def g1(e):
+            return (1 + 4 * e + 4 * e * e - 4 * e ** 3 + e ** 4) / (1 - e) ** 4
+
+        def g2(e):
+            return (8 + 20 * e - 4 * e * e) / (1 - e) ** 5
+
+        ec = brentq(lambda e: g1(e) - e * g2(e), 0.01, 0.5, xtol=1e-16)
+        return 4.0 * ec, 0.5 * g1(ec)
+
+    def __init__(self, theta_star, rho_c=1.0, theta0=None):
+        self.theta0 = oracle.theta0() if theta0 is None else theta0
+        self.theta_c = self.theta0 / theta_star
+        self.rho_c = rho_c
+        bc, ac = self.critical_constants()
+        self.a = ac * self.theta_c / rho_c
+        self.b = bc / rho_c
+
+    def rho_scale(self):
+        return self.rho_c
+
+    def rho_max(self):
+        return 4.0 / self.b  # eta = 1
+
+    def F_nid(self, rho):
+        _, f, _ = _cs_repulsion(self.b * rho / 4.0)
+        return rho * self.theta0 * f - self.a * rho * rho
+
+    def mu_nid(self, rho):
+        _, f, rdf = _cs_repulsion(self.b * rho / 4.0)
+        return self.theta0 * (f + rdf) - 2.0 * self.a * rho
+
+    def p(self, rho):
+        Z, _, _ = _cs_repulsion(self.b * rho / 4.0)
+        return rho * self.theta0 * Z - self.a * rho * rho
 
 
 def force(rho, eos, kappa, eta=0.5):

@@ -379,8 +379,8 @@ lb_status lb_step(lb_ctx* c, int64_t n) {
     const LaunchConsts& lc = lattice().lc;
     for (int64_t t = 0; t < n; ++t) {
         if (c->nonideal)
-            CK(c, launch_nonideal_step(c->prec, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc, c->twobeta, c->ni_eos,
-                                       c->d_ni, c->d_err, c->stream));
+            CK(c, launch_nonideal_step(c->prec, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc, c->twobeta,
+                                       c->nonideal, c->ni_eos, c->d_ni, c->d_err, c->stream));
         else if (c->walls)
             CK(c, launch_wall_step(c->prec, c->eq, c->variant, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc,
                                    c->twobeta, c->d_wall, c->d_err, c->stream));
@@ -618,6 +618,8 @@ lb_status lb_set_nonideal(lb_ctx* c, int enable, double a, double b, double kapp
         c->nonideal = 0;
         return LB_OK;
     }
+    if (enable < LB_EOS_VAN_DER_WAALS || enable > LB_EOS_CARNAHAN_STARLING)
+        return fail(c, LB_ERR_ARG, "lb_set_nonideal: unknown equation of state");
     if (!(a >= 0.0) || !(b > 0.0) || !(kappa >= 0.0) || !(eta >= 0.0 && eta <= 1.0) || !isfinite(a) ||
         !isfinite(b) || !isfinite(kappa))
         return fail(c, LB_ERR_ARG, "lb_set_nonideal: need a >= 0, b > 0, kappa >= 0, 0 <= eta <= 1");
@@ -637,7 +639,7 @@ lb_status lb_set_nonideal(lb_ctx* c, int enable, double a, double b, double kapp
     c->ni_eos[1] = b;
     c->ni_eos[2] = kappa;
     c->ni_eos[3] = eta;
-    c->nonideal = 1;
+    c->nonideal = enable;
     return LB_OK;
 }
 

@@ -31,7 +31,7 @@ struct lb_ctx {
     int64_t time;
     int walls = 0;           // kinetic walls normal to z (lb_set_walls) instead of the periodic wrap
     void* d_wall = nullptr;  // the walls' device block (lb_walls.cu)
-    int nonideal = 0;          // isothermal van der Waals fluid (lb_set_nonideal)
+    int nonideal = 0;          // isothermal nonideal fluid: 0 off, else its equation of state (lb_set_nonideal)
     double ni_eos[4] = {0, 0, 0, 0};  // a, b, kappa, eta
     double* d_ni = nullptr;    // its work buffer (lb_nonideal.cu)
     std::string msg;

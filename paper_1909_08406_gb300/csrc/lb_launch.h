@@ -89,10 +89,12 @@ cudaError_t launch_wall_step(int prec, int eq, int variant, const void* src, voi
                              const LaunchConsts& c, double twobeta, void* blk, int* err, cudaStream_t st);
 
 // Isothermal nonideal fluid (lb_nonideal.cu): doubles of the work buffer for this grid, and
-// one step (density, fields, force, forced step).  eos = {a, b, kappa, eta}.
+// one step (density, fields, force, forced step).  kind: 1 van der Waals, 2 Peng-Robinson type,
+// 3 Carnahan-Starling; eos = {a, b, kappa, eta}.
 size_t nonideal_doubles(const Dims& d);
 cudaError_t launch_nonideal_step(int prec, const void* src, void* dst, const Dims& d, const LaunchConsts& c,
-                                 double twobeta, const double eos[4], double* work, int* err, cudaStream_t st);
+                                 double twobeta, int kind, const double eos[4], double* work, int* err,
+                                 cudaStream_t st);
 
 inline dim3 step_grid(const Dims& d, int threads) {
     return dim3((unsigned)d.rows, (unsigned)((d.nx + threads - 1) / threads), 1);

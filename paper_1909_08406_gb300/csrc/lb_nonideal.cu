@@ -1,5 +1,6 @@
-// Isothermal nonideal (van der Waals) fluid (Sec. "Nonideal Fluids and
-// two-phase flow"; derivative stencil of Appendix A).
+// Isothermal nonideal fluid (Sec. "Nonideal Fluids and two-phase flow"; derivative
+// stencil of Appendix A), with the van der Waals, the Peng-Robinson type (Eq. cspreos)
+// or the Carnahan-Starling equation of state.
 //
 // Per step, from the post-collision state src:
 //   k_ni_density  rho of the streamed populations, sum_i f_i(x - c_i), and
@@ -25,22 +26,55 @@
 
 namespace gblb {
 
+// Equations of state, numbered as the lb_set_nonideal argument that selects them.
+enum NiKind { kVdW = 1, kPengRobinson = 2, kCarnahanStarling = 3 };
+
 struct NiEos {
     double a, b, theta0, kappa, eta;
+    int kind;
 };
 
-__device__ __forceinline__ double ni_log(double v) { return log(v); }
-__device__ __forceinline__ float ni_log(float v) { return logf(v); }
+__host__ __device__ __forceinline__ double ni_log(double v) { return log(v); }
+__host__ __device__ __forceinline__ float ni_log(float v) { return logf(v); }
+__host__ __device__ __forceinline__ double ni_log1p(double v) { return log1p(v); }
+__host__ __device__ __forceinline__ float ni_log1p(float v) { return log1pf(v); }
 
-// F_nid and mu_nid of the van der Waals fluid, in the field type F
+// Carnahan-Starling repulsion at packing fraction p = b rho / 4: its excess free energy per
+// particle over theta0, f = (4p - 3p^2) / (1 - p)^2 (the integral of (Z - 1) / rho with
+// Z = (1 + p + p^2 - p^3) / (1 - p)^3), and rho df/drho = p (4 - 2p) / (1 - p)^3.
 template <class F>
-__device__ __forceinline__ F ni_F(F r, const NiEos& e) {
-    return -r * F(e.theta0) * ni_log(F(1) - F(e.b) * r) - F(e.a) * r * r;
+__host__ __device__ __forceinline__ void cs_repulsion(F p, F& f, F& rdf) {
+    const F inv = F(1) / (F(1) - p), inv2 = inv * inv;
+    f = p * (F(4) - F(3) * p) * inv2;
+    rdf = p * (F(4) - F(2) * p) * inv2 * inv;
 }
+
+// mu_nid and F_nid of node density r, in the field type F: the free energy without the
+// ideal part theta0 rho (ln rho - 1), so that p = rho mu - F and both vanish as rho -> 0.
+//   van der Waals       F = -theta0 rho ln(1 - b rho) - a rho^2
+//   Peng-Robinson type  F = theta0 rho f - a rho L,  L = int_0^rho drho' / (1 + 2b rho' - b^2 rho'^2)
+//                         = [ln(1 + (sqrt2 + 1) b rho) - ln(1 - (sqrt2 - 1) b rho)] / (2 sqrt2 b)
+//   Carnahan-Starling   F = theta0 rho f - a rho^2
 template <class F>
-__device__ __forceinline__ F ni_mu(F r, const NiEos& e) {
-    const F br = F(e.b) * r;
-    return -F(e.theta0) * ni_log(F(1) - br) + F(e.theta0) * br / (F(1) - br) - F(2) * F(e.a) * r;
+__host__ __device__ __forceinline__ void ni_eos(F r, const NiEos& e, F& mu, F& Fe) {
+    const F th = F(e.theta0), a = F(e.a), br = F(e.b) * r;
+    if (e.kind == kPengRobinson) {
+        F f, rdf;
+        cs_repulsion(F(0.25) * br, f, rdf);
+        const F L = (ni_log1p(F(2.414213562373095) * br) - ni_log1p(F(-0.41421356237309503) * br)) *
+                    F(0.35355339059327373) / F(e.b);
+        Fe = r * th * f - a * r * L;
+        mu = th * (f + rdf) - a * L - a * r / (F(1) + br * (F(2) - br));
+    } else if (e.kind == kCarnahanStarling) {
+        F f, rdf;
+        cs_repulsion(F(0.25) * br, f, rdf);
+        Fe = r * th * f - a * r * r;
+        mu = th * (f + rdf) - F(2) * a * r;
+    } else {
+        const F L = ni_log(F(1) - br);
+        Fe = -r * th * L - a * r * r;
+        mu = -th * L + th * br / (F(1) - br) - F(2) * a * r;
+    }
 }
 
 constexpr double kHatTheta = 1.0 / 6.0;
@@ -135,8 +169,10 @@ __global__ void __launch_bounds__(128) k_ni_density(const typename Codec::raw_t*
     static_for<kQ>([&](auto I) { dr += Codec::dev(v[I], K.w[vel(I).shell] * R(1.0 / Codec::kScale)); });
     const R r = R(1) + dr;
     rho[q] = r;
-    A[q] = ni_mu<R>(r, e);
-    A[2 * d.plane + q] = ni_F<R>(r, e);
+    R mu, Fe;
+    ni_eos<R>(r, e, mu, Fe);
+    A[q] = mu;
+    A[2 * d.plane + q] = Fe;
 }
 
 // A[k][node]: 0 mu, 1 F (both from k_ni_density), 2..4 grad2 rho, 5 lap rho, 6 lap F.
@@ -276,10 +312,12 @@ static cudaError_t ni_codec(int prec, F&& f) {
 size_t nonideal_doubles(const Dims& d) { return (size_t)11 * 2 * d.plane; }
 
 cudaError_t launch_nonideal_step(int prec, const void* src, void* dst, const Dims& d, const LaunchConsts& c,
-                                 double twobeta, const double eos[4], double* work, int* err, cudaStream_t st) {
+                                 double twobeta, int kind, const double eos[4], double* work, int* err,
+                                 cudaStream_t st) {
     const int64_t n = 2 * d.plane;
     const unsigned blocks = (unsigned)((n + 127) / 128);
-    const NiEos e{eos[0], eos[1], c.theta0, eos[2], eos[3]};
+    if (kind < kVdW || kind > kCarnahanStarling) return cudaErrorInvalidValue;
+    const NiEos e{eos[0], eos[1], c.theta0, eos[2], eos[3], kind};
     return ni_codec(prec, [&](auto codec) {
         using C = decltype(codec);
         using R = typename C::R;

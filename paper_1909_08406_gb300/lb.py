@@ -234,13 +234,18 @@ def lb_tune(ctx, reps=3):
     return k.value, ms.value
 
 
-def lb_set_nonideal(ctx, a=None, b=None, kappa=0.0, eta=0.5):
-    """Isothermal van der Waals fluid with the paper's momentum-conserving force; a = None
-    restores the energy-conserving update."""
+LB_EOS = {"vdw": 1, "peng_robinson": 2, "carnahan_starling": 3}
+
+
+def lb_set_nonideal(ctx, a=None, b=None, kappa=0.0, eta=0.5, eos="vdw"):
+    """Isothermal nonideal fluid with the paper's momentum-conserving force, for the equation
+    of state `eos` ("vdw", "peng_robinson" or "carnahan_starling", or its LB_EOS_* number) with
+    constants a, b; a = None restores the energy-conserving update."""
     if a is None:
         _check(lib().lb_set_nonideal(ctx, 0, 0.0, 0.0, 0.0, 0.0), ctx)
         return
-    _check(lib().lb_set_nonideal(ctx, 1, float(a), float(b), float(kappa), float(eta)), ctx)
+    kind = LB_EOS[eos] if isinstance(eos, str) else int(eos)
+    _check(lib().lb_set_nonideal(ctx, kind, float(a), float(b), float(kappa), float(eta)), ctx)
 
 
 def lb_grid_of(ctx):

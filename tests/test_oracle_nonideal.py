@@ -1,23 +1,33 @@
 """The isothermal nonideal fluid of Sec. "Nonideal Fluids and two-phase flow"
 in the oracle (``oracle/nonideal.py``): the derivative stencil of Appendix A,
-the momentum-conserving force of Eq. (gradientFinal), and a flat van der Waals
-interface against Maxwell's equal-area construction.
+the momentum-conserving force of Eq. (gradientFinal), the three equations of
+state (van der Waals, the Peng-Robinson type of Eq. (cspreos) and
+Carnahan-Starling), and flat interfaces against Maxwell's equal-area
+construction.
 
 Pins, each independent of the oracle's formula:
+  - each equation of state's free energy is consistent with its pressure
+    (p = rho mu - F with mu = dF/drho, by finite differences), tends to the
+    ideal gas at low density, and has its critical point where its constants
+    put it: dp/drho = d2p/drho2 = 0 at (rho_c, theta_c), with the textbook
+    critical compressibilities 3/8 (van der Waals) and 0.3590 at packing
+    fraction 0.13044 (Carnahan-Starling); for the Peng-Robinson type this pins
+    the printed formula against the printed ten-digit constants;
   - Maxwell's construction is solved to round-off (equal chemical potential
-    and pressure) and reproduces the known van der Waals coexistence
-    densities;
+    and pressure, and equal areas) and reproduces the known van der Waals
+    coexistence densities;
   - the stencil's gradient and Laplacian are second order and the corrected
     gradient of Eq. (gradient4) fourth order (error ratios 4 and 16 when the
     wavenumber halves);
   - the force conserves global momentum to round-off for any density field,
     the property the paper builds it for;
   - a flat interface at theta/theta_c = 0.9 settles on the coexisting
-    densities of Maxwell's construction;
+    densities of Maxwell's construction, for each equation of state;
   - a small density wave in either phase travels at the isothermal sound
-    speed of the equation of state, sqrt(dp/drho) (Sec. "Sound propagation in
-    a nonideal gas", here for the van der Waals fluid), with an error that is
-    second order in the wavenumber."""
+    speed of the equation of state, sqrt(dp/drho), with an error that is
+    second order in the wavenumber: the van der Waals fluid, and the
+    experiment of Sec. "Sound propagation in a nonideal gas" itself, the
+    Peng-Robinson type fluid at its coexisting phase densities."""
 import numpy as np
 import pytest
 
@@ -27,16 +37,71 @@ from oracle import nonideal as ni
 TH0 = oracle.theta0()
 
 
+EOS = {"vdw": ni.VdW, "peng_robinson": ni.PengRobinson, "carnahan_starling": ni.CarnahanStarling}
+
+
+@pytest.mark.parametrize("name", list(EOS))
+def test_equation_of_state_thermodynamics(name):
+    e = EOS[name](0.9)
+    r = np.linspace(0.05, 0.8 * min(e.rho_max(), 4.0), 400)
+    # p = rho mu - F with the ideal parts theta0 rho (ln rho - 1) and theta0 ln rho added back
+    F = TH0 * r * (np.log(r) - 1) + e.F_nid(r)
+    assert np.abs(e.p(r) - (r * e.mu(r) - F)).max() <= 1e-14 * (1 + np.abs(e.p(r)).max())
+    # mu_nid = dF_nid/drho by central differences (truncation h^2/6 times the third derivative)
+    h = 1e-5
+    dF = (e.F_nid(r + h) - e.F_nid(r - h)) / (2 * h)
+    assert np.abs(e.mu_nid(r) - dF).max() <= 1e-8
+    # the ideal gas at low density: F_nid and mu_nid vanish, p -> rho theta0
+    lo = np.array([1e-9, 1e-7])
+    assert np.abs(e.mu_nid(lo)).max() <= 1e-6 and np.abs(e.F_nid(lo)).max() <= 1e-13
+    assert e.p(1e-7) / (1e-7 * TH0) == pytest.approx(1.0, abs=1e-6)
+
+
+@pytest.mark.parametrize("name,Zc", [("vdw", 3 / 8), ("peng_robinson", None), ("carnahan_starling", 0.35896)])
+def test_critical_point(name, Zc):
+    e = EOS[name](1.0)  # theta0 = theta_c
+    h = 1e-4
+    p = e.p(np.array([1 - h, 1.0, 1 + h]))
+    dp = (p[2] - p[0]) / (2 * h)
+    d2p = (p[2] - 2 * p[1] + p[0]) / h ** 2
+    assert abs(dp) <= 1e-8 * TH0 and abs(d2p) <= 1e-6 * TH0, (dp, d2p)
+    if Zc is not None:
+        assert p[1] / TH0 == pytest.approx(Zc, abs=2e-5)
+    if name == "carnahan_starling":
+        assert e.b / 4 == pytest.approx(0.13044, abs=1e-5)  # the critical packing fraction
+    # a loop below theta_c, none above it
+    r = np.linspace(0.05, 0.9 * min(e.rho_max(), 4.0), 20000)
+    assert (np.gradient(EOS[name](0.9).p(r), r) < 0).any()
+    assert (np.gradient(EOS[name](1.05).p(r), r)[: int(0.75 * len(r))] > 0).all()
+
+
 def test_maxwell_construction():
     e = ni.VdW(0.9)
     g, l = e.maxwell()
-    assert abs(e.mu(g) - e.mu(l)) <= 1e-14 and abs(e.p(g) - e.p(l)) <= 1e-14
     # van der Waals coexistence at T / T_c = 0.9, in units of the critical density
     assert g == pytest.approx(0.42574, abs=2e-5) and l == pytest.approx(1.65727, abs=2e-5)
+
+
+@pytest.mark.parametrize("name,theta_star", [("vdw", 0.9), ("vdw", 0.7), ("peng_robinson", 0.9),
+                                             ("peng_robinson", 0.8), ("carnahan_starling", 0.9),
+                                             ("carnahan_starling", 0.7)])
+def test_maxwell_equal_areas(name, theta_star):
+    e = EOS[name](theta_star)
+    g, l = e.maxwell()
+    assert g < e.rho_scale() < l
+    assert abs(e.mu(g) - e.mu(l)) <= 1e-14 and abs(e.p(g) - e.p(l)) <= 1e-14
     # the equal-area rule: the integral of p - p_sat over 1/rho between the phases vanishes
     v = np.linspace(1 / l, 1 / g, 200001)
     integrand = e.p(1 / v) - e.p(g)
     assert abs(np.trapezoid(integrand, v)) <= 1e-7 * e.p(g) * (1 / g - 1 / l)
+
+
+def test_peng_robinson_has_no_coexistence_far_below_critical():
+    """With the printed constants (no temperature factor in a) the Peng-Robinson type loop at
+    theta/theta_c = 0.7 never rises back to a positive pressure before the attraction's pole:
+    no liquid can coexist with a vapour there."""
+    with pytest.raises(ValueError):
+        ni.PengRobinson(0.7).maxwell()
 
 
 def test_stencil_orders():
@@ -62,10 +127,10 @@ def test_force_conserves_global_momentum():
     assert np.abs(rho[None] * g).max() > 1e-2  # and it is not trivially zero
 
 
-def interface(theta_star=0.9, kappa=0.05, tau=0.5, nx=64, steps=1500, width=3.0):
+def interface(theta_star=0.9, kappa=0.05, tau=0.5, nx=64, steps=1500, width=3.0, eos=ni.VdW):
     """A liquid slab in vapour (flat interfaces normal to x), started at the Maxwell densities
     with tanh profiles; returns the bulk densities after `steps` and Maxwell's."""
-    e = ni.VdW(theta_star)
+    e = eos(theta_star)
     g, l = e.maxwell()
     x = np.array([[[[ix + 0.5 * s for ix in range(nx)]]] for s in (0, 1)])
     rho = g + (l - g) * 0.5 * (np.tanh((x - nx / 4) / width) - np.tanh((x - 3 * nx / 4) / width))
@@ -75,13 +140,21 @@ def interface(theta_star=0.9, kappa=0.05, tau=0.5, nx=64, steps=1500, width=3.0)
     return r[0, 0, 0, 0], r[0, 0, 0, nx // 2], g, l
 
 
-def test_flat_interface_reaches_maxwell_densities():
-    gas, liquid, g, l = interface()
-    # measured: vapour +1.5%, liquid +0.13% (kappa = 0.05 gives an interface of a few cells)
-    assert abs(gas / g - 1) <= 0.02 and abs(liquid / l - 1) <= 0.003, (gas, liquid, g, l)
+# (equation of state, kappa, vapour bound, liquid bound); measured: van der Waals +1.5% / +0.13%,
+# Peng-Robinson type +1.9% / +0.23% (density ratio 9.1), Carnahan-Starling +3.1% / +0.21% (5.5).
+# The two with the Carnahan-Starling repulsion take kappa = 0.02: at 0.05 the Peng-Robinson
+# slab diverges.
+INTERFACES = [("vdw", 0.05, 0.02, 0.003), ("peng_robinson", 0.02, 0.025, 0.004),
+              ("carnahan_starling", 0.02, 0.04, 0.004)]
 
 
-def _sound_speed(rho0, nx, eos, eps=1e-4, tau=0.5):
+@pytest.mark.parametrize("name,kappa,gas_tol,liquid_tol", INTERFACES)
+def test_flat_interface_reaches_maxwell_densities(name, kappa, gas_tol, liquid_tol):
+    gas, liquid, g, l = interface(kappa=kappa, eos=EOS[name])
+    assert abs(gas / g - 1) <= gas_tol and abs(liquid / l - 1) <= liquid_tol, (gas, liquid, g, l)
+
+
+def _sound_speed(rho0, nx, eos, eps=1e-4, tau=0.5, kappa=0.05):
     """Speed of a standing density wave of one wavelength over nx cells in a uniform phase, from
     the zero crossings of its amplitude over about 1.6 periods."""
     x = np.array([[[[ix + 0.5 * s for ix in range(nx)]]] for s in (0, 1)])
@@ -93,7 +166,7 @@ def _sound_speed(rho0, nx, eos, eps=1e-4, tau=0.5):
     amp = []
     for _ in range(int(1.6 * 2 * np.pi / (k * np.sqrt(cs2)))):
         amp.append(((f.sum(axis=1) - rho0) * cosx).sum() / (cosx * cosx).sum())
-        f = ni.step(f, tau, eos, 0.05)
+        f = ni.step(f, tau, eos, kappa)
     a = np.array(amp)
     zc = [i + a[i] / (a[i] - a[i + 1]) for i in range(len(a) - 1) if a[i] * a[i + 1] < 0]
     return np.pi / (k * np.diff(zc).mean()), np.sqrt(cs2)
@@ -106,4 +179,18 @@ def test_sound_speed_in_a_nonideal_phase(rho0):
     c128, _ = _sound_speed(rho0, 128, e)
     e64, e128 = abs(c64 / exact - 1), abs(c128 / exact - 1)
     assert e64 <= 3e-3, (c64, exact)  # measured 1.2e-3 (vapour), 1.8e-3 (liquid)
+    assert e64 / e128 >= 3.5, (e64, e128)  # second order: 4.0 measured
+
+
+@pytest.mark.parametrize("phase", [0, 1])
+def test_sound_speed_in_peng_robinson_phases(phase):
+    """Sec. "Sound propagation in a nonideal gas": a small wave in each coexisting phase of the
+    Peng-Robinson type fluid of Eq. (cspreos) at theta/theta_c = 0.9 (vapour 0.272, liquid 2.470)
+    travels at sqrt(dp/drho); kappa = 0.02, with which its interface is stable."""
+    e = ni.PengRobinson(0.9)
+    rho0 = e.maxwell()[phase]
+    c64, exact = _sound_speed(rho0, 64, e, kappa=0.02)
+    c128, _ = _sound_speed(rho0, 128, e, kappa=0.02)
+    e64, e128 = abs(c64 / exact - 1), abs(c128 / exact - 1)
+    assert e64 <= 4e-3, (c64, exact)  # measured 1.6e-3 (vapour), 2.7e-3 (liquid)
     assert e64 / e128 >= 3.5, (e64, e128)  # second order: 4.0 measured
