@@ -28,6 +28,8 @@ Pins, each independent of the oracle's formula:
     second order in the wavenumber: the van der Waals fluid, and the
     experiment of Sec. "Sound propagation in a nonideal gas" itself, the
     Peng-Robinson type fluid at its coexisting phase densities."""
+import os
+
 import numpy as np
 import pytest
 
@@ -223,3 +225,46 @@ def test_quench_separates_into_maxwell_phases(name, kappa, gas_tol, liquid_tol):
     assert abs(rho.sum() - rho0.sum()) <= 1e-12 * rho.size
     gas, liquid = np.quantile(rho, 0.05), np.quantile(rho, 0.95)
     assert abs(gas / g - 1) <= gas_tol and abs(liquid / l - 1) <= liquid_tol, (gas, liquid, g, l)
+
+
+def _golden_spurious():
+    rows = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "spurious_currents.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                name, pr, cs = line.split()
+                rows[name] = {"peng_robinson": float(pr), "carnahan_starling": float(cs)}
+    return rows
+
+
+def droplet(name, eta, kappa=0.02, n=48, steps=1000, theta_star=0.9):
+    """A static cylindrical liquid drop (radius n/4, tanh profile of width 2) in its vapour on an
+    n x n x 1 grid. Returns the largest fluid speed |sum f c / rho + g / 2| after `steps` (the
+    spurious current; the exact answer is 0) and the vapour density relative to Maxwell's."""
+    e = EOS[name](theta_star)
+    g, l = e.maxwell()
+    s = np.arange(2)[:, None, None, None] * 0.5
+    x = np.arange(n)[None, None, None, :] + s
+    y = np.arange(n)[None, None, :, None] + s
+    r = np.sqrt((x - n / 2) ** 2 + (y - n / 2) ** 2) + np.zeros((2, 1, n, n))
+    rho = g + (l - g) * 0.5 * (1 - np.tanh((r - n / 4) / 2.0))
+    f = oracle.init_fields(rho, np.zeros((3,) + rho.shape), np.full(rho.shape, TH0))
+    f = ni.step(f, 0.5, e, kappa, nsteps=steps, eta=eta)
+    fpre = oracle.stream(f)
+    rr = fpre.sum(axis=1)
+    u = np.einsum("sqzyx,qa->aszyx", fpre, oracle.velocities()[0]) / rr + 0.5 * ni.force(rr, e, kappa, eta)
+    return np.sqrt((u ** 2).sum(0)).max(), rr.min() / g - 1
+
+
+@pytest.mark.parametrize("name", ["peng_robinson", "carnahan_starling"])
+def test_eta_half_reduces_spurious_currents(name):
+    """The printed table: Eq. (gradientFinal) with eta = 1/2 has smaller spurious currents than
+    with eta = 1 (ratios 0.59 and 0.67 there). Measured on a 48 x 48 drop: 0.79 (Peng-Robinson
+    type) and 0.69 (Carnahan-Starling); the vapour density is also closer to Maxwell's (+6.3%
+    against +25%, and +6.4% against +16%, the drop's Laplace pressure included)."""
+    paper = _golden_spurious()
+    assert paper["current_eta_half"][name] < paper["current_eta_1"][name]
+    u_half, gas_half = droplet(name, 0.5)
+    u_one, gas_one = droplet(name, 1.0)
+    assert u_half <= 0.85 * u_one, (u_half, u_one)
+    assert abs(gas_half) < 0.5 * abs(gas_one), (gas_half, gas_one)
