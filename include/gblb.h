@@ -256,6 +256,14 @@ lb_status lb_wall_density(lb_ctx *ctx, double *rho_w);
 #define LB_EOS_PENG_ROBINSON 2
 #define LB_EOS_CARNAHAN_STARLING 3
 
+/* The constants a, b of equation of state eos (LB_EOS_*) whose critical point is
+ * (rho_c, theta_c = theta0 / theta_star), for the lattice temperature theta0 of
+ * lb_theta0(): the relations listed above, the Carnahan-Starling packing
+ * fraction solved by bisection to round-off.  Host only (no device, no context);
+ * a and b are caller-owned outputs.  LB_ERR_ARG for an unknown eos, NULL
+ * outputs, or theta_star, rho_c not positive and finite. */
+lb_status lb_nonideal_constants(int eos, double theta_star, double rho_c, double *a, double *b);
+
 /* Isothermal nonideal fluid (Sec. "Nonideal Fluids and two-phase flow"): with
  * eos != 0 (one of LB_EOS_*) each step adds the force of the paper's
  * momentum-conserving formulation, Eq. (gradientFinal), for that equation of

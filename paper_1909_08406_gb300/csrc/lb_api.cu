@@ -612,6 +612,45 @@ lb_status lb_set_wall_columns(lb_ctx* c, const double* bottom, const double* top
     return set_wall_columns(c, p.data());
 }
 
+// Carnahan-Starling critical packing fraction: with g(p) = p Z(p), the critical point of
+// p = rho theta0 Z(b rho / 4) - a rho^2 needs g'(p) = p g''(p), i.e. the root in (0.01, 0.5) of
+// (1 + 4p + 4p^2 - 4p^3 + p^4)(1 - p) - p (8 + 20p - 4p^2), found by bisection.
+static double cs_critical_packing() {
+    auto h = [](double p) {
+        return (1 + 4 * p + 4 * p * p - 4 * p * p * p + p * p * p * p) * (1 - p) - p * (8 + 20 * p - 4 * p * p);
+    };
+    double lo = 0.01, hi = 0.5;  // h(lo) > 0 > h(hi)
+    for (int i = 0; i < 200 && hi - lo > 1e-17; ++i) {
+        const double mid = 0.5 * (lo + hi);
+        (h(mid) > 0 ? lo : hi) = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+lb_status lb_nonideal_constants(int eos, double theta_star, double rho_c, double* a, double* b) {
+    if (!a || !b || !(theta_star > 0.0) || !(rho_c > 0.0) || !isfinite(theta_star) || !isfinite(rho_c))
+        return LB_ERR_ARG;
+    const double theta_c = lattice().theta0 / theta_star;
+    switch (eos) {
+        case LB_EOS_VAN_DER_WAALS:
+            *b = 1.0 / (3.0 * rho_c);
+            *a = 27.0 * *b * theta_c / 8.0;
+            return LB_OK;
+        case LB_EOS_PENG_ROBINSON:  // the constants printed with Eq. (cspreos)
+            *a = 1.851427622 * theta_c / rho_c;
+            *b = 0.353748714 / rho_c;
+            return LB_OK;
+        case LB_EOS_CARNAHAN_STARLING: {
+            const double p = cs_critical_packing();
+            const double g1 = (1 + 4 * p + 4 * p * p - 4 * p * p * p + p * p * p * p) / ((1 - p) * (1 - p) * (1 - p) * (1 - p));
+            *b = 4.0 * p / rho_c;
+            *a = 0.5 * g1 * theta_c / rho_c;
+            return LB_OK;
+        }
+        default: return LB_ERR_ARG;
+    }
+}
+
 lb_status lb_set_nonideal(lb_ctx* c, int enable, double a, double b, double kappa, double eta) {
     if (!c) return LB_ERR_ARG;
     if (!enable) {

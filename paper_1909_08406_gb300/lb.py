@@ -89,6 +89,8 @@ def lib():
         L.lb_get_grid.restype = ctypes.c_int
         L.lb_set_nonideal.argtypes = [vp, ctypes.c_int, dp, dp, dp, dp]
         L.lb_set_nonideal.restype = ctypes.c_int
+        L.lb_nonideal_constants.argtypes = [ctypes.c_int, dp, dp, ctypes.POINTER(dp), ctypes.POINTER(dp)]
+        L.lb_nonideal_constants.restype = ctypes.c_int
         L.lb_sync.argtypes = [vp]
         L.lb_destroy.argtypes = [vp]
         L.lb_last_error.argtypes = [vp]
@@ -235,6 +237,17 @@ def lb_tune(ctx, reps=3):
 
 
 LB_EOS = {"vdw": 1, "peng_robinson": 2, "carnahan_starling": 3}
+
+
+def lb_nonideal_constants(eos, theta_star, rho_c=1.0):
+    """(a, b) of equation of state `eos` with its critical point at rho_c and
+    theta_c = theta0 / theta_star."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    kind = LB_EOS[eos] if isinstance(eos, str) else int(eos)
+    status = lib().lb_nonideal_constants(kind, float(theta_star), float(rho_c), ctypes.byref(a), ctypes.byref(b))
+    if status != LB_OK:
+        raise LbError(status, "lb_nonideal_constants: unknown equation of state or bad theta_star / rho_c")
+    return a.value, b.value
 
 
 def lb_set_nonideal(ctx, a=None, b=None, kappa=0.0, eta=0.5, eos="vdw"):

@@ -108,3 +108,23 @@ def test_wall_and_grid_entry_points_reject_null(L):
     assert L.lb_set_wall_columns(None, None, None) == -1
     assert L.lb_wall_density(None, None) == -1
     assert L.lb_get_grid(None, None) == -1
+
+
+@pytest.mark.parametrize("eos", ["vdw", "peng_robinson", "carnahan_starling"])
+@pytest.mark.parametrize("theta_star,rho_c", [(0.9, 1.0), (0.8, 0.13)])
+def test_nonideal_constants_match_oracle(L, eos, theta_star, rho_c):
+    """lb_nonideal_constants (host only) against the oracle's equations of state."""
+    from oracle import nonideal as ni
+    from paper_1909_08406_gb300 import lb
+    cls = {"vdw": ni.VdW, "peng_robinson": ni.PengRobinson, "carnahan_starling": ni.CarnahanStarling}[eos]
+    e = cls(theta_star, rho_c=rho_c)
+    a, b = lb.lb_nonideal_constants(eos, theta_star, rho_c)
+    assert a == pytest.approx(e.a, rel=1e-12) and b == pytest.approx(e.b, rel=1e-12)
+
+
+def test_nonideal_constants_reject_bad_arguments(L):
+    from paper_1909_08406_gb300 import lb
+    for args in [(0, 0.9, 1.0), (4, 0.9, 1.0), (1, 0.0, 1.0), (1, 0.9, -1.0), (2, float("nan"), 1.0)]:
+        with pytest.raises(lb.LbError) as e:
+            lb.lb_nonideal_constants(*args)
+        assert e.value.status == -1
