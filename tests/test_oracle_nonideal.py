@@ -280,3 +280,29 @@ def test_sound_speed_across_temperatures(theta_star, phase, tol):
     e = ni.PengRobinson(theta_star)
     c, exact = _sound_speed(e.maxwell()[phase], 64, e, kappa=0.02)
     assert abs(c / exact - 1) <= tol, (c, exact)
+
+
+@pytest.mark.parametrize("tau", [0.5, 0.05])
+def test_forced_collision_changes_momentum_by_rho_g(tau):
+    """Eq. (momentumchange): the forced collision of Eq. (multiphaseEvolution) with
+    u = j / rho + g / 2 keeps the mass and adds exactly rho g to the momentum of every node,
+    for any tau (the forcing term carries no mass, its momentum is rho g, and the relaxation
+    removes the half added to u)."""
+    import ctypes
+    rng = np.random.default_rng(21)
+    nx, ny, nz = 4, 3, 2
+    shape = (2, nz, ny, nx)
+    rho = 1.0 + 0.3 * rng.random(shape)
+    u = 0.05 * rng.standard_normal((3,) + shape)
+    fpre = oracle.init_fields(rho, u, np.full(shape, TH0))
+    fpre = fpre * (1 + 0.01 * rng.standard_normal(fpre.shape))  # off equilibrium
+    g = np.ascontiguousarray(0.02 * rng.standard_normal((3,) + shape))
+    out = np.empty_like(fpre)
+    oracle.lib().or_collide_forced(ctypes.c_int64(nx), ctypes.c_int64(ny), ctypes.c_int64(nz), ctypes.c_double(tau),
+                                   ctypes.c_int(1), oracle._p(fpre), oracle._p(g), oracle._p(out), oracle._threads(1))
+    c = oracle.velocities()[0]
+    r0, r1 = fpre.sum(axis=1), out.sum(axis=1)
+    j0 = np.einsum("sqzyx,qa->aszyx", fpre, c)
+    j1 = np.einsum("sqzyx,qa->aszyx", out, c)
+    assert np.abs(r1 - r0).max() <= 1e-14
+    assert np.abs(j1 - (j0 + r0[None] * g)).max() <= 1e-14
