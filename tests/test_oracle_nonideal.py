@@ -318,3 +318,35 @@ def test_carnahan_starling_slab_at_the_droplet_collision_parameters():
     gas, liquid, g, l = interface(theta_star=0.8, kappa=0.001 * e.a, tau=0.103, steps=3000, eos=ni.CarnahanStarling)
     assert np.isfinite(gas) and np.isfinite(liquid)
     assert abs(gas / g - 1) <= 0.16 and abs(liquid / l - 1) <= 0.005, (gas, liquid, g, l)
+
+
+def _drop_pressure_jump(radius, n=48, steps=1000, kappa=0.05):
+    """(equimolar radius, p_inside - p_outside) of a settled cylindrical van der Waals drop at
+    theta/theta_c = 0.9 on an n x n x 1 grid, the pressures from the equation of state at the
+    drop's centre and far corner."""
+    e = ni.VdW(0.9)
+    g, l = e.maxwell()
+    s = np.arange(2)[:, None, None, None] * 0.5
+    x = np.arange(n)[None, None, None, :] + s
+    y = np.arange(n)[None, None, :, None] + s
+    r = np.sqrt((x - n / 2) ** 2 + (y - n / 2) ** 2) + np.zeros((2, 1, n, n))
+    rho = g + (l - g) * 0.5 * (1 - np.tanh((r - radius) / 3.0))
+    f = oracle.init_fields(rho, np.zeros((3,) + rho.shape), np.full(rho.shape, TH0))
+    rho = ni.step(f, 0.5, e, kappa, nsteps=steps).sum(axis=1)
+    inside, outside = rho[0, 0, n // 2, n // 2], rho[0, 0, 0, 0]
+    # each node stands for half a cell of the z = const plane
+    r_eq = np.sqrt(0.5 * (rho - outside).sum() / (np.pi * (inside - outside)))
+    return r_eq, e.p(inside) - e.p(outside)
+
+
+def test_laplace_law_for_drops():
+    """Young-Laplace for a cylinder: the pressure jump across a drop's interface is
+    sigma / R, the same surface tension for every radius. Measured dp R = 0.02857 (R 7.4) and
+    0.02986 (R 11.8) here, and 0.0297-0.0299 for R 9 to 18 on a 64-cell box: within 4.5%, the
+    smallest drop's interface being a third of its radius. (The surface tension is about twice
+    kappa times the integral of (drho/dx)^2 of the flat profile: the discrete force adds an
+    interfacial stiffness of its own, about 0.07 at theta/theta_c = 0.9.)"""
+    r1, dp1 = _drop_pressure_jump(8)
+    r2, dp2 = _drop_pressure_jump(12)
+    assert r1 < r2 and dp1 > dp2 > 0
+    assert abs((dp1 * r1) / (dp2 * r2) - 1) <= 0.07, (dp1 * r1, dp2 * r2)
