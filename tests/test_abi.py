@@ -128,3 +128,20 @@ def test_nonideal_constants_reject_bad_arguments(L):
         with pytest.raises(lb.LbError) as e:
             lb.lb_nonideal_constants(*args)
         assert e.value.status == -1
+
+
+@pytest.mark.parametrize("header", ["gblb.h", "gblb_surrogate.h"])
+@pytest.mark.parametrize("lang,std", [("c", "-std=c99"), ("c++", "-std=c++11")])
+def test_public_headers_compile_as_c_and_cpp(header, lang, std, tmp_path):
+    """The boundary's headers are plain C: a C99 or C++11 program that includes one and calls
+    nothing still compiles (no torch, CUDA or C++-only types in the signatures)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    src = tmp_path / ("main." + ("c" if lang == "c" else "cpp"))
+    src.write_text('#include "%s"\nint main(void) { return 0; }\n' % header)
+    subprocess.run([cc, std, "-Wall", "-Werror", "-pedantic", "-I", inc, "-fsyntax-only", str(src)], check=True,
+                   capture_output=True)
