@@ -145,3 +145,41 @@ def test_public_headers_compile_as_c_and_cpp(header, lang, std, tmp_path):
     src.write_text('#include "%s"\nint main(void) { return 0; }\n' % header)
     subprocess.run([cc, std, "-Wall", "-Werror", "-pedantic", "-I", inc, "-fsyntax-only", str(src)], check=True,
                    capture_output=True)
+
+
+C_CONSUMER = r"""
+#include <math.h>
+#include <stdio.h>
+#include "gblb.h"
+int main(void) {
+    int c2[41 * 3];
+    double w[41], sum = 0.0, a = 0.0, b = 0.0;
+    if (lb_velocity_set(c2, w) != LB_OK) return 1;
+    for (int i = 0; i < 41; ++i) sum += w[i];
+    if (lb_nonideal_constants(LB_EOS_VAN_DER_WAALS, 0.9, 1.0, &a, &b) != LB_OK) return 2;
+    if (lb_nonideal_constants(7, 0.9, 1.0, &a, &b) != LB_ERR_ARG) return 3;
+    printf("%.17g %.17g %.17g\n", lb_theta0(), sum, b);
+    return 0;
+}
+"""
+
+
+def test_plain_c_program_links_and_calls_the_library(L, tmp_path):
+    """A C99 program links against the shared library and calls its host-only entry points
+    (velocity set, theta0, equation-of-state constants): the boundary needs no Python."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no host compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    libdir = os.path.dirname(L._name)
+    src, exe = tmp_path / "consumer.c", tmp_path / "consumer"
+    src.write_text(C_CONSUMER)
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(root, "include"), str(src), "-o", str(exe),
+                    "-L", libdir, "-lgblb", "-Wl,-rpath," + libdir, "-lm"], check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    theta0, wsum, b = (float(v) for v in out)
+    assert theta0 == pytest.approx(oracle.theta0(), rel=1e-15)
+    assert wsum == pytest.approx(1.0, abs=1e-15)
+    assert b == pytest.approx(1.0 / 3.0, rel=1e-15)
