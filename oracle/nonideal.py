@@ -1,5 +1,6 @@
-"""Isothermal nonideal (van der Waals) fluid on the RD3Q41 grid (Sec. "Nonideal
-Fluids and two-phase flow" and Appendix A).
+"""Isothermal nonideal fluid on the RD3Q41 grid (Sec. "Nonideal Fluids and
+two-phase flow" and Appendix A): van der Waals, the Peng-Robinson type of
+Eq. (cspreos) and Carnahan-Starling equations of state.
 
 TEST INFRASTRUCTURE ONLY: loaded by the tests, never by the library.
 
@@ -12,7 +13,8 @@ Written from the paper, step by step:
         grad4_a psi = grad2_a psi - (theta_hat / 2) grad2_a (lap psi)      Eq. (gradient4)
   - the van der Waals free energy, split into the ideal part theta0 rho
     (ln rho - 1) and the rest: F_nid = -theta0 rho ln(1 - b rho) - a rho^2,
-    mu_nid = dF_nid/drho, p = rho theta0 / (1 - b rho) - a rho^2;
+    mu_nid = dF_nid/drho, p = rho theta0 / (1 - b rho) - a rho^2; the other two
+    split the same way (classes PengRobinson and CarnahanStarling);
   - the force of the momentum-conserving formulation, Eq. (gradientFinal):
         rho g_a = -[rho grad2_a mu_nid + mu_nid grad2_a rho
                     - eta grad2_a F_nid - (1 - eta) grad4_a F_nid
@@ -23,7 +25,11 @@ Written from the paper, step by step:
     from it, then the forced BGK collision of Eq. (multiphaseEvolution)
     (or_collide_forced in the C oracle);
   - Maxwell's equal-area construction of the coexisting densities, by
-    solving mu(rho_g) = mu(rho_l) and p(rho_g) = p(rho_l)."""
+    solving mu(rho_g) = mu(rho_l) and p(rho_g) = p(rho_l).
+
+Pinned by tests/test_oracle_nonideal.py (critical points, thermodynamic
+consistency, Maxwell, stencil orders, momentum conservation, the forced
+collision's momentum change, interfaces, quench, Laplace, sound speed)."""
 import numpy as np
 
 import oracle
