@@ -25,6 +25,11 @@
  *   - BGK collision and streaming ............. Sec. II, discrete BGK update
  *   - bcc grid: two sc lattices offset by
  *     half a cell in every direction .......... Sec. IV
+ *   - forced collision of the nonideal fluid .. Sec. "Nonideal Fluids and
+ *                                               two-phase flow", Eq.
+ *                                               (multiphaseEvolution); pinned by
+ *                                               its momentum change, Eq.
+ *                                               (momentumchange)
  *
  * Readings where the paper is silent or garbled (each is listed in the design
  * notes of the repository):
