@@ -355,3 +355,40 @@ def test_laplace_law_for_drops():
     r2, dp2 = _drop_pressure_jump(12)
     assert r1 < r2 and dp1 > dp2 > 0
     assert abs((dp1 * r1) / (dp2 * r2) - 1) <= 0.07, (dp1 * r1, dp2 * r2)
+
+
+def _plane_wave_errors(m, n=48):
+    """Relative errors of grad2 and lap on sin(k.x), k = 2 pi m / n, over the whole bcc grid (the
+    projection of the discrete result on the exact one, minus 1), and |k|^2."""
+    s = np.arange(2)[:, None, None, None] * 0.5
+    z = np.arange(n)[None, :, None, None] + s
+    y = np.arange(n)[None, None, :, None] + s
+    x = np.arange(n)[None, None, None, :] + s
+    k = 2 * np.pi * np.asarray(m, float) / n
+    phase = k[0] * x + k[1] * y + k[2] * z
+    psi = np.sin(phase)
+    exact = np.array([k[a] * np.cos(phase) for a in range(3)])
+    g = ni.grad2(psi)
+    kk = float(k @ k)
+    return kk, (g * exact).sum() / (exact * exact).sum() - 1, (ni.lap(psi) * psi).sum() / (-kk * (psi * psi).sum()) - 1
+
+
+def test_stencil_is_isotropic():
+    """Appendix A: the 15-velocity stencil's derivatives err isotropically at leading order, with
+    theta_hat = 1/6: on a plane wave grad2 is short by theta_hat k^2 / 2 and the Laplacian by
+    theta_hat k^2 / 4 whatever the wave's direction. Along x the stencil sums in closed form to
+    (sin k + 4 sin(k/2)) / (3k) = 1 - k^2/12 + k^4/320 - ... and
+    12 (1/2 - cos(k)/18 - 4 cos(k/2)/9) / k^2 = 1 - k^2/24 + ...; the direction enters only at
+    k^4 (the stencil's sixth moments are not isotropic): measured differences 1.6e-5 and 5e-6
+    against errors of 1.3e-2 and 6.4e-3 for |k| = 2 pi 3 / 48 along (1,0,0) and (2,2,1)/3."""
+    th = 1.0 / 6.0
+    kk, g_axis, l_axis = _plane_wave_errors((3, 0, 0))
+    kk2, g_diag, l_diag = _plane_wave_errors((2, 2, 1))
+    assert kk == pytest.approx(kk2, rel=1e-14)
+    for g_err, l_err in ((g_axis, l_axis), (g_diag, l_diag)):
+        assert g_err / (-th * kk / 2) == pytest.approx(1.0, abs=0.02)
+        assert l_err / (-th * kk / 4) == pytest.approx(1.0, abs=0.02)
+    k = np.sqrt(kk)
+    assert g_axis == pytest.approx((np.sin(k) + 4 * np.sin(k / 2)) / (3 * k) - 1, abs=1e-12)
+    assert l_axis == pytest.approx(12 * (0.5 - np.cos(k) / 18 - 4 * np.cos(k / 2) / 9) / kk - 1, abs=1e-12)
+    assert abs(g_axis - g_diag) <= 1e-4 and abs(l_axis - l_diag) <= 5e-5
