@@ -21,6 +21,10 @@
  *     misses it at O(u^3 eta^2)).
  *   - kinematic viscosity nu = tau theta_0; thermal diffusivity = nu
  *     (Prandtl number 1); isentropic sound speed sqrt(5 theta_0 / 3).
+ *   - optional modes: the exact entropic equilibrium (LB_FLAG_ENTROPIC),
+ *     kinetic walls normal to z (lb_set_walls), and the isothermal nonideal
+ *     fluid with the van der Waals, Peng-Robinson type or Carnahan-Starling
+ *     equation of state (lb_set_nonideal), each documented at its call.
  *
  * Array layouts (all C order, x fastest):
  *   scalar field   a[s][nz][ny][nx]            s = 0 (A), 1 (B)
