@@ -134,7 +134,7 @@ def test_force_conserves_global_momentum():
     assert np.abs(total_mu).max() > 1e-3
 
 
-def interface(theta_star=0.9, kappa=0.05, tau=0.5, nx=64, steps=1500, width=3.0, eos=ni.VdW):
+def interface(theta_star=0.9, kappa=0.05, tau=0.5, nx=64, steps=1500, width=3.0, eos=ni.VdW, eta=0.5):
     """A liquid slab in vapour (flat interfaces normal to x), started at the Maxwell densities
     with tanh profiles; returns the bulk densities after `steps` and Maxwell's."""
     e = eos(theta_star)
@@ -142,7 +142,7 @@ def interface(theta_star=0.9, kappa=0.05, tau=0.5, nx=64, steps=1500, width=3.0,
     x = np.array([[[[ix + 0.5 * s for ix in range(nx)]]] for s in (0, 1)])
     rho = g + (l - g) * 0.5 * (np.tanh((x - nx / 4) / width) - np.tanh((x - 3 * nx / 4) / width))
     f = oracle.init_fields(rho, np.zeros((3,) + rho.shape), np.full(rho.shape, TH0))
-    f = ni.step(f, tau, e, kappa, nsteps=steps)
+    f = ni.step(f, tau, e, kappa, nsteps=steps, eta=eta)
     r = f.sum(axis=1)
     return r[0, 0, 0, 0], r[0, 0, 0, nx // 2], g, l
 
@@ -392,3 +392,15 @@ def test_stencil_is_isotropic():
     assert g_axis == pytest.approx((np.sin(k) + 4 * np.sin(k / 2)) / (3 * k) - 1, abs=1e-12)
     assert l_axis == pytest.approx(12 * (0.5 - np.cos(k) / 18 - 4 * np.cos(k / 2) / 9) / kk - 1, abs=1e-12)
     assert abs(g_axis - g_diag) <= 1e-4 and abs(l_axis - l_diag) <= 5e-5
+
+
+@pytest.mark.parametrize("name,kappa", [("vdw", 0.05), ("peng_robinson", 0.02)])
+def test_eta_half_brings_the_vapour_to_maxwell(name, kappa):
+    """The densities figure of the discretisation section: Eq. (gradientFinal) with eta = 1/2
+    (half of the free-energy gradient at fourth order) puts the coexisting densities of a flat
+    interface closer to Maxwell's than eta = 1 (all at second order). Measured vapour errors:
+    +1.5% against +5.9% (van der Waals), +1.9% against +21.8% (Peng-Robinson type)."""
+    gas_h, liq_h, g, l = interface(kappa=kappa, eos=EOS[name], eta=0.5)
+    gas_1, liq_1, _, _ = interface(kappa=kappa, eos=EOS[name], eta=1.0)
+    assert abs(gas_h / g - 1) <= 0.4 * abs(gas_1 / g - 1), (gas_h, gas_1, g)
+    assert abs(liq_h / l - 1) <= 0.5 * abs(liq_1 / l - 1), (liq_h, liq_1, l)
