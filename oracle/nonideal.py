@@ -58,16 +58,18 @@ def shifted(field, c2):
     return out
 
 
-def grad2(psi):
+def grad2(psi, axis=None):
+    """All three components of the gradient, or only component `axis` (the same sums)."""
+    axes = range(3) if axis is None else (axis,)
     g = np.zeros((3,) + psi.shape)
     for c2, w in _STENCIL:
-        if c2 == (0, 0, 0):
+        if not any(c2[a] for a in axes):
             continue
         sh = shifted(psi, c2)
-        for a in range(3):
+        for a in axes:
             if c2[a]:
                 g[a] += w * (0.5 * c2[a]) * sh
-    return g / THETA_HAT
+    return g / THETA_HAT if axis is None else g[axis] / THETA_HAT
 
 
 def lap(psi):
@@ -262,7 +264,7 @@ def force(rho, eos, kappa, eta=0.5):
         div = np.zeros_like(rho)
         for b in range(3):
             I_ab = grho[a] * grho[b] + (-(0.5 * gsq) - rho * lrho if a == b else 0.0)
-            div += grad2(I_ab)[b]
+            div += grad2(I_ab, axis=b)
         rho_g[a] -= kappa * div
     return rho_g / rho
 
