@@ -30,6 +30,8 @@ Written from the paper, step by step:
 Pinned by tests/test_oracle_nonideal.py (critical points, thermodynamic
 consistency, Maxwell, stencil orders, momentum conservation, the forced
 collision's momentum change, interfaces, quench, Laplace, sound speed)."""
+import functools
+
 import numpy as np
 
 import oracle
@@ -48,7 +50,7 @@ for sx in (1, -1):
             _STENCIL.append(((sx, sy, sz), 2.0 / 36.0))
 
 
-def shifted(field, c2):
+def _shifted_by_roll(field, c2):
     """field at x + c for every node; field[s][z][y][x] on the bcc grid, c2 = 2c (doubled)."""
     out = np.empty_like(field)
     for s in (0, 1):
@@ -56,6 +58,17 @@ def shifted(field, c2):
         dx, dy, dz = ((s + c2[0]) - t) // 2, ((s + c2[1]) - t) // 2, ((s + c2[2]) - t) // 2
         out[s] = np.roll(field[t], shift=(-dz, -dy, -dx), axis=(0, 1, 2))
     return out
+
+
+@functools.lru_cache(maxsize=None)
+def _shift_index(shape, c2):
+    """The same map as flat indices: _shifted_by_roll applied to the node numbers."""
+    return _shifted_by_roll(np.arange(int(np.prod(shape))).reshape(shape), c2).ravel()
+
+
+def shifted(field, c2):
+    """field at x + c for every node (_shifted_by_roll, as one gather)."""
+    return field.ravel()[_shift_index(field.shape, c2)].reshape(field.shape)
 
 
 def grad2(psi, axis=None):
