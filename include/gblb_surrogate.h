@@ -5,7 +5,7 @@
  *
  * The paper (arXiv:1909.08406) has no learned component; this module is the
  * project's addition: a network trained on data the solver generates, with
- * the plain lattice Boltzmann method as its fallback and as the judge of its
+ * the plain lattice Boltzmann method as its fallback and as the arbiter of its
  * rollout error.
  *
  * Tensors are channels-last, periodic volumes: x[b][z][y][x][c] (NDHWC),

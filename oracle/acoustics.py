@@ -1,6 +1,6 @@
 """Exact linear-acoustics solution of the 3D spherical pulse (Sec. VII, "3D
 acoustic spherical pulse source").  TEST INFRASTRUCTURE ONLY, like the rest of
-``oracle/``: used by ``tests/`` to judge whole-step runs of the solver and of
+``oracle/``: used by ``tests/`` to check whole-step runs of the solver and of
 the oracle against physics, never by the library.
 
 An initial density pulse rho' = eps exp(-alpha r^2) with zero velocity, in a

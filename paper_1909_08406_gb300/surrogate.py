@@ -1,7 +1,7 @@
 """Learned surrogate: a 3D convolutional neural operator that advances the
 macroscopic fields (rho, u, theta) of the RD3Q41 solver K lattice Boltzmann
 steps per application, trained on data the solver generates, with the plain
-LB method as its fallback and as the judge of its rollout error.
+LB method as its fallback and as the arbiter of its rollout error.
 
 Network (6 layers, 3x3x3 periodic convolutions, BF16 weights and activations,
 FP32 accumulation, all in the kernels of include/gblb_surrogate.h):
@@ -185,7 +185,7 @@ def evaluate(net, data, batch=4):
 
 def rollout(net, seed, hops=20, hop=50, n=64, threshold=1e-3, fallback=True):
     """Judged rollout from one Gaussian-pulse initial condition: the surrogate advances the
-    fields hop by hop; LB runs alongside as the judge.  After each hop the relative L2 error
+    fields hop by hop; LB runs alongside as the arbiter.  After each hop the relative L2 error
     of the predicted fields against LB is measured; above `threshold` (with fallback on) the
     state is reset to LB's (an LB fallback).  Errors: over the normalised deviation channels
     ('signal') and over the full state (rho, u, theta/theta0) ('state'): with equal channel
