@@ -28,6 +28,8 @@ thermal tests, Secs. VI-VIII):
   * ``shear_wave``         transverse velocity wave u_y = U sin(2 pi x / nx)
   * ``batch_sweep``        per-simulation grid edges, tau and amplitudes
   * ``random_fields``      seeded smooth-ish random fields for parity tests
+  * ``droplet_pair``       two liquid drops in their vapour approaching each other
+                           (Sec. "Droplet Collision")
 """
 from __future__ import annotations
 
@@ -234,3 +236,32 @@ def batch_sweep(count=64, seed=4, edges=(32, 48, 64, 96, 128), tau_range=(0.51, 
     tau = rng.uniform(*tau_range, size=count)
     amp = np.exp(rng.uniform(math.log(amp_range[0]), math.log(amp_range[1]), size=count))
     return [BatchSim(int(a), float(b), float(c)) for a, b, c in zip(n, tau, amp)]
+
+
+def droplet_pair(nx, ny, nz, theta0, rho_gas, rho_liquid, diameter=45.0, separation=30.0, width=5.0, u0=0.2,
+                 offset=0.0, device="cpu"):
+    """Two liquid drops in their vapour approaching each other along x (Sec. "Droplet
+    Collision": a 160 x 200 x 200 box, diameter 45, interface width 5, separation 30, relative
+    speed 0.2).  Drop k has the profile phi_k = (1 - tanh(2 (r_k - R) / width)) / 2 about its
+    centre, the centres at the box centre -+ (diameter + separation) / 2 in x (separation is
+    read as the gap between the drops' surfaces: their centres 30 apart would overlap drops of
+    diameter 45), the second one shifted by `offset` in y (the impact parameter); distances
+    are to the nearest periodic image.  Density
+    rho_gas + (rho_liquid - rho_gas) max(phi_1, phi_2); velocity u_x = (u0 / 2)(phi_1 - phi_2),
+    so the vapour starts at rest; theta = theta0."""
+    X, Y, Z = node_positions(nx, ny, nz, device)
+    R = 0.5 * diameter
+    cx, cy, cz = nx / 2.0, ny / 2.0, nz / 2.0
+    dx = 0.5 * (diameter + separation)
+
+    def image(d, n):  # nearest periodic image of a displacement
+        return torch.remainder(d + 0.5 * n, n) - 0.5 * n
+
+    r1 = torch.sqrt(image(X - (cx - dx), nx) ** 2 + image(Y - cy, ny) ** 2 + image(Z - cz, nz) ** 2)
+    r2 = torch.sqrt(image(X - (cx + dx), nx) ** 2 + image(Y - (cy + offset), ny) ** 2 + image(Z - cz, nz) ** 2)
+    phi1 = 0.5 * (1 - torch.tanh(2 * (r1 - R) / width))
+    phi2 = 0.5 * (1 - torch.tanh(2 * (r2 - R) / width))
+    rho = rho_gas + (rho_liquid - rho_gas) * torch.maximum(phi1, phi2)
+    ux = 0.5 * u0 * (phi1 - phi2)
+    zero = torch.zeros_like(rho)
+    return _fields(rho, ux, zero, zero.clone(), torch.full_like(rho, theta0))

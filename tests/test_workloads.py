@@ -62,3 +62,28 @@ def test_standing_wave_values():
     fl = wl.standing_wave(8, 1, 1, TH0, amplitude=1e-3)
     assert fl["rho"][1, 0, 0, 1].item() == pytest.approx(1 + 1e-3 * math.sin(2 * math.pi * 1.5 / 8))
     assert torch.all(fl["theta"] == TH0)
+
+
+def test_droplet_pair():
+    """Two drops approaching head-on: liquid at the centres moving at +-u0/2, vapour at rest, no
+    net momentum (the pair is mirror-symmetric about the box centre, sub-lattices included), and
+    the liquid volume of two spheres with the tanh profile's correction."""
+    import math
+    nx, ny, nz, d, sep, u0 = 48, 40, 40, 16.0, 8.0, 0.2
+    f = wl.droplet_pair(nx, ny, nz, 0.3, 0.2, 2.4, diameter=d, separation=sep, width=3.0, u0=u0)
+    rho, u = f["rho"], f["u"]
+    assert rho.shape == (2, nz, ny, nx) and u.shape == (3, 2, nz, ny, nx)
+    c1 = int(nx / 2 - (d + sep) / 2)  # centre of the left drop (an A node)
+    c2 = int(nx / 2 + (d + sep) / 2)
+    # at the centres tanh(-2R/width) = -1 + 1e-4
+    assert float(rho[0, nz // 2, ny // 2, c1]) == pytest.approx(2.4, abs=2e-4)
+    assert float(u[0, 0, nz // 2, ny // 2, c1]) == pytest.approx(u0 / 2, rel=1e-4)
+    assert float(u[0, 0, nz // 2, ny // 2, c2]) == pytest.approx(-u0 / 2, rel=1e-4)
+    assert float(rho[0, 0, 0, 0]) == pytest.approx(0.2, abs=1e-9) and abs(float(u[0, 0, 0, 0, 0])) <= 1e-9
+    assert abs(float((rho * u[0]).sum())) <= 1e-12 * float((rho * u[0]).abs().sum())
+    assert float(u[1:].abs().max()) == 0.0 and float((f["theta"] - 0.3).abs().max()) == 0.0
+    # phi = 1 / (1 + exp((r - R) / T)), T = width / 4: by the Sommerfeld expansion each drop holds
+    # (4 pi / 3)(R^3 + pi^2 T^2 R) of liquid
+    volume = 0.5 * float(((rho - 0.2) / (2.4 - 0.2)).sum())
+    R, T = d / 2, 3.0 / 4
+    assert volume == pytest.approx(2 * 4 / 3 * math.pi * (R ** 3 + math.pi ** 2 * T ** 2 * R), rel=0.01)
