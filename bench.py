@@ -299,7 +299,11 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": "MLUPS", "value": v, "unit": "MLUPS", "n_gpus": world, "steps": steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args, world),
+            "config": {"workload": f"thermoacoustic pulse, {box}^3 periodic bcc grid ({nodes} nodes), pulse sigma "
+                                   f"2 cells, nu = {NU}, FP64 oracle on the host cores (a bounded sample of the "
+                                   f"{args.n}^3 workload of the main line)",
+                       "grid": box, "nodes": nodes, "precision": "f64",
+                       "parallelism": f"host threads x{oracle.max_threads()}"},
             "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": oracle.max_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -160,9 +160,13 @@ lb_status lb_conserved(lb_ctx *ctx, double out[5]);
  * device memory, which every GPU that loads the library holds until the
  * process exits.  The first call on each device looks up that array's device
  * address (cudaGetSymbolAddress) with the device current; make that first
- * call before any stream capture.  All calls share the array: calls whose
- * work overlaps on the GPU race.  Each call writes every slot it reads, so no
- * state carries over between calls.  Error message: lb_conserved_noalloc_error. */
+ * call before any stream capture.  The address is kept for the life of the
+ * process; a device reset (cudaDeviceReset) or any other teardown of the
+ * device's primary context invalidates it, so do not call this entry point
+ * again after one.  All calls share the array: calls whose work overlaps on
+ * the GPU race.  Each call writes every slot it reads, so no state carries
+ * over between calls.  lb_conserved_noalloc_error returns the message of the
+ * calling thread's last failed call (the message is kept per host thread). */
 lb_status lb_conserved_noalloc(const void *populations, lb_grid grid, lb_precision precision, double *out,
                                void *cuda_stream);
 const char *lb_conserved_noalloc_error(void);

@@ -31,8 +31,7 @@
  *                                               its momentum change, Eq.
  *                                               (momentumchange)
  *
- * Readings where the paper is silent or garbled (each is listed in the design
- * notes of the repository):
+ * Readings where the paper is silent or garbled:
  *   - theta_0 is not printed: theta_0 = sum_i w_i c_ix^2 (Eq. allWeights).
  *   - w_0 is not printed: w_0 = 1 - sum of the 40 tabulated weights.
  *   - "Delta theta" in M_2, M_2' means eta = theta/theta_0 - 1, and

@@ -84,7 +84,9 @@ namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 double* g_partials_ptr[kMaxDevices] = {};
-std::string g_noalloc_msg;
+// Error message of the calling host thread's last failed call (errno-style, so that
+// threads failing at the same time do not write one string concurrently).
+thread_local std::string g_noalloc_msg;
 }  // namespace
 
 extern "C" {

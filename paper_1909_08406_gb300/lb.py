@@ -445,14 +445,40 @@ def _bind_noalloc():
 
 def lb_conserved_noalloc(populations, grid, precision, out, stream=None):
     """Conservation sums of stored populations (device tensor in the raw layout of lb_get_state)
-    into `out` (device float64 tensor of 5), with no device allocation."""
+    into `out` (device float64 tensor of 5), with no device allocation.  The tensors' element
+    types, sizes and device are checked here, before the call: a mismatch would otherwise become
+    an out-of-bounds access on the GPU."""
+    import torch
     L = _bind_noalloc()
-    pp, dev_in = _ptr(populations)
-    po, dev_out = _ptr(out, writable=True)
-    if not (dev_in and dev_out):
-        raise ValueError("populations and out must be device tensors")
+    if isinstance(precision, str):
+        if precision not in PRECISION:
+            raise ValueError(f"unknown precision {precision!r}")
+        prec = PRECISION[precision]
+    else:
+        prec = int(precision)
+    es = {PRECISION[k]: v for k, v in STORAGE_BYTES.items()}.get(prec)
+    if es is None:
+        raise ValueError(f"unknown precision {precision!r}")
+    if not (isinstance(populations, torch.Tensor) and isinstance(out, torch.Tensor)):
+        raise TypeError("populations and out must be torch tensors on the device")
+    if out.dtype != torch.float64 or out.numel() < 5:
+        raise ValueError("out must be a float64 tensor of at least 5 elements")
     nx, ny, nz = (int(v) for v in grid)
-    st = L.lb_conserved_noalloc(pp, _Grid(nx, ny, nz), PRECISION[precision] if isinstance(precision, str)
-                                else int(precision), po, _stream(stream))
+    if min(nx, ny, nz) < 1:
+        raise ValueError("grid extents must be >= 1")
+    if populations.element_size() != es:
+        raise ValueError(f"populations hold {populations.element_size()}-byte elements; precision {precision!r} "
+                         f"stores {es}-byte elements")
+    if populations.numel() != 2 * 41 * nx * ny * nz:
+        raise ValueError(f"populations hold {populations.numel()} elements, the grid needs 2*41*nx*ny*nz = "
+                         f"{2 * 41 * nx * ny * nz}")
+    if not (populations.is_cuda and out.is_cuda):
+        raise ValueError("populations and out must be device tensors")
+    here = torch.cuda.current_device()
+    if populations.device.index != here or out.device.index != here:
+        raise ValueError(f"populations and out must be on the current device (cuda:{here})")
+    pp, _ = _ptr(populations)
+    po, _ = _ptr(out, writable=True)
+    st = L.lb_conserved_noalloc(pp, _Grid(nx, ny, nz), prec, po, _stream(stream))
     if st != LB_OK:
         raise LbError(st, L.lb_conserved_noalloc_error().decode())

@@ -118,8 +118,7 @@ def test_judged_rollout_and_fallback(small_data):
 def test_trained_network_beats_identity_and_is_faster_than_lb(small_data):
     """What the trained network gains over the method without it: a hop-50 application costs less
     than the 50 LB steps it replaces (64^3), and after training its error is below the identity
-    map's (no change) on held-out data.  Its accuracy limits are measured by the experiment
-    script and stated in the design notes."""
+    map's (no change) on held-out data."""
     net = S.Surrogate(seed=2)
     S.train(net, small_data, iters=60, batch=4, lr=2e-3)
     held = S.make_dataset(8, hop=10, seed0=700000, t0_choices=(0, 20), per_batch=8)

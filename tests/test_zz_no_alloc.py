@@ -22,6 +22,26 @@ def test_rejects_more_planes_than_the_fixed_scratch():
     assert b"4096" in L.lb_conserved_noalloc_error()
 
 
+@pytest.mark.parametrize("bad", ["out_dtype", "out_size", "pop_dtype", "pop_size", "host"])
+def test_wrapper_rejects_mismatched_tensors(bad):
+    """The Python wrapper refuses tensors whose element type, size or device does not match the
+    grid and precision, before any call into the library (CPU tensors: nothing reaches a GPU)."""
+    shape = (4, 3, 2)
+    n = 2 * 41 * 4 * 3 * 2
+    pop = torch.zeros(n, dtype=torch.float16)
+    out = torch.zeros(5, dtype=torch.float64)
+    if bad == "out_dtype":
+        out = torch.zeros(5, dtype=torch.float32)
+    elif bad == "out_size":
+        out = torch.zeros(4, dtype=torch.float64)
+    elif bad == "pop_dtype":
+        pop = torch.zeros(n, dtype=torch.float32)
+    elif bad == "pop_size":
+        pop = torch.zeros(n - 1, dtype=torch.float16)
+    with pytest.raises(ValueError):
+        lb.lb_conserved_noalloc(pop, shape, "f16", out)
+
+
 @pytest.mark.gpu
 @pytest.mark.parametrize("prec", ["f64", "f32", "f16", "bf16"])
 def test_noalloc_matches_lb_conserved_twice(prec):
