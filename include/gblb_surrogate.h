@@ -48,7 +48,7 @@ typedef struct {
 int sg_conv3d_fwd(sg_shape s, int cin, int cout, const void *x, const void *w, const float *bias, int act,
                   int res_in, const void *add, float *z_out, void *y, void *stream);
 
-/* Kernel of the two convolution entry points above:
+/* Kernel of the two convolution entry points above and of sg_conv3d_wgrad:
  *   SG_CONV_TCGEN05  (default) 5th-generation tensor cores: tcgen05.mma with
  *                    the FP32 accumulator in tensor memory, M = 128 voxels,
  *                    N = cout, K = 16 per instruction; persistent CTAs with the
@@ -81,8 +81,14 @@ int sg_transpose_weights(int cin, int cout, const void *w, void *wt, void *strea
 
 /* Weight and bias gradients: dw[co][tap][ci] = sum_v dz[v][co] x[v + d(tap)][ci],
  * db[co] = sum_v dz[v][co] (FP32 out, overwritten).  Deterministic: partial
- * sums per voxel partition in `scratch` (sg_wgrad_scratch_bytes), reduced in
- * a fixed order. */
+ * sums per CTA (SG_CONV_TCGEN05) or per voxel partition (SG_CONV_MMA_SYNC) in
+ * `scratch` (sg_wgrad_scratch_bytes, enough for either), reduced in a fixed
+ * order.  SG_CONV_TCGEN05: per row of 64 voxels a tcgen05.mma GEMM over the
+ * row's voxels, with A = the x rows of the 9 (dz, dy) neighbours (M = 9 cin in
+ * tiles of 128) and B = the dz row in three copies shifted by dx (N =
+ * 3 cout), both read by TMA in their own [voxel][channel] layout (MN-major
+ * operands); the FP32 accumulators stay in tensor memory over all rows of a
+ * CTA.  Its timeouts are reported by sg_status, as the forward kernel's. */
 int64_t sg_wgrad_scratch_bytes(sg_shape s, int cin, int cout);
 int sg_conv3d_wgrad(sg_shape s, int cin, int cout, const void *x, const void *dz, float *dw, float *db,
                     void *scratch, void *stream);

@@ -952,6 +952,289 @@ __global__ void __launch_bounds__(384, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS));
 }
 
+// ---------------------------------------------------------------------------
+// Weight gradient on tcgen05 (TMA operands, accumulators in tensor memory).
+//
+//   dw[co][tap][ci] = sum_v dz[v][co] x[v + d(tap)][ci],  d(tap) = (dz, dy, dx)
+//
+// Over one row (b, z, y) of 64 voxels, with x' = x + dx taken periodically,
+//   sum_x dZ[b,z,y,x][co] X[b,z+dz,y+dy,x+dx][ci]
+//     = sum_x' X[b,z+dz,y+dy,x'][ci] dZ[b,z,y,x'-dx][co],
+// a GEMM with K = the 64 voxels x' of the row:
+//   A[m][k] = X row (z+dz, y+dy) at voxel k,  m = (dz, dy, ci): 9 cin rows,
+//   B[k][n] = dZ row (z, y) at voxel k - dx,  n = (dx, co):     N = 3 cout.
+// Both operands are MN-major, i.e. channels contiguous, which is the
+// activations' own [voxel][channel] layout, in the canonical no-swizzle
+// layout: 8 channels of one row form a column of 64 16-byte chunks (1 KB,
+// written by one TMA box); columns are 1 KB apart (SBO) and the K direction is
+// contiguous (LBO = 128 B), so the k-th 16-voxel step of an MMA is a start
+// address 256 B further on.  The 9 cin/8 channel groups of A are cut into
+// M = 128 tiles of 16 groups (the last tile padded with groups that are never
+// loaded and whose rows are discarded); B holds the dZ row in three copies
+// shifted by dx = -1, 0, +1: each copy is one 64-voxel box starting one voxel
+// before or after the row (every box lands on a 1 KB boundary), whose
+// out-of-range voxel the tensor map fills with zeros and a fixer warp then
+// overwrites with the periodic wrap voxel.  A CTA owns a contiguous range of rows and
+// accumulates each tile's D[128][3 cout] (FP32) in tensor memory over all of
+// them; the epilogue writes the CTA's partial dw, summed over CTAs in a fixed
+// order by k_wgrad_reduce.
+// Warp roles: warp 0 TMA producer, warp 1 MMA issuer (warp-uniform loops, one
+// elected lane issues), warp 2 wrap-voxel fixer, warps 4-7 epilogue (one
+// tensor-memory lane quarter each).  Every wait is bounded; on expiry the status flag is set and each
+// role waits, bounded, for its own asynchronous work before tensor memory is
+// freed.
+// ---------------------------------------------------------------------------
+template <int CIN, int COUT>
+struct WgCfg {
+    static constexpr int CG = CIN / 8;                  // channel groups of A per (dz, dy)
+    static constexpr int GROUPS = 9 * CG;               // column groups of A
+    static constexpr int NT = (GROUPS + 15) / 16;       // M = 128 tiles
+    static constexpr int N = 3 * COUT;                  // B columns: (dx, co)
+    static constexpr int NS = (N + 31) / 32 * 32;       // tensor-memory columns per tile (32-aligned)
+    static constexpr int NG = N / 8;                    // column groups of B
+    static constexpr int SB = 3;                        // B stages (one row each)
+    static constexpr int A_STAGE = 16 * 1024;
+    static constexpr int B_STAGE = NG * 1024;
+    static constexpr int SA = (220 * 1024 - SB * B_STAGE) / A_STAGE;  // A stages (one tile of one row each)
+    static constexpr int SMEM = SA * A_STAGE + SB * B_STAGE + 1024;
+    static constexpr int TMEM_USED = NT * NS;
+    static constexpr int TMEM_COLS = TMEM_USED <= 32 ? 32 : TMEM_USED <= 64 ? 64 : TMEM_USED <= 128 ? 128
+                                     : TMEM_USED <= 256 ? 256 : 512;
+    static constexpr int THREADS = 256;
+    // D F32, A and B BF16, both MN-major (bits 15, 16), N, M = 128
+    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                                      ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    static_assert(N % 16 == 0 && N <= 256, "N = 3 cout must be a multiple of 16, at most 256");
+    static_assert(TMEM_USED <= 512, "tensor memory");
+    static_assert(SMEM <= 232448, "shared memory");
+};
+
+// group g of A (0 .. 9 cin/8 - 1) -> (dz, dy, channel group): g = 3 ((dz+1) cin/8 + c) + (dy+1), so
+// that the three rows y - 1, y, y + 1 of one plane and channel group are consecutive groups (one
+// three-row box fills them)
+template <int CG>
+__device__ __forceinline__ void wg_group(int g, int& dz, int& dy, int& c) {
+    const int p = g / 3;
+    dy = g - 3 * p - 1;
+    c = p % CG;
+    dz = p / CG - 1;
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256, 1)
+    k_conv_wgrad_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap xmap3,
+                    const __grid_constant__ CUtensorMap zmap, sg_shape s,
+                    const bf16* __restrict__ dzg, float* __restrict__ partials, long long wait_limit) {
+    using C = WgCfg<CIN, COUT>;
+    extern __shared__ __align__(1024) unsigned char sm_wg[];
+    // barriers: A full, A empty [SA]; B landed, B full, B empty [SB]; done
+    __shared__ __align__(8) uint64_t bars[2 * C::SA + 3 * C::SB + 1];
+    __shared__ uint32_t tmem_holder;
+    const uint32_t base = (smem_u32(sm_wg) + 1023u) & ~1023u;
+    const uint32_t a_s = base, b_s = base + C::SA * C::A_STAGE;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr int AF = 0, AE = C::SA, BL = 2 * C::SA, BF = BL + C::SB, BE = BF + C::SB, DN = BE + C::SB;
+    auto bar = [&](int k) { return smem_u32(&bars[k]); };
+    auto fail = [&]() { atomicOr(&g_sg_status, 1); };
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
+                     "r"(C::TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int k = 0; k <= DN; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(k)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_holder;
+
+    // this CTA's rows [r0, r1) of the batch x nz x ny rows of 64 voxels (y fastest)
+    const int64_t rows = (int64_t)s.batch * s.nz * s.ny;
+    const int64_t r0 = rows * blockIdx.x / gridDim.x, r1 = rows * (blockIdx.x + 1) / gridDim.x;
+    auto row_coord = [&](int64_t r, int& b, int& z, int& y) {
+        y = (int)(r % s.ny);
+        const int64_t q = r / s.ny;
+        z = (int)(q % s.nz);
+        b = (int)(q / s.nz);
+    };
+
+    if (warp == 0) {
+        // ---- TMA producer: per row, the three shifted dZ copies, then the A tiles ----
+        uint32_t qa = 0, qb = 0;  // A / B stage sequence numbers
+        bool ok = true;
+        for (int64_t r = r0; r < r1 && ok; ++r) {
+            int b, z, y;
+            row_coord(r, b, z, y);
+            {
+                const int st = (int)(qb % C::SB);
+                const uint32_t use = qb / C::SB;
+                if (!__all_sync(0xffffffffu, tc_wait(bar(BE + st), (use & 1) ^ 1, wait_limit))) {
+                    if (lane == 0) fail();
+                    ok = false;
+                    break;
+                }
+                if (elect_one()) {
+                    tp_expect_tx(bar(BL + st), C::B_STAGE);
+                    const uint32_t dst0 = b_s + (uint32_t)(st * C::B_STAGE);
+                    for (int h = 0; h < C::NG; ++h) {
+                        // copy dxi holds dZ[(x' - dx) mod 64], dx = dxi - 1: a box starting at voxel
+                        // -dx (dx = +1: voxel 0 out of range; dx = -1: voxel 63 out of range)
+                        const int dxi = h / (COUT / 8), c0 = 8 * (h % (COUT / 8));
+                        tp_tma5(dst0 + (uint32_t)(h * 1024), &zmap, c0, 1 - dxi, y, z, b, bar(BL + st));
+                    }
+                }
+                __syncwarp();
+                ++qb;
+            }
+            for (int t = 0; t < C::NT; ++t, ++qa) {
+                const int st = (int)(qa % C::SA);
+                const uint32_t use = qa / C::SA;
+                if (!__all_sync(0xffffffffu, tc_wait(bar(AE + st), (use & 1) ^ 1, wait_limit))) {
+                    if (lane == 0) fail();
+                    ok = false;
+                    break;
+                }
+                const int g0 = 16 * t, ng = min(16, C::GROUPS - g0);
+                const bool y_inside = y >= 1 && y + 1 < s.ny;
+                if (elect_one()) {
+                    tp_expect_tx(bar(AF + st), (uint32_t)(ng * 1024));
+                    for (int k = 0; k < ng;) {
+                        int dz, dy, c;
+                        wg_group<C::CG>(g0 + k, dz, dy, c);
+                        const uint32_t dst = a_s + (uint32_t)(st * C::A_STAGE + k * 1024);
+                        if (dy == -1 && k + 2 < ng && y_inside) {  // rows y - 1 .. y + 1 in one box
+                            tp_tma5(dst, &xmap3, 8 * c, 0, y - 1, wrapi(z + dz, s.nz), b, bar(AF + st));
+                            k += 3;
+                        } else {
+                            tp_tma5(dst, &xmap, 8 * c, 0, wrapi(y + dy, s.ny), wrapi(z + dz, s.nz), b, bar(AF + st));
+                            ++k;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        // the CTA must not exit with boxes still landing: wait for the last use of every stage
+        for (uint32_t k = 0; k < (uint32_t)C::SA && k < qa; ++k) {
+            const uint32_t sq = qa - 1 - k;
+            if (!__all_sync(0xffffffffu, tc_wait(bar(AF + (int)(sq % C::SA)), (sq / C::SA) & 1, wait_limit)) &&
+                lane == 0)
+                fail();
+        }
+        for (uint32_t k = 0; k < (uint32_t)C::SB && k < qb; ++k) {
+            const uint32_t sq = qb - 1 - k;
+            if (!__all_sync(0xffffffffu, tc_wait(bar(BL + (int)(sq % C::SB)), (sq / C::SB) & 1, wait_limit)) &&
+                lane == 0)
+                fail();
+        }
+    } else if (warp == 2) {
+        // ---- wrap-voxel fixer: per row, lane l < 2 cout/8 writes one 16-byte voxel of a shifted
+        // copy: side 0 (dx = +1, copy 2) voxel 0 <- dZ[63]; side 1 (dx = -1, copy 0) voxel 63 <- dZ[0] ----
+        constexpr int COG = COUT / 8;
+        const int side = lane / COG, c8 = lane % COG;
+        const bool active = lane < 2 * COG;
+        uint32_t qb = 0;
+        for (int64_t r = r0; r < r1; ++r, ++qb) {
+            int b, z, y;
+            row_coord(r, b, z, y);
+            const int st = (int)(qb % C::SB);
+            uint4 val = make_uint4(0, 0, 0, 0);
+            if (active)
+                val = *reinterpret_cast<const uint4*>(
+                    dzg + ((((int64_t)b * s.nz + z) * s.ny + y) * kW + (side ? 0 : kW - 1)) * COUT + 8 * c8);
+            if (!__all_sync(0xffffffffu, tc_wait(bar(BL + st), (qb / C::SB) & 1, wait_limit))) {
+                if (lane == 0) fail();
+                break;
+            }
+            const int h = (side ? 0 : 2) * COG + c8;
+            const uint32_t dst = b_s + (uint32_t)(st * C::B_STAGE + h * 1024 + (side ? 63 : 0) * 16);
+            if (active)
+                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(val.x), "r"(val.y), "r"(val.z),
+                             "r"(val.w)
+                             : "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) tp_arrive(bar(BF + st));
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer ----
+        uint32_t qa = 0, qb = 0;
+        bool ok = true, first = true;
+        for (int64_t r = r0; r < r1 && ok; ++r) {
+            const int bst = (int)(qb % C::SB);
+            if (!__all_sync(0xffffffffu, tc_wait(bar(BF + bst), (qb / C::SB) & 1, wait_limit))) {
+                if (lane == 0) fail();
+                ok = false;
+                break;
+            }
+            const uint64_t bdesc = umma_desc(b_s + (uint32_t)(bst * C::B_STAGE), 128, 1024);
+            for (int t = 0; t < C::NT; ++t, ++qa) {
+                const int st = (int)(qa % C::SA);
+                if (!__all_sync(0xffffffffu, tc_wait(bar(AF + st), (qa / C::SA) & 1, wait_limit))) {
+                    if (lane == 0) fail();
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint64_t adesc = umma_desc(a_s + (uint32_t)(st * C::A_STAGE), 128, 1024);
+                const uint32_t d_tmem = tmem + (uint32_t)(t * C::NS);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)  // 16 voxels per MMA: start address + 256 B
+                    tc_mma_elect(d_tmem, adesc + (uint64_t)(16 * kk), bdesc + (uint64_t)(16 * kk), C::IDESC,
+                                 (first && kk == 0) ? 0u : 1u);
+                tc_commit_elect(bar(AE + st));
+            }
+            if (!ok) break;
+            tc_commit_elect(bar(BE + bst));
+            ++qb;
+            first = false;
+        }
+        // every MMA this warp issued has completed before the epilogue reads or tensor memory is freed
+        tc_commit_elect(bar(DN));
+        if (!__all_sync(0xffffffffu, tc_wait(bar(DN), 0, wait_limit)) && lane == 0) fail();
+    } else if (warp >= 4) {
+        // ---- epilogue: lanes 32 q .. 32 q + 31 of each tile, all N columns ----
+        const int q = warp & 3;
+        const bool ok = __all_sync(0xffffffffu, tc_wait(bar(DN), 0, wait_limit));
+        if (!ok) {
+            if (lane == 0) fail();
+        } else {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            float* out = partials + (int64_t)blockIdx.x * 27 * COUT * CIN;
+            const int m = 32 * q + lane;
+            for (int t = 0; t < C::NT; ++t) {
+                const int g = 16 * t + (m >> 3), e = m & 7;
+                int dz = 0, dy = 0, c = 0;
+                const bool real = g < C::GROUPS;
+                if (real) wg_group<C::CG>(g, dz, dy, c);
+                const int ci = 8 * c + e;
+#pragma unroll
+                for (int n0 = 0; n0 < C::N; n0 += 16) {
+                    float v[16];
+                    tc_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(t * C::NS + n0), v);
+                    if (real) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const int n = n0 + j, dxi = n / COUT, co = n - dxi * COUT;
+                            const int tap = (dz + 1) * 9 + (dy + 1) * 3 + dxi;
+                            out[(int64_t)tap * COUT * CIN + co * CIN + ci] = v[j];
+                        }
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS));
+}
+
 static int g_fwd_impl = SG_CONV_TCGEN05;  // forward convolution kernel (sg_set_conv_impl)
 
 // cuTensorMapEncodeTiled from the driver, found once through the runtime (no link-time driver dependency)
@@ -1038,13 +1321,73 @@ static int parts_for(sg_shape s) {
     return p < 1 ? 1 : p;
 }
 
+constexpr int kWgMaxCtas = 160;  // partial sums of the tcgen05 weight gradient: at most one per CTA
+
+// CTAs of the tcgen05 weight gradient for this shape (one per SM, at most one per row).
+static int wgrad_tc_ctas(sg_shape s) {
+    static int sms = 0, dev_seen = -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    if (dev != dev_seen) {
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
+        dev_seen = dev;
+    }
+    int64_t n = sms < kWgMaxCtas ? sms : kWgMaxCtas;
+    const int64_t rows = (int64_t)s.batch * s.nz * s.ny;
+    if (n > rows) n = rows;
+    return (int)n;
+}
+
+template <int CIN, int COUT>
+static int launch_wgrad_tc(sg_shape s, const void* x, const void* dz, float* partials, int ctas, cudaStream_t st) {
+    using C = WgCfg<CIN, COUT>;
+    static int configured = -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -3;
+    if (configured != dev) {
+        if (cudaFuncSetAttribute(k_conv_wgrad_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
+            cudaSuccess)
+            return -3;
+        configured = dev;
+    }
+    auto encode = tensor_map_encoder();
+    if (!encode) return -3;
+    // x[b][z][y][x][ci], dz[b][z][y][x][co] as 5D tensors (channels fastest); boxes of 8 channels
+    // (16 bytes) x 64 voxels x 1 or 3 rows, no swizzle: each row one column of an MN-major operand
+    auto enc = [&](CUtensorMap* m, const void* ptr, int ch, uint32_t rows) {
+        const cuuint64_t dims[5] = {(cuuint64_t)ch, (cuuint64_t)kW, (cuuint64_t)s.ny, (cuuint64_t)s.nz,
+                                    (cuuint64_t)s.batch};
+        const cuuint64_t strides[4] = {(cuuint64_t)ch * 2, (cuuint64_t)kW * ch * 2, (cuuint64_t)s.ny * kW * ch * 2,
+                                       (cuuint64_t)s.nz * s.ny * kW * ch * 2};
+        const cuuint32_t box[5] = {8, (cuuint32_t)kW, rows, 1, 1};
+        const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+        return encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(ptr), dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    alignas(64) CUtensorMap xm, xm3, zm;
+    if (!enc(&xm, x, CIN, 1) || !enc(&xm3, x, CIN, 3) || !enc(&zm, dz, COUT, 1)) return -3;
+    const long long wait_limit = 2000000000LL;  // ~1 s of SM clock per wait
+    k_conv_wgrad_tc<CIN, COUT><<<ctas, C::THREADS, C::SMEM, st>>>(xm, xm3, zm, s, static_cast<const bf16*>(dz),
+                                                                   partials, wait_limit);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
 template <int CIN, int COUT>
 static int launch_wgrad(sg_shape s, const void* x, const void* dz, float* dw, float* db, void* scratch,
                         cudaStream_t st) {
-    const int parts = parts_for(s);
     float* partials = static_cast<float*>(scratch);
-    k_conv_wgrad<CIN, COUT><<<dim3(27, parts), kWgThreads, 0, st>>>(s, static_cast<const bf16*>(x),
-                                                                     static_cast<const bf16*>(dz), partials, parts);
+    int parts;
+    if (g_fwd_impl == SG_CONV_TCGEN05) {
+        parts = wgrad_tc_ctas(s);
+        if (parts < 1) return -3;
+        const int rc = launch_wgrad_tc<CIN, COUT>(s, x, dz, partials, parts, st);
+        if (rc) return rc;
+    } else {
+        parts = parts_for(s);
+        k_conv_wgrad<CIN, COUT><<<dim3(27, parts), kWgThreads, 0, st>>>(s, static_cast<const bf16*>(x),
+                                                                         static_cast<const bf16*>(dz), partials, parts);
+    }
     const int n = 27 * CIN * COUT;
     k_wgrad_reduce<<<(n + 255) / 256, 256, 0, st>>>(CIN, COUT, parts, partials, dw);
     const int64_t voxels = (int64_t)s.batch * s.nz * s.ny * s.nx;
@@ -1122,7 +1465,12 @@ int sg_transpose_weights(int cin, int cout, const void* w, void* wt, void* strea
 }
 
 int64_t sg_wgrad_scratch_bytes(sg_shape s, int cin, int cout) {
-    return (int64_t)parts_for(s) * 27 * cin * cout * (int64_t)sizeof(float);
+    // enough for either kernel: the mma.sync one's voxel partitions, the tcgen05 one's CTAs
+    const int64_t rows = (int64_t)s.batch * s.nz * s.ny;
+    int64_t parts = parts_for(s);
+    const int64_t tc = rows < kWgMaxCtas ? rows : kWgMaxCtas;
+    if (tc > parts) parts = tc;
+    return parts * 27 * cin * cout * (int64_t)sizeof(float);
 }
 
 int sg_conv3d_wgrad(sg_shape s, int cin, int cout, const void* x, const void* dz, float* dw, float* db, void* scratch,

@@ -72,16 +72,23 @@ class Surrogate:
             self.cache.append(h)
         return h
 
-    def backward(self, dpred, scratch_w):
-        """Gradients of all weights and biases from dL/dpred (FP32, [..][16])."""
+    def backward(self, dpred, scratch_w, trace=None):
+        """Gradients of all weights and biases from dL/dpred (FP32, [..][16]).  If `trace` is a
+        dict, it receives per layer k the gradient arriving at the layer's output ("dh_out", FP32),
+        the pre-activation gradient ("dz", BF16) and the gradient passed to its input ("dh_in",
+        FP32; layers k > 0)."""
         dh = dpred
         for k in range(len(LAYERS) - 1, -1, -1):
             ci, co, act, res = LAYERS[k]
             dz = sg.act_backward(dh, self.zs[k], act)
             sg.conv3d_wgrad(self.cache[k], dz, self.g[2 * k], self.g[2 * k + 1], scratch_w[(ci, co)])
+            if trace is not None:
+                trace[k] = {"dh_out": dh, "dz": dz}
             if k > 0:
                 wt = sg.transpose_weights(self.w16[k])
                 dh = sg.conv3d_fwd_f32(dz, wt, add=dh if res else None)
+                if trace is not None:
+                    trace[k]["dh_in"] = dh
 
     def adam_step(self, lr):
         self.t += 1

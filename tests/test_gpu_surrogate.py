@@ -66,6 +66,75 @@ def test_network_gradients_match_oracle():
         assert (ab - gb[k]).norm() <= 3e-2 * gb[k].norm() + 1e-6, k
 
 
+def test_network_backward_chain_matches_oracle_elementwise():
+    """Every link of the GPU backward pass, element by element, against FP64 computed from the
+    GPU's own inputs to that link (the BF16 activations and FP32 pre-activations cached by the
+    forward pass, and the gradient the link received):
+      dL/dpred     = 2 (pred - target) / (voxels * 5) on channels 0..4, zero elsewhere;
+      dz_k         = dh_out_k * act'(z_k), one BF16 rounding (2^-8 relative);
+      dW_k, db_k   = sum_v h_k(v + d) dz_k(v), sum_v dz_k(v): FP32 summation, <= 1e-5 of the
+                     sum of absolute terms (the kernel tests' bound);
+      dh_in_k      = the input gradient of conv(h_k; W_k) for dz_k, plus dh_out_k for the
+                     residual layers: <= 1e-5 of the sum of absolute terms.
+    A wiring mistake anywhere in the chain (a dropped residual gradient, a wrong activation or
+    cache index, a transposed tap) moves some element by the size of the term itself."""
+    net = _random_net(5)
+    g = torch.Generator().manual_seed(6)
+    shape = (2, 4, 8, 64)
+    x = torch.zeros(shape + (16,))
+    x[..., :5] = torch.randn(shape + (5,), generator=g)
+    t = x.clone()
+    t[..., :5] += 0.3 * torch.randn(shape + (5,), generator=g)
+    xd, td = x.to(torch.bfloat16).cuda(), t.to(torch.bfloat16).cuda()
+    pred = net.forward(xd, train=True)
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    dpred = torch.empty(xd.shape, dtype=torch.float32, device="cuda")
+    sg.mse(pred, td, 5, loss, dpred, sg.reduce_scratch())
+    scratch = {(ci, co): sg.wgrad_scratch(xd, ci, co) for ci, co, _, _ in S.LAYERS}
+    trace = {}
+    net.backward(dpred, scratch, trace=trace)
+    torch.cuda.synchronize()
+    cpu = lambda a: a.cpu().to(F64)  # noqa: E731
+
+    voxels = float(np.prod(shape))
+    ref = torch.zeros(shape + (16,), dtype=F64)
+    ref[..., :5] = 2 * (cpu(pred) - cpu(td))[..., :5] / (voxels * 5)
+    assert torch.all((cpu(dpred) - ref).abs() <= 1e-6 * ref.abs() + 1e-12)
+    assert torch.equal(cpu(trace[len(S.LAYERS) - 1]["dh_out"]), cpu(dpred))
+
+    for k in range(len(S.LAYERS) - 1, -1, -1):
+        ci, co, act, res = S.LAYERS[k]
+        h = cpu(net.cache[k])                      # the layer's input (BF16 on the GPU)
+        zk = cpu(net.zs[k])                        # pre-activation (FP32)
+        dh_out, dz = cpu(trace[k]["dh_out"]), cpu(trace[k]["dz"])
+        w = cpu(net.w16[k])
+        # activation backward: one BF16 rounding of the product, plus the FP32 error of act'(z) =
+        # Phi(z) + z phi(z), whose two terms cancel near z = -0.75 (a few ulp of each term)
+        zr = zk.clone().requires_grad_(True)
+        (so.gelu(zr) if act == sg.ACT_GELU else zr).backward(dh_out)
+        terms = (0.5 * (1 + torch.erf(zk / math.sqrt(2))) + (zk * torch.exp(-zk * zk / 2)).abs() / math.sqrt(2 * math.pi)
+                 if act == sg.ACT_GELU else torch.ones_like(zk))
+        assert torch.all((dz - zr.grad).abs() <= 2 ** -8 * zr.grad.abs() + 5e-7 * dh_out.abs() * terms + 1e-30), k
+        # weight and bias gradients from the GPU's own h and dz
+        w0 = torch.zeros((co, 27, ci), dtype=F64, requires_grad=True)
+        b0 = torch.zeros(co, dtype=F64, requires_grad=True)
+        (so.conv3d_periodic(h, w0, b0) * dz).sum().backward()
+        wa = torch.zeros((co, 27, ci), dtype=F64, requires_grad=True)
+        (so.conv3d_periodic(h.abs(), wa) * dz.abs()).sum().backward()
+        assert torch.all((cpu(net.g[2 * k]) - w0.grad).abs() <= 1e-5 * wa.grad + 1e-12), k
+        assert torch.all((cpu(net.g[2 * k + 1]) - b0.grad).abs() <= 1e-5 * dz.abs().sum(dim=(0, 1, 2, 3)) + 1e-12), k
+        if k > 0:
+            hr = h.clone().requires_grad_(True)
+            (so.conv3d_periodic(hr, w) * dz).sum().backward()
+            ha = h.abs().requires_grad_(True)
+            (so.conv3d_periodic(ha, w.abs()) * dz.abs()).sum().backward()
+            want = hr.grad + (dh_out if res else 0)
+            bound = 1e-5 * (ha.grad + (dh_out.abs() if res else 0)) + 1e-12
+            assert torch.all((cpu(trace[k]["dh_in"]) - want).abs() <= bound), k
+            # the gradient layer k passes on is the one layer k - 1 receives
+            assert torch.equal(cpu(trace[k - 1]["dh_out"]), cpu(trace[k]["dh_in"])), k
+
+
 def test_pack_unpack_fields():
     n = 64
     th0 = lb.lb_theta0()
