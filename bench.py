@@ -33,6 +33,12 @@ sys.path.insert(0, ROOT)
 BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 DTYPE_NAME = {"f64": "f64", "f32": "f32", "f16": "f32 (f16 storage)", "bf16": "f32 (bf16 storage)"}
 NU = 0.01
+# Field values in the compute type (4 B, FP64 storage 8 B) one nonideal step moves per node: the
+# density pass writes rho, mu, F (3); the field pass reads rho, F and writes grad rho, lap rho,
+# lap F (2 + 5); the force pass reads rho, mu, F, grad rho, lap rho, lap F and writes g (8 + 3);
+# the step reads g (3).  The populations are gathered twice (density pass, step) and written
+# once: 3 x 41 stored values.
+NONIDEAL_FIELD_VALUES = 24
 STEP_KERNEL_SOURCES = ["lb_common.cuh", "lb_kernels.cuh", "lb_step_tma.cuh", "lb_step_ws.cuh", "lb_step_f32.cu",
                        "lb_step_f64.cu"]
 
@@ -57,6 +63,16 @@ def parse():
     p.add_argument("--batch-sims", type=int, default=64, help="simulations in the batched sweep")
     p.add_argument("--kernel", type=int, default=None,
                    help="step kernel for the headline run (LB_KERNEL_* id); default: the fastest that applies")
+    p.add_argument("--no-surrogate", action="store_true", help="skip the surrogate convolution timings")
+    p.add_argument("--conv", action="store_true",
+                   help="only time the surrogate's convolution kernels (forward and weight gradient) and print "
+                        "one JSON object")
+    p.add_argument("--conv-impl", default="both", choices=["tcgen05", "mma_sync", "both"])
+    p.add_argument("--conv-ops", default="fwd,wgrad", help="comma list of fwd, wgrad")
+    p.add_argument("--conv-layers", default="16x32,32x32,32x16")
+    p.add_argument("--conv-batch", default="1,4")
+    p.add_argument("--conv-reps", type=int, default=20)
+    p.add_argument("--conv-warmup", type=int, default=3)
     return p.parse_args()
 
 
@@ -266,6 +282,63 @@ def run_batch(lb, wl, torch, steps, count=64):
     return out
 
 
+def conv_timings(torch, sg, layers, batches, impls, ops, reps, warmup):
+    """CUDA-event time per launch of the surrogate's convolutions on random BF16 activations of
+    batch x 64^3 x cin voxels: the forward convolution with its fused GELU (+ residual when
+    cin == cout) epilogue, and the weight + bias gradient (dz of cout channels).  Rate:
+    2 * voxels * 27 * cin * cout flops per launch."""
+    names = {"tcgen05": sg.CONV_TCGEN05, "mma_sync": sg.CONV_MMA_SYNC}
+    out = {}
+    for name in impls:
+        prev = sg.set_conv_impl(names[name])
+        try:
+            for cin, cout in layers:
+                for batch in batches:
+                    shape = (batch, 64, 64, 64)
+                    g = torch.Generator(device="cuda").manual_seed(cin * 100 + cout)
+                    x = torch.randn(shape + (cin,), device="cuda", generator=g).to(torch.bfloat16)
+                    flops = 2.0 * batch * 64 ** 3 * 27 * cin * cout
+                    for op in ops:
+                        if op == "fwd":
+                            w = (torch.randn((cout, 27, cin), device="cuda", generator=g) / math.sqrt(27 * cin)
+                                 ).to(torch.bfloat16)
+                            b = torch.zeros(cout, device="cuda")
+                            y = torch.empty(shape + (cout,), device="cuda", dtype=torch.bfloat16)
+                            run = lambda: sg.conv3d_fwd(x, w, b, act=sg.ACT_GELU, res_in=(cin == cout), y=y)  # noqa
+                        else:
+                            dz = torch.randn(shape + (cout,), device="cuda", generator=g).to(torch.bfloat16)
+                            dw = torch.empty((cout, 27, cin), device="cuda")
+                            db = torch.empty(cout, device="cuda")
+                            scr = sg.wgrad_scratch(x, cin, cout)
+                            run = lambda: sg.conv3d_wgrad(x, dz, dw, db, scr)  # noqa
+                        for _ in range(warmup):
+                            run()
+                        torch.cuda.synchronize()
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        for _ in range(reps):
+                            run()
+                        e1.record()
+                        e1.synchronize()
+                        ms = e0.elapsed_time(e1) / reps
+                        out[f"{op} {name} {cin}->{cout} b{batch}"] = {
+                            "us": round(ms * 1e3, 2), "tflops": round(flops / (ms * 1e-3) / 1e12, 1)}
+            sg.status()
+        finally:
+            sg.set_conv_impl(prev)
+    return out
+
+
+def bf16_peak():
+    """Measured dense BF16 peak (TFLOP/s, burst) and where it came from."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return float(json.load(fh)["bf16_tflops"]), "measured"
+    return 1900.0, "fallback"
+
+
 def workload_config(args, world):
     """The `config` of both arms' JSON lines: the workload the main arm times."""
     n = args.n
@@ -320,6 +393,16 @@ def main():
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU")
     torch.cuda.set_device(local)
+    if args.conv:
+        from paper_1909_08406_gb300 import sg
+        impls = ["tcgen05", "mma_sync"] if args.conv_impl == "both" else [args.conv_impl]
+        layers = [tuple(int(v) for v in L.split("x")) for L in args.conv_layers.split(",")]
+        batches = [int(b) for b in args.conv_batch.split(",")]
+        res = conv_timings(torch, sg, layers, batches, impls, args.conv_ops.split(","), args.conv_reps,
+                           args.conv_warmup)
+        if rank == 0:
+            print(json.dumps({"conv": res, "bf16_peak_tflops": bf16_peak()[0]}), flush=True)
+        return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -421,11 +504,17 @@ def main():
     nonideal = None
     if not args.no_nonideal:
         r, _ = timed_run(head, best, max(5, args.steps // 10), 3, False, nonideal=True)
+        per_node = 3 * 41 * BYTES[head] + NONIDEAL_FIELD_VALUES * (8 if head == "f64" else 4)
+        ni_gbs = nodes * per_node / (r["kernel_ms"] * 1e-3) / 1e9
+        hbm, hbm_kind = measured_peaks()
         nonideal = {"mlups": r["mlups"], "ms_per_step": r["ms_per_step"], "steps": r["steps"],
                     "vs_energy_conserving": r["mlups"] / results[head]["mlups"],
+                    "roofline": {"bound": "hbm", "alg_bytes_per_node": per_node, "achieved": ni_gbs, "peak": hbm,
+                                 "unit": "GB/s", "frac": ni_gbs / hbm, "peak_kind": hbm_kind},
+                    "kernels_per_step": 4,
                     "note": "isothermal van der Waals fluid (theta/theta_c = 1.1, kappa 0.05) on the same fields, "
-                            "grid and storage: density, stencil-field and force kernels in the storage's compute type "
-                            "and the forced step, one node per thread"}
+                            "grid and storage: density, stencil-field and force passes in the storage's compute "
+                            "type, then the forced step, one node per thread"}
     if not args.no_secondary:
         for prec in precs[1:]:
             steps = max(3, args.steps // 10) if prec == "f64" else max(5, args.steps // 2)
@@ -480,6 +569,16 @@ def main():
                                       "kernel over the host link), K x lb_step, lb_get_moments to pinned "
                                       "host"}
 
+    surrogate = None
+    if not args.no_surrogate and rank == 0:
+        from paper_1909_08406_gb300 import sg
+        pk, pk_kind = bf16_peak()
+        ct = conv_timings(torch, sg, [(32, 32)], [4], ["tcgen05"], ["fwd", "wgrad"], 10, 3)
+        surrogate = {"layer": "32->32, batch 4 x 64^3, BF16 in, FP32 accumulate, tcgen05",
+                     "peak_tflops": pk, "peak_kind": pk_kind,
+                     **{op: {**ct[f"{op} tcgen05 32->32 b4"], "frac": ct[f"{op} tcgen05 32->32 b4"]["tflops"] / pk}
+                        for op in ("fwd", "wgrad")}}
+
     if rank != 0:
         return
     r = results[args.precision]
@@ -503,6 +602,7 @@ def main():
         "walls": walls,
         "nonideal": nonideal,
         "batch": batch,
+        "surrogate_conv": surrogate,
         "gpu_launches": r["steps"],
         "clocks": clocks,
         "e2e": e2e,

@@ -6,7 +6,8 @@
 //   k_ni_density  rho of the streamed populations, sum_i f_i(x - c_i), and
 //                 mu_nid(rho), F_nid(rho) of each node
 //   k_ni_fields   per node: grad2 rho (3), lap rho, lap F_nid
-//   k_ni_force    g^nid of Eq. (gradientFinal):
+//   k_ni_force    g^nid of Eq. (gradientFinal) at the node, from its stencil
+//                 neighbours' fields:
 //                   rho g = -[rho grad2 mu + mu grad2 rho - eta grad2 F
 //                             - (1 - eta) grad4 F + kappa grad2_b I_ab],
 //                   grad4 = grad2 - (theta_hat / 2) grad2 lap,
@@ -62,14 +63,20 @@ __device__ __forceinline__ int64_t ni_neighbor(const Dims& d, int s, int z, int 
     return (((int64_t)t * d.nz + zn) * d.ny + yn) * d.nx + xn;
 }
 
-__device__ __forceinline__ bool ni_node(const Dims& d, int64_t q, int& s, int& z, int& y, int& x) {
-    if (q >= 2 * d.plane) return false;
-    x = (int)(q % d.nx);
-    int64_t r = q / d.nx;
-    y = (int)(r % d.ny);
-    r /= d.ny;
-    z = (int)(r % d.nz);
-    s = (int)(r / d.nz);
+constexpr int kNiThreads = 128;
+
+// Node of this thread: blocks cover (row, x chunk) pairs, row = (s, z, y) with y fastest, so the
+// coordinates come from 32-bit divisions of the block index (2 ny nz < 2^31, checked at init).
+__device__ __forceinline__ bool ni_node(const Dims& d, int chunks, int64_t& q, int& s, int& z, int& y, int& x) {
+    const uint32_t b = blockIdx.x;
+    const uint32_t row = b / (uint32_t)chunks;
+    x = (int)(b - row * (uint32_t)chunks) * kNiThreads + (int)threadIdx.x;
+    if (x >= d.nx) return false;
+    const uint32_t zr = row / (uint32_t)d.ny;
+    y = (int)(row - zr * (uint32_t)d.ny);
+    s = (int)(zr / (uint32_t)d.nz);
+    z = (int)(zr - (uint32_t)s * (uint32_t)d.nz);
+    q = (int64_t)row * d.nx + x;
     return true;
 }
 
@@ -105,14 +112,14 @@ __device__ __forceinline__ void ni_gather(const typename Codec::raw_t* __restric
 }
 
 template <class Codec>
-__global__ void __launch_bounds__(128) k_ni_density(const typename Codec::raw_t* __restrict__ src, Dims d,
-                                                    Consts<typename Codec::R> K, NiEos e,
-                                                    typename Codec::R* __restrict__ rho,
-                                                    typename Codec::R* __restrict__ A) {
+__global__ void __launch_bounds__(kNiThreads) k_ni_density(const typename Codec::raw_t* __restrict__ src, Dims d,
+                                                           int chunks, Consts<typename Codec::R> K, NiEos e,
+                                                           typename Codec::R* __restrict__ rho,
+                                                           typename Codec::R* __restrict__ A) {
     using R = typename Codec::R;
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t q;
     int s, z, y, x;
-    if (!ni_node(d, q, s, z, y, x)) return;
+    if (!ni_node(d, chunks, q, s, z, y, x)) return;
     R v[kQ];
     ni_gather<Codec>(src, d, s, z, y, x, v);
     R dr = 0;  // rho - 1 = sum_i (f_i - w_i)
@@ -125,12 +132,14 @@ __global__ void __launch_bounds__(128) k_ni_density(const typename Codec::raw_t*
     A[2 * d.plane + q] = Fe;
 }
 
-// A[k][node]: 0 mu, 1 F (both from k_ni_density), 2..4 grad2 rho, 5 lap rho, 6 lap F.
+// A[k][node]: 0 mu, 1 F (both from k_ni_density), 2..4 grad2 rho, 5 lap rho, 6 lap F (k_ni_fields),
+// 7..9 g^nid (k_ni_force).
 template <class F>
-__global__ void __launch_bounds__(128) k_ni_fields(Dims d, const F* __restrict__ rho, F* __restrict__ A) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(kNiThreads) k_ni_fields(Dims d, int chunks, const F* __restrict__ rho,
+                                                          F* __restrict__ A) {
+    int64_t q;
     int s, z, y, x;
-    if (!ni_node(d, q, s, z, y, x)) return;
+    if (!ni_node(d, chunks, q, s, z, y, x)) return;
     const int64_t n = 2 * d.plane;
     const F r0 = rho[q], F0 = A[n + q];
     F g[3] = {F(0), F(0), F(0)}, lr = F(14.0 / 36.0) * r0, lF = F(14.0 / 36.0) * F0;
@@ -151,12 +160,10 @@ __global__ void __launch_bounds__(128) k_ni_fields(Dims d, const F* __restrict__
     A[6 * n + q] = F(2.0 / kHatTheta) * (lF - F0);
 }
 
+// g^nid at node q (s, z, y, x) from the fields of its stencil neighbours, into g[3].
 template <class F>
-__global__ void __launch_bounds__(128) k_ni_force(Dims d, NiEos e, const F* __restrict__ rho, const F* __restrict__ A,
-                                                  F* __restrict__ g) {
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int s, z, y, x;
-    if (!ni_node(d, q, s, z, y, x)) return;
+__device__ __forceinline__ void ni_force(const Dims& d, const NiEos& e, const F* __restrict__ rho,
+                                         const F* __restrict__ A, int64_t q, int s, int z, int y, int x, F (&g)[3]) {
     const int64_t n = 2 * d.plane;
     F dmu[3] = {0, 0, 0}, dF[3] = {0, 0, 0}, dlF[3] = {0, 0, 0}, divI[3] = {0, 0, 0};
     for (int k = 0; k < kStencil; ++k) {
@@ -191,23 +198,39 @@ __global__ void __launch_bounds__(128) k_ni_force(Dims d, NiEos e, const F* __re
         const F g4F = g2F - F(0.5 * kHatTheta) * g2lF;
         const F rg = -(r0 * g2mu + mu0 * A[(2 + a) * n + q] - F(e.eta) * g2F - (F(1) - F(e.eta)) * g4F +
                        F(e.kappa) * divI[a] * inv_th);
-        g[a * n + q] = rg / r0;
+        g[a] = rg / r0;
     }
 }
 
+// g^nid of every node into A[7..9] (a pass of its own: folded into the step, the stencil sums raise
+// the step's register count and the fused step ran slower than the two passes).
+template <class F>
+__global__ void __launch_bounds__(kNiThreads) k_ni_force(Dims d, int chunks, NiEos e, const F* __restrict__ rho,
+                                                          F* __restrict__ A) {
+    int64_t q;
+    int s, z, y, x;
+    if (!ni_node(d, chunks, q, s, z, y, x)) return;
+    F g[3];
+    ni_force<F>(d, e, rho, A, q, s, z, y, x, g);
+    const int64_t n = 2 * d.plane;
+    for (int a = 0; a < 3; ++a) A[(7 + a) * n + q] = g[a];
+}
+
+// The pull step with the forced BGK collision; g^nid from A[7..9].
 template <class Codec>
-__global__ void __launch_bounds__(128) k_ni_step(const typename Codec::raw_t* __restrict__ src,
-                                                 typename Codec::raw_t* __restrict__ dst, Dims d,
-                                                 Consts<typename Codec::R> K, typename Codec::R tb,
-                                                 typename Codec::R inv_theta0,
-                                                 const typename Codec::R* __restrict__ g,
-                                                 int* __restrict__ err) {
+__global__ void __launch_bounds__(kNiThreads) k_ni_step(const typename Codec::raw_t* __restrict__ src,
+                                                        typename Codec::raw_t* __restrict__ dst, Dims d, int chunks,
+                                                        Consts<typename Codec::R> K, typename Codec::R tb,
+                                                        typename Codec::R inv_theta0,
+                                                        const typename Codec::R* __restrict__ A,
+                                                        int* __restrict__ err) {
     using R = typename Codec::R;
     using T = typename Codec::raw_t;
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t q;
     int s, z, y, x;
-    if (!ni_node(d, q, s, z, y, x)) return;
+    if (!ni_node(d, chunks, q, s, z, y, x)) return;
     const int64_t n = 2 * d.plane;
+    const R gf[3] = {A[7 * n + q], A[8 * n + q], A[9 * n + q]};
     R v[kQ];
     ni_gather<Codec>(src, d, s, z, y, x, v);
     R dv[kQ];
@@ -217,7 +240,7 @@ __global__ void __launch_bounds__(128) k_ni_step(const typename Codec::raw_t* __
     NodeState<R> st;
     st.drho = m.drho;
     st.rho = R(1) + m.drho;
-    const R gx = g[q], gy = g[n + q], gz = g[2 * n + q];
+    const R gx = gf[0], gy = gf[1], gz = gf[2];
     const R inv_rho = R(1) / st.rho;
     st.ux = m.jx * inv_rho + R(0.5) * gx;
     st.uy = m.jy * inv_rho + R(0.5) * gy;
@@ -265,7 +288,8 @@ cudaError_t launch_nonideal_step(int prec, const void* src, void* dst, const Dim
                                  double twobeta, int kind, const double eos[4], double* work, int* err,
                                  cudaStream_t st) {
     const int64_t n = 2 * d.plane;
-    const unsigned blocks = (unsigned)((n + 127) / 128);
+    const int chunks = (d.nx + kNiThreads - 1) / kNiThreads;
+    const unsigned blocks = (unsigned)(d.rows * chunks);
     if (kind < kVdW || kind > kCarnahanStarling) return cudaErrorInvalidValue;
     const NiEos e{eos[0], eos[1], c.theta0, eos[2], eos[3], kind};
     return ni_codec(prec, [&](auto codec) {
@@ -276,15 +300,15 @@ cudaError_t launch_nonideal_step(int prec, const void* src, void* dst, const Dim
             K = &c.kd;
         else
             K = &c.kf;
-        R* rho = reinterpret_cast<R*>(work);  // fields in the compute type: rho, A[7], g[3]
+        R* rho = reinterpret_cast<R*>(work);  // fields in the compute type: rho, A[10]
         R* A = rho + n;
-        R* g = rho + 8 * n;
-        k_ni_density<C><<<blocks, 128, 0, st>>>(static_cast<const typename C::raw_t*>(src), d, *K, e, rho, A);
-        k_ni_fields<R><<<blocks, 128, 0, st>>>(d, rho, A);
-        k_ni_force<R><<<blocks, 128, 0, st>>>(d, e, rho, A, g);
-        k_ni_step<C><<<blocks, 128, 0, st>>>(static_cast<const typename C::raw_t*>(src),
-                                             static_cast<typename C::raw_t*>(dst), d, *K, (R)twobeta,
-                                             (R)(1.0 / c.theta0), g, err);
+        k_ni_density<C><<<blocks, kNiThreads, 0, st>>>(static_cast<const typename C::raw_t*>(src), d, chunks, *K, e,
+                                                        rho, A);
+        k_ni_fields<R><<<blocks, kNiThreads, 0, st>>>(d, chunks, rho, A);
+        k_ni_force<R><<<blocks, kNiThreads, 0, st>>>(d, chunks, e, rho, A);
+        k_ni_step<C><<<blocks, kNiThreads, 0, st>>>(static_cast<const typename C::raw_t*>(src),
+                                                     static_cast<typename C::raw_t*>(dst), d, chunks, *K,
+                                                     (R)twobeta, (R)(1.0 / c.theta0), A, err);
         return cudaGetLastError();
     });
 }

@@ -697,8 +697,6 @@ __global__ void __launch_bounds__(384, 1)
         // ---- TMA producer: plane loads in order (column, slice, plane); the whole warp runs the
         // loop (warp-uniform coordinates), one elected lane issues ----
         uint32_t q = 0;  // plane-load sequence number
-        int last_slot = -1;
-        uint32_t last_parity = 0;
         bool ok = true;
         for (int64_t c = blockIdx.x; c < ncols && ok; c += gridDim.x) {
             const Col K = col_of(c);
@@ -712,8 +710,6 @@ __global__ void __launch_bounds__(384, 1)
                         ok = false;
                         break;
                     }
-                    last_slot = slot;
-                    last_parity = use & 1;
                     const int zz = wrapi(K.z0 - 1 + p, s.nz);
                     if (elect_one()) {
                         tp_expect_tx(bar(LT + slot), C::SLOT);
@@ -731,10 +727,15 @@ __global__ void __launch_bounds__(384, 1)
                     __syncwarp();
                 }
         }
-        // the CTA must not exit with boxes still landing
-        if (last_slot >= 0 && !__all_sync(0xffffffffu, tc_wait(bar(LT + last_slot), last_parity, wait_limit)) &&
-            lane == 0)
-            fail();
+        // the CTA must not exit with boxes still landing: q plane loads were issued (sequence numbers
+        // 0 .. q - 1; a failed wait breaks before its iteration issues or counts), so wait for the
+        // last use of every slot, whether the loop finished or stopped on a failed wait
+        for (uint32_t k = 0; k < (uint32_t)C::NSLOT && k < q; ++k) {
+            const uint32_t sq = q - 1 - k;
+            if (!__all_sync(0xffffffffu, tc_wait(bar(LT + (int)(sq % C::NSLOT)), (sq / C::NSLOT) & 1, wait_limit)) &&
+                lane == 0)
+                fail();
+        }
     } else if (warp == 1) {
         // ---- periodic-wrap fixer: copy 0 voxel 0 <- in[63], copy 2 voxel 63 <- in[0], 4 rows ----
         uint32_t q = 0;

@@ -53,32 +53,77 @@ def interior(f_padded, halo: int = HALO):
     return f_padded[:, :, halo:f_padded.shape[2] - halo]
 
 
-def exchange_halos(f_padded, group=None, halo: int = HALO):
+def halo_populations(cz2, halo: int = HALO):
+    """Which populations each halo plane must carry.  An interior node pulls population i from
+    ceil(|c_iz|) cells away at most, on the side c_iz points from (doubled components cz2 =
+    2 c_z: 1 for a bcc-1/2 link, 2 and 4 for integer links), so the halo plane at distance d from
+    the interior is read only through populations with ceil(|cz2| / 2) >= d.  Returns
+    (lower, upper): for each halo plane, innermost first, the population indices with c_z > 0
+    (lower halo) or c_z < 0 (upper halo) that reach it."""
+    cz2 = [int(v) for v in cz2]
+    reach = [(abs(v) + 1) // 2 for v in cz2]
+    lower = [[i for i, v in enumerate(cz2) if v > 0 and reach[i] >= d] for d in range(1, halo + 1)]
+    upper = [[i for i, v in enumerate(cz2) if v < 0 and reach[i] >= d] for d in range(1, halo + 1)]
+    return lower, upper
+
+
+def halo_fraction(cz2, halo: int = HALO) -> float:
+    """Bytes a selective exchange moves relative to sending every population of every halo plane."""
+    lower, upper = halo_populations(cz2, halo)
+    return sum(len(p) for p in lower + upper) / (2 * halo * len(cz2))
+
+
+def exchange_halos(f_padded, group=None, halo: int = HALO, cz2=None):
     """Refresh the halo planes of a padded slab from the periodic neighbours' interiors: the
     lower halo receives the top `halo` interior planes of rank - 1, the upper halo the bottom
     `halo` interior planes of rank + 1.  One exchange per step; with one rank the slab is its
-    own neighbour (the periodic wrap)."""
+    own neighbour (the periodic wrap).  With `cz2` (the doubled z components of the populations
+    in the array's velocity order) only the populations an interior node reads from each halo
+    plane are sent (``halo_populations``: 15 of the 82 plane-populations of a 2-plane halo per
+    sub-lattice pair and direction); the others keep stale values that no interior update reads."""
+    import numpy as np
     import torch
     import torch.distributed as dist
     nzp = f_padded.shape[2]
-    lo_send = f_padded[:, :, halo:2 * halo].contiguous()            # to rank - 1 (its upper halo)
-    hi_send = f_padded[:, :, nzp - 2 * halo:nzp - halo].contiguous()  # to rank + 1 (its lower halo)
+    if cz2 is None:
+        every = list(range(f_padded.shape[1]))
+        lower, upper = [every] * halo, [every] * halo
+    else:
+        lower, upper = halo_populations(cz2, halo)
+    # receiver's lower halo plane at distance d (index halo - d) <- sender's plane nzp - halo - d;
+    # receiver's upper halo plane at distance d (index nzp - halo + d - 1) <- sender's plane halo + d - 1
+    def pack(planes_pops):
+        return torch.cat([f_padded[:, pops, z].reshape(-1) for z, pops in planes_pops]).contiguous()
+
+    def unpack(buf, planes_pops):
+        k = 0
+        for z, pops in planes_pops:
+            shape = f_padded[:, pops, z].shape
+            n = int(np.prod(shape))
+            f_padded[:, pops, z] = buf[k:k + n].reshape(shape)
+            k += n
+
+    hi_src = [(nzp - halo - d, lower[d - 1]) for d in range(1, halo + 1)]  # to rank + 1
+    lo_src = [(halo + d - 1, upper[d - 1]) for d in range(1, halo + 1)]    # to rank - 1
+    lo_dst = [(halo - d, lower[d - 1]) for d in range(1, halo + 1)]        # from rank - 1
+    hi_dst = [(nzp - halo + d - 1, upper[d - 1]) for d in range(1, halo + 1)]  # from rank + 1
+    hi_send, lo_send = pack(hi_src), pack(lo_src)
     world = dist.get_world_size(group) if dist.is_initialized() else 1
     if world == 1:
-        f_padded[:, :, :halo] = hi_send
-        f_padded[:, :, nzp - halo:] = lo_send
+        unpack(hi_send, lo_dst)
+        unpack(lo_send, hi_dst)
         return f_padded
     rank = dist.get_rank(group)
     down, up = (rank - 1) % world, (rank + 1) % world
-    lo_recv = torch.empty_like(lo_send)
-    hi_recv = torch.empty_like(hi_send)
+    lo_recv = torch.empty_like(hi_send)
+    hi_recv = torch.empty_like(lo_send)
     # tag 0: planes going up (they land in the receiver's lower halo); tag 1: going down
     ops = [dist.P2POp(dist.isend, hi_send, up, group, 0), dist.P2POp(dist.isend, lo_send, down, group, 1),
            dist.P2POp(dist.irecv, lo_recv, down, group, 0), dist.P2POp(dist.irecv, hi_recv, up, group, 1)]
     for r in dist.batch_isend_irecv(ops):
         r.wait()
-    f_padded[:, :, :halo] = lo_recv
-    f_padded[:, :, nzp - halo:] = hi_recv
+    unpack(lo_recv, lo_dst)
+    unpack(hi_recv, hi_dst)
     return f_padded
 
 

@@ -60,6 +60,37 @@ def test_batch_modes_match_oracle(prec, mode):
         assert rel.max() <= TOL[prec], (k, rel.max())
 
 
+@pytest.mark.parametrize("mode", [lb.LB_BATCH_GRAPH, lb.LB_BATCH_PERSISTENT])
+def test_batch_config4_member_sizes_match_oracle(mode):
+    """Members of the sizes the 64-simulation sweep draws (edges 48 and 128, the smallest odd multiple
+    of 16 and the largest; tau at the sweep's extremes 0.51 and 1.0), FP32, stepped with the plan the
+    autotuner picks for this batch (as the benchmark does), every population against the oracle."""
+    grids = [(48, 48, 48), (128, 128, 128)]
+    taus = [0.51, 1.0]
+    steps = 3
+    th0 = lb.lb_theta0()
+    fields = [wl.random_fields(*g, th0, seed=60 + k, du=0.03, drho=0.03, dtheta=0.03) for k, g in enumerate(grids)]
+    b = lb.lb_batch_init(grids, taus, "f32")
+    got = []
+    try:
+        for k, fl in enumerate(fields):
+            lb.lb_set_fields(lb.lb_batch_sim(b, k), fl["rho"].cuda(), fl["u"].cuda(), fl["theta"].cuda())
+        lb.lb_batch_tune(b, reps=1)
+        lb.lb_batch_step(b, steps, mode)
+        lb.lb_batch_sync(b)
+        for k, (nx, ny, nz) in enumerate(grids):
+            f = np.empty((2, 41, nz, ny, nx))
+            lb.lb_get_populations(lb.lb_batch_sim(b, k), f)
+            got.append(f)
+    finally:
+        lb.lb_batch_destroy(b)
+    perm = lib_to_oracle_perm()
+    for k, fl in enumerate(fields):
+        ref = oracle.step(oracle.init_fields(fl["rho"].numpy(), fl["u"].numpy(), fl["theta"].numpy()), taus[k], steps)
+        rel = np.abs(to_oracle_order(got[k], perm) - ref) / ref
+        assert rel.max() <= TOL["f32"], (grids[k], rel.max())
+
+
 TILES = [(16, 4), (16, 8), (32, 2), (32, 4), (64, 1), (64, 2), (128, 1), (64, 0), (128, 0)]
 
 
