@@ -282,32 +282,67 @@ __global__ void __launch_bounds__(kWgThreads) k_conv_wgrad(sg_shape s, const bf1
     }
 }
 
-// dw[co][tap][ci] = sum_p partials[p][tap][co][ci]  (fixed order)
+// dw[co][tap][ci] = sum_p partials[p][tap][co][ci]: one warp per element, lane l sums the parts
+// l, l + 32, ... in order, then a fixed shuffle tree (deterministic).
 __global__ void k_wgrad_reduce(int cin, int cout, int parts, const float* __restrict__ partials,
                                float* __restrict__ dw) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
     const int n = 27 * cin * cout;
     if (e >= n) return;
     const int ci = e % cin, tap = (e / cin) % 27, co = e / (27 * cin);
-    const int64_t off = (int64_t)tap * cout * cin + co * cin + ci;
+    const int64_t off = (int64_t)tap * cout * cin + co * cin + ci, stride = (int64_t)27 * cout * cin;
     float sum = 0.f;
-    for (int p = 0; p < parts; ++p) sum += partials[(int64_t)p * 27 * cout * cin + off];
-    dw[e] = sum;
+    for (int p = lane; p < parts; p += 32) sum += partials[(int64_t)p * stride + off];
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, w);
+    if (lane == 0) dw[e] = sum;
 }
 
-// db[co] = sum_v dz[v][co]: one block per channel, fixed-order tree.
-__global__ void k_bias_grad(int64_t voxels, int cout, const bf16* __restrict__ dz, float* __restrict__ db) {
-    __shared__ float sh[256];
-    const int co = blockIdx.x;
-    float sum = 0.f;
-    for (int64_t v = threadIdx.x; v < voxels; v += 256) sum += __bfloat162float(dz[v * cout + co]);
-    sh[threadIdx.x] = sum;
+constexpr int kBiasBlocks = 512;  // blocks of the bias-gradient partial sums
+
+// Partial sums of db[co] = sum_v dz[v][co] over a contiguous range of voxels per block: thread t
+// reads 16-byte chunks t, t + 256, ... of the range (8 channels each; with cout / 8 chunks per
+// voxel its channel group is t % (cout / 8)), then a fixed tree over the threads of one group.
+__global__ void __launch_bounds__(256) k_bias_partials(int64_t voxels, int cout, const bf16* __restrict__ dz,
+                                                       float* __restrict__ partial) {
+    __shared__ float sh[256][8];
+    const int cg = cout / 8;
+    const int64_t v0 = voxels * blockIdx.x / gridDim.x, v1 = voxels * (blockIdx.x + 1) / gridDim.x;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const uint4* src = reinterpret_cast<const uint4*>(dz);
+    for (int64_t i = v0 * cg + threadIdx.x; i < v1 * cg; i += 256) {
+        const uint4 raw = src[i];
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&raw);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            acc[2 * k] += __bfloat162float(h[k].x);
+            acc[2 * k + 1] += __bfloat162float(h[k].y);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sh[threadIdx.x][k] = acc[k];
     __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    // threads of channel group g: g, g + cg, ...; halve that set in a fixed order
+    for (int w = 128; w >= cg; w >>= 1) {
+        if ((int)threadIdx.x < w)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) sh[threadIdx.x][k] += sh[threadIdx.x + w][k];
         __syncthreads();
     }
-    if (threadIdx.x == 0) db[co] = sh[0];
+    if ((int)threadIdx.x < cg)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) partial[(int64_t)blockIdx.x * cout + 8 * threadIdx.x + k] = sh[threadIdx.x][k];
+}
+
+// db[co] = sum over blocks of the partials, one warp per channel, fixed order.
+__global__ void k_bias_finish(int blocks, int cout, const float* __restrict__ partial, float* __restrict__ db) {
+    const int co = (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (co >= cout) return;
+    float sum = 0.f;
+    for (int b = lane; b < blocks; b += 32) sum += partial[(int64_t)b * cout + co];
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, w);
+    if (lane == 0) db[co] = sum;
 }
 
 __global__ void k_act_bwd(int64_t n, int act, const float* __restrict__ dy, const float* __restrict__ z,
@@ -711,18 +746,19 @@ __global__ void __launch_bounds__(384, 1)
                         break;
                     }
                     const int zz = wrapi(K.z0 - 1 + p, s.nz);
-                    if (elect_one()) {
-                        tp_expect_tx(bar(LT + slot), C::SLOT);
-                        for (int d = 0; d < 3; ++d) {
-                            const uint32_t dst = a_s + (uint32_t)(slot * C::SLOT + d * C::COPYB);
-                            if (y_inside) {
-                                tp_tma5(dst, &xrows, 16 * j, d - 1, K.y0 - 1, zz, K.b, bar(LT + slot));
-                            } else {
-                                for (int r = 0; r < C::HY; ++r)
-                                    tp_tma5(dst + (uint32_t)(r * kW * 32), &xrow, 16 * j, d - 1,
-                                            wrapi(K.y0 + r - 1, s.ny), zz, K.b, bar(LT + slot));
-                            }
-                        }
+                    // one box per lane, after lane 0 has posted the slot's byte count: lanes 0-2 the
+                    // three x-shifted copies (4 rows each), or, where rows wrap in y, lanes 0-11 one
+                    // row of one copy each
+                    if (lane == 0) tp_expect_tx(bar(LT + slot), C::SLOT);
+                    __syncwarp();
+                    if (y_inside) {
+                        if (lane < 3)
+                            tp_tma5(a_s + (uint32_t)(slot * C::SLOT + lane * C::COPYB), &xrows, 16 * j, lane - 1,
+                                    K.y0 - 1, zz, K.b, bar(LT + slot));
+                    } else if (lane < 3 * C::HY) {
+                        const int d = lane / C::HY, r = lane % C::HY;
+                        tp_tma5(a_s + (uint32_t)(slot * C::SLOT + d * C::COPYB + r * kW * 32), &xrow, 16 * j, d - 1,
+                                wrapi(K.y0 + r - 1, s.ny), zz, K.b, bar(LT + slot));
                     }
                     __syncwarp();
                 }
@@ -969,7 +1005,8 @@ __global__ void __launch_bounds__(384, 1)
 // layout: 8 channels of one row form a column of 64 16-byte chunks (1 KB,
 // written by one TMA box); columns are 1 KB apart (SBO) and the K direction is
 // contiguous (LBO = 128 B), so the k-th 16-voxel step of an MMA is a start
-// address 256 B further on.  The 9 cin/8 channel groups of A are cut into
+// address 256 B further on.  The producer issues a stage's boxes from as many
+// lanes, one box each.  The 9 cin/8 channel groups of A are cut into
 // M = 128 tiles of 16 groups (the last tile padded with groups that are never
 // loaded and whose rows are discarded); B holds the dZ row in three copies
 // shifted by dx = -1, 0, +1: each copy is one 64-voxel box starting one voxel
@@ -987,44 +1024,52 @@ __global__ void __launch_bounds__(384, 1)
 // ---------------------------------------------------------------------------
 template <int CIN, int COUT>
 struct WgCfg {
-    static constexpr int CG = CIN / 8;                  // channel groups of A per (dz, dy)
-    static constexpr int GROUPS = 9 * CG;               // column groups of A
-    static constexpr int NT = (GROUPS + 15) / 16;       // M = 128 tiles
+    static constexpr int RA = 2 * CIN;                  // bytes of one voxel's channels in A (32 or 64)
+    static constexpr int RB = 2 * COUT;                 // and in B
+    static constexpr int COLA = 64 * RA;                // one x row: a column (swizzle atom group) of A
+    static constexpr int COLB = 64 * RB;                // one shifted dz row: a column of B
+    static constexpr int PER_TILE = 128 / CIN;          // columns of A per M = 128 tile
+    static constexpr int NT = (9 + PER_TILE - 1) / PER_TILE;  // tiles over the 9 (dz, dy) rows
     static constexpr int N = 3 * COUT;                  // B columns: (dx, co)
     static constexpr int NS = (N + 31) / 32 * 32;       // tensor-memory columns per tile (32-aligned)
-    static constexpr int NG = N / 8;                    // column groups of B
     static constexpr int SB = 3;                        // B stages (one row each)
-    static constexpr int A_STAGE = 16 * 1024;
-    static constexpr int B_STAGE = NG * 1024;
+    static constexpr int A_STAGE = PER_TILE * COLA;     // 16 KB
+    static constexpr int B_STAGE = 3 * COLB;
     static constexpr int SA = (220 * 1024 - SB * B_STAGE) / A_STAGE;  // A stages (one tile of one row each)
     static constexpr int SMEM = SA * A_STAGE + SB * B_STAGE + 1024;
     static constexpr int TMEM_USED = NT * NS;
     static constexpr int TMEM_COLS = TMEM_USED <= 32 ? 32 : TMEM_USED <= 64 ? 64 : TMEM_USED <= 128 ? 128
                                      : TMEM_USED <= 256 ? 256 : 512;
     static constexpr int THREADS = 256;
+    // layout types of the shared-memory descriptors: 32- or 64-byte swizzle
+    static constexpr uint64_t SWA = RA == 64 ? 4 : 6, SWB = RB == 64 ? 4 : 6;
     // D F32, A and B BF16, both MN-major (bits 15, 16), N, M = 128
     static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
                                       ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    static_assert((CIN == 16 || CIN == 32) && (COUT == 16 || COUT == 32), "16 or 32 channels");
     static_assert(N % 16 == 0 && N <= 256, "N = 3 cout must be a multiple of 16, at most 256");
     static_assert(TMEM_USED <= 512, "tensor memory");
     static_assert(SMEM <= 232448, "shared memory");
 };
 
-// group g of A (0 .. 9 cin/8 - 1) -> (dz, dy, channel group): g = 3 ((dz+1) cin/8 + c) + (dy+1), so
-// that the three rows y - 1, y, y + 1 of one plane and channel group are consecutive groups (one
-// three-row box fills them)
-template <int CG>
-__device__ __forceinline__ void wg_group(int g, int& dz, int& dy, int& c) {
-    const int p = g / 3;
-    dy = g - 3 * p - 1;
-    c = p % CG;
-    dz = p / CG - 1;
+// Shared-memory descriptor of a swizzled MN-major operand: start address, LBO = stride between
+// atoms along M (N), SBO = stride between groups of 8 rows along K, layout type (6: 32-byte, 4:
+// 64-byte swizzle), descriptor version 1.
+__device__ __forceinline__ uint64_t umma_desc_mn(uint32_t saddr, uint32_t lbo, uint32_t sbo, uint64_t layout) {
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46) | (layout << 61);
+}
+
+// 16-byte chunk c of row v of a swizzled row of R bytes (R = 32: 32-byte swizzle, rows 4..7 of
+// each 8-row group swap their halves; R = 64: 64-byte swizzle, chunk c ^ ((v >> 1) & 3))
+template <int R>
+__device__ __forceinline__ uint32_t swz_chunk(int v, int c) {
+    return (uint32_t)(R == 64 ? (c ^ ((v >> 1) & 3)) : (c ^ ((v >> 2) & 1)));
 }
 
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(256, 1)
-    k_conv_wgrad_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap xmap3,
-                    const __grid_constant__ CUtensorMap zmap, sg_shape s,
+    k_conv_wgrad_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap zmap, sg_shape s,
                     const bf16* __restrict__ dzg, float* __restrict__ partials, long long wait_limit) {
     using C = WgCfg<CIN, COUT>;
     extern __shared__ __align__(1024) unsigned char sm_wg[];
@@ -1078,15 +1123,15 @@ __global__ void __launch_bounds__(256, 1)
                     ok = false;
                     break;
                 }
-                if (elect_one()) {
-                    tp_expect_tx(bar(BL + st), C::B_STAGE);
-                    const uint32_t dst0 = b_s + (uint32_t)(st * C::B_STAGE);
-                    for (int h = 0; h < C::NG; ++h) {
-                        // copy dxi holds dZ[(x' - dx) mod 64], dx = dxi - 1: a box starting at voxel
-                        // -dx (dx = +1: voxel 0 out of range; dx = -1: voxel 63 out of range)
-                        const int dxi = h / (COUT / 8), c0 = 8 * (h % (COUT / 8));
-                        tp_tma5(dst0 + (uint32_t)(h * 1024), &zmap, c0, 1 - dxi, y, z, b, bar(BL + st));
-                    }
+                // one box per lane (a TMA issue from one lane takes ~140 cycles; the lanes issue in
+                // parallel), after lane 0 has posted the stage's byte count
+                if (lane == 0) tp_expect_tx(bar(BL + st), C::B_STAGE);
+                __syncwarp();
+                if (lane < 3) {
+                    // copy dxi holds dZ[(x' - dx) mod 64], dx = dxi - 1: a box starting at voxel -dx
+                    // (dx = +1: voxel 0 out of range; dx = -1: voxel 63 out of range)
+                    const int dxi = lane;
+                    tp_tma5(b_s + (uint32_t)(st * C::B_STAGE + dxi * C::COLB), &zmap, 0, 1 - dxi, y, z, b, bar(BL + st));
                 }
                 __syncwarp();
                 ++qb;
@@ -1099,22 +1144,14 @@ __global__ void __launch_bounds__(256, 1)
                     ok = false;
                     break;
                 }
-                const int g0 = 16 * t, ng = min(16, C::GROUPS - g0);
-                const bool y_inside = y >= 1 && y + 1 < s.ny;
-                if (elect_one()) {
-                    tp_expect_tx(bar(AF + st), (uint32_t)(ng * 1024));
-                    for (int k = 0; k < ng;) {
-                        int dz, dy, c;
-                        wg_group<C::CG>(g0 + k, dz, dy, c);
-                        const uint32_t dst = a_s + (uint32_t)(st * C::A_STAGE + k * 1024);
-                        if (dy == -1 && k + 2 < ng && y_inside) {  // rows y - 1 .. y + 1 in one box
-                            tp_tma5(dst, &xmap3, 8 * c, 0, y - 1, wrapi(z + dz, s.nz), b, bar(AF + st));
-                            k += 3;
-                        } else {
-                            tp_tma5(dst, &xmap, 8 * c, 0, wrapi(y + dy, s.ny), wrapi(z + dz, s.nz), b, bar(AF + st));
-                            ++k;
-                        }
-                    }
+                // columns g0 .. g0 + ng - 1 of the 9 (dz, dy) rows, p = 3 (dz + 1) + (dy + 1)
+                const int g0 = C::PER_TILE * t, ng = min(C::PER_TILE, 9 - g0);
+                if (lane == 0) tp_expect_tx(bar(AF + st), (uint32_t)(ng * C::COLA));
+                __syncwarp();
+                if (lane < ng) {
+                    const int p = g0 + lane, dz = p / 3 - 1, dy = p % 3 - 1;
+                    tp_tma5(a_s + (uint32_t)(st * C::A_STAGE + lane * C::COLA), &xmap, 0, 0, wrapi(y + dy, s.ny),
+                            wrapi(z + dz, s.nz), b, bar(AF + st));
                 }
                 __syncwarp();
             }
@@ -1133,8 +1170,9 @@ __global__ void __launch_bounds__(256, 1)
                 fail();
         }
     } else if (warp == 2) {
-        // ---- wrap-voxel fixer: per row, lane l < 2 cout/8 writes one 16-byte voxel of a shifted
-        // copy: side 0 (dx = +1, copy 2) voxel 0 <- dZ[63]; side 1 (dx = -1, copy 0) voxel 63 <- dZ[0] ----
+        // ---- wrap-voxel fixer: per row, lane l < 2 cout/8 writes one 16-byte chunk of a shifted
+        // copy's wrap voxel: side 0 (dx = +1, copy 2) voxel 0 <- dZ[63]; side 1 (dx = -1, copy 0)
+        // voxel 63 <- dZ[0], at its swizzled place ----
         constexpr int COG = COUT / 8;
         const int side = lane / COG, c8 = lane % COG;
         const bool active = lane < 2 * COG;
@@ -1151,8 +1189,9 @@ __global__ void __launch_bounds__(256, 1)
                 if (lane == 0) fail();
                 break;
             }
-            const int h = (side ? 0 : 2) * COG + c8;
-            const uint32_t dst = b_s + (uint32_t)(st * C::B_STAGE + h * 1024 + (side ? 63 : 0) * 16);
+            const int v = side ? 63 : 0;
+            const uint32_t dst = b_s + (uint32_t)(st * C::B_STAGE + (side ? 0 : 2) * C::COLB + v * C::RB) +
+                                 16u * swz_chunk<C::RB>(v, c8);
             if (active)
                 asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(val.x), "r"(val.y), "r"(val.z),
                              "r"(val.w)
@@ -1172,7 +1211,7 @@ __global__ void __launch_bounds__(256, 1)
                 ok = false;
                 break;
             }
-            const uint64_t bdesc = umma_desc(b_s + (uint32_t)(bst * C::B_STAGE), 128, 1024);
+            const uint64_t bdesc = umma_desc_mn(b_s + (uint32_t)(bst * C::B_STAGE), C::COLB, 8 * C::RB, C::SWB);
             for (int t = 0; t < C::NT; ++t, ++qa) {
                 const int st = (int)(qa % C::SA);
                 if (!__all_sync(0xffffffffu, tc_wait(bar(AF + st), (qa / C::SA) & 1, wait_limit))) {
@@ -1181,12 +1220,12 @@ __global__ void __launch_bounds__(256, 1)
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint64_t adesc = umma_desc(a_s + (uint32_t)(st * C::A_STAGE), 128, 1024);
+                const uint64_t adesc = umma_desc_mn(a_s + (uint32_t)(st * C::A_STAGE), C::COLA, 8 * C::RA, C::SWA);
                 const uint32_t d_tmem = tmem + (uint32_t)(t * C::NS);
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk)  // 16 voxels per MMA: start address + 256 B
-                    tc_mma_elect(d_tmem, adesc + (uint64_t)(16 * kk), bdesc + (uint64_t)(16 * kk), C::IDESC,
-                                 (first && kk == 0) ? 0u : 1u);
+                for (int kk = 0; kk < 4; ++kk)  // 16 voxels per MMA: start address + 16 rows
+                    tc_mma_elect(d_tmem, adesc + (uint64_t)((16 * C::RA * kk) >> 4),
+                                 bdesc + (uint64_t)((16 * C::RB * kk) >> 4), C::IDESC, (first && kk == 0) ? 0u : 1u);
                 tc_commit_elect(bar(AE + st));
             }
             if (!ok) break;
@@ -1208,11 +1247,10 @@ __global__ void __launch_bounds__(256, 1)
             float* out = partials + (int64_t)blockIdx.x * 27 * COUT * CIN;
             const int m = 32 * q + lane;
             for (int t = 0; t < C::NT; ++t) {
-                const int g = 16 * t + (m >> 3), e = m & 7;
-                int dz = 0, dy = 0, c = 0;
-                const bool real = g < C::GROUPS;
-                if (real) wg_group<C::CG>(g, dz, dy, c);
-                const int ci = 8 * c + e;
+                // row m of tile t: column p = PER_TILE t + m / cin (the (dz, dy) row), channel m % cin
+                const int p = C::PER_TILE * t + m / CIN, ci = m % CIN;
+                const bool real = p < 9;
+                const int dz = p / 3 - 1, dy = p % 3 - 1;
 #pragma unroll
                 for (int n0 = 0; n0 < C::N; n0 += 16) {
                     float v[16];
@@ -1353,25 +1391,34 @@ static int launch_wgrad_tc(sg_shape s, const void* x, const void* dz, float* par
     }
     auto encode = tensor_map_encoder();
     if (!encode) return -3;
-    // x[b][z][y][x][ci], dz[b][z][y][x][co] as 5D tensors (channels fastest); boxes of 8 channels
-    // (16 bytes) x 64 voxels x 1 or 3 rows, no swizzle: each row one column of an MN-major operand
-    auto enc = [&](CUtensorMap* m, const void* ptr, int ch, uint32_t rows) {
+    // x[b][z][y][x][ci], dz[b][z][y][x][co] as 5D tensors (channels fastest); boxes of all channels
+    // x 64 voxels of one row, 32- or 64-byte swizzled: one column of a swizzled MN-major operand
+    auto enc = [&](CUtensorMap* m, const void* ptr, int ch) {
         const cuuint64_t dims[5] = {(cuuint64_t)ch, (cuuint64_t)kW, (cuuint64_t)s.ny, (cuuint64_t)s.nz,
                                     (cuuint64_t)s.batch};
         const cuuint64_t strides[4] = {(cuuint64_t)ch * 2, (cuuint64_t)kW * ch * 2, (cuuint64_t)s.ny * kW * ch * 2,
                                        (cuuint64_t)s.nz * s.ny * kW * ch * 2};
-        const cuuint32_t box[5] = {8, (cuuint32_t)kW, rows, 1, 1};
+        const cuuint32_t box[5] = {(cuuint32_t)ch, (cuuint32_t)kW, 1, 1, 1};
         const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
         return encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(ptr), dims, strides, box, estr,
-                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, ch == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     };
-    alignas(64) CUtensorMap xm, xm3, zm;
-    if (!enc(&xm, x, CIN, 1) || !enc(&xm3, x, CIN, 3) || !enc(&zm, dz, COUT, 1)) return -3;
+    alignas(64) CUtensorMap xm, zm;
+    if (!enc(&xm, x, CIN) || !enc(&zm, dz, COUT)) return -3;
     const long long wait_limit = 2000000000LL;  // ~1 s of SM clock per wait
-    k_conv_wgrad_tc<CIN, COUT><<<ctas, C::THREADS, C::SMEM, st>>>(xm, xm3, zm, s, static_cast<const bf16*>(dz),
-                                                                   partials, wait_limit);
+    k_conv_wgrad_tc<CIN, COUT><<<ctas, C::THREADS, C::SMEM, st>>>(xm, zm, s, static_cast<const bf16*>(dz), partials,
+                                                                   wait_limit);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+// Weight-gradient partial sums either kernel may write: the mma.sync one's voxel partitions or the
+// tcgen05 one's CTAs (at most one per row, at most kWgMaxCtas).
+static int64_t wgrad_parts_max(sg_shape s) {
+    const int64_t rows = (int64_t)s.batch * s.nz * s.ny;
+    const int64_t tc = rows < kWgMaxCtas ? rows : kWgMaxCtas;
+    const int64_t mma = parts_for(s);
+    return tc > mma ? tc : mma;
 }
 
 template <int CIN, int COUT>
@@ -1390,9 +1437,14 @@ static int launch_wgrad(sg_shape s, const void* x, const void* dz, float* dw, fl
                                                                          static_cast<const bf16*>(dz), partials, parts);
     }
     const int n = 27 * CIN * COUT;
-    k_wgrad_reduce<<<(n + 255) / 256, 256, 0, st>>>(CIN, COUT, parts, partials, dw);
-    const int64_t voxels = (int64_t)s.batch * s.nz * s.ny * s.nx;
-    if (db) k_bias_grad<<<COUT, 256, 0, st>>>(voxels, COUT, static_cast<const bf16*>(dz), db);
+    k_wgrad_reduce<<<(n + 7) / 8, 256, 0, st>>>(CIN, COUT, parts, partials, dw);
+    if (db) {
+        // bias partials after the largest weight-gradient partials either kernel writes
+        float* bias_part = partials + wgrad_parts_max(s) * 27 * CIN * COUT;
+        const int64_t voxels = (int64_t)s.batch * s.nz * s.ny * s.nx;
+        k_bias_partials<<<kBiasBlocks, 256, 0, st>>>(voxels, COUT, static_cast<const bf16*>(dz), bias_part);
+        k_bias_finish<<<1, 32 * COUT, 0, st>>>(kBiasBlocks, COUT, bias_part, db);
+    }
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -1466,12 +1518,8 @@ int sg_transpose_weights(int cin, int cout, const void* w, void* wt, void* strea
 }
 
 int64_t sg_wgrad_scratch_bytes(sg_shape s, int cin, int cout) {
-    // enough for either kernel: the mma.sync one's voxel partitions, the tcgen05 one's CTAs
-    const int64_t rows = (int64_t)s.batch * s.nz * s.ny;
-    int64_t parts = parts_for(s);
-    const int64_t tc = rows < kWgMaxCtas ? rows : kWgMaxCtas;
-    if (tc > parts) parts = tc;
-    return parts * 27 * cin * cout * (int64_t)sizeof(float);
+    // the weight-gradient partials of either kernel, then the bias partials
+    return (wgrad_parts_max(s) * 27 * cin * cout + (int64_t)kBiasBlocks * cout) * (int64_t)sizeof(float);
 }
 
 int sg_conv3d_wgrad(sg_shape s, int cin, int cout, const void* x, const void* dz, float* dw, float* db, void* scratch,
