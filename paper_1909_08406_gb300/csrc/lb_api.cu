@@ -74,6 +74,13 @@ static Lattice make_lattice() {
             k.n4[s] += cx * cx * cx * cx;
             k.n22[s] += cx * cx * cy * cy;
         }
+        // the projection's shell sums folded into cubics in eta
+        for (int p = 0; p < 4; ++p) {
+            k.pj[0][p] += k.w[s] * k.n2[s] * pk[s][p];
+            k.pj[1][p] += k.w[s] * k.n2[s] * csq * pk[s][p];
+            k.pj[2][p] += k.w[s] * k.n4[s] * pk[s][p];
+            k.pj[3][p] += k.w[s] * k.n22[s] * pk[s][p];
+        }
     }
     double A[4] = {0, 0, 0, 0}, B[4] = {0, 0, 0, 0};
     for (int i = 0; i < kQ; ++i) {
@@ -105,6 +112,8 @@ static Lattice make_lattice() {
         f.n4[s] = (float)k.n4[s];
         f.n22[s] = (float)k.n22[s];
     }
+    for (int j = 0; j < 4; ++j)
+        for (int p = 0; p < 4; ++p) f.pj[j][p] = (float)k.pj[j][p];
     for (int p = 0; p < 4; ++p) {
         f.m2[p] = (float)k.m2[p];
         f.m2p[p] = (float)k.m2p[p];
