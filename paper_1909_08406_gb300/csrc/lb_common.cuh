@@ -285,10 +285,13 @@ __device__ __forceinline__ bool state_ok(const NodeState<R>& st) {
            fabs(st.uz) < R(1e30);
 }
 
+// Two nodes: rho > 0, theta > 0 and |rho| + |eta| + |u_x| + |u_y| + |u_z| below 1e30 for both (a NaN
+// or an infinity in any of them fails the last comparison).
 __device__ __forceinline__ bool state_ok(const NodeState<F2>& st) {
-    NodeState<float> a{st.drho.v.x, st.rho.v.x, st.ux.v.x, st.uy.v.x, st.uz.v.x, st.eta.v.x};
-    NodeState<float> b{st.drho.v.y, st.rho.v.y, st.ux.v.y, st.uy.v.y, st.uz.v.y, st.eta.v.y};
-    return state_ok(a) && state_ok(b);
+    const float ma = st.rho.v.x + st.eta.v.x + fabsf(st.ux.v.x) + fabsf(st.uy.v.x) + fabsf(st.uz.v.x);
+    const float mb = st.rho.v.y + st.eta.v.y + fabsf(st.ux.v.y) + fabsf(st.uy.v.y) + fabsf(st.uz.v.y);
+    return st.rho.v.x > 0.f && st.rho.v.y > 0.f && st.eta.v.x > -1.f && st.eta.v.y > -1.f && ma < 1e30f &&
+           mb < 1e30f;
 }
 
 // Equilibrium (Eq. feqGenU3, with the optional momentum projection) and BGK
