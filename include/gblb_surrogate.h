@@ -51,10 +51,12 @@ int sg_conv3d_fwd(sg_shape s, int cin, int cout, const void *x, const void *w, c
 /* Kernel of the two convolution entry points above and of sg_conv3d_wgrad:
  *   SG_CONV_TCGEN05  (default) 5th-generation tensor cores: tcgen05.mma with
  *                    the FP32 accumulator in tensor memory, M = 128 voxels,
- *                    N = cout, K = 16 per instruction; persistent CTAs with the
- *                    weights resident in shared memory.  A wait for the tensor
- *                    cores that runs out of time (~1 s) ends the kernel and
- *                    is reported by sg_status.
+ *                    K = 16 per instruction; the forward kernel puts the
+ *                    three x taps of a (dz, dy) side by side in N = 3 cout
+ *                    and combines them, shifted by one voxel, in its epilogue.
+ *                    Persistent CTAs with the weights resident in shared
+ *                    memory.  A wait for the tensor cores that runs out of
+ *                    time (~1 s) ends the kernel and is reported by sg_status.
  *   SG_CONV_MMA_SYNC warp-level mma.sync.m16n8k16.
  * Returns the previous setting, or -1 for an unknown value.  Process-wide. */
 #define SG_CONV_MMA_SYNC 0

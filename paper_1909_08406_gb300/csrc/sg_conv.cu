@@ -495,20 +495,12 @@ __global__ void k_unpack(sg_shape s, int item, const bf16* __restrict__ x, doubl
 }
 
 // ---------------------------------------------------------------------------
-// Forward convolution on the 5th-generation tensor cores (tcgen05, TMEM).
-//
-// Implicit GEMM per tile of M = 128 output voxels (two 64-voxel rows of one
-// z-plane): D[128][cout] (FP32, in tensor memory) = sum over the 27 taps and
-// the cin/16 K-slices of A_tap[128][16] x B_tap[16][cout], one
-// tcgen05.mma.kind::f16 (BF16 in, FP32 accumulate, M=128, N=cout, K=16) each,
-// issued by one thread.  Operands sit in shared memory in the canonical
-// no-swizzle K-major layout: 8 x 16-byte "core matrices", stride 128 B along
-// M (or N) and LBO along K.  The halo (3 planes x 4 rows x 64 voxels) is kept
-// in three copies shifted by dx = -1, 0, +1 in x (periodic), with the 64
-// voxels of a row unpadded, so that the 128 rows of A for any tap are
-// uniformly 16 bytes apart and a tap is only a different descriptor start
-// address: + (dz+1) planes + (dy+1) rows in the copy of its dx.  The weights
-// of all 27 taps stay resident in shared memory.
+// Helpers of the kernels on the 5th-generation tensor cores (tcgen05, tensor
+// memory, TMA): shared-memory matrix descriptors, MMA issue and commit by one
+// elected lane, bounded mbarrier waits and tensor-memory loads.  Descriptors
+// follow the canonical layouts: no swizzle (8-row x 16-byte core matrices,
+// LBO along K and SBO along M or N for a K-major operand) and the 32/64-byte
+// swizzled layouts that TMA writes.
 // ---------------------------------------------------------------------------
 __device__ int g_sg_status;  // bit 0: a tensor-core wait ran out of time
 
@@ -574,42 +566,6 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// ---------------------------------------------------------------------------
-// Pipelined forward convolution on tcgen05 with TMA operand loads.
-//
-// Same implicit GEMM as above (tile = 128 voxels of two rows, one
-// tcgen05.mma M=128 x N=cout x K=16 per tap and 16-channel slice).  A CTA
-// walks columns of ZC tiles along z (same batch item and row pair); for each
-// 16-channel slice it streams the column's ZC + 2 halo planes (4 rows x 64
-// voxels x 16 channels, in the three x-shifted copies) through a ring of 6
-// plane slots, so each plane is loaded once per column instead of once per
-// tile, tile k of the column uses the slots of planes k, k+1, k+2, and the
-// producer runs up to three planes ahead of the MMAs.
-// Operand A uses the 32-byte-swizzled K-major layout (rows of 16 channels =
-// 32 B, 8-row atoms of 256 B), which the TMA writes directly
-// (CU_TENSOR_MAP_SWIZZLE_32B); B stays in the no-swizzle layout.  Warp roles:
-//   warp 0               TMA producer (warp-uniform loop, one elected lane issues):
-//                        per plane slot one box of 16 channels x
-//                        64 voxels x 4 rows per x-shifted copy (or one box per
-//                        row where the rows wrap around the periodic y
-//                        boundary; z wraps per plane).  A box shifted by -1 /
-//                        +1 in x starts or ends one voxel outside the row; the
-//                        tensor map fills that voxel with zeros.
-//   warp 1               periodic-wrap fixer: writes those voxels (loaded from
-//                        global memory before the box lands) and marks the slot
-//                        full.
-//   warp 2               MMA issuer (warp-uniform loop, one elected lane issues):
-//                        27 MMAs per tile and slice into one of
-//                        2 x ZC accumulators in tensor memory; tcgen05.commit
-//                        frees plane slots and fills accumulators.
-//   warps 4-11           epilogue (two per tensor-memory lane quarter, half the
-//                        columns each): tcgen05.ld of an accumulator, free it, bias,
-//                        activation, residual and add, store -- concurrently
-//                        with the MMAs of the next tiles.
-// All hand-offs are mbarriers; every wait is bounded (on expiry the kernel
-// sets the status flag and the roles wind down after waiting, bounded, for
-// their own asynchronous work).
-// ---------------------------------------------------------------------------
 __device__ __forceinline__ void tc_ld8(uint32_t taddr, float (&v)[8]) {
     uint32_t r[8];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -619,31 +575,6 @@ __device__ __forceinline__ void tc_ld8(uint32_t taddr, float (&v)[8]) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
-
-template <int CIN, int COUT>
-struct TczCfg {
-    static constexpr int K8 = CIN / 8;
-    static constexpr int SL = CIN / 16;                 // 16-channel K slices
-    static constexpr int HY = 4;                        // halo rows of a 2-row tile
-    static constexpr int ZC = 4;                        // tiles per column along z
-    static constexpr int NSLOT = 6;                     // plane slots in the ring (3 in use, 3 ahead)
-    static constexpr int COPYB = HY * kW * 32;          // one x-shifted copy of one plane: 8 KB
-    static constexpr int SLOT = 3 * COPYB;              // 24 KB
-    static constexpr int A_BYTES = NSLOT * SLOT;
-    static constexpr int WTAP = K8 * COUT * 16;
-    static constexpr int B_BYTES = 27 * WTAP;
-    static constexpr int SMEM = A_BYTES + B_BYTES + 1024;
-    static constexpr int THREADS = 384;                 // warps 0-2 roles, 3 spare, 4-11 epilogue
-    static constexpr int EPI_WARPS = 8;                 // two per tensor-memory lane quarter
-    static constexpr int EPI_COLS = COUT / 2;           // accumulator columns per epilogue warp
-    static constexpr int NACC = 2 * ZC;                 // accumulators of 32 columns
-    static constexpr int TMEM_COLS = NACC * 32;         // 256
-    static constexpr uint32_t IDESC =
-        (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(COUT >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-    static_assert(COUT % 16 == 0 && COUT <= 32, "N = cout: 16 or 32");
-    static_assert(CIN % 16 == 0, "cin: multiple of 16");
-    static_assert(SMEM <= 232448, "shared memory");
-};
 
 // Shared-memory descriptor of a 32-byte-swizzled K-major operand: 8-row atoms
 // of 256 B (SBO), layout type 6; the leading offset is unused for K = 16.
@@ -670,29 +601,154 @@ __device__ __forceinline__ void tp_tma5(uint32_t dst, const CUtensorMap* map, in
         : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Forward convolution on tcgen05 with the three x taps side by side in N.
+//
+// A tile is 128 output voxels (two rows y0, y0 + 1 of one plane z).  For each
+// (dz, dy) and 16-channel slice one tcgen05.mma multiplies the UNSHIFTED halo
+// rows (A: 128 voxels x 16 channels, rows y0 + dy .. of plane z + dz) by the
+// weights of the three taps dx = -1, 0, +1 of that (dz, dy) stacked along N
+// (B: 3 cout x 16 channels).  Accumulator column block dxi then holds
+//   D_dx[x'] = sum_(dz, dy, ci) W[co][dz, dy, dx][ci] X[z + dz, y + dy, x'][ci]
+// at the lane of input voxel x', and the output is
+//   y[x] = D_-1[x - 1] + D_0[x] + D_+1[x + 1]    (x periodic over the row),
+// which the epilogue forms from its own lane, the neighbouring lanes (warp
+// shuffles), and, at the two ends of each 32-lane quarter, the partner warp
+// that holds the other half of the row (through shared memory).  Against the
+// 27-tap form this reads each A operand once per (dz, dy) instead of three
+// times, and keeps one copy of each halo plane instead of three x-shifted ones.
+//
+// Work: the tiles, numbered z fastest within a column (batch item, row pair),
+// are split into one contiguous range per CTA.  A run of consecutive z within
+// a column streams its planes z - 1 .. z_end through a ring of NSLOT plane
+// slots (each plane: all channel slices, 4 rows x 64 voxels, 32-byte-swizzled
+// K-major as TMA writes it), so tile k uses the slots of planes k, k + 1, k + 2.
+// Warp roles:
+//   warp 0     TMA producer (one box per slice and plane, one per row where the
+//              rows wrap around the periodic y boundary)
+//   warp 1     MMA issuer (9 x slices MMAs per tile, one elected lane)
+//   warps 4-11 epilogue (two per tensor-memory lane quarter, half the output
+//              channels each)
+// All hand-offs are mbarriers and every wait is bounded; on expiry the kernel
+// sets the status flag and each role waits, bounded, for its own asynchronous
+// work before tensor memory is freed.
+// ---------------------------------------------------------------------------
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(384, 1)
-    k_conv_fwd_tcz(const __grid_constant__ CUtensorMap xrows, const __grid_constant__ CUtensorMap xrow, sg_shape s,
+struct TcxCfg {
+    static constexpr int K8 = CIN / 8;
+    static constexpr int SL = CIN / 16;                  // 16-channel K slices
+    static constexpr int HY = 4;                         // halo rows of a 2-row tile
+    static constexpr int SLICEB = HY * kW * 32;          // one slice of one plane: 8 KB
+    static constexpr int PLANE = SL * SLICEB;
+    static constexpr int N = 3 * COUT;                   // dx-stacked output columns
+    static constexpr int GB = K8 * N * 16;               // weights of one (dz, dy)
+    static constexpr int B_BYTES = 9 * GB;
+    static constexpr int NSLOT_FIT = (225 * 1024 - 1024 - B_BYTES) / PLANE;
+    static constexpr int NSLOT = NSLOT_FIT < 12 ? NSLOT_FIT : 12;
+    static constexpr int A_BYTES = NSLOT * PLANE;
+    static constexpr int SMEM = A_BYTES + B_BYTES + 1024;
+    static constexpr int THREADS = 640;                  // warps 0-1 roles, 2-3 spare, 4-19 epilogue
+    static constexpr int EPI_GROUPS = 2;                 // epilogue groups, alternating tiles
+    static constexpr int EPI_WARPS = 8;                  // per group
+    static constexpr int EC = COUT / 2;                  // output channels per epilogue warp
+    static constexpr int ACOLS = (N + 31) / 32 * 32;     // tensor-memory columns per accumulator
+    static constexpr int NACC = 512 / ACOLS;
+    static constexpr int TMEM_COLS = 512;
+    static constexpr uint32_t IDESC =
+        (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    static_assert(COUT == 16 || COUT == 32, "cout: 16 or 32");
+    static_assert(CIN % 16 == 0, "cin: multiple of 16");
+    static_assert(NSLOT >= 4, "plane ring");
+    static_assert(SMEM <= 232448 - 4096, "shared memory");
+};
+
+// Three blocks of N columns of a lane quarter (at ta, tb, tc), one wait for all three.
+__device__ __forceinline__ void tc_ld3(uint32_t ta, uint32_t tb, uint32_t tc, float (&fa)[16], float (&fb)[16],
+                                       float (&fc)[16]) {
+    uint32_t a[16], b[16], c[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%48];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%49];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47}, [%50];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]), "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15]),
+          "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3]), "=r"(b[4]), "=r"(b[5]), "=r"(b[6]), "=r"(b[7]), "=r"(b[8]), "=r"(b[9]), "=r"(b[10]), "=r"(b[11]), "=r"(b[12]), "=r"(b[13]), "=r"(b[14]), "=r"(b[15]),
+          "=r"(c[0]), "=r"(c[1]), "=r"(c[2]), "=r"(c[3]), "=r"(c[4]), "=r"(c[5]), "=r"(c[6]), "=r"(c[7]), "=r"(c[8]), "=r"(c[9]), "=r"(c[10]), "=r"(c[11]), "=r"(c[12]), "=r"(c[13]), "=r"(c[14]), "=r"(c[15])
+        : "r"(ta), "r"(tb), "r"(tc));
+#pragma unroll
+    for (int j = 0; j < 16; ++j) fa[j] = __uint_as_float(a[j]), fb[j] = __uint_as_float(b[j]), fc[j] = __uint_as_float(c[j]);
+}
+__device__ __forceinline__ void tc_ld3(uint32_t ta, uint32_t tb, uint32_t tc, float (&fa)[8], float (&fb)[8],
+                                       float (&fc)[8]) {
+    uint32_t a[8], b[8], c[8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%24];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%25];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%26];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]),
+          "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3]), "=r"(b[4]), "=r"(b[5]), "=r"(b[6]), "=r"(b[7]),
+          "=r"(c[0]), "=r"(c[1]), "=r"(c[2]), "=r"(c[3]), "=r"(c[4]), "=r"(c[5]), "=r"(c[6]), "=r"(c[7])
+        : "r"(ta), "r"(tb), "r"(tc));
+#pragma unroll
+    for (int j = 0; j < 8; ++j) fa[j] = __uint_as_float(a[j]), fb[j] = __uint_as_float(b[j]), fc[j] = __uint_as_float(c[j]);
+}
+
+// NW 32-bit words from p (16-byte aligned), and their addition to EC values: FP32 words (NW = EC)
+// or pairs of bf16 (NW = EC / 2).
+template <int NW>
+__device__ __forceinline__ void ld_words(const uint4* p, uint32_t (&dst)[NW]) {
+#pragma unroll
+    for (int h = 0; h < NW / 4; ++h) {
+        const uint4 raw = __ldg(p + h);
+        dst[4 * h] = raw.x, dst[4 * h + 1] = raw.y, dst[4 * h + 2] = raw.z, dst[4 * h + 3] = raw.w;
+    }
+}
+template <int EC, int NW>
+__device__ __forceinline__ void add_words(float (&o)[EC], const uint32_t (&src)[NW]) {
+    if constexpr (NW == EC) {
+#pragma unroll
+        for (int e = 0; e < EC; ++e) o[e] += __uint_as_float(src[e]);
+    } else {
+#pragma unroll
+        for (int e = 0; e < EC / 2; ++e) {
+            const __nv_bfloat162 h2 = *reinterpret_cast<const __nv_bfloat162*>(&src[e]);
+            o[2 * e] += __bfloat162float(h2.x);
+            o[2 * e + 1] += __bfloat162float(h2.y);
+        }
+    }
+}
+
+// WIDE: the values loaded ahead are FP32 (an FP32 added tensor and no residual input).
+template <int CIN, int COUT, bool WIDE>
+__global__ void __launch_bounds__(640, 1)
+    k_conv_fwd_tcx(const __grid_constant__ CUtensorMap xrows, const __grid_constant__ CUtensorMap xrow, sg_shape s,
                    const bf16* __restrict__ x, const bf16* __restrict__ w, const float* __restrict__ bias, Epi epi,
                    void* y, long long wait_limit) {
-    using C = TczCfg<CIN, COUT>;
-    extern __shared__ __align__(1024) unsigned char sm_tcz[];
-    // barriers: TMA landed, slot full, slot empty [NSLOT each], accumulator full, accumulator empty [NACC each], drain
-    __shared__ __align__(8) uint64_t bars[3 * C::NSLOT + 2 * C::NACC + 1];
+    using C = TcxCfg<CIN, COUT>;
+    constexpr int EC = C::EC;
+    extern __shared__ __align__(1024) unsigned char sm_tcx[];
+    // barriers: plane landed, plane slot empty [NSLOT each], accumulator full, accumulator empty
+    // [NACC each], row-end exchange [2 groups x 4 warp pairs], drain
+    __shared__ __align__(8) uint64_t bars[2 * C::NSLOT + 2 * C::NACC + 8 + 1];
+    // row-end exchange: [group][pair][warp of the pair][use parity][0: D_-1 of lane 31, 1: D_+1 of lane 0][EC]
+    __shared__ float xch[2][4][2][2][2][EC];
     __shared__ uint32_t tmem_holder;
-    const uint32_t base = (smem_u32(sm_tcz) + 1023u) & ~1023u;
-    unsigned char* smem = sm_tcz + (base - smem_u32(sm_tcz));
+    const uint32_t base = (smem_u32(sm_tcx) + 1023u) & ~1023u;
+    unsigned char* smem = sm_tcx + (base - smem_u32(sm_tcx));
     const uint32_t a_s = base, b_s = base + C::A_BYTES;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    constexpr int LT = 0, FU = C::NSLOT, EM = 2 * C::NSLOT, AF = 3 * C::NSLOT, AE = AF + C::NACC, DR = AE + C::NACC;
+    constexpr int LT = 0, EM = C::NSLOT, AF = 2 * C::NSLOT, AE = AF + C::NACC, XF = AE + C::NACC, DR = XF + 8;
     auto bar = [&](int k) { return smem_u32(&bars[k]); };
 
-    // weights of all taps: B[tap][k8][co][8 channels] <- w[co][tap][k8 * 8 ..]
+    // weights: B[g = 3 (dz+1) + (dy+1)][k8][n = 3-tap column dxi * cout + co][8 channels]
+    //          <- w[co][tap = 3 g + dxi][k8 * 8 ..]
     unsigned char* Bw = smem + C::A_BYTES;
     for (int i = tid; i < 27 * C::K8 * COUT; i += C::THREADS) {
         const int co = i % COUT, r = i / COUT;
         const int k8 = r % C::K8, tap = r / C::K8;
-        *reinterpret_cast<uint4*>(Bw + (size_t)((tap * C::K8 + k8) * COUT + co) * 16) =
+        const int g = tap / 3, dxi = tap % 3;
+        *reinterpret_cast<uint4*>(Bw + (size_t)((g * C::K8 + k8) * C::N + dxi * COUT + co) * 16) =
             *reinterpret_cast<const uint4*>(w + ((size_t)co * 27 + tap) * CIN + k8 * 8);
     }
     if (warp == 0) {
@@ -701,8 +757,10 @@ __global__ void __launch_bounds__(384, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int k = 0; k <= DR; ++k)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(k)), "r"(k >= AE && k < DR ? C::EPI_WARPS : 1));
+        for (int k = 0; k <= DR; ++k) {
+            const int cnt = (k >= AE && k < XF) ? C::EPI_WARPS : (k >= XF && k < DR ? 4 : 1);  // AE: one group
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(k)), "r"(cnt));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -711,61 +769,55 @@ __global__ void __launch_bounds__(384, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_holder;
 
-    // columns: (batch item, row pair, chunk of ZC planes); consecutive columns are neighbouring row pairs
+    // tiles t = (column (b, row pair), z), z fastest; CTA c owns [t0, t1)
     const int tiles_y = s.ny / 2;
-    const int nchunks = (s.nz + C::ZC - 1) / C::ZC;
-    const int64_t ncols = (int64_t)s.batch * nchunks * tiles_y;
-    struct Col {
-        int b, z0, len, y0;
+    const int64_t ntiles = (int64_t)s.batch * tiles_y * s.nz;
+    const int64_t t0 = ntiles * blockIdx.x / gridDim.x, t1 = ntiles * (blockIdx.x + 1) / gridDim.x;
+    // the run of tiles that starts at t: same column, consecutive z, within [t, t1)
+    struct Run {
+        int b, y0, z0, len;
     };
-    auto col_of = [&](int64_t c) {
-        const int yt = (int)(c % tiles_y);
-        const int64_t r = c / tiles_y;
-        const int ch = (int)(r % nchunks);
-        const int b = (int)(r / nchunks);
-        const int z0 = ch * C::ZC;
-        return Col{b, z0, min(C::ZC, s.nz - z0), 2 * yt};
+    auto run_at = [&](int64_t t) {
+        const int64_t col = t / s.nz;
+        const int z0 = (int)(t - col * s.nz);
+        const int64_t end = min(t1, (col + 1) * (int64_t)s.nz);
+        return Run{(int)(col / tiles_y), 2 * (int)(col % tiles_y), z0, (int)(end - t)};
     };
     auto fail = [&]() { atomicOr(&g_sg_status, 1); };
 
     if (warp == 0) {
-        // ---- TMA producer: plane loads in order (column, slice, plane); the whole warp runs the
-        // loop (warp-uniform coordinates), one elected lane issues ----
+        // ---- TMA producer: plane loads in order (run, plane); warp-uniform loop ----
         uint32_t q = 0;  // plane-load sequence number
         bool ok = true;
-        for (int64_t c = blockIdx.x; c < ncols && ok; c += gridDim.x) {
-            const Col K = col_of(c);
-            const bool y_inside = K.y0 >= 1 && K.y0 + 2 < s.ny;
-            for (int j = 0; j < C::SL && ok; ++j)
-                for (int p = 0; p < K.len + 2; ++p, ++q) {
-                    const int slot = (int)(q % C::NSLOT);
-                    const uint32_t use = q / C::NSLOT;
-                    if (!__all_sync(0xffffffffu, tc_wait(bar(EM + slot), (use & 1) ^ 1, wait_limit))) {
-                        if (lane == 0) fail();
-                        ok = false;
-                        break;
-                    }
-                    const int zz = wrapi(K.z0 - 1 + p, s.nz);
-                    // one box per lane, after lane 0 has posted the slot's byte count: lanes 0-2 the
-                    // three x-shifted copies (4 rows each), or, where rows wrap in y, lanes 0-11 one
-                    // row of one copy each
-                    if (lane == 0) tp_expect_tx(bar(LT + slot), C::SLOT);
-                    __syncwarp();
-                    if (y_inside) {
-                        if (lane < 3)
-                            tp_tma5(a_s + (uint32_t)(slot * C::SLOT + lane * C::COPYB), &xrows, 16 * j, lane - 1,
-                                    K.y0 - 1, zz, K.b, bar(LT + slot));
-                    } else if (lane < 3 * C::HY) {
-                        const int d = lane / C::HY, r = lane % C::HY;
-                        tp_tma5(a_s + (uint32_t)(slot * C::SLOT + d * C::COPYB + r * kW * 32), &xrow, 16 * j, d - 1,
-                                wrapi(K.y0 + r - 1, s.ny), zz, K.b, bar(LT + slot));
-                    }
-                    __syncwarp();
+        for (int64_t t = t0; t < t1 && ok;) {
+            const Run R = run_at(t);
+            const bool y_inside = R.y0 >= 1 && R.y0 + 2 < s.ny;
+            for (int p = 0; p < R.len + 2; ++p, ++q) {
+                const int slot = (int)(q % C::NSLOT);
+                const uint32_t use = q / C::NSLOT;
+                if (!__all_sync(0xffffffffu, tc_wait(bar(EM + slot), (use & 1) ^ 1, wait_limit))) {
+                    if (lane == 0) fail();
+                    ok = false;
+                    break;
                 }
+                const int zz = wrapi(R.z0 - 1 + p, s.nz);
+                if (lane == 0) tp_expect_tx(bar(LT + slot), C::PLANE);
+                __syncwarp();
+                const uint32_t dst = a_s + (uint32_t)(slot * C::PLANE);
+                if (y_inside) {
+                    if (lane < C::SL)
+                        tp_tma5(dst + (uint32_t)(lane * C::SLICEB), &xrows, 16 * lane, 0, R.y0 - 1, zz, R.b,
+                                bar(LT + slot));
+                } else if (lane < C::SL * C::HY) {
+                    const int j = lane / C::HY, r = lane % C::HY;
+                    tp_tma5(dst + (uint32_t)(j * C::SLICEB + r * kW * 32), &xrow, 16 * j, 0, wrapi(R.y0 + r - 1, s.ny),
+                            zz, R.b, bar(LT + slot));
+                }
+                __syncwarp();
+            }
+            t += R.len;
         }
-        // the CTA must not exit with boxes still landing: q plane loads were issued (sequence numbers
-        // 0 .. q - 1; a failed wait breaks before its iteration issues or counts), so wait for the
-        // last use of every slot, whether the loop finished or stopped on a failed wait
+        // wait for the last use of every slot that was loaded (sequence numbers q - 1 down)
         for (uint32_t k = 0; k < (uint32_t)C::NSLOT && k < q; ++k) {
             const uint32_t sq = q - 1 - k;
             if (!__all_sync(0xffffffffu, tc_wait(bar(LT + (int)(sq % C::NSLOT)), (sq / C::NSLOT) & 1, wait_limit)) &&
@@ -773,213 +825,203 @@ __global__ void __launch_bounds__(384, 1)
                 fail();
         }
     } else if (warp == 1) {
-        // ---- periodic-wrap fixer: copy 0 voxel 0 <- in[63], copy 2 voxel 63 <- in[0], 4 rows ----
-        uint32_t q = 0;
+        // ---- MMA issuer ----
+        uint32_t q = 0;   // sequence number of the first plane of the current run
+        uint32_t tt = 0;  // tile ordinal of this CTA (accumulator ring)
         bool ok = true;
-        for (int64_t c = blockIdx.x; c < ncols && ok; c += gridDim.x) {
-            const Col K = col_of(c);
-            for (int j = 0; j < C::SL && ok; ++j)
-                for (int p = 0; p < K.len + 2; ++p, ++q) {
-                    const int slot = (int)(q % C::NSLOT);
-                    const uint32_t use = q / C::NSLOT;
-                    // lane < 16: side (2) x row (4) x 16-byte half of the voxel (2)
-                    const int l = lane & 15;
-                    const int side = l >> 3, r = (l >> 1) & 3, h = l & 1;
-                    const int zz = wrapi(K.z0 - 1 + p, s.nz), yy = wrapi(K.y0 + r - 1, s.ny);
-                    const int xs = side ? 0 : kW - 1, pos = side ? kW - 1 : 0;
-                    const uint4 val = *reinterpret_cast<const uint4*>(
-                        x + ((((int64_t)K.b * s.nz + zz) * s.ny + yy) * kW + xs) * CIN + 16 * j + 8 * h);
-                    // 32-byte swizzle: the two 16-byte halves of rows 4..7 of an 8-row atom trade places
-                    const uint32_t dst = a_s + (uint32_t)(slot * C::SLOT + (side ? 2 : 0) * C::COPYB + r * kW * 32 +
-                                                          pos * 32 + ((h ^ ((pos >> 2) & 1)) * 16));
-                    if (!__all_sync(0xffffffffu, tc_wait(bar(LT + slot), use & 1, wait_limit))) {
+        for (int64_t t = t0; t < t1 && ok;) {
+            const Run R = run_at(t);
+            for (int k = 0; k < R.len && ok; ++k, ++tt) {
+                for (int p = (k == 0 ? 0 : k + 2); p <= k + 2; ++p) {
+                    const uint32_t qq = q + p;
+                    if (!__all_sync(0xffffffffu, tc_wait(bar(LT + (int)(qq % C::NSLOT)), (qq / C::NSLOT) & 1,
+                                                         wait_limit))) {
                         if (lane == 0) fail();
                         ok = false;
                         break;
                     }
-                    if (lane < 16)
-                        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(val.x), "r"(val.y),
-                                     "r"(val.z), "r"(val.w)
-                                     : "memory");
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    __syncwarp();
-                    if (lane == 0) tp_arrive(bar(FU + slot));
                 }
-        }
-    } else if (warp == 2) {
-        // ---- MMA issuer: the whole warp runs the loop (warp-uniform operands), one lane issues ----
-        uint32_t q = 0;  // sequence number of the first plane of the current (column, slice)
-        int64_t u = 0;   // column ordinal of this CTA
-        bool ok = true;
-        for (int64_t c = blockIdx.x; c < ncols && ok; c += gridDim.x, ++u) {
-            const Col K = col_of(c);
-            for (int j = 0; j < C::SL && ok; ++j) {
-                for (int k = 0; k < C::ZC && ok; ++k) {
-                    const int acc = (int)(u & 1) * C::ZC + k;
-                    const uint32_t au = (uint32_t)(u >> 1);
-                    if (k >= K.len) {
-                        // a short last chunk: keep every accumulator's barrier phases in step
-                        if (j == 0 && !__all_sync(0xffffffffu, tc_wait(bar(AE + acc), (au & 1) ^ 1, wait_limit))) {
-                            if (lane == 0) fail();
-                            ok = false;
-                            break;
-                        }
-                        if (j == C::SL - 1) tc_commit_elect(bar(AF + acc));
-                        continue;
-                    }
-                    // planes k, k + 1, k + 2 of this slice must be in their slots
-                    for (int p = (k == 0 ? 0 : k + 2); p <= k + 2; ++p) {
-                        const uint32_t qq = q + p;
-                        if (!__all_sync(0xffffffffu, tc_wait(bar(FU + (int)(qq % C::NSLOT)), (qq / C::NSLOT) & 1,
-                                                             wait_limit))) {
-                            if (lane == 0) fail();
-                            ok = false;
-                            break;
-                        }
-                    }
-                    if (!ok) break;
-                    if (j == 0 && !__all_sync(0xffffffffu, tc_wait(bar(AE + acc), (au & 1) ^ 1, wait_limit))) {
-                        if (lane == 0) fail();
-                        ok = false;
-                        break;
-                    }
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t d_tmem = tmem + (uint32_t)(acc * 32);
-                    // descriptors of the three planes' slots and of the slice's weights; a tap adds a
-                    // compile-time offset to the start-address field (addresses stay below 2^18 bytes,
-                    // so the 14-bit field never carries)
-                    const uint64_t a_pl[3] = {umma_desc_sw32(a_s + ((q + k) % C::NSLOT) * C::SLOT),
-                                              umma_desc_sw32(a_s + ((q + k + 1) % C::NSLOT) * C::SLOT),
-                                              umma_desc_sw32(a_s + ((q + k + 2) % C::NSLOT) * C::SLOT)};
-                    const uint64_t b0 = umma_desc(b_s + (uint32_t)(2 * j * COUT * 16), COUT * 16, 128);
-                    const uint32_t first = j == 0 ? 0u : 1u;
-                    static_for<27>([&](auto TAP) {
-                        constexpr int dz = TAP / 9, dy = (TAP / 3) % 3, dxi = TAP % 3;  // each + 1
-                        constexpr uint64_t aoff = (uint64_t)((dxi * C::COPYB + dy * kW * 32) >> 4);
-                        constexpr uint64_t boff = (uint64_t)((TAP * C::WTAP) >> 4);
-                        tc_mma_elect(d_tmem, a_pl[dz] + aoff, b0 + boff, C::IDESC, TAP == 0 ? first : 1u);
+                if (!ok) break;
+                const int acc = (int)(tt % C::NACC);
+                const uint32_t au = tt / C::NACC;
+                if (!__all_sync(0xffffffffu, tc_wait(bar(AE + acc), (au & 1) ^ 1, wait_limit))) {
+                    if (lane == 0) fail();
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d_tmem = tmem + (uint32_t)(acc * C::ACOLS);
+                const uint64_t a_pl[3] = {umma_desc_sw32(a_s + ((q + k) % C::NSLOT) * C::PLANE),
+                                          umma_desc_sw32(a_s + ((q + k + 1) % C::NSLOT) * C::PLANE),
+                                          umma_desc_sw32(a_s + ((q + k + 2) % C::NSLOT) * C::PLANE)};
+                const uint64_t b0 = umma_desc(b_s, C::N * 16, 128);
+                static_for<C::SL>([&](auto J) {
+                    static_for<9>([&](auto G) {
+                        constexpr int dz = G / 3, dy = G % 3;  // each + 1
+                        constexpr uint64_t aoff = (uint64_t)((J * C::SLICEB + dy * kW * 32) >> 4);
+                        constexpr uint64_t boff = (uint64_t)(((G * C::K8 + 2 * J) * C::N * 16) >> 4);
+                        tc_mma_elect(d_tmem, a_pl[dz] + aoff, b0 + boff, C::IDESC, (J == 0 && G == 0) ? 0u : 1u);
                     });
-                    // plane k is not used by later tiles of this slice; the last tile frees all three
-                    tc_commit_elect(bar(EM + (int)((q + k) % C::NSLOT)));
-                    if (k == K.len - 1) {
-                        tc_commit_elect(bar(EM + (int)((q + k + 1) % C::NSLOT)));
-                        tc_commit_elect(bar(EM + (int)((q + k + 2) % C::NSLOT)));
-                    }
-                    if (j == C::SL - 1) tc_commit_elect(bar(AF + acc));
+                });
+                // plane k is not used by later tiles of the run; the last tile frees all three
+                tc_commit_elect(bar(EM + (int)((q + k) % C::NSLOT)));
+                if (k == R.len - 1) {
+                    tc_commit_elect(bar(EM + (int)((q + k + 1) % C::NSLOT)));
+                    tc_commit_elect(bar(EM + (int)((q + k + 2) % C::NSLOT)));
                 }
-                q += K.len + 2;
+                tc_commit_elect(bar(AF + acc));
             }
+            q += R.len + 2;
+            t += R.len;
         }
         // every MMA this warp issued has completed before tensor memory can be freed
         tc_commit_elect(bar(DR));
         if (!__all_sync(0xffffffffu, tc_wait(bar(DR), 0, wait_limit)) && lane == 0) fail();
     } else if (warp >= 4) {
-        // ---- epilogue: warp reads lanes 32 (warp % 4) .. + 31 and columns half * cout / 2 .. + cout / 2 ----
-        const int quarter = warp & 3, half = (warp - 4) >> 2;
-        constexpr int EC = C::EPI_COLS;
+        // ---- epilogue: group grp takes the tiles tt = grp, grp + 2, ...; a warp reads lanes
+        // 32 (warp % 4) .. + 31 and output channels half * EC .. + EC ----
+        const int grp = (warp - 4) >> 3, quarter = warp & 3, half = ((warp - 4) >> 2) & 1;
         const int c_lo = half * EC;
         const int m = 32 * quarter + lane;
         const int yl = m >> 6, xx = m & 63;
-        float bv[EC];
-#pragma unroll
-        for (int e = 0; e < EC; ++e) bv[e] = bias ? bias[c_lo + e] : 0.f;
-        int64_t u = 0;
-        bool ok = true;
-        for (int64_t c = blockIdx.x; c < ncols && ok; c += gridDim.x, ++u) {
-            const Col K = col_of(c);
-            for (int k = 0; k < C::ZC; ++k) {
-                const int acc = (int)(u & 1) * C::ZC + k;
-                const uint32_t au = (uint32_t)(u >> 1);
-                if (!__all_sync(0xffffffffu, tc_wait(bar(AF + acc), au & 1, wait_limit))) {
-                    if (lane == 0) fail();
-                    ok = false;
-                    break;
-                }
-                if (k >= K.len) {  // ghost tile of a short chunk
-                    __syncwarp();
-                    if (lane == 0) tp_arrive(bar(AE + acc));
-                    continue;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                float zc[EC];
-                const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(acc * 32 + c_lo);
-                if constexpr (EC == 16) {
-                    tc_ld16(taddr, zc);
-                } else {
-                    tc_ld8(taddr, zc);
-                }
-                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) tp_arrive(bar(AE + acc));
-
-                const int64_t v = (((int64_t)K.b * s.nz + (K.z0 + k)) * s.ny + (K.y0 + yl)) * kW + xx;
-                float o[EC];
-#pragma unroll
-                for (int e = 0; e < EC; ++e) {
-                    const float zj = zc[e] + bv[e];
-                    zc[e] = zj;
-                    o[e] = epi.act == SG_ACT_GELU ? gelu(zj) : zj;
-                }
-                if (epi.z_out) {
-                    float4* zo = reinterpret_cast<float4*>(epi.z_out + v * COUT + c_lo);
-#pragma unroll
-                    for (int e = 0; e < EC / 4; ++e)
-                        zo[e] = make_float4(zc[4 * e], zc[4 * e + 1], zc[4 * e + 2], zc[4 * e + 3]);
-                }
-                if (epi.res_in && CIN == COUT) {
-                    const uint4* rp = reinterpret_cast<const uint4*>(x + v * CIN + c_lo);
-#pragma unroll
-                    for (int h = 0; h < EC / 8; ++h) {
-                        const uint4 raw = rp[h];
-                        const __nv_bfloat162* pr = reinterpret_cast<const __nv_bfloat162*>(&raw);
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            o[8 * h + 2 * e] += __bfloat162float(pr[e].x);
-                            o[8 * h + 2 * e + 1] += __bfloat162float(pr[e].y);
-                        }
-                    }
-                }
-                if (epi.add) {
-                    if (epi.add_f32) {
-                        const float4* ad =
-                            reinterpret_cast<const float4*>(static_cast<const float*>(epi.add) + v * COUT + c_lo);
-#pragma unroll
-                        for (int e = 0; e < EC / 4; ++e) {
-                            const float4 r = ad[e];
-                            o[4 * e] += r.x;
-                            o[4 * e + 1] += r.y;
-                            o[4 * e + 2] += r.z;
-                            o[4 * e + 3] += r.w;
-                        }
-                    } else {
-                        const uint4* ad =
-                            reinterpret_cast<const uint4*>(static_cast<const bf16*>(epi.add) + v * COUT + c_lo);
-#pragma unroll
-                        for (int h = 0; h < EC / 8; ++h) {
-                            const uint4 raw = ad[h];
-                            const __nv_bfloat162* pr = reinterpret_cast<const __nv_bfloat162*>(&raw);
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                o[8 * h + 2 * e] += __bfloat162float(pr[e].x);
-                                o[8 * h + 2 * e + 1] += __bfloat162float(pr[e].y);
-                            }
-                        }
-                    }
-                }
-                if (epi.y_f32) {
-                    float4* yo = reinterpret_cast<float4*>(static_cast<float*>(y) + v * COUT + c_lo);
-#pragma unroll
-                    for (int e = 0; e < EC / 4; ++e) yo[e] = make_float4(o[4 * e], o[4 * e + 1], o[4 * e + 2], o[4 * e + 3]);
-                } else {
-                    uint4 pk[EC / 8];
-                    __nv_bfloat162* pp = reinterpret_cast<__nv_bfloat162*>(pk);
-#pragma unroll
-                    for (int e = 0; e < EC / 2; ++e) pp[e] = __floats2bfloat162_rn(o[2 * e], o[2 * e + 1]);
-                    uint4* yo = reinterpret_cast<uint4*>(static_cast<bf16*>(y) + v * COUT + c_lo);
-#pragma unroll
-                    for (int h = 0; h < EC / 8; ++h) yo[h] = pk[h];
+        const int pair = half * 2 + yl, pw = quarter & 1;  // the two quarters of a row form a pair
+        // the residual input (or, without one, the added values) of a tile is loaded one tile of
+        // this group ahead: EC bf16 values in EC / 2 words, or EC FP32 values in EC words
+        const bool res = epi.res_in && CIN == COUT;
+        const bool pre_add = !res && epi.add;
+        const bool bias4 = bias && ((uintptr_t)bias & 15) == 0;
+        constexpr int XW = WIDE ? EC : EC / 2;  // 32-bit words loaded ahead
+        uint32_t nxt[XW];
+        auto voxel_of = [&](const Run& R, int k) {
+            return (((int64_t)R.b * s.nz + (R.z0 + k)) * s.ny + (R.y0 + yl)) * kW + xx;
+        };
+        // EC bf16 values (EC / 2 words) or EC FP32 values (EC words) of voxel v: the residual input
+        // or the added tensor
+        auto extra_ptr = [&](int64_t v, bool is_res, bool f32) {
+            return is_res ? reinterpret_cast<const uint4*>(x + v * CIN + c_lo)
+                          : (f32 ? reinterpret_cast<const uint4*>(static_cast<const float*>(epi.add) + v * COUT + c_lo)
+                                 : reinterpret_cast<const uint4*>(static_cast<const bf16*>(epi.add) + v * COUT + c_lo));
+        };
+        // the tiles of this group in order
+        int64_t t = t0;
+        Run R = run_at(t);
+        int k = 0;
+        auto advance = [&](int steps) {  // move (t, R, k) forward by `steps` tiles
+            for (int i = 0; i < steps && t < t1; ++i) {
+                ++t;
+                if (++k == R.len && t < t1) {
+                    R = run_at(t);
+                    k = 0;
                 }
             }
+        };
+        advance(grp);
+        if (t < t1 && (res || pre_add)) ld_words(extra_ptr(voxel_of(R, k), res, WIDE), nxt);
+        uint32_t tt = (uint32_t)grp, use = 0;
+        bool ok = true;
+        while (t < t1 && ok) {
+            const int64_t v = voxel_of(R, k);
+            uint32_t cur[XW];
+#pragma unroll
+            for (int i = 0; i < XW; ++i) cur[i] = nxt[i];
+            advance(C::EPI_GROUPS);
+            if (t < t1 && (res || pre_add)) ld_words(extra_ptr(voxel_of(R, k), res, WIDE), nxt);
+
+            const int acc = (int)(tt % C::NACC);
+            const uint32_t au = tt / C::NACC;
+            if (!__all_sync(0xffffffffu, tc_wait(bar(AF + acc), au & 1, wait_limit))) {
+                if (lane == 0) fail();
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // z[x] = D_-1[x - 1] + D_0[x] + D_+1[x + 1]; lane 0's left and lane 31's right term
+            // come from the partner warp, which holds the other half of the row
+            const int par = (int)(use & 1);
+            const int xb = XF + 4 * grp + pair;
+            const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(acc * C::ACOLS + c_lo);
+            float zc[EC];
+            {
+                float dm[EC], dp[EC];
+                tc_ld3(taddr, taddr + COUT, taddr + 2 * COUT, dm, zc, dp);  // D_-1, D_0, D_+1
+                if (lane == 31) {
+#pragma unroll
+                    for (int e = 0; e < EC; ++e) xch[grp][pair][pw][par][0][e] = dm[e];
+                }
+                if (lane == 0) {
+#pragma unroll
+                    for (int e = 0; e < EC; ++e) xch[grp][pair][pw][par][1][e] = dp[e];
+                }
+#pragma unroll
+                for (int e = 0; e < EC; ++e) {
+                    const float l = __shfl_up_sync(0xffffffffu, dm[e], 1);
+                    const float r = __shfl_down_sync(0xffffffffu, dp[e], 1);
+                    zc[e] += (lane == 0 ? 0.f : l) + (lane == 31 ? 0.f : r);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) tp_arrive(bar(AE + acc));
+            if (lane == 0 || lane == 31) tp_arrive(bar(xb));
+            if (!__all_sync(0xffffffffu, tc_wait(bar(xb), use & 1, wait_limit))) {
+                if (lane == 0) fail();
+                ok = false;
+                break;
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int e = 0; e < EC; ++e) zc[e] += xch[grp][pair][pw ^ 1][par][0][e];
+            }
+            if (lane == 31) {
+#pragma unroll
+                for (int e = 0; e < EC; ++e) zc[e] += xch[grp][pair][pw ^ 1][par][1][e];
+            }
+            if (bias4) {
+#pragma unroll
+                for (int e = 0; e < EC / 4; ++e) {
+                    const float4 b4 = __ldg(reinterpret_cast<const float4*>(bias + c_lo) + e);
+                    zc[4 * e] += b4.x, zc[4 * e + 1] += b4.y, zc[4 * e + 2] += b4.z, zc[4 * e + 3] += b4.w;
+                }
+            } else if (bias) {
+#pragma unroll
+                for (int e = 0; e < EC; ++e) zc[e] += __ldg(bias + c_lo + e);
+            }
+            if (epi.z_out) {
+                float4* zo = reinterpret_cast<float4*>(epi.z_out + v * COUT + c_lo);
+#pragma unroll
+                for (int e = 0; e < EC / 4; ++e) zo[e] = make_float4(zc[4 * e], zc[4 * e + 1], zc[4 * e + 2], zc[4 * e + 3]);
+            }
+            if (epi.act == SG_ACT_GELU) {
+#pragma unroll
+                for (int e = 0; e < EC; ++e) zc[e] = gelu(zc[e]);
+            }
+            if (res || pre_add) add_words(zc, cur);
+            if (res && epi.add) {  // both a residual and an added tensor: the added one read here
+                if (epi.add_f32) {
+                    uint32_t ex[EC];
+                    ld_words(extra_ptr(v, false, true), ex);
+                    add_words(zc, ex);
+                } else {
+                    uint32_t ex[EC / 2];
+                    ld_words(extra_ptr(v, false, false), ex);
+                    add_words(zc, ex);
+                }
+            }
+            if (epi.y_f32) {
+                float4* yo = reinterpret_cast<float4*>(static_cast<float*>(y) + v * COUT + c_lo);
+#pragma unroll
+                for (int e = 0; e < EC / 4; ++e) yo[e] = make_float4(zc[4 * e], zc[4 * e + 1], zc[4 * e + 2], zc[4 * e + 3]);
+            } else {
+                uint4 pk[EC / 8];
+                __nv_bfloat162* pp = reinterpret_cast<__nv_bfloat162*>(pk);
+#pragma unroll
+                for (int e = 0; e < EC / 2; ++e) pp[e] = __floats2bfloat162_rn(zc[2 * e], zc[2 * e + 1]);
+                uint4* yo = reinterpret_cast<uint4*>(static_cast<bf16*>(y) + v * COUT + c_lo);
+#pragma unroll
+                for (int h = 0; h < EC / 8; ++h) yo[h] = pk[h];
+            }
+            tt += C::EPI_GROUPS;
+            ++use;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1292,19 +1334,21 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 template <int CIN, int COUT>
-static int launch_fwd_tc(sg_shape s, const void* x, const void* w, const float* bias, Epi epi, void* y,
-                         cudaStream_t st) {
-    using C = TczCfg<CIN, COUT>;
+static int launch_fwd_tcx(sg_shape s, const void* x, const void* w, const float* bias, Epi epi, void* y,
+                          cudaStream_t st) {
+    using C = TcxCfg<CIN, COUT>;
     static int configured = -1, grid_max = 0;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return -3;
     if (configured != dev) {
-        if (cudaFuncSetAttribute(k_conv_fwd_tcz<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) !=
-            cudaSuccess)
+        if (cudaFuncSetAttribute(k_conv_fwd_tcx<CIN, COUT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 C::SMEM) != cudaSuccess ||
+            cudaFuncSetAttribute(k_conv_fwd_tcx<CIN, COUT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 C::SMEM) != cudaSuccess)
             return -3;
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -3;
-        grid_max = sms;  // one CTA per SM (shared memory, tensor memory)
+        grid_max = sms;  // one CTA per SM (shared memory, all of tensor memory)
         configured = dev;
     }
     auto encode = tensor_map_encoder();
@@ -1325,18 +1369,20 @@ static int launch_fwd_tc(sg_shape s, const void* x, const void* w, const float* 
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return -3;
-    const int64_t cols = (int64_t)s.batch * ((s.nz + C::ZC - 1) / C::ZC) * (s.ny / 2);
-    const int grid = (int)(cols < grid_max ? cols : grid_max);
+    const int64_t tiles = (int64_t)s.batch * (s.ny / 2) * s.nz;
+    const int grid = (int)(tiles < grid_max ? tiles : grid_max);
     const long long wait_limit = 2000000000LL;  // ~1 s of SM clock per wait
-    k_conv_fwd_tcz<CIN, COUT><<<grid, C::THREADS, C::SMEM, st>>>(rows, row, s, static_cast<const bf16*>(x),
-                                                                static_cast<const bf16*>(w), bias, epi, y, wait_limit);
+    const bool wide = !(epi.res_in && CIN == COUT) && epi.add && epi.add_f32;
+    auto kern = wide ? k_conv_fwd_tcx<CIN, COUT, true> : k_conv_fwd_tcx<CIN, COUT, false>;
+    kern<<<grid, C::THREADS, C::SMEM, st>>>(rows, row, s, static_cast<const bf16*>(x), static_cast<const bf16*>(w),
+                                            bias, epi, y, wait_limit);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
 template <int CIN, int COUT>
 static int launch_fwd(sg_shape s, const void* x, const void* w, const float* bias, Epi epi, void* y,
                       cudaStream_t st) {
-    if (g_fwd_impl == SG_CONV_TCGEN05) return launch_fwd_tc<CIN, COUT>(s, x, w, bias, epi, y, st);
+    if (g_fwd_impl == SG_CONV_TCGEN05) return launch_fwd_tcx<CIN, COUT>(s, x, w, bias, epi, y, st);
     constexpr int smem = HaloCfg<CIN>::BYTES + WCfg<CIN, COUT>::BYTES;
     static int configured = -1;
     int dev = 0;

@@ -29,9 +29,9 @@ def impl(request):
     sg.set_conv_impl(prev)
 
 
-# tcgen05 kernel: (2, 3, 4, 64) a short z chunk (3 of 4 tiles) and rows wrapping in y;
-# (1, 4, 8, 64) interior and wrapping row pairs; (4, 6, 64, 64) 256 columns of tiles for at most
-# 152 CTAs (several columns per CTA, both accumulator sets) with chunks of 4 and 2 planes
+# tcgen05 kernel: (2, 3, 4, 64) 12 tiles, one per CTA, with rows wrapping in y; (1, 4, 8, 64)
+# interior and wrapping row pairs; (4, 6, 64, 64) 768 tiles over at most 152 CTAs: runs of z that
+# end inside a column and continue in the next, both epilogue groups, the accumulator ring reused
 @pytest.mark.parametrize("cin,cout", [(16, 32), (32, 32), (32, 16), (16, 16)])
 @pytest.mark.parametrize("shape", [(1, 4, 8, 64), (2, 3, 4, 64), (4, 6, 64, 64)])
 def test_conv_forward_matches_oracle(cin, cout, shape, impl):
