@@ -214,13 +214,37 @@ lb_status lb_set_state(lb_ctx *ctx, const void *raw, int on_device);
 #define LB_KERNEL_DIRECT2X 5
 #define LB_KERNEL_DIRECT2XL 6
 
-/* Kernel lb_step will run for this context (LB_KERNEL_DIRECT1 .. LB_KERNEL_DIRECT2XL). */
+/* Kernel lb_step will run for this context (LB_KERNEL_DIRECT1 .. LB_KERNEL_DIRECT2XL;
+ * with stochastic rounding on, the one that carries the stochastic store). */
 int lb_step_variant(const lb_ctx *ctx);
 /* Request a step kernel (LB_KERNEL_*). */
 lb_status lb_set_step_kernel(lb_ctx *ctx, int kernel);
 /* Autotuner: time every step kernel that applies to this grid for reps steps
  * (the state is not advanced), keep the fastest, report it and its ms per step. */
 lb_status lb_tune(lb_ctx *ctx, int reps, int *kernel, double *ms_per_step);
+
+/* Stochastic rounding of the BF16 store (LB_F32_S16B contexts; the rounding
+ * of 16-bit storage is a choice the paper leaves open).  Round to nearest
+ * rounds a slowly varying field the same way at every step, so its error adds
+ * up coherently; an unbiased random rounding makes it a random walk instead.
+ * With enable != 0, step t (t = 0 for the first lb_step after this call)
+ * stores population i of node q (q = s nx ny nz + (z ny + y) nx + x, taken
+ * mod 2^32) as the upper half of bits(h_i) + r, h_i the FP32 value and r 16
+ * random bits, so the magnitude is rounded up with probability (lower half of
+ * bits(h_i)) / 2^16.  r is the low (q even) or high (q odd) half of
+ *   w_i = s_(i+1) ^ (s_(i+1) >> 16),  s_(i+1) = 1664525 s_i + 1013904223,
+ *   s_0 = H(k_t ^ (q >> 1)),  k_t = H(H(lo32(seed) ^ H(hi32(seed))) + t),
+ * all mod 2^32, i in the library's population order, H the 32-bit PCG hash
+ * of Jarzynski and Olano (JCGT 9(3), 2020): with v = x * 747796405 +
+ * 2891336453 and u = ((v >> ((v >> 28) + 4)) ^ v) * 277803737, H(x) = (u >> 22)
+ * ^ u.  The step then always runs the x-pair kernel (nx even) or one node per
+ * thread, whatever lb_set_step_kernel or lb_tune chose.  Requires BF16
+ * storage and the series equilibrium with the momentum projection (no
+ * LB_FLAG_PAPER_LITERAL or LB_FLAG_ENTROPIC: LB_ERR_ARG), and neither walls
+ * nor the nonideal mode (LB_ERR_STATE; those refuse to start while it is on).
+ * enable = 0 restores round to nearest.  A batch (lb_batch_step) refuses
+ * members with it on (LB_ERR_STATE). */
+lb_status lb_set_stochastic_rounding(lb_ctx *ctx, int enable, uint64_t seed);
 
 /* Kinetic walls normal to z (Sec. "Viscous heat dissipation", which applies
  * the kinetic boundary condition of Ansumali and Karlin 2002 at the walls and
@@ -294,9 +318,10 @@ lb_status lb_nonideal_constants(int eos, double theta_star, double rho_c, double
  * synchronising call; the Carnahan-Starling form is checked only for
  * rho > 0 and finite moments.  An eos outside LB_EOS_* gives LB_ERR_ARG.
  * Needs the projected series equilibrium (no LB_FLAG_PAPER_LITERAL or
- * LB_FLAG_ENTROPIC; LB_ERR_ARG) and no walls (LB_ERR_STATE).  Each step runs
- * four one-node-per-thread kernels; the work buffer is 88 bytes per node.
- * eos = 0 restores the energy-conserving update. */
+ * LB_FLAG_ENTROPIC; LB_ERR_ARG), and neither walls nor stochastic rounding
+ * (LB_ERR_STATE).  Each step runs four one-node-per-thread kernels; the work
+ * buffer is 88 bytes per node.  A batch (lb_batch_step) refuses members with
+ * it on (LB_ERR_STATE).  eos = 0 restores the energy-conserving update. */
 lb_status lb_set_nonideal(lb_ctx *ctx, int eos, double a, double b, double kappa, double eta);
 
 /* Number of time steps taken since the last lb_set_fields / lb_set_populations / lb_set_state. */

@@ -3,8 +3,9 @@
 Runs the thermoacoustic case (Gaussian density pulse 1e-2, sigma 8 cells, plus
 a 16^3-Fourier-box temperature perturbation of max 1e-3, nu = 0.01) on an n^3
 grid for `steps` steps in FP64 (the GPU FP64 mode, itself matched to the CPU
-oracle to 1e-12 on small grids), FP32, FP32 + FP16 storage and FP32 + BF16
-storage, and reports for each the relative L2 error of the density
+oracle to 1e-12 on small grids), FP32, FP32 + FP16 storage, FP32 + BF16
+storage rounded to nearest and FP32 + BF16 storage rounded stochastically
+("bf16sr", lb_set_stochastic_rounding), and reports for each the relative L2 error of the density
 fluctuation rho - 1 and of the temperature fluctuation theta - theta0 against
 FP64, the maximum absolute density error, and the drift of the global mass
 and energy sums.
@@ -25,6 +26,7 @@ import time
 import torch
 
 NU = 0.01
+SR_SEED = 20191909
 
 
 def run(n, steps, prec, fields, kernel=None):
@@ -32,9 +34,11 @@ def run(n, steps, prec, fields, kernel=None):
     `kernel` fixes the step kernel (an LB_KERNEL_* id); None lets the autotuner pick."""
     from . import lb
     th0 = lb.lb_theta0()
-    ctx = lb.lb_init((n, n, n), NU / th0, prec)
+    ctx = lb.lb_init((n, n, n), NU / th0, "bf16" if prec == "bf16sr" else prec)
     try:
         lb.lb_set_fields(ctx, fields["rho"], fields["u"], fields["theta"])
+        if prec == "bf16sr":
+            lb.lb_set_stochastic_rounding(ctx, SR_SEED)
         c0 = lb.lb_conserved(ctx)
         if kernel is not None:
             lb.lb_set_step_kernel(ctx, kernel)
@@ -88,7 +92,7 @@ def main(argv=None):
     torch.cuda.set_device(0)
     fields = wl.thermoacoustic_pulse(a.n, lb.lb_theta0(), device="cuda")
     out = {"n": a.n, "steps": a.steps, "workload": "thermoacoustic pulse (1e-2, sigma 8) + theta Fourier box (1e-3)"}
-    out.update(compare(a.n, a.steps, ("f32", "f16", "bf16"), fields))
+    out.update(compare(a.n, a.steps, ("f32", "f16", "bf16", "bf16sr"), fields))
     print(json.dumps(out))
 
 

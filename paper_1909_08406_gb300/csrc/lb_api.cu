@@ -294,6 +294,8 @@ lb_status lb_sync(lb_ctx* c) {
 int lb_step_variant(const lb_ctx* c) {
     if (!c) return -1;
     if (c->eq == 2) return kKernelDirect1;  // the exact entropic equilibrium runs in k_step only
+    if (c->sr)  // the stochastic store: the x-pair kernel where it applies, else one node per thread
+        return resolve_kernel(c->prec, c->d, kKernelDirect2XL) == kKernelDirect2XL ? kKernelDirect2XL : kKernelDirect1;
     return resolve_kernel(c->prec, c->d, c->variant);
 }
 
@@ -390,6 +392,9 @@ lb_status lb_step(lb_ctx* c, int64_t n) {
         if (c->nonideal)
             CK(c, launch_nonideal_step(c->prec, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc, c->twobeta,
                                        c->nonideal, c->ni_eos, c->d_ni, c->d_err, c->stream));
+        else if (c->sr)
+            CK(c, launch_step_sr(c->buf[c->cur], c->buf[1 - c->cur], c->d, lc, c->twobeta, c->d_err, c->stream,
+                                 sr_step_key(c->sr_seed, c->sr_t++)));
         else if (c->walls)
             CK(c, launch_wall_step(c->prec, c->eq, c->variant, c->buf[c->cur], c->buf[1 - c->cur], c->d, lc,
                                    c->twobeta, c->d_wall, c->d_err, c->stream));
@@ -580,6 +585,23 @@ static bool wall_checks(lb_ctx* c) {
     return true;
 }
 
+lb_status lb_set_stochastic_rounding(lb_ctx* c, int enable, uint64_t seed) {
+    if (!c) return LB_ERR_ARG;
+    if (!enable) {
+        c->sr = 0;
+        return LB_OK;
+    }
+    if (c->prec != kBF16) return fail(c, LB_ERR_ARG, "lb_set_stochastic_rounding: needs BF16 storage");
+    if (c->eq != 1)
+        return fail(c, LB_ERR_ARG, "lb_set_stochastic_rounding: needs the series equilibrium with the projection");
+    if (c->walls || c->nonideal)
+        return fail(c, LB_ERR_STATE, "lb_set_stochastic_rounding: not combined with walls or the nonideal mode");
+    c->sr = 1;
+    c->sr_seed = seed;
+    c->sr_t = 0;
+    return LB_OK;
+}
+
 lb_status lb_set_walls(lb_ctx* c, int enable, const double bottom[4], const double top[4]) {
     if (!c) return LB_ERR_ARG;
     if (!enable) {
@@ -587,6 +609,7 @@ lb_status lb_set_walls(lb_ctx* c, int enable, const double bottom[4], const doub
         return LB_OK;
     }
     if (!bottom || !top) return fail(c, LB_ERR_ARG, "lb_set_walls: null wall");
+    if (c->sr) return fail(c, LB_ERR_STATE, "lb_set_walls: not combined with stochastic rounding");
     if (c->nonideal) return fail(c, LB_ERR_STATE, "lb_set_walls: not combined with the nonideal mode");
     if (!wall_checks(c)) return LB_ERR_ARG;
     if (bottom[2] != 0.0 || top[2] != 0.0) return fail(c, LB_ERR_ARG, "lb_set_walls: a wall cannot move along z");
@@ -674,6 +697,7 @@ lb_status lb_set_nonideal(lb_ctx* c, int enable, double a, double b, double kapp
     if (c->eq != 1)
         return fail(c, LB_ERR_ARG, "lb_set_nonideal: the nonideal mode uses the projected series equilibrium");
     if (c->walls) return fail(c, LB_ERR_STATE, "lb_set_nonideal: not combined with walls");
+    if (c->sr) return fail(c, LB_ERR_STATE, "lb_set_nonideal: not combined with stochastic rounding");
     CK(c, cudaSetDevice(c->device));
     if (!c->d_ni) {
         cudaError_t e = cudaMalloc(&c->d_ni, sizeof(double) * nonideal_doubles(c->d));

@@ -588,7 +588,9 @@ lb_status lb_batch_step(lb_batch* b, int64_t nsteps, int mode) {
     if (!b || nsteps < 0) return bfail(b, LB_ERR_ARG, "lb_batch_step: bad argument");
     if (nsteps == 0) return LB_OK;
     for (auto* c : b->ctx)
-        if (c->walls) return bfail(b, LB_ERR_STATE, "lb_batch_step: a simulation of the batch has walls");
+        if (c->walls || c->nonideal || c->sr)
+            return bfail(b, LB_ERR_STATE,
+                         "lb_batch_step: a simulation of the batch has walls, the nonideal mode or stochastic rounding");
     BCK(b, cudaSetDevice(b->device));
     const int parity = b->ctx[0]->cur;
     if (mode == LB_BATCH_SEQUENTIAL) {

@@ -17,6 +17,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <type_traits>
 #include <utility>
@@ -562,6 +563,62 @@ __device__ __forceinline__ void equilibrium_relax(const NodeState<typename Codec
         entropic_relax<Codec>(st, K, tb, omb, [&](auto I) { return v[I]; }, sink, ok);
     else
         equilibrium_relax_g<Codec, EQ == 1>(st, K, tb, omb, [&](auto I) { return v[I]; }, sink);
+}
+
+// ---------------------------------------------------------------------------
+// Stochastic rounding of the BF16 store (lb_set_stochastic_rounding).  A BF16
+// number is the upper half of an FP32 bit pattern; adding 16 uniform random
+// bits r to the lower half and truncating rounds the magnitude up with
+// probability (lower half) / 2^16, so the stored value is unbiased:
+//   SR(v; r) = upper half of (bits(v) + r).
+// The bits come from a counter-based generator:
+//   step key    k_t = H(H(lo(seed) ^ H(hi(seed))) + t),  t = steps since enabling
+//   node pair   s_0 = H(k_t ^ (q >> 1)),  q = s nx ny nz + (z ny + y) nx + x
+//   population  s_(i+1) = 1664525 s_i + 1013904223 (mod 2^32), i = 0..40 in the
+//               library's population order,  w_i = s_(i+1) ^ (s_(i+1) >> 16)
+//   r = low 16 bits of w_i for even q, high 16 bits for odd q
+// where H is the 32-bit PCG hash of Jarzynski and Olano (Hash Functions for GPU
+// Rendering, JCGT 9(3), 2020) and the recurrence is the Numerical Recipes
+// linear congruential generator.  The two nodes of an x pair share one word.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr uint32_t pcg_hash(uint32_t x) {
+    const uint32_t state = x * 747796405u + 2891336453u;
+    const uint32_t word = ((state >> ((state >> 28u) + 4u)) ^ state) * 277803737u;
+    return (word >> 22u) ^ word;
+}
+constexpr uint32_t kSrLcgA = 1664525u, kSrLcgC = 1013904223u;
+// s_n = sr_lcg_a(n) s_0 + sr_lcg_c(n) after n steps of the recurrence
+__host__ __device__ constexpr uint32_t sr_lcg_a(int n) {
+    uint32_t a = 1u;
+    for (int k = 0; k < n; ++k) a *= kSrLcgA;
+    return a;
+}
+__host__ __device__ constexpr uint32_t sr_lcg_c(int n) {
+    uint32_t c = 0u;
+    for (int k = 0; k < n; ++k) c = c * kSrLcgA + kSrLcgC;
+    return c;
+}
+inline uint32_t sr_step_key(uint64_t seed, uint32_t t) {
+    return pcg_hash(pcg_hash((uint32_t)seed ^ pcg_hash((uint32_t)(seed >> 32))) + t);
+}
+// w_I of a node pair with first state s0
+template <int I>
+__device__ __forceinline__ uint32_t sr_word(uint32_t s0) {
+    constexpr uint32_t A = sr_lcg_a(I + 1), C = sr_lcg_c(I + 1);
+    const uint32_t s = A * s0 + C;
+    return s ^ (s >> 16);
+}
+__device__ __forceinline__ __nv_bfloat16 sr_bf16(float v, uint32_t r16) {
+    return __ushort_as_bfloat16((unsigned short)((__float_as_uint(v) + r16) >> 16));
+}
+// the pair (v.x, v.y) of nodes q (even) and q + 1 with one word w
+__device__ __forceinline__ __nv_bfloat162 sr_bf16x2(float2 v, uint32_t w) {
+    const uint32_t lo = __float_as_uint(v.x) + (w & 0xFFFFu);
+    const uint32_t hi = __float_as_uint(v.y) + (w >> 16);
+    const uint32_t packed = __byte_perm(lo, hi, 0x7632);
+    __nv_bfloat162 r;
+    memcpy(&r, &packed, 4);
+    return r;
 }
 
 // Geometry of one population buffer.

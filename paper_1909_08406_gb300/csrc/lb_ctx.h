@@ -34,6 +34,9 @@ struct lb_ctx {
     int nonideal = 0;          // isothermal nonideal fluid: 0 off, else its equation of state (lb_set_nonideal)
     double ni_eos[4] = {0, 0, 0, 0};  // a, b, kappa, eta
     double* d_ni = nullptr;    // its work buffer (lb_nonideal.cu)
+    int sr = 0;                // stochastic rounding of the BF16 store (lb_set_stochastic_rounding)
+    uint64_t sr_seed = 0;
+    uint32_t sr_t = 0;         // steps taken since it was enabled
     std::string msg;
 };
 

@@ -31,11 +31,12 @@ struct LoadCG {
 // the sub-lattice (shifts 0, +-1, +-2 cells); the bcc-1/2 links come from the
 // other sub-lattice: for A (s = 0) a component +1/2 reads cell r - 1 and -1/2
 // reads cell r; for B (s = 1) +1/2 reads cell r and -1/2 reads cell r + 1.
-template <class Codec, int EQ, class Ld = LoadNC>
+// SR: BF16 storage with the stochastic store of lb_common.cuh, step key sr_key.
+template <class Codec, int EQ, class Ld = LoadNC, bool SR = false>
 __device__ __forceinline__ void step_node(const typename Codec::raw_t* __restrict__ src,
                                           typename Codec::raw_t* __restrict__ dst, const Dims& d,
                                           const Consts<typename Codec::R>& K, typename Codec::R tb,
-                                          int* __restrict__ err, int s, int z, int y, int x) {
+                                          int* __restrict__ err, int s, int z, int y, int x, uint32_t sr_key = 0) {
     using R = typename Codec::R;
     using T = typename Codec::raw_t;
     const int64_t nxy = (int64_t)d.nx * d.ny;
@@ -76,9 +77,21 @@ __device__ __forceinline__ void step_node(const typename Codec::raw_t* __restric
     const NodeState<R> st = state_from_moments(m, K);
     bool ok = state_ok(st);
 
-    T* out = dst + (int64_t)s * kQ * d.plane + (int64_t)z * nxy + (int64_t)y * d.nx + x;
-    equilibrium_relax<Codec, EQ>(st, K, tb * R(Codec::kScale), R(1) - tb, v,
-                                 [&](auto I, R val) { out[(int64_t)I * d.plane] = Codec::to_raw(val); }, ok);
+    const int64_t qn = (int64_t)z * nxy + (int64_t)y * d.nx + x;
+    T* out = dst + (int64_t)s * kQ * d.plane + qn;
+    if constexpr (SR) {
+        const uint32_t q = (uint32_t)((int64_t)s * d.plane + qn);
+        const uint32_t s0 = pcg_hash(sr_key ^ (q >> 1));
+        equilibrium_relax<Codec, EQ>(st, K, tb * R(Codec::kScale), R(1) - tb, v,
+                                     [&](auto I, R val) {
+                                         const uint32_t w = sr_word<decltype(I)::value>(s0);
+                                         out[(int64_t)I * d.plane] = sr_bf16(val, (q & 1u) ? (w >> 16) : (w & 0xFFFFu));
+                                     },
+                                     ok);
+    } else {
+        equilibrium_relax<Codec, EQ>(st, K, tb * R(Codec::kScale), R(1) - tb, v,
+                                     [&](auto I, R val) { out[(int64_t)I * d.plane] = Codec::to_raw(val); }, ok);
+    }
     if (!ok) atomicOr(err, 1);
 }
 
@@ -105,6 +118,22 @@ __device__ __forceinline__ void step_node2(const typename Codec::raw_t* __restri
                                            typename Codec::raw_t* __restrict__ dst, const Dims& d,
                                            const Consts<float>& K, float tb, int* __restrict__ err, int s, int z,
                                            int y, int x);
+
+// k_step with the stochastic BF16 store (series equilibrium with the momentum projection).
+template <class Codec>
+__global__ void __launch_bounds__(kStepThreads) k_step_sr(const typename Codec::raw_t* __restrict__ src,
+                                                          typename Codec::raw_t* __restrict__ dst, Dims d,
+                                                          Consts<typename Codec::R> K, typename Codec::R tb,
+                                                          int* __restrict__ err, uint32_t sr_key) {
+    const int x = blockIdx.y * blockDim.x + threadIdx.x;
+    if (x >= d.nx) return;
+    const int64_t row = blockIdx.x;
+    const int y = (int)(row % d.ny);
+    const int64_t zr = row / d.ny;
+    const int z = (int)(zr % d.nz);
+    const int s = (int)(zr / d.nz);
+    step_node<Codec, 1, LoadNC, true>(src, dst, d, K, tb, err, s, z, y, x, sr_key);
+}
 
 // Two-rows-per-thread direct-load step kernel (FP32 arithmetic, any storage
 // except FP64): each thread updates nodes (s, z, y, x) and (s, z, y + 1, x)
@@ -296,11 +325,13 @@ __device__ __forceinline__ void prefetch_row_l2(const typename Codec::raw_t* src
 //         (one per population, by threads 0..40; a block of only 32 threads,
 //         on a narrow grid, prefetches its first 32 populations) at the start
 //         of the current row, so that the next row's loads hit in L2.
-template <class Codec, bool PROJECT, int MINB, int MODE>
+// SR: BF16 storage with the stochastic store of lb_common.cuh, step key sr_key (one word per
+// population and x pair).
+template <class Codec, bool PROJECT, int MINB, int MODE, bool SR = false>
 __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Codec::raw_t* __restrict__ src,
                                                          typename Codec::raw_t* __restrict__ dst, Dims d,
                                                          Consts<float> K, float tb, int* __restrict__ err,
-                                                         int chunks, int rpb) {
+                                                         int chunks, int rpb, uint32_t sr_key) {
     using T = typename Codec::raw_t;
     using P = typename Codec::pair_t;
     using C2 = Codec2<Codec>;
@@ -359,8 +390,18 @@ __global__ void __launch_bounds__(kStepThreads, MINB) k_step2x(const typename Co
         if (!state_ok(st)) atomicOr(err, 1);
 
         P* outp = reinterpret_cast<P*>(dst + (size_t)s * kQ * d.plane + ((uint32_t)z * nxy + (uint32_t)y * nx + x0));
-        equilibrium_relax_g<C2, PROJECT>(st, K, F2(tb * (float)Codec::kScale), F2(1.f - tb), vget,
-                                         [&](auto I, F2 val) { outp[(size_t)I * (plane / 2)] = Codec::to_raw2(val.v); });
+        if constexpr (SR) {
+            const uint32_t q = (uint32_t)s * plane + (uint32_t)z * nxy + (uint32_t)y * nx + x0;
+            const uint32_t s0 = pcg_hash(sr_key ^ (q >> 1));
+            equilibrium_relax_g<C2, PROJECT>(st, K, F2(tb * (float)Codec::kScale), F2(1.f - tb), vget,
+                                             [&](auto I, F2 val) {
+                                                 outp[(size_t)I * (plane / 2)] =
+                                                     sr_bf16x2(val.v, sr_word<decltype(I)::value>(s0));
+                                             });
+        } else {
+            equilibrium_relax_g<C2, PROJECT>(st, K, F2(tb * (float)Codec::kScale), F2(1.f - tb), vget,
+                                             [&](auto I, F2 val) { outp[(size_t)I * (plane / 2)] = Codec::to_raw2(val.v); });
+        }
         s = sn;
         z = zn;
         y = yn;

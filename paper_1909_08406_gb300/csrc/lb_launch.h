@@ -46,6 +46,11 @@ size_t storage_bytes(int prec);
 cudaError_t launch_step(int prec, int eq, int variant, const void* src, void* dst, const Dims& d,
                         const LaunchConsts& c, double twobeta, int* err, cudaStream_t st);
 
+// One fused step with the stochastic BF16 store (BF16 storage, series equilibrium with the
+// momentum projection, periodic grid); sr_key is the step key k_t of lb_common.cuh.
+cudaError_t launch_step_sr(const void* src, void* dst, const Dims& d, const LaunchConsts& c, double twobeta, int* err,
+                           cudaStream_t st, uint32_t sr_key);
+
 // Equilibrium of float64 fields for nodes [q0, q0 + count).
 cudaError_t launch_init(int prec, int eq, void* dst, const Dims& d, const LaunchConsts& c, int64_t q0,
                         int64_t count, const double* rho, const double* u, int64_t ustride, const double* theta,

@@ -37,9 +37,9 @@ static cudaError_t run_direct2(const void* src, void* dst, const Dims& d, const 
     return cudaGetLastError();
 }
 
-template <class Codec, bool P, int MINB, int MODE>
+template <class Codec, bool P, int MINB, int MODE, bool SR = false>
 static cudaError_t run_direct2x(const void* src, void* dst, const Dims& d, const LaunchConsts& c, double twobeta,
-                                int* err, cudaStream_t st, int rpb) {
+                                int* err, cudaStream_t st, int rpb, uint32_t sr_key = 0) {
     using T = typename Codec::raw_t;
     if constexpr (sizeof(T) != 2) {
         return cudaErrorInvalidValue;
@@ -48,9 +48,9 @@ static cudaError_t run_direct2x(const void* src, void* dst, const Dims& d, const
         const int th = half >= 128 ? 128 : ((half + 31) / 32) * 32;
         const int chunks = (half + th - 1) / th;
         const int64_t blocks = ((d.rows + rpb - 1) / rpb) * chunks;
-        auto kern = k_step2x<Codec, P, MINB, MODE>;
+        auto kern = k_step2x<Codec, P, MINB, MODE, SR>;
         kern<<<(unsigned)blocks, th, 0, st>>>(static_cast<const T*>(src), static_cast<T*>(dst), d, c.kf,
-                                                 (float)twobeta, err, chunks, rpb);
+                                                 (float)twobeta, err, chunks, rpb, sr_key);
         return cudaGetLastError();
     }
 }
@@ -208,6 +208,19 @@ cudaError_t launch_step_f32(int prec, bool project, int kernel, const void* src,
                            : step_codec<CodecBF16, false>(prec, kernel, src, dst, d, c, twobeta, err, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// The fused step with the stochastic BF16 store (series equilibrium with the momentum projection):
+// the x-pair kernel where it applies, else one node per thread.
+cudaError_t launch_step_sr(const void* src, void* dst, const Dims& d, const LaunchConsts& c, double twobeta, int* err,
+                           cudaStream_t st, uint32_t sr_key) {
+    using T = CodecBF16::raw_t;
+    if (resolve_kernel(kBF16, d, kKernelDirect2XL) == kKernelDirect2XL)
+        return run_direct2x<CodecBF16, true, 3, 2, true>(src, dst, d, c, twobeta, err, st, 2, sr_key);
+    const int th = step_threads(d);
+    k_step_sr<CodecBF16><<<step_grid(d, th), th, 0, st>>>(static_cast<const T*>(src), static_cast<T*>(dst), d, c.kf,
+                                                         (float)twobeta, err, sr_key);
+    return cudaGetLastError();
 }
 
 }  // namespace gblb

@@ -87,6 +87,8 @@ def lib():
         L.lb_set_wall_columns.restype = ctypes.c_int
         L.lb_get_grid.argtypes = [vp, ctypes.POINTER(_Grid)]
         L.lb_get_grid.restype = ctypes.c_int
+        L.lb_set_stochastic_rounding.argtypes = [vp, ctypes.c_int, ctypes.c_uint64]
+        L.lb_set_stochastic_rounding.restype = ctypes.c_int
         L.lb_set_nonideal.argtypes = [vp, ctypes.c_int, dp, dp, dp, dp]
         L.lb_set_nonideal.restype = ctypes.c_int
         L.lb_nonideal_constants.argtypes = [ctypes.c_int, dp, dp, ctypes.POINTER(dp), ctypes.POINTER(dp)]
@@ -259,6 +261,15 @@ def lb_set_nonideal(ctx, a=None, b=None, kappa=0.0, eta=0.5, eos="vdw"):
         return
     kind = LB_EOS[eos] if isinstance(eos, str) else int(eos)
     _check(lib().lb_set_nonideal(ctx, kind, float(a), float(b), float(kappa), float(eta)), ctx)
+
+
+def lb_set_stochastic_rounding(ctx, seed=None):
+    """Stochastic rounding of the BF16 store with the given 64-bit seed (the step counter starts
+    again at 0); seed = None restores round to nearest."""
+    if seed is None:
+        _check(lib().lb_set_stochastic_rounding(ctx, 0, 0), ctx)
+    else:
+        _check(lib().lb_set_stochastic_rounding(ctx, 1, int(seed) & 0xFFFFFFFFFFFFFFFF), ctx)
 
 
 def lb_grid_of(ctx):
