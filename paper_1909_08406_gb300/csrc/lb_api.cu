@@ -698,6 +698,8 @@ lb_status lb_set_nonideal(lb_ctx* c, int enable, double a, double b, double kapp
         return fail(c, LB_ERR_ARG, "lb_set_nonideal: the nonideal mode uses the projected series equilibrium");
     if (c->walls) return fail(c, LB_ERR_STATE, "lb_set_nonideal: not combined with walls");
     if (c->sr) return fail(c, LB_ERR_STATE, "lb_set_nonideal: not combined with stochastic rounding");
+    if (2 * c->d.plane >= ((int64_t)1 << 32))
+        return fail(c, LB_ERR_ARG, "lb_set_nonideal: the grid must have fewer than 2^31 cells");
     CK(c, cudaSetDevice(c->device));
     if (!c->d_ni) {
         cudaError_t e = cudaMalloc(&c->d_ni, sizeof(double) * nonideal_doubles(c->d));

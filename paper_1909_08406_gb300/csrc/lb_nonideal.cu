@@ -16,6 +16,8 @@
 //                 Eq. (multiphaseEvolution), alpha = 2: u = j / rho + g / 2,
 //                 f^eq = f^eq(rho, u, theta_0), F_i = g.(c_i - u)/theta_0 f^eq_i,
 //                 f' = f + 2 beta (f^eq - f) + (1 - beta) F_i.
+// With 16-bit storage and nx even the two gathering passes run on x pairs (k_ni_density2x,
+// k_ni_step2x: the x-pair gather of k_step2x, packed FP32x2 arithmetic).
 // The stencil is the 15-velocity bcc set of Appendix A: rest, (+-1, 0, 0) and
 // permutations (on the node's own sub-lattice), (+-1/2, +-1/2, +-1/2) (on the
 // other); weights 14/36, 1/36, 2/36; theta_hat = 1/6.  The fields are in
@@ -53,31 +55,45 @@ __device__ __forceinline__ void stencil(int k, int& cx, int& cy, int& cz, F& w) 
     }
 }
 
-// Field index of the node at x + c for node (s, z, y, x), c doubled; periodic.
-__device__ __forceinline__ int64_t ni_neighbor(const Dims& d, int s, int z, int y, int x, int cx, int cy, int cz) {
-    const int t = (s + cx) & 1;
-    int xn = x + (s + cx - t) / 2, yn = y + (s + cy - t) / 2, zn = z + (s + cz - t) / 2;
-    xn = xn < 0 ? xn + d.nx : (xn >= d.nx ? xn - d.nx : xn);
-    yn = yn < 0 ? yn + d.ny : (yn >= d.ny ? yn - d.ny : yn);
-    zn = zn < 0 ? zn + d.nz : (zn >= d.nz ? zn - d.nz : zn);
-    return (((int64_t)t * d.nz + zn) * d.ny + yn) * d.nx + xn;
-}
-
 constexpr int kNiThreads = 128;
 
-// Node of this thread: blocks cover (row, x chunk) pairs, row = (s, z, y) with y fastest, so the
-// coordinates come from 32-bit divisions of the block index (2 ny nz < 2^31, checked at init).
+// Node of this thread: blocks cover (row, x chunk) pairs, rows running (z, s, y) with y fastest, so
+// that the two sub-lattices of a plane are visited together (the stencil passes read the other
+// sub-lattice's fields, which then come from L2).  The coordinates come from 32-bit divisions of
+// the block index (2 ny nz < 2^31, checked at init); q is the node's field index
+// ((s nz + z) ny + y) nx + x.
 __device__ __forceinline__ bool ni_node(const Dims& d, int chunks, int64_t& q, int& s, int& z, int& y, int& x) {
     const uint32_t b = blockIdx.x;
     const uint32_t row = b / (uint32_t)chunks;
     x = (int)(b - row * (uint32_t)chunks) * kNiThreads + (int)threadIdx.x;
     if (x >= d.nx) return false;
-    const uint32_t zr = row / (uint32_t)d.ny;
-    y = (int)(row - zr * (uint32_t)d.ny);
-    s = (int)(zr / (uint32_t)d.nz);
-    z = (int)(zr - (uint32_t)s * (uint32_t)d.nz);
-    q = (int64_t)row * d.nx + x;
+    const uint32_t zs = row / (uint32_t)d.ny;
+    y = (int)(row - zs * (uint32_t)d.ny);
+    z = (int)(zs >> 1);
+    s = (int)(zs & 1u);
+    q = (((int64_t)s * d.nz + z) * d.ny + y) * d.nx + x;
     return true;
+}
+
+// Field indices of the 14 moving stencil neighbours of node (s, z, y, x), in the order of
+// stencil(): the sc-1 links +x, -x, +y, -y, +z, -z on the node's own sub-lattice, then the
+// bcc-1/2 links on the other, whose +1/2 neighbour along an axis has index coordinate + s and
+// whose -1/2 neighbour has + s - 1.  32-bit: 2 nx ny nz < 2^32 (checked when the mode is enabled).
+__device__ __forceinline__ void ni_neighbors(const Dims& d, int s, int z, int y, int x, uint32_t (&m)[kStencil]) {
+    const uint32_t nx = (uint32_t)d.nx, nxy = nx * (uint32_t)d.ny, pl = (uint32_t)d.plane;
+    const uint32_t own = (uint32_t)s * pl, oth = (uint32_t)(1 - s) * pl;
+    const uint32_t xs = (uint32_t)x, ys = (uint32_t)y * nx, zs = (uint32_t)z * nxy;
+    m[0] = own + zs + ys + (uint32_t)wrap(x + 1, d.nx);
+    m[1] = own + zs + ys + (uint32_t)wrap(x - 1, d.nx);
+    m[2] = own + zs + (uint32_t)wrap(y + 1, d.ny) * nx + xs;
+    m[3] = own + zs + (uint32_t)wrap(y - 1, d.ny) * nx + xs;
+    m[4] = own + (uint32_t)wrap(z + 1, d.nz) * nxy + ys + xs;
+    m[5] = own + (uint32_t)wrap(z - 1, d.nz) * nxy + ys + xs;
+    const uint32_t X[2] = {(uint32_t)wrap(x + s, d.nx), (uint32_t)wrap(x + s - 1, d.nx)};
+    const uint32_t Y[2] = {(uint32_t)wrap(y + s, d.ny) * nx, (uint32_t)wrap(y + s - 1, d.ny) * nx};
+    const uint32_t Z[2] = {(uint32_t)wrap(z + s, d.nz) * nxy, (uint32_t)wrap(z + s - 1, d.nz) * nxy};
+#pragma unroll
+    for (int j = 0; j < 8; ++j) m[6 + j] = oth + Z[(j >> 2) & 1] + Y[(j >> 1) & 1] + X[j & 1];
 }
 
 // The pull gather of step_node: v[i] = f_i(x - c_i) in the codec's working value.
@@ -143,11 +159,14 @@ __global__ void __launch_bounds__(kNiThreads) k_ni_fields(Dims d, int chunks, co
     const int64_t n = 2 * d.plane;
     const F r0 = rho[q], F0 = A[n + q];
     F g[3] = {F(0), F(0), F(0)}, lr = F(14.0 / 36.0) * r0, lF = F(14.0 / 36.0) * F0;
+    uint32_t nb[kStencil];
+    ni_neighbors(d, s, z, y, x, nb);
+#pragma unroll
     for (int k = 0; k < kStencil; ++k) {
         int cx, cy, cz;
         F w;
         stencil(k, cx, cy, cz, w);
-        const int64_t m = ni_neighbor(d, s, z, y, x, cx, cy, cz);
+        const uint32_t m = nb[k];
         const F rn = rho[m];
         g[0] += w * F(0.5 * cx) * rn;
         g[1] += w * F(0.5 * cy) * rn;
@@ -166,11 +185,14 @@ __device__ __forceinline__ void ni_force(const Dims& d, const NiEos& e, const F*
                                          const F* __restrict__ A, int64_t q, int s, int z, int y, int x, F (&g)[3]) {
     const int64_t n = 2 * d.plane;
     F dmu[3] = {0, 0, 0}, dF[3] = {0, 0, 0}, dlF[3] = {0, 0, 0}, divI[3] = {0, 0, 0};
+    uint32_t nb[kStencil];
+    ni_neighbors(d, s, z, y, x, nb);
+#pragma unroll
     for (int k = 0; k < kStencil; ++k) {
         int cx, cy, cz;
         F w;
         stencil(k, cx, cy, cz, w);
-        const int64_t m = ni_neighbor(d, s, z, y, x, cx, cy, cz);
+        const uint32_t m = nb[k];
         const int cc[3] = {cx, cy, cz};
         const F gr[3] = {A[2 * n + m], A[3 * n + m], A[4 * n + m]};
         const F iso = F(-0.5) * (gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]) - rho[m] * A[5 * n + m];
@@ -271,6 +293,102 @@ __global__ void __launch_bounds__(kNiThreads) k_ni_step(const typename Codec::ra
     if (!ok) atomicOr(err, 1);
 }
 
+// Two x-adjacent nodes per thread (16-bit storage, nx even): the x-pair gather of k_step2x and
+// packed FP32x2 arithmetic.  Blocks cover (row, chunk of x pairs), rows (s, z, y); x is the
+// thread's even node, q its field index.
+__device__ __forceinline__ bool ni_pair(const Dims& d, int chunks, uint32_t& q, int& s, int& z, int& y, int& x) {
+    const uint32_t b = blockIdx.x;
+    const uint32_t row = b / (uint32_t)chunks;
+    x = 2 * ((int)(b - row * (uint32_t)chunks) * (int)blockDim.x + (int)threadIdx.x);
+    if (x >= d.nx) return false;
+    const uint32_t zr = row / (uint32_t)d.ny;
+    y = (int)(row - zr * (uint32_t)d.ny);
+    s = (int)(zr / (uint32_t)d.nz);
+    z = (int)(zr - (uint32_t)s * (uint32_t)d.nz);
+    q = row * (uint32_t)d.nx + (uint32_t)x;
+    return true;
+}
+
+template <class Codec>
+__device__ __forceinline__ void ni_gather2x(const typename Codec::raw_t* __restrict__ src, const Dims& d, int s, int z,
+                                            int y, int x, typename Codec::pair_t (&pv)[kQ]) {
+    const uint32_t xm = (uint32_t)wrap(x - 2, d.nx), x0 = (uint32_t)x, xq = (uint32_t)wrap(x + 2, d.nx);
+    RowAddr2x<Codec> a;
+    a.set(src, d, s, z, y);
+    static_for<kQ>([&](auto I) { pv[I] = load_pair2x<Codec, I>(a, (uint32_t)d.plane, xm, x0, xq); });
+}
+
+// k_ni_density for an x pair.
+template <class Codec>
+__global__ void __launch_bounds__(kStepThreads) k_ni_density2x(const typename Codec::raw_t* __restrict__ src, Dims d,
+                                                               int chunks, Consts<float> K, NiEos e,
+                                                               float* __restrict__ rho, float* __restrict__ A) {
+    uint32_t q;
+    int s, z, y, x;
+    if (!ni_pair(d, chunks, q, s, z, y, x)) return;
+    typename Codec::pair_t pv[kQ];
+    ni_gather2x<Codec>(src, d, s, z, y, x, pv);
+    constexpr float inv_scale = (float)(1.0 / Codec::kScale);
+    F2 dr(0.f);  // rho - 1 = sum_i (f_i - w_i), in the population order of k_ni_density
+    static_for<kQ>([&](auto I) { dr += F2(Codec::unpack2(pv[I])) * F2(K.w[vel(I).shell] * inv_scale); });
+    const F2 r = F2(1.f) + dr;
+    float mu0, F0, mu1, F1;
+    ni_eos<float>(r.v.x, e, mu0, F0);
+    ni_eos<float>(r.v.y, e, mu1, F1);
+    const size_t n = 2 * (size_t)d.plane;
+    *reinterpret_cast<float2*>(rho + q) = r.v;
+    *reinterpret_cast<float2*>(A + q) = make_float2(mu0, mu1);
+    *reinterpret_cast<float2*>(A + n + q) = make_float2(F0, F1);
+}
+
+// k_ni_step for an x pair: the forcing is applied as each population's equilibrium is formed.
+template <class Codec>
+__global__ void __launch_bounds__(kStepThreads, 3) k_ni_step2x(const typename Codec::raw_t* __restrict__ src,
+                                                               typename Codec::raw_t* __restrict__ dst, Dims d,
+                                                               int chunks, Consts<float> K, float tb, float inv_theta0,
+                                                               const float* __restrict__ A, int* __restrict__ err) {
+    using P = typename Codec::pair_t;
+    using C2 = Codec2<Codec>;
+    uint32_t q;
+    int s, z, y, x;
+    if (!ni_pair(d, chunks, q, s, z, y, x)) return;
+    P pv[kQ];
+    ni_gather2x<Codec>(src, d, s, z, y, x, pv);
+    auto vget = [&](auto I) { return F2(Codec::unpack2(pv[I])); };
+    const size_t n = 2 * (size_t)d.plane;
+    const F2 gx(*reinterpret_cast<const float2*>(A + 7 * n + q)), gy(*reinterpret_cast<const float2*>(A + 8 * n + q)),
+        gz(*reinterpret_cast<const float2*>(A + 9 * n + q));
+    constexpr float inv_scale = (float)(1.0 / Codec::kScale);
+    const NodeMoments<F2> m =
+        moments_from<F2>([&](auto I) { return C2::dev(vget(I), F2(K.w[vel(I).shell] * inv_scale)); });
+    NodeState<F2> st;
+    st.drho = m.drho;
+    st.rho = F2(1.f) + m.drho;
+    const F2 inv_rho = recip(st.rho);
+    st.ux = fma(F2(0.5f), gx, m.jx * inv_rho);
+    st.uy = fma(F2(0.5f), gy, m.jy * inv_rho);
+    st.uz = fma(F2(0.5f), gz, m.jz * inv_rho);
+    st.eta = F2(0.f);  // isothermal: the equilibrium at theta_0
+    if (!state_ok(st)) atomicOr(err, 1);
+    // F_i / w_i = g.(c_i - u) / theta0 (1 + h^eq_i), in units of the stored scale
+    const F2 it(inv_theta0);
+    const F2 hx = gx * it, hy = gy * it, hz = gz * it;
+    const F2 hu = hx * st.ux + hy * st.uy + hz * st.uz;
+    const F2 tbv(tb), half_f(1.f - 0.5f * tb), scale((float)Codec::kScale);
+    P* outp = reinterpret_cast<P*>(dst + (size_t)s * kQ * d.plane + (q - (uint32_t)s * (uint32_t)d.plane));
+    const size_t pstride = (size_t)d.plane / 2;
+    equilibrium_relax_g<C2, true>(st, K, scale, F2(0.f), vget, [&](auto I, F2 veq) {
+        constexpr Vel c = vel(I);
+        F2 gc = F2(0.f) - hu;
+        if constexpr (c.x != 0) gc = fma(F2(0.5f * c.x), hx, gc);
+        if constexpr (c.y != 0) gc = fma(F2(0.5f * c.y), hy, gc);
+        if constexpr (c.z != 0) gc = fma(F2(0.5f * c.z), hz, gc);
+        const F2 v = vget(I);
+        const F2 val = fma(half_f, gc * (scale + veq), fma(tbv, veq - v, v));
+        outp[(size_t)I * pstride] = Codec::to_raw2(val.v);
+    });
+}
+
 template <class F>
 static cudaError_t ni_codec(int prec, F&& f) {
     switch (prec) {
@@ -302,13 +420,29 @@ cudaError_t launch_nonideal_step(int prec, const void* src, void* dst, const Dim
             K = &c.kf;
         R* rho = reinterpret_cast<R*>(work);  // fields in the compute type: rho, A[10]
         R* A = rho + n;
-        k_ni_density<C><<<blocks, kNiThreads, 0, st>>>(static_cast<const typename C::raw_t*>(src), d, chunks, *K, e,
-                                                        rho, A);
+        const auto* in = static_cast<const typename C::raw_t*>(src);
+        auto* out = static_cast<typename C::raw_t*>(dst);
+        // 16-bit storage with nx even: the gathering passes on x pairs
+        constexpr bool kPairs = sizeof(typename C::raw_t) == 2;
+        const bool pairs = kPairs && d.nx % 2 == 0;
+        const int half = d.nx / 2;
+        const int th2 = half >= 128 ? 128 : ((half + 31) / 32) * 32;
+        const int chunks2 = (half + th2 - 1) / th2;
+        const unsigned blocks2 = (unsigned)(d.rows * chunks2);
+        if constexpr (kPairs) {
+            if (pairs) k_ni_density2x<C><<<blocks2, th2, 0, st>>>(in, d, chunks2, *K, e, rho, A);
+        }
+        if (!pairs) k_ni_density<C><<<blocks, kNiThreads, 0, st>>>(in, d, chunks, *K, e, rho, A);
         k_ni_fields<R><<<blocks, kNiThreads, 0, st>>>(d, chunks, rho, A);
         k_ni_force<R><<<blocks, kNiThreads, 0, st>>>(d, chunks, e, rho, A);
-        k_ni_step<C><<<blocks, kNiThreads, 0, st>>>(static_cast<const typename C::raw_t*>(src),
-                                                     static_cast<typename C::raw_t*>(dst), d, chunks, *K,
-                                                     (R)twobeta, (R)(1.0 / c.theta0), A, err);
+        if constexpr (kPairs) {
+            if (pairs)
+                k_ni_step2x<C><<<blocks2, th2, 0, st>>>(in, out, d, chunks2, *K, (float)twobeta,
+                                                         (float)(1.0 / c.theta0), A, err);
+        }
+        if (!pairs)
+            k_ni_step<C><<<blocks, kNiThreads, 0, st>>>(in, out, d, chunks, *K, (R)twobeta, (R)(1.0 / c.theta0), A,
+                                                         err);
         return cudaGetLastError();
     });
 }

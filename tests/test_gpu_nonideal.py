@@ -11,7 +11,14 @@ the relative error of a population is about n (1 + sqrt(41)) 2^-24 max|h| /
 min(1 + h).  The van der Waals slab (0.43 to 1.66) measures 1.2e-6, within
 2e-6; the Peng-Robinson and Carnahan-Starling slabs reach down to 0.27 and
 0.35 and up to 2.47 and 1.90, for which the estimate is 1.5e-5 and 9e-6:
-their bound is 1.5e-5 (measured 1.6e-6 and 1.1e-6)."""
+their bound is 1.5e-5 (measured 1.6e-6 and 1.1e-6).
+
+16-bit storage (FP16 2^8 h, BF16 h): h is rounded to nearest at initialisation and after every
+step, a relative error in f of at most u |h| / (1 + h) each time (u = 2^-11, 2^-8), and the
+errors of n steps add at most linearly: (n + 1) u max(|h| / (1 + h)) over the oracle's final
+state.  Measured after 5 steps: 3.6-4.2e-4 (FP16) and 2.7-3.4e-3 (BF16), no more than about twice
+the initial rounding, against bounds of 2.9e-3 and more.  Both the x-pair passes (nx even) and
+the one-node passes (nx odd) run."""
 import functools
 
 import numpy as np
@@ -72,6 +79,23 @@ def test_nonideal_step_matches_oracle(prec, tol, eos):
     ref = ni.step(f0, 0.5, e, EOS[eos][1], nsteps=steps)
     rel = np.abs(to_oracle_order(got, lib_to_oracle_perm()) - ref) / np.abs(ref)
     assert rel.max() <= tol, rel.max()
+
+
+@pytest.mark.parametrize("shape", [(12, 4, 6), (13, 4, 6)])
+@pytest.mark.parametrize("prec", ["f16", "bf16"])
+@pytest.mark.parametrize("eos", list(EOS))
+def test_nonideal_16bit_step_matches_oracle(prec, eos, shape):
+    steps = 5
+    u = {"f16": 2.0 ** -11, "bf16": 2.0 ** -8}[prec]
+    e, rho = _slab(shape, noise=0.02, eos=eos)
+    got, _, _ = _gpu(shape, prec, e, rho, steps, eos=eos)
+    f0 = oracle.init_fields(rho, np.zeros((3,) + rho.shape), np.full(rho.shape, TH0))
+    ref = ni.step(f0, 0.5, e, EOS[eos][1], nsteps=steps)
+    w = np.asarray(oracle.velocities()[1])[None, :, None, None, None]
+    h = ref / w - 1.0
+    tol = (steps + 1) * u * float((np.abs(h) / (1.0 + h)).max())
+    rel = np.abs(to_oracle_order(got, lib_to_oracle_perm()) - ref) / np.abs(ref)
+    assert rel.max() <= tol, (rel.max(), tol)
 
 
 @pytest.mark.parametrize("eos", list(EOS))
