@@ -320,7 +320,7 @@ lb_status lb_nonideal_constants(int eos, double theta_star, double rho_c, double
  * Needs the projected series equilibrium (no LB_FLAG_PAPER_LITERAL or
  * LB_FLAG_ENTROPIC; LB_ERR_ARG), fewer than 2^31 cells (LB_ERR_ARG), and
  * neither walls nor stochastic rounding (LB_ERR_STATE).  Each step runs four one-node-per-thread kernels; the work
- * buffer is 88 bytes per node.  A batch (lb_batch_step) refuses members with
+ * buffer is 96 bytes per node.  A batch (lb_batch_step) refuses members with
  * it on (LB_ERR_STATE).  eos = 0 restores the energy-conserving update. */
 lb_status lb_set_nonideal(lb_ctx *ctx, int eos, double a, double b, double kappa, double eta);
 

@@ -57,6 +57,23 @@ __device__ __forceinline__ void stencil(int k, int& cx, int& cy, int& cz, F& w) 
 
 constexpr int kNiThreads = 128;
 
+// Per-node field records in the compute type F (n = 2 nx ny nz nodes, field index q):
+//   P1[q] = {rho, mu, F, 0}                        (density pass)
+//   P2[q] = {grad2 rho (3), lap rho}, P3[q] = lap F (field pass)
+//   G[a n + q] = g^nid_a                           (force pass)
+// A stencil neighbour's values then take three loads.
+template <class F>
+struct alignas(4 * sizeof(F)) NiRec {
+    F x, y, z, w;
+};
+template <class F>
+struct NiFields {
+    NiRec<F>* P1;
+    NiRec<F>* P2;
+    F* P3;
+    F* G;
+};
+
 // Node of this thread: blocks cover (row, x chunk) pairs, rows running (z, s, y) with y fastest, so
 // that the two sub-lattices of a plane are visited together (the stencil passes read the other
 // sub-lattice's fields, which then come from L2).  The coordinates come from 32-bit divisions of
@@ -130,8 +147,7 @@ __device__ __forceinline__ void ni_gather(const typename Codec::raw_t* __restric
 template <class Codec>
 __global__ void __launch_bounds__(kNiThreads) k_ni_density(const typename Codec::raw_t* __restrict__ src, Dims d,
                                                            int chunks, Consts<typename Codec::R> K, NiEos e,
-                                                           typename Codec::R* __restrict__ rho,
-                                                           typename Codec::R* __restrict__ A) {
+                                                           NiFields<typename Codec::R> fl) {
     using R = typename Codec::R;
     int64_t q;
     int s, z, y, x;
@@ -141,23 +157,18 @@ __global__ void __launch_bounds__(kNiThreads) k_ni_density(const typename Codec:
     R dr = 0;  // rho - 1 = sum_i (f_i - w_i)
     static_for<kQ>([&](auto I) { dr += Codec::dev(v[I], K.w[vel(I).shell] * R(1.0 / Codec::kScale)); });
     const R r = R(1) + dr;
-    rho[q] = r;
     R mu, Fe;
     ni_eos<R>(r, e, mu, Fe);
-    A[q] = mu;
-    A[2 * d.plane + q] = Fe;
+    fl.P1[q] = NiRec<R>{r, mu, Fe, R(0)};
 }
 
-// A[k][node]: 0 mu, 1 F (both from k_ni_density), 2..4 grad2 rho, 5 lap rho, 6 lap F (k_ni_fields),
-// 7..9 g^nid (k_ni_force).
 template <class F>
-__global__ void __launch_bounds__(kNiThreads) k_ni_fields(Dims d, int chunks, const F* __restrict__ rho,
-                                                          F* __restrict__ A) {
+__global__ void __launch_bounds__(kNiThreads) k_ni_fields(Dims d, int chunks, NiFields<F> fl) {
     int64_t q;
     int s, z, y, x;
     if (!ni_node(d, chunks, q, s, z, y, x)) return;
-    const int64_t n = 2 * d.plane;
-    const F r0 = rho[q], F0 = A[n + q];
+    const NiRec<F> p0 = fl.P1[q];
+    const F r0 = p0.x, F0 = p0.z;
     F g[3] = {F(0), F(0), F(0)}, lr = F(14.0 / 36.0) * r0, lF = F(14.0 / 36.0) * F0;
     uint32_t nb[kStencil];
     ni_neighbors(d, s, z, y, x, nb);
@@ -166,24 +177,23 @@ __global__ void __launch_bounds__(kNiThreads) k_ni_fields(Dims d, int chunks, co
         int cx, cy, cz;
         F w;
         stencil(k, cx, cy, cz, w);
-        const uint32_t m = nb[k];
-        const F rn = rho[m];
+        const NiRec<F> pn = fl.P1[nb[k]];
+        const F rn = pn.x;
         g[0] += w * F(0.5 * cx) * rn;
         g[1] += w * F(0.5 * cy) * rn;
         g[2] += w * F(0.5 * cz) * rn;
         lr += w * rn;
-        lF += w * A[n + m];
+        lF += w * pn.z;
     }
-    for (int a = 0; a < 3; ++a) A[(2 + a) * n + q] = g[a] * F(1.0 / kHatTheta);
-    A[5 * n + q] = F(2.0 / kHatTheta) * (lr - r0);
-    A[6 * n + q] = F(2.0 / kHatTheta) * (lF - F0);
+    fl.P2[q] = NiRec<F>{g[0] * F(1.0 / kHatTheta), g[1] * F(1.0 / kHatTheta), g[2] * F(1.0 / kHatTheta),
+                        F(2.0 / kHatTheta) * (lr - r0)};
+    fl.P3[q] = F(2.0 / kHatTheta) * (lF - F0);
 }
 
 // g^nid at node q (s, z, y, x) from the fields of its stencil neighbours, into g[3].
 template <class F>
-__device__ __forceinline__ void ni_force(const Dims& d, const NiEos& e, const F* __restrict__ rho,
-                                         const F* __restrict__ A, int64_t q, int s, int z, int y, int x, F (&g)[3]) {
-    const int64_t n = 2 * d.plane;
+__device__ __forceinline__ void ni_force(const Dims& d, const NiEos& e, const NiFields<F>& fl, int64_t q, int s,
+                                         int z, int y, int x, F (&g)[3]) {
     F dmu[3] = {0, 0, 0}, dF[3] = {0, 0, 0}, dlF[3] = {0, 0, 0}, divI[3] = {0, 0, 0};
     uint32_t nb[kStencil];
     ni_neighbors(d, s, z, y, x, nb);
@@ -194,14 +204,16 @@ __device__ __forceinline__ void ni_force(const Dims& d, const NiEos& e, const F*
         stencil(k, cx, cy, cz, w);
         const uint32_t m = nb[k];
         const int cc[3] = {cx, cy, cz};
-        const F gr[3] = {A[2 * n + m], A[3 * n + m], A[4 * n + m]};
-        const F iso = F(-0.5) * (gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]) - rho[m] * A[5 * n + m];
+        const NiRec<F> p1 = fl.P1[m], p2 = fl.P2[m];
+        const F lFm = fl.P3[m];
+        const F gr[3] = {p2.x, p2.y, p2.z};
+        const F iso = F(-0.5) * (gr[0] * gr[0] + gr[1] * gr[1] + gr[2] * gr[2]) - p1.x * p2.w;
         for (int a = 0; a < 3; ++a) {
             if (cc[a] == 0) continue;
             const F wc = w * F(0.5 * cc[a]);
-            dmu[a] += wc * A[m];
-            dF[a] += wc * A[n + m];
-            dlF[a] += wc * A[6 * n + m];
+            dmu[a] += wc * p1.y;
+            dF[a] += wc * p1.z;
+            dlF[a] += wc * lFm;
         }
         // grad2_b I_ab: sum over the stencil of w c_b I_ab(x + c)
         for (int a = 0; a < 3; ++a) {
@@ -214,37 +226,38 @@ __device__ __forceinline__ void ni_force(const Dims& d, const NiEos& e, const F*
             divI[a] += t;
         }
     }
-    const F r0 = rho[q], mu0 = A[q], inv_th = F(1.0 / kHatTheta);
+    const NiRec<F> q1 = fl.P1[q], q2 = fl.P2[q];
+    const F r0 = q1.x, mu0 = q1.y, inv_th = F(1.0 / kHatTheta);
+    const F g2r[3] = {q2.x, q2.y, q2.z};
     for (int a = 0; a < 3; ++a) {
         const F g2mu = dmu[a] * inv_th, g2F = dF[a] * inv_th, g2lF = dlF[a] * inv_th;
         const F g4F = g2F - F(0.5 * kHatTheta) * g2lF;
-        const F rg = -(r0 * g2mu + mu0 * A[(2 + a) * n + q] - F(e.eta) * g2F - (F(1) - F(e.eta)) * g4F +
+        const F rg = -(r0 * g2mu + mu0 * g2r[a] - F(e.eta) * g2F - (F(1) - F(e.eta)) * g4F +
                        F(e.kappa) * divI[a] * inv_th);
         g[a] = rg / r0;
     }
 }
 
-// g^nid of every node into A[7..9] (a pass of its own: folded into the step, the stencil sums raise
-// the step's register count and the fused step ran slower than the two passes).
+// g^nid of every node into G (a pass of its own: folded into the step, the stencil sums raise the
+// step's register count and the fused step ran slower than the two passes).
 template <class F>
-__global__ void __launch_bounds__(kNiThreads) k_ni_force(Dims d, int chunks, NiEos e, const F* __restrict__ rho,
-                                                          F* __restrict__ A) {
+__global__ void __launch_bounds__(kNiThreads) k_ni_force(Dims d, int chunks, NiEos e, NiFields<F> fl) {
     int64_t q;
     int s, z, y, x;
     if (!ni_node(d, chunks, q, s, z, y, x)) return;
     F g[3];
-    ni_force<F>(d, e, rho, A, q, s, z, y, x, g);
+    ni_force<F>(d, e, fl, q, s, z, y, x, g);
     const int64_t n = 2 * d.plane;
-    for (int a = 0; a < 3; ++a) A[(7 + a) * n + q] = g[a];
+    for (int a = 0; a < 3; ++a) fl.G[a * n + q] = g[a];
 }
 
-// The pull step with the forced BGK collision; g^nid from A[7..9].
+// The pull step with the forced BGK collision; g^nid from G.
 template <class Codec>
 __global__ void __launch_bounds__(kNiThreads) k_ni_step(const typename Codec::raw_t* __restrict__ src,
                                                         typename Codec::raw_t* __restrict__ dst, Dims d, int chunks,
                                                         Consts<typename Codec::R> K, typename Codec::R tb,
                                                         typename Codec::R inv_theta0,
-                                                        const typename Codec::R* __restrict__ A,
+                                                        const typename Codec::R* __restrict__ G,
                                                         int* __restrict__ err) {
     using R = typename Codec::R;
     using T = typename Codec::raw_t;
@@ -252,7 +265,7 @@ __global__ void __launch_bounds__(kNiThreads) k_ni_step(const typename Codec::ra
     int s, z, y, x;
     if (!ni_node(d, chunks, q, s, z, y, x)) return;
     const int64_t n = 2 * d.plane;
-    const R gf[3] = {A[7 * n + q], A[8 * n + q], A[9 * n + q]};
+    const R gf[3] = {G[q], G[n + q], G[2 * n + q]};
     R v[kQ];
     ni_gather<Codec>(src, d, s, z, y, x, v);
     R dv[kQ];
@@ -322,7 +335,7 @@ __device__ __forceinline__ void ni_gather2x(const typename Codec::raw_t* __restr
 template <class Codec>
 __global__ void __launch_bounds__(kStepThreads) k_ni_density2x(const typename Codec::raw_t* __restrict__ src, Dims d,
                                                                int chunks, Consts<float> K, NiEos e,
-                                                               float* __restrict__ rho, float* __restrict__ A) {
+                                                               NiFields<float> fl) {
     uint32_t q;
     int s, z, y, x;
     if (!ni_pair(d, chunks, q, s, z, y, x)) return;
@@ -335,10 +348,8 @@ __global__ void __launch_bounds__(kStepThreads) k_ni_density2x(const typename Co
     float mu0, F0, mu1, F1;
     ni_eos<float>(r.v.x, e, mu0, F0);
     ni_eos<float>(r.v.y, e, mu1, F1);
-    const size_t n = 2 * (size_t)d.plane;
-    *reinterpret_cast<float2*>(rho + q) = r.v;
-    *reinterpret_cast<float2*>(A + q) = make_float2(mu0, mu1);
-    *reinterpret_cast<float2*>(A + n + q) = make_float2(F0, F1);
+    fl.P1[q] = NiRec<float>{r.v.x, mu0, F0, 0.f};
+    fl.P1[q + 1] = NiRec<float>{r.v.y, mu1, F1, 0.f};
 }
 
 // k_ni_step for an x pair: the forcing is applied as each population's equilibrium is formed.
@@ -346,7 +357,7 @@ template <class Codec>
 __global__ void __launch_bounds__(kStepThreads, 3) k_ni_step2x(const typename Codec::raw_t* __restrict__ src,
                                                                typename Codec::raw_t* __restrict__ dst, Dims d,
                                                                int chunks, Consts<float> K, float tb, float inv_theta0,
-                                                               const float* __restrict__ A, int* __restrict__ err) {
+                                                               const float* __restrict__ G, int* __restrict__ err) {
     using P = typename Codec::pair_t;
     using C2 = Codec2<Codec>;
     uint32_t q;
@@ -356,8 +367,8 @@ __global__ void __launch_bounds__(kStepThreads, 3) k_ni_step2x(const typename Co
     ni_gather2x<Codec>(src, d, s, z, y, x, pv);
     auto vget = [&](auto I) { return F2(Codec::unpack2(pv[I])); };
     const size_t n = 2 * (size_t)d.plane;
-    const F2 gx(*reinterpret_cast<const float2*>(A + 7 * n + q)), gy(*reinterpret_cast<const float2*>(A + 8 * n + q)),
-        gz(*reinterpret_cast<const float2*>(A + 9 * n + q));
+    const F2 gx(*reinterpret_cast<const float2*>(G + q)), gy(*reinterpret_cast<const float2*>(G + n + q)),
+        gz(*reinterpret_cast<const float2*>(G + 2 * n + q));
     constexpr float inv_scale = (float)(1.0 / Codec::kScale);
     const NodeMoments<F2> m =
         moments_from<F2>([&](auto I) { return C2::dev(vget(I), F2(K.w[vel(I).shell] * inv_scale)); });
@@ -400,7 +411,7 @@ static cudaError_t ni_codec(int prec, F&& f) {
     }
 }
 
-size_t nonideal_doubles(const Dims& d) { return (size_t)11 * 2 * d.plane; }
+size_t nonideal_doubles(const Dims& d) { return (size_t)12 * 2 * d.plane; }
 
 cudaError_t launch_nonideal_step(int prec, const void* src, void* dst, const Dims& d, const LaunchConsts& c,
                                  double twobeta, int kind, const double eos[4], double* work, int* err,
@@ -418,8 +429,12 @@ cudaError_t launch_nonideal_step(int prec, const void* src, void* dst, const Dim
             K = &c.kd;
         else
             K = &c.kf;
-        R* rho = reinterpret_cast<R*>(work);  // fields in the compute type: rho, A[10]
-        R* A = rho + n;
+        // field records in the compute type: P1, P2 (4 values per node each), P3, G (1 and 3)
+        NiFields<R> fl;
+        fl.P1 = reinterpret_cast<NiRec<R>*>(work);
+        fl.P2 = fl.P1 + n;
+        fl.P3 = reinterpret_cast<R*>(fl.P2 + n);
+        fl.G = fl.P3 + n;
         const auto* in = static_cast<const typename C::raw_t*>(src);
         auto* out = static_cast<typename C::raw_t*>(dst);
         // 16-bit storage with nx even: the gathering passes on x pairs
@@ -430,18 +445,18 @@ cudaError_t launch_nonideal_step(int prec, const void* src, void* dst, const Dim
         const int chunks2 = (half + th2 - 1) / th2;
         const unsigned blocks2 = (unsigned)(d.rows * chunks2);
         if constexpr (kPairs) {
-            if (pairs) k_ni_density2x<C><<<blocks2, th2, 0, st>>>(in, d, chunks2, *K, e, rho, A);
+            if (pairs) k_ni_density2x<C><<<blocks2, th2, 0, st>>>(in, d, chunks2, *K, e, fl);
         }
-        if (!pairs) k_ni_density<C><<<blocks, kNiThreads, 0, st>>>(in, d, chunks, *K, e, rho, A);
-        k_ni_fields<R><<<blocks, kNiThreads, 0, st>>>(d, chunks, rho, A);
-        k_ni_force<R><<<blocks, kNiThreads, 0, st>>>(d, chunks, e, rho, A);
+        if (!pairs) k_ni_density<C><<<blocks, kNiThreads, 0, st>>>(in, d, chunks, *K, e, fl);
+        k_ni_fields<R><<<blocks, kNiThreads, 0, st>>>(d, chunks, fl);
+        k_ni_force<R><<<blocks, kNiThreads, 0, st>>>(d, chunks, e, fl);
         if constexpr (kPairs) {
             if (pairs)
                 k_ni_step2x<C><<<blocks2, th2, 0, st>>>(in, out, d, chunks2, *K, (float)twobeta,
-                                                         (float)(1.0 / c.theta0), A, err);
+                                                         (float)(1.0 / c.theta0), fl.G, err);
         }
         if (!pairs)
-            k_ni_step<C><<<blocks, kNiThreads, 0, st>>>(in, out, d, chunks, *K, (R)twobeta, (R)(1.0 / c.theta0), A,
+            k_ni_step<C><<<blocks, kNiThreads, 0, st>>>(in, out, d, chunks, *K, (R)twobeta, (R)(1.0 / c.theta0), fl.G,
                                                          err);
         return cudaGetLastError();
     });

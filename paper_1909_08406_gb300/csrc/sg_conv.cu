@@ -282,20 +282,31 @@ __global__ void __launch_bounds__(kWgThreads) k_conv_wgrad(sg_shape s, const bf1
     }
 }
 
-// dw[co][tap][ci] = sum_p partials[p][tap][co][ci]: one warp per element, lane l sums the parts
-// l, l + 32, ... in order, then a fixed shuffle tree (deterministic).
-__global__ void k_wgrad_reduce(int cin, int cout, int parts, const float* __restrict__ partials,
-                               float* __restrict__ dw) {
-    const int e = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+// dw[co][tap][ci] = sum_p partials[p][tap][co][ci] (deterministic).  A block takes 32 consecutive
+// partial entries (one per lane, coalesced); warp w adds the parts of the w-th of 8 equal ranges
+// in order, then the 8 range sums are added in the order w = 0 .. 7.
+__global__ void __launch_bounds__(256) k_wgrad_reduce(int cin, int cout, int parts, const float* __restrict__ partials,
+                                                      float* __restrict__ dw) {
+    __shared__ float sh[8][32];
     const int n = 27 * cin * cout;
-    if (e >= n) return;
-    const int ci = e % cin, tap = (e / cin) % 27, co = e / (27 * cin);
-    const int64_t off = (int64_t)tap * cout * cin + co * cin + ci, stride = (int64_t)27 * cout * cin;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int off = (int)blockIdx.x * 32 + lane;  // tap * cout * cin + co * cin + ci
     float sum = 0.f;
-    for (int p = lane; p < parts; p += 32) sum += partials[(int64_t)p * stride + off];
+    if (off < n) {
+        const int p0 = parts * w / 8, p1 = parts * (w + 1) / 8;
+        const float* p = partials + off;
+#pragma unroll 4
+        for (int k = p0; k < p1; ++k) sum += p[(int64_t)k * n];
+    }
+    sh[w][lane] = sum;
+    __syncthreads();
+    if (w == 0 && off < n) {
+        float t = sh[0][lane];
 #pragma unroll
-    for (int w = 16; w > 0; w >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, w);
-    if (lane == 0) dw[e] = sum;
+        for (int k = 1; k < 8; ++k) t += sh[k][lane];
+        const int ci = off % cin, co = (off / cin) % cout, tap = off / (cin * cout);
+        dw[((int64_t)co * 27 + tap) * cin + ci] = t;
+    }
 }
 
 constexpr int kBiasBlocks = 512;  // blocks of the bias-gradient partial sums
@@ -334,12 +345,21 @@ __global__ void __launch_bounds__(256) k_bias_partials(int64_t voxels, int cout,
         for (int k = 0; k < 8; ++k) partial[(int64_t)blockIdx.x * cout + 8 * threadIdx.x + k] = sh[threadIdx.x][k];
 }
 
-// db[co] = sum over blocks of the partials, one warp per channel, fixed order.
+// db[co] = sum over blocks of the partials, one warp per channel, fixed order: lane l adds the
+// partials l, l + 32, ... (all loads issued before the additions), then a shuffle tree.
 __global__ void k_bias_finish(int blocks, int cout, const float* __restrict__ partial, float* __restrict__ db) {
     const int co = (int)(threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (co >= cout) return;
+    constexpr int kMaxPer = kBiasBlocks / 32;
+    float v[kMaxPer];
+#pragma unroll
+    for (int j = 0; j < kMaxPer; ++j) {
+        const int b = lane + 32 * j;
+        v[j] = b < blocks ? partial[(int64_t)b * cout + co] : 0.f;
+    }
     float sum = 0.f;
-    for (int b = lane; b < blocks; b += 32) sum += partial[(int64_t)b * cout + co];
+#pragma unroll
+    for (int j = 0; j < kMaxPer; ++j) sum += v[j];
 #pragma unroll
     for (int w = 16; w > 0; w >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, w);
     if (lane == 0) db[co] = sum;
@@ -1483,7 +1503,7 @@ static int launch_wgrad(sg_shape s, const void* x, const void* dz, float* dw, fl
                                                                          static_cast<const bf16*>(dz), partials, parts);
     }
     const int n = 27 * CIN * COUT;
-    k_wgrad_reduce<<<(n + 7) / 8, 256, 0, st>>>(CIN, COUT, parts, partials, dw);
+    k_wgrad_reduce<<<(n + 31) / 32, 256, 0, st>>>(CIN, COUT, parts, partials, dw);
     if (db) {
         // bias partials after the largest weight-gradient partials either kernel writes
         float* bias_part = partials + wgrad_parts_max(s) * 27 * CIN * COUT;
