@@ -1063,18 +1063,22 @@ __global__ void __launch_bounds__(640, 1)
 //   A[m][k] = X row (z+dz, y+dy) at voxel k,  m = (dz, dy, ci): 9 cin rows,
 //   B[k][n] = dZ row (z, y) at voxel k - dx,  n = (dx, co):     N = 3 cout.
 // Both operands are MN-major, i.e. channels contiguous, which is the
-// activations' own [voxel][channel] layout, in the canonical no-swizzle
-// layout: 8 channels of one row form a column of 64 16-byte chunks (1 KB,
-// written by one TMA box); columns are 1 KB apart (SBO) and the K direction is
-// contiguous (LBO = 128 B), so the k-th 16-voxel step of an MMA is a start
-// address 256 B further on.  The producer issues a stage's boxes from as many
-// lanes, one box each.  The 9 cin/8 channel groups of A are cut into
-// M = 128 tiles of 16 groups (the last tile padded with groups that are never
-// loaded and whose rows are discarded); B holds the dZ row in three copies
-// shifted by dx = -1, 0, +1: each copy is one 64-voxel box starting one voxel
-// before or after the row (every box lands on a 1 KB boundary), whose
-// out-of-range voxel the tensor map fills with zeros and a fixer warp then
-// overwrites with the periodic wrap voxel.  A CTA owns a contiguous range of rows and
+// activations' own [voxel][channel] layout: one TMA box writes an x row with
+// all its channels (32 or 64 bytes per voxel) as one column of the 32- or
+// 64-byte swizzled layout (LBO = the column's bytes between atoms along M or
+// N, SBO = 8 voxels along K), so the k-th 16-voxel step of an MMA is a start
+// address 16 voxels further on.  The producer issues a stage's boxes from as
+// many lanes, one box each.  Rows are taken in pairs (y, y + 1): one A stage
+// holds the 12 x rows (z + dz, y + dy'), dy' = -1 .. 2, at positions
+// p = 3 (dy' + 1) + (dz + 1), so output row y + j reads the window of 9
+// positions starting at 3 j, in the same (dy, dz) order, and the pair loads 12
+// x rows instead of 18.  The 9 rows of a window are cut into M = 128 tiles of
+// 128 / cin rows (the last tile padded with rows whose products are
+// discarded); B holds each dZ row of the pair in three copies shifted by dx = -1, 0, +1:
+// each copy is one 64-voxel box starting one voxel before or after the row
+// (every box lands on a column boundary), whose out-of-range voxel the tensor
+// map fills with zeros and a fixer warp then overwrites, at its swizzled place,
+// with the periodic wrap voxel.  A CTA owns a contiguous range of row pairs and
 // accumulates each tile's D[128][3 cout] (FP32) in tensor memory over all of
 // them; the epilogue writes the CTA's partial dw, summed over CTAs in a fixed
 // order by k_wgrad_reduce.
@@ -1094,10 +1098,12 @@ struct WgCfg {
     static constexpr int NT = (9 + PER_TILE - 1) / PER_TILE;  // tiles over the 9 (dz, dy) rows
     static constexpr int N = 3 * COUT;                  // B columns: (dx, co)
     static constexpr int NS = (N + 31) / 32 * 32;       // tensor-memory columns per tile (32-aligned)
-    static constexpr int SB = 3;                        // B stages (one row each)
-    static constexpr int A_STAGE = PER_TILE * COLA;     // 16 KB
-    static constexpr int B_STAGE = 3 * COLB;
-    static constexpr int SA = (220 * 1024 - SB * B_STAGE) / A_STAGE;  // A stages (one tile of one row each)
+    static constexpr int NLOAD = 12;                    // x rows loaded per row pair
+    static constexpr int NPOS = 3 + PER_TILE * NT;      // positions the two windows' tiles reach
+    static constexpr int A_STAGE = NPOS * COLA;         // one row pair's x rows
+    static constexpr int B_STAGE = 2 * 3 * COLB;        // one row pair's shifted dZ rows
+    static constexpr int SB = 3;                        // B stages
+    static constexpr int SA = (220 * 1024 - SB * B_STAGE) / A_STAGE;  // A stages
     static constexpr int SMEM = SA * A_STAGE + SB * B_STAGE + 1024;
     static constexpr int TMEM_USED = NT * NS;
     static constexpr int TMEM_COLS = TMEM_USED <= 32 ? 32 : TMEM_USED <= 64 ? 64 : TMEM_USED <= 128 ? 128
@@ -1112,6 +1118,7 @@ struct WgCfg {
     static_assert(N % 16 == 0 && N <= 256, "N = 3 cout must be a multiple of 16, at most 256");
     static_assert(TMEM_USED <= 512, "tensor memory");
     static_assert(SMEM <= 232448, "shared memory");
+    static_assert(SA >= 2, "A stages");
 };
 
 // Shared-memory descriptor of a swizzled MN-major operand: start address, LBO = stride between
@@ -1160,18 +1167,19 @@ __global__ void __launch_bounds__(256, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_holder;
 
-    // this CTA's rows [r0, r1) of the batch x nz x ny rows of 64 voxels (y fastest)
-    const int64_t rows = (int64_t)s.batch * s.nz * s.ny;
+    // this CTA's row pairs [r0, r1) of the batch x nz x ny / 2 pairs (y, y + 1) of 64-voxel rows
+    const int hy = s.ny / 2;
+    const int64_t rows = (int64_t)s.batch * s.nz * hy;
     const int64_t r0 = rows * blockIdx.x / gridDim.x, r1 = rows * (blockIdx.x + 1) / gridDim.x;
-    auto row_coord = [&](int64_t r, int& b, int& z, int& y) {
-        y = (int)(r % s.ny);
-        const int64_t q = r / s.ny;
+    auto row_coord = [&](int64_t r, int& b, int& z, int& y) {  // y: the pair's first row
+        y = 2 * (int)(r % hy);
+        const int64_t q = r / hy;
         z = (int)(q % s.nz);
         b = (int)(q / s.nz);
     };
 
     if (warp == 0) {
-        // ---- TMA producer: per row, the three shifted dZ copies, then the A tiles ----
+        // ---- TMA producer: per row pair, the six shifted dZ copies, then the 12 x rows ----
         uint32_t qa = 0, qb = 0;  // A / B stage sequence numbers
         bool ok = true;
         for (int64_t r = r0; r < r1 && ok; ++r) {
@@ -1189,16 +1197,17 @@ __global__ void __launch_bounds__(256, 1)
                 // parallel), after lane 0 has posted the stage's byte count
                 if (lane == 0) tp_expect_tx(bar(BL + st), C::B_STAGE);
                 __syncwarp();
-                if (lane < 3) {
-                    // copy dxi holds dZ[(x' - dx) mod 64], dx = dxi - 1: a box starting at voxel -dx
-                    // (dx = +1: voxel 0 out of range; dx = -1: voxel 63 out of range)
-                    const int dxi = lane;
-                    tp_tma5(b_s + (uint32_t)(st * C::B_STAGE + dxi * C::COLB), &zmap, 0, 1 - dxi, y, z, b, bar(BL + st));
+                if (lane < 6) {
+                    // copy dxi of row y + j holds dZ[(x' - dx) mod 64], dx = dxi - 1: a box starting at
+                    // voxel -dx (dx = +1: voxel 0 out of range; dx = -1: voxel 63 out of range)
+                    const int j = lane / 3, dxi = lane % 3;
+                    tp_tma5(b_s + (uint32_t)(st * C::B_STAGE + (3 * j + dxi) * C::COLB), &zmap, 0, 1 - dxi, y + j, z,
+                            b, bar(BL + st));
                 }
                 __syncwarp();
                 ++qb;
             }
-            for (int t = 0; t < C::NT; ++t, ++qa) {
+            {
                 const int st = (int)(qa % C::SA);
                 const uint32_t use = qa / C::SA;
                 if (!__all_sync(0xffffffffu, tc_wait(bar(AE + st), (use & 1) ^ 1, wait_limit))) {
@@ -1206,16 +1215,16 @@ __global__ void __launch_bounds__(256, 1)
                     ok = false;
                     break;
                 }
-                // columns g0 .. g0 + ng - 1 of the 9 (dz, dy) rows, p = 3 (dz + 1) + (dy + 1)
-                const int g0 = C::PER_TILE * t, ng = min(C::PER_TILE, 9 - g0);
-                if (lane == 0) tp_expect_tx(bar(AF + st), (uint32_t)(ng * C::COLA));
+                // position p = 3 (dy' + 1) + (dz + 1) holds the x row (z + dz, y + dy'), dy' = -1 .. 2
+                if (lane == 0) tp_expect_tx(bar(AF + st), (uint32_t)(C::NLOAD * C::COLA));
                 __syncwarp();
-                if (lane < ng) {
-                    const int p = g0 + lane, dz = p / 3 - 1, dy = p % 3 - 1;
+                if (lane < C::NLOAD) {
+                    const int dy = lane / 3 - 1, dz = lane % 3 - 1;
                     tp_tma5(a_s + (uint32_t)(st * C::A_STAGE + lane * C::COLA), &xmap, 0, 0, wrapi(y + dy, s.ny),
                             wrapi(z + dz, s.nz), b, bar(AF + st));
                 }
                 __syncwarp();
+                ++qa;
             }
         }
         // the CTA must not exit with boxes still landing: wait for the last use of every stage
@@ -1232,12 +1241,12 @@ __global__ void __launch_bounds__(256, 1)
                 fail();
         }
     } else if (warp == 2) {
-        // ---- wrap-voxel fixer: per row, lane l < 2 cout/8 writes one 16-byte chunk of a shifted
-        // copy's wrap voxel: side 0 (dx = +1, copy 2) voxel 0 <- dZ[63]; side 1 (dx = -1, copy 0)
-        // voxel 63 <- dZ[0], at its swizzled place ----
+        // ---- wrap-voxel fixer: per row pair, lane l < 4 cout/8 writes one 16-byte chunk of a
+        // shifted copy's wrap voxel of row y + j: side 0 (dx = +1, copy 2) voxel 0 <- dZ[63]; side 1
+        // (dx = -1, copy 0) voxel 63 <- dZ[0], at its swizzled place ----
         constexpr int COG = COUT / 8;
-        const int side = lane / COG, c8 = lane % COG;
-        const bool active = lane < 2 * COG;
+        const int j = lane / (2 * COG), side = (lane / COG) & 1, c8 = lane % COG;
+        const bool active = lane < 4 * COG;
         uint32_t qb = 0;
         for (int64_t r = r0; r < r1; ++r, ++qb) {
             int b, z, y;
@@ -1246,13 +1255,14 @@ __global__ void __launch_bounds__(256, 1)
             uint4 val = make_uint4(0, 0, 0, 0);
             if (active)
                 val = *reinterpret_cast<const uint4*>(
-                    dzg + ((((int64_t)b * s.nz + z) * s.ny + y) * kW + (side ? 0 : kW - 1)) * COUT + 8 * c8);
+                    dzg + ((((int64_t)b * s.nz + z) * s.ny + y + j) * kW + (side ? 0 : kW - 1)) * COUT + 8 * c8);
             if (!__all_sync(0xffffffffu, tc_wait(bar(BL + st), (qb / C::SB) & 1, wait_limit))) {
                 if (lane == 0) fail();
                 break;
             }
             const int v = side ? 63 : 0;
-            const uint32_t dst = b_s + (uint32_t)(st * C::B_STAGE + (side ? 0 : 2) * C::COLB + v * C::RB) +
+            const uint32_t dst = b_s +
+                                 (uint32_t)(st * C::B_STAGE + (3 * j + (side ? 0 : 2)) * C::COLB + v * C::RB) +
                                  16u * swz_chunk<C::RB>(v, c8);
             if (active)
                 asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(val.x), "r"(val.y), "r"(val.z),
@@ -1273,25 +1283,32 @@ __global__ void __launch_bounds__(256, 1)
                 ok = false;
                 break;
             }
-            const uint64_t bdesc = umma_desc_mn(b_s + (uint32_t)(bst * C::B_STAGE), C::COLB, 8 * C::RB, C::SWB);
-            for (int t = 0; t < C::NT; ++t, ++qa) {
-                const int st = (int)(qa % C::SA);
-                if (!__all_sync(0xffffffffu, tc_wait(bar(AF + st), (qa / C::SA) & 1, wait_limit))) {
-                    if (lane == 0) fail();
-                    ok = false;
-                    break;
-                }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint64_t adesc = umma_desc_mn(a_s + (uint32_t)(st * C::A_STAGE), C::COLA, 8 * C::RA, C::SWA);
-                const uint32_t d_tmem = tmem + (uint32_t)(t * C::NS);
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk)  // 16 voxels per MMA: start address + 16 rows
-                    tc_mma_elect(d_tmem, adesc + (uint64_t)((16 * C::RA * kk) >> 4),
-                                 bdesc + (uint64_t)((16 * C::RB * kk) >> 4), C::IDESC, (first && kk == 0) ? 0u : 1u);
-                tc_commit_elect(bar(AE + st));
+            const int st = (int)(qa % C::SA);
+            if (!__all_sync(0xffffffffu, tc_wait(bar(AF + st), (qa / C::SA) & 1, wait_limit))) {
+                if (lane == 0) fail();
+                ok = false;
+                break;
             }
-            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int j = 0; j < 2; ++j) {
+                // row y + j: its three shifted dZ copies, and the window of x rows starting at position 3 j
+                const uint64_t bdesc =
+                    umma_desc_mn(b_s + (uint32_t)(bst * C::B_STAGE + 3 * j * C::COLB), C::COLB, 8 * C::RB, C::SWB);
+                for (int t = 0; t < C::NT; ++t) {
+                    const uint64_t adesc = umma_desc_mn(
+                        a_s + (uint32_t)(st * C::A_STAGE + (3 * j + C::PER_TILE * t) * C::COLA), C::COLA, 8 * C::RA,
+                        C::SWA);
+                    const uint32_t d_tmem = tmem + (uint32_t)(t * C::NS);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)  // 16 voxels per MMA: start address + 16 rows
+                        tc_mma_elect(d_tmem, adesc + (uint64_t)((16 * C::RA * kk) >> 4),
+                                     bdesc + (uint64_t)((16 * C::RB * kk) >> 4), C::IDESC,
+                                     (first && j == 0 && kk == 0) ? 0u : 1u);
+                }
+            }
+            tc_commit_elect(bar(AE + st));
             tc_commit_elect(bar(BE + bst));
+            ++qa;
             ++qb;
             first = false;
         }
@@ -1309,10 +1326,11 @@ __global__ void __launch_bounds__(256, 1)
             float* out = partials + (int64_t)blockIdx.x * 27 * COUT * CIN;
             const int m = 32 * q + lane;
             for (int t = 0; t < C::NT; ++t) {
-                // row m of tile t: column p = PER_TILE t + m / cin (the (dz, dy) row), channel m % cin
+                // row m of tile t: window position p = PER_TILE t + m / cin = 3 (dy + 1) + (dz + 1),
+                // channel m % cin
                 const int p = C::PER_TILE * t + m / CIN, ci = m % CIN;
                 const bool real = p < 9;
-                const int dz = p / 3 - 1, dy = p % 3 - 1;
+                const int dy = p / 3 - 1, dz = p % 3 - 1;
 #pragma unroll
                 for (int n0 = 0; n0 < C::N; n0 += 16) {
                     float v[16];
@@ -1438,8 +1456,8 @@ static int wgrad_tc_ctas(sg_shape s) {
         dev_seen = dev;
     }
     int64_t n = sms < kWgMaxCtas ? sms : kWgMaxCtas;
-    const int64_t rows = (int64_t)s.batch * s.nz * s.ny;
-    if (n > rows) n = rows;
+    const int64_t pairs = (int64_t)s.batch * s.nz * (s.ny / 2);
+    if (n > pairs) n = pairs;
     return (int)n;
 }
 
