@@ -1139,7 +1139,8 @@ __device__ __forceinline__ uint32_t swz_chunk(int v, int c) {
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(256, 1)
     k_conv_wgrad_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap zmap, sg_shape s,
-                    const bf16* __restrict__ dzg, float* __restrict__ partials, long long wait_limit) {
+                    const bf16* __restrict__ dzg, float* __restrict__ partials, float* __restrict__ bias_part,
+                    long long wait_limit) {
     using C = WgCfg<CIN, COUT>;
     extern __shared__ __align__(1024) unsigned char sm_wg[];
     // barriers: A full, A empty [SA]; B landed, B full, B empty [SB]; done
@@ -1158,7 +1159,10 @@ __global__ void __launch_bounds__(256, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int k = 0; k <= DN; ++k) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(k)));
+        // a B stage is empty once the MMAs have read it and, with a bias gradient, the fixer has summed it
+        for (int k = 0; k <= DN; ++k)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(k)),
+                         "r"(k >= BE && k < BE + C::SB && bias_part ? 2 : 1));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -1247,6 +1251,7 @@ __global__ void __launch_bounds__(256, 1)
         constexpr int COG = COUT / 8;
         const int j = lane / (2 * COG), side = (lane / COG) & 1, c8 = lane % COG;
         const bool active = lane < 4 * COG;
+        float bsum = 0.f;
         uint32_t qb = 0;
         for (int64_t r = r0; r < r1; ++r, ++qb) {
             int b, z, y;
@@ -1271,7 +1276,27 @@ __global__ void __launch_bounds__(256, 1)
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) tp_arrive(bar(BF + st));
+            if (bias_part) {
+                // bias gradient: lane co adds dZ[x][co] of the pair's unshifted copies (copy 1), x in order
+                if (lane < COUT) {
+#pragma unroll 1
+                    for (int jj = 0; jj < 2; ++jj) {
+                        const uint32_t cb = b_s + (uint32_t)(st * C::B_STAGE + (3 * jj + 1) * C::COLB);
+#pragma unroll 8
+                        for (int x = 0; x < kW; ++x) {
+                            unsigned short hv;
+                            const uint32_t a = cb + (uint32_t)(x * C::RB) + 16u * swz_chunk<C::RB>(x, lane >> 3) +
+                                               2u * (uint32_t)(lane & 7);
+                            asm volatile("ld.shared.u16 %0, [%1];" : "=h"(hv) : "r"(a));
+                            bsum += __bfloat162float(__ushort_as_bfloat16(hv));
+                        }
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) tp_arrive(bar(BE + st));
+            }
         }
+        if (bias_part && lane < COUT) bias_part[(int64_t)blockIdx.x * COUT + lane] = bsum;
     } else if (warp == 1) {
         // ---- MMA issuer ----
         uint32_t qa = 0, qb = 0;
@@ -1462,7 +1487,8 @@ static int wgrad_tc_ctas(sg_shape s) {
 }
 
 template <int CIN, int COUT>
-static int launch_wgrad_tc(sg_shape s, const void* x, const void* dz, float* partials, int ctas, cudaStream_t st) {
+static int launch_wgrad_tc(sg_shape s, const void* x, const void* dz, float* partials, float* bias_part, int ctas,
+                           cudaStream_t st) {
     using C = WgCfg<CIN, COUT>;
     static int configured = -1;
     int dev = 0;
@@ -1492,6 +1518,7 @@ static int launch_wgrad_tc(sg_shape s, const void* x, const void* dz, float* par
     if (!enc(&xm, x, CIN) || !enc(&zm, dz, COUT)) return -3;
     const long long wait_limit = 2000000000LL;  // ~1 s of SM clock per wait
     k_conv_wgrad_tc<CIN, COUT><<<ctas, C::THREADS, C::SMEM, st>>>(xm, zm, s, static_cast<const bf16*>(dz), partials,
+                                                                   bias_part,
                                                                    wait_limit);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
@@ -1509,26 +1536,28 @@ template <int CIN, int COUT>
 static int launch_wgrad(sg_shape s, const void* x, const void* dz, float* dw, float* db, void* scratch,
                         cudaStream_t st) {
     float* partials = static_cast<float*>(scratch);
-    int parts;
+    // bias partials after the largest weight-gradient partials either kernel writes
+    float* bias_part = db ? partials + wgrad_parts_max(s) * 27 * CIN * COUT : nullptr;
+    int parts, bias_parts = kBiasBlocks;
     if (g_fwd_impl == SG_CONV_TCGEN05) {
+        // the tcgen05 kernel also sums the bias gradient, one partial per CTA
         parts = wgrad_tc_ctas(s);
         if (parts < 1) return -3;
-        const int rc = launch_wgrad_tc<CIN, COUT>(s, x, dz, partials, parts, st);
+        const int rc = launch_wgrad_tc<CIN, COUT>(s, x, dz, partials, bias_part, parts, st);
         if (rc) return rc;
+        bias_parts = parts;
     } else {
         parts = parts_for(s);
         k_conv_wgrad<CIN, COUT><<<dim3(27, parts), kWgThreads, 0, st>>>(s, static_cast<const bf16*>(x),
                                                                          static_cast<const bf16*>(dz), partials, parts);
+        if (db) {
+            const int64_t voxels = (int64_t)s.batch * s.nz * s.ny * s.nx;
+            k_bias_partials<<<kBiasBlocks, 256, 0, st>>>(voxels, COUT, static_cast<const bf16*>(dz), bias_part);
+        }
     }
     const int n = 27 * CIN * COUT;
     k_wgrad_reduce<<<(n + 31) / 32, 256, 0, st>>>(CIN, COUT, parts, partials, dw);
-    if (db) {
-        // bias partials after the largest weight-gradient partials either kernel writes
-        float* bias_part = partials + wgrad_parts_max(s) * 27 * CIN * COUT;
-        const int64_t voxels = (int64_t)s.batch * s.nz * s.ny * s.nx;
-        k_bias_partials<<<kBiasBlocks, 256, 0, st>>>(voxels, COUT, static_cast<const bf16*>(dz), bias_part);
-        k_bias_finish<<<1, 32 * COUT, 0, st>>>(kBiasBlocks, COUT, bias_part, db);
-    }
+    if (db) k_bias_finish<<<1, 32 * COUT, 0, st>>>(bias_parts, COUT, bias_part, db);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
