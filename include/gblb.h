@@ -143,6 +143,35 @@ lb_status lb_get_moments(lb_ctx *ctx, double *rho, double *u, double *theta, int
 /* Global sums in FP64, deterministic order: out[0] = mass sum <f,1>,
  * out[1..3] = momentum sum <f,c>, out[4] = energy sum <f,c^2/2>.  out is host memory. */
 lb_status lb_conserved(lb_ctx *ctx, double out[5]);
+/* The same sums over the planes z0 <= z < z1 of both sub-lattices (a z slab's
+ * interior); LB_ERR_ARG unless 0 <= z0 < z1 <= nz. */
+lb_status lb_conserved_planes(lb_ctx *ctx, int64_t z0, int64_t z1, double out[5]);
+
+/* z-slab decomposition over ranks (one process per GPU), the host side of
+ * which is paper_1909_08406_gb300/decomp.py.  Rank r's context holds its slab
+ * of nz_r planes plus LB_HALO planes below and above (lb_init with
+ * nz = nz_r + 2 LB_HALO, nz_r >= LB_HALO), and the ordinary periodic update
+ * steps it: its wrap touches only halo planes.  Before each step the halo
+ * planes are refreshed from the neighbouring ranks' interiors, after which the
+ * slab's interior update is identical to that of the whole grid.  An interior
+ * node pulls population i from at most ceil(|c_iz|) cells away, so the halo
+ * plane at distance d from the interior is read only through the populations
+ * whose c_z points into the slab and for which (|2 c_z| + 1) / 2 >= d; only
+ * those are sent (15 of the 82 plane-populations of each direction).
+ * Messages are device buffers of lb_halo_bytes bytes, laid out
+ * [entry][s][y][x] in the storage type, entries ordered by distance d = 1, 2,
+ * then population index:
+ *   lb_halo_pack(ctx, 1, buf)    the top interior planes, for rank + 1's lower halo
+ *   lb_halo_pack(ctx, 0, buf)    the bottom interior planes, for rank - 1's upper halo
+ *   lb_halo_unpack(ctx, 0, buf)  the lower halo, from rank - 1's pack of side 1
+ *   lb_halo_unpack(ctx, 1, buf)  the upper halo, from rank + 1's pack of side 0
+ * Both are enqueued on the context's stream (lb_set_stream) and return
+ * without waiting.  LB_ERR_ARG for nz < 3 LB_HALO, a side other than 0 or 1,
+ * or a buffer that is not device memory. */
+#define LB_HALO 2
+lb_status lb_halo_bytes(lb_ctx *ctx, int64_t *bytes);
+lb_status lb_halo_pack(lb_ctx *ctx, int side, void *buf);
+lb_status lb_halo_unpack(lb_ctx *ctx, int side, const void *buf);
 
 /* The global sums of lb_conserved, for callers that cannot allocate device
  * memory (code running under a memory budget owned by another allocator, or

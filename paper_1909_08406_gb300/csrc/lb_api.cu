@@ -167,6 +167,16 @@ static const void* mapped_host_view(const void* p) {
     return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
 }
 
+// True for device memory (or managed memory) the kernels can write.
+static bool is_device_pointer(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
 // Staging buffer for host transfers (float64), allocated on first use.
 static lb_status ensure_stage(lb_ctx* c) {
     if (c->d_stage) return LB_OK;
@@ -463,6 +473,88 @@ lb_status lb_conserved(lb_ctx* c, double out[5]) {
     out[3] = s[3];
     out[4] = 0.5 * (3.0 * lattice().theta0 * n + s[4]);
     return LB_OK;
+}
+
+lb_status lb_conserved_planes(lb_ctx* c, int64_t z0, int64_t z1, double out[5]) {
+    if (!c || !out) return fail(c, LB_ERR_ARG, "lb_conserved_planes: null argument");
+    if (z0 < 0 || z1 > c->d.nz || z0 >= z1) return fail(c, LB_ERR_ARG, "lb_conserved_planes: need 0 <= z0 < z1 <= nz");
+    CK(c, cudaSetDevice(c->device));
+    const LaunchConsts& lc = lattice().lc;
+    CK(c, launch_conserved(c->prec, c->buf[c->cur], c->d, lc, c->d_partials, c->nblocks, c->d_out5, c->stream, z0,
+                           z1 - z0));
+    double s[5];
+    CK(c, cudaMemcpyAsync(s, c->d_out5, sizeof s, cudaMemcpyDeviceToHost, c->stream));
+    lb_status st = lb_sync(c);
+    if (st != LB_OK) return st;
+    const double n = 2.0 * (double)(z1 - z0) * (double)c->d.nx * (double)c->d.ny;
+    out[0] = n + s[0];
+    out[1] = s[1];
+    out[2] = s[2];
+    out[3] = s[3];
+    out[4] = 0.5 * (3.0 * lattice().theta0 * n + s[4]);
+    return LB_OK;
+}
+
+// The (plane, population) entries of one halo message of a padded slab of nzp planes (LB_HALO
+// halo planes at each end).  An interior node pulls population i from ceil(|c_iz|) cells away at
+// most, so the halo plane at distance d from the interior is read only through the populations
+// with c_z pointing into the slab and (|2 c_z| + 1) / 2 >= d.  Entries run d = 1, 2, populations
+// ascending.  pack: the interior planes a neighbour's halo receives (side 0: the bottom ones, for
+// rank - 1's upper halo; side 1: the top ones, for rank + 1's lower halo); unpack: this slab's
+// halo (side 0: lower, from rank - 1; side 1: upper, from rank + 1).
+static HaloList halo_list(int nzp, int side, bool pack) {
+    HaloList L{};
+    L.n = 0;
+    // populations arriving through the lower halo have c_z > 0, through the upper one c_z < 0
+    const bool up = pack ? side == 1 : side == 0;
+    for (int dist = 1; dist <= LB_HALO; ++dist) {
+        int plane;
+        if (pack)
+            plane = side == 1 ? nzp - LB_HALO - dist : LB_HALO + dist - 1;
+        else
+            plane = side == 0 ? LB_HALO - dist : nzp - LB_HALO + dist - 1;
+        for (int i = 0; i < kQ; ++i) {
+            const int cz2 = vel(i).z;
+            const int reach = ((cz2 < 0 ? -cz2 : cz2) + 1) / 2;
+            if ((up ? cz2 > 0 : cz2 < 0) && reach >= dist) {
+                L.plane[L.n] = plane;
+                L.pop[L.n] = i;
+                ++L.n;
+            }
+        }
+    }
+    return L;
+}
+
+static bool halo_ok(lb_ctx* c, const char* who) {
+    if (c->d.nz < 3 * LB_HALO) {
+        fail(c, LB_ERR_ARG, std::string(who) + ": a padded slab has at least 3 LB_HALO planes");
+        return false;
+    }
+    return true;
+}
+
+lb_status lb_halo_bytes(lb_ctx* c, int64_t* bytes) {
+    if (!c || !bytes) return fail(c, LB_ERR_ARG, "lb_halo_bytes: null argument");
+    if (!halo_ok(c, "lb_halo_bytes")) return LB_ERR_ARG;
+    const HaloList L = halo_list(c->d.nz, 0, true);
+    *bytes = (int64_t)L.n * 2 * c->d.nx * c->d.ny * (int64_t)c->esize;
+    return LB_OK;
+}
+
+static lb_status halo_copy(lb_ctx* c, int side, void* buf, bool pack, const char* who) {
+    if (!c || !buf || (side != 0 && side != 1)) return fail(c, LB_ERR_ARG, std::string(who) + ": bad argument");
+    if (!halo_ok(c, who)) return LB_ERR_ARG;
+    if (!is_device_pointer(buf)) return fail(c, LB_ERR_ARG, std::string(who) + ": the buffer must be device memory");
+    CK(c, cudaSetDevice(c->device));
+    CK(c, launch_halo_copy(c->prec, c->buf[c->cur], c->d, halo_list(c->d.nz, side, pack), buf, pack, c->stream));
+    return LB_OK;
+}
+
+lb_status lb_halo_pack(lb_ctx* c, int side, void* buf) { return halo_copy(c, side, buf, true, "lb_halo_pack"); }
+
+lb_status lb_halo_unpack(lb_ctx* c, int side, const void* buf) {
+    return halo_copy(c, side, const_cast<void*>(buf), false, "lb_halo_unpack");
 }
 
 lb_status lb_get_populations(lb_ctx* c, double* f, int on_device) {

@@ -98,15 +98,47 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_partials(const double* _
 }
 
 cudaError_t launch_conserved(int prec, const void* src, const Dims& d, const LaunchConsts& c, double* partials,
-                             int nblocks, double* out5, cudaStream_t st) {
+                             int nblocks, double* out5, cudaStream_t st, int64_t z0, int64_t nzr) {
+    if (nzr < 0) nzr = d.nz;
     cudaError_t e = dispatch(prec, [&](auto codec) {
         using C = decltype(codec);
         using T = typename C::raw_t;
-        k_conserved<C><<<nblocks, kRedThreads, 0, st>>>(static_cast<const T*>(src), d, consts_for<C>(c), partials);
+        k_conserved<C><<<nblocks, kRedThreads, 0, st>>>(static_cast<const T*>(src), d, consts_for<C>(c), partials, z0,
+                                                         nzr);
         return cudaGetLastError();
     });
     if (e != cudaSuccess) return e;
     k_reduce_partials<<<1, kRedThreads, 0, st>>>(partials, nblocks, out5);
+    return cudaGetLastError();
+}
+
+// blockIdx.y = entry k of the list, blockIdx.z = sub-lattice s, x over the plane's ny nx elements.
+template <class T>
+__global__ void __launch_bounds__(256) k_halo_copy(T* __restrict__ f, Dims d, HaloList list, T* __restrict__ buf,
+                                                   int pack) {
+    const int k = blockIdx.y, s = blockIdx.z;
+    const int64_t nxy = (int64_t)d.nx * d.ny;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nxy) return;
+    T* a = f + ((int64_t)s * kQ + list.pop[k]) * d.plane + (int64_t)list.plane[k] * nxy + e;
+    T* b = buf + ((int64_t)k * 2 + s) * nxy + e;
+    if (pack)
+        *b = *a;
+    else
+        *a = *b;
+}
+
+cudaError_t launch_halo_copy(int prec, void* f, const Dims& d, const HaloList& list, void* buf, bool pack,
+                             cudaStream_t st) {
+    if (list.n <= 0) return cudaSuccess;
+    const int64_t nxy = (int64_t)d.nx * d.ny;
+    const dim3 grid(blocks_for(nxy, 256), (unsigned)list.n, 2);
+    switch (storage_bytes(prec)) {
+        case 8: k_halo_copy<uint64_t><<<grid, 256, 0, st>>>(static_cast<uint64_t*>(f), d, list, static_cast<uint64_t*>(buf), pack); break;
+        case 4: k_halo_copy<uint32_t><<<grid, 256, 0, st>>>(static_cast<uint32_t*>(f), d, list, static_cast<uint32_t*>(buf), pack); break;
+        case 2: k_halo_copy<uint16_t><<<grid, 256, 0, st>>>(static_cast<uint16_t*>(f), d, list, static_cast<uint16_t*>(buf), pack); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

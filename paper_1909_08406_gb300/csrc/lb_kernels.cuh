@@ -481,12 +481,19 @@ constexpr int kRedThreads = 256;
 // fixed order (grid-stride loop, then a shared-memory tree): deterministic
 // for a given grid size.
 template <class Codec>
+// Over the planes [z0, z0 + nzr) of both sub-lattices (all of them: z0 = 0, nzr = nz).
 __global__ void __launch_bounds__(kRedThreads) k_conserved(const typename Codec::raw_t* __restrict__ src, Dims d,
-                                                           Consts<typename Codec::R> K, double* __restrict__ partials) {
+                                                           Consts<typename Codec::R> K, double* __restrict__ partials,
+                                                           int64_t z0, int64_t nzr) {
     using R = typename Codec::R;
     double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    const int64_t n = 2 * d.plane;
-    for (int64_t q = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; q < n; q += (int64_t)gridDim.x * kRedThreads) {
+    const int64_t nxy = (int64_t)d.nx * d.ny, span = nzr * nxy, n = 2 * span;
+    for (int64_t j = (int64_t)blockIdx.x * kRedThreads + threadIdx.x; j < n; j += (int64_t)gridDim.x * kRedThreads) {
+        int64_t q = j;
+        if (nzr != d.nz) {
+            const int64_t s = j / span;
+            q = s * d.plane + z0 * nxy + (j - s * span);
+        }
         const NodeMoments<R> m = node_moments_at<Codec>(src, d, q, K);
         acc[0] += (double)m.drho;
         acc[1] += (double)m.jx;

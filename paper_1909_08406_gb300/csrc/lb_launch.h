@@ -62,7 +62,18 @@ cudaError_t launch_moments(int prec, const void* src, const Dims& d, const Launc
 
 // Global FP64 sums (drho, jx, jy, jz, dk) -> out5 (device), via nblocks partials.
 cudaError_t launch_conserved(int prec, const void* src, const Dims& d, const LaunchConsts& c, double* partials,
-                             int nblocks, double* out5, cudaStream_t st);
+                             int nblocks, double* out5, cudaStream_t st, int64_t z0 = 0, int64_t nzr = -1);
+
+// Halo planes of a z slab: copy, for each of n (plane, population) entries, both sub-lattices' ny nx
+// elements of that population on that plane between the population array and a packed buffer
+// [entry][s][y][x] (pack: array -> buffer; else buffer -> array).
+struct HaloList {
+    int n;
+    int plane[2 * kQ];
+    int pop[2 * kQ];
+};
+cudaError_t launch_halo_copy(int prec, void* f, const Dims& d, const HaloList& list, void* buf, bool pack,
+                             cudaStream_t st);
 
 // Raw storage <-> float64 populations for elements [e0, e0 + count).
 cudaError_t launch_to_f64(int prec, const void* src, const Dims& d, const LaunchConsts& c, int64_t e0, int64_t count,

@@ -19,7 +19,10 @@ Two splits of the periodic bcc grid are described here.
 
 The functions take array-like tensors in the population layout
 ``f[s][i][z][y][x]`` and a ``torch.distributed`` process group; with NCCL they
-move device tensors, with gloo host tensors.
+move device tensors, with gloo host tensors.  ``exchange_halos_lb`` does the
+same exchange on a library context holding the padded slab, with the
+library's packed halo messages (lb_halo_pack / lb_halo_unpack) in device
+memory.
 """
 from __future__ import annotations
 
@@ -125,6 +128,52 @@ def exchange_halos(f_padded, group=None, halo: int = HALO, cz2=None):
     unpack(lo_recv, lo_dst)
     unpack(hi_recv, hi_dst)
     return f_padded
+
+
+def exchange_halos_lb(ctx, bufs, group=None):
+    """The exchange of ``exchange_halos`` on a library context that holds this rank's padded slab
+    (lb_init with nz = nz_r + 2 HALO): the library packs the populations an interior node reads
+    from each halo plane into device buffers and unpacks the received ones (lb_halo_pack,
+    lb_halo_unpack); the ranks swap them by NCCL point-to-point.  ``bufs`` = four uint8 device
+    tensors of ``lb.lb_halo_bytes(ctx)`` bytes (top and bottom to send, lower and upper to
+    receive), reused from step to step.  With one rank the slab is its own neighbour."""
+    import torch.distributed as dist
+    from . import lb
+    send_up, send_down, recv_low, recv_high = bufs
+    lb.lb_halo_pack(ctx, 1, send_up)
+    lb.lb_halo_pack(ctx, 0, send_down)
+    world = dist.get_world_size(group) if dist.is_initialized() else 1
+    if world == 1:
+        lb.lb_halo_unpack(ctx, 0, send_up)
+        lb.lb_halo_unpack(ctx, 1, send_down)
+        return
+    lb.lb_sync(ctx)  # the packed messages are complete before the communicator reads them
+    rank = dist.get_rank(group)
+    down, up = (rank - 1) % world, (rank + 1) % world
+    ops = [dist.P2POp(dist.isend, send_up, up, group, 0), dist.P2POp(dist.isend, send_down, down, group, 1),
+           dist.P2POp(dist.irecv, recv_low, down, group, 0), dist.P2POp(dist.irecv, recv_high, up, group, 1)]
+    for r in dist.batch_isend_irecv(ops):
+        r.wait()
+    lb.lb_halo_unpack(ctx, 0, recv_low)
+    lb.lb_halo_unpack(ctx, 1, recv_high)
+
+
+def exchange_halos_lb_local(ctxs, bufs):
+    """The same exchange among slabs held by one process, in rank order around the ring (used to
+    check the library's slab path on one device): rank r's top interior goes to rank r + 1's
+    lower halo, its bottom interior to rank r - 1's upper halo.  ``bufs[r]`` as above."""
+    from . import lb
+    n = len(ctxs)
+    for r in range(n):  # earlier unpacks from the buffers are complete before they are refilled
+        lb.lb_sync(ctxs[r])
+    for r in range(n):
+        lb.lb_halo_pack(ctxs[r], 1, bufs[r][0])
+        lb.lb_halo_pack(ctxs[r], 0, bufs[r][1])
+    for r in range(n):
+        lb.lb_sync(ctxs[r])
+    for r in range(n):
+        lb.lb_halo_unpack(ctxs[r], 0, bufs[(r - 1) % n][0])
+        lb.lb_halo_unpack(ctxs[r], 1, bufs[(r + 1) % n][1])
 
 
 def allreduce_sum_f64(values, group=None, device="cpu"):

@@ -28,6 +28,7 @@ LB_FLAG_STAGED = 2
 LB_FLAG_ENTROPIC = 4
 LB_KERNEL_AUTO, LB_KERNEL_DIRECT1, LB_KERNEL_DIRECT2, LB_KERNEL_DIRECT2R, LB_KERNEL_STAGED, LB_KERNEL_WARPSPEC = -1, 0, 1, 2, 3, 4
 LB_KERNEL_DIRECT2X, LB_KERNEL_DIRECT2XL = 5, 6
+LB_HALO = 2  # halo planes at each end of a padded z slab (lb_halo_pack)
 KERNEL_NAMES = {0: "k_step (direct, 1 node/thread)", 1: "k_step2 (direct, 2 rows/thread, FP32x2)",
                 2: "k_step2 (direct, 2 rows/thread, FP32x2, 4 CTAs/SM)", 3: "k_step_tma (TMA-staged)",
                 4: "k_step_ws (TMA-staged, warp-specialised, FP32x2)",
@@ -87,6 +88,14 @@ def lib():
         L.lb_set_wall_columns.restype = ctypes.c_int
         L.lb_get_grid.argtypes = [vp, ctypes.POINTER(_Grid)]
         L.lb_get_grid.restype = ctypes.c_int
+        L.lb_conserved_planes.argtypes = [vp, i64, i64, ctypes.POINTER(ctypes.c_double)]
+        L.lb_conserved_planes.restype = ctypes.c_int
+        L.lb_halo_bytes.argtypes = [vp, ctypes.POINTER(i64)]
+        L.lb_halo_bytes.restype = ctypes.c_int
+        L.lb_halo_pack.argtypes = [vp, ctypes.c_int, vp]
+        L.lb_halo_pack.restype = ctypes.c_int
+        L.lb_halo_unpack.argtypes = [vp, ctypes.c_int, vp]
+        L.lb_halo_unpack.restype = ctypes.c_int
         L.lb_set_stochastic_rounding.argtypes = [vp, ctypes.c_int, ctypes.c_uint64]
         L.lb_set_stochastic_rounding.restype = ctypes.c_int
         L.lb_set_nonideal.argtypes = [vp, ctypes.c_int, dp, dp, dp, dp]
@@ -261,6 +270,38 @@ def lb_set_nonideal(ctx, a=None, b=None, kappa=0.0, eta=0.5, eos="vdw"):
         return
     kind = LB_EOS[eos] if isinstance(eos, str) else int(eos)
     _check(lib().lb_set_nonideal(ctx, kind, float(a), float(b), float(kappa), float(eta)), ctx)
+
+
+def lb_conserved_planes(ctx, z0, z1):
+    """lb_conserved over the planes z0 <= z < z1 of both sub-lattices (a slab's interior)."""
+    out = (ctypes.c_double * 5)()
+    _check(lib().lb_conserved_planes(ctx, int(z0), int(z1), out), ctx)
+    return [out[k] for k in range(5)]
+
+
+def lb_halo_bytes(ctx):
+    """Bytes of one halo message of a padded z slab (see gblb.h)."""
+    n = ctypes.c_int64()
+    _check(lib().lb_halo_bytes(ctx, ctypes.byref(n)), ctx)
+    return int(n.value)
+
+
+def lb_halo_pack(ctx, side, buf):
+    """Interior planes for a neighbour's halo into the device tensor buf (side 1: the top ones,
+    for rank + 1; side 0: the bottom ones, for rank - 1)."""
+    p, dev = _ptr(buf, writable=True)
+    if not dev or buf.numel() * buf.element_size() < lb_halo_bytes(ctx):
+        raise ValueError("lb_halo_pack: buf must be a device tensor of lb_halo_bytes bytes")
+    _check(lib().lb_halo_pack(ctx, int(side), p), ctx)
+
+
+def lb_halo_unpack(ctx, side, buf):
+    """This slab's halo from the device tensor buf (side 0: lower, from rank - 1; side 1: upper,
+    from rank + 1)."""
+    p, dev = _ptr(buf)
+    if not dev or buf.numel() * buf.element_size() < lb_halo_bytes(ctx):
+        raise ValueError("lb_halo_unpack: buf must be a device tensor of lb_halo_bytes bytes")
+    _check(lib().lb_halo_unpack(ctx, int(side), p), ctx)
 
 
 def lb_set_stochastic_rounding(ctx, seed=None):
