@@ -63,9 +63,9 @@ def test_conv_forward_f32_with_add(impl):
     assert torch.allclose(y.cpu().to(F64), ref, rtol=1e-5, atol=1e-5)
 
 
-# tcgen05 kernel: (2, 4, 8, 64) one row per CTA (64 rows), rows wrapping in y and z;
-# (3, 5, 12, 64) 180 rows over at most 152 CTAs (one or two rows each), odd nz;
-# (4, 6, 64, 64) ten rows per CTA (accumulation over rows, both operand rings wrapping)
+# tcgen05 kernel (rows in pairs): (2, 4, 8, 64) one pair per CTA (32 pairs), windows wrapping in y
+# and z; (3, 5, 12, 64) 90 pairs, one per CTA, odd nz; (4, 6, 64, 64) 768 pairs over at most 152
+# CTAs, five or six each (accumulation over pairs, both operand rings wrapping)
 @pytest.mark.parametrize("cin,cout", [(16, 32), (32, 32), (32, 16), (16, 16)])
 @pytest.mark.parametrize("shape", [(2, 4, 8, 64), (3, 5, 12, 64), (4, 6, 64, 64)])
 def test_weight_and_bias_gradient_matches_oracle(cin, cout, shape, impl):
