@@ -211,3 +211,22 @@ def test_persistent_barrier_timeout_is_reported_not_hung():
     # a fresh batch still runs normally
     out = _run("f32", lb.LB_BATCH_PERSISTENT, 2)
     assert all(np.isfinite(f).all() for f in out)
+
+
+def test_batch_refuses_members_with_the_nonideal_mode_or_stochastic_rounding():
+    """A batched step runs the energy-conserving update with the round-to-nearest store only: a
+    member in the nonideal mode or with the stochastic BF16 store is refused before any launch."""
+    for setup in ("nonideal", "stochastic"):
+        prec = "bf16" if setup == "stochastic" else "f32"
+        b = lb.lb_batch_init([(4, 4, 4), (4, 4, 6)], [0.3, 0.4], prec)
+        try:
+            sim = lb.lb_batch_sim(b, 1)
+            if setup == "nonideal":
+                lb.lb_set_nonideal(sim, 0.1, 0.3)
+            else:
+                lb.lb_set_stochastic_rounding(sim, 1)
+            with pytest.raises(lb.LbError) as e:
+                lb.lb_batch_step(b, 1)
+            assert e.value.status == -7  # LB_ERR_STATE
+        finally:
+            lb.lb_batch_destroy(b)
