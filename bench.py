@@ -51,6 +51,9 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=512)
     p.add_argument("--precision", default="f16", choices=list(BYTES))
+    p.add_argument("--stochastic", action="store_true",
+                   help="with --precision bf16: the stochastic BF16 store (lb_set_stochastic_rounding) in the "
+                        "timed runs of that precision")
     p.add_argument("--no-secondary", action="store_true", help="skip the other storage precisions")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -343,11 +346,16 @@ def workload_config(args, world):
     """The `config` of both arms' JSON lines: the workload the main arm times."""
     n = args.n
     nodes = 2 * n ** 3
-    return {"workload": f"thermoacoustic pulse, {n}^3 periodic bcc grid ({nodes} nodes), nu = {NU}, "
-                        f"{args.precision} storage", "grid": n, "nodes": nodes, "precision": args.precision,
-            "l2": "inputs larger than L2 (population buffers of "
-                  f"{nodes * 41 * BYTES[args.precision] / 1e9:.1f} GB each)",
-            "parallelism": f"replicas x{world}"}
+    sr = getattr(args, "stochastic", False) and args.precision == "bf16"
+    cfg = {"workload": f"thermoacoustic pulse, {n}^3 periodic bcc grid ({nodes} nodes), nu = {NU}, "
+                       f"{args.precision} storage" + (", stochastic rounding" if sr else ""),
+           "grid": n, "nodes": nodes, "precision": args.precision,
+           "l2": "inputs larger than L2 (population buffers of "
+                 f"{nodes * 41 * BYTES[args.precision] / 1e9:.1f} GB each)",
+           "parallelism": f"replicas x{world}"}
+    if sr:
+        cfg["rounding"] = "stochastic"
+    return cfg
 
 
 def run_reference(args, rank, world):
@@ -444,6 +452,8 @@ def main():
             if nonideal:  # van der Waals at theta0 / theta_c = 1.1 (one phase), rho_c = 1
                 theta_c = th0 / 1.1
                 lb.lb_set_nonideal(ctx, 27.0 / 3.0 * theta_c / 8.0, 1.0 / 3.0, 0.05, 0.5)
+            elif args.stochastic and prec == "bf16" and not walls:
+                lb.lb_set_stochastic_rounding(ctx, 20191909)
             if kernel is None:
                 lb.lb_tune(ctx, reps=3)
             else:
