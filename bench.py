@@ -594,7 +594,8 @@ def main():
         return
     r = results[args.precision]
     peak, peak_kind = measured_peaks()
-    traffic = ncu_traffic(args.precision, r["kernel_id"], n)
+    traffic = ncu_traffic(args.precision + ("sr" if args.stochastic and args.precision == "bf16" else ""),
+                          r["kernel_id"], n)
     line = {
         "metric": "MLUPS", "value": r["mlups"], "unit": "MLUPS", "n_gpus": world, "steps": r["steps"],
         "warmup": r["warmup"], "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
