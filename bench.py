@@ -34,11 +34,11 @@ BYTES = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}
 DTYPE_NAME = {"f64": "f64", "f32": "f32", "f16": "f32 (f16 storage)", "bf16": "f32 (bf16 storage)"}
 NU = 0.01
 # Field values in the compute type (4 B, FP64 storage 8 B) one nonideal step moves per node: the
-# density pass writes rho, mu, F (3); the field pass reads rho, F and writes grad rho, lap rho,
-# lap F (2 + 5); the force pass reads rho, mu, F, grad rho, lap rho, lap F and writes g (8 + 3);
-# the step reads g (3).  The populations are gathered twice (density pass, step) and written
-# once: 3 x 41 stored values.
-NONIDEAL_FIELD_VALUES = 24
+# density pass writes rho, mu, F (3); the field pass reads them and writes mu, F, lap F, the
+# isotropic part of I_ab and grad rho (3 + 7); the force pass reads those seven and rho and
+# writes g (8 + 3); the step reads g (3).  The populations are gathered twice (density pass,
+# step) and written once: 3 x 41 stored values.
+NONIDEAL_FIELD_VALUES = 27
 STEP_KERNEL_SOURCES = ["lb_common.cuh", "lb_kernels.cuh", "lb_step_tma.cuh", "lb_step_ws.cuh", "lb_step_f32.cu",
                        "lb_step_f64.cu"]
 

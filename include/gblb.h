@@ -348,8 +348,9 @@ lb_status lb_nonideal_constants(int eos, double theta_star, double rho_c, double
  * rho > 0 and finite moments.  An eos outside LB_EOS_* gives LB_ERR_ARG.
  * Needs the projected series equilibrium (no LB_FLAG_PAPER_LITERAL or
  * LB_FLAG_ENTROPIC; LB_ERR_ARG), fewer than 2^31 cells (LB_ERR_ARG), and
- * neither walls nor stochastic rounding (LB_ERR_STATE).  Each step runs four one-node-per-thread kernels; the work
- * buffer is 96 bytes per node.  A batch (lb_batch_step) refuses members with
+ * neither walls nor stochastic rounding (LB_ERR_STATE).  Each step runs four kernels (density,
+ * stencil fields, force, forced step); the work buffer holds 13 field values per node, 104 bytes
+ * with FP64 storage and 52 otherwise.  A batch (lb_batch_step) refuses members with
  * it on (LB_ERR_STATE).  eos = 0 restores the energy-conserving update. */
 lb_status lb_set_nonideal(lb_ctx *ctx, int eos, double a, double b, double kappa, double eta);
 

@@ -794,7 +794,7 @@ lb_status lb_set_nonideal(lb_ctx* c, int enable, double a, double b, double kapp
         return fail(c, LB_ERR_ARG, "lb_set_nonideal: the grid must have fewer than 2^31 cells");
     CK(c, cudaSetDevice(c->device));
     if (!c->d_ni) {
-        cudaError_t e = cudaMalloc(&c->d_ni, sizeof(double) * nonideal_doubles(c->d));
+        cudaError_t e = cudaMalloc(&c->d_ni, sizeof(double) * nonideal_doubles(c->d, c->prec));
         if (e != cudaSuccess) {
             c->d_ni = nullptr;
             return fail(c, e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA,

@@ -15,6 +15,18 @@ struct NiEos {
     int kind;
 };
 
+// The same constants in the field type F, converted once on the host (an FP64-to-FP32 conversion
+// in every thread runs at GB300's FP64 rate).
+template <class F>
+struct NiEosT {
+    F a, b, theta0, kappa, eta;
+    int kind;
+};
+template <class F>
+inline NiEosT<F> ni_eos_in(const NiEos& e) {
+    return NiEosT<F>{(F)e.a, (F)e.b, (F)e.theta0, (F)e.kappa, (F)e.eta, e.kind};
+}
+
 __host__ __device__ __forceinline__ double ni_log(double v) { return log(v); }
 __host__ __device__ __forceinline__ float ni_log(float v) { return logf(v); }
 __host__ __device__ __forceinline__ double ni_log1p(double v) { return log1p(v); }
@@ -36,8 +48,8 @@ __host__ __device__ __forceinline__ void cs_repulsion(F p, F& f, F& rdf) {
 //   Peng-Robinson type  F = theta0 rho f - a rho L,  L = int_0^rho drho' / (1 + 2b rho' - b^2 rho'^2)
 //                         = [ln(1 + (sqrt2 + 1) b rho) - ln(1 - (sqrt2 - 1) b rho)] / (2 sqrt2 b)
 //   Carnahan-Starling   F = theta0 rho f - a rho^2
-template <class F>
-__host__ __device__ __forceinline__ void ni_eos(F r, const NiEos& e, F& mu, F& Fe) {
+template <class F, class E>
+__host__ __device__ __forceinline__ void ni_eos(F r, const E& e, F& mu, F& Fe) {
     const F th = F(e.theta0), a = F(e.a), br = F(e.b) * r;
     if (e.kind == kPengRobinson) {
         F f, rdf;

@@ -107,7 +107,7 @@ cudaError_t launch_wall_step(int prec, int eq, int variant, const void* src, voi
 // Isothermal nonideal fluid (lb_nonideal.cu): doubles of the work buffer for this grid, and
 // one step (density, fields, force, forced step).  kind: 1 van der Waals, 2 Peng-Robinson type,
 // 3 Carnahan-Starling; eos = {a, b, kappa, eta}.
-size_t nonideal_doubles(const Dims& d);
+size_t nonideal_doubles(const Dims& d, int prec);
 cudaError_t launch_nonideal_step(int prec, const void* src, void* dst, const Dims& d, const LaunchConsts& c,
                                  double twobeta, int kind, const double eos[4], double* work, int* err,
                                  cudaStream_t st);

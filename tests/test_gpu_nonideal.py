@@ -81,6 +81,19 @@ def test_nonideal_step_matches_oracle(prec, tol, eos):
     assert rel.max() <= tol, rel.max()
 
 
+@pytest.mark.parametrize("shape", [(13, 4, 6), (260, 2, 3)])
+def test_nonideal_fp32_stencil_paths_match_oracle(shape):
+    """FP32 fields with nx odd (one node per thread) and with a row of 130 x pairs (two blocks of
+    pairs, the second ragged); nx = 12 above runs the x pairs in one block."""
+    steps = 5
+    e, rho = _slab(shape, noise=0.02)
+    got, _, _ = _gpu(shape, "f32", e, rho, steps)
+    f0 = oracle.init_fields(rho, np.zeros((3,) + rho.shape), np.full(rho.shape, TH0))
+    ref = ni.step(f0, 0.5, e, EOS["vdw"][1], nsteps=steps)
+    rel = np.abs(to_oracle_order(got, lib_to_oracle_perm()) - ref) / np.abs(ref)
+    assert rel.max() <= 2e-6, rel.max()
+
+
 @pytest.mark.parametrize("shape", [(12, 4, 6), (13, 4, 6)])
 @pytest.mark.parametrize("prec", ["f16", "bf16"])
 @pytest.mark.parametrize("eos", list(EOS))
