@@ -524,8 +524,8 @@ def main():
                     "kernels_per_step": 4,
                     "note": "isothermal van der Waals fluid (theta/theta_c = 1.1, kappa 0.05) on the same fields, "
                             "grid and storage: density, stencil-field and force passes in the storage's compute "
-                            "type, then the forced step; the density pass and the step on x pairs with 16-bit "
-                            "storage"}
+                            "type, then the forced step; all four on x pairs (the density pass and the step with "
+                            "16-bit storage, the stencil passes with FP32 fields)"}
     if not args.no_secondary:
         for prec in precs[1:]:
             steps = max(3, args.steps // 10) if prec == "f64" else max(5, args.steps // 2)
