@@ -8,9 +8,14 @@ activations x[b][z][y][x][c] (channels last), weights w[cout][tap][cin] with
 tap = (dz+1)*9 + (dy+1)*3 + (dx+1), so that
     z[v][co] = bias[co] + sum_{tap,ci} w[co][tap][ci] x[v + d(tap)][ci].
 
+With dilation d the taps sit d voxels apart,
+    z[v][co] = bias[co] + sum_{tap,ci} w[co][tap][ci] x[v + d * d(tap)][ci],
+still periodic over the volume.
+
 Network (6 layers): 16 -> 32 (GELU), four 32 -> 32 residual layers
 y = x + GELU(conv(x)), and 32 -> 16 linear with the input added
-(prediction = input + conv(h)).  GELU is z Phi(z) with the Gaussian CDF Phi.
+(prediction = input + conv(h)), each layer with its own dilation.  GELU is
+z Phi(z) with the Gaussian CDF Phi.
 """
 import math
 
@@ -29,15 +34,19 @@ def w_to_conv(w):
     return w.permute(0, 2, 1).reshape(co, ci, 3, 3, 3)
 
 
-def conv3d_periodic(x, w, bias=None):
-    """x: [b][z][y][x][cin] float64, w: [cout][27][cin] -> [b][z][y][x][cout]."""
-    xc = x.permute(0, 4, 1, 2, 3)
-    xp = F.pad(xc, (1, 1, 1, 1, 1, 1), mode="circular")
-    out = F.conv3d(xp, w_to_conv(w), bias=bias)
+def conv3d_periodic(x, w, bias=None, dilation=1):
+    """x: [b][z][y][x][cin] float64, w: [cout][27][cin] -> [b][z][y][x][cout]; taps `dilation`
+    voxels apart (the circular padding is as wide)."""
+    d = dilation
+    xp = x.permute(0, 4, 1, 2, 3)
+    for dim in (2, 3, 4):  # periodic padding: index (i - d) mod n for i = 0 .. n + 2d - 1
+        n = xp.shape[dim]
+        xp = xp.index_select(dim, torch.arange(-d, n + d) % n)
+    out = F.conv3d(xp, w_to_conv(w), bias=bias, dilation=d)
     return out.permute(0, 2, 3, 4, 1)
 
 
-def conv3d_bruteforce(x, w, bias=None):
+def conv3d_bruteforce(x, w, bias=None, dilation=1):
     """The same periodic convolution by explicit loops (small inputs only)."""
     b_, nz, ny, nx, ci = x.shape
     co = w.shape[0]
@@ -48,7 +57,8 @@ def conv3d_bruteforce(x, w, bias=None):
                 for xx in range(nx):
                     acc = torch.zeros(co, dtype=F64) if bias is None else bias.clone().to(F64)
                     for tap in range(27):
-                        dz, dy, dx = tap // 9 - 1, (tap // 3) % 3 - 1, tap % 3 - 1
+                        dz, dy, dx = (dilation * (tap // 9 - 1), dilation * ((tap // 3) % 3 - 1),
+                                      dilation * (tap % 3 - 1))
                         v = x[b, (z + dz) % nz, (y + dy) % ny, (xx + dx) % nx]
                         acc = acc + w[:, tap, :] @ v
                     out[b, z, y, xx] = acc
@@ -59,12 +69,14 @@ def gelu(z):
     return 0.5 * z * (1.0 + torch.erf(z / math.sqrt(2.0)))
 
 
-def forward(x, weights, biases):
-    """Whole network; returns (prediction, list of (pre-activation, layer output))."""
+def forward(x, weights, biases, dilations=None):
+    """Whole network (layer k with dilation dilations[k], default 1); returns (prediction, list of
+    (pre-activation, layer output))."""
+    dil = dilations or [1] * len(LAYERS)
     h = x
     trace = []
-    for (ci, co, act, res), w, b in zip(LAYERS, weights, biases):
-        z = conv3d_periodic(h, w, b)
+    for (ci, co, act, res), w, b, d in zip(LAYERS, weights, biases, dil):
+        z = conv3d_periodic(h, w, b, dilation=d)
         y = gelu(z) if act == "gelu" else z
         if res:
             y = h + y
@@ -79,11 +91,11 @@ def mse(pred, target, nch):
     return (d * d).mean()
 
 
-def loss_and_grads(x, target, weights, biases, nch=5):
+def loss_and_grads(x, target, weights, biases, nch=5, dilations=None):
     """FP64 loss and gradients of all weights and biases by autograd."""
     ws = [w.detach().clone().to(F64).requires_grad_(True) for w in weights]
     bs = [b.detach().clone().to(F64).requires_grad_(True) for b in biases]
-    pred, _ = forward(x.to(F64), ws, bs)
+    pred, _ = forward(x.to(F64), ws, bs, dilations)
     loss = mse(pred, target.to(F64), nch)
     loss.backward()
     return loss.item(), [w.grad for w in ws], [b.grad for b in bs], pred.detach()
