@@ -9,7 +9,7 @@
  * rollout error.
  *
  * Tensors are channels-last, periodic volumes: x[b][z][y][x][c] (NDHWC),
- * with nx = 64 and ny even (a CTA owns whole 64-voxel rows), any nz.
+ * with nx = 64 and ny a multiple of 4 (a CTA owns whole 64-voxel rows), any nz.
  * Activations and weights are BF16; accumulation is FP32.  Weights are
  * w[cout][tap][cin] with tap = (dz+1)*9 + (dy+1)*3 + (dx+1) for a 3x3x3
  * periodic ("circular") convolution
@@ -33,6 +33,9 @@ extern "C" {
 
 typedef struct {
     int batch, nz, ny, nx;  /* volume: batch x nz x ny x nx voxels */
+    int xper;               /* convolutions: the period along x, 0 (= nx, the periodic row) or 32,
+                               16, 8: each row holds nx / xper independent periodic segments, the
+                               d-layout of sg_relabel with xper = 64 / d; other values give -1 */
 } sg_shape;
 
 /* Activation of the forward convolution epilogue. */
@@ -119,6 +122,19 @@ int sg_adam(int64_t n, float *p, const float *g, float *m, float *v, void *p16, 
  * unpack: channels 0..4 of item `item` -> float64 fields on both
  * sub-lattices; a B node (cell + (1/2,1/2,1/2)) takes the mean of its eight
  * A neighbours.  scales (3 floats: s0, s1, s2) is host memory. */
+/* Dilated convolutions.  The periodic 3x3x3 convolution with taps d voxels apart (dilation d in
+ * {1, 2, 4, 8}) of a volume s (nx = 64; nz, ny multiples of d) equals the plain convolution of
+ * its d-layout: the volume of batch * d^2 items of (nz / d) x (ny / d) x 64 voxels with
+ * xper = 64 / d, in which voxel (b, z, y, x) sits at
+ *     b' = (b d + z mod d) d + y mod d,  z' = z / d,  y' = y / d,  x' = (x mod d)(64 / d) + x / d.
+ * Its neighbours at +-1 along x' (inside the x segment), y' and z' are the volume's at +-d, all
+ * periodic.  sg_relabel copies src, in the df-layout of s, to dst in the dt-layout (df, dt in
+ * {1, 2, 4, 8}; 1 is the volume itself).  Element-wise operations commute with it, so a network
+ * keeps each layer's activations in its layer's layout.  bytes_per_voxel: channels x element size,
+ * 16 x a power of two up to 4096; fewer than 2^31 16-byte chunks in all; src and dst 16-byte
+ * aligned, distinct.  s.xper is ignored. */
+int sg_relabel(sg_shape s, int bytes_per_voxel, int df, int dt, const void *src, void *dst, void *stream);
+
 int sg_pack_fields(sg_shape s, int item, const double *rho, const double *u, const double *theta, double theta0,
                    const float *scales, void *x, void *stream);
 int sg_unpack_fields(sg_shape s, int item, const void *x, double theta0, const float *scales, double *rho, double *u,

@@ -4,6 +4,11 @@
 // weight gradient, and the small element-wise / reduction kernels of training
 // and rollout.  C ABI in include/gblb_surrogate.h.
 //
+// Rows are 64 voxels, periodic as a whole or (sg_shape.xper < 64) as 64 / xper
+// independent segments: the d-layout of a dilated convolution (k_relabel), in
+// which x + d of the volume is the next voxel of the segment.  Every kernel
+// takes x +- 1 inside the segment (xseg).
+//
 // mma.sync forward tile: one CTA owns RT = 4 consecutive rows (64 voxels each) of one
 // z-plane of one batch item: M = 256 voxels, N = cout, K = 27 * cin.  The
 // CTA stages the periodic halo (3 planes x 6 rows x 66 voxels x cin) and all
@@ -16,6 +21,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <type_traits>
 #include <utility>
 
@@ -91,6 +97,11 @@ __device__ __forceinline__ float gelu_grad(float z) {
     return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
 }
 
+// x + dx inside the periodic segment of length L (a power of two dividing kW) that holds voxel x
+// of a row: L = kW is the periodic row; L < kW splits the row into kW / L independent periodic
+// segments (the layout of a dilated convolution, sg_relabel).
+__device__ __forceinline__ int xseg(int x, int dx, int L) { return (x & ~(L - 1)) | ((x + dx) & (L - 1)); }
+
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(kFwdThreads, 1) k_conv_fwd(sg_shape s, const bf16* __restrict__ x,
                                                               const bf16* __restrict__ w,
@@ -137,7 +148,7 @@ __global__ void __launch_bounds__(kFwdThreads, 1) k_conv_fwd(sg_shape s, const b
     const int bn = (lane & 7) + 8 * (lane >> 4), bkc = (lane >> 3) & 1;
     for (int tap = 0; tap < 27; ++tap) {
         const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-        const int hrow = ((dz + 1) * kHR + (yl + 1 + dy)) * kHX + (x0 + ar + 1 + dx);
+        const int hrow = ((dz + 1) * kHR + (yl + 1 + dy)) * kHX + (xseg(x0 + ar, dx, s.xper) + 1);
         const uint32_t a0 = hs + hrow * H::STRIDE + akc * 16;
 #pragma unroll
         for (int kb = 0; kb < CIN / 16; ++kb) {
@@ -242,7 +253,7 @@ __global__ void __launch_bounds__(kWgThreads) k_conv_wgrad(sg_shape s, const bf1
             const int zz = (int)(q % s.nz);
             const int bb = (int)(q / s.nz);
             const int64_t src = ((((int64_t)bb * s.nz + wrapi(zz + ddz, s.nz)) * s.ny + wrapi(yy + ddy, s.ny)) * kW +
-                                 wrapi(xx + ddx, kW)) * CIN + c * 8;
+                                 xseg(xx, ddx, s.xper)) * CIN + c * 8;
             *reinterpret_cast<uint4*>(xs + v * XS + c * 16) = *reinterpret_cast<const uint4*>(x + src);
         }
         __syncthreads();
@@ -465,6 +476,34 @@ __global__ void k_adam(int64_t n, float* __restrict__ p, const float* __restrict
     const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
     p[i] = pi;
     if (p16) p16[i] = __float2bfloat16_rn(pi);
+}
+
+// Relabelling of a volume (nz x ny x 64 voxels per item, 2^lc 16-byte chunks per voxel) from its
+// df-layout to its dt-layout (df = 2^lf, dt = 2^lt).  Voxel (b, z, y, x) sits in the d-layout at
+//   b' = (b d + z mod d) d + y mod d,  z' = z / d,  y' = y / d,  x' = (x mod d)(64 / d) + x / d,
+// a volume of d^2 times the items, of (nz / d) x (ny / d) x 64 voxels whose rows hold d periodic x
+// segments; its neighbours at +-1 along x' (inside the segment), y' and z' are the volume's at +-d,
+// so the convolution with taps d apart is the plain one of the d-layout (d = 1: the volume).
+// One thread per 16-byte chunk of the destination, chunks of a voxel in adjacent lanes; 32-bit
+// index arithmetic (fewer than 2^31 chunks, checked by the caller), grid-stride.
+__global__ void k_relabel(int nchunks, int nz, int ny, int lc, int lf, int lt, const uint4* __restrict__ src,
+                          uint4* __restrict__ dst) {
+    const int nyt = ny >> lt, nzt = nz >> lt, nyf = ny >> lf, nzf = nz >> lf;
+    const int mt = (1 << lt) - 1, mf = (1 << lf) - 1;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nchunks; i += gridDim.x * blockDim.x) {
+        const int c = i & ((1 << lc) - 1), t = i >> lc;
+        const int xq = t & (kW - 1);
+        int r = t >> 6;
+        const int yq = r % nyt;
+        r /= nyt;
+        const int zq = r % nzt, bq = r / nzt;
+        const int x = ((xq & ((kW >> lt) - 1)) << lt) | (xq >> (6 - lt));
+        const int y = (yq << lt) | (bq & mt), z = (zq << lt) | ((bq >> lt) & mt), b = bq >> (2 * lt);
+        const int bs = (((b << lf) | (z & mf)) << lf) | (y & mf);
+        const int xs = ((x & mf) << (6 - lf)) | (x >> lf);
+        const int64_t sv = (((int64_t)bs * nzf + (z >> lf)) * nyf + (y >> lf)) * kW + xs;
+        dst[i] = src[(sv << lc) + c];
+    }
 }
 
 // A-sub-lattice fields of one batch item -> 16 normalised channels.
@@ -905,6 +944,7 @@ __global__ void __launch_bounds__(640, 1)
         const int m = 32 * quarter + lane;
         const int yl = m >> 6, xx = m & 63;
         const int pair = half * 2 + yl, pw = quarter & 1;  // the two quarters of a row form a pair
+        const bool seg = s.xper < kW;  // rows of independent periodic segments (within a quarter)
         // the residual input (or, without one, the added values) of a tile is loaded one tile of
         // this group ahead: EC bf16 values in EC / 2 words, or EC FP32 values in EC words
         const bool res = epi.res_in && CIN == COUT;
@@ -972,11 +1012,19 @@ __global__ void __launch_bounds__(640, 1)
 #pragma unroll
                     for (int e = 0; e < EC; ++e) xch[grp][pair][pw][par][1][e] = dp[e];
                 }
+                if (seg) {
+                    // x-period L <= 32: the segment lies inside this warp's 32 voxels
+                    const int sl = xseg(lane, -1, s.xper), sr = xseg(lane, 1, s.xper);
 #pragma unroll
-                for (int e = 0; e < EC; ++e) {
-                    const float l = __shfl_up_sync(0xffffffffu, dm[e], 1);
-                    const float r = __shfl_down_sync(0xffffffffu, dp[e], 1);
-                    zc[e] += (lane == 0 ? 0.f : l) + (lane == 31 ? 0.f : r);
+                    for (int e = 0; e < EC; ++e)
+                        zc[e] += __shfl_sync(0xffffffffu, dm[e], sl) + __shfl_sync(0xffffffffu, dp[e], sr);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < EC; ++e) {
+                        const float l = __shfl_up_sync(0xffffffffu, dm[e], 1);
+                        const float r = __shfl_down_sync(0xffffffffu, dp[e], 1);
+                        zc[e] += (lane == 0 ? 0.f : l) + (lane == 31 ? 0.f : r);
+                    }
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -988,11 +1036,11 @@ __global__ void __launch_bounds__(640, 1)
                 ok = false;
                 break;
             }
-            if (lane == 0) {
+            if (lane == 0 && !seg) {
 #pragma unroll
                 for (int e = 0; e < EC; ++e) zc[e] += xch[grp][pair][pw ^ 1][par][0][e];
             }
-            if (lane == 31) {
+            if (lane == 31 && !seg) {
 #pragma unroll
                 for (int e = 0; e < EC; ++e) zc[e] += xch[grp][pair][pw ^ 1][par][1][e];
             }
@@ -1245,34 +1293,47 @@ __global__ void __launch_bounds__(256, 1)
                 fail();
         }
     } else if (warp == 2) {
-        // ---- wrap-voxel fixer: per row pair, lane l < 4 cout/8 writes one 16-byte chunk of a
-        // shifted copy's wrap voxel of row y + j: side 0 (dx = +1, copy 2) voxel 0 <- dZ[63]; side 1
-        // (dx = -1, copy 0) voxel 63 <- dZ[0], at its swizzled place ----
-        constexpr int COG = COUT / 8;
-        const int j = lane / (2 * COG), side = (lane / COG) & 1, c8 = lane % COG;
-        const bool active = lane < 4 * COG;
+        // ---- wrap-voxel fixer: per row pair and x segment g (length L = xper; one segment for a
+        // periodic row), item (j, side, c8) writes one 16-byte chunk of a shifted copy's wrap voxel
+        // of row y + j: side 0 (dx = +1, copy 2) voxel g L <- dZ[g L + L - 1]; side 1 (dx = -1,
+        // copy 0) voxel g L + L - 1 <- dZ[g L], at its swizzled place.  The 4 cout/8 items of a
+        // segment go to consecutive lanes, all loads issued before the stage's wait ----
+        constexpr int COG = COUT / 8, PER_SEG = 4 * COG, KMAX = (PER_SEG * (kW / 8) + 31) / 32;
+        const int L = s.xper, items = PER_SEG * (kW / L);
         float bsum = 0.f;
         uint32_t qb = 0;
         for (int64_t r = r0; r < r1; ++r, ++qb) {
             int b, z, y;
             row_coord(r, b, z, y);
             const int st = (int)(qb % C::SB);
-            uint4 val = make_uint4(0, 0, 0, 0);
-            if (active)
-                val = *reinterpret_cast<const uint4*>(
-                    dzg + ((((int64_t)b * s.nz + z) * s.ny + y + j) * kW + (side ? 0 : kW - 1)) * COUT + 8 * c8);
+            uint4 val[KMAX];
+#pragma unroll
+            for (int i = 0; i < KMAX; ++i) {
+                const int it = lane + 32 * i, g = it / PER_SEG, rem = it % PER_SEG;
+                const int j = rem / (2 * COG), side = (rem / COG) & 1, c8 = rem % COG;
+                val[i] = make_uint4(0, 0, 0, 0);
+                if (it < items)
+                    val[i] = *reinterpret_cast<const uint4*>(
+                        dzg + ((((int64_t)b * s.nz + z) * s.ny + y + j) * kW + (side ? g * L : g * L + L - 1)) * COUT +
+                        8 * c8);
+            }
             if (!__all_sync(0xffffffffu, tc_wait(bar(BL + st), (qb / C::SB) & 1, wait_limit))) {
                 if (lane == 0) fail();
                 break;
             }
-            const int v = side ? 63 : 0;
-            const uint32_t dst = b_s +
-                                 (uint32_t)(st * C::B_STAGE + (3 * j + (side ? 0 : 2)) * C::COLB + v * C::RB) +
-                                 16u * swz_chunk<C::RB>(v, c8);
-            if (active)
-                asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(val.x), "r"(val.y), "r"(val.z),
-                             "r"(val.w)
-                             : "memory");
+#pragma unroll
+            for (int i = 0; i < KMAX; ++i) {
+                const int it = lane + 32 * i, g = it / PER_SEG, rem = it % PER_SEG;
+                const int j = rem / (2 * COG), side = (rem / COG) & 1, c8 = rem % COG;
+                const int v = side ? g * L + L - 1 : g * L;
+                const uint32_t dst = b_s +
+                                     (uint32_t)(st * C::B_STAGE + (3 * j + (side ? 0 : 2)) * C::COLB + v * C::RB) +
+                                     16u * swz_chunk<C::RB>(v, c8);
+                if (it < items)
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(val[i].x), "r"(val[i].y),
+                                 "r"(val[i].z), "r"(val[i].w)
+                                 : "memory");
+            }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) tp_arrive(bar(BF + st));
@@ -1561,8 +1622,11 @@ static int launch_wgrad(sg_shape s, const void* x, const void* dz, float* dw, fl
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
-static bool shape_ok(sg_shape s) {
-    return s.batch >= 1 && s.nz >= 1 && s.nx == kW && s.ny >= kRT && s.ny % kRT == 0;
+// Valid convolution volume; an x period of 0 becomes the row (kW).
+static bool shape_ok(sg_shape& s) {
+    if (s.xper == 0) s.xper = kW;
+    const bool per = s.xper == kW || s.xper == 32 || s.xper == 16 || s.xper == 8;
+    return per && s.batch >= 1 && s.nz >= 1 && s.nx == kW && s.ny >= kRT && s.ny % kRT == 0;
 }
 
 }  // namespace sg
@@ -1675,6 +1739,25 @@ int sg_adam(int64_t n, float* p, const float* g, float* m, float* v, void* p16, 
     const float c1 = 1.f - powf(beta1, (float)t), c2 = 1.f - powf(beta2, (float)t);
     k_adam<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, p, g, m, v, static_cast<bf16*>(p16), lr,
                                                                            beta1, beta2, eps, c1, c2);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+int sg_relabel(sg_shape s, int bytes_per_voxel, int df, int dt, const void* src, void* dst, void* stream) {
+    auto log2_of = [](int v) {  // log2 of a power of two in [1, 256], else -1
+        for (int l = 0; l <= 8; ++l)
+            if (v == (1 << l)) return l;
+        return -1;
+    };
+    const int lf = log2_of(df), lt = log2_of(dt), lc = log2_of(bytes_per_voxel / 16);
+    auto dil_ok = [&](int l, int d) { return l >= 0 && l <= 3 && s.nz % d == 0 && s.ny % d == 0; };
+    const int64_t nchunks = (int64_t)s.batch * s.nz * s.ny * kW << (lc < 0 ? 0 : lc);
+    if (!src || !dst || src == dst || s.batch < 1 || s.nz < 1 || s.ny < 1 || s.nx != kW || !dil_ok(lf, df) ||
+        !dil_ok(lt, dt) || bytes_per_voxel % 16 || lc < 0 || nchunks >= ((int64_t)1 << 31) || ((uintptr_t)src & 15) ||
+        ((uintptr_t)dst & 15))
+        return -1;
+    const unsigned blocks = (unsigned)std::min<int64_t>((nchunks + 255) / 256, 152 * 16);
+    k_relabel<<<blocks, 256, 0, (cudaStream_t)stream>>>((int)nchunks, s.nz, s.ny, lc, lf, lt,
+                                                        static_cast<const uint4*>(src), static_cast<uint4*>(dst));
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

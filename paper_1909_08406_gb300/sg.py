@@ -2,7 +2,8 @@
 
 Argument marshalling only: tensors are torch CUDA tensors (BF16 activations
 and weights, FP32 accumulators / gradients); every computation runs in
-libgblb.so.  Shapes: activations [batch][nz][ny][nx][channels] (nx = 64).
+libgblb.so.  Shapes: activations [batch][nz][ny][nx][channels] (nx = 64); a dilated convolution
+runs on the volume's d-layout (relabel) with xper = 64 / d.
 """
 from __future__ import annotations
 
@@ -16,7 +17,8 @@ _bound = False
 
 
 class SgShape(ctypes.Structure):
-    _fields_ = [("batch", ctypes.c_int), ("nz", ctypes.c_int), ("ny", ctypes.c_int), ("nx", ctypes.c_int)]
+    _fields_ = [("batch", ctypes.c_int), ("nz", ctypes.c_int), ("ny", ctypes.c_int), ("nx", ctypes.c_int),
+                ("xper", ctypes.c_int)]
 
 
 ACT_NONE, ACT_GELU = 0, 1
@@ -42,6 +44,7 @@ def _L():
                         ctypes.c_int, vp],
             "sg_pack_fields": [SgShape, ctypes.c_int, vp, vp, vp, ctypes.c_double, vp, vp, vp],
             "sg_unpack_fields": [SgShape, ctypes.c_int, vp, ctypes.c_double, vp, vp, vp, vp, vp],
+            "sg_relabel": [SgShape, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp],
             "sg_set_conv_impl": [ctypes.c_int],
             "sg_status": [vp],
         }
@@ -80,14 +83,31 @@ def status():
     _ok(_L().sg_status(_stream()), "sg_status")
 
 
-def shape_of(t):
+def shape_of(t, xper=0):
     b, nz, ny, nx, _ = t.shape
-    return SgShape(b, nz, ny, nx)
+    return SgShape(b, nz, ny, nx, xper)
 
 
-def conv3d_fwd(x, w, bias=None, act=ACT_NONE, res_in=False, add=None, z_out=None, y=None):
+def relabelled_shape(shape, d):
+    """Shape of the d-layout of a volume [batch][nz][ny][64][c] (sg_relabel)."""
+    b, nz, ny, nx, c = shape
+    return (b * d * d, nz // d, ny // d, nx, c)
+
+
+def relabel(x, df, dt, natural, y=None):
+    """x in the df-layout of a volume of shape `natural` -> its dt-layout (a new tensor unless y)."""
+    if y is None:
+        y = torch.empty(relabelled_shape(natural, dt), dtype=x.dtype, device=x.device)
+    b, nz, ny, nx, c = natural
+    _ok(_L().sg_relabel(SgShape(b, nz, ny, nx, 0), c * x.element_size(), df, dt, _p(x), _p(y), _stream()),
+        "sg_relabel")
+    return y
+
+
+def conv3d_fwd(x, w, bias=None, act=ACT_NONE, res_in=False, add=None, z_out=None, y=None, xper=0):
+    """x in a d-layout with xper = 64 / d gives the convolution with taps d voxels apart."""
     cout, _, cin = w.shape
-    s = shape_of(x)
+    s = shape_of(x, xper)
     if y is None:
         y = torch.empty(x.shape[:-1] + (cout,), dtype=torch.bfloat16, device=x.device)
     _ok(_L().sg_conv3d_fwd(s, cin, cout, _p(x), _p(w), _p(bias), act, int(res_in), _p(add), _p(z_out), _p(y),
@@ -95,11 +115,12 @@ def conv3d_fwd(x, w, bias=None, act=ACT_NONE, res_in=False, add=None, z_out=None
     return y
 
 
-def conv3d_fwd_f32(x, w, add=None, y=None):
+def conv3d_fwd_f32(x, w, add=None, y=None, xper=0):
     cout, _, cin = w.shape
     if y is None:
         y = torch.empty(x.shape[:-1] + (cout,), dtype=torch.float32, device=x.device)
-    _ok(_L().sg_conv3d_fwd_f32(shape_of(x), cin, cout, _p(x), _p(w), _p(add), _p(y), _stream()), "sg_conv3d_fwd_f32")
+    _ok(_L().sg_conv3d_fwd_f32(shape_of(x, xper), cin, cout, _p(x), _p(w), _p(add), _p(y), _stream()),
+        "sg_conv3d_fwd_f32")
     return y
 
 
@@ -123,9 +144,9 @@ def wgrad_scratch(x, cin, cout):
     return torch.empty(n, dtype=torch.uint8, device=x.device)
 
 
-def conv3d_wgrad(x, dz, dw, db, scratch):
+def conv3d_wgrad(x, dz, dw, db, scratch, xper=0):
     cin, cout = x.shape[-1], dz.shape[-1]
-    _ok(_L().sg_conv3d_wgrad(shape_of(x), cin, cout, _p(x), _p(dz), _p(dw), _p(db), _p(scratch), _stream()),
+    _ok(_L().sg_conv3d_wgrad(shape_of(x, xper), cin, cout, _p(x), _p(dz), _p(dw), _p(db), _p(scratch), _stream()),
         "sg_conv3d_wgrad")
 
 

@@ -9,6 +9,9 @@ FP32 accumulation, all in the kernels of include/gblb_surrogate.h):
     h2..h5 = h + GELU(conv(h))               32 -> 32 (residual)
     pred = x + conv(h5)                      32 -> 16 (5 used)
 on the A sub-lattice fields of a 64^3 grid (channels (rho-1)/s, u/s, (theta/theta0-1)/s).
+The taps of layer k sit DILATIONS[k] voxels apart (1, 2, 4, 8, 8, 8: a receptive field of
++-31 voxels, against +-6 undilated); each layer runs on its input's d-layout (sg.relabel), where
+the dilated convolution is the plain one with rows of 64 / d-voxel periodic segments.
 Training: mean-squared error, Adam on FP32 master weights.  Orchestration
 lives here (argument marshalling, loops); every arithmetic step is a kernel
 of libgblb.so.  torch supplies device memory only.
@@ -27,15 +30,17 @@ from . import workloads as wl
 
 LAYERS = [(16, 32, sg.ACT_GELU, False), (32, 32, sg.ACT_GELU, True), (32, 32, sg.ACT_GELU, True),
           (32, 32, sg.ACT_GELU, True), (32, 32, sg.ACT_GELU, True), (32, 16, sg.ACT_NONE, False)]
+DILATIONS = (1, 2, 4, 8, 8, 8)
 NCH = 5           # physical channels
 SCALES = (5e-3, 5e-3, 5e-3)
 NU = 0.01
 
 
 class Surrogate:
-    def __init__(self, seed=0, device="cuda"):
+    def __init__(self, seed=0, device="cuda", dilations=DILATIONS):
         rng = np.random.default_rng(seed)
         self.device = device
+        self.dil = tuple(dilations)
         self.w32, self.b32, self.w16 = [], [], []
         for k, (ci, co, act, res) in enumerate(LAYERS):
             fan = 27 * ci
@@ -60,33 +65,46 @@ class Surrogate:
             sg.adam(w32, zero, torch.zeros_like(m), torch.zeros_like(v), w16, 0.0, 1)
 
     def forward(self, x, train=False):
-        """x: [B][nz][ny][64][16] BF16 -> prediction (BF16, same shape)."""
-        h = x
-        self.cache = [x]
-        self.zs = []
+        """x: [B][nz][ny][64][16] BF16 -> prediction (BF16, same shape).  Keeps, for the backward
+        pass, each layer's input (cache) and FP32 pre-activation (zs) in that layer's d-layout."""
+        nat = tuple(x.shape[:-1])
+        h, cur = x, 1
+        self.cache, self.zs = [], []
         for k, (ci, co, act, res) in enumerate(LAYERS):
+            d = self.dil[k]
+            if d != cur:
+                h = sg.relabel(h, cur, d, nat + (h.shape[-1],))
+                cur = d
             last = k == len(LAYERS) - 1
-            z = torch.empty(x.shape[:-1] + (co,), dtype=torch.float32, device=x.device) if train else None
-            h = sg.conv3d_fwd(h, self.w16[k], self.b32[k], act=act, res_in=res, add=x if last else None, z_out=z)
-            self.zs.append(z)
+            add = None
+            if last:
+                add = x if d == 1 else sg.relabel(x, 1, d, nat + (x.shape[-1],))
+            z = torch.empty(h.shape[:-1] + (co,), dtype=torch.float32, device=x.device) if train else None
             self.cache.append(h)
-        return h
+            h = sg.conv3d_fwd(h, self.w16[k], self.b32[k], act=act, res_in=res, add=add, z_out=z, xper=64 // d)
+            self.zs.append(z)
+        return h if cur == 1 else sg.relabel(h, cur, 1, nat + (h.shape[-1],))
 
     def backward(self, dpred, scratch_w, trace=None):
-        """Gradients of all weights and biases from dL/dpred (FP32, [..][16]).  If `trace` is a
-        dict, it receives per layer k the gradient arriving at the layer's output ("dh_out", FP32),
-        the pre-activation gradient ("dz", BF16) and the gradient passed to its input ("dh_in",
-        FP32; layers k > 0)."""
-        dh = dpred
+        """Gradients of all weights and biases from dL/dpred (FP32, [..][16], natural layout).  If
+        `trace` is a dict, it receives per layer k, in the layer's d-layout, the gradient arriving
+        at the layer's output ("dh_out", FP32), the pre-activation gradient ("dz", BF16) and the
+        gradient passed to its input ("dh_in", FP32; layers k > 0)."""
+        nat = tuple(dpred.shape[:-1])
+        dh, cur = dpred, 1
         for k in range(len(LAYERS) - 1, -1, -1):
             ci, co, act, res = LAYERS[k]
+            d = self.dil[k]
+            if d != cur:
+                dh = sg.relabel(dh, cur, d, nat + (dh.shape[-1],))
+                cur = d
             dz = sg.act_backward(dh, self.zs[k], act)
-            sg.conv3d_wgrad(self.cache[k], dz, self.g[2 * k], self.g[2 * k + 1], scratch_w[(ci, co)])
+            sg.conv3d_wgrad(self.cache[k], dz, self.g[2 * k], self.g[2 * k + 1], scratch_w[(ci, co)], xper=64 // d)
             if trace is not None:
                 trace[k] = {"dh_out": dh, "dz": dz}
             if k > 0:
                 wt = sg.transpose_weights(self.w16[k])
-                dh = sg.conv3d_fwd_f32(dz, wt, add=dh if res else None)
+                dh = sg.conv3d_fwd_f32(dz, wt, add=dh if res else None, xper=64 // d)
                 if trace is not None:
                     trace[k]["dh_in"] = dh
 

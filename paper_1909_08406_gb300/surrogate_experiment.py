@@ -4,6 +4,7 @@ error against the identity map, a judged 20-hop rollout with LB fallback, and
 the time of one surrogate application against the LB steps it replaces.
 
     python -m paper_1909_08406_gb300.surrogate_experiment [--count 2000] [--iters 1500] [--hop 50]
+        [--dilations 1,2,4,8,8,8]
 
 Prints one JSON object.
 """
@@ -29,12 +30,14 @@ def main(argv=None):
     p.add_argument("--hops", type=int, default=20)
     p.add_argument("--threshold", type=float, default=1e-3)
     p.add_argument("--rollouts", type=int, default=4)
+    p.add_argument("--dilations", default="1,2,4,8,8,8", help="tap spacing of the six layers")
     a = p.parse_args(argv)
+    dil = tuple(int(v) for v in a.dilations.split(","))
 
     from . import surrogate as S
 
     torch.cuda.set_device(0)
-    out = {"config": vars(a), "receptive_field_cells": 6, "sound_travel_cells_per_hop": None}
+    out = {"config": vars(a), "receptive_field_cells": sum(dil), "sound_travel_cells_per_hop": None}
     import math
     from . import lb
     cs = math.sqrt(5 * lb.lb_theta0() / 3)
@@ -44,7 +47,7 @@ def main(argv=None):
     test = S.make_dataset(a.test, hop=a.hop, seed0=900000, t0_choices=(0, 100, 250, 500))
     torch.cuda.synchronize()
     out["data_seconds"] = time.perf_counter() - t0
-    net = S.Surrogate(seed=0)
+    net = S.Surrogate(seed=0, dilations=dil)
     t0 = time.perf_counter()
     hist = S.train(net, train, a.iters, batch=a.batch, lr=a.lr, log_every=max(1, a.iters // 10))
     torch.cuda.synchronize()

@@ -43,3 +43,26 @@ def decode(raw, prec, w_lib):
         return v
     w = np.asarray(w_lib)[None, :, None, None, None]
     return w * (1.0 + v / STORE_SCALE[prec])
+
+
+def _d_layout_index(natural, d):
+    """Index arrays (b', z', y', x') of every voxel (b, z, y, x) of a volume [b][nz][ny][nx][c] in
+    its d-layout (include/gblb_surrogate.h): b' = (b d + z mod d) d + y mod d, z' = z / d,
+    y' = y / d, x' = (x mod d)(nx / d) + x / d."""
+    b, nz, ny, nx = natural[:4]
+    B, Z, Y, X = np.meshgrid(np.arange(b), np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    idx = ((B * d + Z % d) * d + Y % d, Z // d, Y // d, (X % d) * (nx // d) + X // d)
+    return tuple(torch.from_numpy(np.ascontiguousarray(i)) for i in idx)
+
+
+def from_d_layout(t, d, natural):
+    """A CPU tensor in the d-layout of a volume of shape `natural` back to the volume's layout."""
+    return t[_d_layout_index(natural, d)]
+
+
+def to_d_layout(t, d):
+    """A CPU volume [b][nz][ny][nx][c] in its d-layout [b d^2][nz / d][ny / d][nx][c]."""
+    b, nz, ny, nx, c = t.shape
+    out = torch.empty((b * d * d, nz // d, ny // d, nx, c), dtype=t.dtype)
+    out[_d_layout_index(t.shape, d)] = t
+    return out

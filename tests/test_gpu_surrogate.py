@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 import torch
 
+from helpers import from_d_layout
 from oracle import surrogate as so
 from paper_1909_08406_gb300 import lb, sg
 from paper_1909_08406_gb300 import surrogate as S
@@ -16,8 +17,14 @@ pytestmark = pytest.mark.gpu
 F64 = torch.float64
 
 
-def _random_net(seed):
-    net = S.Surrogate(seed=seed)
+# (dilations, volume): the plain network, and the dilated one of the surrogate on a volume whose
+# d = 8 layout still has rows of 4 (ny / 8 a multiple of 4)
+NETS = [((1,) * 6, (2, 4, 8, 64)), (S.DILATIONS, (1, 8, 32, 64))]
+NET_IDS = ["plain", "dilated"]
+
+
+def _random_net(seed, dil=S.DILATIONS):
+    net = S.Surrogate(seed=seed, dilations=dil)
     g = torch.Generator().manual_seed(seed)
     for k, (ci, co, _, _) in enumerate(S.LAYERS):
         w = torch.randn((co, 27, ci), generator=g) / math.sqrt(27 * ci) * (0.5 if k else 1.0)
@@ -29,14 +36,14 @@ def _random_net(seed):
     return net
 
 
-def test_network_gradients_match_oracle():
+@pytest.mark.parametrize("dil,shape", NETS, ids=NET_IDS)
+def test_network_gradients_match_oracle(dil, shape):
     """GPU forward + backward (BF16 storage of activations, FP32 accumulation) against FP64
     autograd on the same BF16 weights and inputs: per layer, the relative Frobenius error of
     the weight gradient <= 3e-2 and the cosine similarity >= 0.999 (activations are rounded to
     BF16 between layers, 2^-9 relative each)."""
-    net = _random_net(3)
+    net = _random_net(3, dil)
     g = torch.Generator().manual_seed(4)
-    shape = (2, 4, 8, 64)
     x = torch.zeros(shape + (16,))
     x[..., :5] = torch.randn(shape + (5,), generator=g)
     t = x.clone()
@@ -52,7 +59,7 @@ def test_network_gradients_match_oracle():
     torch.cuda.synchronize()
     ws = [w.cpu().to(F64) for w in net.w16]
     bs = [b.cpu().to(F64) for b in net.b32]
-    l_or, gw, gb, _ = so.loss_and_grads(xb.to(F64), tb.to(F64), ws, bs)
+    l_or, gw, gb, _ = so.loss_and_grads(xb.to(F64), tb.to(F64), ws, bs, dilations=list(dil))
     assert loss.item() == pytest.approx(l_or, rel=2e-2)
     for k in range(len(S.LAYERS)):
         a = net.g[2 * k].cpu().to(F64).flatten()
@@ -66,7 +73,8 @@ def test_network_gradients_match_oracle():
         assert (ab - gb[k]).norm() <= 3e-2 * gb[k].norm() + 1e-6, k
 
 
-def test_network_backward_chain_matches_oracle_elementwise():
+@pytest.mark.parametrize("dil,shape", NETS, ids=NET_IDS)
+def test_network_backward_chain_matches_oracle_elementwise(dil, shape):
     """Every link of the GPU backward pass, element by element, against FP64 computed from the
     GPU's own inputs to that link (the BF16 activations and FP32 pre-activations cached by the
     forward pass, and the gradient the link received):
@@ -77,10 +85,11 @@ def test_network_backward_chain_matches_oracle_elementwise():
       dh_in_k      = the input gradient of conv(h_k; W_k) for dz_k, plus dh_out_k for the
                      residual layers: <= 1e-5 of the sum of absolute terms.
     A wiring mistake anywhere in the chain (a dropped residual gradient, a wrong activation or
-    cache index, a transposed tap) moves some element by the size of the term itself."""
-    net = _random_net(5)
+    cache index, a transposed tap, a layer in the wrong layout) moves some element by the size of
+    the term itself.  Each layer's tensors are in its d-layout; they are compared on the volume
+    (tests/helpers.py from_d_layout) against the oracle's convolution with the layer's dilation."""
+    net = _random_net(5, dil)
     g = torch.Generator().manual_seed(6)
-    shape = (2, 4, 8, 64)
     x = torch.zeros(shape + (16,))
     x[..., :5] = torch.randn(shape + (5,), generator=g)
     t = x.clone()
@@ -96,17 +105,22 @@ def test_network_backward_chain_matches_oracle_elementwise():
     torch.cuda.synchronize()
     cpu = lambda a: a.cpu().to(F64)  # noqa: E731
 
+    def nat(a, k):  # layer k's tensor, in its d-layout, on the volume (FP64, CPU)
+        return from_d_layout(cpu(a), dil[k], shape)
+
     voxels = float(np.prod(shape))
     ref = torch.zeros(shape + (16,), dtype=F64)
     ref[..., :5] = 2 * (cpu(pred) - cpu(td))[..., :5] / (voxels * 5)
     assert torch.all((cpu(dpred) - ref).abs() <= 1e-6 * ref.abs() + 1e-12)
-    assert torch.equal(cpu(trace[len(S.LAYERS) - 1]["dh_out"]), cpu(dpred))
+    last = len(S.LAYERS) - 1
+    assert torch.equal(nat(trace[last]["dh_out"], last), cpu(dpred))
 
     for k in range(len(S.LAYERS) - 1, -1, -1):
         ci, co, act, res = S.LAYERS[k]
-        h = cpu(net.cache[k])                      # the layer's input (BF16 on the GPU)
-        zk = cpu(net.zs[k])                        # pre-activation (FP32)
-        dh_out, dz = cpu(trace[k]["dh_out"]), cpu(trace[k]["dz"])
+        dk = dil[k]
+        h = nat(net.cache[k], k)                   # the layer's input (BF16 on the GPU)
+        zk = nat(net.zs[k], k)                     # pre-activation (FP32)
+        dh_out, dz = nat(trace[k]["dh_out"], k), nat(trace[k]["dz"], k)
         w = cpu(net.w16[k])
         # activation backward: one BF16 rounding of the product, plus the FP32 error of act'(z) =
         # Phi(z) + z phi(z), whose two terms cancel near z = -0.75 (a few ulp of each term)
@@ -118,21 +132,21 @@ def test_network_backward_chain_matches_oracle_elementwise():
         # weight and bias gradients from the GPU's own h and dz
         w0 = torch.zeros((co, 27, ci), dtype=F64, requires_grad=True)
         b0 = torch.zeros(co, dtype=F64, requires_grad=True)
-        (so.conv3d_periodic(h, w0, b0) * dz).sum().backward()
+        (so.conv3d_periodic(h, w0, b0, dilation=dk) * dz).sum().backward()
         wa = torch.zeros((co, 27, ci), dtype=F64, requires_grad=True)
-        (so.conv3d_periodic(h.abs(), wa) * dz.abs()).sum().backward()
+        (so.conv3d_periodic(h.abs(), wa, dilation=dk) * dz.abs()).sum().backward()
         assert torch.all((cpu(net.g[2 * k]) - w0.grad).abs() <= 1e-5 * wa.grad + 1e-12), k
         assert torch.all((cpu(net.g[2 * k + 1]) - b0.grad).abs() <= 1e-5 * dz.abs().sum(dim=(0, 1, 2, 3)) + 1e-12), k
         if k > 0:
             hr = h.clone().requires_grad_(True)
-            (so.conv3d_periodic(hr, w) * dz).sum().backward()
+            (so.conv3d_periodic(hr, w, dilation=dk) * dz).sum().backward()
             ha = h.abs().requires_grad_(True)
-            (so.conv3d_periodic(ha, w.abs()) * dz.abs()).sum().backward()
+            (so.conv3d_periodic(ha, w.abs(), dilation=dk) * dz.abs()).sum().backward()
             want = hr.grad + (dh_out if res else 0)
             bound = 1e-5 * (ha.grad + (dh_out.abs() if res else 0)) + 1e-12
-            assert torch.all((cpu(trace[k]["dh_in"]) - want).abs() <= bound), k
+            assert torch.all((nat(trace[k]["dh_in"], k) - want).abs() <= bound), k
             # the gradient layer k passes on is the one layer k - 1 receives
-            assert torch.equal(cpu(trace[k - 1]["dh_out"]), cpu(trace[k]["dh_in"])), k
+            assert torch.equal(nat(trace[k - 1]["dh_out"], k - 1), nat(trace[k]["dh_in"], k)), k
 
 
 def test_pack_unpack_fields():
@@ -203,9 +217,9 @@ def test_trained_network_gain_at_hop_50():
     """What the trained network gains over the method without it, judged at one hop length (50 LB
     steps, the configured hop): after training on hop-50 pairs its held-out error is below the
     identity map's (no change), and one application costs less than the 50 LB steps it replaces
-    (64^3).  Its error against LB is the perturbation's, which stays of order one at this hop
-    (the network sees +-6 cells, sound travels 35 in 50 steps); the judged rollout therefore
-    falls back to LB under the perturbation criterion."""
+    (64^3).  Its error against LB is the perturbation's, which stays far above 1e-3 at this hop
+    (the dilated network sees +-31 cells, sound travels 35 in 50 steps); the judged rollout
+    therefore falls back to LB under the perturbation criterion."""
     data = S.make_dataset(24, hop=50, t0_choices=(0, 40), per_batch=12)
     held = S.make_dataset(8, hop=50, seed0=700000, t0_choices=(0, 40), per_batch=8)
     net = S.Surrogate(seed=2)
