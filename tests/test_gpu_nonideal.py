@@ -81,10 +81,11 @@ def test_nonideal_step_matches_oracle(prec, tol, eos):
     assert rel.max() <= tol, rel.max()
 
 
-@pytest.mark.parametrize("shape", [(13, 4, 6), (260, 2, 3)])
+@pytest.mark.parametrize("shape", [(13, 4, 6), (260, 2, 3), (2, 3, 4), (6, 1, 1)])
 def test_nonideal_fp32_stencil_paths_match_oracle(shape):
     """FP32 fields with nx odd (one node per thread) and with a row of 130 x pairs (two blocks of
-    pairs, the second ragged); nx = 12 above runs the x pairs in one block."""
+    pairs, the second ragged); nx = 12 above runs the x pairs in one block.  nx = 2: the pairs at
+    x - 2 and x + 2 are the thread's own; ny = nz = 1: every y and z neighbour is the node's row."""
     steps = 5
     e, rho = _slab(shape, noise=0.02)
     got, _, _ = _gpu(shape, "f32", e, rho, steps)
@@ -94,7 +95,7 @@ def test_nonideal_fp32_stencil_paths_match_oracle(shape):
     assert rel.max() <= 2e-6, rel.max()
 
 
-@pytest.mark.parametrize("shape", [(12, 4, 6), (13, 4, 6)])
+@pytest.mark.parametrize("shape", [(12, 4, 6), (13, 4, 6), (2, 3, 4)])
 @pytest.mark.parametrize("prec", ["f16", "bf16"])
 @pytest.mark.parametrize("eos", list(EOS))
 def test_nonideal_16bit_step_matches_oracle(prec, eos, shape):
