@@ -33,6 +33,7 @@ def lib():
         L.or_nvel.restype = ctypes.c_int
         L.or_max_threads.restype = ctypes.c_int
         L.or_entropic_equilibrium.restype = ctypes.c_int
+        L.or_path_length.restype = ctypes.c_double
         _lib = L
     return _lib
 
@@ -44,10 +45,13 @@ def _p(a):
 
 def _kind(project):
     """Equilibrium used by collide/step/init_fields: project=True (series with the momentum
-    projection), False (the series as printed) or "entropic" (the exact entropic equilibrium,
-    Eq. (discreteentropiceq), by Newton's method)."""
+    projection), False (the series as printed), "entropic" (the exact entropic equilibrium,
+    Eq. (discreteentropiceq), by Newton's method) or "entropic_path" (that equilibrium, and the
+    relaxation alpha beta with the entropic path length alpha of path_length)."""
     if project == "entropic":
         return ctypes.c_int(2)
+    if project == "entropic_path":
+        return ctypes.c_int(3)
     return ctypes.c_int(1 if project else 0)
 
 
@@ -101,6 +105,15 @@ def equilibrium(rho, u, theta, project=True):
     out = np.zeros(NV)
     lib().or_equilibrium(ctypes.c_double(rho), _p(u), ctypes.c_double(theta), ctypes.c_int(int(project)), _p(out))
     return out
+
+
+def path_length(f, feq):
+    """Entropic path length alpha of one node (Sec. "Droplet Collision"): the nontrivial root of
+    H(f + alpha (f^eq - f)) = H(f), H(f) = sum_i f_i ln(f_i / w_i); 2 when f = f^eq or no root
+    lies below the positivity limit.  f, feq: [41] float64 in the oracle's velocity order."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    feq = np.ascontiguousarray(feq, dtype=np.float64)
+    return lib().or_path_length(_p(f), _p(feq))
 
 
 def entropic_equilibrium(rho, u, theta):

@@ -22,6 +22,8 @@
  *                                               M_2, M_2', A_1, A_2
  *   - exact entropic equilibrium (Newton) ..... Sec. V, Eqs. (discreteentropiceq)
  *                                               and (fivelagrangemultipliersystem)
+ *   - entropic path length alpha ............. Sec. "Droplet Collision" (the
+ *                                               update with alpha beta, x_i)
  *   - BGK collision and streaming ............. Sec. II, discrete BGK update
  *   - bcc grid: two sc lattices offset by
  *     half a cell in every direction .......... Sec. IV
@@ -356,11 +358,68 @@ void or_moments(const double *f, double *rho, double *u, double *theta) {
 
 static double beta_of_tau(double tau) { return isinf(tau) ? 0.0 : 1.0 / (2.0 * tau + 1.0); }
 
+/* Entropic path length (Sec. "Droplet Collision": the update written with a
+ * factor alpha beta, alpha chosen so that the dynamics obeys the H theorem,
+ * from x_i = f^eq_i / f_i - 1).  alpha is the nontrivial root of
+ *   Delta H(alpha) = H(f + alpha (f^eq - f)) - H(f) = 0,  H(f) = sum_i f_i ln(f_i / w_i),
+ * which with f_i + alpha (f^eq_i - f_i) = f_i (1 + alpha x_i) reads
+ *   Delta H(alpha) = sum_i f_i [(1 + alpha x_i) ln(1 + alpha x_i) + alpha x_i ln(f_i / w_i)].
+ * Delta H(0) = 0 and Delta H is convex in alpha; when H falls towards f^eq
+ * (Delta H < 0 just above 0) it returns to zero once more below
+ * alpha_max = min over x_i < 0 of -1/x_i (where a population reaches zero).
+ * The root is bracketed (a point where Delta H < 0, one where it is > 0) and
+ * bisected to the last bit.  Readings: alpha = 2 (plain BGK) when every
+ * |x_i| <= 1e-7 (there the FP64 round-off of f^eq - f, and the residual of an
+ * iterated f^eq's moments, dominate Delta H ~ sum f x^2; the root is 2 + O(x),
+ * so f' moves by less than beta |x|^2), and when no root lies below alpha_max. */
+static double path_dh(const double *f, const double *x, double a) {
+    double s = 0.0;
+    for (int i = 0; i < NV; ++i) {
+        const double y = a * x[i];
+        s += f[i] * ((1.0 + y) * log1p(y) + y * log(f[i] / W[i]));
+    }
+    return s;
+}
+
+double or_path_length(const double *f, const double *feq) {
+    init_lattice();
+    double x[NV], amax = INFINITY;
+    int resolved = 0;
+    for (int i = 0; i < NV; ++i) {
+        x[i] = feq[i] / f[i] - 1.0;
+        if (fabs(x[i]) > 1e-7) resolved = 1;
+        if (x[i] < 0.0 && -1.0 / x[i] < amax) amax = -1.0 / x[i];
+    }
+    if (!resolved) return 2.0;
+    /* hi: Delta H > 0, from 2 outwards (halfway to alpha_max at each try) */
+    double hi = amax > 2.0 ? 2.0 : 0.5 * amax;
+    for (int k = 0; k < 200 && path_dh(f, x, hi) <= 0.0; ++k) {
+        if (isinf(amax))
+            hi *= 2.0;
+        else
+            hi = 0.5 * (hi + amax);
+    }
+    if (!(path_dh(f, x, hi) > 0.0)) return 2.0;
+    /* lo: Delta H < 0, from hi towards 0 */
+    double lo = 0.5 * hi;
+    for (int k = 0; k < 200 && path_dh(f, x, lo) >= 0.0; ++k) lo *= 0.5;
+    if (!(path_dh(f, x, lo) < 0.0)) return 2.0;
+    for (int k = 0; k < 200; ++k) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (path_dh(f, x, mid) < 0.0)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
 /* The equilibrium used by the update.  kind 0: Eq. (feqGenU3) as printed;
  * 1: Eq. (feqGenU3) with the momentum projection; 2: the exact entropic
  * equilibrium, Eq. (discreteentropiceq) (NaN if Newton fails). */
 static void equilibrium_of_kind(double rho, const double *u, double theta, int kind, double *feq) {
-    if (kind == 2) {
+    if (kind == 2 || kind == 3) {
         if (or_entropic_equilibrium(rho, u, theta, feq) < 0)
             for (int i = 0; i < NV; ++i) feq[i] = NAN;
     } else {
@@ -369,13 +428,16 @@ static void equilibrium_of_kind(double rho, const double *u, double theta, int k
 }
 
 /* Discrete BGK collision f* = f + 2 beta (f^eq(rho(f), u(f), theta(f)) - f),
- * with the equilibrium of the given kind (see equilibrium_of_kind). */
+ * with the equilibrium of the given kind (see equilibrium_of_kind); kind 3 is
+ * the exact entropic equilibrium with the entropic path length,
+ * f* = f + alpha beta (f^eq - f), alpha = or_path_length(f, f^eq). */
 void or_collide(const double *f, double tau, int project, double *out) {
     init_lattice();
     double rho, u[3], theta, feq[NV];
     or_moments(f, &rho, u, &theta);
     equilibrium_of_kind(rho, u, theta, project, feq);
     double b2 = 2.0 * beta_of_tau(tau);
+    if (project == 3) b2 = or_path_length(f, feq) * beta_of_tau(tau);
     for (int i = 0; i < NV; ++i) out[i] = f[i] + b2 * (feq[i] - f[i]);
 }
 
