@@ -89,6 +89,14 @@ typedef enum {
  * reported as LB_ERR_UNSTABLE.  Excludes LB_FLAG_PAPER_LITERAL; not for
  * lb_batch_init. */
 #define LB_FLAG_ENTROPIC 4u
+/* With LB_FLAG_ENTROPIC: the entropic path length (Sec. "Droplet Collision", the update with
+ * alpha beta, alpha such that the dynamics obeys the H theorem).  The collision becomes
+ * f' = f + alpha beta (f^eq - f), beta = 1 / (2 tau + 1), with alpha per node the nontrivial
+ * root of H(f + alpha (f^eq - f)) = H(f), H(f) = sum_i f_i ln(f_i / w_i) (alpha = 2 is BGK).
+ * Solved by Newton's method in the storage's compute type; alpha = 2 where f = f^eq or where no
+ * root lies below the value at which a population reaches zero.  Needs LB_FLAG_ENTROPIC
+ * (LB_ERR_ARG otherwise); lb_set_walls refuses it (LB_ERR_ARG); not for lb_batch_init. */
+#define LB_FLAG_ENTROPIC_PATH 8u
 
 typedef struct {
     int64_t nx, ny, nz; /* simple-cubic cells per axis, each >= 1; nodes = 2 nx ny nz */

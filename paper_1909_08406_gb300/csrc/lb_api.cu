@@ -221,10 +221,12 @@ lb_status lb_init(lb_ctx** out, lb_grid grid, int velocity_set, double theta0, d
     if ((int)precision < LB_F64 || (int)precision > LB_F32_S16B)
         return fail(nullptr, LB_ERR_ARG, "lb_init: unknown precision");
     if (!(tau > 0.0)) return fail(nullptr, LB_ERR_ARG, "lb_init: tau must be > 0 (or +inf)");
-    if (flags & ~(LB_FLAG_PAPER_LITERAL | LB_FLAG_STAGED | LB_FLAG_ENTROPIC))
+    if (flags & ~(LB_FLAG_PAPER_LITERAL | LB_FLAG_STAGED | LB_FLAG_ENTROPIC | LB_FLAG_ENTROPIC_PATH))
         return fail(nullptr, LB_ERR_ARG, "lb_init: unknown flag bits");
     if ((flags & LB_FLAG_ENTROPIC) && (flags & LB_FLAG_PAPER_LITERAL))
         return fail(nullptr, LB_ERR_ARG, "lb_init: LB_FLAG_ENTROPIC and LB_FLAG_PAPER_LITERAL exclude each other");
+    if ((flags & LB_FLAG_ENTROPIC_PATH) && !(flags & LB_FLAG_ENTROPIC))
+        return fail(nullptr, LB_ERR_ARG, "lb_init: LB_FLAG_ENTROPIC_PATH needs LB_FLAG_ENTROPIC");
     const Lattice& L = lattice();
     if (theta0 > 0.0 && fabs(theta0 / L.theta0 - 1.0) > 1e-12)
         return fail(nullptr, LB_ERR_THETA0, "lb_init: theta0 differs from sum_i w_i c_ix^2 of the Table I weights");
@@ -237,7 +239,7 @@ lb_status lb_init(lb_ctx** out, lb_grid grid, int velocity_set, double theta0, d
     c->d.plane = grid.nx * grid.ny * grid.nz;
     c->d.rows = 2 * grid.ny * grid.nz;
     c->prec = (int)precision;
-    c->eq = (flags & LB_FLAG_ENTROPIC) ? 2 : (flags & LB_FLAG_PAPER_LITERAL) ? 0 : 1;
+    c->eq = (flags & LB_FLAG_ENTROPIC) ? ((flags & LB_FLAG_ENTROPIC_PATH) ? 3 : 2) : (flags & LB_FLAG_PAPER_LITERAL) ? 0 : 1;
     c->variant = (flags & LB_FLAG_STAGED) ? kKernelStaged : kKernelAuto;
     c->tau = tau;
     c->twobeta = isinf(tau) ? 0.0 : 2.0 / (2.0 * tau + 1.0);
@@ -303,7 +305,7 @@ lb_status lb_sync(lb_ctx* c) {
 
 int lb_step_variant(const lb_ctx* c) {
     if (!c) return -1;
-    if (c->eq == 2) return kKernelDirect1;  // the exact entropic equilibrium runs in k_step only
+    if (c->eq >= 2) return kKernelDirect1;  // the exact entropic equilibrium runs in k_step only
     if (c->sr)  // the stochastic store: the x-pair kernel where it applies, else one node per thread
         return resolve_kernel(c->prec, c->d, kKernelDirect2XL) == kKernelDirect2XL ? kKernelDirect2XL : kKernelDirect1;
     return resolve_kernel(c->prec, c->d, c->variant);
@@ -670,6 +672,10 @@ static lb_status set_wall_columns(lb_ctx* c, const double* params) {
 }
 
 static bool wall_checks(lb_ctx* c) {
+    if (c->eq == 3) {
+        fail(c, LB_ERR_ARG, "lb_set_walls: walls are not combined with the entropic path length");
+        return false;
+    }
     if (c->d.nz < 4) {
         fail(c, LB_ERR_ARG, "lb_set_walls: walls need nz >= 4");
         return false;

@@ -39,7 +39,7 @@ static unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + thre
 cudaError_t launch_step(int prec, int eq, int variant, const void* src, void* dst, const Dims& d,
                         const LaunchConsts& c, double twobeta, int* err, cudaStream_t st) {
     if (prec == kF64) return launch_step_f64(eq, src, dst, d, c, twobeta, err, st);
-    if (eq == 2) return launch_step_entropic(prec, src, dst, d, c, twobeta, err, st);
+    if (eq >= 2) return launch_step_entropic(prec, eq, src, dst, d, c, twobeta, err, st);
     return launch_step_f32(prec, eq == 1, variant, src, dst, d, c, twobeta, err, st);
 }
 
@@ -52,7 +52,7 @@ cudaError_t launch_init(int prec, int eq, void* dst, const Dims& d, const Launch
         using T = typename C::raw_t;
         const unsigned nb = blocks_for(count, 256);
         T* o = static_cast<T*>(dst);
-        if (eq == 2)
+        if (eq >= 2)  // the exact entropic equilibrium (kind 3 adds only the path length)
             k_init<C, 2><<<nb, 256, 0, st>>>(o, d, consts_for<C>(c), c.theta0, q0, count, rho, u, ustride, theta, err);
         else if (eq == 1)
             k_init<C, 1><<<nb, 256, 0, st>>>(o, d, consts_for<C>(c), c.theta0, q0, count, rho, u, ustride, theta, err);

@@ -425,7 +425,7 @@ lb_status lb_batch_init(lb_batch** out, int nsims, const lb_grid* grids, const d
                         unsigned flags, void* cuda_stream) {
     if (!out || nsims < 1 || !grids || !tau) return bfail(nullptr, LB_ERR_ARG, "lb_batch_init: bad argument");
     *out = nullptr;
-    if (flags & LB_FLAG_ENTROPIC)
+    if (flags & (LB_FLAG_ENTROPIC | LB_FLAG_ENTROPIC_PATH))
         return bfail(nullptr, LB_ERR_ARG, "lb_batch_init: the exact entropic equilibrium is a single-grid mode");
     for (int k = 0; k < nsims; ++k) {
         const lb_grid& g = grids[k];

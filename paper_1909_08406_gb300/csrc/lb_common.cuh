@@ -409,6 +409,75 @@ __device__ __forceinline__ void equilibrium_relax_g(const NodeState<typename Cod
 __device__ __forceinline__ double expm1_of(double x) { return expm1(x); }
 __device__ __forceinline__ float expm1_of(float x) { return expm1f(x); }
 
+__device__ __forceinline__ double log1p_of(double x) { return log1p(x); }
+__device__ __forceinline__ float log1p_of(float x) { return log1pf(x); }
+
+// phi(y) = (1 + y) ln(1 + y) - y, the entropy change along the path per unit population.  For
+// |y| < 1/8 its series sum_{n >= 2} (-y)^n / (n (n - 1)) (to y^8 in FP32, y^18 in FP64: below
+// the unit roundoff of y^2 / 2), else the formula (cancellation at most 16 ulp there).
+template <class R>
+__device__ __forceinline__ R path_phi(R y) {
+    constexpr int N = sizeof(R) == 8 ? 18 : 8;
+    if (fabs(y) < R(0.125)) {
+        R s = R(0);
+#pragma unroll
+        for (int n = N; n >= 2; --n) s = fma(s, -y, R(1.0 / (n * (n - 1.0))));
+        return s * y * y;
+    }
+    return (R(1) + y) * log1p_of(y) - y;
+}
+
+// Entropic path length alpha of one node (Sec. "Droplet Collision": the update with alpha beta,
+// alpha such that the H theorem holds, from x_i = f^eq_i / f_i - 1): the nontrivial root of
+// Delta H(alpha) = H(f + alpha (f^eq - f)) - H(f), H = sum_i f_i ln(f_i / w_i).  For an f^eq
+// with the moments of f whose logarithm is a sum of collision invariants (the exact entropic
+// equilibrium: ln(f^eq_i / w_i) = ln rho + X_i), sum_i f_i x_i (1 + ln(f^eq_i / w_i)) vanishes
+// and, with ln(f_i / w_i) = ln(f^eq_i / w_i) - ln(1 + x_i),
+//   Delta H(alpha) = sum_i f_i [phi(alpha x_i) - alpha x_i ln(1 + x_i)],
+//   d/dalpha     = sum_i f_i x_i [ln(1 + alpha x_i) - ln(1 + x_i)],
+// both free of cancellation as x -> 0 (alpha -> 2).  Newton from 2, kept inside (0, alpha_max),
+// alpha_max = min over x_i < 0 of -1/x_i; left of Delta H's minimum it doubles alpha instead.
+// fw[i] = f_i / w_i, lx[i] = ln(1 + x_i).  Returns 2 (plain BGK) when f = f^eq or when Newton
+// does not converge (no root below alpha_max).
+template <class R>
+__device__ __forceinline__ R entropic_path(const Consts<R>& K, const R (&x)[kQ], const R (&lx)[kQ],
+                                           const R (&fw)[kQ]) {
+    constexpr bool kDouble = sizeof(R) == 8;
+    constexpr int MAXIT = kDouble ? 40 : 30;
+    const R tol = kDouble ? R(1e-14) : R(1e-6);
+    R amax = R(0), xmax = R(0);  // amax as 1 / alpha_max = max over i of -x_i
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        amax = fmax(amax, -x[i]);
+        xmax = fmax(xmax, fabs(x[i]));
+    }
+    if (!(xmax > R(0))) return R(2);
+    const bool bounded = amax > R(0);
+    const R alim = bounded ? R(1) / amax : R(0);
+    R a = (!bounded || alim > R(2)) ? R(2) : R(0.5) * alim;
+    bool conv = false;
+#pragma unroll 1
+    for (int it = 0; it < MAXIT; ++it) {
+        R g = R(0), dg = R(0);
+        static_for<kQ>([&](auto I) {
+            const R f = K.w[vel(I).shell] * fw[I], y = a * x[I];
+            g = fma(f, path_phi(y) - y * lx[I], g);
+            dg = fma(f * x[I], log1p_of(y) - lx[I], dg);
+        });
+        R an;
+        if (!(dg > R(0)))
+            an = (!bounded || R(2) * a < alim) ? R(2) * a : R(0.5) * (a + alim);
+        else
+            an = a - g / dg;
+        if (bounded && !(an < alim)) an = R(0.5) * (a + alim);
+        if (!(an > R(0))) an = R(0.5) * a;
+        conv = dg > R(0) && fabs(an - a) <= tol * an;
+        a = an;
+        if (conv) break;
+    }
+    return conv ? a : R(2);
+}
+
 // Exact entropic equilibrium (Eqs. (discreteentropiceq) and
 // (fivelagrangemultipliersystem)) and BGK relaxation of one node.
 //   f^eq_i = w_i rho exp(X_i),  X_i = l0 + l.c_i + l4 (c_i^2 - 3 theta_0),
@@ -422,7 +491,9 @@ __device__ __forceinline__ float expm1_of(float x) { return expm1f(x); }
 // convergence then leaves round-off), and `ok` is cleared if that does not
 // happen within MAXIT steps.  The working value passed on is x_i = tb h^eq_i
 // with h^eq_i = rho expm1(X_i) + (rho - 1).
-template <class Codec, class VGet, class Sink>
+// PATH: the relaxation factor 2 beta becomes alpha beta with the entropic path length alpha of
+// entropic_path (tb and 1 - omb scaled by alpha / 2).
+template <class Codec, bool PATH = false, class VGet, class Sink>
 __device__ __forceinline__ void entropic_relax(const NodeState<typename Codec::R>& st,
                                                const Consts<typename Codec::KS>& K, typename Codec::R tb,
                                                typename Codec::R omb, VGet&& vget, Sink&& sink, bool& ok) {
@@ -529,6 +600,42 @@ __device__ __forceinline__ void entropic_relax(const NodeState<typename Codec::R
         if (conv) break;
     }
     if (!conv) ok = false;
+    if constexpr (PATH) {
+        // h_i and x_i = f^eq_i / f_i - 1 = (h^eq_i - h_i) / (1 + h_i), h^eq = rho expm1(X) + drho
+        auto h_of = [&](auto I) {
+            if constexpr (Codec::stores_f)
+                return vget(I) / K.w[vel(I).shell] - R(1);
+            else
+                return vget(I) * R(1.0 / Codec::kScale);
+        };
+        R x[kQ], lx[kQ], fw[kQ];
+        auto set_x = [&](auto I, R heq) {
+            const R h = h_of(I);
+            fw[I] = R(1) + h;
+            x[I] = (heq - h) / fw[I];
+            lx[I] = log1p_of(x[I]);
+        };
+        set_x(std::integral_constant<int, 0>{}, st.rho * expm1_of(l[0] + l[4] * (K.c2[0] - R(3) * th0)) + st.drho);
+        static_for<20>([&](auto KK) {
+            constexpr int ip = 2 * KK + 1, im = 2 * KK + 2;
+            constexpr Vel c = vel(ip);
+            const R E = l[0] + l[4] * (K.c2[c.shell] - R(3) * th0);
+            R O = R(0);
+            if constexpr (c.x != 0) O += R(0.5 * c.x) * l[1];
+            if constexpr (c.y != 0) O += R(0.5 * c.y) * l[2];
+            if constexpr (c.z != 0) O += R(0.5 * c.z) * l[3];
+            set_x(std::integral_constant<int, ip>{}, st.rho * expm1_of(E + O) + st.drho);
+            set_x(std::integral_constant<int, im>{}, st.rho * expm1_of(E - O) + st.drho);
+        });
+        const R half_alpha = R(0.5) * entropic_path<R>(K, x, lx, fw);
+        const R tba = tb * half_alpha, omba = R(1) - (R(1) - omb) * half_alpha;
+        // relaxation towards h^eq = h + x (1 + h)
+        static_for<kQ>([&](auto I) {
+            const R heq = fma(x[I], fw[I], h_of(I));
+            sink(I, Codec::relax(vget(I), omba, tba * heq, K.w[vel(I).shell], tba));
+        });
+        return;
+    }
     // relaxation towards h^eq = rho expm1(X) + drho
     {
         const R em = expm1_of(l[0] + l[4] * (K.c2[0] - R(3) * th0));
@@ -553,14 +660,15 @@ __device__ __forceinline__ void entropic_relax(const NodeState<typename Codec::R
 }
 
 // Equilibrium kinds: 0 = Eq. (feqGenU3) as printed, 1 = with the momentum
-// projection, 2 = the exact entropic equilibrium (clears `ok` if Newton fails).
+// projection, 2 = the exact entropic equilibrium (clears `ok` if Newton fails),
+// 3 = that equilibrium with the entropic path length (entropic_path).
 template <class Codec, int EQ, class Sink>
 __device__ __forceinline__ void equilibrium_relax(const NodeState<typename Codec::R>& st,
                                                   const Consts<typename Codec::KS>& K, typename Codec::R tb,
                                                   typename Codec::R omb, const typename Codec::R (&v)[kQ], Sink&& sink,
                                                   bool& ok) {
-    if constexpr (EQ == 2)
-        entropic_relax<Codec>(st, K, tb, omb, [&](auto I) { return v[I]; }, sink, ok);
+    if constexpr (EQ == 2 || EQ == 3)
+        entropic_relax<Codec, EQ == 3>(st, K, tb, omb, [&](auto I) { return v[I]; }, sink, ok);
     else
         equilibrium_relax_g<Codec, EQ == 1>(st, K, tb, omb, [&](auto I) { return v[I]; }, sink);
 }

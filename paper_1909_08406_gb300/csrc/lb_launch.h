@@ -87,7 +87,7 @@ cudaError_t launch_step_f64(int eq, const void* src, void* dst, const Dims& d, c
 cudaError_t launch_step_f32(int prec, bool project, int variant, const void* src, void* dst, const Dims& d,
                             const LaunchConsts& c, double twobeta, int* err, cudaStream_t st);
 // The exact-entropic-equilibrium update (FP32 arithmetic, any storage but FP64), k_step only.
-cudaError_t launch_step_entropic(int prec, const void* src, void* dst, const Dims& d, const LaunchConsts& c,
+cudaError_t launch_step_entropic(int prec, int eq, const void* src, void* dst, const Dims& d, const LaunchConsts& c,
                                  double twobeta, int* err, cudaStream_t st);
 
 // Kinetic walls normal to z (lb_walls.cu), one device block per context of

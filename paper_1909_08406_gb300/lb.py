@@ -26,6 +26,7 @@ LB_RD3Q41 = 41
 LB_FLAG_PAPER_LITERAL = 1
 LB_FLAG_STAGED = 2
 LB_FLAG_ENTROPIC = 4
+LB_FLAG_ENTROPIC_PATH = 8
 LB_KERNEL_AUTO, LB_KERNEL_DIRECT1, LB_KERNEL_DIRECT2, LB_KERNEL_DIRECT2R, LB_KERNEL_STAGED, LB_KERNEL_WARPSPEC = -1, 0, 1, 2, 3, 4
 LB_KERNEL_DIRECT2X, LB_KERNEL_DIRECT2XL = 5, 6
 LB_HALO = 2  # halo planes at each end of a padded z slab (lb_halo_pack)
