@@ -183,3 +183,35 @@ def test_plain_c_program_links_and_calls_the_library(L, tmp_path):
     assert theta0 == pytest.approx(oracle.theta0(), rel=1e-15)
     assert wsum == pytest.approx(1.0, abs=1e-15)
     assert b == pytest.approx(1.0 / 3.0, rel=1e-15)
+
+
+def test_entropic_path_flag_rules_on_the_host(L):
+    """LB_FLAG_ENTROPIC_PATH needs LB_FLAG_ENTROPIC, and batches refuse it, before any device work."""
+    from paper_1909_08406_gb300 import lb
+    with pytest.raises(lb.LbError) as e:
+        lb.lb_init((8, 8, 8), tau=0.5, flags=lb.LB_FLAG_ENTROPIC_PATH)
+    assert e.value.status == -1 and "LB_FLAG_ENTROPIC" in str(e.value)
+    with pytest.raises(lb.LbError) as e:
+        lb.lb_batch_init([(8, 8, 8)], [0.6], "f32", flags=lb.LB_FLAG_ENTROPIC | lb.LB_FLAG_ENTROPIC_PATH)
+    assert e.value.status == -1
+
+
+def test_relabel_and_x_period_reject_bad_arguments(L):
+    """sg_relabel and the convolutions check dilations, sizes, aliasing and the x period before
+    launching anything (the pointers below are never dereferenced)."""
+    from paper_1909_08406_gb300 import sg
+    sg._L()
+    a, b = ctypes.c_void_p(4096), ctypes.c_void_p(8192)
+    nat = sg.SgShape(1, 8, 16, 64, 0)
+    assert L.sg_relabel(nat, 64, 1, 3, a, b, None) == -1        # dilation not a power of two
+    assert L.sg_relabel(nat, 64, 1, 16, a, b, None) == -1       # dilation above 8
+    assert L.sg_relabel(nat, 48, 1, 2, a, b, None) == -1        # 3 chunks per voxel
+    assert L.sg_relabel(nat, 64, 1, 2, a, a, None) == -1        # in place
+    assert L.sg_relabel(nat, 64, 1, 2, ctypes.c_void_p(4100), b, None) == -1  # unaligned
+    assert L.sg_relabel(sg.SgShape(1, 6, 16, 64, 0), 64, 1, 4, a, b, None) == -1  # nz % d
+    assert L.sg_relabel(sg.SgShape(1, 8, 16, 32, 0), 64, 1, 2, a, b, None) == -1  # nx != 64
+    for xper in (4, 24, 128, -8):
+        s = sg.SgShape(1, 8, 16, 64, xper)
+        assert L.sg_conv3d_fwd(s, 32, 32, a, b, None, 0, 0, None, None, b, None) == -1, xper
+        assert L.sg_conv3d_fwd_f32(s, 32, 32, a, b, None, b, None) == -1, xper
+        assert L.sg_conv3d_wgrad(s, 32, 32, a, b, b, None, a, None) == -1, xper
